@@ -1,0 +1,326 @@
+"""Pin checks for the CPU oracle, shared by the pin tests and the planted-mistake tests.
+
+Every check compares the oracle with something other than itself: a matrix
+exponential, the exact statevector simulation, an SVD of the exact state, a
+closed-form single-qubit evolution, a symmetry, or an invariant the paper states.
+Each returns the observed error (a float); the callers assert it is small.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg
+
+from instances import make_instance, make_tree_instance, Instance
+from oracle import gtqa_oracle as O
+from oracle import statevector as SV
+
+X = np.array([[0, 1], [1, 0]], dtype=complex)
+Z = np.diag([1.0, -1.0]).astype(complex)
+I2 = np.eye(2, dtype=complex)
+
+
+def gate_vs_expm(seed: int = 0) -> float:
+    """ising_gate / mixing_gate against scipy's expm of the defining Hamiltonians (App. F)."""
+    rng = np.random.default_rng(seed)
+    err = 0.0
+    for _ in range(5):
+        J, ha, hb, t = rng.normal(size=4)
+        Da, Db = rng.integers(1, 4, size=2)
+        H = J * np.kron(Z, Z) + ha / Da * np.kron(Z, I2) + hb / Db * np.kron(I2, Z)
+        U = scipy.linalg.expm(-1j * t * H)
+        W = O.ising_gate(J, ha, hb, int(Da), int(Db), t).reshape(4, 4)
+        err = max(err, np.abs(U - W).max())
+        Ux = scipy.linalg.expm(-1j * t * X)
+        err = max(err, np.abs(Ux - O.mixing_gate(t)).max())
+    return float(err)
+
+
+def statevector_vs_dense(seed: int = 0) -> float:
+    """The statevector simulator against dense expm products on K4 (n=4)."""
+    rng = np.random.default_rng(seed)
+    n = 4
+    edges = np.array([[0, 1], [0, 2], [0, 3], [1, 2], [1, 3], [2, 3]])
+    J = rng.normal(size=6)
+    h = rng.normal(size=4)
+    K, dt = 3, 0.4
+    ops = lambda P, q: np.kron(np.kron(np.eye(2 ** q), P), np.eye(2 ** (n - q - 1)))
+    H = sum(J[e] * ops(Z, a) @ ops(Z, b) for e, (a, b) in enumerate(edges)) + sum(h[a] * ops(Z, a) for a in range(n))
+    HX = sum(ops(X, a) for a in range(n))
+    psi = np.full(2 ** n, 2 ** (-n / 2), dtype=complex)
+    for k in range(1, K + 1):
+        tau = k / K
+        psi = scipy.linalg.expm(-1j * dt * (1 - tau) * HX) @ (scipy.linalg.expm(-1j * dt * tau * H) @ psi)
+    psi2, _ = SV.evolve(n, edges, J, h, K, dt)
+    return float(np.abs(psi - psi2.reshape(-1)).max())
+
+
+def _overlap_err(a: np.ndarray, b: np.ndarray) -> float:
+    a = a.reshape(-1)
+    b = b.reshape(-1)
+    return float(abs(1 - abs(np.vdot(a, b)) / (np.linalg.norm(a) * np.linalg.norm(b))) +
+                 abs(np.linalg.norm(a) - np.linalg.norm(b)))
+
+
+def gates_exact_without_truncation(inst: Instance, layers: int = 2, dt: float = 0.4) -> float:
+    """Trotter layers (simple update, App. E) with no truncation reproduce the
+    exact state, up to a global phase (no BP, no regauge)."""
+    st = O.plus_state(inst.n, inst.edges)
+    K = 5
+    for k in range(1, layers + 1):
+        tZ, tX = O.schedule(k, K, dt)
+        O.trotter_layer(st, inst.colour, inst.J, inst.h, tZ, tX, chi=1 << 12)
+    psi, _ = SV.evolve(inst.n, inst.edges, inst.J, inst.h, K, dt, layers=layers, record=False)
+    return _overlap_err(O.to_statevector(st), psi)
+
+
+def gtqa_tree_exact(seed: int, n: int = 10, K: int = 6, dt: float = 0.3) -> dict:
+    """On trees BP is exact (Sec. II B), so GTQA marginals without truncation equal
+    the exact ones at every layer; lambda equals the edge-cut Schmidt values
+    (Sec. II C); the contracted network equals the exact state."""
+    inst = make_tree_instance(n, seed)
+    st = O.plus_state(inst.n, inst.edges)
+    psi, rhos = SV.evolve(inst.n, inst.edges, inst.J, inst.h, K, dt)
+    rho_err = 0.0
+    for k in range(1, K + 1):
+        tZ, tX = O.schedule(k, K, dt)
+        st, info = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 256, 1e-13, 100)
+        rho_err = max(rho_err, float(np.abs(O.reduced_density_matrices(st) - rhos[k - 1]).max()))
+    # Schmidt values across each edge cut
+    lam_err = 0.0
+    for e in range(st.m):
+        a, b = inst.edges[e]
+        side = _component(inst, e, int(a))
+        sv = SV.schmidt_values(psi, side)
+        sv = sv / np.linalg.norm(sv)
+        d = st.lam[e].size
+        top = sv[:d]
+        lam_err = max(lam_err, float(np.abs(np.sort(st.lam[e])[::-1][:8] - top[:8]).max()))
+    return {"rho": rho_err, "lam": lam_err, "state": _overlap_err(O.to_statevector(st), psi)}
+
+
+def _component(inst: Instance, e_cut: int, start: int):
+    adj = {a: [] for a in range(inst.n)}
+    for e, (u, v) in enumerate(inst.edges.tolist()):
+        if e != e_cut:
+            adj[u].append(v)
+            adj[v].append(u)
+    seen = {start}
+    stack = [start]
+    while stack:
+        x = stack.pop()
+        for y in adj[x]:
+            if y not in seen:
+                seen.add(y)
+                stack.append(y)
+    return sorted(seen)
+
+
+def gtqa_loopy_state_exact(seed: int = 0, n: int = 8, layers: int = 2, dt: float = 0.4) -> float:
+    """Full GTQA layers (gates, BP, regauge) on a loopy 3-regular graph with no
+    truncation: the regauge is an exact gauge transformation (App. D), so the
+    contracted network still equals the exact state."""
+    inst = make_instance(n, seed)
+    K = 5
+    st = O.plus_state(inst.n, inst.edges)
+    for k in range(1, layers + 1):
+        tZ, tX = O.schedule(k, K, dt)
+        st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 1 << 12, 1e-13, 200)
+    psi, _ = SV.evolve(inst.n, inst.edges, inst.J, inst.h, K, dt, layers=layers, record=False)
+    return _overlap_err(O.to_statevector(st), psi)
+
+
+def product_state_closed_form(seed: int = 0, n: int = 16, K: int = 12, dt: float = 0.3) -> float:
+    """J = 0: the state stays a product state; each qubit follows the 2x2 evolution
+    prod_k exp(-i t_X X) exp(-i t_Z h_a Z) applied to |+> (closed form)."""
+    inst = make_instance(n, seed)
+    inst.J[:] = 0.0
+    st = O.plus_state(inst.n, inst.edges)
+    err = 0.0
+    for k in range(1, K + 1):
+        tZ, tX = O.schedule(k, K, dt)
+        st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 4, 1e-13, 100)
+        rho = O.reduced_density_matrices(st)
+        for a in range(n):
+            v = np.array([1, 1], dtype=complex) / np.sqrt(2)
+            for q in range(1, k + 1):
+                tz, tx = O.schedule(q, K, dt)
+                v = np.diag(np.exp(-1j * tz * inst.h[a] * np.array([1, -1]))) @ v
+                v = np.array([[np.cos(tx), -1j * np.sin(tx)], [-1j * np.sin(tx), np.cos(tx)]]) @ v
+            err = max(err, float(np.abs(rho[a] - np.outer(v, v.conj())).max()))
+        err = max(err, float(max(l.size for l in st.lam) - 1))
+    return err
+
+
+def z2_symmetry(seed: int = 0, n: int = 16, K: int = 20, dt: float = 0.1, chi: int = 4) -> float:
+    """h = 0: prod_a X_a commutes with H(t) and |+>^N is symmetric, so <Z_a> = 0 exactly."""
+    inst = make_instance(n, seed, h_std=0.0)
+    st = O.plus_state(inst.n, inst.edges)
+    err = 0.0
+    for k in range(1, K + 1):
+        tZ, tX = O.schedule(k, K, dt)
+        st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, chi, 1e-12, 100)
+        rho = O.reduced_density_matrices(st)
+        err = max(err, float(np.abs(rho[:, 0, 0].real - 0.5).max()))
+    return err
+
+
+def loopy_state(seed: int = 0, n: int = 16, layers: int = 5, K: int = 20, dt: float = 0.1, chi: int = 4):
+    inst = make_instance(n, seed)
+    st = O.plus_state(inst.n, inst.edges)
+    for k in range(1, layers + 1):
+        tZ, tX = O.schedule(k, K, dt)
+        st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, chi, 1e-13, 100)
+    return inst, st
+
+
+def after_gates(seed: int = 0, n: int = 16, layers: int = 5, K: int = 20, dt: float = 0.1, chi: int = 4):
+    """A loopy state right after a Trotter layer (Vidal gauge broken by truncation)."""
+    inst, st = loopy_state(seed, n, layers, K, dt, chi)
+    tZ, tX = O.schedule(layers + 1, K, dt)
+    O.trotter_layer(st, inst.colour, inst.J, inst.h, tZ, tX, chi)
+    return inst, st
+
+
+def bp_gauge_covariance(seed: int = 0) -> float:
+    """Inserting an invertible G and G^{-T} on every bond of T leaves the network (and
+    so the BP fixed point's marginals) unchanged: checks the index placement of
+    Eq. (local_consistency) and Eq. (partial_dens)."""
+    inst, st = after_gates(seed)
+    rng = np.random.default_rng(seed)
+    T = O.symmetric_gauge(st)
+    T2 = [t.copy() for t in T]
+    for e in range(st.m):
+        d = st.lam[e].size
+        G = np.eye(d) + 0.3 * (rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d)))
+        Gi = np.linalg.inv(G).T
+        for x, M in ((int(inst.edges[e][0]), G), (int(inst.edges[e][1]), Gi)):
+            s = st.slot(x, e)
+            g = np.moveaxis(T2[x], 1 + s, -1) @ M
+            T2[x] = np.moveaxis(g, -1, 1 + s)
+    A = {}
+    for e in range(st.m):
+        d = st.lam[e].size
+        for dd in (0, 1):
+            A[(e, dd)] = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    m1, _, _ = O.bp(st, T, O.random_messages(st, A), 1e-14, 400)
+    m2, _, _ = O.bp(st, T2, O.random_messages(st, A), 1e-14, 400)
+    r1 = O.reduced_density_matrices(st, T, m1)
+    r2 = O.reduced_density_matrices(st, T2, m2)
+    return float(np.abs(r1 - r2).max())
+
+
+def bp_invariants(seed: int = 0) -> float:
+    """Messages are Hermitian, positive semi-definite and of unit trace (Sec. II B, App. B)."""
+    inst, st = after_gates(seed)
+    T = O.symmetric_gauge(st)
+    msgs, _, _ = O.bp(st, T, O.reconstructed_messages(st), 1e-12, 100)
+    err = 0.0
+    for mm in msgs.values():
+        err = max(err, float(np.abs(mm - mm.conj().T).max()))
+        err = max(err, float(abs(np.trace(mm) - 1)))
+        err = max(err, float(max(0.0, -np.linalg.eigvalsh(0.5 * (mm + mm.conj().T)).min())))
+    return err
+
+
+def flooding_vs_sequential(seed: int = 0) -> float:
+    """Both schedules solve the same fixed-point equation, Eq. (local_consistency)."""
+    inst, st = after_gates(seed)
+    T = O.symmetric_gauge(st)
+    m1, _, _ = O.bp(st, T, O.reconstructed_messages(st), 1e-14, 300, "flooding")
+    m2, _, _ = O.bp(st, T, O.reconstructed_messages(st), 1e-14, 300, "sequential")
+    return float(np.abs(O.reduced_density_matrices(st, T, m1) - O.reduced_density_matrices(st, T, m2)).max())
+
+
+def warm_start_fixed_point(seed: int = 0) -> float:
+    """After regauging (R = 0) the warm-start messages solve Eq. (local_consistency):
+    one BP sweep changes them by nothing (Sec. II C)."""
+    inst, st = loopy_state(seed)
+    T = O.symmetric_gauge(st)
+    _, it, hist = O.bp(st, T, O.reconstructed_messages(st), 0.0, 1)
+    return float(hist[0])
+
+
+def residual_after_regauge(seed: int = 0) -> float:
+    """The Vidal gauge found from converged messages has R = 0 (App. C-D)."""
+    inst, st = loopy_state(seed)
+    return O.local_orthogonality_residual(st)
+
+
+def regauge_is_exact_gauge_transform(seed: int = 0) -> float:
+    """Algorithm "Vidal gauge finding" changes only the gauge: the contracted state
+    is unchanged (loopy 3-regular graph, n = 8, truncated state)."""
+    inst = make_instance(8, seed)
+    st = O.plus_state(inst.n, inst.edges)
+    K, dt = 10, 0.3
+    for k in range(1, 4):
+        tZ, tX = O.schedule(k, K, dt)
+        st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 2, 1e-13, 200)
+    tZ, tX = O.schedule(4, K, dt)
+    O.trotter_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 2)
+    before = O.to_statevector(st)
+    T = O.symmetric_gauge(st)
+    msgs, _, _ = O.bp(st, T, O.reconstructed_messages(st), 1e-14, 300)
+    new = O.vidal_gauge(st, T, msgs)
+    after = O.to_statevector(new)
+    return float(np.abs(before - after).max() / np.abs(before).max())
+
+
+def truncation_frobenius(seed: int = 0) -> float:
+    """Truncating the smallest Schmidt values of one edge of a tree in the Vidal
+    gauge moves the state by exactly sqrt(sum of dropped lambda^2) (Sec. II C)."""
+    inst = make_tree_instance(10, seed)
+    st = O.plus_state(inst.n, inst.edges)
+    K, dt = 6, 0.3
+    for k in range(1, 5):
+        tZ, tX = O.schedule(k, K, dt)
+        st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 256, 1e-13, 100)
+    psi = O.to_statevector(st)
+    err = 0.0
+    for e in range(st.m):
+        d = st.lam[e].size
+        if d < 3:
+            continue
+        cut = O.VidalState(st.n, st.edges, st.inc, [g.copy() for g in st.Gamma], [l.copy() for l in st.lam])
+        dropped = st.lam[e][d - 1:]
+        O.truncate(cut, e, d - 1)
+        dpsi = np.linalg.norm(psi - O.to_statevector(cut))
+        err = max(err, abs(dpsi - np.sqrt(np.sum(dropped ** 2))))
+    return float(err)
+
+
+def single_edge_exact(seed: int = 0) -> float:
+    """n = 2, one edge: the Schmidt rank is at most 2, so GTQA is exact at chi = 2."""
+    rng = np.random.default_rng(seed)
+    edges = np.array([[0, 1]])
+    J = rng.normal(size=1)
+    h = rng.normal(size=2)
+    colour = np.zeros(1, dtype=np.int32)
+    K, dt = 10, 0.5
+    st = O.plus_state(2, edges)
+    psi, rhos = SV.evolve(2, edges, J, h, K, dt)
+    err = 0.0
+    for k in range(1, K + 1):
+        tZ, tX = O.schedule(k, K, dt)
+        st, _ = O.gtqa_layer(st, colour, J, h, tZ, tX, 2, 1e-13, 100)
+        err = max(err, float(np.abs(O.reduced_density_matrices(st) - rhos[k - 1]).max()))
+    return err
+
+
+def trace_distance_band(seeds=(0, 1, 2), n: int = 14, T: float = 20.0, dt: float = 0.2, chi: int = 4) -> float:
+    """Eq. (error): qubit- and time-averaged trace distance between BP and exact
+    marginals.  The paper reports 1e-3 .. a few 1e-2 at N = 14..26, T = 20, chi = 4."""
+    K = int(round(T / dt))
+    errs = []
+    for s in seeds:
+        inst = make_instance(n, s)
+        st = O.plus_state(inst.n, inst.edges)
+        _, rhos = SV.evolve(inst.n, inst.edges, inst.J, inst.h, K, dt)
+        tot = 0.0
+        for k in range(1, K + 1):
+            tZ, tX = O.schedule(k, K, dt)
+            st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, chi, 1e-10, 100)
+            rho = O.reduced_density_matrices(st)
+            for a in range(n):
+                tot += O.trace_norm(rho[a] - rhos[k - 1][a])
+        errs.append(dt / (2 * T * n) * tot)
+    return float(np.mean(errs))

@@ -1,0 +1,143 @@
+"""Pins of the CPU oracle against the paper's exact statements and independent routes.
+
+Each test names the passage of arXiv:2409.12240 that fixes the expected value.
+"""
+import numpy as np
+import pytest
+
+import oracle_pins as P
+from instances import make_instance, make_tree_instance
+from oracle import gtqa_oracle as O
+
+
+def test_gates_match_matrix_exponentials():
+    # App. F: U_Z factors exp(-i t (J ZZ + h/D Z + h/D Z)) and U_X factors exp(-i t X)
+    assert P.gate_vs_expm() < 1e-14
+
+
+def test_ising_gate_has_operator_schmidt_rank_two():
+    # A diagonal two-qubit gate splits into two single-qubit terms (App. E raises d_ab to at most 2 d_ab)
+    W = O.ising_gate(0.7, -0.3, 1.1, 3, 2, 0.9)
+    M = W.transpose(0, 2, 1, 3).reshape(4, 4)
+    s = np.linalg.svd(M, compute_uv=False)
+    assert np.sum(s > 1e-12 * s[0]) == 2
+
+
+def test_statevector_matches_dense_exponentials():
+    assert P.statevector_vs_dense() < 1e-12
+
+
+def test_schedule_reading():
+    # Eq. (discretizatoion), reading R1: s(t) = 1 - t/T sampled at k dt
+    assert O.schedule(20, 20, 0.1) == pytest.approx((0.1, 0.0))
+    tz, tx = O.schedule(1, 20, 0.1)
+    assert tz == pytest.approx(0.005) and tx == pytest.approx(0.095)
+
+
+@pytest.mark.parametrize("kind,n,layers", [("tree", 10, 4), ("loopy", 6, 2), ("loopy", 8, 1)])
+def test_simple_update_without_truncation_is_exact(kind, n, layers):
+    # App. E: absorbing lambda's and dividing them back out is an exact rewrite
+    inst = make_tree_instance(n, 1) if kind == "tree" else make_instance(n, 1)
+    assert P.gates_exact_without_truncation(inst, layers=layers) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tree_marginals_schmidt_values_and_state_are_exact(seed):
+    # Sec. II B: BP is exact on trees; Sec. II C: lambda are the Schmidt coefficients
+    r = P.gtqa_tree_exact(seed)
+    assert r["rho"] < 1e-10 and r["lam"] < 1e-10 and r["state"] < 1e-10
+
+
+def test_loopy_gtqa_state_exact_without_truncation():
+    # App. D: the regauge is a gauge transformation; App. E: exact without truncation
+    assert P.gtqa_loopy_state_exact(0, n=6, layers=2) < 1e-12
+    assert P.gtqa_loopy_state_exact(1, n=8, layers=1) < 1e-12
+
+
+def test_product_state_closed_form():
+    # J = 0: each qubit evolves alone under exp(-i t_X X) exp(-i t_Z h Z) (App. F)
+    assert P.product_state_closed_form() < 1e-12
+
+
+def test_z2_symmetric_instance_has_zero_magnetisation():
+    # h = 0: prod X commutes with H(t) and |+>^N is symmetric (Sec. III A, App. F)
+    assert P.z2_symmetry() < 1e-10
+
+
+def test_bp_marginals_are_gauge_covariant():
+    # Eq. (local_consistency) and Eq. (partial_dens) contract ket with ket, bra with bra
+    assert P.bp_gauge_covariance() < 1e-10
+
+
+def test_messages_hermitian_psd_unit_trace():
+    # Sec. II B, App. B: messages are Hermitian PSD, normalised to unit trace
+    assert P.bp_invariants() < 1e-12
+
+
+def test_flooding_and_sequential_reach_same_fixed_point():
+    # App. B: both schedules iterate the same fixed-point equation
+    assert P.flooding_vs_sequential() < 1e-10
+
+
+def test_warm_start_is_fixed_point_after_regauge():
+    # Sec. II C: for R = 0 the reconstructed messages satisfy Eq. (local_consistency)
+    assert P.warm_start_fixed_point() < 1e-10
+
+
+def test_residual_zero_after_regauge():
+    # App. C-D: the Vidal gauge from converged messages has R = 0
+    assert P.residual_after_regauge() < 1e-9
+
+
+def test_regauge_changes_only_the_gauge():
+    assert P.regauge_is_exact_gauge_transform() < 1e-12
+
+
+def test_truncation_error_is_frobenius_norm_of_dropped_lambda():
+    # Sec. II C: eps_ab = sqrt(sum_{j >= chi} lambda^2) on trees in the Vidal gauge
+    assert P.truncation_frobenius() < 1e-12
+
+
+def test_two_qubit_instance_exact():
+    assert P.single_edge_exact() < 1e-12
+
+
+def test_rounding_rule_and_objective():
+    # Eq. (rounding_rule) with reading R9, Eq. (objective_function)
+    rho = np.zeros((3, 2, 2), dtype=complex)
+    rho[:, 0, 0] = [0.9, 0.5, 0.1]
+    assert list(O.rounding(rho)) == [1, -1, -1]
+    edges = np.array([[0, 1], [1, 2]])
+    assert O.objective(edges, np.array([1.0, -2.0]), np.array([0.5, 0.0, -1.0]), [1, -1, 1]) == pytest.approx(-1 + 2 + 0.5 - 1)
+
+
+def test_trace_norm_and_hermitian_sqrt():
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(5, 5)) + 1j * rng.normal(size=(5, 5))
+    H = A + A.conj().T
+    assert O.trace_norm(H) == pytest.approx(np.abs(np.linalg.eigvalsh(H)).sum())
+    m = A @ A.conj().T
+    sq, isq = O.hermitian_sqrt(m)
+    assert np.abs(sq @ sq - m).max() < 1e-12
+    assert np.abs(isq @ m @ isq - np.eye(5)).max() < 1e-10
+
+
+def test_padded_round_trip():
+    inst, st = P.loopy_state(0, n=16, layers=3)
+    G, L = O.to_padded(st, 4)
+    st2 = O.from_padded(st.n, st.edges, G, L)
+    for a in range(st.n):
+        assert np.array_equal(st.Gamma[a], st2.Gamma[a])
+    tree = make_tree_instance(12, 0)
+    s3 = O.plus_state(tree.n, tree.edges)
+    G, L = O.to_padded(s3, 4)
+    assert G.shape == (12, 2, 4, 4, 4)
+    s4 = O.from_padded(tree.n, tree.edges, G, L)
+    assert all(np.array_equal(a, b) for a, b in zip(s3.Gamma, s4.Gamma))
+
+
+@pytest.mark.slow
+def test_trace_distance_error_in_paper_band():
+    # Eq. (error), Fig. 4(b): 1e-3 .. a few 1e-2 for N = 14, T = 20, chi = 4 (sanity band)
+    e = P.trace_distance_band(seeds=(0, 1))
+    assert 1e-4 < e < 5e-2
