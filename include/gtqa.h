@@ -1,0 +1,175 @@
+/*
+ * gtqa.h -- C ABI of the GB300 graph tensor-network quantum annealer (GTQA) hot path.
+ *
+ * Method: arXiv:2409.12240, "Large-scale quantum annealing simulation with tensor
+ * networks and belief propagation".  One annealing layer is
+ *   (1) the Trotterised interaction layer U_Z: one two-qubit gate per edge, applied
+ *       by the simple update with truncation back to bond dimension chi
+ *       (App. E, App. D Algorithm "Truncation", App. F Eq. (discretizatoion));
+ *   (2) the mixing layer U_X: one single-qubit gate per vertex (Sec. II D);
+ *   (3) belief propagation on the symmetric-gauge network from warm-start
+ *       messages (Sec. II C Eq. (symmetric_gauge), Eq. (reconstructed_messages);
+ *       App. B Algorithm "Belief propagation", flooding schedule);
+ *   (4) Vidal gauge finding from the messages (App. D Algorithm "Vidal gauge finding");
+ * plus single-qubit reduced density matrices and the sign read-out
+ * (Eq. (partial_dens), Eq. (bp_approx), Eq. (rounding_rule)).
+ *
+ * Conventions shared by every call:
+ *  - Vertices 0..n-1, edges 0..m-1 given as pairs (u, v); u is the edge's "first"
+ *    endpoint.  Degree <= 3.  A vertex's bond slots are its incident edges in
+ *    ascending edge id; missing slots (degree < 3) are phantom bonds of dimension 1.
+ *  - Bond storage is padded to CHI = smallest of {2, 4, 8} >= chi; entries beyond a
+ *    bond's current dimension are exactly zero.
+ *  - Gamma layout: complex128 interleaved (re, im) array [n][2][CHI][CHI][CHI],
+ *    index (i, j_slot0, j_slot1, j_slot2); lambda: float64 [m][CHI], descending;
+ *    messages: complex128 [2m][CHI][CHI], row 2e holds m_{u->v}, row 2e+1 holds
+ *    m_{v->u} for edge e = (u, v); m[j][j'] pairs j with the ket, j' with the bra.
+ *  - Physical index i = 0 is |0> (Z = +1, x = +1), i = 1 is |1> (Sec. III A).
+ *  - Pointers named *_out or taking arrays may be host or device memory; the library
+ *    detects which with cudaPointerGetAttributes.  The caller owns every array it
+ *    passes; inputs are copied before the call returns.
+ *  - All device work is ordered on the stream given in gtqa_options.cuda_stream.
+ *    Calls that return values to the host synchronise that stream.
+ *  - Every call returns GTQA_OK (0) or an error code.  Errors other than
+ *    GTQA_ERR_INVALID_ARG and GTQA_ERR_NOT_CONVERGED are sticky: the state refuses
+ *    further work until gtqa_destroy.  A state is not thread-safe.
+ */
+#ifndef GTQA_H
+#define GTQA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GTQA_OK 0
+#define GTQA_ERR_INVALID_ARG 1   /* bad size, index, degree > 3, duplicate edge, bad colouring, NaN input */
+#define GTQA_ERR_NOT_CONVERGED 2 /* BP hit max_iter before dist/|E| < tol; state and outputs valid */
+#define GTQA_ERR_NUMERIC 3       /* NaN or Inf detected on the device */
+#define GTQA_ERR_OOM 4           /* device allocation failed */
+#define GTQA_ERR_CUDA 5          /* a CUDA runtime call failed */
+#define GTQA_ERR_TIMEOUT 6       /* a bounded device-side wait gave up */
+#define GTQA_ERR_UNSUPPORTED 7   /* chi or precision not built into this library */
+
+/* arithmetic modes */
+#define GTQA_FP64 0   /* complex128 everywhere */
+#define GTQA_MIXED 1  /* complex64 tensors and BP contractions; FP64 QR/SVD, gauge roots, normalisation */
+
+/* flags of gtqa_bp_sweep */
+#define GTQA_BP_WARM_START 1u  /* start from m_{a->b} = diag(lambda_ab)/sum(lambda_ab) (Eq. reconstructed_messages) */
+#define GTQA_BP_REGAUGE 2u     /* afterwards run Vidal gauge finding (App. D) */
+#define GTQA_BP_DEFAULT 3u
+
+typedef struct gtqa_state gtqa_state;
+
+typedef struct gtqa_options {
+    int32_t precision;   /* GTQA_FP64 or GTQA_MIXED */
+    int32_t reserved0;   /* must be 0 */
+    double svd_cutoff;   /* singular values <= svd_cutoff * s_0 are dropped; <= 0 selects 1e-14 */
+    double eig_cutoff;   /* message eigenvalues <= eig_cutoff * w_max count as zero; <= 0 selects 1e-13 */
+    void* cuda_stream;   /* cudaStream_t for all work; NULL selects the legacy default stream */
+} gtqa_options;
+
+typedef struct gtqa_stats_t {
+    int64_t layers;          /* gtqa_trotter_layer calls completed */
+    int64_t gates;           /* two-qubit gates applied (all instances) */
+    int32_t last_bp_iters;   /* sweeps run by the last gtqa_bp_sweep (max over instances) */
+    int32_t not_converged;   /* instances that reached max_iter in the last gtqa_bp_sweep */
+    double last_bp_dist;     /* dist/|E| after the last sweep (max over instances), App. B */
+    double discarded_weight; /* sum over gates of sum_{dropped} s^2 / sum s^2 */
+    double log_fidelity;     /* sum over gates of log f, f = (1 - discarded)^2, Eq. (gate_fidelity) */
+} gtqa_stats_t;
+
+/* Fill *opt with defaults: FP64, default cut-offs, default stream. */
+void gtqa_options_init(gtqa_options* opt);
+
+/*
+ * Create the state |+>^N (all bond dimensions 1, Sec. III A) of one problem instance.
+ *   n, m       vertices and edges
+ *   edges      host int32 [m][2]; 0 <= u, v < n, u != v, no repeated pair, degree <= 3
+ *   colour     host int32 [m] proper edge colouring (each colour a matching), or NULL
+ *              for the library's own Misra-Gries colouring (<= Delta + 1 colours).
+ *              Gates run colour by colour, ascending (the paper leaves the order open).
+ *   J, h       host float64 couplings [m] and fields [n] of Eq. (objective_function)
+ *   chi        maximal bond dimension, 1 <= chi <= 8
+ *   opt        options or NULL for defaults
+ *   out        receives the new state; *out is NULL on failure
+ */
+int gtqa_create(int32_t n, int32_t m, const int32_t* edges, const int32_t* colour,
+                const double* J, const double* h, int32_t chi,
+                const gtqa_options* opt, gtqa_state** out);
+
+/*
+ * Create B independent instances that evolve together (one launch per phase covers
+ * all of them).  Arrays are concatenations over instances: n[B], m[B]; edges (local
+ * vertex ids per instance) sum(m) pairs; colour sum(m) or NULL; J sum(m); h sum(n).
+ * BP convergence is tracked per instance: dist_b/|E_b| < tol.
+ */
+int gtqa_create_batch(int32_t B, const int32_t* n, const int32_t* m, const int32_t* edges,
+                      const int32_t* colour, const double* J, const double* h, int32_t chi,
+                      const gtqa_options* opt, gtqa_state** out);
+
+/*
+ * One Trotter layer U_X(t_X) U_Z(t_Z) with t_Z = dt * tau and t_X = dt * (1 - tau)
+ * (App. F Eq. (discretizatoion); tau = k/K is the Ising weight of layer k).
+ * Each edge gate exp(-i t_Z (J Z_a Z_b + h_a/D_a Z_a + h_b/D_b Z_b)) is applied by the
+ * simple update (App. E) and truncated to chi (App. D "Truncation"); then
+ * exp(-i t_X X) acts on every vertex (Sec. II D).  Asynchronous.
+ */
+int gtqa_trotter_layer(gtqa_state* s, double tau, double dt);
+
+/*
+ * Belief propagation on T_a = Gamma_a prod lambda^{1/2} (Eq. (symmetric_gauge)),
+ * flooding schedule, Eq. (local_consistency) with unit-trace normalisation, until
+ * dist/|E| < tol or max_iter sweeps (App. B).  flags: GTQA_BP_WARM_START starts from
+ * the reconstructed messages, otherwise from the state's current messages;
+ * GTQA_BP_REGAUGE then applies Vidal gauge finding (App. D), which rewrites Gamma
+ * and lambda.  iters_out / dist_out (nullable host pointers) receive the sweeps run
+ * and the final dist/|E| (max over instances).  Synchronises the stream.
+ * Returns GTQA_ERR_NOT_CONVERGED if some instance reached max_iter.
+ */
+int gtqa_bp_sweep(gtqa_state* s, double tol, int32_t max_iter, uint32_t flags,
+                  int32_t* iters_out, double* dist_out);
+
+/* Vidal gauge finding (App. D) from the state's current messages.  Asynchronous. */
+int gtqa_regauge(gtqa_state* s);
+
+/*
+ * Single-qubit reduced density matrices rho_a = sum Gamma Gamma^* prod_b lambda_ba^2 / tr
+ * (Eq. (partial_dens) with the environment of Eq. (bp_approx) from the warm-start
+ * messages of the current Vidal-gauge state) and the read-out of Eq. (rounding_rule).
+ *   rho_out   complex128 [n][2][2] interleaved (host or device)
+ *   sign_out  int8 [n] (+1 / -1), or NULL
+ */
+int gtqa_marginals(gtqa_state* s, double* rho_out, int8_t* sign_out);
+
+/* Counters accumulated since creation (see gtqa_stats_t).  Synchronises the stream. */
+int gtqa_stats(gtqa_state* s, gtqa_stats_t* out);
+
+/*
+ * Copy the state out (complex128 Gamma, float64 lambda, complex128 messages in the
+ * layouts above; any pointer may be NULL to skip that array) or overwrite it (set:
+ * every pointer required; lambda must be >= 0 and zero exactly beyond each bond's
+ * dimension).  Used to start the library and a reference from identical states.
+ */
+int gtqa_get_state(gtqa_state* s, double* gamma_out, double* lambda_out, double* messages_out);
+int gtqa_set_state(gtqa_state* s, const double* gamma, const double* lambda, const double* messages);
+
+/* Sizes: total vertices and edges, storage bond dimension CHI, number of colours. */
+int gtqa_sizes(const gtqa_state* s, int64_t* n, int64_t* m, int32_t* chi_storage, int32_t* n_colours);
+
+/* Host-only: the library's Misra-Gries edge colouring (<= Delta + 1 colours). */
+int gtqa_edge_colouring(int32_t n, int32_t m, const int32_t* edges, int32_t* colour_out,
+                        int32_t* n_colours_out);
+
+/* Static description of an error code. */
+const char* gtqa_strerror(int code);
+
+/* Release all device and host memory of s; NULL is allowed. */
+void gtqa_destroy(gtqa_state* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GTQA_H */

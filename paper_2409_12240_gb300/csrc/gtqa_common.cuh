@@ -1,0 +1,173 @@
+// Small device-side toolkit shared by the GTQA kernels: complex arithmetic,
+// thread-team synchronisation, butterfly reductions and the batched one-sided
+// Jacobi SVD used for every small matrix decomposition of the method.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gtqa {
+
+// ---------------------------------------------------------------------------
+// complex numbers over float or double
+// ---------------------------------------------------------------------------
+template <typename R>
+struct __align__(sizeof(R) * 2) C {
+    R x, y;
+};
+using cd = C<double>;
+using cf = C<float>;
+
+template <typename R> __device__ __forceinline__ C<R> cmk(R a, R b) { return C<R>{a, b}; }
+template <typename R> __device__ __forceinline__ C<R> operator+(C<R> a, C<R> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename R> __device__ __forceinline__ C<R> operator-(C<R> a, C<R> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename R> __device__ __forceinline__ C<R> operator*(C<R> a, C<R> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename R> __device__ __forceinline__ C<R> operator*(R s, C<R> a) { return {s * a.x, s * a.y}; }
+template <typename R> __device__ __forceinline__ C<R> conj(C<R> a) { return {a.x, -a.y}; }
+template <typename R> __device__ __forceinline__ R norm2(C<R> a) { return a.x * a.x + a.y * a.y; }
+// acc + a * b
+template <typename R> __device__ __forceinline__ C<R> cfma(C<R> a, C<R> b, C<R> acc) {
+    acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+    return acc;
+}
+// acc + conj(a) * b
+template <typename R> __device__ __forceinline__ C<R> cfmac(C<R> a, C<R> b, C<R> acc) {
+    acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+    return acc;
+}
+template <typename To, typename From> __device__ __forceinline__ C<To> ccast(C<From> a) {
+    return C<To>{(To)a.x, (To)a.y};
+}
+
+// ---------------------------------------------------------------------------
+// thread groups: G contiguous lanes inside one warp, G a power of two <= 32
+// ---------------------------------------------------------------------------
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if constexpr (G >= 32) {
+        return 0xffffffffu;
+    } else {
+        const unsigned lane = threadIdx.x & 31u;
+        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    }
+}
+
+// Butterfly sum over aligned groups of G lanes.  Every lane ends with the same
+// bits: at each level a lane adds a + b while its partner adds b + a.
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v, unsigned mask) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off);
+    return v;
+}
+
+// Synchronisation policy for a group that lives inside one warp.
+struct WarpGroup {
+    unsigned mask;
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+    __device__ __forceinline__ bool any(int p) const { return __any_sync(mask, p) != 0; }
+};
+
+// Synchronisation policy for a group that is the whole thread block.
+struct BlockGroup {
+    int* flag;  // one int of shared memory
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ bool any(int p) const {
+        __syncthreads();
+        if (threadIdx.x == 0) *flag = 0;
+        __syncthreads();
+        if (p) atomicOr(flag, 1);
+        __syncthreads();
+        return *flag != 0;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Batched one-sided (Hestenes) Jacobi SVD of an N x N complex matrix.
+//
+// A and V are column-major in shared memory (element (row r, col c) at c*N + r).
+// The group has N*N/2 threads: thread g works on pair k = g / N at row r = g % N,
+// so the N lanes of a pair are contiguous and reduce with shuffles.  Columns are
+// paired by the round-robin (circle) ordering, N/2 disjoint pairs per step and
+// N-1 steps per sweep.  For a pair (p, q) with alpha = |a_p|^2, beta = |a_q|^2,
+// gamma = a_p^H a_q, the 2x2 unitary J = [[c, s e],[-s conj(e), c]] (e = gamma/|gamma|,
+// t = tan(theta) the smaller root of t^2 + 2 zeta t - 1 = 0, zeta = (beta-alpha)/(2|gamma|))
+// makes the rotated columns orthogonal.  Sweeps stop when no pair has
+// |gamma| > tol * sqrt(alpha beta).  On exit A holds U*S (columns unsorted) and
+// V the accumulated right rotations: A_in = (A_out) V^H.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void round_robin_pair(int N, int step, int k, int& p, int& q) {
+    if (k == 0) {
+        p = step;
+        q = N - 1;
+    } else {
+        p = (step + k) % (N - 1);
+        q = (step - k + (N - 1)) % (N - 1);
+    }
+    if (p > q) { int t = p; p = q; q = t; }
+}
+
+template <int N, typename R, typename Group>
+__device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pair_mask,
+                          R tol, int max_sweeps, bool init_v) {
+    const int k = g / N;
+    const int r = g % N;
+    if (init_v) {
+        V[(2 * k) * N + r] = C<R>{(R)((2 * k) == r), (R)0};
+        V[(2 * k + 1) * N + r] = C<R>{(R)((2 * k + 1) == r), (R)0};
+    }
+    grp.sync();
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        int rotated = 0;
+        for (int step = 0; step < N - 1; ++step) {
+            int p, q;
+            round_robin_pair(N, step, k, p, q);
+            C<R> ap = A[p * N + r], aq = A[q * N + r];
+            R alpha = norm2(ap), beta = norm2(aq);
+            C<R> gam = cfmac(ap, aq, C<R>{(R)0, (R)0});
+            alpha = group_sum<N>(alpha, pair_mask);
+            beta = group_sum<N>(beta, pair_mask);
+            gam.x = group_sum<N>(gam.x, pair_mask);
+            gam.y = group_sum<N>(gam.y, pair_mask);
+            const R ag = sqrt(gam.x * gam.x + gam.y * gam.y);
+            if (ag > (R)0 && ag > tol * sqrt(alpha * beta)) {
+                const R zeta = (beta - alpha) / ((R)2 * ag);
+                const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
+                const R c = (R)1 / sqrt((R)1 + t * t);
+                const R s = c * t;
+                const C<R> e = C<R>{gam.x / ag, gam.y / ag};
+                const C<R> se = s * e;
+                const C<R> sec = conj(se);
+                A[p * N + r] = c * ap - sec * aq;
+                A[q * N + r] = se * ap + c * aq;
+                const C<R> vp = V[p * N + r], vq = V[q * N + r];
+                V[p * N + r] = c * vp - sec * vq;
+                V[q * N + r] = se * vp + c * vq;
+                rotated = 1;
+            }
+            grp.sync();
+        }
+        if (!grp.any(rotated)) break;
+    }
+    return sweep;
+}
+
+// Rank of value i among n values, descending, ties by index (used to sort
+// singular values without data movement).
+template <typename R>
+__device__ __forceinline__ int desc_rank(const R* v, int n, int i) {
+    const R x = v[i];
+    int rk = 0;
+    for (int j = 0; j < n; ++j) {
+        const R y = v[j];
+        rk += (y > x) || (y == x && j < i);
+    }
+    return rk;
+}
+
+}  // namespace gtqa

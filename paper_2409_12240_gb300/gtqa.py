@@ -1,0 +1,272 @@
+"""Python binding of the GTQA C ABI (include/gtqa.h).
+
+Argument marshalling only: every step of the annealer runs in libgtqa.so.
+Functions keep the C names.  Arrays may be numpy arrays (host) or CUDA torch
+tensors (device; passed by data_ptr()).  There is no CPU fallback: if the
+library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _build
+
+GTQA_OK = 0
+GTQA_ERR_INVALID_ARG = 1
+GTQA_ERR_NOT_CONVERGED = 2
+GTQA_ERR_NUMERIC = 3
+GTQA_ERR_OOM = 4
+GTQA_ERR_CUDA = 5
+GTQA_ERR_TIMEOUT = 6
+GTQA_ERR_UNSUPPORTED = 7
+
+GTQA_FP64 = 0
+GTQA_MIXED = 1
+
+GTQA_BP_WARM_START = 1
+GTQA_BP_REGAUGE = 2
+GTQA_BP_DEFAULT = 3
+
+EXPORTED = [
+    "gtqa_options_init", "gtqa_create", "gtqa_create_batch", "gtqa_trotter_layer", "gtqa_bp_sweep",
+    "gtqa_regauge", "gtqa_marginals", "gtqa_stats", "gtqa_get_state", "gtqa_set_state", "gtqa_sizes",
+    "gtqa_edge_colouring", "gtqa_strerror", "gtqa_destroy",
+]
+
+
+class gtqa_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("svd_cutoff", ctypes.c_double), ("eig_cutoff", ctypes.c_double),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class gtqa_stats_t(ctypes.Structure):
+    _fields_ = [("layers", ctypes.c_int64), ("gates", ctypes.c_int64), ("last_bp_iters", ctypes.c_int32),
+                ("not_converged", ctypes.c_int32), ("last_bp_dist", ctypes.c_double),
+                ("discarded_weight", ctypes.c_double), ("log_fidelity", ctypes.c_double)]
+
+
+class GTQAError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (code {code})")
+
+
+_LIB: Optional[ctypes.CDLL] = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libgtqa.so (raises if it is missing and build_if_missing is False)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB_PATH
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"GTQA CUDA library not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint32
+    sig = {
+        "gtqa_options_init": (None, [ctypes.POINTER(gtqa_options)]),
+        "gtqa_create": (I32, [I32, I32, P, P, P, P, I32, ctypes.POINTER(gtqa_options), ctypes.POINTER(P)]),
+        "gtqa_create_batch": (I32, [I32, P, P, P, P, P, P, I32, ctypes.POINTER(gtqa_options), ctypes.POINTER(P)]),
+        "gtqa_trotter_layer": (I32, [P, D, D]),
+        "gtqa_bp_sweep": (I32, [P, D, I32, U32, ctypes.POINTER(I32), ctypes.POINTER(D)]),
+        "gtqa_regauge": (I32, [P]),
+        "gtqa_marginals": (I32, [P, P, P]),
+        "gtqa_stats": (I32, [P, ctypes.POINTER(gtqa_stats_t)]),
+        "gtqa_get_state": (I32, [P, P, P, P]),
+        "gtqa_set_state": (I32, [P, P, P, P]),
+        "gtqa_sizes": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "gtqa_edge_colouring": (I32, [I32, I32, P, P, ctypes.POINTER(I32)]),
+        "gtqa_strerror": (ctypes.c_char_p, [I32]),
+        "gtqa_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().gtqa_strerror(int(code)).decode()
+
+
+def _ptr(a) -> Tuple[int, object]:
+    """(address, keep-alive) of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return 0, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_contiguous"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return int(a.data_ptr()), a
+    if not (a.flags["C_CONTIGUOUS"]):
+        raise ValueError("array must be C-contiguous")
+    return int(a.ctypes.data), a
+
+
+def _check(code: int, where: str, allow=(GTQA_OK,)) -> int:
+    if code not in allow:
+        raise GTQAError(code, where)
+    return code
+
+
+def gtqa_options_init(precision: int = GTQA_FP64, svd_cutoff: float = 0.0, eig_cutoff: float = 0.0,
+                      cuda_stream: int = 0) -> gtqa_options:
+    o = gtqa_options()
+    load().gtqa_options_init(ctypes.byref(o))
+    o.precision = precision
+    if svd_cutoff > 0:
+        o.svd_cutoff = svd_cutoff
+    if eig_cutoff > 0:
+        o.eig_cutoff = eig_cutoff
+    o.cuda_stream = cuda_stream or None
+    return o
+
+
+def gtqa_create(n: int, edges, J, h, chi: int, colour=None, opt: Optional[gtqa_options] = None) -> int:
+    """Create a single-instance state; returns the opaque handle (an int)."""
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    col = None if colour is None else np.ascontiguousarray(colour, dtype=np.int32)
+    handle = ctypes.c_void_p()
+    m = int(edges.shape[0]) if edges.size else 0
+    rc = load().gtqa_create(int(n), m, _ptr(edges)[0] or None, _ptr(col)[0] or None, _ptr(J)[0] or None,
+                            _ptr(h)[0], int(chi), ctypes.byref(opt) if opt is not None else None,
+                            ctypes.byref(handle))
+    _check(rc, "gtqa_create")
+    return int(handle.value)
+
+
+def gtqa_create_batch(ns: Sequence[int], edges_list, J_list, h_list, chi: int, colour_list=None,
+                      opt: Optional[gtqa_options] = None) -> int:
+    """Create B instances evolving together; arrays are given per instance."""
+    B = len(ns)
+    n = np.ascontiguousarray(ns, dtype=np.int32)
+    m = np.ascontiguousarray([len(e) for e in edges_list], dtype=np.int32)
+    edges = np.ascontiguousarray(np.concatenate([np.asarray(e, dtype=np.int32).reshape(-1, 2) for e in edges_list]))
+    J = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in J_list]))
+    h = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in h_list]))
+    col = None
+    if colour_list is not None:
+        col = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.int32) for c in colour_list]))
+    handle = ctypes.c_void_p()
+    rc = load().gtqa_create_batch(B, _ptr(n)[0], _ptr(m)[0], _ptr(edges)[0], _ptr(col)[0] or None, _ptr(J)[0],
+                                  _ptr(h)[0], int(chi), ctypes.byref(opt) if opt is not None else None,
+                                  ctypes.byref(handle))
+    _check(rc, "gtqa_create_batch")
+    return int(handle.value)
+
+
+def gtqa_trotter_layer(s: int, tau: float, dt: float) -> None:
+    _check(load().gtqa_trotter_layer(s, float(tau), float(dt)), "gtqa_trotter_layer")
+
+
+def gtqa_bp_sweep(s: int, tol: float, max_iter: int, flags: int = GTQA_BP_DEFAULT,
+                  raise_not_converged: bool = False) -> Tuple[int, float, bool]:
+    """Returns (sweeps run, final dist/|E|, converged)."""
+    it = ctypes.c_int32()
+    d = ctypes.c_double()
+    allow = (GTQA_OK,) if raise_not_converged else (GTQA_OK, GTQA_ERR_NOT_CONVERGED)
+    rc = _check(load().gtqa_bp_sweep(s, float(tol), int(max_iter), int(flags), ctypes.byref(it), ctypes.byref(d)),
+                "gtqa_bp_sweep", allow)
+    return int(it.value), float(d.value), rc == GTQA_OK
+
+
+def gtqa_regauge(s: int) -> None:
+    _check(load().gtqa_regauge(s), "gtqa_regauge")
+
+
+def gtqa_sizes(s: int) -> Tuple[int, int, int, int]:
+    n, m, c, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().gtqa_sizes(s, ctypes.byref(n), ctypes.byref(m), ctypes.byref(c), ctypes.byref(k)), "gtqa_sizes")
+    return int(n.value), int(m.value), int(c.value), int(k.value)
+
+
+def gtqa_marginals(s: int, rho_out=None, sign_out=None):
+    """rho (n, 2, 2) complex128 and signs (n,) int8.  Allocates host arrays if none given."""
+    n, _, _, _ = gtqa_sizes(s)
+    if rho_out is None:
+        rho_out = np.zeros((n, 2, 2), dtype=np.complex128)
+    if sign_out is None:
+        sign_out = np.zeros(n, dtype=np.int8)
+    _check(load().gtqa_marginals(s, _ptr(rho_out)[0], _ptr(sign_out)[0] or None), "gtqa_marginals")
+    return rho_out, sign_out
+
+
+def gtqa_stats(s: int) -> dict:
+    st = gtqa_stats_t()
+    _check(load().gtqa_stats(s, ctypes.byref(st)), "gtqa_stats")
+    return {k: getattr(st, k) for k, _ in gtqa_stats_t._fields_}
+
+
+def gtqa_get_state(s: int):
+    """(Gamma (n,2,CHI,CHI,CHI) complex128, lambda (m,CHI), messages (2m,CHI,CHI) complex128)."""
+    n, m, C, _ = gtqa_sizes(s)
+    G = np.zeros((n, 2, C, C, C), dtype=np.complex128)
+    L = np.zeros((m, C), dtype=np.float64)
+    Mg = np.zeros((2 * m, C, C), dtype=np.complex128)
+    _check(load().gtqa_get_state(s, _ptr(G)[0], _ptr(L)[0], _ptr(Mg)[0]), "gtqa_get_state")
+    return G, L, Mg
+
+
+def gtqa_set_state(s: int, G, L, Mg) -> None:
+    G = np.ascontiguousarray(G, dtype=np.complex128)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    Mg = np.ascontiguousarray(Mg, dtype=np.complex128)
+    _check(load().gtqa_set_state(s, _ptr(G)[0], _ptr(L)[0], _ptr(Mg)[0]), "gtqa_set_state")
+
+
+def gtqa_edge_colouring(n: int, edges) -> Tuple[np.ndarray, int]:
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    col = np.zeros(edges.shape[0], dtype=np.int32)
+    k = ctypes.c_int32()
+    _check(load().gtqa_edge_colouring(int(n), int(edges.shape[0]), _ptr(edges)[0], _ptr(col)[0], ctypes.byref(k)),
+           "gtqa_edge_colouring")
+    return col, int(k.value)
+
+
+def gtqa_destroy(s: int) -> None:
+    if s:
+        load().gtqa_destroy(s)
+
+
+class Annealer:
+    """Convenience owner of one state handle: layer(), marginals(), close()."""
+
+    def __init__(self, n, edges, J, h, chi, colour=None, precision=GTQA_FP64, cuda_stream=0, batch=None):
+        opt = gtqa_options_init(precision=precision, cuda_stream=cuda_stream)
+        if batch is None:
+            self.handle = gtqa_create(n, edges, J, h, chi, colour, opt)
+        else:
+            ns, el, Jl, hl, cl = batch
+            self.handle = gtqa_create_batch(ns, el, Jl, hl, chi, cl, opt)
+
+    def layer(self, tau: float, dt: float, tol: float, max_iter: int) -> Tuple[int, float, bool]:
+        gtqa_trotter_layer(self.handle, tau, dt)
+        return gtqa_bp_sweep(self.handle, tol, max_iter, GTQA_BP_DEFAULT)
+
+    def marginals(self):
+        return gtqa_marginals(self.handle)
+
+    def close(self):
+        gtqa_destroy(self.handle)
+        self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

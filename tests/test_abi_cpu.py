@@ -1,0 +1,85 @@
+"""The C-ABI library loads on a machine without a GPU, exports every declared
+entry point, and rejects invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from instances import check_colouring, make_instance, random_regular_graph
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2409_12240_gb300 import gtqa
+    gtqa.load(build_if_missing=True)
+    return gtqa
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gtqa.h")).read()
+    return sorted(set(re.findall(r"\b(gtqa_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declarations_are_exported(G):
+    lib = ctypes.CDLL(G.library_path())
+    names = _declared()
+    assert len(names) >= 14
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert set(names) == set(G.EXPORTED)
+
+
+def test_strerror_codes(G):
+    for c in range(8):
+        assert len(G.strerror(c)) > 0
+    assert G.strerror(99) == "unknown error code"
+
+
+@pytest.mark.parametrize("n,seed", [(16, 0), (50, 1), (1000, 2)])
+def test_library_colouring_is_proper(G, n, seed):
+    e = random_regular_graph(n, 3, seed)
+    col, k = G.gtqa_edge_colouring(n, e)
+    assert k <= 4 and check_colouring(n, e, col)
+
+
+def _rc(G, n, edges, J, h, chi, colour=None, precision=0):
+    opt = G.gtqa_options_init(precision=precision)
+    handle = ctypes.c_void_p()
+    edges = np.ascontiguousarray(edges, dtype=np.int32)
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    col = None if colour is None else np.ascontiguousarray(colour, dtype=np.int32)
+    rc = G.load().gtqa_create(n, edges.shape[0], edges.ctypes.data, None if col is None else col.ctypes.data,
+                              J.ctypes.data, h.ctypes.data, chi, ctypes.byref(opt), ctypes.byref(handle))
+    return rc, handle.value
+
+
+def test_invalid_graphs_rejected_on_host(G):
+    h = np.zeros(4)
+    # self-loop
+    assert _rc(G, 4, [[0, 0]], [1.0], h, 4)[0] == G.GTQA_ERR_INVALID_ARG
+    # duplicate edge
+    assert _rc(G, 4, [[0, 1], [1, 0]], [1.0, 1.0], h, 4)[0] == G.GTQA_ERR_INVALID_ARG
+    # degree 4
+    star = [[0, 1], [0, 2], [0, 3], [0, 4]]
+    assert _rc(G, 5, star, np.ones(4), np.zeros(5), 4)[0] == G.GTQA_ERR_INVALID_ARG
+    # out of range vertex
+    assert _rc(G, 4, [[0, 7]], [1.0], h, 4)[0] == G.GTQA_ERR_INVALID_ARG
+    # colouring that is not a matching
+    assert _rc(G, 4, [[0, 1], [1, 2]], [1.0, 1.0], h, 4, colour=[0, 0])[0] == G.GTQA_ERR_INVALID_ARG
+    # NaN coupling
+    assert _rc(G, 4, [[0, 1]], [np.nan], h, 4)[0] == G.GTQA_ERR_INVALID_ARG
+    # unsupported bond dimension / precision
+    assert _rc(G, 4, [[0, 1]], [1.0], h, 64)[0] == G.GTQA_ERR_UNSUPPORTED
+    assert _rc(G, 4, [[0, 1]], [1.0], h, 0)[0] == G.GTQA_ERR_INVALID_ARG
+
+
+def test_null_handles_are_rejected(G):
+    lib = G.load()
+    assert lib.gtqa_trotter_layer(None, 0.5, 0.1) == G.GTQA_ERR_INVALID_ARG
+    assert lib.gtqa_regauge(None) == G.GTQA_ERR_INVALID_ARG
+    lib.gtqa_destroy(None)
