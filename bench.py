@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Throughput of the GTQA hot path: Trotter layers per second on one GB300.
+
+Workload (the single-instance annealing run): seeded random 3-regular graph with
+n = 1000 vertices (m = 1500 edges, Misra-Gries 4-colour matching schedule),
+J_ab ~ N(0, 1), h_a ~ N(0, 0.1), bond dimension chi = 4, linear schedule over
+K = 3200 Trotter layers with dt = 0.2, BP tolerance 1e-8 (at most 100 sweeps).
+One step = one full annealing layer: every edge gate with truncation, the mixing
+layer, flooding BP to tolerance from the warm start, and Vidal-gauge finding.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py --impl reference ...     # the CPU oracle on the same workload
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own replica of
+the workload (no collective on the data path) and the slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Trotter layers/sec at n=1000, chi=4 (mixed vs FP64 GPU) at stated marginal error"
+WL = dict(n=1000, seed=0, chi=4, K=3200, dt=0.2, tol=1e-8, max_iter=100)
+WORKLOAD_NAME = ("random 3-regular n=1000 (m=1500, 4-colour schedule), J~N(0,1), h~N(0,0.1), "
+                 "chi=4, K=3200 layers, dt=0.2, BP tol 1e-8, max 100 sweeps")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=None)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gtqa", choices=["gtqa", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--budget", type=float, default=15.0, help=argparse.SUPPRESS)
+    a = p.parse_args()
+    if a.steps is None:
+        a.steps = WL["K"] - a.warmup
+    a.warmup = max(0, a.warmup)
+    if a.warmup + a.steps > WL["K"]:
+        a.steps = max(1, WL["K"] - a.warmup)
+    return a
+
+
+def instance():
+    from instances import make_instance
+    return make_instance(WL["n"], WL["seed"])
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle, timed on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def oracle_sampled_rate(W: int, K: int, budget_s: float) -> dict:
+    """Layers/s of the CPU oracle on this workload.
+
+    W full oracle layers (k = 1..W) are run first.  Each of the K steps then times a
+    fraction f of one layer's per-unit work with the oracle's own functions: the gates
+    of f*m edges (in schedule order), the mixing gate on the matching share of
+    vertices, the symmetric split of the touched vertices, s BP message updates of
+    the 2 f m directed messages of those edges (s = sweeps the last full layer used),
+    and the per-edge Vidal-gauge step of those edges.  value = sum of fractions /
+    sum of times.  f is chosen so the K steps take about budget_s seconds.
+    """
+    from oracle import gtqa_oracle as O
+    inst = instance()
+    n, m = inst.n, inst.m
+    st = O.plus_state(n, inst.edges)
+    deg = [len(x) for x in st.inc]
+    t_layer, s_ref = None, 1
+    for k in range(1, max(W, 1) + 1):
+        tZ, tX = O.schedule(k, WL["K"], WL["dt"])
+        t0 = time.perf_counter()
+        st, info = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, WL["chi"], WL["tol"], WL["max_iter"])
+        t_layer = time.perf_counter() - t0
+        s_ref = max(1, int(info["bp_iters"]))
+    f = min(1.0, budget_s / (K * t_layer))
+    q = max(1, int(round(f * m)))
+    order = sorted(range(m), key=lambda e: (int(inst.colour[e]), e))
+    tot_t, tot_units = 0.0, 0.0
+    for j in range(K):
+        k = min(WL["K"], max(W, 1) + 1 + j)
+        tZ, tX = O.schedule(k, WL["K"], WL["dt"])
+        sel = [order[(j * q + i) % m] for i in range(q)]
+        verts = sorted({int(x) for e in sel for x in inst.edges[e]})
+        t0 = time.perf_counter()
+        for e in sel:
+            a, b = int(inst.edges[e][0]), int(inst.edges[e][1])
+            Wg = O.ising_gate(float(inst.J[e]), float(inst.h[a]), float(inst.h[b]), deg[a], deg[b], tZ)
+            O.simple_update(st, e, Wg, WL["chi"])
+        Wx = O.mixing_gate(tX)
+        for a in verts[: max(1, int(round(q * n / m)))]:
+            O.apply_single_qubit_gate(st, a, Wx)
+        T = {a: O.symmetric_gauge_vertex(st, a) for a in verts}
+        msgs = {}
+        for a in verts:
+            for e in st.inc[a]:
+                lam = st.lam[e]
+                mm = np.diag(lam / lam.sum()).astype(np.complex128)
+                msgs[(e, 0)] = mm
+                msgs[(e, 1)] = mm
+        new = {}
+        for _ in range(s_ref):
+            for e in sel:
+                for a in (int(inst.edges[e][0]), int(inst.edges[e][1])):
+                    key = O.directed(st, a, e)
+                    mm = O.message_update(st, T, msgs, a, e)
+                    mm = mm / np.trace(mm)
+                    O.trace_norm(mm - msgs[key])
+                    new[key] = mm
+        view = O.VidalState(st.n, st.edges, st.inc, dict(T), {e: st.lam[e] for a in verts for e in st.inc[a]})
+        for e in sel:
+            O.vidal_gauge_edge(view, e, new)
+        tot_t += time.perf_counter() - t0
+        tot_units += q / m
+    return {"value": tot_units / tot_t, "unit": "layers/s", "cores": 1, "kind": "oracle",
+            "sample": (f"{max(W, 1)} full oracle layers from |+>, then {K} steps each timing {q} of {m} edges' "
+                       f"gate, {s_ref} BP update(s) of their {2 * q} directed messages, symmetric split, mixing "
+                       f"and regauge (fraction {q / m:.4f} of a layer per step), scaled to whole layers"),
+            "seconds": tot_t}
+
+
+def cpu_baseline_subprocess(W: int, budget: float) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    env.pop("WORLD_SIZE", None)
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample", "--warmup", str(W),
+           "--steps", "20", "--budget", str(budget)]
+    r = subprocess.run(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "error": r.stderr.decode(errors="replace")[-400:]}
+    return json.loads(r.stdout.decode().strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS),
+                                       "--format=csv,noheader,nounits", "-lms", "200", "-i", str(self.index)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.decode(errors="replace").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per unit (flop counts of the variant that runs)
+# ---------------------------------------------------------------------------
+def gate_flops(chi: int, edges: int, pairs: int, rotations: int) -> float:
+    """FP64 flops of the simple-update kernel (real adds/muls, fma = 2).
+
+    Per edge at storage bond dimension C (rows R = C^2 per QR block, N = 2C):
+      X = Gamma * lambda products  8C^3 + 2C^2
+      Householder QR of 4 blocks   4 sum_k [3(R-k) + 16 (R-k)(C-1-k)]
+      core M (triangular R's)      sum_{r,r'} 10 (C - max(r, r')) + 26 per entry, 4 blocks
+      singular values              3 N^2
+      Q U / lambda (4 blocks)      4 C sum_k 16 (R-k) + 8 C R
+    plus per Jacobi pair examined 14 N (alpha, beta, gamma) and per rotation 40 N + 15.
+    """
+    C = {1: 2, 2: 2, 3: 4, 4: 4, 5: 8, 6: 8, 7: 8, 8: 8}[chi]
+    R, N = C * C, 2 * C
+    x = 8 * C ** 3 + 2 * C * C
+    qr = 4 * sum(3 * (R - k) + 16 * (R - k) * (C - 1 - k) for k in range(C))
+    core = 4 * sum(10 * (C - max(r, rp)) + 26 for r in range(C) for rp in range(C))
+    sv = 3 * N * N
+    back = 4 * C * sum(16 * (R - k) for k in range(C)) + 8 * C * R
+    fixed = x + qr + core + sv + back
+    return float(edges * fixed + pairs * 14 * N + rotations * (40 * N + 15))
+
+
+def bp_flops(chi: int, vertices: int) -> float:
+    """Flops of one flooding sweep: 3 outgoing messages per vertex, each 3 contractions
+    of 2 C^4 complex MACs (48 C^4 real flops) plus unit-trace scaling (Eq. local_consistency)."""
+    C = {1: 2, 2: 2, 3: 4, 4: 4, 5: 8, 6: 8, 7: 8, 8: 8}[chi]
+    return float(vertices * 3 * (48 * C ** 4 + 2 * C * C))
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+def run_gtqa(a):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2409_12240_gb300 import gtqa as G
+    G.load(build_if_missing=True)
+    prec = G.GTQA_MIXED if a.precision == "mixed" else G.GTQA_FP64
+    inst = instance()
+    W, K = a.warmup, a.steps
+    Ks, dt, tol, mi, chi = WL["K"], WL["dt"], WL["tol"], WL["max_iter"], WL["chi"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = cpu_baseline_subprocess(W, a.budget)
+
+    stream = torch.cuda.Stream()
+    opt = G.gtqa_options_init(precision=prec, cuda_stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def make():
+        return G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour, opt)
+
+    def layer(s, k):
+        G.gtqa_trotter_layer(s, k / Ks, dt)
+        it, d, conv = G.gtqa_bp_sweep(s, tol, mi)
+        return it
+
+    # ---- main timed region ----
+    s = make()
+    for k in range(1, W + 1):
+        layer(s, k)
+    st0 = G.gtqa_stats(s)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    sweeps = 0
+    with torch.cuda.stream(stream):
+        for j in range(K):
+            flush.fill_(j & 0xFF)
+            ev[j][0].record(stream)
+            sweeps += layer(s, W + 1 + j)
+            ev[j][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    t_ms = float(sum(e0.elapsed_time(e1) for e0, e1 in ev))
+    st1 = G.gtqa_stats(s)
+    rho_main, sign_main = G.gtqa_marginals(s)
+    G.gtqa_destroy(s)
+    if dist:
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * K / (t_ms / 1e3)
+    launches = int(st1["launches"] - st0["launches"])
+
+    # ---- per-kernel profile over the same layers (separate replica) ----
+    Kp = min(K, 400)
+    s2 = make()
+    for k in range(1, W + 1):
+        layer(s2, k)
+    G.gtqa_profile(s2, True)
+    p0 = G.gtqa_stats(s2)
+    with torch.cuda.stream(stream):
+        for j in range(Kp):
+            flush.fill_(j & 0xFF)
+            layer(s2, W + 1 + j)
+    prof = G.gtqa_profile_read(s2)
+    p1 = G.gtqa_stats(s2)
+    G.gtqa_profile(s2, False)
+    G.gtqa_destroy(s2)
+    total_prof = sum(v[1] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][1])
+    fp64_peak = G.gtqa_alu_peak(True)
+    fp32_peak = G.gtqa_alu_peak(False)
+    roof = None
+    nl, ms, units = prof[dom]
+    if dom == "gate" and nl:
+        fl = gate_flops(chi, units, int(p1["svd_pairs"] - p0["svd_pairs"]),
+                        int(p1["svd_rotations"] - p0["svd_rotations"]))
+        ach = fl / nl / (ms / nl * 1e-3) / 1e12
+        roof = {"kernel": "gate_kernel", "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": "FP64 FMA microbenchmark measured in this run (gtqa_alu_peak)",
+                "algorithmic_flops_per_launch": fl / nl, "avg_launch_us": ms / nl * 1e3}
+    elif dom == "bp_sweep" and nl:
+        fl = bp_flops(chi, units)
+        peak = fp64_peak if prec == G.GTQA_FP64 else fp32_peak
+        ach = fl / nl / (ms / nl * 1e-3) / 1e12
+        roof = {"kernel": "bp_sweep_kernel", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "FMA microbenchmark measured in this run (gtqa_alu_peak)",
+                "algorithmic_flops_per_launch": fl / nl, "avg_launch_us": ms / nl * 1e3}
+    kernel_share = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_prof, 4) if total_prof else 0}
+                    for k, v in prof.items() if v[0]}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not a.no_e2e:
+        import torch as _t
+        rho_h = _t.empty((inst.n, 2, 2), dtype=_t.complex128, pin_memory=True).numpy()
+        sign_h = _t.empty(inst.n, dtype=_t.int8, pin_memory=True).numpy()
+        h2d = inst.edges.nbytes + inst.J.nbytes + inst.h.nbytes + inst.colour.nbytes
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s3 = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour, opt)
+        for j in range(K):
+            layer(s3, j + 1)
+            G.gtqa_marginals(s3, rho_h, sign_h)
+        G.gtqa_destroy(s3)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": world * K / t_e2e, "unit": "layers/s", "h2d_bytes_per_step": h2d / K,
+               "d2h_bytes_per_step": rho_h.nbytes + sign_h.nbytes,
+               "note": "create from host arrays, K layers from |+> each followed by marginals into pinned host buffers, destroy"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128/f64" if prec == G.GTQA_FP64 else "c64/f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "precision": a.precision, "layers_timed": [W + 1, W + K],
+                   "l2": "flushed between timed layers (256 MiB write, outside the timed events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "bp_sweeps_per_layer": sweeps / K,
+        "roofline": roof, "kernel_share": kernel_share, "fp32_peak_tflops": fp32_peak,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
+        "final_marginals": {"mean_abs_z": float(np.mean(np.abs(rho_main[:, 0, 0].real - rho_main[:, 1, 1].real)))},
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    W, K = a.warmup, a.steps
+    r = oracle_sampled_rate(W, K, budget_s=120.0)
+    out = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": "layers/s", "n_gpus": world,
+           "steps": K, "warmup": W, "ms_per_step": 1e3 / r["value"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c128/f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD_NAME, "precision": "fp64 (CPU oracle)", "layers_timed": [W + 1, W + K]},
+           "cpu_baseline": {"value": r["value"], "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": r["sample"]},
+           "e2e": {"value": r["value"], "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    a = parse()
+    if a.oracle_sample:
+        r = oracle_sampled_rate(a.warmup, a.steps, a.budget)
+        print(json.dumps(r))
+        return
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gtqa(a)
+
+
+if __name__ == "__main__":
+    main()

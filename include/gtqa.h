@@ -79,7 +79,24 @@ typedef struct gtqa_stats_t {
     double last_bp_dist;     /* dist/|E| after the last sweep (max over instances), App. B */
     double discarded_weight; /* sum over gates of sum_{dropped} s^2 / sum s^2 */
     double log_fidelity;     /* sum over gates of log f, f = (1 - discarded)^2, Eq. (gate_fidelity) */
+    int64_t svd_pairs;       /* column pairs examined by the gate-core Jacobi SVDs (work counter) */
+    int64_t svd_rotations;   /* rotations applied by the gate-core Jacobi SVDs (work counter) */
+    int64_t bp_sweeps;       /* BP sweeps run since creation (sum over calls, max over instances) */
+    int64_t launches;        /* kernels launched by the library since creation */
 } gtqa_stats_t;
+
+/* kernel classes timed by the optional profiler (gtqa_profile) */
+#define GTQA_K_GATE 0           /* simple update + truncation, one launch per colour */
+#define GTQA_K_MIXING 1         /* exp(-i t X) on every vertex */
+#define GTQA_K_LAYER_STATS 2    /* per-layer discarded-weight / fidelity / work sums */
+#define GTQA_K_SYMMETRIC 3      /* T = Gamma lambda^{1/2} */
+#define GTQA_K_WARM_START 4     /* reconstructed messages */
+#define GTQA_K_BP_SWEEP 5       /* one flooding sweep */
+#define GTQA_K_BP_REDUCE 6      /* dist/|E| and the stopping rule */
+#define GTQA_K_REGAUGE_EDGE 7   /* per-edge part of Vidal gauge finding */
+#define GTQA_K_REGAUGE_VERTEX 8 /* per-vertex part of Vidal gauge finding */
+#define GTQA_K_MARGINALS 9      /* reduced density matrices and read-out */
+#define GTQA_K_COUNT 10
 
 /* Fill *opt with defaults: FP64, default cut-offs, default stream. */
 void gtqa_options_init(gtqa_options* opt);
@@ -162,6 +179,30 @@ int gtqa_sizes(const gtqa_state* s, int64_t* n, int64_t* m, int32_t* chi_storage
 /* Host-only: the library's Misra-Gries edge colouring (<= Delta + 1 colours). */
 int gtqa_edge_colouring(int32_t n, int32_t m, const int32_t* edges, int32_t* colour_out,
                         int32_t* n_colours_out);
+
+/*
+ * Optional profiler: with enable = 1 every launch is bracketed by CUDA events on the
+ * state's stream (adds a little host overhead); enable = 0 stops recording.  Either
+ * call clears the accumulated figures.
+ */
+int gtqa_profile(gtqa_state* s, int32_t enable);
+
+/*
+ * Accumulated figures of one kernel class (GTQA_K_*): launches, summed device time in
+ * milliseconds (event pairs), and work units processed (edges for gate and regauge-edge
+ * launches, vertices for vertex launches).  Synchronises the stream.
+ */
+int gtqa_profile_read(gtqa_state* s, int32_t kind, int64_t* launches, double* total_ms, int64_t* units);
+
+/* Name of a kernel class, or NULL if kind is out of range. */
+const char* gtqa_profile_name(int32_t kind);
+
+/*
+ * Diagnostic: measured CUDA-core FMA throughput of the current device in TFLOP/s
+ * (fp64 = 1: double, 0: float), the ALU roofline denominator for the arithmetic-bound
+ * kernels.  Runs for a few milliseconds on the legacy default stream and synchronises.
+ */
+int gtqa_alu_peak(int32_t fp64, double* tflops_out);
 
 /* Static description of an error code. */
 const char* gtqa_strerror(int code);

@@ -256,15 +256,17 @@ def trotter_layer(st: VidalState, colour: np.ndarray, J: np.ndarray, h: np.ndarr
 # --------------------------------------------------------------------------
 # belief propagation (Sec. II B-C, App. A-B)
 # --------------------------------------------------------------------------
+def symmetric_gauge_vertex(st: VidalState, a: int) -> np.ndarray:
+    """Eq. (symmetric_gauge) for one vertex: T_a = Gamma_a prod_b lambda_ba^{1/2}."""
+    t = st.Gamma[a]
+    for k, e in enumerate(st.inc[a]):
+        t = _scale_slot(t, k, np.sqrt(st.lam[e]))
+    return t
+
+
 def symmetric_gauge(st: VidalState) -> List[np.ndarray]:
-    """Eq. (symmetric_gauge): T_a = Gamma_a prod_b lambda_ba^{1/2}."""
-    T = []
-    for a in range(st.n):
-        t = st.Gamma[a]
-        for k, e in enumerate(st.inc[a]):
-            t = _scale_slot(t, k, np.sqrt(st.lam[e]))
-        T.append(t)
-    return T
+    """Eq. (symmetric_gauge) for every vertex."""
+    return [symmetric_gauge_vertex(st, a) for a in range(st.n)]
 
 
 def reconstructed_messages(st: VidalState, paper_sqrt_warmstart: bool = False) -> Dict[Tuple[int, int], np.ndarray]:
@@ -380,6 +382,27 @@ def hermitian_sqrt(m: np.ndarray, eig_cutoff: float = EIG_CUTOFF) -> Tuple[np.nd
     return (V * sq) @ V.conj().T, (V * isq) @ V.conj().T
 
 
+def vidal_gauge_edge(out: VidalState, e: int, msgs: Dict[Tuple[int, int], np.ndarray],
+                     eig_cutoff: float = EIG_CUTOFF) -> None:
+    """The loop body of Algorithm "Vidal gauge finding" for edge e = {a, b} (a = edges[e][0]):
+    SVD of sum_j m^{1/2}_{a->b}[j, k] m^{1/2}_{b->a}[j, l], the two bond transforms applied
+    to out.Gamma[a], out.Gamma[b] (reading R7 scaling), and lambda_ab = S / ||S||."""
+    a, b = int(out.edges[e][0]), int(out.edges[e][1])
+    sq_a, isq_a = hermitian_sqrt(msgs[(e, 0)], eig_cutoff)
+    sq_b, isq_b = hermitian_sqrt(msgs[(e, 1)], eig_cutoff)
+    M = np.einsum("jk,jl->kl", sq_a, sq_b)
+    U, S, Vh = np.linalg.svd(M)
+    nrm = float(np.linalg.norm(S))
+    Xa = np.einsum("pq,pj->qj", isq_a, U) * np.sqrt(nrm)
+    Xb = np.einsum("pq,jp->qj", isq_b, Vh) * np.sqrt(nrm)
+    for x, X in ((a, Xa), (b, Xb)):
+        s = out.slot(x, e)
+        g = np.moveaxis(out.Gamma[x], 1 + s, -1)
+        g = g @ X
+        out.Gamma[x] = np.moveaxis(g, -1, 1 + s)
+    out.lam[e] = S / nrm if nrm > 0 else S
+
+
 def vidal_gauge(st: VidalState, T: List[np.ndarray], msgs: Dict[Tuple[int, int], np.ndarray],
                 eig_cutoff: float = EIG_CUTOFF, svd_cutoff: float = SVD_CUTOFF) -> VidalState:
     """Algorithm "Vidal gauge finding" (App. D).
@@ -394,20 +417,7 @@ def vidal_gauge(st: VidalState, T: List[np.ndarray], msgs: Dict[Tuple[int, int],
     """
     out = VidalState(st.n, st.edges, st.inc, [t.copy() for t in T], [l.copy() for l in st.lam])
     for e in range(st.m):
-        a, b = int(st.edges[e][0]), int(st.edges[e][1])
-        sq_a, isq_a = hermitian_sqrt(msgs[(e, 0)], eig_cutoff)
-        sq_b, isq_b = hermitian_sqrt(msgs[(e, 1)], eig_cutoff)
-        M = np.einsum("jk,jl->kl", sq_a, sq_b)
-        U, S, Vh = np.linalg.svd(M)
-        nrm = float(np.linalg.norm(S))
-        Xa = np.einsum("pq,pj->qj", isq_a, U) * np.sqrt(nrm)
-        Xb = np.einsum("pq,jp->qj", isq_b, Vh) * np.sqrt(nrm)
-        for x, X in ((a, Xa), (b, Xb)):
-            s = out.slot(x, e)
-            g = np.moveaxis(out.Gamma[x], 1 + s, -1)
-            g = g @ X
-            out.Gamma[x] = np.moveaxis(g, -1, 1 + s)
-        out.lam[e] = S / nrm if nrm > 0 else S
+        vidal_gauge_edge(out, e, msgs, eig_cutoff)
     for e in range(out.m):
         lam = out.lam[e]
         keep = int(np.sum(lam > svd_cutoff * lam[0])) if lam[0] > 0 else 1

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG_DIR, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_PATH = os.path.join(PKG_DIR, "libgtqa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gtqa_api.cu"]
+SOURCES = ["gtqa_api.cu", "gtqa_diag.cu"]
 
 
 def _nvcc() -> str:

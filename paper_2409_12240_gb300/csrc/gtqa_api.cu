@@ -38,7 +38,8 @@ struct gtqa_state {
     double* h = nullptr;
     int* colour_edges = nullptr;
     double* disc = nullptr;
-    double* stats = nullptr;            // [2]: discarded weight, log fidelity
+    int2* work = nullptr;               // per edge: core-SVD sweeps and rotations of the last gate
+    double* stats = nullptr;            // [4]: discarded weight, log fidelity, SVD pairs, SVD rotations
     double* vdelta = nullptr;
     int* inst_vbeg = nullptr;
     int* inst_m = nullptr;
@@ -50,7 +51,15 @@ struct gtqa_state {
     int8_t* sign = nullptr;
     int* h_flags = nullptr;             // pinned mirror of flags
     // counters
-    long long layers = 0, gates = 0;
+    long long layers = 0, gates = 0, bp_sweeps = 0, launches = 0;
+    // optional profiler: pending event pairs and accumulated figures per kernel class
+    bool prof_on = false;
+    struct Pending { int kind; cudaEvent_t a, b; long long units; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[GTQA_K_COUNT] = {};
+    long long prof_launches[GTQA_K_COUNT] = {};
+    long long prof_units[GTQA_K_COUNT] = {};
     int last_iters = 0, not_conv = 0;
     double last_dist = 0.0;
     int sticky = GTQA_OK;
@@ -68,7 +77,54 @@ bool cuda_ok(gtqa_state* s, cudaError_t e) {
 
 int launch_check(gtqa_state* s) {
     if (!cuda_ok(s, cudaGetLastError())) return GTQA_ERR_CUDA;
+    s->launches += 1;
     return GTQA_OK;
+}
+
+cudaEvent_t prof_event(gtqa_state* s) {
+    if (!s->pool.empty()) {
+        cudaEvent_t e = s->pool.back();
+        s->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Bracket one launch with events when the profiler is on.
+struct ProfScope {
+    gtqa_state* s;
+    int kind;
+    long long units;
+    cudaEvent_t a = nullptr;
+    ProfScope(gtqa_state* st, int k, long long u) : s(st), kind(k), units(u) {
+        if (s->prof_on) {
+            a = prof_event(s);
+            if (a) cudaEventRecord(a, s->stream);
+        }
+    }
+    ~ProfScope() {
+        if (!a) return;
+        cudaEvent_t b = prof_event(s);
+        if (!b) return;
+        cudaEventRecord(b, s->stream);
+        s->pending.push_back({kind, a, b, units});
+    }
+};
+
+void prof_collect(gtqa_state* s) {
+    for (auto& p : s->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            s->prof_ms[p.kind] += ms;
+            s->prof_launches[p.kind] += 1;
+            s->prof_units[p.kind] += p.units;
+        }
+        s->pool.push_back(p.a);
+        s->pool.push_back(p.b);
+    }
+    s->pending.clear();
 }
 
 template <typename T>
@@ -225,7 +281,13 @@ void free_state(gtqa_state* s) {
                     s->inst_vbeg, s->inst_m, s->inst_done, s->inst_iters, s->inst_dist, s->flags, s->rho,
                     s->sign};
     for (void* p : ptrs) if (p) cudaFree(p);
+    if (s->work) cudaFree(s->work);
     if (s->h_flags) cudaFreeHost(s->h_flags);
+    for (auto& p : s->pending) {
+        s->pool.push_back(p.a);
+        s->pool.push_back(p.b);
+    }
+    for (cudaEvent_t e : s->pool) cudaEventDestroy(e);
     delete s;
 }
 
@@ -257,6 +319,7 @@ int trotter_layer_t(gtqa_state* s, double tZ, double tX) {
     a.chi = s->chi;
     a.svd_cutoff = s->svd_cutoff;
     a.disc = s->disc;
+    a.work = s->work;
     const size_t smem = sizeof(GateSmem<CHI>) * GS::TEAMS;
     for (int c = 0; c < s->ncol; ++c) {
         const int cnt = s->colour_off[c + 1] - s->colour_off[c];
@@ -264,14 +327,19 @@ int trotter_layer_t(gtqa_state* s, double tZ, double tX) {
         a.edge_list = s->colour_edges + s->colour_off[c];
         a.count = cnt;
         const int grid = (cnt + GS::TEAMS - 1) / GS::TEAMS;
+        ProfScope ps(s, GTQA_K_GATE, cnt);
         gate_kernel<CHI, TS><<<grid, GS::TPB, smem, s->stream>>>(a);
         if (launch_check(s)) return GTQA_ERR_CUDA;
     }
     const size_t work = (size_t)s->n * CHI * CHI * CHI;
-    xrot_kernel<CHI, TS><<<grid_for(work, 256), 256, 0, s->stream>>>((C<TS>*)s->Gamma, s->n, tX);
-    if (launch_check(s)) return GTQA_ERR_CUDA;
+    {
+        ProfScope ps(s, GTQA_K_MIXING, s->n);
+        xrot_kernel<CHI, TS><<<grid_for(work, 256), 256, 0, s->stream>>>((C<TS>*)s->Gamma, s->n, tX);
+        if (launch_check(s)) return GTQA_ERR_CUDA;
+    }
     if (s->m > 0) {
-        layer_stats_kernel<<<1, 256, 0, s->stream>>>(s->disc, s->m, s->stats);
+        ProfScope ps(s, GTQA_K_LAYER_STATS, s->m);
+        layer_stats_kernel<<<1, 256, 0, s->stream>>>(s->disc, s->work, s->m, (2 * CHI - 1) * CHI, s->stats);
         if (launch_check(s)) return GTQA_ERR_CUDA;
     }
     return GTQA_OK;
@@ -280,6 +348,7 @@ int trotter_layer_t(gtqa_state* s, double tZ, double tX) {
 template <int CHI, typename TS>
 int symmetric_t(gtqa_state* s) {
     const size_t work = (size_t)s->n * 2 * CHI * CHI * CHI;
+    ProfScope ps(s, GTQA_K_SYMMETRIC, s->n);
     symmetric_kernel<CHI, TS><<<grid_for(work, 256), 256, 0, s->stream>>>((const C<TS>*)s->Gamma, s->lam, view(s), s->T);
     return launch_check(s);
 }
@@ -290,6 +359,7 @@ int bp_t(gtqa_state* s, double tol, int max_iter, unsigned flags, int* iters_out
     if (symmetric_t<CHI, TS>(s)) return GTQA_ERR_CUDA;
     if (flags & GTQA_BP_WARM_START) {
         const size_t work = msg_elems(s);
+        ProfScope ps(s, GTQA_K_WARM_START, s->m);
         warm_start_kernel<CHI><<<grid_for(work, 256), 256, 0, s->stream>>>(s->lam, s->m, s->msg[s->cur]);
         if (launch_check(s)) return GTQA_ERR_CUDA;
     }
@@ -318,10 +388,16 @@ int bp_t(gtqa_state* s, double tol, int max_iter, unsigned flags, int* iters_out
     for (int it = 0; it < max_iter; ++it) {
         a.src = s->msg[s->cur];
         a.dst = s->msg[s->cur ^ 1];
-        bp_sweep_kernel<CHI><<<grid, BS::TPB, smem, s->stream>>>(a);
-        if (launch_check(s)) return GTQA_ERR_CUDA;
-        bp_reduce_kernel<<<1, 256, 0, s->stream>>>(r);
-        if (launch_check(s)) return GTQA_ERR_CUDA;
+        {
+            ProfScope ps(s, GTQA_K_BP_SWEEP, s->n);
+            bp_sweep_kernel<CHI><<<grid, BS::TPB, smem, s->stream>>>(a);
+            if (launch_check(s)) return GTQA_ERR_CUDA;
+        }
+        {
+            ProfScope ps(s, GTQA_K_BP_REDUCE, s->n);
+            bp_reduce_kernel<<<1, 256, 0, s->stream>>>(r);
+            if (launch_check(s)) return GTQA_ERR_CUDA;
+        }
         s->cur ^= 1;
         if (!cuda_ok(s, cudaMemcpyAsync(s->h_flags, s->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s->stream)))
             return GTQA_ERR_CUDA;
@@ -344,6 +420,7 @@ int bp_t(gtqa_state* s, double tol, int max_iter, unsigned flags, int* iters_out
         if (!(dist[b] < tol) && s->h_inst_m[b] > 0) nc++;
     }
     s->last_iters = mi;
+    s->bp_sweeps += mi;
     s->last_dist = md;
     s->not_conv = nc;
     if (iters_out) *iters_out = mi;
@@ -362,8 +439,12 @@ int regauge_t(gtqa_state* s) {
     a.m = s->m;
     a.eig_cutoff = s->eig_cutoff;
     a.svd_cutoff = s->svd_cutoff;
-    regauge_edge_kernel<CHI><<<(s->m + RS::TEAMS - 1) / RS::TEAMS, RS::TPB, 0, s->stream>>>(a);
-    if (launch_check(s)) return GTQA_ERR_CUDA;
+    {
+        ProfScope ps(s, GTQA_K_REGAUGE_EDGE, s->m);
+        regauge_edge_kernel<CHI><<<(s->m + RS::TEAMS - 1) / RS::TEAMS, RS::TPB, 0, s->stream>>>(a);
+        if (launch_check(s)) return GTQA_ERR_CUDA;
+    }
+    ProfScope ps(s, GTQA_K_REGAUGE_VERTEX, s->n);
     regauge_vertex_kernel<CHI, TS><<<s->n, 128, 0, s->stream>>>(s->T, s->X, view(s), (C<TS>*)s->Gamma);
     return launch_check(s);
 }
@@ -371,6 +452,7 @@ int regauge_t(gtqa_state* s) {
 template <int CHI, typename TS>
 int marginals_t(gtqa_state* s) {
     const int warps_per_block = 4;
+    ProfScope ps(s, GTQA_K_MARGINALS, s->n);
     marginals_kernel<CHI, TS><<<(s->n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s->stream>>>(
         (const C<TS>*)s->Gamma, s->lam, view(s), s->rho, s->sign, s->flags + 2);
     return launch_check(s);
@@ -519,7 +601,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         (rc = dalloc(s, &s->vert_edges, s->n)) || (rc = dalloc(s, &s->vert_inst, s->n)) ||
         (rc = dalloc(s, &s->edge_inst, s->m)) || (rc = dalloc(s, &s->J, s->m)) || (rc = dalloc(s, &s->h, s->n)) ||
         (rc = dalloc(s, &s->colour_edges, s->m)) || (rc = dalloc(s, &s->disc, s->m)) ||
-        (rc = dalloc(s, &s->stats, 2)) || (rc = dalloc(s, &s->vdelta, s->n)) ||
+        (rc = dalloc(s, &s->work, s->m)) || (rc = dalloc(s, &s->stats, 4)) || (rc = dalloc(s, &s->vdelta, s->n)) ||
         (rc = dalloc(s, &s->inst_vbeg, B + 1)) || (rc = dalloc(s, &s->inst_m, B)) ||
         (rc = dalloc(s, &s->inst_done, B)) || (rc = dalloc(s, &s->inst_iters, B)) ||
         (rc = dalloc(s, &s->inst_dist, B)) || (rc = dalloc(s, &s->flags, 4)) ||
@@ -556,7 +638,8 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
               cuda_ok(s, cudaMemcpyAsync(s->h, hv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->colour_edges, cedges.data(), sizeof(int) * Mtot, cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemsetAsync(s->disc, 0, sizeof(double) * (Mtot > 0 ? Mtot : 1), st)) &&
-              cuda_ok(s, cudaMemsetAsync(s->stats, 0, sizeof(double) * 2, st)) &&
+              cuda_ok(s, cudaMemsetAsync(s->stats, 0, sizeof(double) * 4, st)) &&
+              cuda_ok(s, cudaMemsetAsync(s->work, 0, sizeof(int2) * (Mtot > 0 ? Mtot : 1), st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->inst_vbeg, vbeg.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->inst_m, minst.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, st)) &&
@@ -648,7 +731,7 @@ int gtqa_marginals(gtqa_state* s, double* rho_out, int8_t* sign_out) {
 
 int gtqa_stats(gtqa_state* s, gtqa_stats_t* out) {
     if (!s || !out) return GTQA_ERR_INVALID_ARG;
-    double st[2] = {0.0, 0.0};
+    double st[4] = {0.0, 0.0, 0.0, 0.0};
     if (!cuda_ok(s, cudaMemcpyAsync(st, s->stats, sizeof(st), cudaMemcpyDeviceToHost, s->stream)) ||
         !cuda_ok(s, cudaStreamSynchronize(s->stream)))
         return GTQA_ERR_CUDA;
@@ -659,6 +742,10 @@ int gtqa_stats(gtqa_state* s, gtqa_stats_t* out) {
     out->last_bp_dist = s->last_dist;
     out->discarded_weight = st[0];
     out->log_fidelity = st[1];
+    out->svd_pairs = (int64_t)st[2];
+    out->svd_rotations = (int64_t)st[3];
+    out->bp_sweeps = s->bp_sweeps;
+    out->launches = s->launches;
     return GTQA_OK;
 }
 
@@ -713,6 +800,37 @@ int gtqa_edge_colouring(int32_t n, int32_t m, const int32_t* edges, int32_t* col
     for (int e = 0; e < m; ++e) colour_out[e] = col[e];
     if (n_colours_out) *n_colours_out = nc;
     return GTQA_OK;
+}
+
+int gtqa_profile(gtqa_state* s, int32_t enable) {
+    if (!s) return GTQA_ERR_INVALID_ARG;
+    if (!cuda_ok(s, cudaStreamSynchronize(s->stream))) return GTQA_ERR_CUDA;
+    prof_collect(s);
+    for (int k = 0; k < GTQA_K_COUNT; ++k) {
+        s->prof_ms[k] = 0.0;
+        s->prof_launches[k] = 0;
+        s->prof_units[k] = 0;
+    }
+    s->prof_on = enable != 0;
+    return GTQA_OK;
+}
+
+int gtqa_profile_read(gtqa_state* s, int32_t kind, int64_t* launches, double* total_ms, int64_t* units) {
+    if (!s || kind < 0 || kind >= GTQA_K_COUNT) return GTQA_ERR_INVALID_ARG;
+    if (!cuda_ok(s, cudaStreamSynchronize(s->stream))) return GTQA_ERR_CUDA;
+    prof_collect(s);
+    if (launches) *launches = s->prof_launches[kind];
+    if (total_ms) *total_ms = s->prof_ms[kind];
+    if (units) *units = s->prof_units[kind];
+    return GTQA_OK;
+}
+
+const char* gtqa_profile_name(int32_t kind) {
+    static const char* names[GTQA_K_COUNT] = {"gate", "mixing", "layer_stats", "symmetric", "warm_start",
+                                              "bp_sweep", "bp_reduce", "regauge_edge", "regauge_vertex",
+                                              "marginals"};
+    if (kind < 0 || kind >= GTQA_K_COUNT) return nullptr;
+    return names[kind];
 }
 
 const char* gtqa_strerror(int code) {

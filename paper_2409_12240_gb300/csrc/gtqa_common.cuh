@@ -113,7 +113,7 @@ __device__ __forceinline__ void round_robin_pair(int N, int step, int k, int& p,
 
 template <int N, typename R, typename Group>
 __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pair_mask,
-                          R tol, int max_sweeps, bool init_v) {
+                          R tol, int max_sweeps, bool init_v, int* nrot = nullptr) {
     const int k = g / N;
     const int r = g % N;
     if (init_v) {
@@ -149,12 +149,16 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
                 V[p * N + r] = c * vp - sec * vq;
                 V[q * N + r] = se * vp + c * vq;
                 rotated = 1;
+                if (nrot && r == 0) ++*nrot;
             }
             grp.sync();
         }
-        if (!grp.any(rotated)) break;
+        if (!grp.any(rotated)) {
+            ++sweep;
+            break;
+        }
     }
-    return sweep;
+    return sweep;   // sweeps run, including the final one without rotations
 }
 
 // Rank of value i among n values, descending, ties by index (used to sort

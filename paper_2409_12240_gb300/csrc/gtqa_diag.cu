@@ -1,0 +1,63 @@
+// Diagnostics: CUDA-core FMA throughput (the ALU roofline denominator of the
+// FP64- and FP32-bound kernels).  Many independent FMA chains per thread, grid
+// sized to fill every SM; best of three timed runs with CUDA events.
+#include "gtqa.h"
+
+#include <cuda_runtime.h>
+
+namespace {
+
+template <typename T, int NACC>
+__global__ void fma_chains(T* sink, int iters, T a, T b) {
+    T acc[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k] = (T)(threadIdx.x + k);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) acc[k] = fma(acc[k], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) s += acc[k];
+    if (s == (T)-1) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;   // never true; keeps the work
+}
+
+template <typename T>
+int measure(double* tflops) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GTQA_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GTQA_ERR_CUDA;
+    const int threads = 256, blocks = sms * 8;
+    const int iters = sizeof(T) == 8 ? 1000 : 20000;
+    constexpr int NACC = 8;
+    T* sink = nullptr;
+    if (cudaMalloc(&sink, sizeof(T) * (size_t)threads * blocks) != cudaSuccess) return GTQA_ERR_OOM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    fma_chains<T, NACC><<<blocks, threads>>>(sink, 10, (T)0.999, (T)0.001);
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+        cudaEventRecord(e0);
+        fma_chains<T, NACC><<<blocks, threads>>>(sink, iters, (T)0.999, (T)0.001);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    const cudaError_t err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (err != cudaSuccess) return GTQA_ERR_CUDA;
+    *tflops = 2.0 * NACC * (double)iters * blocks * threads / (best * 1e-3) / 1e12;
+    return GTQA_OK;
+}
+
+}  // namespace
+
+extern "C" int gtqa_alu_peak(int32_t fp64, double* tflops_out) {
+    if (!tflops_out) return GTQA_ERR_INVALID_ARG;
+    return fp64 ? measure<double>(tflops_out) : measure<float>(tflops_out);
+}

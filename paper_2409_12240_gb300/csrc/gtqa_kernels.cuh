@@ -75,6 +75,7 @@ struct GateSmem {
     int perm[2 * CHI];
     double scal[2];            // 1/norm of kept singular values, keep count
     int flag;
+    int nrot;
 };
 
 template <typename TS>
@@ -88,6 +89,7 @@ struct GateArgs {
     int chi;
     double svd_cutoff;
     double* disc;              // per edge: discarded weight of this gate
+    int2* work;                // per edge: (Jacobi sweeps, rotations) of the core SVD
 };
 
 template <int CHI, typename TS>
@@ -196,14 +198,18 @@ gate_kernel(GateArgs<TS> A) {
     team_sync<TEAM>();
 
     // ---- SVD of M ----
+    if (tid == 0) sm.nrot = 0;
+    int nrot = 0, sweeps;
     if constexpr (TEAM <= 32) {
         WarpGroup grp{group_mask<TEAM>()};
-        jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), 1e-15, 60, true);
+        sweeps = jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), 1e-15, 60, true, &nrot);
     } else {
         BlockGroup grp{&sm.flag};
-        jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), 1e-15, 60, true);
+        sweeps = jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), 1e-15, 60, true, &nrot);
     }
+    if (nrot) atomicAdd(&sm.nrot, nrot);
     team_sync<TEAM>();
+    if (tid == 0) A.work[e] = make_int2(sweeps, sm.nrot);
     for (int c = tid; c < NM; c += TEAM) {
         double s2 = 0.0;
         for (int r = 0; r < NM; ++r) s2 += norm2(sm.M[c * NM + r]);
@@ -758,29 +764,32 @@ __global__ void marginals_kernel(const C<TS>* Gamma, const double* lam, GraphVie
     }
 }
 
-// Per-layer statistics: sum of discarded weights and of log gate fidelities.
-__global__ void layer_stats_kernel(const double* disc, int m, double* stats) {
-    __shared__ double p0[256], p1[256];
-    double s0 = 0.0, s1 = 0.0;
+// Per-layer statistics: sums of discarded weights, log gate fidelities
+// (Eq. (gate_fidelity)), and the core-SVD work counters (sweeps, rotations).
+__global__ void layer_stats_kernel(const double* disc, const int2* work, int m, int pairs_per_sweep,
+                                   double* stats) {
+    __shared__ double p[4][256];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     for (int e = threadIdx.x; e < m; e += blockDim.x) {
         const double d = disc[e];
         s0 += d;
         s1 += 2.0 * log1p(-d);
+        const int2 w = work[e];
+        s2 += (double)w.x * pairs_per_sweep;
+        s3 += (double)w.y;
     }
-    p0[threadIdx.x] = s0;
-    p1[threadIdx.x] = s1;
+    p[0][threadIdx.x] = s0;
+    p[1][threadIdx.x] = s1;
+    p[2][threadIdx.x] = s2;
+    p[3][threadIdx.x] = s3;
     __syncthreads();
     for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < off) {
-            p0[threadIdx.x] += p0[threadIdx.x + off];
-            p1[threadIdx.x] += p1[threadIdx.x + off];
-        }
+        if (threadIdx.x < off)
+            for (int q = 0; q < 4; ++q) p[q][threadIdx.x] += p[q][threadIdx.x + off];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        stats[0] += p0[0];
-        stats[1] += p1[0];
-    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 4; ++q) stats[q] += p[q][0];
 }
 
 }  // namespace gtqa

@@ -34,8 +34,11 @@ GTQA_BP_DEFAULT = 3
 EXPORTED = [
     "gtqa_options_init", "gtqa_create", "gtqa_create_batch", "gtqa_trotter_layer", "gtqa_bp_sweep",
     "gtqa_regauge", "gtqa_marginals", "gtqa_stats", "gtqa_get_state", "gtqa_set_state", "gtqa_sizes",
-    "gtqa_edge_colouring", "gtqa_strerror", "gtqa_destroy",
+    "gtqa_edge_colouring", "gtqa_strerror", "gtqa_destroy", "gtqa_profile", "gtqa_profile_read",
+    "gtqa_profile_name", "gtqa_alu_peak",
 ]
+KERNEL_KINDS = ["gate", "mixing", "layer_stats", "symmetric", "warm_start", "bp_sweep", "bp_reduce",
+                "regauge_edge", "regauge_vertex", "marginals"]
 
 
 class gtqa_options(ctypes.Structure):
@@ -47,7 +50,9 @@ class gtqa_options(ctypes.Structure):
 class gtqa_stats_t(ctypes.Structure):
     _fields_ = [("layers", ctypes.c_int64), ("gates", ctypes.c_int64), ("last_bp_iters", ctypes.c_int32),
                 ("not_converged", ctypes.c_int32), ("last_bp_dist", ctypes.c_double),
-                ("discarded_weight", ctypes.c_double), ("log_fidelity", ctypes.c_double)]
+                ("discarded_weight", ctypes.c_double), ("log_fidelity", ctypes.c_double),
+                ("svd_pairs", ctypes.c_int64), ("svd_rotations", ctypes.c_int64), ("bp_sweeps", ctypes.c_int64),
+                ("launches", ctypes.c_int64)]
 
 
 class GTQAError(RuntimeError):
@@ -90,6 +95,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_edge_colouring": (I32, [I32, I32, P, P, ctypes.POINTER(I32)]),
         "gtqa_strerror": (ctypes.c_char_p, [I32]),
         "gtqa_destroy": (None, [P]),
+        "gtqa_profile": (I32, [P, I32]),
+        "gtqa_profile_read": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(I64)]),
+        "gtqa_profile_name": (ctypes.c_char_p, [I32]),
+        "gtqa_alu_peak": (I32, [I32, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -236,6 +245,32 @@ def gtqa_edge_colouring(n: int, edges) -> Tuple[np.ndarray, int]:
     _check(load().gtqa_edge_colouring(int(n), int(edges.shape[0]), _ptr(edges)[0], _ptr(col)[0], ctypes.byref(k)),
            "gtqa_edge_colouring")
     return col, int(k.value)
+
+
+def gtqa_profile(s: int, enable: bool) -> None:
+    _check(load().gtqa_profile(s, 1 if enable else 0), "gtqa_profile")
+
+
+def gtqa_profile_read(s: int) -> dict:
+    """{kernel class: (launches, total ms, units)} for every class."""
+    out = {}
+    for k, name in enumerate(KERNEL_KINDS):
+        l, ms, u = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+        _check(load().gtqa_profile_read(s, k, ctypes.byref(l), ctypes.byref(ms), ctypes.byref(u)), "gtqa_profile_read")
+        out[name] = (int(l.value), float(ms.value), int(u.value))
+    return out
+
+
+def gtqa_profile_name(kind: int) -> Optional[str]:
+    r = load().gtqa_profile_name(int(kind))
+    return None if r is None else r.decode()
+
+
+def gtqa_alu_peak(fp64: bool) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current device."""
+    t = ctypes.c_double()
+    _check(load().gtqa_alu_peak(1 if fp64 else 0, ctypes.byref(t)), "gtqa_alu_peak")
+    return float(t.value)
 
 
 def gtqa_destroy(s: int) -> None:
