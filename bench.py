@@ -42,8 +42,9 @@ def parse():
     p.add_argument("--steps", type=int, default=None)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gtqa", choices=["gtqa", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison run")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--budget", type=float, default=15.0, help=argparse.SUPPRESS)
@@ -197,8 +198,12 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # algorithmic work per unit (flop counts of the variant that runs)
 # ---------------------------------------------------------------------------
+def storage_chi(chi: int) -> int:
+    return 2 if chi <= 2 else (4 if chi <= 4 else 8)
+
+
 def gate_flops(chi: int, edges: int, pairs: int, rotations: int) -> float:
-    """FP64 flops of the simple-update kernel (real adds/muls, fma = 2).
+    """FP64 flops of the simple-update phase (real adds/muls, fma = 2).
 
     Per edge at storage bond dimension C (rows R = C^2 per QR block, N = 2C):
       X = Gamma * lambda products  8C^3 + 2C^2
@@ -207,8 +212,9 @@ def gate_flops(chi: int, edges: int, pairs: int, rotations: int) -> float:
       singular values              3 N^2
       Q U / lambda (4 blocks)      4 C sum_k 16 (R-k) + 8 C R
     plus per Jacobi pair examined 14 N (alpha, beta, gamma) and per rotation 40 N + 15.
+    In the mixed mode the last line (Q U / lambda) runs in FP32; it is still counted here.
     """
-    C = {1: 2, 2: 2, 3: 4, 4: 4, 5: 8, 6: 8, 7: 8, 8: 8}[chi]
+    C = storage_chi(chi)
     R, N = C * C, 2 * C
     x = 8 * C ** 3 + 2 * C * C
     qr = 4 * sum(3 * (R - k) + 16 * (R - k) * (C - 1 - k) for k in range(C))
@@ -219,11 +225,46 @@ def gate_flops(chi: int, edges: int, pairs: int, rotations: int) -> float:
     return float(edges * fixed + pairs * 14 * N + rotations * (40 * N + 15))
 
 
-def bp_flops(chi: int, vertices: int) -> float:
-    """Flops of one flooding sweep: 3 outgoing messages per vertex, each 3 contractions
-    of 2 C^4 complex MACs (48 C^4 real flops) plus unit-trace scaling (Eq. local_consistency)."""
-    C = {1: 2, 2: 2, 3: 4, 4: 4, 5: 8, 6: 8, 7: 8, 8: 8}[chi]
-    return float(vertices * 3 * (48 * C ** 4 + 2 * C * C))
+def bp_sweep_flops(chi: int, vertices: int, mixed: bool) -> float:
+    """Flops of one flooding sweep (Eq. local_consistency) over `vertices` vertices of degree 3:
+    FP64 mode 3 outgoing messages x 3 contractions of 2 C^4 complex MACs (48 C^4 real flops);
+    mixed mode 3 outgoing messages x 4 contractions of 2 C^4 complex MACs (64 C^4; the
+    delta-form update), FP32."""
+    C = storage_chi(chi)
+    per = (64 if mixed else 48) * C ** 4
+    return float(vertices * 3 * per)
+
+
+def per_layer_error(G, make, inst, k_last: int, samples: int = 6) -> dict:
+    """Marginal error introduced by one mixed-precision layer: at sampled layers k the
+    FP64 state after layer k-1 is loaded into a mixed and an FP64 state, layer k runs in
+    both, and max |rho_mixed - rho_fp64| over vertices is recorded."""
+    Ks, dt, tol, mi = WL["K"], WL["dt"], WL["tol"], WL["max_iter"]
+    ks = sorted({max(2, int(round(k_last * (i + 1) / samples))) for i in range(samples)})
+    ref = make(G.GTQA_FP64)
+    out, done = {}, 0
+    try:
+        for k in ks:
+            G.gtqa_anneal(ref, done + 1, k - 1, Ks, dt, tol, mi)
+            done = k - 1
+            Gm, L, Mg = G.gtqa_get_state(ref)
+            errs = []
+            rhos = []
+            for p in (G.GTQA_MIXED, G.GTQA_FP64):
+                s = make(p)
+                G.gtqa_set_state(s, Gm, L, Mg)
+                G.gtqa_anneal(s, k, k, Ks, dt, tol, mi)
+                rhos.append(G.gtqa_marginals(s))
+                G.gtqa_destroy(s)
+            (rm, sm_), (rf, sf) = rhos
+            clear = np.abs(rf[:, 0, 0].real - 0.5) > 1e-3
+            out[str(k)] = {"max_abs": float(np.abs(rm - rf).max()),
+                           "sign_agreement": float(np.mean(sm_[clear] == sf[clear]))}
+    finally:
+        G.gtqa_destroy(ref)
+    return {"max_abs": max(v["max_abs"] for v in out.values()),
+            "min_sign_agreement": min(v["sign_agreement"] for v in out.values()), "samples": out,
+            "note": "one layer in each mode from the same FP64 state at layer k-1"}
 
 
 # ---------------------------------------------------------------------------
@@ -241,7 +282,8 @@ def run_gtqa(a):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2409_12240_gb300 import gtqa as G
     G.load(build_if_missing=True)
-    prec = G.GTQA_MIXED if a.precision == "mixed" else G.GTQA_FP64
+    mixed = a.precision == "mixed"
+    prec = G.GTQA_MIXED if mixed else G.GTQA_FP64
     inst = instance()
     W, K = a.warmup, a.steps
     Ks, dt, tol, mi, chi = WL["K"], WL["dt"], WL["tol"], WL["max_iter"], WL["chi"]
@@ -251,63 +293,80 @@ def run_gtqa(a):
         cpu = cpu_baseline_subprocess(W, a.budget)
 
     stream = torch.cuda.Stream()
-    opt = G.gtqa_options_init(precision=prec, cuda_stream=stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    def make():
-        return G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour, opt)
+    def make(p):
+        return G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour,
+                             G.gtqa_options_init(precision=p, cuda_stream=stream.cuda_stream))
 
-    def layer(s, k):
-        G.gtqa_trotter_layer(s, k / Ks, dt)
-        it, d, conv = G.gtqa_bp_sweep(s, tol, mi)
-        return it
+    def timed_window(p, clocks=None):
+        """Warm-up layers 1..W, then layers W+1..W+K, one gtqa_anneal call per layer with an
+        L2 flush between layers (outside the events).  Returns (ms, stats delta, final rho)."""
+        s = make(p)
+        if W:
+            G.gtqa_anneal(s, 1, W, Ks, dt, tol, mi)
+        st0 = G.gtqa_stats(s)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        with torch.cuda.stream(stream):
+            for j in range(K):
+                flush.fill_(j & 0xFF)
+                ev[j][0].record(stream)
+                G.gtqa_anneal(s, W + 1 + j, W + 1 + j, Ks, dt, tol, mi)
+                ev[j][1].record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ck = clocks.stop() if clocks else None
+        t_ms = float(sum(e0.elapsed_time(e1) for e0, e1 in ev))
+        st1 = G.gtqa_stats(s)
+        rho, sign = G.gtqa_marginals(s)
+        G.gtqa_destroy(s)
+        delta = {k: st1[k] - st0[k] for k in ("launches", "bp_sweeps", "bp_calls", "bp_not_converged_calls",
+                                               "svd_pairs", "svd_rotations")}
+        return t_ms, delta, rho, sign, ck
 
-    # ---- main timed region ----
-    s = make()
-    for k in range(1, W + 1):
-        layer(s, k)
-    st0 = G.gtqa_stats(s)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     clocks = Clocks(local)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    sweeps = 0
-    with torch.cuda.stream(stream):
-        for j in range(K):
-            flush.fill_(j & 0xFF)
-            ev[j][0].record(stream)
-            sweeps += layer(s, W + 1 + j)
-            ev[j][1].record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ck = clocks.stop()
-    t_ms = float(sum(e0.elapsed_time(e1) for e0, e1 in ev))
-    st1 = G.gtqa_stats(s)
-    rho_main, sign_main = G.gtqa_marginals(s)
-    G.gtqa_destroy(s)
+    t_ms, dlt, rho_main, sign_main, ck = timed_window(prec, clocks)
     if dist:
         tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_ms = float(tt.item())
     value = world * K / (t_ms / 1e3)
-    launches = int(st1["launches"] - st0["launches"])
 
-    # ---- per-kernel profile over the same layers (separate replica) ----
-    Kp = min(K, 400)
-    s2 = make()
-    for k in range(1, W + 1):
-        layer(s2, k)
+    # the FP64 path on the same layers, and the marginal error of the mixed path against it
+    fp64 = None
+    if mixed and not a.no_fp64:
+        t64, d64, rho64, sign64, _ = timed_window(G.GTQA_FP64)
+        err = np.abs(rho_main - rho64)
+        clear = np.abs(rho64[:, 0, 0].real - 0.5) > 1e-3
+        fp64 = {"value": world * K / (t64 / 1e3), "unit": "layers/s", "ms_per_step": t64 / K,
+                "bp_sweeps_per_layer": d64["bp_sweeps"] / K,
+                "speedup_mixed_over_fp64": t64 / t_ms,
+                "marginal_error_per_layer": per_layer_error(G, make, inst, W + K),
+                "trajectory_divergence_at_last_layer": {
+                    "max_abs": float(err.max()), "mean_abs": float(err.mean()),
+                    "sign_agreement": float(np.mean(sign_main[clear] == sign64[clear])), "at_layer": W + K,
+                    "note": "whole trajectories; BP stops at max_iter in part of the anneal, after which both "
+                            "runs follow the chaotic BP map and decorrelate"}}
+
+    # ---- per-kernel profile (CUDA events around each launch) on the same layers ----
+    Kp = min(K, 300)
+    s2 = make(prec)
+    if W:
+        G.gtqa_anneal(s2, 1, W, Ks, dt, tol, mi)
     G.gtqa_profile(s2, True)
     p0 = G.gtqa_stats(s2)
     with torch.cuda.stream(stream):
         for j in range(Kp):
             flush.fill_(j & 0xFF)
-            layer(s2, W + 1 + j)
+            G.gtqa_anneal(s2, W + 1 + j, W + 1 + j, Ks, dt, tol, mi)
     prof = G.gtqa_profile_read(s2)
     p1 = G.gtqa_stats(s2)
     G.gtqa_profile(s2, False)
@@ -316,46 +375,46 @@ def run_gtqa(a):
     dom = max(prof, key=lambda k: prof[k][1])
     fp64_peak = G.gtqa_alu_peak(True)
     fp32_peak = G.gtqa_alu_peak(False)
-    roof = None
     nl, ms, units = prof[dom]
-    if dom == "gate" and nl:
-        fl = gate_flops(chi, units, int(p1["svd_pairs"] - p0["svd_pairs"]),
-                        int(p1["svd_rotations"] - p0["svd_rotations"]))
-        ach = fl / nl / (ms / nl * 1e-3) / 1e12
-        roof = {"kernel": "gate_kernel", "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None,
-                "peak_source": "FP64 FMA microbenchmark measured in this run (gtqa_alu_peak)",
+    roof = None
+    if dom == "gates_kernel" and nl:
+        fl = gate_flops(chi, units, int(p1["svd_pairs"] - p0["svd_pairs"]), int(p1["svd_rotations"] - p0["svd_rotations"]))
+        ach = fl / (ms * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": None, "peak_source": "FP64 FMA microbenchmark, this run",
                 "algorithmic_flops_per_launch": fl / nl, "avg_launch_us": ms / nl * 1e3}
-    elif dom == "bp_sweep" and nl:
-        fl = bp_flops(chi, units)
-        peak = fp64_peak if prec == G.GTQA_FP64 else fp32_peak
-        ach = fl / nl / (ms / nl * 1e-3) / 1e12
-        roof = {"kernel": "bp_sweep_kernel", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+    elif dom == "bp_kernel" and nl:
+        sweeps = int(p1["bp_sweeps"] - p0["bp_sweeps"])
+        fl = bp_sweep_flops(chi, inst.n, mixed) * sweeps
+        peak = fp32_peak if mixed else fp64_peak
+        ach = fl / (ms * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None,
-                "peak_source": "FMA microbenchmark measured in this run (gtqa_alu_peak)",
-                "algorithmic_flops_per_launch": fl / nl, "avg_launch_us": ms / nl * 1e3}
+                "peak_source": ("FP32" if mixed else "FP64") + " FMA microbenchmark, this run",
+                "algorithmic_flops_per_launch": fl / nl, "avg_launch_us": ms / nl * 1e3,
+                "sweeps_per_launch": sweeps / nl,
+                "note": "flops of the BP contractions only; each sweep is bounded by the grid-barrier and memory latency"}
     kernel_share = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_prof, 4) if total_prof else 0}
                     for k, v in prof.items() if v[0]}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if not a.no_e2e:
-        import torch as _t
-        rho_h = _t.empty((inst.n, 2, 2), dtype=_t.complex128, pin_memory=True).numpy()
-        sign_h = _t.empty(inst.n, dtype=_t.int8, pin_memory=True).numpy()
+        rho_h = torch.empty((inst.n, 2, 2), dtype=torch.complex128, pin_memory=True).numpy()
+        sign_h = torch.empty(inst.n, dtype=torch.int8, pin_memory=True).numpy()
         h2d = inst.edges.nbytes + inst.J.nbytes + inst.h.nbytes + inst.colour.nbytes
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s3 = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour, opt)
+        s3 = make(prec)
         for j in range(K):
-            layer(s3, j + 1)
+            G.gtqa_anneal(s3, j + 1, j + 1, Ks, dt, tol, mi)
             G.gtqa_marginals(s3, rho_h, sign_h)
         G.gtqa_destroy(s3)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         e2e = {"value": world * K / t_e2e, "unit": "layers/s", "h2d_bytes_per_step": h2d / K,
                "d2h_bytes_per_step": rho_h.nbytes + sign_h.nbytes,
-               "note": "create from host arrays, K layers from |+> each followed by marginals into pinned host buffers, destroy"}
+               "note": "create from host arrays, layers 1..K each followed by marginals into pinned host buffers, destroy"}
 
     if rank != 0:
         if dist:
@@ -364,13 +423,15 @@ def run_gtqa(a):
     out = {
         "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c128/f64" if prec == G.GTQA_FP64 else "c64/f64", "data": "synthetic",
+        "dtype": "c64/f64" if mixed else "c128/f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "precision": a.precision, "layers_timed": [W + 1, W + K],
                    "l2": "flushed between timed layers (256 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "bp_sweeps_per_layer": sweeps / K,
-        "roofline": roof, "kernel_share": kernel_share, "fp32_peak_tflops": fp32_peak,
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
+        "bp_sweeps_per_layer": dlt["bp_sweeps"] / K,
+        "bp_layers_at_max_iter": dlt["bp_not_converged_calls"] / K,
+        "fp64_path": fp64,
+        "roofline": roof, "kernel_share": kernel_share, "fp32_peak_tflops": fp32_peak, "fp64_peak_tflops": fp64_peak,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(dlt["launches"]), "clocks": ck,
         "final_marginals": {"mean_abs_z": float(np.mean(np.abs(rho_main[:, 0, 0].real - rho_main[:, 1, 1].real)))},
     }
     print(json.dumps(out))

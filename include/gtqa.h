@@ -20,6 +20,9 @@
  *    ascending edge id; missing slots (degree < 3) are phantom bonds of dimension 1.
  *  - Bond storage is padded to CHI = smallest of {2, 4, 8} >= chi; entries beyond a
  *    bond's current dimension are exactly zero.
+ *  - Device work runs in three persistent kernels (gates, BP, regauge), each launched
+ *    cooperatively with one block per SM; their grid barriers poll with a bound and
+ *    report GTQA_ERR_TIMEOUT instead of hanging.
  *  - Gamma layout: complex128 interleaved (re, im) array [n][2][CHI][CHI][CHI],
  *    index (i, j_slot0, j_slot1, j_slot2); lambda: float64 [m][CHI], descending;
  *    messages: complex128 [2m][CHI][CHI], row 2e holds m_{u->v}, row 2e+1 holds
@@ -54,7 +57,9 @@ extern "C" {
 
 /* arithmetic modes */
 #define GTQA_FP64 0   /* complex128 everywhere */
-#define GTQA_MIXED 1  /* complex64 tensors and BP contractions; FP64 QR/SVD, gauge roots, normalisation */
+#define GTQA_MIXED 1  /* complex64 tensors and BP contractions; FP64 QR/SVD, gauge roots, normalisation.
+                         Messages are held as m0 + delta: m0 = diag(lambda)/sum(lambda) (exact),
+                         delta in complex64; get/set_state convert to and from complex128. */
 
 /* flags of gtqa_bp_sweep */
 #define GTQA_BP_WARM_START 1u  /* start from m_{a->b} = diag(lambda_ab)/sum(lambda_ab) (Eq. reconstructed_messages) */
@@ -83,20 +88,16 @@ typedef struct gtqa_stats_t {
     int64_t svd_rotations;   /* rotations applied by the gate-core Jacobi SVDs (work counter) */
     int64_t bp_sweeps;       /* BP sweeps run since creation (sum over calls, max over instances) */
     int64_t launches;        /* kernels launched by the library since creation */
+    int64_t bp_calls;        /* BP runs since creation (one per layer in gtqa_anneal) */
+    int64_t bp_not_converged_calls; /* BP runs in which some instance reached max_iter */
 } gtqa_stats_t;
 
-/* kernel classes timed by the optional profiler (gtqa_profile) */
-#define GTQA_K_GATE 0           /* simple update + truncation, one launch per colour */
-#define GTQA_K_MIXING 1         /* exp(-i t X) on every vertex */
-#define GTQA_K_LAYER_STATS 2    /* per-layer discarded-weight / fidelity / work sums */
-#define GTQA_K_SYMMETRIC 3      /* T = Gamma lambda^{1/2} */
-#define GTQA_K_WARM_START 4     /* reconstructed messages */
-#define GTQA_K_BP_SWEEP 5       /* one flooding sweep */
-#define GTQA_K_BP_REDUCE 6      /* dist/|E| and the stopping rule */
-#define GTQA_K_REGAUGE_EDGE 7   /* per-edge part of Vidal gauge finding */
-#define GTQA_K_REGAUGE_VERTEX 8 /* per-vertex part of Vidal gauge finding */
-#define GTQA_K_MARGINALS 9      /* reduced density matrices and read-out */
-#define GTQA_K_COUNT 10
+/* kernels timed by the optional profiler (gtqa_profile) */
+#define GTQA_K_TROTTER 0    /* gates_kernel: the gate phases of one layer (gtqa_trotter_layer, gtqa_anneal) */
+#define GTQA_K_BP 1         /* bp_kernel: warm start and BP sweeps of one BP run */
+#define GTQA_K_REGAUGE 2    /* regauge_kernel: Vidal gauge finding */
+#define GTQA_K_MARGINALS 3  /* marginals_kernel */
+#define GTQA_K_COUNT 4
 
 /* Fill *opt with defaults: FP64, default cut-offs, default stream. */
 void gtqa_options_init(gtqa_options* opt);
@@ -153,6 +154,16 @@ int gtqa_bp_sweep(gtqa_state* s, double tol, int32_t max_iter, uint32_t flags,
 int gtqa_regauge(gtqa_state* s);
 
 /*
+ * Layers k_begin..k_end (1-based, k_end <= K) of the K-layer linear anneal with step dt:
+ * for each k, gtqa_trotter_layer(tau = k/K, dt) followed by gtqa_bp_sweep(tol, max_iter,
+ * GTQA_BP_DEFAULT): three cooperative launches per layer and no host synchronisation
+ * (BP stops on the device).  Asynchronous: BP counters go to gtqa_stats (bp_calls,
+ * bp_not_converged_calls, bp_sweeps).
+ */
+int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double dt, double tol,
+                int32_t max_iter);
+
+/*
  * Single-qubit reduced density matrices rho_a = sum Gamma Gamma^* prod_b lambda_ba^2 / tr
  * (Eq. (partial_dens) with the environment of Eq. (bp_approx) from the warm-start
  * messages of the current Vidal-gauge state) and the read-out of Eq. (rounding_rule).
@@ -194,7 +205,15 @@ int gtqa_profile(gtqa_state* s, int32_t enable);
  */
 int gtqa_profile_read(gtqa_state* s, int32_t kind, int64_t* launches, double* total_ms, int64_t* units);
 
-/* Name of a kernel class, or NULL if kind is out of range. */
+/*
+ * Test hook for the failure path of the bounded grid barriers: spin_limit sets the polls
+ * a barrier waits before it gives up; extra_arrivals = 1 makes every barrier wait for one
+ * block that does not exist, so the next launch returns GTQA_ERR_TIMEOUT (sticky) with the
+ * device context intact.  Defaults: 4194304 polls, 0 extra arrivals.
+ */
+int gtqa_debug_barrier(gtqa_state* s, int64_t spin_limit, int32_t extra_arrivals);
+
+/* Name of a launch class, or NULL if kind is out of range. */
 const char* gtqa_profile_name(int32_t kind);
 
 /*
@@ -203,6 +222,13 @@ const char* gtqa_profile_name(int32_t kind);
  * kernels.  Runs for a few milliseconds on the legacy default stream and synchronises.
  */
 int gtqa_alu_peak(int32_t fp64, double* tflops_out);
+
+/*
+ * Diagnostic: for n positive host doubles x, writes 6 n host doubles: per x the kernels'
+ * Newton-refined reciprocal, CUDA's 1/x, the refined 1/sqrt(x), CUDA's 1/sqrt(x), the
+ * refined sqrt(x) and CUDA's sqrt(x) (accuracy tests of the divide-free arithmetic).
+ */
+int gtqa_math_check(int32_t n, const double* x, double* out);
 
 /* Static description of an error code. */
 const char* gtqa_strerror(int code);

@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG_DIR, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_PATH = os.path.join(PKG_DIR, "libgtqa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gtqa_api.cu", "gtqa_diag.cu"]
+SOURCES = ["gtqa_api.cu", "gtqa_fp64_gates.cu", "gtqa_fp64_bp.cu", "gtqa_fp64_regauge.cu",
+           "gtqa_mixed_gates.cu", "gtqa_mixed_bp.cu", "gtqa_mixed_regauge.cu", "gtqa_diag.cu"]
 
 
 def _nvcc() -> str:

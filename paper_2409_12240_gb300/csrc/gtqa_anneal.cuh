@@ -1,0 +1,1033 @@
+// Persistent annealing kernel: one cooperative launch runs whole GTQA layers.
+//
+// Phases of one layer (each separated by a bounded grid barrier):
+//   gates      for each colour class: simple update + truncation of every edge of
+//              that matching (App. E, App. D "Truncation"); the mixing gate
+//              exp(-i t_X X) (Sec. II D) is applied to a vertex right after its last
+//              gate of the layer.
+//   bp init    T_a = Gamma_a prod lambda^{1/2} (Eq. (symmetric_gauge)); warm-start
+//              messages diag(lambda)/sum(lambda) (Eq. (reconstructed_messages)).
+//   bp sweeps  flooding update of every directed message, Eq. (local_consistency),
+//              unit-trace normalisation and trace-norm distance (App. B), until
+//              dist_b/|E_b| < tol for every instance b or max_iter sweeps.
+//   regauge    Vidal gauge finding (App. D): per-edge transforms, then per-vertex
+//              application to T.
+//
+// Layout: Gamma[n][2][CHI][CHI][CHI] (slot k = k-th incident edge, ascending id),
+// lambda[m][CHI], messages[2m][CHI][CHI] (2e = m_{u->v}, 2e+1 = m_{v->u}); phantom
+// slots (degree < 3) have dimension 1 with lambda = e_0 and message e_0 e_0^T.
+//
+// Precision modes:
+//   FP64   complex128 tensors and messages, FP64 arithmetic throughout.
+//   Mixed  complex64 Gamma, T and message corrections; the simple update's QR and
+//          SVD, the regauge's eigen/SVD and square roots, and the message
+//          normalisation in FP64.  Messages are kept as m = m0 + delta with m0 the
+//          warm start (exact, from lambda) and delta in complex64; each sweep
+//          contracts only delta in FP32, and the warm-start part F(m0) is contracted
+//          once per BP call in FP64.
+#pragma once
+
+#include "gtqa_common.cuh"
+
+namespace gtqa {
+
+struct ModeFP64 {
+    using TS = double;   // storage of Gamma, T, messages
+    static constexpr bool mixed = false;
+};
+struct ModeMixed {
+    using TS = float;
+    static constexpr bool mixed = true;
+};
+
+enum : unsigned { PH_GATES = 1u, PH_BP = 2u, PH_WARM = 4u, PH_REGAUGE = 8u };
+
+struct Control {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int err;
+    int cur;                 // message buffer holding the latest messages
+    long long sweeps_total;  // sum over BP calls of max-over-instances sweeps
+    int last_iters;          // sweeps of the last BP call (max over instances)
+    int not_conv;            // instances at max_iter in the last BP call
+    double last_dist;        // max over instances of the final dist/|E|
+    long long bp_calls;
+    long long nc_calls;      // BP calls in which some instance hit max_iter
+};
+
+struct Ctx {
+    // graph
+    const int4* edge_info;    // u, v, slot in u, slot in v
+    const int4* vert_edges;   // edge at slots 0..2 (-1 phantom), degree
+    const int* vert_inst;
+    const double* J;
+    const double* h;
+    const int* colour_edges;
+    const int* colour_off;    // [ncol + 1]
+    const int* last_colour;   // per vertex: colour of its last gate in a layer (-1: none)
+    const int* iso;           // vertices of degree 0
+    int n_iso;
+    int ncol;
+    int n, m, B;
+    const int* inst_vbeg;     // [B + 1]
+    const int* inst_m;
+    // state
+    void* Gamma;
+    double* lam;
+    void* T;
+    void* msg[2];
+    cd* D0;                   // mixed: warm-start defect F(m0) - tr F(m0) m0, [2m][CHI^2]
+    cd* t0;                   // mixed: tr F(m0), [2m]
+    cd* X;                    // regauge transforms [m][2][CHI^2]
+    double* acc;              // [3][B] per-sweep distance accumulators
+    int* inst_done;
+    int* inst_iters;
+    double* inst_dist;
+    double* stats;            // discarded weight, log fidelity, SVD pairs, SVD rotations
+    Control* ctl;
+    // parameters
+    int chi;
+    double svd_cut, eig_cut;
+    double tol;
+    int max_iter;
+    unsigned phases;
+    int k0, k1, Ksched;       // layers k0..k1 with tau = k/Ksched; Ksched = 0: one layer at (tZ1, tX1)
+    double dt, tZ1, tX1;
+    int nblocks;
+    int bar_expect;           // arrivals per grid barrier (= nblocks; larger only in the timeout test)
+    long long spin_limit;
+};
+
+template <int CHI> __host__ __device__ constexpr int sstride(int k) {
+    return k == 0 ? CHI * CHI : (k == 1 ? CHI : 1);
+}
+__host__ __device__ inline void others_of(int s, int& o0, int& o1) {
+    o0 = (s == 0) ? 1 : 0;
+    o1 = (s == 2) ? 1 : 2;
+}
+__device__ __forceinline__ double lam_get(const double* lam, int CHI, int e, int j) {
+    return e < 0 ? (j == 0 ? 1.0 : 0.0) : __ldcg(lam + (size_t)e * CHI + j);
+}
+
+template <int CHI> struct Shape {
+    static constexpr int TPB = CHI >= 8 ? 256 : 512;
+    static constexpr int TG = 2 * CHI * CHI;                    // gate team
+    static constexpr int TB = 2 * CHI * CHI >= 32 ? 2 * CHI * CHI : 32;   // BP team
+    static constexpr int TR = CHI * CHI;                        // regauge-edge team
+    static constexpr int TV = 32;                               // BP-init team (one warp)
+    static constexpr int TRV = CHI >= 8 ? 128 : 32;             // regauge-vertex team
+};
+
+// ===========================================================================
+// gates: simple update of one edge (team of 2 CHI^2 threads)
+// ===========================================================================
+template <int CHI>
+struct GateSm {
+    cd X[4][CHI][CHI * CHI];   // [block][col][row]: (a,0) (a,1) (b,0) (b,1); reused for staging
+    cd vk[4][CHI];
+    double tau[4][CHI];
+    cd M[4 * CHI * CHI];
+    cd V[4 * CHI * CHI];
+    double w[2][CHI * CHI];
+    double lab[CHI];
+    double sig[2 * CHI];
+    cd ph[4];
+    int perm[2 * CHI];
+    int keep;
+    int flag;
+    int nrot;
+};
+
+template <int CHI, class Mode>
+__device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& sm, double tZ, double cX, double sX,
+                          int colour) {
+    using TS = typename Mode::TS;
+    constexpr int NM = 2 * CHI, NR = CHI * CHI, G = NR / 2, TEAM = 2 * CHI * CHI;
+    C<TS>* Gam = (C<TS>*)c.Gamma;
+    const int4 ei = c.edge_info[e];
+    const int vtx[2] = {ei.x, ei.y};
+    const int slot[2] = {ei.z, ei.w};
+    int oe[2][2], os[2][2];
+    for (int x = 0; x < 2; ++x) {
+        const int4 ve = c.vert_edges[vtx[x]];
+        const int es[3] = {ve.x, ve.y, ve.z};
+        others_of(slot[x], os[x][0], os[x][1]);
+        oe[x][0] = es[os[x][0]];
+        oe[x][1] = es[os[x][1]];
+    }
+    for (int t = tid; t < 2 * NR; t += TEAM) {
+        const int x = t / NR, J = t % NR;
+        sm.w[x][J] = lam_get(c.lam, CHI, oe[x][0], J / CHI) * lam_get(c.lam, CHI, oe[x][1], J % CHI);
+    }
+    for (int t = tid; t < CHI; t += TEAM) sm.lab[t] = __ldcg(c.lam + (size_t)e * CHI + t);
+    team_bar<TEAM>(team);
+    for (int t = tid; t < 4 * CHI * NR; t += TEAM) {
+        const int blk = t / (CHI * NR), rem = t % (CHI * NR);
+        const int col = rem / NR, row = rem % NR;
+        const int x = blk >> 1, i = blk & 1;
+        const size_t off = (size_t)vtx[x] * (2 * CHI * CHI * CHI) + (size_t)i * CHI * CHI * CHI +
+                           col * sstride<CHI>(slot[x]) + (row / CHI) * sstride<CHI>(os[x][0]) +
+                           (row % CHI) * sstride<CHI>(os[x][1]);
+        const cd gv = ccast<double>(ldcg(Gam + off));
+        sm.X[blk][col][row] = sm.w[x][row] * gv;
+    }
+    team_bar<TEAM>(team);
+
+    // ---- Householder QR of the four CHI^2 x CHI blocks, G threads per block ----
+    const int blk = tid / G, l = tid % G;
+    const unsigned gm = group_mask<G>();
+    const int r0 = l, r1 = l + G;
+    for (int k = 0; k < CHI; ++k) {
+        cd* Xk = sm.X[blk][k];
+        const cd z = cd{0.0, 0.0};
+        const cd x0 = (r0 >= k) ? Xk[r0] : z;
+        const cd x1 = (r1 >= k) ? Xk[r1] : z;
+        const double nrm2 = group_sum<G>(norm2(x0) + norm2(x1), gm);
+        const cd xkk = Xk[k];
+        const double nrm = nr_sqrt(nrm2);
+        const double a2 = norm2(xkk);
+        const double ra = a2 > 0.0 ? nr_rsqrt(a2) : 0.0;
+        const double axkk = a2 * ra;
+        const cd ph = a2 > 0.0 ? cd{xkk.x * ra, xkk.y * ra} : cd{1.0, 0.0};
+        const double tau = nrm > 0.0 ? nr_rcp(nrm * (nrm + axkk)) : 0.0;
+        const cd vkk = (axkk + nrm) * ph;
+        const cd v0 = (r0 == k) ? vkk : x0;
+        const cd v1 = x1;
+        for (int cc = k + 1; cc < CHI; ++cc) {
+            cd* Xc = sm.X[blk][cc];
+            const cd y0 = Xc[r0], y1 = Xc[r1];
+            cd d = cfmac(v0, y0, cfmac(v1, y1, z));
+            d.x = group_sum<G>(d.x, gm);
+            d.y = group_sum<G>(d.y, gm);
+            const cd td = tau * d;
+            if (r0 >= k) Xc[r0] = y0 - v0 * td;
+            Xc[r1] = y1 - v1 * td;
+        }
+        __syncwarp(gm);
+        if (r0 == k) Xk[k] = (-nrm) * ph;
+        if (l == 0) {
+            sm.vk[blk][k] = vkk;
+            sm.tau[blk][k] = tau;
+        }
+        __syncwarp(gm);
+    }
+    team_bar<TEAM>(team);
+
+    // ---- core matrix M (column-major NM x NM); the 4 diagonal gate phases first ----
+    if (tid < 4) {
+        const int Da = c.vert_edges[vtx[0]].w, Db = c.vert_edges[vtx[1]].w;
+        const double ha = c.h[vtx[0]] * nr_rcp((double)Da), hb = c.h[vtx[1]] * nr_rcp((double)Db), Je = c.J[e];
+        const double za = 1.0 - 2.0 * (tid >> 1), zb = 1.0 - 2.0 * (tid & 1);
+        double sn, cs;
+        sincos(-tZ * (Je * za * zb + ha * za + hb * zb), &sn, &cs);
+        sm.ph[tid] = cd{cs, sn};
+    }
+    team_bar<TEAM>(team);
+    for (int t = tid; t < NM * NM; t += TEAM) {
+        const int col = t / NM, row = t % NM;
+        const int ia = row / CHI, r = row % CHI, ib = col / CHI, rp = col % CHI;
+        cd acc = cd{0.0, 0.0};
+        const int j0 = r > rp ? r : rp;
+        for (int j = j0; j < CHI; ++j) acc = cfma(sm.lab[j] * sm.X[ia][j][r], sm.X[2 + ib][j][rp], acc);
+        sm.M[t] = sm.ph[2 * ia + ib] * acc;
+    }
+    if (tid == 0) sm.nrot = 0;
+    team_bar<TEAM>(team);
+
+    // ---- SVD of M ----
+    int nrot = 0, sweeps;
+    if constexpr (TEAM <= 32) {
+        WarpGroup grp{group_mask<TEAM>()};
+        sweeps = jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), 1e-15, 60, true, &nrot);
+    } else {
+        TeamGroup<TEAM> grp{team, &sm.flag};
+        sweeps = jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), 1e-15, 60, true, &nrot);
+    }
+    if (nrot) atomicAdd(&sm.nrot, nrot);
+    team_bar<TEAM>(team);
+    for (int cc = tid; cc < NM; cc += TEAM) {
+        double s2 = 0.0;
+        for (int r = 0; r < NM; ++r) s2 += norm2(sm.M[cc * NM + r]);
+        sm.sig[cc] = nr_sqrt(s2);
+    }
+    team_bar<TEAM>(team);
+    for (int cc = tid; cc < NM; cc += TEAM) sm.perm[desc_rank(sm.sig, NM, cc)] = cc;
+    team_bar<TEAM>(team);
+    if (tid == 0) {
+        const double smax = sm.sig[sm.perm[0]];
+        int cnt = 0;
+        double tot = 0.0;
+        for (int r = 0; r < NM; ++r) {
+            const double s = sm.sig[sm.perm[r]];
+            tot += s * s;
+            cnt += (s > c.svd_cut * smax) ? 1 : 0;
+        }
+        int keep = cnt < c.chi ? cnt : c.chi;
+        if (keep < 1) keep = 1;
+        double kept = 0.0, drop = 0.0;
+        for (int r = 0; r < NM; ++r) {
+            const double s = sm.sig[sm.perm[r]];
+            if (r < keep) kept += s * s; else drop += s * s;
+        }
+        const double inv = kept > 0.0 ? nr_rsqrt(kept) : 0.0;
+        for (int r = 0; r < CHI; ++r) c.lam[(size_t)e * CHI + r] = (r < keep) ? sm.sig[sm.perm[r]] * inv : 0.0;
+        const double disc = tot > 0.0 ? drop * nr_rcp(tot) : 0.0;
+        atomicAdd(&c.stats[0], disc);
+        atomicAdd(&c.stats[1], 2.0 * log1p(-disc));
+        atomicAdd(&c.stats[2], (double)sweeps * (NM - 1) * (NM / 2));
+        atomicAdd(&c.stats[3], (double)sm.nrot);
+        sm.keep = keep;
+    }
+    team_bar<TEAM>(team);
+    const int keep = sm.keep;
+
+    // ---- new Gamma: reflectors of each block applied to U (side a) / V^* (side b) ----
+    // FP64 mode in double, mixed mode in float (the result is stored in complex64).
+    using RB = typename Mode::TS;
+    C<RB> E0[CHI], E1[CHI];
+    const int x = blk >> 1, i = blk & 1;
+#pragma unroll
+    for (int cc = 0; cc < CHI; ++cc) {
+        E0[cc] = C<RB>{(RB)0, (RB)0};
+        E1[cc] = C<RB>{(RB)0, (RB)0};
+        if (r0 < CHI && cc < keep) {
+            const int pc = sm.perm[cc];
+            const int row = i * CHI + r0;
+            const cd u = (x == 0) ? nr_rcp(sm.sig[pc]) * sm.M[pc * NM + row] : conj(sm.V[pc * NM + row]);
+            E0[cc] = ccast<RB>(u);
+        }
+    }
+    // H_k = I - tau v v^H is applied as I - u u^H with u = sqrt(tau) v (|u| = sqrt 2), so
+    // neither factor over- or underflows when the reflector is tiny (matters in float).
+    for (int k = CHI - 1; k >= 0; --k) {
+        const double st = nr_sqrt(sm.tau[blk][k]);
+        const C<RB> v0 = ccast<RB>(st * ((r0 == k) ? sm.vk[blk][k] : ((r0 > k) ? sm.X[blk][k][r0] : cd{0.0, 0.0})));
+        const C<RB> v1 = ccast<RB>(st * sm.X[blk][k][r1]);
+#pragma unroll
+        for (int cc = 0; cc < CHI; ++cc) {
+            C<RB> d = cfmac(v0, E0[cc], cfmac(v1, E1[cc], C<RB>{(RB)0, (RB)0}));
+            d.x = group_sum<G>(d.x, gm);
+            d.y = group_sum<G>(d.y, gm);
+            E0[cc] = E0[cc] - v0 * d;
+            E1[cc] = E1[cc] - v1 * d;
+        }
+    }
+    const double w0 = sm.w[x][r0], w1 = sm.w[x][r1];
+    const RB iw0 = w0 > 0.0 ? (RB)nr_rcp(w0) : (RB)0, iw1 = w1 > 0.0 ? (RB)nr_rcp(w1) : (RB)0;
+    team_bar<TEAM>(team);   // everyone is done reading the reflectors in sm.X
+    // stage Gamma~ (rounded to storage) in sm.X as [x*2+i][col][row]
+#pragma unroll
+    for (int cc = 0; cc < CHI; ++cc) {
+        sm.X[blk][cc][r0] = ccast<double>(ccast<TS>(iw0 * E0[cc]));
+        sm.X[blk][cc][r1] = ccast<double>(ccast<TS>(iw1 * E1[cc]));
+    }
+    team_bar<TEAM>(team);
+    // write back, applying the mixing gate to a vertex after its last gate of the layer
+    for (int t = tid; t < 2 * CHI * NR; t += TEAM) {
+        const int xx = t / (CHI * NR), rem = t % (CHI * NR);
+        const int col = rem / NR, row = rem % NR;
+        C<TS> g0 = ccast<TS>(sm.X[2 * xx][col][row]);
+        C<TS> g1 = ccast<TS>(sm.X[2 * xx + 1][col][row]);
+        if (c.last_colour[vtx[xx]] == colour) {
+            const C<TS> a0 = g0, a1 = g1;
+            const TS cs = (TS)cX, sn = (TS)sX;
+            // [[c, -i s], [-i s, c]]
+            g0 = C<TS>{cs * a0.x + sn * a1.y, cs * a0.y - sn * a1.x};
+            g1 = C<TS>{sn * a0.y + cs * a1.x, -sn * a0.x + cs * a1.y};
+        }
+        const size_t base = (size_t)vtx[xx] * (2 * CHI * CHI * CHI);
+        const size_t off = col * sstride<CHI>(slot[xx]) + (row / CHI) * sstride<CHI>(os[xx][0]) +
+                           (row % CHI) * sstride<CHI>(os[xx][1]);
+        Gam[base + off] = g0;
+        Gam[base + CHI * CHI * CHI + off] = g1;
+    }
+}
+
+// mixing gate on one vertex (used for degree-0 vertices only)
+template <int CHI, class Mode>
+__device__ void mixing_vertex(const Ctx& c, int a, int tid, int TEAM, double cX, double sX) {
+    using TS = typename Mode::TS;
+    constexpr int H = CHI * CHI * CHI;
+    C<TS>* g = (C<TS>*)c.Gamma + (size_t)a * 2 * H;
+    for (int r = tid; r < H; r += TEAM) {
+        const C<TS> a0 = ldcg(g + r), a1 = ldcg(g + H + r);
+        const TS cs = (TS)cX, sn = (TS)sX;
+        g[r] = C<TS>{cs * a0.x + sn * a1.y, cs * a0.y - sn * a1.x};
+        g[H + r] = C<TS>{sn * a0.y + cs * a1.x, -sn * a0.x + cs * a1.y};
+    }
+}
+
+// ===========================================================================
+// BP init: symmetric split, warm start, and (mixed) the FP64 warm-start defect
+// ===========================================================================
+template <int CHI, class Mode>
+__device__ void bp_init_vertex(const Ctx& c, int a, int tid, int team, int cur, bool warm, double* wsm, cd* tsm) {
+    using TS = typename Mode::TS;
+    constexpr int H = CHI * CHI * CHI, CC = CHI * CHI, TEAM = Shape<CHI>::TV;
+    const int4 ve = c.vert_edges[a];
+    const int es[3] = {ve.x, ve.y, ve.z};
+    // wsm[3][CHI]: lambda^{1/2} per slot, then m0 diagonal per slot
+    if (tid < 3 * CHI) {
+        const int k = tid / CHI, j = tid % CHI;
+        wsm[tid] = nr_sqrt(lam_get(c.lam, CHI, es[k], j));
+        double s = 0.0;
+        for (int q = 0; q < CHI; ++q) s += lam_get(c.lam, CHI, es[k], q);
+        wsm[3 * CHI + tid] = s > 0.0 ? lam_get(c.lam, CHI, es[k], j) * nr_rcp(s) : 0.0;
+    }
+    __syncwarp();
+    const C<TS>* g = (const C<TS>*)c.Gamma + (size_t)a * 2 * H;
+    C<TS>* T = (C<TS>*)c.T + (size_t)a * 2 * H;
+    for (int t = tid; t < 2 * H; t += TEAM) {
+        const int r = t % H;
+        const int j0 = r / CC, j1 = (r / CHI) % CHI, j2 = r % CHI;
+        const double f = wsm[j0] * wsm[CHI + j1] * wsm[2 * CHI + j2];
+        const cd tv = f * ccast<double>(ldcg(g + t));
+        T[t] = ccast<TS>(tv);
+        if constexpr (Mode::mixed) tsm[t] = ccast<double>(ccast<TS>(tv));
+    }
+    // outgoing messages of a
+    for (int s = 0; s < 3; ++s) {
+        if (es[s] < 0) continue;
+        const int u = c.edge_info[es[s]].x;
+        const int out = 2 * es[s] + (a == u ? 0 : 1);
+        if constexpr (!Mode::mixed) {
+            if (warm) {
+                cd* mo = (cd*)c.msg[cur] + (size_t)out * CC;
+                for (int r = tid; r < CC; r += TEAM) {
+                    const int j = r / CHI, jp = r % CHI;
+                    mo[r] = cd{j == jp ? wsm[3 * CHI + s * CHI + j] : 0.0, 0.0};
+                }
+            }
+        } else {
+            if (warm) {
+                cf* mo = (cf*)c.msg[cur] + (size_t)out * CC;
+                for (int r = tid; r < CC; r += TEAM) mo[r] = cf{0.f, 0.f};
+            }
+        }
+    }
+    if constexpr (Mode::mixed) {
+        __syncwarp();
+        // F0 = F(m0_o0, m0_o1) in FP64 for each outgoing slot; D0 = F0 - tr(F0) m0_s
+        constexpr int NPL = (CC + 31) / 32;   // entries per lane
+        for (int s = 0; s < 3; ++s) {
+            if (es[s] < 0) continue;
+            int o0, o1;
+            others_of(s, o0, o1);
+            const int ss = sstride<CHI>(s), s0 = sstride<CHI>(o0), s1 = sstride<CHI>(o1);
+            const int u = c.edge_info[es[s]].x;
+            const int out = 2 * es[s] + (a == u ? 0 : 1);
+            cd f[NPL];
+            cd tr = cd{0.0, 0.0};
+#pragma unroll
+            for (int q8 = 0; q8 < NPL; ++q8) {
+                f[q8] = cd{0.0, 0.0};
+                const int r = tid + 32 * q8;
+                if (r >= CC) continue;
+                const int j = r / CHI, jp = r % CHI;
+                for (int ii = 0; ii < 2; ++ii)
+                    for (int p = 0; p < CHI; ++p) {
+                        const double wp = wsm[3 * CHI + o0 * CHI + p];
+                        if (wp == 0.0) continue;
+                        for (int q = 0; q < CHI; ++q) {
+                            const double wq = wsm[3 * CHI + o1 * CHI + q];
+                            if (wq == 0.0) continue;
+                            const int base = ii * H + p * s0 + q * s1;
+                            f[q8] = cfmac(tsm[base + jp * ss], (wp * wq) * tsm[base + j * ss], f[q8]);
+                        }
+                    }
+                if (j == jp) tr = tr + f[q8];
+            }
+            tr.x = group_sum<32>(tr.x, 0xffffffffu);
+            tr.y = group_sum<32>(tr.y, 0xffffffffu);
+#pragma unroll
+            for (int q8 = 0; q8 < NPL; ++q8) {
+                const int r = tid + 32 * q8;
+                if (r >= CC) continue;
+                const int j = r / CHI, jp = r % CHI;
+                const double m0 = (j == jp) ? wsm[3 * CHI + s * CHI + j] : 0.0;
+                c.D0[(size_t)out * CC + r] = f[q8] - m0 * tr;
+            }
+            if (tid == 0) c.t0[out] = tr;
+        }
+    }
+}
+
+// ===========================================================================
+// BP sweep for one vertex: all of its outgoing messages (team TB)
+// ===========================================================================
+template <int CHI, class Mode>
+struct BPSm {
+    using TS = typename Mode::TS;
+    C<TS> T[2 * CHI * CHI * CHI];
+    C<TS> P[2 * CHI * CHI * CHI];
+    C<TS> Q[2 * CHI * CHI * CHI];
+    C<TS> min[3][CHI * CHI];       // FP64: incoming messages; mixed: incoming m = m0 + delta
+    C<TS> din[3][CHI * CHI];       // mixed: incoming delta
+    C<TS> mout[3][CHI * CHI];
+    C<TS> D[3][CHI * CHI];
+    C<TS> DV[3][CHI * CHI];
+    double m0[3][CHI];             // warm-start diagonals per slot
+    cd itr[3];
+    cd trd[3];                     // mixed: tr F(delta terms)
+    double dl[3];
+};
+
+template <int CHI, class Mode>
+__device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode>& sm) {
+    using TS = typename Mode::TS;
+    using CT = C<TS>;
+    constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H = CHI * CHI * CHI;
+    const int4 ve = c.vert_edges[a];
+    const int es[3] = {ve.x, ve.y, ve.z};
+    int out_idx[3], in_idx[3];
+    for (int k = 0; k < 3; ++k) {
+        if (es[k] >= 0) {
+            const int u = c.edge_info[es[k]].x;
+            out_idx[k] = 2 * es[k] + (a == u ? 0 : 1);
+            in_idx[k] = 2 * es[k] + (a == u ? 1 : 0);
+        } else {
+            out_idx[k] = in_idx[k] = -1;
+        }
+    }
+    const CT* src = (const CT*)c.msg[cur];
+    CT* dst = (CT*)c.msg[cur ^ 1];
+    const CT* Tg = (const CT*)c.T + (size_t)a * 2 * H;
+    for (int t = tid; t < 2 * H; t += TEAM) sm.T[t] = ldcg(Tg + t);
+    if (tid < 3 * CHI) {
+        const int k = tid / CHI, j = tid % CHI;
+        double s = 0.0;
+        for (int q = 0; q < CHI; ++q) s += lam_get(c.lam, CHI, es[k], q);
+        sm.m0[k][j] = s > 0.0 ? lam_get(c.lam, CHI, es[k], j) * nr_rcp(s) : 0.0;
+    }
+    team_bar<TEAM>(team);
+    for (int t = tid; t < 3 * CC; t += TEAM) {
+        const int k = t / CC, r = t % CC;
+        const int j = r / CHI, jp = r % CHI;
+        if constexpr (!Mode::mixed) {
+            sm.min[k][r] = (in_idx[k] >= 0) ? ldcg(src + (size_t)in_idx[k] * CC + r)
+                                            : CT{(TS)(r == 0 ? 1 : 0), (TS)0};
+        } else {
+            const CT dv = (in_idx[k] >= 0) ? ldcg(src + (size_t)in_idx[k] * CC + r) : CT{0.f, 0.f};
+            sm.din[k][r] = dv;
+            const float m0 = (j == jp) ? (float)sm.m0[k][j] : 0.f;
+            sm.min[k][r] = CT{dv.x + m0, dv.y};
+        }
+    }
+    team_bar<TEAM>(team);
+    for (int s = 0; s < 3; ++s) {
+        if (es[s] < 0) continue;
+        int o0, o1;
+        others_of(s, o0, o1);
+        const int ss = sstride<CHI>(s), s0 = sstride<CHI>(o0), s1 = sstride<CHI>(o1);
+        // P[i][a'][b][j] = sum_a T[i; a@o0, b@o1, j@s] x_o0[a][a']
+        //   FP64: x = m;  mixed: x = delta (and P2 = T * m0_o0 handled in the Q step)
+        const CT* x0 = Mode::mixed ? sm.din[o0] : sm.min[o0];
+        for (int t = tid; t < 2 * H; t += TEAM) {
+            const int i = t / H, ap = (t / CC) % CHI, b = (t / CHI) % CHI, j = t % CHI;
+            CT acc = CT{(TS)0, (TS)0};
+            for (int q = 0; q < CHI; ++q) acc = cfma(sm.T[i * H + q * s0 + b * s1 + j * ss], x0[q * CHI + ap], acc);
+            sm.P[t] = acc;
+        }
+        team_bar<TEAM>(team);
+        // Q[i][a'][b'][j] = sum_b P[i][a'][b][j] m_o1[b][b']  (+ mixed: m0_o0[a'] T[i; a'@o0, b@o1] delta_o1[b][b'])
+        for (int t = tid; t < 2 * H; t += TEAM) {
+            const int i = t / H, ap = (t / CC) % CHI, bp = (t / CHI) % CHI, j = t % CHI;
+            CT acc = CT{(TS)0, (TS)0};
+            for (int q = 0; q < CHI; ++q) acc = cfma(sm.P[i * H + ap * CC + q * CHI + j], sm.min[o1][q * CHI + bp], acc);
+            if constexpr (Mode::mixed) {
+                const TS w = (TS)sm.m0[o0][ap];
+                if (w != (TS)0) {
+                    CT a2 = CT{(TS)0, (TS)0};
+                    for (int q = 0; q < CHI; ++q)
+                        a2 = cfma(sm.T[i * H + ap * s0 + q * s1 + j * ss], sm.din[o1][q * CHI + bp], a2);
+                    acc = acc + w * a2;
+                }
+            }
+            sm.Q[t] = acc;
+        }
+        team_bar<TEAM>(team);
+        // out[j][j'] = sum_{i,a',b'} Q[i][a'][b'][j] conj(T[i; a'@o0, b'@o1, j'@s])
+        for (int t = tid; t < CC; t += TEAM) {
+            const int j = t / CHI, jp = t % CHI;
+            CT acc = CT{(TS)0, (TS)0};
+            for (int i = 0; i < 2; ++i)
+                for (int ap = 0; ap < CHI; ++ap)
+                    for (int bp = 0; bp < CHI; ++bp)
+                        acc = cfmac(sm.T[i * H + ap * s0 + bp * s1 + jp * ss], sm.Q[i * H + ap * CC + bp * CHI + j], acc);
+            sm.mout[s][t] = acc;
+        }
+        team_bar<TEAM>(team);
+    }
+    // normalisation (FP64): FP64 mode m' = F / tr F; mixed delta' = (D0 + Fd - m0 tr Fd) / (t0 + tr Fd)
+    if (tid < 3) {
+        cd tr = cd{0.0, 0.0};
+        if (es[tid] >= 0)
+            for (int j = 0; j < CHI; ++j) tr = tr + ccast<double>(sm.mout[tid][j * CHI + j]);
+        if constexpr (Mode::mixed) {
+            if (es[tid] >= 0) tr = tr + ldcg(c.t0 + out_idx[tid]);
+        }
+        const double n2 = norm2(tr);
+        const double in2 = n2 > 0.0 ? nr_rcp(n2) : 0.0;
+        sm.itr[tid] = cd{tr.x * in2, -tr.y * in2};
+        if constexpr (Mode::mixed) {
+            // tr F(delta terms), without t0, for the m0 term of the update
+            cd trd = cd{0.0, 0.0};
+            if (es[tid] >= 0)
+                for (int j = 0; j < CHI; ++j) trd = trd + ccast<double>(sm.mout[tid][j * CHI + j]);
+            sm.trd[tid] = trd;
+        }
+    }
+    team_bar<TEAM>(team);
+    for (int t = tid; t < 3 * CC; t += TEAM) {
+        const int k = t / CC, r = t % CC;
+        if (es[k] < 0) {
+            sm.D[k][r] = CT{(TS)0, (TS)0};
+            continue;
+        }
+        const CT old = ldcg(src + (size_t)out_idx[k] * CC + r);
+        CT nv;
+        if constexpr (!Mode::mixed) {
+            nv = sm.itr[k] * sm.mout[k][r];
+        } else {
+            const int j = r / CHI, jp = r % CHI;
+            const double m0 = (j == jp) ? sm.m0[k][j] : 0.0;
+            const cd num = ldcg(c.D0 + (size_t)out_idx[k] * CC + r) + ccast<double>(sm.mout[k][r]) - m0 * sm.trd[k];
+            nv = ccast<TS>(sm.itr[k] * num);
+        }
+        dst[(size_t)out_idx[k] * CC + r] = nv;
+        sm.D[k][r] = nv - old;
+    }
+    team_bar<TEAM>(team);
+    constexpr int GJ = CC / 2;
+    if (tid < 3 * GJ) {
+        const int k = tid / GJ, g = tid % GJ;
+        WarpGroup grp{group_mask<GJ>()};
+        jacobi_svd<CHI, TS>(sm.D[k], sm.DV[k], g, grp, group_mask<CHI>(), Mode::mixed ? (TS)1e-6 : (TS)1e-15, 60,
+                            true);
+        if (g == 0) {
+            double sacc = 0.0;
+            for (int cc = 0; cc < CHI; ++cc) {
+                double n2 = 0.0;
+                for (int r = 0; r < CHI; ++r) n2 += (double)norm2(sm.D[k][cc * CHI + r]);
+                sacc += nr_sqrt(n2);
+            }
+            sm.dl[k] = sacc;
+        }
+    }
+    team_bar<TEAM>(team);
+    return sm.dl[0] + sm.dl[1] + sm.dl[2];
+}
+
+// copy a frozen instance's outgoing messages to the other buffer
+template <int CHI, class Mode>
+__device__ void bp_copy_vertex(const Ctx& c, int a, int tid, int TEAM, int cur) {
+    using CT = C<typename Mode::TS>;
+    constexpr int CC = CHI * CHI;
+    const int4 ve = c.vert_edges[a];
+    const int es[3] = {ve.x, ve.y, ve.z};
+    const CT* src = (const CT*)c.msg[cur];
+    CT* dst = (CT*)c.msg[cur ^ 1];
+    for (int k = 0; k < 3; ++k) {
+        if (es[k] < 0) continue;
+        const int u = c.edge_info[es[k]].x;
+        const int out = 2 * es[k] + (a == u ? 0 : 1);
+        for (int r = tid; r < CC; r += TEAM) dst[(size_t)out * CC + r] = ldcg(src + (size_t)out * CC + r);
+    }
+}
+
+// ===========================================================================
+// regauge, edge part (team CHI^2): FP64 eigen/SVD, transforms X_a, X_b and lambda
+// ===========================================================================
+template <int CHI>
+struct RGSm {
+    cd Am[2][CHI * CHI];
+    cd Vm[2][CHI * CHI];
+    double w[2][CHI];
+    cd sq[2][CHI * CHI];
+    cd isq[2][CHI * CHI];
+    cd M[CHI * CHI];
+    cd VM[CHI * CHI];
+    double sig[CHI];
+    int perm[CHI];
+    double scal[2];
+};
+
+template <int CHI, class Mode>
+__device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RGSm<CHI>& sm) {
+    constexpr int TEAM = CHI * CHI, CC = CHI * CHI, GJ = CC / 2;
+    // Hermitian parts of m_{a->b} (x = 0) and m_{b->a} (x = 1), column-major
+    for (int t = tid; t < 2 * CC; t += TEAM) {
+        const int x = t / CC, r = t % CC;
+        const int row = r % CHI, col = r / CHI;
+        cd v, vt;
+        if constexpr (!Mode::mixed) {
+            const cd* mm = (const cd*)c.msg[cur] + (size_t)(2 * e + x) * CC;
+            v = ldcg(mm + row * CHI + col);
+            vt = ldcg(mm + col * CHI + row);
+        } else {
+            const cf* mm = (const cf*)c.msg[cur] + (size_t)(2 * e + x) * CC;
+            v = ccast<double>(ldcg(mm + row * CHI + col));
+            vt = ccast<double>(ldcg(mm + col * CHI + row));
+            if (row == col) {
+                double s = 0.0;
+                for (int q = 0; q < CHI; ++q) s += __ldcg(c.lam + (size_t)e * CHI + q);
+                const double m0 = s > 0.0 ? __ldcg(c.lam + (size_t)e * CHI + row) * nr_rcp(s) : 0.0;
+                v.x += m0;
+                vt.x += m0;
+            }
+        }
+        sm.Am[x][col * CHI + row] = cd{0.5 * (v.x + vt.x), 0.5 * (v.y - vt.y)};
+    }
+    team_bar<TEAM>(team);
+    {
+        const int x = tid / GJ, g = tid % GJ;
+        WarpGroup grp{group_mask<GJ>()};
+        jacobi_svd<CHI, double>(sm.Am[x], sm.Vm[x], g, grp, group_mask<CHI>(), 1e-15, 60, true);
+    }
+    team_bar<TEAM>(team);
+    for (int t = tid; t < 2 * CHI; t += TEAM) {
+        const int x = t / CHI, k = t % CHI;
+        double n2 = 0.0, sg = 0.0;
+        for (int r = 0; r < CHI; ++r) {
+            const cd av = sm.Am[x][k * CHI + r], vv = sm.Vm[x][k * CHI + r];
+            n2 += norm2(av);
+            sg += vv.x * av.x + vv.y * av.y;
+        }
+        const double wv = nr_sqrt(n2);
+        sm.w[x][k] = sg >= 0.0 ? wv : -wv;
+    }
+    team_bar<TEAM>(team);
+    for (int t = tid; t < 2 * CC; t += TEAM) {
+        const int x = t / CC, r = t % CC;
+        const int j = r / CHI, jp = r % CHI;
+        double wmax = 0.0;
+        for (int k = 0; k < CHI; ++k) wmax = fmax(wmax, sm.w[x][k]);
+        cd s1 = cd{0.0, 0.0}, s2 = cd{0.0, 0.0};
+        for (int k = 0; k < CHI; ++k) {
+            const double wk = sm.w[x][k];
+            if (!(wk > c.eig_cut * wmax)) continue;
+            const double isq = nr_rsqrt(wk);
+            const double sq = wk * isq;
+            const cd vv = sm.Vm[x][k * CHI + j] * conj(sm.Vm[x][k * CHI + jp]);
+            s1 = cfma(cd{sq, 0.0}, vv, s1);
+            s2 = cfma(cd{isq, 0.0}, vv, s2);
+        }
+        sm.sq[x][r] = s1;
+        sm.isq[x][r] = s2;
+    }
+    team_bar<TEAM>(team);
+    for (int t = tid; t < CC; t += TEAM) {
+        const int k = t % CHI, l = t / CHI;
+        cd acc = cd{0.0, 0.0};
+        for (int j = 0; j < CHI; ++j) acc = cfma(sm.sq[0][j * CHI + k], sm.sq[1][j * CHI + l], acc);
+        sm.M[l * CHI + k] = acc;
+    }
+    team_bar<TEAM>(team);
+    if (tid < GJ) {
+        WarpGroup grp{group_mask<GJ>()};
+        jacobi_svd<CHI, double>(sm.M, sm.VM, tid, grp, group_mask<CHI>(), 1e-15, 60, true);
+    }
+    team_bar<TEAM>(team);
+    for (int cc = tid; cc < CHI; cc += TEAM) {
+        double n2 = 0.0;
+        for (int r = 0; r < CHI; ++r) n2 += norm2(sm.M[cc * CHI + r]);
+        sm.sig[cc] = nr_sqrt(n2);
+    }
+    team_bar<TEAM>(team);
+    for (int cc = tid; cc < CHI; cc += TEAM) sm.perm[desc_rank(sm.sig, CHI, cc)] = cc;
+    team_bar<TEAM>(team);
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int cc = 0; cc < CHI; ++cc) tot += sm.sig[cc] * sm.sig[cc];
+        const double nrm = nr_sqrt(tot);
+        sm.scal[0] = nrm;
+        sm.scal[1] = nr_sqrt(nrm);
+        const double inrm = nrm > 0.0 ? nr_rcp(nrm) : 0.0;
+        const double smax = sm.sig[sm.perm[0]];
+        for (int r = 0; r < CHI; ++r) {
+            const double s = sm.sig[sm.perm[r]];
+            c.lam[(size_t)e * CHI + r] = (nrm > 0.0 && s > c.svd_cut * smax) ? s * inrm : 0.0;
+        }
+    }
+    team_bar<TEAM>(team);
+    for (int t = tid; t < 2 * CC; t += TEAM) {
+        const int x = t / CC, r = t % CC;
+        const int jpp = r / CHI, j = r % CHI;
+        const int pc = sm.perm[j];
+        const double s = sm.sig[pc];
+        cd acc = cd{0.0, 0.0};
+        const bool kept = sm.scal[0] > 0.0 && s > c.svd_cut * sm.sig[sm.perm[0]];
+        if (kept) {
+            for (int jp = 0; jp < CHI; ++jp) {
+                const cd u = (x == 0) ? nr_rcp(s) * sm.M[pc * CHI + jp] : conj(sm.VM[pc * CHI + jp]);
+                acc = cfma(sm.isq[x][jp * CHI + jpp], u, acc);
+            }
+            acc = sm.scal[1] * acc;
+        }
+        c.X[((size_t)e * 2 + x) * CC + r] = acc;
+    }
+}
+
+// regauge, vertex part: Gamma_a = T_a x_slot X (team TV, buffers in shared memory)
+template <int CHI, class Mode>
+__device__ void regauge_vertex(const Ctx& c, int a, int tid, int team, C<typename Mode::TS>* buf) {
+    using TS = typename Mode::TS;
+    using CT = C<TS>;
+    constexpr int H = CHI * CHI * CHI, CC = CHI * CHI, TEAM = Shape<CHI>::TRV;
+    const int4 ve = c.vert_edges[a];
+    const int es[3] = {ve.x, ve.y, ve.z};
+    CT* b0 = buf;
+    CT* b1 = buf + 2 * H;
+    CT* Xs = buf + 4 * H;   // [3][CC]
+    for (int t = tid; t < 2 * H; t += TEAM) b0[t] = ldcg((const CT*)c.T + (size_t)a * 2 * H + t);
+    for (int t = tid; t < 3 * CC; t += TEAM) {
+        const int k = t / CC, r = t % CC;
+        cd v;
+        if (es[k] >= 0) {
+            const int side = (c.edge_info[es[k]].x == a) ? 0 : 1;
+            v = ldcg(c.X + ((size_t)es[k] * 2 + side) * CC + r);
+        } else {
+            v = cd{(r / CHI == r % CHI) ? 1.0 : 0.0, 0.0};
+        }
+        Xs[t] = ccast<TS>(v);
+    }
+    team_bar<TEAM>(team);
+    CT* cur = b0;
+    CT* nxt = b1;
+    for (int k = 0; k < 3; ++k) {
+        const int st = sstride<CHI>(k);
+        for (int t = tid; t < 2 * H; t += TEAM) {
+            const int jk = (t / st) % CHI;
+            const int base = t - jk * st;
+            CT acc = CT{(TS)0, (TS)0};
+            for (int q = 0; q < CHI; ++q) acc = cfma(cur[base + q * st], Xs[k * CC + q * CHI + jk], acc);
+            nxt[t] = acc;
+        }
+        team_bar<TEAM>(team);
+        CT* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    CT* g = (CT*)c.Gamma + (size_t)a * 2 * H;
+    for (int t = tid; t < 2 * H; t += TEAM) g[t] = cur[t];
+}
+
+// ===========================================================================
+// the persistent kernel
+// ===========================================================================
+template <int CHI, class Mode, unsigned PH>
+struct SmemSize {
+    static constexpr int TPB = Shape<CHI>::TPB;
+    static constexpr size_t gate = sizeof(GateSm<CHI>) * (TPB / Shape<CHI>::TG);
+    static constexpr size_t bp = sizeof(BPSm<CHI, Mode>) * (TPB / Shape<CHI>::TB) + 64 * sizeof(double);
+    static constexpr size_t rg = sizeof(RGSm<CHI>) * (TPB / Shape<CHI>::TR);
+    static constexpr size_t rv =
+        sizeof(C<typename Mode::TS>) * (4 * CHI * CHI * CHI + 3 * CHI * CHI) * (TPB / Shape<CHI>::TRV);
+    static constexpr size_t init = (sizeof(double) * 6 * CHI + (Mode::mixed ? sizeof(cd) * 2 * CHI * CHI * CHI : 0)) *
+                                   (TPB / 32);
+    static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
+    // bytes before the per-instance flags (which follow at this offset in the BP kernel)
+    static constexpr size_t value = mx(mx((PH & PH_GATES) ? gate : 0, (PH & PH_BP) ? mx(bp, init) : 0),
+                                       (PH & PH_REGAUGE) ? mx(rg, rv) : 0) + 16;
+};
+
+template <int CHI, class Mode, unsigned PH>
+__device__ __forceinline__ void anneal_body(const Ctx& c) {
+    using S = Shape<CHI>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const GridBarrier gb{&c.ctl->bar_count, &c.ctl->bar_gen, &c.ctl->err};
+    const unsigned nb = (unsigned)c.bar_expect;
+    const int nteams_total_g = c.nblocks * (S::TPB / S::TG);
+    int cur = *(volatile int*)&c.ctl->cur;
+    for (int k = c.k0; k <= c.k1; ++k) {
+        double tZ, tX;
+        if (c.Ksched > 0) {
+            const double tau = (double)k / (double)c.Ksched;
+            tZ = c.dt * tau;
+            tX = c.dt * (1.0 - tau);
+        } else {
+            tZ = c.tZ1;
+            tX = c.tX1;
+        }
+        double sX, cX;
+        sincos(tX, &sX, &cX);
+        if constexpr ((PH & PH_GATES) != 0u) {
+            const int team = threadIdx.x / S::TG, tid = threadIdx.x % S::TG;
+            GateSm<CHI>& sm = reinterpret_cast<GateSm<CHI>*>(smem)[team];
+            const int gteam = team * c.nblocks + blockIdx.x;
+            for (int col = 0; col < c.ncol; ++col) {
+                const int beg = c.colour_off[col], end = c.colour_off[col + 1];
+                for (int idx = beg + gteam; idx < end; idx += nteams_total_g)
+                    gate_edge<CHI, Mode>(c, c.colour_edges[idx], tid, team, sm, tZ, cX, sX, col);
+                if (col == c.ncol - 1)
+                    for (int q = gteam; q < c.n_iso; q += nteams_total_g)
+                        mixing_vertex<CHI, Mode>(c, c.iso[q], tid, S::TG, cX, sX);
+                if (!grid_sync(gb, nb, c.spin_limit)) return;
+            }
+            if (c.ncol == 0) {
+                for (int q = gteam; q < c.n_iso; q += nteams_total_g)
+                    mixing_vertex<CHI, Mode>(c, c.iso[q], tid, S::TG, cX, sX);
+                if (!grid_sync(gb, nb, c.spin_limit)) return;
+            }
+        }
+        if constexpr ((PH & PH_BP) != 0u) {
+            {
+                const int team = threadIdx.x / S::TV, tid = threadIdx.x % S::TV;
+                const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * (S::TPB / S::TV);
+                double* wsm = reinterpret_cast<double*>(smem) + team * 6 * CHI;
+                cd* tsm = reinterpret_cast<cd*>(reinterpret_cast<double*>(smem) + (S::TPB / 32) * 6 * CHI) +
+                          team * 2 * CHI * CHI * CHI;
+                for (int a = gteam; a < c.n; a += nt)
+                    bp_init_vertex<CHI, Mode>(c, a, tid, team, cur, (c.phases & PH_WARM) != 0, wsm, tsm);
+                const int g = blockIdx.x * S::TPB + threadIdx.x;
+                for (int b = g; b < c.B; b += c.nblocks * S::TPB) {
+                    c.inst_done[b] = 0;   // host-visible copy
+                    c.inst_iters[b] = 0;
+                    c.inst_dist[b] = 0.0;
+                    c.acc[b] = 0.0;
+                    c.acc[c.B + b] = 0.0;
+                    c.acc[2 * c.B + b] = 0.0;
+                }
+                if (!grid_sync(gb, nb, c.spin_limit)) return;
+            }
+            const int team = threadIdx.x / S::TB, tid = threadIdx.x % S::TB;
+            const int tpb_teams = S::TPB / S::TB;
+            BPSm<CHI, Mode>& sm = reinterpret_cast<BPSm<CHI, Mode>*>(smem)[team];
+            double* bsum = reinterpret_cast<double*>(smem + sizeof(BPSm<CHI, Mode>) * tpb_teams);
+            // every block keeps its own copy of the per-instance state; all blocks take
+            // identical decisions from the same accumulators, so one barrier per sweep suffices
+            int* done = reinterpret_cast<int*>(smem + SmemSize<CHI, Mode, PH>::value);
+            for (int b = threadIdx.x; b < c.B; b += S::TPB) done[b] = 0;
+            __syncthreads();
+            const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * tpb_teams;
+            int it = 0;
+            for (; it < c.max_iter; ++it) {
+                double* acc = c.acc + (size_t)(it % 3) * c.B;
+                double* acc_next = c.acc + (size_t)((it + 1) % 3) * c.B;
+                for (int b = blockIdx.x * S::TPB + threadIdx.x; b < c.B; b += c.nblocks * S::TPB) acc_next[b] = 0.0;
+                double mine = 0.0;
+                for (int a = gteam; a < c.n; a += nt) {
+                    const int inst = c.vert_inst[a];
+                    if (done[inst]) {
+                        bp_copy_vertex<CHI, Mode>(c, a, tid, S::TB, cur);
+                        continue;
+                    }
+                    const double d = bp_vertex<CHI, Mode>(c, a, tid, team, cur, sm);
+                    if (c.B == 1) mine += d;
+                    else if (tid == 0) atomicAdd(acc + inst, d);
+                }
+                if (c.B == 1) {
+                    if (tid == 0) bsum[team] = mine;
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        double s = 0.0;
+                        for (int q = 0; q < tpb_teams; ++q) s += bsum[q];
+                        atomicAdd(acc, s);
+                    }
+                }
+                cur ^= 1;
+                if (!grid_sync(gb, nb, c.spin_limit)) return;
+                // stopping rule of App. B, per instance, evaluated identically by every block
+                int open_local = 0;
+                for (int b = threadIdx.x; b < c.B; b += S::TPB) {
+                    if (done[b]) continue;
+                    const double d = c.inst_m[b] > 0 ? __ldcg(acc + b) / c.inst_m[b] : 0.0;
+                    const bool fin = (d < c.tol) || (it + 1 >= c.max_iter) || !(d == d);
+                    if (blockIdx.x == 0) {
+                        c.inst_dist[b] = d;
+                        c.inst_iters[b] = it + 1;
+                        if (fin) c.inst_done[b] = 1;
+                    }
+                    if (fin) done[b] = 1;
+                    else open_local = 1;
+                }
+                if (!__syncthreads_or(open_local)) {
+                    ++it;
+                    break;
+                }
+            }
+            __syncthreads();
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                int mi = 0, ncv = 0;
+                double md = 0.0;
+                for (int b = 0; b < c.B; ++b) {
+                    mi = c.inst_iters[b] > mi ? c.inst_iters[b] : mi;
+                    md = c.inst_dist[b] > md ? c.inst_dist[b] : md;
+                    if (!(c.inst_dist[b] < c.tol) && c.inst_m[b] > 0) ++ncv;
+                }
+                c.ctl->last_iters = mi;
+                c.ctl->last_dist = md;
+                c.ctl->not_conv = ncv;
+                c.ctl->sweeps_total += mi;
+                c.ctl->bp_calls += 1;
+                c.ctl->nc_calls += (ncv > 0) ? 1 : 0;
+                c.ctl->cur = cur;
+            }
+        }
+        if constexpr ((PH & PH_REGAUGE) != 0u) {
+            {
+                const int team = threadIdx.x / S::TR, tid = threadIdx.x % S::TR;
+                RGSm<CHI>& sm = reinterpret_cast<RGSm<CHI>*>(smem)[team];
+                const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * (S::TPB / S::TR);
+                for (int e = gteam; e < c.m; e += nt) regauge_edge<CHI, Mode>(c, e, tid, team, cur, sm);
+                if (!grid_sync(gb, nb, c.spin_limit)) return;
+            }
+            {
+                using CT = C<typename Mode::TS>;
+                const int team = threadIdx.x / S::TRV, tid = threadIdx.x % S::TRV;
+                CT* buf = reinterpret_cast<CT*>(smem) + (size_t)team * (4 * CHI * CHI * CHI + 3 * CHI * CHI);
+                const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * (S::TPB / S::TRV);
+                for (int a = gteam; a < c.n; a += nt) {
+                    regauge_vertex<CHI, Mode>(c, a, tid, team, buf);
+                    team_bar<S::TRV>(team);
+                }
+                if (!grid_sync(gb, nb, c.spin_limit)) return;
+            }
+        }
+    }
+}
+
+// The three phase kernels (one cooperative launch each).
+template <int CHI, class Mode>
+__global__ void __launch_bounds__(Shape<CHI>::TPB, 1) gates_kernel(Ctx c) { anneal_body<CHI, Mode, PH_GATES>(c); }
+template <int CHI, class Mode>
+__global__ void __launch_bounds__(Shape<CHI>::TPB, 1) bp_kernel(Ctx c) { anneal_body<CHI, Mode, PH_BP>(c); }
+template <int CHI, class Mode>
+__global__ void __launch_bounds__(Shape<CHI>::TPB, 1) regauge_kernel(Ctx c) { anneal_body<CHI, Mode, PH_REGAUGE>(c); }
+
+// marginals rho_a = sum Gamma Gamma^* prod lambda^2 / tr and the read-out (one warp per vertex)
+template <int CHI, class Mode>
+__global__ void marginals_kernel2(const C<typename Mode::TS>* Gamma, const double* lam, const int4* vert_edges, int n,
+                                  cd* rho, int8_t* sign, int* nan_flag) {
+    constexpr int H = CHI * CHI * CHI;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int a = warp;
+    const int4 ve = vert_edges[a];
+    cd acc[4] = {cd{0, 0}, cd{0, 0}, cd{0, 0}, cd{0, 0}};
+    for (int r = lane; r < H; r += 32) {
+        const int j0 = r / (CHI * CHI), j1 = (r / CHI) % CHI, j2 = r % CHI;
+        const double l0 = lam_get(lam, CHI, ve.x, j0), l1 = lam_get(lam, CHI, ve.y, j1), l2 = lam_get(lam, CHI, ve.z, j2);
+        const double wgt = (l0 * l0) * (l1 * l1) * (l2 * l2);
+        const cd g0 = ccast<double>(Gamma[(size_t)a * 2 * H + r]);
+        const cd g1 = ccast<double>(Gamma[(size_t)a * 2 * H + H + r]);
+        acc[0] = cfmac(g0, wgt * g0, acc[0]);
+        acc[1] = cfmac(g1, wgt * g0, acc[1]);
+        acc[2] = cfmac(g0, wgt * g1, acc[2]);
+        acc[3] = cfmac(g1, wgt * g1, acc[3]);
+    }
+    for (int q = 0; q < 4; ++q) {
+        acc[q].x = group_sum<32>(acc[q].x, 0xffffffffu);
+        acc[q].y = group_sum<32>(acc[q].y, 0xffffffffu);
+    }
+    if (lane == 0) {
+        const double tr = acc[0].x + acc[3].x;
+        const double it = 1.0 / tr;
+        for (int q = 0; q < 4; ++q) rho[(size_t)a * 4 + q] = it * acc[q];
+        if (sign) sign[a] = (acc[0].x * it > 0.5) ? 1 : -1;
+        if (!(tr == tr) || tr == 0.0) atomicOr(nan_flag, 1);
+    }
+}
+
+}  // namespace gtqa

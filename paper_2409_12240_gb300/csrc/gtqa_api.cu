@@ -1,7 +1,7 @@
-// C ABI of the GTQA hot path: state management, graph bookkeeping, launch
-// sequencing.  Declarations and argument contracts are in include/gtqa.h.
+// C ABI of the GTQA hot path: validation, graph bookkeeping, state management and
+// the launches of the persistent annealing kernel.  Contracts are in include/gtqa.h.
 #include "gtqa.h"
-#include "gtqa_kernels.cuh"
+#include "gtqa_launch.h"
 
 #include <algorithm>
 #include <cmath>
@@ -19,40 +19,44 @@ struct gtqa_state {
     cudaStream_t stream = nullptr;
     double svd_cutoff = 1e-14, eig_cutoff = 1e-13;
     int ncol = 0;
-    std::vector<int> colour_off;        // [ncol + 1] ranges in colour_edges
-    std::vector<int> h_inst_vbeg;       // [B + 1]
-    std::vector<int> h_inst_m;          // [B]
-    std::vector<int4> h_edge_info;
+    int nblocks = 0;
+    size_t smem[PK_COUNT] = {0, 0, 0};   // dynamic shared memory of the three phase kernels
+    std::vector<int> h_inst_m;
     // device buffers
     void* Gamma = nullptr;
     double* lam = nullptr;
-    cd* msg[2] = {nullptr, nullptr};
-    int cur = 0;
-    cd* T = nullptr;
+    void* T = nullptr;
+    void* msg[2] = {nullptr, nullptr};
+    cd* D0 = nullptr;
+    cd* t0 = nullptr;
     cd* X = nullptr;
     int4* edge_info = nullptr;
     int4* vert_edges = nullptr;
     int* vert_inst = nullptr;
-    int* edge_inst = nullptr;
     double* J = nullptr;
     double* h = nullptr;
     int* colour_edges = nullptr;
-    double* disc = nullptr;
-    int2* work = nullptr;               // per edge: core-SVD sweeps and rotations of the last gate
-    double* stats = nullptr;            // [4]: discarded weight, log fidelity, SVD pairs, SVD rotations
-    double* vdelta = nullptr;
+    int* colour_off = nullptr;
+    int* last_colour = nullptr;
+    int* iso = nullptr;
+    int n_iso = 0;
     int* inst_vbeg = nullptr;
     int* inst_m = nullptr;
+    double* acc = nullptr;
     int* inst_done = nullptr;
     int* inst_iters = nullptr;
     double* inst_dist = nullptr;
-    int* flags = nullptr;               // [0] all done, [1] NaN in BP, [2] NaN in marginals
+    double* stats = nullptr;    // discarded weight, log fidelity, SVD pairs, SVD rotations
+    Control* ctl = nullptr;
     cd* rho = nullptr;
     int8_t* sign = nullptr;
-    int* h_flags = nullptr;             // pinned mirror of flags
-    // counters
-    long long layers = 0, gates = 0, bp_sweeps = 0, launches = 0;
-    // optional profiler: pending event pairs and accumulated figures per kernel class
+    int* flags = nullptr;       // [0]: NaN in marginals
+    // host counters
+    long long layers = 0, gates = 0, launches = 0;
+    int sticky = GTQA_OK;
+    long long spin_limit = 1LL << 22;   // polls per grid barrier before GTQA_ERR_TIMEOUT (about a second)
+    int bar_extra = 0;                  // test hook: extra arrivals the barrier waits for
+    // optional profiler (per launch class)
     bool prof_on = false;
     struct Pending { int kind; cudaEvent_t a, b; long long units; };
     std::vector<Pending> pending;
@@ -60,9 +64,6 @@ struct gtqa_state {
     double prof_ms[GTQA_K_COUNT] = {};
     long long prof_launches[GTQA_K_COUNT] = {};
     long long prof_units[GTQA_K_COUNT] = {};
-    int last_iters = 0, not_conv = 0;
-    double last_dist = 0.0;
-    int sticky = GTQA_OK;
 };
 
 namespace {
@@ -75,11 +76,33 @@ bool cuda_ok(gtqa_state* s, cudaError_t e) {
     return true;
 }
 
-int launch_check(gtqa_state* s) {
-    if (!cuda_ok(s, cudaGetLastError())) return GTQA_ERR_CUDA;
-    s->launches += 1;
+template <typename T>
+int dalloc(gtqa_state* s, T** p, size_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        s->sticky = GTQA_ERR_OOM;
+        return GTQA_ERR_OOM;
+    }
+    if (e != cudaSuccess) {
+        s->sticky = GTQA_ERR_CUDA;
+        return GTQA_ERR_CUDA;
+    }
     return GTQA_OK;
 }
+
+int storage_chi(int chi) {
+    if (chi <= 2) return 2;
+    if (chi <= 4) return 4;
+    if (chi <= 8) return 8;
+    return 0;
+}
+
+bool mixed(const gtqa_state* s) { return s->precision == GTQA_MIXED; }
+size_t elem_bytes(const gtqa_state* s) { return mixed(s) ? sizeof(cf) : sizeof(cd); }
+size_t gamma_elems(const gtqa_state* s) { return (size_t)s->n * 2 * s->CHI * s->CHI * s->CHI; }
+size_t msg_elems(const gtqa_state* s) { return (size_t)s->m * 2 * s->CHI * s->CHI; }
 
 cudaEvent_t prof_event(gtqa_state* s) {
     if (!s->pool.empty()) {
@@ -92,7 +115,6 @@ cudaEvent_t prof_event(gtqa_state* s) {
     return e;
 }
 
-// Bracket one launch with events when the profiler is on.
 struct ProfScope {
     gtqa_state* s;
     int kind;
@@ -125,52 +147,6 @@ void prof_collect(gtqa_state* s) {
         s->pool.push_back(p.b);
     }
     s->pending.clear();
-}
-
-template <typename T>
-int dalloc(gtqa_state* s, T** p, size_t count) {
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-    if (e == cudaErrorMemoryAllocation) {
-        cudaGetLastError();
-        s->sticky = GTQA_ERR_OOM;
-        return GTQA_ERR_OOM;
-    }
-    if (e != cudaSuccess) {
-        s->sticky = GTQA_ERR_CUDA;
-        return GTQA_ERR_CUDA;
-    }
-    return GTQA_OK;
-}
-
-int storage_chi(int chi) {
-    if (chi <= 2) return 2;
-    if (chi <= 4) return 4;
-    if (chi <= 8) return 8;
-    return 0;
-}
-
-size_t gamma_elems(const gtqa_state* s) { return (size_t)s->n * 2 * s->CHI * s->CHI * s->CHI; }
-size_t msg_elems(const gtqa_state* s) { return (size_t)s->m * 2 * s->CHI * s->CHI; }
-
-GraphView view(const gtqa_state* s) {
-    GraphView g;
-    g.edge_info = s->edge_info;
-    g.vert_edges = s->vert_edges;
-    g.vert_inst = s->vert_inst;
-    g.edge_inst = s->edge_inst;
-    g.J = s->J;
-    g.h = s->h;
-    g.n = s->n;
-    g.m = s->m;
-    return g;
-}
-
-int grid_for(size_t work, int tpb) {
-    size_t b = (work + tpb - 1) / tpb;
-    if (b < 1) b = 1;
-    if (b > 152 * 32) b = 152 * 32;
-    return (int)b;
 }
 
 // Misra-Gries proper edge colouring with at most Delta + 1 colours.
@@ -276,13 +252,12 @@ bool misra_gries(int n, int m, const int* edges, std::vector<int>& colour, int& 
 
 void free_state(gtqa_state* s) {
     if (!s) return;
-    void* ptrs[] = {s->Gamma, s->lam, s->msg[0], s->msg[1], s->T, s->X, s->edge_info, s->vert_edges,
-                    s->vert_inst, s->edge_inst, s->J, s->h, s->colour_edges, s->disc, s->stats, s->vdelta,
-                    s->inst_vbeg, s->inst_m, s->inst_done, s->inst_iters, s->inst_dist, s->flags, s->rho,
-                    s->sign};
-    for (void* p : ptrs) if (p) cudaFree(p);
-    if (s->work) cudaFree(s->work);
-    if (s->h_flags) cudaFreeHost(s->h_flags);
+    void* ptrs[] = {s->Gamma, s->lam, s->T, s->msg[0], s->msg[1], s->D0, s->t0, s->X, s->edge_info,
+                    s->vert_edges, s->vert_inst, s->J, s->h, s->colour_edges, s->colour_off, s->last_colour,
+                    s->iso, s->inst_vbeg, s->inst_m, s->acc, s->inst_done, s->inst_iters, s->inst_dist,
+                    s->stats, s->ctl, s->rho, s->sign, s->flags};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
     for (auto& p : s->pending) {
         s->pool.push_back(p.a);
         s->pool.push_back(p.b);
@@ -291,182 +266,75 @@ void free_state(gtqa_state* s) {
     delete s;
 }
 
-// --------------------------------------------------------------------------
-// launch sequences (templated on the storage bond dimension)
-// --------------------------------------------------------------------------
-template <int CHI, typename TS>
-int set_kernel_attrs() {
-    static bool done = false;
-    if (done) return GTQA_OK;
-    cudaError_t e1 = cudaFuncSetAttribute(gate_kernel<CHI, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(sizeof(GateSmem<CHI>) * GateShape<CHI>::TEAMS));
-    cudaError_t e2 = cudaFuncSetAttribute(bp_sweep_kernel<CHI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(sizeof(BPSmem<CHI>) * BPShape<CHI>::TEAMS));
-    if (e1 != cudaSuccess || e2 != cudaSuccess) return GTQA_ERR_CUDA;
-    done = true;
+Ctx make_ctx(const gtqa_state* s) {
+    Ctx c;
+    std::memset(&c, 0, sizeof(c));
+    c.edge_info = s->edge_info;
+    c.vert_edges = s->vert_edges;
+    c.vert_inst = s->vert_inst;
+    c.J = s->J;
+    c.h = s->h;
+    c.colour_edges = s->colour_edges;
+    c.colour_off = s->colour_off;
+    c.last_colour = s->last_colour;
+    c.iso = s->iso;
+    c.n_iso = s->n_iso;
+    c.ncol = s->ncol;
+    c.n = s->n;
+    c.m = s->m;
+    c.B = s->B;
+    c.inst_vbeg = s->inst_vbeg;
+    c.inst_m = s->inst_m;
+    c.Gamma = s->Gamma;
+    c.lam = s->lam;
+    c.T = s->T;
+    c.msg[0] = s->msg[0];
+    c.msg[1] = s->msg[1];
+    c.D0 = s->D0;
+    c.t0 = s->t0;
+    c.X = s->X;
+    c.acc = s->acc;
+    c.inst_done = s->inst_done;
+    c.inst_iters = s->inst_iters;
+    c.inst_dist = s->inst_dist;
+    c.stats = s->stats;
+    c.ctl = s->ctl;
+    c.chi = s->chi;
+    c.svd_cut = s->svd_cutoff;
+    c.eig_cut = s->eig_cutoff;
+    c.nblocks = s->nblocks;
+    c.bar_expect = s->nblocks + s->bar_extra;
+    c.spin_limit = s->spin_limit;
+    return c;
+}
+
+// One cooperative launch of a phase kernel.
+int run(gtqa_state* s, const Ctx& c, int pk, int kind, long long units) {
+    cudaError_t e;
+    {
+        ProfScope ps(s, kind, units);
+        e = phase_launch(mixed(s), pk, s->CHI, c, s->smem[pk], s->stream);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->sticky = GTQA_ERR_CUDA;
+        return GTQA_ERR_CUDA;
+    }
+    s->launches += 1;
     return GTQA_OK;
 }
 
-template <int CHI, typename TS>
-int trotter_layer_t(gtqa_state* s, double tZ, double tX) {
-    if (set_kernel_attrs<CHI, TS>() != GTQA_OK) { s->sticky = GTQA_ERR_CUDA; return GTQA_ERR_CUDA; }
-    using GS = GateShape<CHI>;
-    GateArgs<TS> a;
-    a.Gamma = (C<TS>*)s->Gamma;
-    a.lam = s->lam;
-    a.g = view(s);
-    a.tZ = tZ;
-    a.chi = s->chi;
-    a.svd_cutoff = s->svd_cutoff;
-    a.disc = s->disc;
-    a.work = s->work;
-    const size_t smem = sizeof(GateSmem<CHI>) * GS::TEAMS;
-    for (int c = 0; c < s->ncol; ++c) {
-        const int cnt = s->colour_off[c + 1] - s->colour_off[c];
-        if (cnt == 0) continue;
-        a.edge_list = s->colour_edges + s->colour_off[c];
-        a.count = cnt;
-        const int grid = (cnt + GS::TEAMS - 1) / GS::TEAMS;
-        ProfScope ps(s, GTQA_K_GATE, cnt);
-        gate_kernel<CHI, TS><<<grid, GS::TPB, smem, s->stream>>>(a);
-        if (launch_check(s)) return GTQA_ERR_CUDA;
-    }
-    const size_t work = (size_t)s->n * CHI * CHI * CHI;
-    {
-        ProfScope ps(s, GTQA_K_MIXING, s->n);
-        xrot_kernel<CHI, TS><<<grid_for(work, 256), 256, 0, s->stream>>>((C<TS>*)s->Gamma, s->n, tX);
-        if (launch_check(s)) return GTQA_ERR_CUDA;
-    }
-    if (s->m > 0) {
-        ProfScope ps(s, GTQA_K_LAYER_STATS, s->m);
-        layer_stats_kernel<<<1, 256, 0, s->stream>>>(s->disc, s->work, s->m, (2 * CHI - 1) * CHI, s->stats);
-        if (launch_check(s)) return GTQA_ERR_CUDA;
+// Read the device control block (synchronises) and surface a device-side error.
+int read_ctl(gtqa_state* s, Control* out) {
+    if (!cuda_ok(s, cudaMemcpyAsync(out, s->ctl, sizeof(Control), cudaMemcpyDeviceToHost, s->stream)) ||
+        !cuda_ok(s, cudaStreamSynchronize(s->stream)))
+        return GTQA_ERR_CUDA;
+    if (out->err) {
+        s->sticky = out->err;
+        return out->err;
     }
     return GTQA_OK;
 }
-
-template <int CHI, typename TS>
-int symmetric_t(gtqa_state* s) {
-    const size_t work = (size_t)s->n * 2 * CHI * CHI * CHI;
-    ProfScope ps(s, GTQA_K_SYMMETRIC, s->n);
-    symmetric_kernel<CHI, TS><<<grid_for(work, 256), 256, 0, s->stream>>>((const C<TS>*)s->Gamma, s->lam, view(s), s->T);
-    return launch_check(s);
-}
-
-template <int CHI, typename TS>
-int bp_t(gtqa_state* s, double tol, int max_iter, unsigned flags, int* iters_out, double* dist_out) {
-    if (set_kernel_attrs<CHI, TS>() != GTQA_OK) { s->sticky = GTQA_ERR_CUDA; return GTQA_ERR_CUDA; }
-    if (symmetric_t<CHI, TS>(s)) return GTQA_ERR_CUDA;
-    if (flags & GTQA_BP_WARM_START) {
-        const size_t work = msg_elems(s);
-        ProfScope ps(s, GTQA_K_WARM_START, s->m);
-        warm_start_kernel<CHI><<<grid_for(work, 256), 256, 0, s->stream>>>(s->lam, s->m, s->msg[s->cur]);
-        if (launch_check(s)) return GTQA_ERR_CUDA;
-    }
-    if (!cuda_ok(s, cudaMemsetAsync(s->inst_done, 0, sizeof(int) * s->B, s->stream))) return GTQA_ERR_CUDA;
-    if (!cuda_ok(s, cudaMemsetAsync(s->inst_iters, 0, sizeof(int) * s->B, s->stream))) return GTQA_ERR_CUDA;
-    if (!cuda_ok(s, cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, s->stream))) return GTQA_ERR_CUDA;
-    using BS = BPShape<CHI>;
-    BPArgs a;
-    a.T = s->T;
-    a.vdelta = s->vdelta;
-    a.inst_done = s->inst_done;
-    a.g = view(s);
-    ReduceArgs r;
-    r.vdelta = s->vdelta;
-    r.inst_vbeg = s->inst_vbeg;
-    r.inst_m = s->inst_m;
-    r.inst_done = s->inst_done;
-    r.inst_iters = s->inst_iters;
-    r.inst_dist = s->inst_dist;
-    r.flags = s->flags;
-    r.tol = tol;
-    r.max_iter = max_iter;
-    r.B = s->B;
-    const size_t smem = sizeof(BPSmem<CHI>) * BS::TEAMS;
-    const int grid = (s->n + BS::TEAMS - 1) / BS::TEAMS;
-    for (int it = 0; it < max_iter; ++it) {
-        a.src = s->msg[s->cur];
-        a.dst = s->msg[s->cur ^ 1];
-        {
-            ProfScope ps(s, GTQA_K_BP_SWEEP, s->n);
-            bp_sweep_kernel<CHI><<<grid, BS::TPB, smem, s->stream>>>(a);
-            if (launch_check(s)) return GTQA_ERR_CUDA;
-        }
-        {
-            ProfScope ps(s, GTQA_K_BP_REDUCE, s->n);
-            bp_reduce_kernel<<<1, 256, 0, s->stream>>>(r);
-            if (launch_check(s)) return GTQA_ERR_CUDA;
-        }
-        s->cur ^= 1;
-        if (!cuda_ok(s, cudaMemcpyAsync(s->h_flags, s->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s->stream)))
-            return GTQA_ERR_CUDA;
-        if (!cuda_ok(s, cudaStreamSynchronize(s->stream))) return GTQA_ERR_CUDA;
-        if (s->h_flags[1]) { s->sticky = GTQA_ERR_NUMERIC; return GTQA_ERR_NUMERIC; }
-        if (s->h_flags[0]) break;
-    }
-    std::vector<int> iters(s->B), done(s->B);
-    std::vector<double> dist(s->B);
-    if (!cuda_ok(s, cudaMemcpyAsync(iters.data(), s->inst_iters, sizeof(int) * s->B, cudaMemcpyDeviceToHost, s->stream)))
-        return GTQA_ERR_CUDA;
-    if (!cuda_ok(s, cudaMemcpyAsync(dist.data(), s->inst_dist, sizeof(double) * s->B, cudaMemcpyDeviceToHost, s->stream)))
-        return GTQA_ERR_CUDA;
-    if (!cuda_ok(s, cudaStreamSynchronize(s->stream))) return GTQA_ERR_CUDA;
-    int mi = 0, nc = 0;
-    double md = 0.0;
-    for (int b = 0; b < s->B; ++b) {
-        mi = iters[b] > mi ? iters[b] : mi;
-        md = dist[b] > md ? dist[b] : md;
-        if (!(dist[b] < tol) && s->h_inst_m[b] > 0) nc++;
-    }
-    s->last_iters = mi;
-    s->bp_sweeps += mi;
-    s->last_dist = md;
-    s->not_conv = nc;
-    if (iters_out) *iters_out = mi;
-    if (dist_out) *dist_out = md;
-    return nc > 0 ? GTQA_ERR_NOT_CONVERGED : GTQA_OK;
-}
-
-template <int CHI, typename TS>
-int regauge_t(gtqa_state* s) {
-    if (s->m == 0) return GTQA_OK;
-    using RS = RGShape<CHI>;
-    RGArgs a;
-    a.msg = s->msg[s->cur];
-    a.X = s->X;
-    a.lam = s->lam;
-    a.m = s->m;
-    a.eig_cutoff = s->eig_cutoff;
-    a.svd_cutoff = s->svd_cutoff;
-    {
-        ProfScope ps(s, GTQA_K_REGAUGE_EDGE, s->m);
-        regauge_edge_kernel<CHI><<<(s->m + RS::TEAMS - 1) / RS::TEAMS, RS::TPB, 0, s->stream>>>(a);
-        if (launch_check(s)) return GTQA_ERR_CUDA;
-    }
-    ProfScope ps(s, GTQA_K_REGAUGE_VERTEX, s->n);
-    regauge_vertex_kernel<CHI, TS><<<s->n, 128, 0, s->stream>>>(s->T, s->X, view(s), (C<TS>*)s->Gamma);
-    return launch_check(s);
-}
-
-template <int CHI, typename TS>
-int marginals_t(gtqa_state* s) {
-    const int warps_per_block = 4;
-    ProfScope ps(s, GTQA_K_MARGINALS, s->n);
-    marginals_kernel<CHI, TS><<<(s->n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s->stream>>>(
-        (const C<TS>*)s->Gamma, s->lam, view(s), s->rho, s->sign, s->flags + 2);
-    return launch_check(s);
-}
-
-#define GTQA_DISPATCH(s, FN, ...)                                         \
-    do {                                                                  \
-        switch ((s)->CHI) {                                               \
-            case 2: return FN<2, double>((s), ##__VA_ARGS__);             \
-            case 4: return FN<4, double>((s), ##__VA_ARGS__);             \
-            case 8: return FN<8, double>((s), ##__VA_ARGS__);             \
-            default: return GTQA_ERR_UNSUPPORTED;                         \
-        }                                                                 \
-    } while (0)
 
 int check_state(const gtqa_state* s) {
     if (!s) return GTQA_ERR_INVALID_ARG;
@@ -477,12 +345,12 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
                 const double* h, int chi, const gtqa_options* opt, gtqa_state** out) {
     if (!out) return GTQA_ERR_INVALID_ARG;
     *out = nullptr;
-    if (B < 1 || !n || !m || !h || chi < 1) return GTQA_ERR_INVALID_ARG;
+    if (B < 1 || B > 4096 || !n || !m || !h || chi < 1) return GTQA_ERR_INVALID_ARG;
     if (storage_chi(chi) == 0) return GTQA_ERR_UNSUPPORTED;
     gtqa_options o;
     gtqa_options_init(&o);
     if (opt) o = *opt;
-    if (o.precision != GTQA_FP64) return GTQA_ERR_UNSUPPORTED;
+    if (o.precision != GTQA_FP64 && o.precision != GTQA_MIXED) return GTQA_ERR_UNSUPPORTED;
     if (o.reserved0 != 0) return GTQA_ERR_INVALID_ARG;
     long long N = 0, Mtot = 0;
     for (int b = 0; b < B; ++b) {
@@ -490,10 +358,9 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         N += n[b];
         Mtot += m[b];
     }
-    if (N > (1LL << 30) || Mtot > (1LL << 30)) return GTQA_ERR_INVALID_ARG;
+    if (N > (1LL << 28) || Mtot > (1LL << 28)) return GTQA_ERR_INVALID_ARG;
     if (Mtot > 0 && (!edges || !J)) return GTQA_ERR_INVALID_ARG;
-    // validate and globalise the graph
-    std::vector<int> ge((size_t)Mtot * 2), gcol((size_t)Mtot), vinst(N), einst(Mtot);
+    std::vector<int> ge((size_t)Mtot * 2), gcol((size_t)Mtot), vinst(N);
     std::vector<int> deg(N, 0);
     std::vector<int> vbeg(B + 1, 0), minst(B);
     int ncol = 0;
@@ -512,17 +379,16 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
                 keys.push_back(a * n[b] + c);
                 ge[2 * (eoff + e)] = (int)(u + voff);
                 ge[2 * (eoff + e) + 1] = (int)(v + voff);
-                einst[eoff + e] = b;
                 if (++deg[u + voff] > 3 || ++deg[v + voff] > 3) return GTQA_ERR_INVALID_ARG;
             }
             std::vector<long long> sk = keys;
             std::sort(sk.begin(), sk.end());
-            for (size_t i = 1; i < sk.size(); ++i) if (sk[i] == sk[i - 1]) return GTQA_ERR_INVALID_ARG;
+            for (size_t i = 1; i < sk.size(); ++i)
+                if (sk[i] == sk[i - 1]) return GTQA_ERR_INVALID_ARG;
             for (int a = 0; a < n[b]; ++a) {
                 if (!std::isfinite(h[voff + a])) return GTQA_ERR_INVALID_ARG;
                 vinst[voff + a] = b;
             }
-            // colouring
             if (colour) {
                 for (int e = 0; e < m[b]; ++e) {
                     const int c = colour[eoff + e];
@@ -539,7 +405,6 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
             eoff += m[b];
         }
         vbeg[B] = (int)voff;
-        // each colour must be a matching
         std::vector<unsigned long long> seen((size_t)N, 0ull);
         for (long long e = 0; e < Mtot; ++e) {
             const unsigned long long bit = 1ull << gcol[e];
@@ -563,92 +428,152 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
     s->svd_cutoff = o.svd_cutoff > 0 ? o.svd_cutoff : 1e-14;
     s->eig_cutoff = o.eig_cutoff > 0 ? o.eig_cutoff : 1e-13;
     s->ncol = ncol;
-    s->h_inst_vbeg = vbeg;
     s->h_inst_m = minst;
-    // slots: incident edges in ascending id
+    // launch shapes: one resident block per SM for each cooperative phase kernel
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return GTQA_ERR_CUDA;
+    }
+    for (int pk = 0; pk < PK_COUNT; ++pk) {
+        size_t base = 0;
+        int tpb = 0, bps = 0;
+        if (!phase_shape(mixed(s), pk, s->CHI, &base, &tpb)) {
+            delete s;
+            return GTQA_ERR_UNSUPPORTED;
+        }
+        s->smem[pk] = (base + (pk == PK_BP ? sizeof(int) * (size_t)B : 0) + 15) / 16 * 16;
+        const cudaError_t pe = phase_prepare(mixed(s), pk, s->CHI, s->smem[pk], &bps);
+        if (pe != cudaSuccess || bps < 1) {
+            cudaGetLastError();
+            delete s;
+            return pe != cudaSuccess ? GTQA_ERR_CUDA : GTQA_ERR_UNSUPPORTED;
+        }
+    }
+    s->nblocks = sms;
+    // slots: incident edges in ascending id; colour of each vertex's last gate
     std::vector<int4> vedges(N, make_int4(-1, -1, -1, 0));
     std::vector<int4> einfo(Mtot);
+    std::vector<int> lastc(N, -1);
     for (long long e = 0; e < Mtot; ++e) {
         int sl[2];
         for (int q = 0; q < 2; ++q) {
             const int v = ge[2 * e + q];
             int4& ve = vedges[v];
-            int k = ve.w;
+            const int k = ve.w;
             if (k == 0) ve.x = (int)e; else if (k == 1) ve.y = (int)e; else ve.z = (int)e;
             sl[q] = k;
             ve.w = k + 1;
+            lastc[v] = std::max(lastc[v], gcol[e]);
         }
         einfo[e] = make_int4(ge[2 * e], ge[2 * e + 1], sl[0], sl[1]);
     }
-    s->h_edge_info = einfo;
+    std::vector<int> iso;
+    for (long long a = 0; a < N; ++a)
+        if (vedges[a].w == 0) iso.push_back((int)a);
+    s->n_iso = (int)iso.size();
     std::vector<int> cedges;
     cedges.reserve(Mtot);
-    s->colour_off.assign(ncol + 1, 0);
+    std::vector<int> coff(ncol + 1, 0);
     for (int c = 0; c < ncol; ++c) {
-        s->colour_off[c] = (int)cedges.size();
-        for (long long e = 0; e < Mtot; ++e) if (gcol[e] == c) cedges.push_back((int)e);
+        coff[c] = (int)cedges.size();
+        for (long long e = 0; e < Mtot; ++e)
+            if (gcol[e] == c) cedges.push_back((int)e);
     }
-    s->colour_off[ncol] = (int)cedges.size();
-    // device allocations
+    coff[ncol] = (int)cedges.size();
     const int CHI = s->CHI;
-    const size_t gel = gamma_elems(s), mel = msg_elems(s);
-    const size_t rsz = sizeof(cd);
+    const size_t gel = gamma_elems(s), mel = msg_elems(s), eb = elem_bytes(s);
     int rc = GTQA_OK;
-    if ((rc = dalloc(s, (unsigned char**)&s->Gamma, gel * rsz)) ||
-        (rc = dalloc(s, &s->lam, (size_t)s->m * CHI)) || (rc = dalloc(s, &s->msg[0], mel)) ||
-        (rc = dalloc(s, &s->msg[1], mel)) || (rc = dalloc(s, &s->T, gel)) ||
+    if ((rc = dalloc(s, (unsigned char**)&s->Gamma, gel * eb)) || (rc = dalloc(s, (unsigned char**)&s->T, gel * eb)) ||
+        (rc = dalloc(s, (unsigned char**)&s->msg[0], mel * eb)) ||
+        (rc = dalloc(s, (unsigned char**)&s->msg[1], mel * eb)) || (rc = dalloc(s, &s->lam, (size_t)s->m * CHI)) ||
+        (rc = dalloc(s, &s->D0, mixed(s) ? mel : 1)) || (rc = dalloc(s, &s->t0, mixed(s) ? (size_t)2 * s->m : 1)) ||
         (rc = dalloc(s, &s->X, (size_t)s->m * 2 * CHI * CHI)) || (rc = dalloc(s, &s->edge_info, s->m)) ||
         (rc = dalloc(s, &s->vert_edges, s->n)) || (rc = dalloc(s, &s->vert_inst, s->n)) ||
-        (rc = dalloc(s, &s->edge_inst, s->m)) || (rc = dalloc(s, &s->J, s->m)) || (rc = dalloc(s, &s->h, s->n)) ||
-        (rc = dalloc(s, &s->colour_edges, s->m)) || (rc = dalloc(s, &s->disc, s->m)) ||
-        (rc = dalloc(s, &s->work, s->m)) || (rc = dalloc(s, &s->stats, 4)) || (rc = dalloc(s, &s->vdelta, s->n)) ||
-        (rc = dalloc(s, &s->inst_vbeg, B + 1)) || (rc = dalloc(s, &s->inst_m, B)) ||
+        (rc = dalloc(s, &s->J, s->m)) || (rc = dalloc(s, &s->h, s->n)) || (rc = dalloc(s, &s->colour_edges, s->m)) ||
+        (rc = dalloc(s, &s->colour_off, ncol + 1)) || (rc = dalloc(s, &s->last_colour, s->n)) ||
+        (rc = dalloc(s, &s->iso, iso.size())) || (rc = dalloc(s, &s->inst_vbeg, B + 1)) ||
+        (rc = dalloc(s, &s->inst_m, B)) || (rc = dalloc(s, &s->acc, 3 * (size_t)B)) ||
         (rc = dalloc(s, &s->inst_done, B)) || (rc = dalloc(s, &s->inst_iters, B)) ||
-        (rc = dalloc(s, &s->inst_dist, B)) || (rc = dalloc(s, &s->flags, 4)) ||
-        (rc = dalloc(s, &s->rho, (size_t)s->n * 4)) || (rc = dalloc(s, &s->sign, s->n))) {
+        (rc = dalloc(s, &s->inst_dist, B)) || (rc = dalloc(s, &s->stats, 4)) || (rc = dalloc(s, &s->ctl, 1)) ||
+        (rc = dalloc(s, &s->rho, (size_t)s->n * 4)) || (rc = dalloc(s, &s->sign, s->n)) ||
+        (rc = dalloc(s, &s->flags, 4))) {
         free_state(s);
         return rc;
     }
-    if (cudaMallocHost((void**)&s->h_flags, sizeof(int) * 4) != cudaSuccess) {
-        free_state(s);
-        return GTQA_ERR_OOM;
-    }
-    // initial state |+>^N: Gamma[a][i][0][0][0] = 1/sqrt(2), lambda_e = (1, 0, ...)
-    std::vector<cd> g0(gel, cd{0.0, 0.0});
+    // |+>^N: Gamma[a][i][0][0][0] = 1/sqrt(2); lambda_e = (1, 0, ...)
     const size_t H = (size_t)CHI * CHI * CHI;
+    std::vector<unsigned char> g0(gel * eb, 0);
     for (long long a = 0; a < N; ++a) {
-        g0[a * 2 * H] = cd{M_SQRT1_2, 0.0};
-        g0[a * 2 * H + H] = cd{M_SQRT1_2, 0.0};
+        for (int i = 0; i < 2; ++i) {
+            const size_t idx = a * 2 * H + i * H;
+            if (mixed(s)) reinterpret_cast<cf*>(g0.data())[idx] = cf{(float)M_SQRT1_2, 0.f};
+            else reinterpret_cast<cd*>(g0.data())[idx] = cd{M_SQRT1_2, 0.0};
+        }
     }
     std::vector<double> l0((size_t)s->m * CHI, 0.0);
     for (long long e = 0; e < Mtot; ++e) l0[e * CHI] = 1.0;
-    std::vector<double> Jv(Mtot), hv(N);
-    for (long long e = 0; e < Mtot; ++e) Jv[e] = J[e];
-    for (long long a = 0; a < N; ++a) hv[a] = h[a];
+    std::vector<double> Jv(J ? J : (const double*)nullptr, J ? J + Mtot : (const double*)nullptr);
+    std::vector<double> hv(h, h + N);
+    Control ctl0;
+    std::memset(&ctl0, 0, sizeof(ctl0));
     cudaStream_t st = s->stream;
-    bool ok = cuda_ok(s, cudaMemcpyAsync(s->Gamma, g0.data(), gel * rsz, cudaMemcpyHostToDevice, st)) &&
+    bool ok = cuda_ok(s, cudaMemcpyAsync(s->Gamma, g0.data(), g0.size(), cudaMemcpyHostToDevice, st)) &&
+              cuda_ok(s, cudaMemsetAsync(s->T, 0, gel * eb, st)) &&
+              cuda_ok(s, cudaMemsetAsync(s->msg[0], 0, mel * eb, st)) &&
+              cuda_ok(s, cudaMemsetAsync(s->msg[1], 0, mel * eb, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->lam, l0.data(), l0.size() * sizeof(double), cudaMemcpyHostToDevice, st)) &&
-              cuda_ok(s, cudaMemsetAsync(s->msg[0], 0, mel * sizeof(cd), st)) &&
-              cuda_ok(s, cudaMemsetAsync(s->msg[1], 0, mel * sizeof(cd), st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->edge_info, einfo.data(), sizeof(int4) * Mtot, cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->vert_edges, vedges.data(), sizeof(int4) * N, cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->vert_inst, vinst.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st)) &&
-              cuda_ok(s, cudaMemcpyAsync(s->edge_inst, einst.data(), sizeof(int) * Mtot, cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->J, Jv.data(), sizeof(double) * Mtot, cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->h, hv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->colour_edges, cedges.data(), sizeof(int) * Mtot, cudaMemcpyHostToDevice, st)) &&
-              cuda_ok(s, cudaMemsetAsync(s->disc, 0, sizeof(double) * (Mtot > 0 ? Mtot : 1), st)) &&
-              cuda_ok(s, cudaMemsetAsync(s->stats, 0, sizeof(double) * 4, st)) &&
-              cuda_ok(s, cudaMemsetAsync(s->work, 0, sizeof(int2) * (Mtot > 0 ? Mtot : 1), st)) &&
+              cuda_ok(s, cudaMemcpyAsync(s->colour_off, coff.data(), sizeof(int) * (ncol + 1), cudaMemcpyHostToDevice, st)) &&
+              cuda_ok(s, cudaMemcpyAsync(s->last_colour, lastc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st)) &&
+              (iso.empty() || cuda_ok(s, cudaMemcpyAsync(s->iso, iso.data(), sizeof(int) * iso.size(), cudaMemcpyHostToDevice, st))) &&
               cuda_ok(s, cudaMemcpyAsync(s->inst_vbeg, vbeg.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->inst_m, minst.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st)) &&
-              cuda_ok(s, cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, st)) &&
-              cuda_ok(s, cudaStreamSynchronize(st));
+              cuda_ok(s, cudaMemsetAsync(s->stats, 0, sizeof(double) * 4, st)) &&
+              cuda_ok(s, cudaMemcpyAsync(s->ctl, &ctl0, sizeof(Control), cudaMemcpyHostToDevice, st)) &&
+              cuda_ok(s, cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, st)) && cuda_ok(s, cudaStreamSynchronize(st));
     if (!ok) {
         free_state(s);
         return GTQA_ERR_CUDA;
     }
     *out = s;
+    return GTQA_OK;
+}
+
+// messages of the state in complex128 (mixed mode: m0 from lambda plus the stored correction)
+int read_messages(gtqa_state* s, int cur, std::vector<cd>& out) {
+    const size_t mel = msg_elems(s);
+    const int CC = s->CHI * s->CHI;
+    out.assign(mel, cd{0.0, 0.0});
+    if (!mixed(s)) {
+        if (!cuda_ok(s, cudaMemcpyAsync(out.data(), s->msg[cur], mel * sizeof(cd), cudaMemcpyDeviceToHost, s->stream)))
+            return GTQA_ERR_CUDA;
+        return cuda_ok(s, cudaStreamSynchronize(s->stream)) ? GTQA_OK : GTQA_ERR_CUDA;
+    }
+    std::vector<cf> d(mel);
+    std::vector<double> L((size_t)s->m * s->CHI);
+    if (!cuda_ok(s, cudaMemcpyAsync(d.data(), s->msg[cur], mel * sizeof(cf), cudaMemcpyDeviceToHost, s->stream)) ||
+        !cuda_ok(s, cudaMemcpyAsync(L.data(), s->lam, L.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream)) ||
+        !cuda_ok(s, cudaStreamSynchronize(s->stream)))
+        return GTQA_ERR_CUDA;
+    for (int e = 0; e < s->m; ++e) {
+        double sum = 0.0;
+        for (int q = 0; q < s->CHI; ++q) sum += L[(size_t)e * s->CHI + q];
+        for (int x = 0; x < 2; ++x)
+            for (int r = 0; r < CC; ++r) {
+                const size_t idx = ((size_t)2 * e + x) * CC + r;
+                const int j = r / s->CHI, jp = r % s->CHI;
+                double m0 = (j == jp && sum > 0.0) ? L[(size_t)e * s->CHI + j] / sum : 0.0;
+                out[idx] = cd{m0 + (double)d[idx].x, (double)d[idx].y};
+            }
+    }
     return GTQA_OK;
 }
 
@@ -679,13 +604,16 @@ int gtqa_trotter_layer(gtqa_state* s, double tau, double dt) {
     int rc = check_state(s);
     if (rc) return rc;
     if (!std::isfinite(tau) || !std::isfinite(dt)) return GTQA_ERR_INVALID_ARG;
-    const double tZ = dt * tau, tX = dt * (1.0 - tau);
-    rc = [&]() -> int { GTQA_DISPATCH(s, trotter_layer_t, tZ, tX); }();
-    if (rc == GTQA_OK) {
-        s->layers += 1;
-        s->gates += s->m;
-    }
-    return rc;
+    Ctx c = make_ctx(s);
+    c.phases = PH_GATES;
+    c.k0 = c.k1 = 0;
+    c.Ksched = 0;
+    c.tZ1 = dt * tau;
+    c.tX1 = dt * (1.0 - tau);
+    if ((rc = run(s, c, PK_GATES, GTQA_K_TROTTER, s->m))) return rc;
+    s->layers += 1;
+    s->gates += s->m;
+    return GTQA_OK;
 }
 
 int gtqa_bp_sweep(gtqa_state* s, double tol, int32_t max_iter, uint32_t flags, int32_t* iters_out,
@@ -693,36 +621,77 @@ int gtqa_bp_sweep(gtqa_state* s, double tol, int32_t max_iter, uint32_t flags, i
     int rc = check_state(s);
     if (rc) return rc;
     if (max_iter < 1 || !(tol >= 0.0) || (flags & ~3u)) return GTQA_ERR_INVALID_ARG;
-    rc = [&]() -> int { GTQA_DISPATCH(s, bp_t, tol, max_iter, flags, iters_out, dist_out); }();
-    if (rc != GTQA_OK && rc != GTQA_ERR_NOT_CONVERGED) return rc;
-    if (flags & GTQA_BP_REGAUGE) {
-        int r2 = [&]() -> int { GTQA_DISPATCH(s, regauge_t); }();
-        if (r2) return r2;
+    Ctx c = make_ctx(s);
+    c.phases = PH_BP | ((flags & GTQA_BP_WARM_START) ? PH_WARM : 0u);
+    c.k0 = c.k1 = 0;
+    c.tol = tol;
+    c.max_iter = max_iter;
+    if ((rc = run(s, c, PK_BP, GTQA_K_BP, s->n))) return rc;
+    if ((flags & GTQA_BP_REGAUGE) && (rc = run(s, c, PK_REGAUGE, GTQA_K_REGAUGE, s->m))) return rc;
+    Control ctl;
+    if ((rc = read_ctl(s, &ctl))) return rc;
+    if (iters_out) *iters_out = ctl.last_iters;
+    if (dist_out) *dist_out = ctl.last_dist;
+    if (!(ctl.last_dist == ctl.last_dist)) {
+        s->sticky = GTQA_ERR_NUMERIC;
+        return GTQA_ERR_NUMERIC;
     }
-    return rc;
+    return ctl.not_conv > 0 ? GTQA_ERR_NOT_CONVERGED : GTQA_OK;
 }
 
 int gtqa_regauge(gtqa_state* s) {
     int rc = check_state(s);
     if (rc) return rc;
-    GTQA_DISPATCH(s, regauge_t);
+    Ctx c = make_ctx(s);
+    c.phases = PH_REGAUGE;
+    c.k0 = c.k1 = 0;
+    return run(s, c, PK_REGAUGE, GTQA_K_REGAUGE, s->m);
+}
+
+int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double dt, double tol, int32_t max_iter) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (K < 1 || k_begin < 1 || k_end < k_begin || k_end > K || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1)
+        return GTQA_ERR_INVALID_ARG;
+    Ctx c = make_ctx(s);
+    c.phases = PH_GATES | PH_BP | PH_WARM | PH_REGAUGE;
+    c.Ksched = K;
+    c.dt = dt;
+    c.tol = tol;
+    c.max_iter = max_iter;
+    for (int k = k_begin; k <= k_end; ++k) {
+        c.k0 = c.k1 = k;
+        if ((rc = run(s, c, PK_GATES, GTQA_K_TROTTER, s->m)) || (rc = run(s, c, PK_BP, GTQA_K_BP, s->n)) ||
+            (rc = run(s, c, PK_REGAUGE, GTQA_K_REGAUGE, s->m)))
+            return rc;
+        s->layers += 1;
+        s->gates += s->m;
+    }
+    return GTQA_OK;
 }
 
 int gtqa_marginals(gtqa_state* s, double* rho_out, int8_t* sign_out) {
     int rc = check_state(s);
     if (rc) return rc;
     if (!rho_out) return GTQA_ERR_INVALID_ARG;
-    rc = [&]() -> int { GTQA_DISPATCH(s, marginals_t); }();
-    if (rc) return rc;
+    {
+        ProfScope ps(s, GTQA_K_MARGINALS, s->n);
+        const cudaError_t e = mixed(s) ? marginals_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho,
+                                                                s->sign, s->flags, s->stream)
+                                       : marginals_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho,
+                                                               s->sign, s->flags, s->stream);
+        if (!cuda_ok(s, e)) return GTQA_ERR_CUDA;
+        s->launches += 1;
+    }
+    int hf[4] = {0, 0, 0, 0};
     if (!cuda_ok(s, cudaMemcpyAsync(rho_out, s->rho, sizeof(cd) * 4 * (size_t)s->n, cudaMemcpyDefault, s->stream)))
         return GTQA_ERR_CUDA;
-    if (sign_out &&
-        !cuda_ok(s, cudaMemcpyAsync(sign_out, s->sign, (size_t)s->n, cudaMemcpyDefault, s->stream)))
+    if (sign_out && !cuda_ok(s, cudaMemcpyAsync(sign_out, s->sign, (size_t)s->n, cudaMemcpyDefault, s->stream)))
         return GTQA_ERR_CUDA;
-    if (!cuda_ok(s, cudaMemcpyAsync(s->h_flags, s->flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s->stream)))
+    if (!cuda_ok(s, cudaMemcpyAsync(hf, s->flags, sizeof(hf), cudaMemcpyDeviceToHost, s->stream)) ||
+        !cuda_ok(s, cudaStreamSynchronize(s->stream)))
         return GTQA_ERR_CUDA;
-    if (!cuda_ok(s, cudaStreamSynchronize(s->stream))) return GTQA_ERR_CUDA;
-    if (s->h_flags[2]) {
+    if (hf[0]) {
         s->sticky = GTQA_ERR_NUMERIC;
         return GTQA_ERR_NUMERIC;
     }
@@ -732,35 +701,59 @@ int gtqa_marginals(gtqa_state* s, double* rho_out, int8_t* sign_out) {
 int gtqa_stats(gtqa_state* s, gtqa_stats_t* out) {
     if (!s || !out) return GTQA_ERR_INVALID_ARG;
     double st[4] = {0.0, 0.0, 0.0, 0.0};
+    Control ctl;
     if (!cuda_ok(s, cudaMemcpyAsync(st, s->stats, sizeof(st), cudaMemcpyDeviceToHost, s->stream)) ||
+        !cuda_ok(s, cudaMemcpyAsync(&ctl, s->ctl, sizeof(ctl), cudaMemcpyDeviceToHost, s->stream)) ||
         !cuda_ok(s, cudaStreamSynchronize(s->stream)))
         return GTQA_ERR_CUDA;
     out->layers = s->layers;
     out->gates = s->gates;
-    out->last_bp_iters = s->last_iters;
-    out->not_converged = s->not_conv;
-    out->last_bp_dist = s->last_dist;
+    out->last_bp_iters = ctl.last_iters;
+    out->not_converged = ctl.not_conv;
+    out->last_bp_dist = ctl.last_dist;
     out->discarded_weight = st[0];
     out->log_fidelity = st[1];
     out->svd_pairs = (int64_t)st[2];
     out->svd_rotations = (int64_t)st[3];
-    out->bp_sweeps = s->bp_sweeps;
+    out->bp_sweeps = ctl.sweeps_total;
     out->launches = s->launches;
-    return GTQA_OK;
+    out->bp_calls = ctl.bp_calls;
+    out->bp_not_converged_calls = ctl.nc_calls;
+    return ctl.err ? ctl.err : GTQA_OK;
 }
 
 int gtqa_get_state(gtqa_state* s, double* gamma_out, double* lambda_out, double* messages_out) {
     int rc = check_state(s);
     if (rc) return rc;
+    Control ctl;
+    if ((rc = read_ctl(s, &ctl))) return rc;
     const cudaStream_t st = s->stream;
-    if (gamma_out && !cuda_ok(s, cudaMemcpyAsync(gamma_out, s->Gamma, gamma_elems(s) * sizeof(cd), cudaMemcpyDefault, st)))
-        return GTQA_ERR_CUDA;
+    const size_t gel = gamma_elems(s), mel = msg_elems(s);
+    if (gamma_out) {
+        if (!mixed(s)) {
+            if (!cuda_ok(s, cudaMemcpyAsync(gamma_out, s->Gamma, gel * sizeof(cd), cudaMemcpyDefault, st)))
+                return GTQA_ERR_CUDA;
+        } else {
+            std::vector<cf> g(gel);
+            std::vector<cd> g2(gel);
+            if (!cuda_ok(s, cudaMemcpyAsync(g.data(), s->Gamma, gel * sizeof(cf), cudaMemcpyDeviceToHost, st)) ||
+                !cuda_ok(s, cudaStreamSynchronize(st)))
+                return GTQA_ERR_CUDA;
+            for (size_t i = 0; i < gel; ++i) g2[i] = cd{(double)g[i].x, (double)g[i].y};
+            if (!cuda_ok(s, cudaMemcpyAsync(gamma_out, g2.data(), gel * sizeof(cd), cudaMemcpyDefault, st)) ||
+                !cuda_ok(s, cudaStreamSynchronize(st)))
+                return GTQA_ERR_CUDA;
+        }
+    }
     if (lambda_out &&
         !cuda_ok(s, cudaMemcpyAsync(lambda_out, s->lam, sizeof(double) * s->m * s->CHI, cudaMemcpyDefault, st)))
         return GTQA_ERR_CUDA;
-    if (messages_out &&
-        !cuda_ok(s, cudaMemcpyAsync(messages_out, s->msg[s->cur], msg_elems(s) * sizeof(cd), cudaMemcpyDefault, st)))
-        return GTQA_ERR_CUDA;
+    if (messages_out) {
+        std::vector<cd> mm;
+        if ((rc = read_messages(s, ctl.cur, mm))) return rc;
+        if (!cuda_ok(s, cudaMemcpyAsync(messages_out, mm.data(), mel * sizeof(cd), cudaMemcpyDefault, st)))
+            return GTQA_ERR_CUDA;
+    }
     if (!cuda_ok(s, cudaStreamSynchronize(st))) return GTQA_ERR_CUDA;
     return GTQA_OK;
 }
@@ -769,10 +762,44 @@ int gtqa_set_state(gtqa_state* s, const double* gamma, const double* lambda, con
     int rc = check_state(s);
     if (rc) return rc;
     if (!gamma || !lambda || !messages) return GTQA_ERR_INVALID_ARG;
+    Control ctl;
+    if ((rc = read_ctl(s, &ctl))) return rc;
     const cudaStream_t st = s->stream;
-    if (!cuda_ok(s, cudaMemcpyAsync(s->Gamma, gamma, gamma_elems(s) * sizeof(cd), cudaMemcpyDefault, st)) ||
-        !cuda_ok(s, cudaMemcpyAsync(s->lam, lambda, sizeof(double) * s->m * s->CHI, cudaMemcpyDefault, st)) ||
-        !cuda_ok(s, cudaMemcpyAsync(s->msg[s->cur], messages, msg_elems(s) * sizeof(cd), cudaMemcpyDefault, st)) ||
+    const size_t gel = gamma_elems(s), mel = msg_elems(s);
+    const int CC = s->CHI * s->CHI;
+    std::vector<cd> g(gel), mm(mel);
+    std::vector<double> L((size_t)s->m * s->CHI);
+    if (!cuda_ok(s, cudaMemcpyAsync(g.data(), gamma, gel * sizeof(cd), cudaMemcpyDefault, st)) ||
+        !cuda_ok(s, cudaMemcpyAsync(L.data(), lambda, L.size() * sizeof(double), cudaMemcpyDefault, st)) ||
+        !cuda_ok(s, cudaMemcpyAsync(mm.data(), messages, mel * sizeof(cd), cudaMemcpyDefault, st)) ||
+        !cuda_ok(s, cudaStreamSynchronize(st)))
+        return GTQA_ERR_CUDA;
+    for (double x : L)
+        if (!(x >= 0.0) || !std::isfinite(x)) return GTQA_ERR_INVALID_ARG;
+    if (!mixed(s)) {
+        if (!cuda_ok(s, cudaMemcpyAsync(s->Gamma, g.data(), gel * sizeof(cd), cudaMemcpyHostToDevice, st)) ||
+            !cuda_ok(s, cudaMemcpyAsync(s->msg[ctl.cur], mm.data(), mel * sizeof(cd), cudaMemcpyHostToDevice, st)))
+            return GTQA_ERR_CUDA;
+    } else {
+        std::vector<cf> gf(gel), df(mel);
+        for (size_t i = 0; i < gel; ++i) gf[i] = cf{(float)g[i].x, (float)g[i].y};
+        for (int e = 0; e < s->m; ++e) {
+            double sum = 0.0;
+            for (int q = 0; q < s->CHI; ++q) sum += L[(size_t)e * s->CHI + q];
+            for (int x = 0; x < 2; ++x)
+                for (int r = 0; r < CC; ++r) {
+                    const size_t idx = ((size_t)2 * e + x) * CC + r;
+                    const int j = r / s->CHI, jp = r % s->CHI;
+                    const double m0 = (j == jp && sum > 0.0) ? L[(size_t)e * s->CHI + j] / sum : 0.0;
+                    df[idx] = cf{(float)(mm[idx].x - m0), (float)mm[idx].y};
+                }
+        }
+        if (!cuda_ok(s, cudaMemcpyAsync(s->Gamma, gf.data(), gel * sizeof(cf), cudaMemcpyHostToDevice, st)) ||
+            !cuda_ok(s, cudaMemcpyAsync(s->msg[ctl.cur], df.data(), mel * sizeof(cf), cudaMemcpyHostToDevice, st)) ||
+            !cuda_ok(s, cudaStreamSynchronize(st)))
+            return GTQA_ERR_CUDA;
+    }
+    if (!cuda_ok(s, cudaMemcpyAsync(s->lam, L.data(), L.size() * sizeof(double), cudaMemcpyHostToDevice, st)) ||
         !cuda_ok(s, cudaStreamSynchronize(st)))
         return GTQA_ERR_CUDA;
     return GTQA_OK;
@@ -789,7 +816,6 @@ int gtqa_sizes(const gtqa_state* s, int64_t* n, int64_t* m, int32_t* chi_storage
 
 int gtqa_edge_colouring(int32_t n, int32_t m, const int32_t* edges, int32_t* colour_out, int32_t* n_colours_out) {
     if (n < 1 || m < 0 || (m > 0 && (!edges || !colour_out))) return GTQA_ERR_INVALID_ARG;
-    std::vector<int> deg(n, 0);
     for (int e = 0; e < m; ++e) {
         const int u = edges[2 * e], v = edges[2 * e + 1];
         if (u < 0 || v < 0 || u >= n || v >= n || u == v) return GTQA_ERR_INVALID_ARG;
@@ -825,10 +851,15 @@ int gtqa_profile_read(gtqa_state* s, int32_t kind, int64_t* launches, double* to
     return GTQA_OK;
 }
 
+int gtqa_debug_barrier(gtqa_state* s, int64_t spin_limit, int32_t extra_arrivals) {
+    if (!s || spin_limit < 1 || extra_arrivals < 0 || extra_arrivals > 1) return GTQA_ERR_INVALID_ARG;
+    s->spin_limit = spin_limit;
+    s->bar_extra = extra_arrivals;
+    return GTQA_OK;
+}
+
 const char* gtqa_profile_name(int32_t kind) {
-    static const char* names[GTQA_K_COUNT] = {"gate", "mixing", "layer_stats", "symmetric", "warm_start",
-                                              "bp_sweep", "bp_reduce", "regauge_edge", "regauge_vertex",
-                                              "marginals"};
+    static const char* names[GTQA_K_COUNT] = {"gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"};
     if (kind < 0 || kind >= GTQA_K_COUNT) return nullptr;
     return names[kind];
 }

@@ -87,6 +87,41 @@ struct BlockGroup {
 };
 
 // ---------------------------------------------------------------------------
+// Reciprocal and (reciprocal) square root without the FP64 divide/sqrt sequences,
+// which cost ~10-15 FP64 pipe instructions each on this part.  A hardware seed
+// (PTX rcp.approx.ftz.f64 / rsqrt.approx.ftz.f64, ~2^-22 relative error) is refined by
+// two Newton-Raphson steps (quadratic convergence: error ~2^-88, i.e. FP64 rounding).
+// Float versions use the single-precision hardware approximations directly.
+// Inputs must be finite and positive (callers guard zero).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double nr_rcp(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ double nr_rsqrt(double x) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    // y <- y + y (1 - x y^2) / 2
+    double e = fma(-x * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+    e = fma(-x * y, y, 1.0);
+    return fma(0.5 * y, e, y);
+}
+__device__ __forceinline__ double nr_sqrt(double x) {
+    if (!(x > 0.0)) return 0.0;
+    const double y = nr_rsqrt(x);
+    const double s = x * y;
+    return fma(0.5 * y, fma(-s, s, x), s);   // one correction of s = sqrt(x)
+}
+__device__ __forceinline__ float nr_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float nr_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float nr_sqrt(float x) { return x > 0.f ? sqrtf(x) : 0.f; }
+
+// ---------------------------------------------------------------------------
 // Batched one-sided (Hestenes) Jacobi SVD of an N x N complex matrix.
 //
 // A and V are column-major in shared memory (element (row r, col c) at c*N + r).
@@ -134,13 +169,17 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
             beta = group_sum<N>(beta, pair_mask);
             gam.x = group_sum<N>(gam.x, pair_mask);
             gam.y = group_sum<N>(gam.y, pair_mask);
-            const R ag = sqrt(gam.x * gam.x + gam.y * gam.y);
-            if (ag > (R)0 && ag > tol * sqrt(alpha * beta)) {
-                const R zeta = (beta - alpha) / ((R)2 * ag);
-                const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
-                const R c = (R)1 / sqrt((R)1 + t * t);
+            const R g2 = gam.x * gam.x + gam.y * gam.y;
+            if (g2 > (R)0 && g2 > (tol * tol) * (alpha * beta)) {
+                const R rg = nr_rsqrt(g2);                      // 1 / |gamma|
+                const R zeta = (beta - alpha) * ((R)0.5 * rg);
+                const R az = fabs(zeta);
+                // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), the smaller root; 1/(2 zeta) for huge zeta
+                const R t = (zeta >= (R)0 ? (R)1 : (R)-1) *
+                            (az < (R)1e15 ? nr_rcp(az + nr_sqrt((R)1 + az * az)) : (R)0.5 * nr_rcp(az));
+                const R c = nr_rsqrt((R)1 + t * t);
                 const R s = c * t;
-                const C<R> e = C<R>{gam.x / ag, gam.y / ag};
+                const C<R> e = C<R>{gam.x * rg, gam.y * rg};
                 const C<R> se = s * e;
                 const C<R> sec = conj(se);
                 A[p * N + r] = c * ap - sec * aq;
@@ -172,6 +211,95 @@ __device__ __forceinline__ int desc_rank(const R* v, int n, int i) {
         rk += (y > x) || (y == x && j < i);
     }
     return rk;
+}
+
+}  // namespace gtqa
+
+namespace gtqa {
+
+// ---------------------------------------------------------------------------
+// Teams of TEAM threads inside a block: TEAM <= 32 lives in one warp (warp-level
+// sync with the team's lane mask); TEAM a multiple of 32 syncs with named barrier
+// 1 + team id (barrier 0 stays free for __syncthreads).
+// ---------------------------------------------------------------------------
+template <int TEAM>
+__device__ __forceinline__ void team_bar(int team) {
+    if constexpr (TEAM <= 32) {
+        __syncwarp(group_mask<TEAM>());
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(TEAM) : "memory");
+    }
+}
+
+// Synchronisation policy for a multi-warp team (named barrier + shared flag).
+template <int TEAM>
+struct TeamGroup {
+    int team;
+    int* flag;
+    __device__ __forceinline__ void sync() const { team_bar<TEAM>(team); }
+    __device__ __forceinline__ bool any(int p) const {
+        team_bar<TEAM>(team);
+        if ((threadIdx.x % TEAM) == 0) *flag = 0;
+        team_bar<TEAM>(team);
+        if (p) atomicOr(flag, 1);
+        team_bar<TEAM>(team);
+        return *(volatile int*)flag != 0;
+    }
+};
+
+// L2-coherent loads for data written by other blocks during the same launch.
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ C<double> ldcg(const C<double>* p) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+    return C<double>{v.x, v.y};
+}
+template <>
+__device__ __forceinline__ C<float> ldcg(const C<float>* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return C<float>{v.x, v.y};
+}
+
+// ---------------------------------------------------------------------------
+// Grid-wide barrier for a cooperative (co-resident) launch.  Sense reversal on a
+// generation counter; the wait is bounded: after `limit` polls the block records
+// GTQA timeout in *err and leaves.  Callers test *err after every barrier and
+// return, so a lost block can never hang the device.
+// ---------------------------------------------------------------------------
+struct GridBarrier {
+    unsigned int* count;
+    unsigned int* gen;
+    int* err;
+};
+
+__device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned int nblocks, long long limit) {
+    __shared__ int ok_shared;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int g = *(volatile unsigned int*)gb.gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(gb.count, 1u);
+        if (arrived == nblocks - 1) {
+            *(volatile unsigned int*)gb.count = 0u;
+            __threadfence();
+            atomicAdd(gb.gen, 1u);
+        } else {
+            long long polls = 0;
+            while (*(volatile unsigned int*)gb.gen == g) {
+                if (++polls > limit) {
+                    atomicExch(gb.err, 6);   // GTQA_ERR_TIMEOUT
+                    break;
+                }
+                if (polls > 64) __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_shared = (*(volatile int*)gb.err == 0) ? 1 : 0;
+    }
+    __syncthreads();
+    return ok_shared != 0;   // one value per block, so the whole block leaves together
 }
 
 }  // namespace gtqa

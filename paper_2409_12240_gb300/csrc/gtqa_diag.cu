@@ -2,6 +2,7 @@
 // FP64- and FP32-bound kernels).  Many independent FMA chains per thread, grid
 // sized to fill every SM; best of three timed runs with CUDA events.
 #include "gtqa.h"
+#include "gtqa_common.cuh"
 
 #include <cuda_runtime.h>
 
@@ -60,4 +61,36 @@ int measure(double* tflops) {
 extern "C" int gtqa_alu_peak(int32_t fp64, double* tflops_out) {
     if (!tflops_out) return GTQA_ERR_INVALID_ARG;
     return fp64 ? measure<double>(tflops_out) : measure<float>(tflops_out);
+}
+
+// Diagnostic: the Newton-refined reciprocal / rsqrt / sqrt used by the kernels next to
+// CUDA's own 1/x, 1/sqrt(x) and sqrt(x), for accuracy tests.
+namespace {
+__global__ void math_check_kernel(int n, const double* x, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    out[6 * i + 0] = gtqa::nr_rcp(v);
+    out[6 * i + 1] = 1.0 / v;
+    out[6 * i + 2] = gtqa::nr_rsqrt(v);
+    out[6 * i + 3] = 1.0 / sqrt(v);
+    out[6 * i + 4] = gtqa::nr_sqrt(v);
+    out[6 * i + 5] = sqrt(v);
+}
+}  // namespace
+
+extern "C" int gtqa_math_check(int32_t n, const double* x, double* out) {
+    if (n < 1 || !x || !out) return GTQA_ERR_INVALID_ARG;
+    double *dx = nullptr, *dout = nullptr;
+    if (cudaMalloc(&dx, sizeof(double) * n) != cudaSuccess) return GTQA_ERR_OOM;
+    if (cudaMalloc(&dout, sizeof(double) * 6 * n) != cudaSuccess) {
+        cudaFree(dx);
+        return GTQA_ERR_OOM;
+    }
+    cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice);
+    math_check_kernel<<<(n + 127) / 128, 128>>>(n, dx, dout);
+    cudaError_t e = cudaMemcpy(out, dout, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost);
+    cudaFree(dx);
+    cudaFree(dout);
+    return e == cudaSuccess ? GTQA_OK : GTQA_ERR_CUDA;
 }

@@ -1,0 +1,53 @@
+// Host-side launchers of the annealing kernels.  One translation unit per
+// (precision mode, phase kernel) so the six instantiation sets compile in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gtqa_anneal.cuh"
+
+namespace gtqa {
+
+enum PhaseKernel { PK_GATES = 0, PK_BP = 1, PK_REGAUGE = 2, PK_COUNT = 3 };
+
+#define GTQA_DECLARE_PHASE(MODE, PHASE)                                                                 \
+    bool PHASE##_##MODE##_shape(int CHI, size_t* smem_base, int* tpb);                                  \
+    cudaError_t PHASE##_##MODE##_prepare(int CHI, size_t smem, int* blocks_per_sm);                      \
+    cudaError_t PHASE##_##MODE##_launch(int CHI, const Ctx& c, size_t smem, cudaStream_t st);
+GTQA_DECLARE_PHASE(fp64, gates)
+GTQA_DECLARE_PHASE(fp64, bp)
+GTQA_DECLARE_PHASE(fp64, regauge)
+GTQA_DECLARE_PHASE(mixed, gates)
+GTQA_DECLARE_PHASE(mixed, bp)
+GTQA_DECLARE_PHASE(mixed, regauge)
+#undef GTQA_DECLARE_PHASE
+
+cudaError_t marginals_launch_fp64(int CHI, const void* Gamma, const double* lam, const int4* vert_edges, int n,
+                                  cd* rho, int8_t* sign, int* flag, cudaStream_t st);
+cudaError_t marginals_launch_mixed(int CHI, const void* Gamma, const double* lam, const int4* vert_edges, int n,
+                                   cd* rho, int8_t* sign, int* flag, cudaStream_t st);
+
+inline bool phase_shape(bool mixed, int pk, int CHI, size_t* sb, int* tpb) {
+    switch (pk) {
+        case PK_GATES: return mixed ? gates_mixed_shape(CHI, sb, tpb) : gates_fp64_shape(CHI, sb, tpb);
+        case PK_BP: return mixed ? bp_mixed_shape(CHI, sb, tpb) : bp_fp64_shape(CHI, sb, tpb);
+        default: return mixed ? regauge_mixed_shape(CHI, sb, tpb) : regauge_fp64_shape(CHI, sb, tpb);
+    }
+}
+inline cudaError_t phase_prepare(bool mixed, int pk, int CHI, size_t smem, int* bps) {
+    switch (pk) {
+        case PK_GATES: return mixed ? gates_mixed_prepare(CHI, smem, bps) : gates_fp64_prepare(CHI, smem, bps);
+        case PK_BP: return mixed ? bp_mixed_prepare(CHI, smem, bps) : bp_fp64_prepare(CHI, smem, bps);
+        default: return mixed ? regauge_mixed_prepare(CHI, smem, bps) : regauge_fp64_prepare(CHI, smem, bps);
+    }
+}
+inline cudaError_t phase_launch(bool mixed, int pk, int CHI, const Ctx& c, size_t smem, cudaStream_t st) {
+    switch (pk) {
+        case PK_GATES: return mixed ? gates_mixed_launch(CHI, c, smem, st) : gates_fp64_launch(CHI, c, smem, st);
+        case PK_BP: return mixed ? bp_mixed_launch(CHI, c, smem, st) : bp_fp64_launch(CHI, c, smem, st);
+        default: return mixed ? regauge_mixed_launch(CHI, c, smem, st) : regauge_fp64_launch(CHI, c, smem, st);
+    }
+}
+
+}  // namespace gtqa

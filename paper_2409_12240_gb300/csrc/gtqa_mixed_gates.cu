@@ -1,0 +1,70 @@
+// gates kernel instantiations, mixed precision mode.
+#include "gtqa_launch.h"
+
+namespace gtqa {
+
+namespace {
+template <int CHI>
+cudaError_t launch_t(const Ctx& c, size_t smem, cudaStream_t st) {
+    Ctx copy = c;
+    void* args[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void*)gates_kernel<CHI, ModeMixed>, dim3(c.nblocks), dim3(Shape<CHI>::TPB), args,
+                                       smem, st);
+}
+template <int CHI>
+cudaError_t prepare_t(size_t smem, int* bps) {
+    cudaError_t e = cudaFuncSetAttribute(gates_kernel<CHI, ModeMixed>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, gates_kernel<CHI, ModeMixed>, Shape<CHI>::TPB, smem);
+}
+}  // namespace
+
+bool gates_mixed_shape(int CHI, size_t* smem_base, int* tpb) {
+    switch (CHI) {
+        case 2: *smem_base = SmemSize<2, ModeMixed, PH_GATES>::value; *tpb = Shape<2>::TPB; return true;
+        case 4: *smem_base = SmemSize<4, ModeMixed, PH_GATES>::value; *tpb = Shape<4>::TPB; return true;
+        case 8: *smem_base = SmemSize<8, ModeMixed, PH_GATES>::value; *tpb = Shape<8>::TPB; return true;
+        default: return false;
+    }
+}
+
+cudaError_t gates_mixed_prepare(int CHI, size_t smem, int* bps) {
+    switch (CHI) {
+        case 2: return prepare_t<2>(smem, bps);
+        case 4: return prepare_t<4>(smem, bps);
+        case 8: return prepare_t<8>(smem, bps);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t gates_mixed_launch(int CHI, const Ctx& c, size_t smem, cudaStream_t st) {
+    switch (CHI) {
+        case 2: return launch_t<2>(c, smem, st);
+        case 4: return launch_t<4>(c, smem, st);
+        case 8: return launch_t<8>(c, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+namespace {
+template <int CHI>
+cudaError_t marg_t(const void* G, const double* lam, const int4* ve, int n, cd* rho, int8_t* sign, int* flag,
+                   cudaStream_t st) {
+    const int wpb = 4;
+    marginals_kernel2<CHI, ModeMixed><<<(n + wpb - 1) / wpb, 32 * wpb, 0, st>>>((const C<typename ModeMixed::TS>*)G, lam, ve, n,
+                                                                             rho, sign, flag);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t marginals_launch_mixed(int CHI, const void* G, const double* lam, const int4* ve, int n, cd* rho,
+                                     int8_t* sign, int* flag, cudaStream_t st) {
+    switch (CHI) {
+        case 2: return marg_t<2>(G, lam, ve, n, rho, sign, flag, st);
+        case 4: return marg_t<4>(G, lam, ve, n, rho, sign, flag, st);
+        case 8: return marg_t<8>(G, lam, ve, n, rho, sign, flag, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gtqa

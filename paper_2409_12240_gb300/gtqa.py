@@ -33,12 +33,11 @@ GTQA_BP_DEFAULT = 3
 
 EXPORTED = [
     "gtqa_options_init", "gtqa_create", "gtqa_create_batch", "gtqa_trotter_layer", "gtqa_bp_sweep",
-    "gtqa_regauge", "gtqa_marginals", "gtqa_stats", "gtqa_get_state", "gtqa_set_state", "gtqa_sizes",
+    "gtqa_regauge", "gtqa_anneal", "gtqa_marginals", "gtqa_stats", "gtqa_get_state", "gtqa_set_state", "gtqa_sizes",
     "gtqa_edge_colouring", "gtqa_strerror", "gtqa_destroy", "gtqa_profile", "gtqa_profile_read",
-    "gtqa_profile_name", "gtqa_alu_peak",
+    "gtqa_profile_name", "gtqa_alu_peak", "gtqa_debug_barrier", "gtqa_math_check",
 ]
-KERNEL_KINDS = ["gate", "mixing", "layer_stats", "symmetric", "warm_start", "bp_sweep", "bp_reduce",
-                "regauge_edge", "regauge_vertex", "marginals"]
+KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
 
 class gtqa_options(ctypes.Structure):
@@ -52,7 +51,7 @@ class gtqa_stats_t(ctypes.Structure):
                 ("not_converged", ctypes.c_int32), ("last_bp_dist", ctypes.c_double),
                 ("discarded_weight", ctypes.c_double), ("log_fidelity", ctypes.c_double),
                 ("svd_pairs", ctypes.c_int64), ("svd_rotations", ctypes.c_int64), ("bp_sweeps", ctypes.c_int64),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("bp_calls", ctypes.c_int64), ("bp_not_converged_calls", ctypes.c_int64)]
 
 
 class GTQAError(RuntimeError):
@@ -87,6 +86,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_trotter_layer": (I32, [P, D, D]),
         "gtqa_bp_sweep": (I32, [P, D, I32, U32, ctypes.POINTER(I32), ctypes.POINTER(D)]),
         "gtqa_regauge": (I32, [P]),
+        "gtqa_anneal": (I32, [P, I32, I32, I32, D, D, I32]),
         "gtqa_marginals": (I32, [P, P, P]),
         "gtqa_stats": (I32, [P, ctypes.POINTER(gtqa_stats_t)]),
         "gtqa_get_state": (I32, [P, P, P, P]),
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_profile_read": (I32, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "gtqa_profile_name": (ctypes.c_char_p, [I32]),
         "gtqa_alu_peak": (I32, [I32, ctypes.POINTER(D)]),
+        "gtqa_debug_barrier": (I32, [P, I64, I32]),
+        "gtqa_math_check": (I32, [I32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -198,6 +200,12 @@ def gtqa_regauge(s: int) -> None:
     _check(load().gtqa_regauge(s), "gtqa_regauge")
 
 
+def gtqa_anneal(s: int, k_begin: int, k_end: int, K: int, dt: float, tol: float, max_iter: int) -> None:
+    """Layers k_begin..k_end of the K-layer anneal in one persistent launch (asynchronous)."""
+    _check(load().gtqa_anneal(s, int(k_begin), int(k_end), int(K), float(dt), float(tol), int(max_iter)),
+           "gtqa_anneal")
+
+
 def gtqa_sizes(s: int) -> Tuple[int, int, int, int]:
     n, m, c, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().gtqa_sizes(s, ctypes.byref(n), ctypes.byref(m), ctypes.byref(c), ctypes.byref(k)), "gtqa_sizes")
@@ -271,6 +279,18 @@ def gtqa_alu_peak(fp64: bool) -> float:
     t = ctypes.c_double()
     _check(load().gtqa_alu_peak(1 if fp64 else 0, ctypes.byref(t)), "gtqa_alu_peak")
     return float(t.value)
+
+
+def gtqa_debug_barrier(s: int, spin_limit: int, extra_arrivals: int) -> None:
+    _check(load().gtqa_debug_barrier(s, int(spin_limit), int(extra_arrivals)), "gtqa_debug_barrier")
+
+
+def gtqa_math_check(x) -> np.ndarray:
+    """(n, 6): refined 1/x, CUDA 1/x, refined x^-1/2, CUDA x^-1/2, refined sqrt, CUDA sqrt."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros((x.size, 6))
+    _check(load().gtqa_math_check(int(x.size), _ptr(x)[0], _ptr(out)[0]), "gtqa_math_check")
+    return out
 
 
 def gtqa_destroy(s: int) -> None:

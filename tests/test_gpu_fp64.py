@@ -178,3 +178,29 @@ def test_n1000_prefix_against_oracle():
     out = U.run_pair(inst, 4, 3200, 0.2, 1e-8, 100, 3, check_every=3)
     assert max(out["rho"]) < 1e-9
     assert max(out["lam"]) < 1e-9
+
+
+def test_many_flooding_sweeps_stay_on_the_oracle_trajectory():
+    """80 sweeps with tol = 0: errors in the common phase of the messages must not grow.
+    Dividing by the complex trace (App. B, unit-trace condition) keeps the flooding
+    iteration identical to the oracle's; a real-part-only division lets that mode
+    double every sweep on a degree-3 graph."""
+    G = U.lib()
+    inst, st = _oracle_state(seed=5, layers=8)
+    tZ, tX = O.schedule(9, 20, 0.1)
+    O.trotter_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 4)
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 4, inst.colour)
+    try:
+        n, m, C, _ = G.gtqa_sizes(s)
+        Gp, Lp = O.to_padded(st, C)
+        G.gtqa_set_state(s, Gp, Lp, np.zeros((2 * m, C, C), dtype=np.complex128))
+        it, dist, conv = G.gtqa_bp_sweep(s, 0.0, 80, G.GTQA_BP_WARM_START)
+        assert it == 80
+        T = O.symmetric_gauge(st)
+        msgs, it_o, hist = O.bp(st, T, O.reconstructed_messages(st), 0.0, 80)
+        _, _, Mg = G.gtqa_get_state(s)
+        Mo = O.messages_to_padded(st, msgs, C)
+        assert np.abs(Mg - Mo).max() < 1e-10
+        assert abs(np.trace(Mg, axis1=1, axis2=2) - 1.0).max() < 1e-13
+    finally:
+        G.gtqa_destroy(s)

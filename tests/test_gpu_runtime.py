@@ -1,0 +1,92 @@
+"""The fused multi-layer launch, batching and the bounded-barrier failure path."""
+import numpy as np
+import pytest
+
+import gpu_util as U
+from instances import make_instance
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fused_anneal_equals_stepwise_calls(precision):
+    G = U.lib()
+    inst = make_instance(40, 3)
+    opt = G.gtqa_options_init(precision=precision)
+    a = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 4, inst.colour, opt)
+    b = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 4, inst.colour, opt)
+    try:
+        K, dt, tol, mi = 30, 0.2, 1e-9, 60
+        G.gtqa_anneal(a, 1, 12, K, dt, tol, mi)
+        G.gtqa_anneal(a, 13, 20, K, dt, tol, mi)
+        for k in range(1, 21):
+            G.gtqa_trotter_layer(b, k / K, dt)
+            G.gtqa_bp_sweep(b, tol, mi)
+        ra, _ = G.gtqa_marginals(a)
+        rb, _ = G.gtqa_marginals(b)
+        assert np.array_equal(ra, rb)
+        Ga, La, _ = G.gtqa_get_state(a)
+        Gb, Lb, _ = G.gtqa_get_state(b)
+        assert np.array_equal(Ga, Gb) and np.array_equal(La, Lb)
+        sa, sb = G.gtqa_stats(a), G.gtqa_stats(b)
+        assert sa["bp_sweeps"] == sb["bp_sweeps"] and sa["layers"] == sb["layers"] == 20
+        assert sa["bp_calls"] == 20
+    finally:
+        G.gtqa_destroy(a)
+        G.gtqa_destroy(b)
+
+
+def test_batch_per_instance_convergence_matches_single_runs():
+    G = U.lib()
+    insts = [make_instance(n, 40 + i) for i, n in enumerate((16, 30, 50, 24))]
+    sb = G.gtqa_create_batch([x.n for x in insts], [x.edges for x in insts], [x.J for x in insts],
+                             [x.h for x in insts], 4, [x.colour for x in insts])
+    singles = [G.gtqa_create(x.n, x.edges, x.J, x.h, 4, x.colour) for x in insts]
+    try:
+        G.gtqa_anneal(sb, 1, 10, 20, 0.2, 1e-10, 80)
+        for s in singles:
+            G.gtqa_anneal(s, 1, 10, 20, 0.2, 1e-10, 80)
+        rb, _ = G.gtqa_marginals(sb)
+        rs = np.concatenate([G.gtqa_marginals(s)[0] for s in singles])
+        assert np.abs(rb - rs).max() < 1e-12
+    finally:
+        G.gtqa_destroy(sb)
+        for s in singles:
+            G.gtqa_destroy(s)
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    """A grid barrier that waits for a block that does not exist gives up after its poll
+    budget; the library reports GTQA_ERR_TIMEOUT and the device stays usable."""
+    G = U.lib()
+    inst = make_instance(16, 0)
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 4, inst.colour)
+    try:
+        G.gtqa_debug_barrier(s, 20000, 1)
+        G.gtqa_trotter_layer(s, 0.5, 0.1)   # asynchronous; the failure shows at the next sync
+        with pytest.raises(G.GTQAError) as ei:
+            G.gtqa_bp_sweep(s, 1e-8, 10)
+        assert ei.value.code == G.GTQA_ERR_TIMEOUT
+        with pytest.raises(G.GTQAError):
+            G.gtqa_trotter_layer(s, 0.5, 0.1)   # sticky
+    finally:
+        G.gtqa_destroy(s)
+    s2 = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 4, inst.colour)
+    try:
+        G.gtqa_trotter_layer(s2, 0.5, 0.1)
+        it, d, conv = G.gtqa_bp_sweep(s2, 1e-10, 100)
+        assert conv
+    finally:
+        G.gtqa_destroy(s2)
+
+
+def test_newton_refined_reciprocal_and_roots_match_cuda():
+    """The kernels replace FP64 divide/sqrt by Newton-Raphson refinement of the PTX
+    approximations; they must agree with CUDA's correctly rounded results to a few ulp."""
+    G = U.lib()
+    rng = np.random.default_rng(0)
+    x = np.concatenate([10.0 ** rng.uniform(-250, 250, 4000), rng.uniform(0.5, 2.0, 1000), [1.0, 2.0, 4.0, 1e-30]])
+    out = G.gtqa_math_check(x)
+    for a, b in ((0, 1), (2, 3), (4, 5)):
+        rel = np.abs(out[:, a] - out[:, b]) / np.abs(out[:, b])
+        assert rel.max() < 4 * np.finfo(float).eps, (a, rel.max())
