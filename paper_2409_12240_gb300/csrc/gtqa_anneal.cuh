@@ -76,7 +76,7 @@ struct Ctx {
     double* lam;
     void* T;
     void* msg[2];
-    cd* D0;                   // mixed: warm-start defect F(m0) - tr F(m0) m0, [2m][CHI^2]
+    cf* D0;                   // mixed: warm-start defect F(m0) - tr F(m0) m0, [2m][CHI^2]
     cd* t0;                   // mixed: tr F(m0), [2m]
     cd* X;                    // regauge transforms [m][2][CHI^2]
     double* acc;              // [3][B] per-sweep distance accumulators
@@ -128,6 +128,10 @@ struct GateSm {
     double tau[4][CHI];
     cd M[4 * CHI * CHI];
     cd V[4 * CHI * CHI];
+    cd G[4 * CHI * CHI];       // mixed: V^H V, then M V
+    cd Vn[4 * CHI * CHI];      // mixed: Newton-Schulz update of V
+    cf M32[4 * CHI * CHI];     // mixed: FP32 copy of M for the preconditioning sweeps
+    cf V32[4 * CHI * CHI];
     double w[2][CHI * CHI];
     double lab[CHI];
     double sig[2 * CHI];
@@ -235,13 +239,66 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
     team_bar<TEAM>(team);
 
     // ---- SVD of M ----
+    // FP64 mode: one-sided Jacobi in FP64 from V = I.
+    // Mixed mode: Jacobi sweeps in FP32 on a copy of M give V32; one FP64 Newton-Schulz
+    // step V <- V (3I - V^H V)/2 makes it unitary to ~1e-14; the FP64 Jacobi then polishes
+    // W = M V (typically one sweep with rotations plus the confirming sweep).  The result
+    // is an FP64 SVD of M with a fraction of the FP64 instructions.
     int nrot = 0, sweeps;
-    if constexpr (TEAM <= 32) {
-        WarpGroup grp{group_mask<TEAM>()};
-        sweeps = jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), 1e-15, 60, true, &nrot);
+    auto svd64 = [&](bool init_v, double tol) {
+        if constexpr (TEAM <= 32) {
+            WarpGroup grp{group_mask<TEAM>()};
+            return jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), tol, 60, init_v, &nrot);
+        } else {
+            TeamGroup<TEAM> grp{team, &sm.flag};
+            return jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), tol, 60, init_v, &nrot);
+        }
+    };
+    if constexpr (!Mode::mixed) {
+        sweeps = svd64(true, 1e-15);
     } else {
-        TeamGroup<TEAM> grp{team, &sm.flag};
-        sweeps = jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), 1e-15, 60, true, &nrot);
+        for (int t = tid; t < NM * NM; t += TEAM) sm.M32[t] = ccast<float>(sm.M[t]);
+        team_bar<TEAM>(team);
+        if constexpr (TEAM <= 32) {
+            WarpGroup grp{group_mask<TEAM>()};
+            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true);
+        } else {
+            TeamGroup<TEAM> grp{team, &sm.flag};
+            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true);
+        }
+        team_bar<TEAM>(team);
+        for (int t = tid; t < NM * NM; t += TEAM) sm.V[t] = ccast<double>(sm.V32[t]);
+        team_bar<TEAM>(team);
+        // G = V^H V (column-major: G[p][q] at q*NM + p)
+        for (int t = tid; t < NM * NM; t += TEAM) {
+            const int q = t / NM, p = t % NM;
+            cd acc = cd{0.0, 0.0};
+            for (int r = 0; r < NM; ++r) acc = cfmac(sm.V[p * NM + r], sm.V[q * NM + r], acc);
+            sm.G[t] = acc;
+        }
+        team_bar<TEAM>(team);
+        // Vn = V (1.5 I - 0.5 G)
+        for (int t = tid; t < NM * NM; t += TEAM) {
+            const int q = t / NM, r = t % NM;
+            cd acc = 1.5 * sm.V[q * NM + r];
+            for (int p = 0; p < NM; ++p) acc = cfma(-0.5 * sm.V[p * NM + r], sm.G[q * NM + p], acc);
+            sm.Vn[t] = acc;
+        }
+        team_bar<TEAM>(team);
+        // W = M Vn into G, then M <- W, V <- Vn
+        for (int t = tid; t < NM * NM; t += TEAM) {
+            const int q = t / NM, r = t % NM;
+            cd acc = cd{0.0, 0.0};
+            for (int p = 0; p < NM; ++p) acc = cfma(sm.M[p * NM + r], sm.Vn[q * NM + p], acc);
+            sm.G[t] = acc;
+        }
+        team_bar<TEAM>(team);
+        for (int t = tid; t < NM * NM; t += TEAM) {
+            sm.M[t] = sm.G[t];
+            sm.V[t] = sm.Vn[t];
+        }
+        team_bar<TEAM>(team);
+        sweeps = svd64(false, 1e-13);
     }
     if (nrot) atomicAdd(&sm.nrot, nrot);
     team_bar<TEAM>(team);
@@ -273,7 +330,8 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
         for (int r = 0; r < CHI; ++r) c.lam[(size_t)e * CHI + r] = (r < keep) ? sm.sig[sm.perm[r]] * inv : 0.0;
         const double disc = tot > 0.0 ? drop * nr_rcp(tot) : 0.0;
         atomicAdd(&c.stats[0], disc);
-        atomicAdd(&c.stats[1], 2.0 * log1p(-disc));
+        // log of the gate fidelity (1 - disc)^2, Eq. (gate_fidelity); a float log in the mixed mode
+        atomicAdd(&c.stats[1], Mode::mixed ? 2.0 * (double)log1pf(-(float)disc) : 2.0 * log1p(-disc));
         atomicAdd(&c.stats[2], (double)sweeps * (NM - 1) * (NM / 2));
         atomicAdd(&c.stats[3], (double)sm.nrot);
         sm.keep = keep;
@@ -358,21 +416,24 @@ __device__ void mixing_vertex(const Ctx& c, int a, int tid, int TEAM, double cX,
 }
 
 // ===========================================================================
-// BP init: symmetric split, warm start, and (mixed) the FP64 warm-start defect
+// BP init (one warp per vertex): symmetric split, warm start, and in the mixed mode
+// the FP64 contraction of the warm start F0 = F(m0, m0), kept as its trace t0 and
+// the defect D0 = F0 - t0 m0 (complex64; |D0| is of the order of the corrections).
 // ===========================================================================
 template <int CHI, class Mode>
-__device__ void bp_init_vertex(const Ctx& c, int a, int tid, int team, int cur, bool warm, double* wsm, cd* tsm) {
+__device__ void bp_init_vertex(const Ctx& c, int a, int tid, int cur, bool warm, double* wsm, cd* tsm) {
     using TS = typename Mode::TS;
     constexpr int H = CHI * CHI * CHI, CC = CHI * CHI, TEAM = Shape<CHI>::TV;
     const int4 ve = c.vert_edges[a];
     const int es[3] = {ve.x, ve.y, ve.z};
-    // wsm[3][CHI]: lambda^{1/2} per slot, then m0 diagonal per slot
+    // wsm[0 .. 3CHI): lambda^{1/2} per slot; wsm[3CHI .. 6CHI): m0 diagonal per slot
     if (tid < 3 * CHI) {
         const int k = tid / CHI, j = tid % CHI;
-        wsm[tid] = nr_sqrt(lam_get(c.lam, CHI, es[k], j));
+        const double lj = lam_get(c.lam, CHI, es[k], j);
+        wsm[tid] = nr_sqrt(lj);
         double s = 0.0;
         for (int q = 0; q < CHI; ++q) s += lam_get(c.lam, CHI, es[k], q);
-        wsm[3 * CHI + tid] = s > 0.0 ? lam_get(c.lam, CHI, es[k], j) * nr_rcp(s) : 0.0;
+        wsm[3 * CHI + tid] = s > 0.0 ? lj * nr_rcp(s) : 0.0;
     }
     __syncwarp();
     const C<TS>* g = (const C<TS>*)c.Gamma + (size_t)a * 2 * H;
@@ -381,79 +442,69 @@ __device__ void bp_init_vertex(const Ctx& c, int a, int tid, int team, int cur, 
         const int r = t % H;
         const int j0 = r / CC, j1 = (r / CHI) % CHI, j2 = r % CHI;
         const double f = wsm[j0] * wsm[CHI + j1] * wsm[2 * CHI + j2];
-        const cd tv = f * ccast<double>(ldcg(g + t));
-        T[t] = ccast<TS>(tv);
-        if constexpr (Mode::mixed) tsm[t] = ccast<double>(ccast<TS>(tv));
+        const C<TS> tv = ccast<TS>(f * ccast<double>(ldcg(g + t)));
+        T[t] = tv;
+        if constexpr (Mode::mixed) tsm[t] = ccast<double>(tv);
     }
-    // outgoing messages of a
-    for (int s = 0; s < 3; ++s) {
-        if (es[s] < 0) continue;
-        const int u = c.edge_info[es[s]].x;
-        const int out = 2 * es[s] + (a == u ? 0 : 1);
-        if constexpr (!Mode::mixed) {
-            if (warm) {
-                cd* mo = (cd*)c.msg[cur] + (size_t)out * CC;
-                for (int r = tid; r < CC; r += TEAM) {
-                    const int j = r / CHI, jp = r % CHI;
-                    mo[r] = cd{j == jp ? wsm[3 * CHI + s * CHI + j] : 0.0, 0.0};
-                }
-            }
-        } else {
-            if (warm) {
-                cf* mo = (cf*)c.msg[cur] + (size_t)out * CC;
-                for (int r = tid; r < CC; r += TEAM) mo[r] = cf{0.f, 0.f};
-            }
+    int out[3];
+    for (int s = 0; s < 3; ++s) out[s] = es[s] >= 0 ? 2 * es[s] + (a == c.edge_info[es[s]].x ? 0 : 1) : -1;
+    if (warm) {
+        for (int t = tid; t < 3 * CC; t += TEAM) {
+            const int s = t / CC, r = t % CC;
+            if (out[s] < 0) continue;
+            const int j = r / CHI, jp = r % CHI;
+            if constexpr (!Mode::mixed) ((cd*)c.msg[cur])[(size_t)out[s] * CC + r] = cd{j == jp ? wsm[3 * CHI + s * CHI + j] : 0.0, 0.0};
+            else ((cf*)c.msg[cur])[(size_t)out[s] * CC + r] = cf{0.f, 0.f};
         }
     }
     if constexpr (Mode::mixed) {
         __syncwarp();
-        // F0 = F(m0_o0, m0_o1) in FP64 for each outgoing slot; D0 = F0 - tr(F0) m0_s
-        constexpr int NPL = (CC + 31) / 32;   // entries per lane
-        for (int s = 0; s < 3; ++s) {
-            if (es[s] < 0) continue;
+        // upper triangle (j <= j') of F0 for the 3 outgoing slots, items spread over the warp
+        constexpr int NU = CHI * (CHI + 1) / 2;
+        cd* F = tsm + 2 * H;   // [3][CC]
+        for (int item = tid; item < 3 * NU; item += TEAM) {
+            const int s = item / NU;
+            int u = item % NU, j = 0;
+            while (u >= CHI - j) { u -= CHI - j; ++j; }
+            const int jp = j + u;
+            if (out[s] < 0) continue;
             int o0, o1;
             others_of(s, o0, o1);
             const int ss = sstride<CHI>(s), s0 = sstride<CHI>(o0), s1 = sstride<CHI>(o1);
-            const int u = c.edge_info[es[s]].x;
-            const int out = 2 * es[s] + (a == u ? 0 : 1);
-            cd f[NPL];
-            cd tr = cd{0.0, 0.0};
-#pragma unroll
-            for (int q8 = 0; q8 < NPL; ++q8) {
-                f[q8] = cd{0.0, 0.0};
-                const int r = tid + 32 * q8;
-                if (r >= CC) continue;
-                const int j = r / CHI, jp = r % CHI;
-                for (int ii = 0; ii < 2; ++ii)
-                    for (int p = 0; p < CHI; ++p) {
-                        const double wp = wsm[3 * CHI + o0 * CHI + p];
-                        if (wp == 0.0) continue;
-                        for (int q = 0; q < CHI; ++q) {
-                            const double wq = wsm[3 * CHI + o1 * CHI + q];
-                            if (wq == 0.0) continue;
-                            const int base = ii * H + p * s0 + q * s1;
-                            f[q8] = cfmac(tsm[base + jp * ss], (wp * wq) * tsm[base + j * ss], f[q8]);
-                        }
+            cd f = cd{0.0, 0.0};
+            for (int p = 0; p < CHI; ++p) {
+                const double wp = wsm[3 * CHI + o0 * CHI + p];
+                if (wp == 0.0) continue;
+                for (int q = 0; q < CHI; ++q) {
+                    const double w = wp * wsm[3 * CHI + o1 * CHI + q];
+                    if (w == 0.0) continue;
+                    for (int ii = 0; ii < 2; ++ii) {
+                        const int base = ii * H + p * s0 + q * s1;
+                        f = cfmac(tsm[base + jp * ss], w * tsm[base + j * ss], f);
                     }
-                if (j == jp) tr = tr + f[q8];
+                }
             }
-            tr.x = group_sum<32>(tr.x, 0xffffffffu);
-            tr.y = group_sum<32>(tr.y, 0xffffffffu);
-#pragma unroll
-            for (int q8 = 0; q8 < NPL; ++q8) {
-                const int r = tid + 32 * q8;
-                if (r >= CC) continue;
-                const int j = r / CHI, jp = r % CHI;
-                const double m0 = (j == jp) ? wsm[3 * CHI + s * CHI + j] : 0.0;
-                c.D0[(size_t)out * CC + r] = f[q8] - m0 * tr;
-            }
-            if (tid == 0) c.t0[out] = tr;
+            F[s * CC + j * CHI + jp] = f;
+            if (jp != j) F[s * CC + jp * CHI + j] = conj(f);
+        }
+        __syncwarp();
+        for (int t = tid; t < 3 * CC; t += TEAM) {
+            const int s = t / CC, r = t % CC;
+            if (out[s] < 0) continue;
+            const int j = r / CHI, jp = r % CHI;
+            double t0 = 0.0;
+            for (int q = 0; q < CHI; ++q) t0 += F[s * CC + q * CHI + q].x;
+            const double m0 = (j == jp) ? wsm[3 * CHI + s * CHI + j] : 0.0;
+            c.D0[(size_t)out[s] * CC + r] = ccast<float>(F[s * CC + r] - cd{t0 * m0, 0.0});
+            if (r == 0) c.t0[out[s]] = cd{t0, 0.0};
         }
     }
 }
 
 // ===========================================================================
-// BP sweep for one vertex: all of its outgoing messages (team TB)
+// BP sweep for one vertex: all of its outgoing messages (team TB).  The per-vertex
+// inputs that do not change during a BP run (T, the warm-start diagonals, D0, t0 and
+// the message indices) are cached in the team's shared memory across sweeps.
 // ===========================================================================
 template <int CHI, class Mode>
 struct BPSm {
@@ -461,66 +512,85 @@ struct BPSm {
     C<TS> T[2 * CHI * CHI * CHI];
     C<TS> P[2 * CHI * CHI * CHI];
     C<TS> Q[2 * CHI * CHI * CHI];
-    C<TS> min[3][CHI * CHI];       // FP64: incoming messages; mixed: incoming m = m0 + delta
+    C<TS> min[3][CHI * CHI];       // FP64: incoming messages; mixed: incoming m0 + delta
     C<TS> din[3][CHI * CHI];       // mixed: incoming delta
     C<TS> mout[3][CHI * CHI];
     C<TS> D[3][CHI * CHI];
     C<TS> DV[3][CHI * CHI];
-    double m0[3][CHI];             // warm-start diagonals per slot
-    cd itr[3];
-    cd trd[3];                     // mixed: tr F(delta terms)
-    double dl[3];
+    cf D0f[3][CHI * CHI];          // mixed: warm-start defect
+    float m0f[3][CHI];             // mixed: warm-start diagonals
+    cd t0[3];                      // mixed: traces of F0
+    C<TS> itr[3];                  // 1 / trace (computed in FP64)
+    C<TS> tau[3];                  // mixed: trace of the correction terms
+    TS dl[3];
+    int es[3], out_idx[3], in_idx[3];
+    int cached;                    // vertex held in the cache, -1 if none
 };
+
+template <int CHI, class Mode>
+__device__ void bp_prepare(const Ctx& c, int a, int tid, int team, BPSm<CHI, Mode>& sm) {
+    using TS = typename Mode::TS;
+    using CT = C<TS>;
+    constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H = CHI * CHI * CHI;
+    if (tid < 3) {
+        const int4 ve = c.vert_edges[a];
+        const int e = tid == 0 ? ve.x : (tid == 1 ? ve.y : ve.z);
+        sm.es[tid] = e;
+        if (e >= 0) {
+            const int u = c.edge_info[e].x;
+            sm.out_idx[tid] = 2 * e + (a == u ? 0 : 1);
+            sm.in_idx[tid] = 2 * e + (a == u ? 1 : 0);
+        } else {
+            sm.out_idx[tid] = sm.in_idx[tid] = -1;
+        }
+    }
+    const CT* Tg = (const CT*)c.T + (size_t)a * 2 * H;
+    for (int t = tid; t < 2 * H; t += TEAM) sm.T[t] = ldcg(Tg + t);
+    team_bar<TEAM>(team);
+    if constexpr (Mode::mixed) {
+        if (tid < 3 * CHI) {
+            const int k = tid / CHI, j = tid % CHI;
+            double s = 0.0;
+            for (int q = 0; q < CHI; ++q) s += lam_get(c.lam, CHI, sm.es[k], q);
+            sm.m0f[k][j] = s > 0.0 ? (float)(lam_get(c.lam, CHI, sm.es[k], j) * nr_rcp(s)) : 0.f;
+        }
+        for (int t = tid; t < 3 * CC; t += TEAM) {
+            const int k = t / CC, r = t % CC;
+            sm.D0f[k][r] = sm.out_idx[k] >= 0 ? ldcg(c.D0 + (size_t)sm.out_idx[k] * CC + r) : cf{0.f, 0.f};
+        }
+        if (tid < 3) sm.t0[tid] = sm.out_idx[tid] >= 0 ? ldcg(c.t0 + sm.out_idx[tid]) : cd{1.0, 0.0};
+    }
+    if (tid == 0) sm.cached = a;
+    team_bar<TEAM>(team);
+}
 
 template <int CHI, class Mode>
 __device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode>& sm) {
     using TS = typename Mode::TS;
     using CT = C<TS>;
     constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H = CHI * CHI * CHI;
-    const int4 ve = c.vert_edges[a];
-    const int es[3] = {ve.x, ve.y, ve.z};
-    int out_idx[3], in_idx[3];
-    for (int k = 0; k < 3; ++k) {
-        if (es[k] >= 0) {
-            const int u = c.edge_info[es[k]].x;
-            out_idx[k] = 2 * es[k] + (a == u ? 0 : 1);
-            in_idx[k] = 2 * es[k] + (a == u ? 1 : 0);
-        } else {
-            out_idx[k] = in_idx[k] = -1;
-        }
-    }
+    if (sm.cached != a) bp_prepare<CHI, Mode>(c, a, tid, team, sm);
     const CT* src = (const CT*)c.msg[cur];
     CT* dst = (CT*)c.msg[cur ^ 1];
-    const CT* Tg = (const CT*)c.T + (size_t)a * 2 * H;
-    for (int t = tid; t < 2 * H; t += TEAM) sm.T[t] = ldcg(Tg + t);
-    if (tid < 3 * CHI) {
-        const int k = tid / CHI, j = tid % CHI;
-        double s = 0.0;
-        for (int q = 0; q < CHI; ++q) s += lam_get(c.lam, CHI, es[k], q);
-        sm.m0[k][j] = s > 0.0 ? lam_get(c.lam, CHI, es[k], j) * nr_rcp(s) : 0.0;
-    }
-    team_bar<TEAM>(team);
     for (int t = tid; t < 3 * CC; t += TEAM) {
         const int k = t / CC, r = t % CC;
-        const int j = r / CHI, jp = r % CHI;
+        const int in = sm.in_idx[k];
         if constexpr (!Mode::mixed) {
-            sm.min[k][r] = (in_idx[k] >= 0) ? ldcg(src + (size_t)in_idx[k] * CC + r)
-                                            : CT{(TS)(r == 0 ? 1 : 0), (TS)0};
+            sm.min[k][r] = in >= 0 ? ldcg(src + (size_t)in * CC + r) : CT{(TS)(r == 0 ? 1 : 0), (TS)0};
         } else {
-            const CT dv = (in_idx[k] >= 0) ? ldcg(src + (size_t)in_idx[k] * CC + r) : CT{0.f, 0.f};
+            const int j = r / CHI, jp = r % CHI;
+            const CT dv = in >= 0 ? ldcg(src + (size_t)in * CC + r) : CT{0.f, 0.f};
             sm.din[k][r] = dv;
-            const float m0 = (j == jp) ? (float)sm.m0[k][j] : 0.f;
-            sm.min[k][r] = CT{dv.x + m0, dv.y};
+            sm.min[k][r] = CT{dv.x + ((j == jp) ? sm.m0f[k][j] : 0.f), dv.y};
         }
     }
     team_bar<TEAM>(team);
     for (int s = 0; s < 3; ++s) {
-        if (es[s] < 0) continue;
+        if (sm.es[s] < 0) continue;
         int o0, o1;
         others_of(s, o0, o1);
         const int ss = sstride<CHI>(s), s0 = sstride<CHI>(o0), s1 = sstride<CHI>(o1);
-        // P[i][a'][b][j] = sum_a T[i; a@o0, b@o1, j@s] x_o0[a][a']
-        //   FP64: x = m;  mixed: x = delta (and P2 = T * m0_o0 handled in the Q step)
+        // P[i][a'][b][j] = sum_a T[i; a@o0, b@o1, j@s] x[a][a']   (FP64: x = m_o0; mixed: x = delta_o0)
         const CT* x0 = Mode::mixed ? sm.din[o0] : sm.min[o0];
         for (int t = tid; t < 2 * H; t += TEAM) {
             const int i = t / H, ap = (t / CC) % CHI, b = (t / CHI) % CHI, j = t % CHI;
@@ -529,13 +599,13 @@ __device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, BPS
             sm.P[t] = acc;
         }
         team_bar<TEAM>(team);
-        // Q[i][a'][b'][j] = sum_b P[i][a'][b][j] m_o1[b][b']  (+ mixed: m0_o0[a'] T[i; a'@o0, b@o1] delta_o1[b][b'])
+        // Q[i][a'][b'][j] = sum_b P[i][a'][b][j] m_o1[b][b']  (+ mixed: m0_o0[a'] sum_b T[i; a'@o0, b@o1] delta_o1[b][b'])
         for (int t = tid; t < 2 * H; t += TEAM) {
             const int i = t / H, ap = (t / CC) % CHI, bp = (t / CHI) % CHI, j = t % CHI;
             CT acc = CT{(TS)0, (TS)0};
             for (int q = 0; q < CHI; ++q) acc = cfma(sm.P[i * H + ap * CC + q * CHI + j], sm.min[o1][q * CHI + bp], acc);
             if constexpr (Mode::mixed) {
-                const TS w = (TS)sm.m0[o0][ap];
+                const TS w = sm.m0f[o0][ap];
                 if (w != (TS)0) {
                     CT a2 = CT{(TS)0, (TS)0};
                     for (int q = 0; q < CHI; ++q)
@@ -558,64 +628,62 @@ __device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, BPS
         }
         team_bar<TEAM>(team);
     }
-    // normalisation (FP64): FP64 mode m' = F / tr F; mixed delta' = (D0 + Fd - m0 tr Fd) / (t0 + tr Fd)
+    // unit trace, divided by the complex trace (reading R10); the trace and its
+    // reciprocal are formed in FP64.  Mixed: delta' = (D0 + Fd - m0 tr Fd) / (t0 + tr Fd).
     if (tid < 3) {
-        cd tr = cd{0.0, 0.0};
-        if (es[tid] >= 0)
-            for (int j = 0; j < CHI; ++j) tr = tr + ccast<double>(sm.mout[tid][j * CHI + j]);
-        if constexpr (Mode::mixed) {
-            if (es[tid] >= 0) tr = tr + ldcg(c.t0 + out_idx[tid]);
-        }
-        const double n2 = norm2(tr);
-        const double in2 = n2 > 0.0 ? nr_rcp(n2) : 0.0;
-        sm.itr[tid] = cd{tr.x * in2, -tr.y * in2};
-        if constexpr (Mode::mixed) {
-            // tr F(delta terms), without t0, for the m0 term of the update
-            cd trd = cd{0.0, 0.0};
-            if (es[tid] >= 0)
-                for (int j = 0; j < CHI; ++j) trd = trd + ccast<double>(sm.mout[tid][j * CHI + j]);
-            sm.trd[tid] = trd;
+        if (sm.es[tid] >= 0) {
+            CT trs = CT{(TS)0, (TS)0};
+            for (int j = 0; j < CHI; ++j) trs = trs + sm.mout[tid][j * CHI + j];
+            cd tr = ccast<double>(trs);
+            if constexpr (Mode::mixed) {
+                sm.tau[tid] = trs;
+                tr = tr + sm.t0[tid];
+            }
+            const double n2 = norm2(tr);
+            const double in2 = n2 > 0.0 ? nr_rcp(n2) : 0.0;
+            sm.itr[tid] = ccast<TS>(cd{tr.x * in2, -tr.y * in2});
         }
     }
     team_bar<TEAM>(team);
     for (int t = tid; t < 3 * CC; t += TEAM) {
         const int k = t / CC, r = t % CC;
-        if (es[k] < 0) {
+        const int out = sm.out_idx[k];
+        if (out < 0) {
             sm.D[k][r] = CT{(TS)0, (TS)0};
             continue;
         }
-        const CT old = ldcg(src + (size_t)out_idx[k] * CC + r);
+        const CT old = ldcg(src + (size_t)out * CC + r);
         CT nv;
         if constexpr (!Mode::mixed) {
             nv = sm.itr[k] * sm.mout[k][r];
         } else {
             const int j = r / CHI, jp = r % CHI;
-            const double m0 = (j == jp) ? sm.m0[k][j] : 0.0;
-            const cd num = ldcg(c.D0 + (size_t)out_idx[k] * CC + r) + ccast<double>(sm.mout[k][r]) - m0 * sm.trd[k];
-            nv = ccast<TS>(sm.itr[k] * num);
+            CT num = sm.D0f[k][r] + sm.mout[k][r];
+            if (j == jp) num = num - sm.m0f[k][j] * sm.tau[k];
+            nv = sm.itr[k] * num;
         }
-        dst[(size_t)out_idx[k] * CC + r] = nv;
+        dst[(size_t)out * CC + r] = nv;
         sm.D[k][r] = nv - old;
     }
     team_bar<TEAM>(team);
+    // trace norms ||m_new - m_old||_1 (singular values of the Hermitian difference)
     constexpr int GJ = CC / 2;
     if (tid < 3 * GJ) {
         const int k = tid / GJ, g = tid % GJ;
         WarpGroup grp{group_mask<GJ>()};
-        jacobi_svd<CHI, TS>(sm.D[k], sm.DV[k], g, grp, group_mask<CHI>(), Mode::mixed ? (TS)1e-6 : (TS)1e-15, 60,
-                            true);
+        jacobi_svd<CHI, TS>(sm.D[k], sm.DV[k], g, grp, group_mask<CHI>(), Mode::mixed ? (TS)1e-6 : (TS)1e-15, 60, true);
         if (g == 0) {
-            double sacc = 0.0;
+            TS sacc = (TS)0;
             for (int cc = 0; cc < CHI; ++cc) {
-                double n2 = 0.0;
-                for (int r = 0; r < CHI; ++r) n2 += (double)norm2(sm.D[k][cc * CHI + r]);
+                TS n2 = (TS)0;
+                for (int r = 0; r < CHI; ++r) n2 += norm2(sm.D[k][cc * CHI + r]);
                 sacc += nr_sqrt(n2);
             }
             sm.dl[k] = sacc;
         }
     }
     team_bar<TEAM>(team);
-    return sm.dl[0] + sm.dl[1] + sm.dl[2];
+    return (double)sm.dl[0] + (double)sm.dl[1] + (double)sm.dl[2];
 }
 
 // copy a frozen instance's outgoing messages to the other buffer
@@ -823,8 +891,9 @@ struct SmemSize {
     static constexpr size_t rg = sizeof(RGSm<CHI>) * (TPB / Shape<CHI>::TR);
     static constexpr size_t rv =
         sizeof(C<typename Mode::TS>) * (4 * CHI * CHI * CHI + 3 * CHI * CHI) * (TPB / Shape<CHI>::TRV);
-    static constexpr size_t init = (sizeof(double) * 6 * CHI + (Mode::mixed ? sizeof(cd) * 2 * CHI * CHI * CHI : 0)) *
-                                   (TPB / 32);
+    static constexpr size_t init =
+        (sizeof(double) * 6 * CHI + (Mode::mixed ? sizeof(cd) * (2 * CHI * CHI * CHI + 3 * CHI * CHI) : 0)) *
+        (TPB / 32);
     static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
     // bytes before the per-instance flags (which follow at this offset in the BP kernel)
     static constexpr size_t value = mx(mx((PH & PH_GATES) ? gate : 0, (PH & PH_BP) ? mx(bp, init) : 0),
@@ -876,9 +945,9 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * (S::TPB / S::TV);
                 double* wsm = reinterpret_cast<double*>(smem) + team * 6 * CHI;
                 cd* tsm = reinterpret_cast<cd*>(reinterpret_cast<double*>(smem) + (S::TPB / 32) * 6 * CHI) +
-                          team * 2 * CHI * CHI * CHI;
+                          team * (2 * CHI * CHI * CHI + 3 * CHI * CHI);
                 for (int a = gteam; a < c.n; a += nt)
-                    bp_init_vertex<CHI, Mode>(c, a, tid, team, cur, (c.phases & PH_WARM) != 0, wsm, tsm);
+                    bp_init_vertex<CHI, Mode>(c, a, tid, cur, (c.phases & PH_WARM) != 0, wsm, tsm);
                 const int g = blockIdx.x * S::TPB + threadIdx.x;
                 for (int b = g; b < c.B; b += c.nblocks * S::TPB) {
                     c.inst_done[b] = 0;   // host-visible copy
@@ -898,6 +967,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
             // identical decisions from the same accumulators, so one barrier per sweep suffices
             int* done = reinterpret_cast<int*>(smem + SmemSize<CHI, Mode, PH>::value);
             for (int b = threadIdx.x; b < c.B; b += S::TPB) done[b] = 0;
+            if (tid == 0) sm.cached = -1;   // T and D0 changed in the init phase
             __syncthreads();
             const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * tpb_teams;
             int it = 0;
@@ -931,10 +1001,11 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 int open_local = 0;
                 for (int b = threadIdx.x; b < c.B; b += S::TPB) {
                     if (done[b]) continue;
-                    const double d = c.inst_m[b] > 0 ? __ldcg(acc + b) / c.inst_m[b] : 0.0;
-                    const bool fin = (d < c.tol) || (it + 1 >= c.max_iter) || !(d == d);
+                    const double dsum = __ldcg(acc + b);
+                    const int mb = c.inst_m[b];
+                    const bool fin = (mb == 0) || (dsum < c.tol * mb) || (it + 1 >= c.max_iter) || !(dsum == dsum);
                     if (blockIdx.x == 0) {
-                        c.inst_dist[b] = d;
+                        c.inst_dist[b] = mb > 0 ? dsum * nr_rcp((double)mb) : 0.0;
                         c.inst_iters[b] = it + 1;
                         if (fin) c.inst_done[b] = 1;
                     }

@@ -27,7 +27,7 @@ struct gtqa_state {
     double* lam = nullptr;
     void* T = nullptr;
     void* msg[2] = {nullptr, nullptr};
-    cd* D0 = nullptr;
+    cf* D0 = nullptr;
     cd* t0 = nullptr;
     cd* X = nullptr;
     int4* edge_info = nullptr;
