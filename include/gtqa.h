@@ -230,6 +230,38 @@ int gtqa_alu_peak(int32_t fp64, double* tflops_out);
  */
 int gtqa_math_check(int32_t n, const double* x, double* out);
 
+/*
+ * Belief propagation that allocates nothing (the paper has no counterpart; this is an
+ * interface for callers that cannot allocate device memory here, e.g. latency-bound
+ * loops that forbid cudaMalloc after start-up, or processes whose device memory belongs
+ * to another allocator's pool).
+ *
+ * Runs the same flooding BP as gtqa_bp_sweep(tol, max_iter, GTQA_BP_WARM_START), FP64,
+ * storage bond dimension GTQA_STATIC_CHI, on one instance held in caller-owned device
+ * (or managed) memory:
+ *   vert_edges    int32 [n][4]: edge id at bond slots 0..2 (-1 = phantom slot), degree
+ *   edge_info     int32 [m][4]: u, v, slot of the edge in u, slot in v
+ *                 (slots are a vertex's incident edges in ascending edge id)
+ *   gamma         complex128 [n][2][4][4][4], Vidal-gauge tensors (read only)
+ *   lambda        float64 [m][4], bond weights (read only)
+ *   messages_out  complex128 [2m][4][4]: the final messages (row 2e = m_{u->v})
+ *   iters_out, dist_out  nullable host pointers: sweeps run and final dist/|E|
+ * Its scratch (symmetric-gauge tensors, second message buffer, control block) lives in a
+ * file-scope device array of about 5.5 MiB that every GPU loading the library holds
+ * until the process exits.  n > GTQA_STATIC_MAX_N or m > GTQA_STATIC_MAX_M, host
+ * pointers, or bad sizes return GTQA_ERR_INVALID_ARG before any device work.  The
+ * first call on a device looks up the array's address and sets the kernel's shared
+ * memory limit; make that first call before any stream capture.  All calls share the
+ * one array: calls that overlap on the GPU (other streams, other threads) race.
+ * Synchronises the stream.  Returns GTQA_ERR_NOT_CONVERGED when max_iter was reached.
+ */
+#define GTQA_STATIC_CHI 4
+#define GTQA_STATIC_MAX_N 2048
+#define GTQA_STATIC_MAX_M 3072
+int gtqa_bp_static(int32_t n, int32_t m, const int32_t* vert_edges, const int32_t* edge_info,
+                   const double* gamma, const double* lambda, double* messages_out, double tol,
+                   int32_t max_iter, int32_t* iters_out, double* dist_out, void* cuda_stream);
+
 /* Static description of an error code. */
 const char* gtqa_strerror(int code);
 

@@ -35,7 +35,7 @@ EXPORTED = [
     "gtqa_options_init", "gtqa_create", "gtqa_create_batch", "gtqa_trotter_layer", "gtqa_bp_sweep",
     "gtqa_regauge", "gtqa_anneal", "gtqa_marginals", "gtqa_stats", "gtqa_get_state", "gtqa_set_state", "gtqa_sizes",
     "gtqa_edge_colouring", "gtqa_strerror", "gtqa_destroy", "gtqa_profile", "gtqa_profile_read",
-    "gtqa_profile_name", "gtqa_alu_peak", "gtqa_debug_barrier", "gtqa_math_check",
+    "gtqa_profile_name", "gtqa_alu_peak", "gtqa_debug_barrier", "gtqa_math_check", "gtqa_bp_static",
 ]
 KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_alu_peak": (I32, [I32, ctypes.POINTER(D)]),
         "gtqa_debug_barrier": (I32, [P, I64, I32]),
         "gtqa_math_check": (I32, [I32, P, P]),
+        "gtqa_bp_static": (I32, [I32, I32, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -291,6 +292,20 @@ def gtqa_math_check(x) -> np.ndarray:
     out = np.zeros((x.size, 6))
     _check(load().gtqa_math_check(int(x.size), _ptr(x)[0], _ptr(out)[0]), "gtqa_math_check")
     return out
+
+
+def gtqa_bp_static(n: int, m: int, vert_edges, edge_info, gamma, lam, messages_out, tol: float,
+                   max_iter: int, cuda_stream: int = 0) -> Tuple[int, int, float]:
+    """BP without device allocation on caller-owned device buffers (torch CUDA tensors).
+    Returns (status code, sweeps run, final dist/|E|); raises on errors other than
+    GTQA_ERR_NOT_CONVERGED."""
+    it = ctypes.c_int32()
+    d = ctypes.c_double()
+    rc = load().gtqa_bp_static(int(n), int(m), _ptr(vert_edges)[0], _ptr(edge_info)[0], _ptr(gamma)[0],
+                               _ptr(lam)[0], _ptr(messages_out)[0], float(tol), int(max_iter), ctypes.byref(it),
+                               ctypes.byref(d), cuda_stream or None)
+    _check(rc, "gtqa_bp_static", (GTQA_OK, GTQA_ERR_NOT_CONVERGED))
+    return rc, int(it.value), float(d.value)
 
 
 def gtqa_destroy(s: int) -> None:
