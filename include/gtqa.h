@@ -231,6 +231,13 @@ int gtqa_alu_peak(int32_t fp64, double* tflops_out);
 int gtqa_math_check(int32_t n, const double* x, double* out);
 
 /*
+ * Diagnostic: average latency in microseconds of the bounded grid barrier that separates
+ * the phases of the kernels (cooperative launch, one block of `threads` per SM, `rounds`
+ * consecutive barriers, best of three launches).
+ */
+int gtqa_barrier_bench(int32_t threads, int32_t rounds, double* us_per_barrier);
+
+/*
  * Belief propagation that allocates nothing (the paper has no counterpart; this is an
  * interface for callers that cannot allocate device memory here, e.g. latency-bound
  * loops that forbid cudaMalloc after start-up, or processes whose device memory belongs

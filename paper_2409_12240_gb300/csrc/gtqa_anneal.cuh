@@ -616,15 +616,29 @@ __device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, BPS
             sm.Q[t] = acc;
         }
         team_bar<TEAM>(team);
-        // out[j][j'] = sum_{i,a',b'} Q[i][a'][b'][j] conj(T[i; a'@o0, b'@o1, j'@s])
-        for (int t = tid; t < CC; t += TEAM) {
+        // out[j][j'] = sum_{i,a',b'} Q[i][a'][b'][j] conj(T[i; a'@o0, b'@o1, j'@s]); the two
+        // physical indices go to the two halves of the team and are added at the end
+        if constexpr (2 * CC <= 32 && TEAM >= 2 * CC) {
+            const int i = tid / CC, t = tid % CC;
             const int j = t / CHI, jp = t % CHI;
             CT acc = CT{(TS)0, (TS)0};
-            for (int i = 0; i < 2; ++i)
+            if (tid < 2 * CC)
                 for (int ap = 0; ap < CHI; ++ap)
                     for (int bp = 0; bp < CHI; ++bp)
                         acc = cfmac(sm.T[i * H + ap * s0 + bp * s1 + jp * ss], sm.Q[i * H + ap * CC + bp * CHI + j], acc);
-            sm.mout[s][t] = acc;
+            acc.x += __shfl_down_sync(0xffffffffu, acc.x, CC);
+            acc.y += __shfl_down_sync(0xffffffffu, acc.y, CC);
+            if (tid < CC) sm.mout[s][t] = acc;
+        } else {
+            for (int t = tid; t < CC; t += TEAM) {
+                const int j = t / CHI, jp = t % CHI;
+                CT acc = CT{(TS)0, (TS)0};
+                for (int i = 0; i < 2; ++i)
+                    for (int ap = 0; ap < CHI; ++ap)
+                        for (int bp = 0; bp < CHI; ++bp)
+                            acc = cfmac(sm.T[i * H + ap * s0 + bp * s1 + jp * ss], sm.Q[i * H + ap * CC + bp * CHI + j], acc);
+                sm.mout[s][t] = acc;
+            }
         }
         team_bar<TEAM>(team);
     }

@@ -275,8 +275,7 @@ struct GridBarrier {
 
 __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned int nblocks, long long limit) {
     __shared__ int ok_shared;
-    __threadfence();
-    __syncthreads();
+    __syncthreads();   // the block's writes happen before thread 0's release below
     if (threadIdx.x == 0) {
         const unsigned int g = *(volatile unsigned int*)gb.gen;
         __threadfence();
@@ -292,7 +291,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned int nb
                     atomicExch(gb.err, 6);   // GTQA_ERR_TIMEOUT
                     break;
                 }
-                if (polls > 64) __nanosleep(64);
+                if (polls > 2048) __nanosleep(32);
             }
         }
         __threadfence();

@@ -94,3 +94,50 @@ extern "C" int gtqa_math_check(int32_t n, const double* x, double* out) {
     cudaFree(dout);
     return e == cudaSuccess ? GTQA_OK : GTQA_ERR_CUDA;
 }
+
+// Diagnostic: latency of the bounded grid barrier used by the phase kernels
+// (cooperative launch, one block of `threads` per SM, `rounds` barriers).
+namespace {
+__global__ void barrier_bench_kernel(unsigned int* cnt, unsigned int* gen, int* err, int rounds) {
+    const gtqa::GridBarrier gb{cnt, gen, err};
+    for (int r = 0; r < rounds; ++r)
+        if (!gtqa::grid_sync(gb, gridDim.x, 1LL << 22)) return;
+}
+}  // namespace
+
+extern "C" int gtqa_barrier_bench(int32_t threads, int32_t rounds, double* us_per_barrier) {
+    if (threads < 32 || threads > 1024 || rounds < 1 || !us_per_barrier) return GTQA_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GTQA_ERR_CUDA;
+    unsigned int* buf = nullptr;
+    if (cudaMalloc(&buf, 4 * sizeof(unsigned int)) != cudaSuccess) return GTQA_ERR_OOM;
+    cudaMemset(buf, 0, 4 * sizeof(unsigned int));
+    unsigned int* cnt = buf;
+    unsigned int* gen = buf + 1;
+    int* err = reinterpret_cast<int*>(buf + 2);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        void* args[] = {&cnt, &gen, &err, &rounds};
+        cudaEventRecord(e0);
+        cudaLaunchCooperativeKernel((const void*)barrier_bench_kernel, dim3(sms), dim3(threads), args, 0, nullptr);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    int herr = 0;
+    cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    const cudaError_t ce = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (ce != cudaSuccess) return GTQA_ERR_CUDA;
+    if (herr) return herr;
+    *us_per_barrier = best * 1e3 / rounds;
+    return GTQA_OK;
+}

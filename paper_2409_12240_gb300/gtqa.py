@@ -36,6 +36,7 @@ EXPORTED = [
     "gtqa_regauge", "gtqa_anneal", "gtqa_marginals", "gtqa_stats", "gtqa_get_state", "gtqa_set_state", "gtqa_sizes",
     "gtqa_edge_colouring", "gtqa_strerror", "gtqa_destroy", "gtqa_profile", "gtqa_profile_read",
     "gtqa_profile_name", "gtqa_alu_peak", "gtqa_debug_barrier", "gtqa_math_check", "gtqa_bp_static",
+    "gtqa_barrier_bench",
 ]
 KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
@@ -101,6 +102,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_alu_peak": (I32, [I32, ctypes.POINTER(D)]),
         "gtqa_debug_barrier": (I32, [P, I64, I32]),
         "gtqa_math_check": (I32, [I32, P, P]),
+        "gtqa_barrier_bench": (I32, [I32, I32, ctypes.POINTER(D)]),
         "gtqa_bp_static": (I32, [I32, I32, P, P, P, P, P, D, I32, ctypes.POINTER(I32), ctypes.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
@@ -306,6 +308,13 @@ def gtqa_bp_static(n: int, m: int, vert_edges, edge_info, gamma, lam, messages_o
                                ctypes.byref(d), cuda_stream or None)
     _check(rc, "gtqa_bp_static", (GTQA_OK, GTQA_ERR_NOT_CONVERGED))
     return rc, int(it.value), float(d.value)
+
+
+def gtqa_barrier_bench(threads: int = 512, rounds: int = 2000) -> float:
+    """Microseconds per grid barrier (cooperative launch, one block per SM)."""
+    us = ctypes.c_double()
+    _check(load().gtqa_barrier_bench(int(threads), int(rounds), ctypes.byref(us)), "gtqa_barrier_bench")
+    return float(us.value)
 
 
 def gtqa_destroy(s: int) -> None:
