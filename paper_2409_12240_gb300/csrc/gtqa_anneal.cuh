@@ -112,7 +112,7 @@ __device__ __forceinline__ double lam_get(const double* lam, int CHI, int e, int
 template <int CHI> struct Shape {
     static constexpr int TPB = CHI >= 8 ? 256 : 512;
     static constexpr int TG = 2 * CHI * CHI;                    // gate team
-    static constexpr int TB = 2 * CHI * CHI >= 32 ? 2 * CHI * CHI : 32;   // BP team
+    static constexpr int TB = CHI >= 8 ? 256 : 64;               // BP team (one vertex)
     static constexpr int TR = CHI * CHI;                        // regauge-edge team
     static constexpr int TV = 32;                               // BP-init team (one warp)
     static constexpr int TRV = CHI >= 8 ? 128 : 32;             // regauge-vertex team
@@ -502,36 +502,45 @@ __device__ void bp_init_vertex(const Ctx& c, int a, int tid, int cur, bool warm,
 }
 
 // ===========================================================================
-// BP sweep for one vertex: all of its outgoing messages (team TB).  The per-vertex
-// inputs that do not change during a BP run (T, the warm-start diagonals, D0, t0 and
-// the message indices) are cached in the team's shared memory across sweeps.
+// BP sweep for one vertex: all three outgoing messages at once (team TB).
+//
+// With T in its natural layout [i][j0][j1][j2] the message out of slot s is
+//   F_s[j][j'] = sum T[..j@s..] conj(T[..j'@s..]) x (m_o0 (x) m_o1),        Eq. (local_consistency)
+// computed as: first contractions along single slots (shared between the outgoing
+// slots), second contractions per slot (Q_s), then the overlap with conj(T).  In the
+// mixed mode the incoming messages are m = m0 + delta and only the delta terms are
+// contracted (FP32): F_s - F_s(m0) = T x_{o0} delta x_{o1} m + m0_{o0} T x_{o1} delta.
+// The per-vertex inputs that do not change during a BP run (T, the warm-start
+// diagonals, D0, t0, this vertex's previous outgoing messages) are cached in the
+// team's shared memory across sweeps.
 // ===========================================================================
 template <int CHI, class Mode>
 struct BPSm {
     using TS = typename Mode::TS;
-    C<TS> T[2 * CHI * CHI * CHI];
-    C<TS> P[2 * CHI * CHI * CHI];
-    C<TS> Q[2 * CHI * CHI * CHI];
-    C<TS> min[3][CHI * CHI];       // FP64: incoming messages; mixed: incoming m0 + delta
-    C<TS> din[3][CHI * CHI];       // mixed: incoming delta
-    C<TS> mout[3][CHI * CHI];
-    C<TS> D[3][CHI * CHI];
-    C<TS> DV[3][CHI * CHI];
-    cf D0f[3][CHI * CHI];          // mixed: warm-start defect
-    float m0f[3][CHI];             // mixed: warm-start diagonals
-    cd t0[3];                      // mixed: traces of F0
-    C<TS> itr[3];                  // 1 / trace (computed in FP64)
-    C<TS> tau[3];                  // mixed: trace of the correction terms
+    static constexpr int H2 = 2 * CHI * CHI * CHI, CC = CHI * CHI, NP = Mode::mixed ? 3 : 2;
+    C<TS> T[H2];
+    C<TS> P[NP][H2];     // FP64: T x0 m0, T x1 m1; mixed: T x0 d0, T x1 d1, T x2 d2
+    C<TS> Q[3][H2];      // per outgoing slot
+    C<TS> min[3][CC];    // incoming messages (mixed: m0 + delta)
+    C<TS> din[3][CC];    // mixed: incoming delta
+    C<TS> Fh[2][3][CC];  // the two physical-index halves of the outgoing messages
+    C<TS> prev[3][CC];   // outgoing messages of the previous sweep
+    C<TS> D[3][CC];      // new - old, for the trace norm
+    cf D0f[3][CC];       // mixed: warm-start defect
+    float m0f[3][CHI];   // mixed: warm-start diagonals
+    cd t0[3];            // mixed: traces of F0
+    C<TS> itr[3];        // 1 / trace (formed in FP64)
+    C<TS> tau[3];        // mixed: trace of the correction terms
     TS dl[3];
     int es[3], out_idx[3], in_idx[3];
-    int cached;                    // vertex held in the cache, -1 if none
+    int cached;          // vertex held in the cache, -1 if none
 };
 
 template <int CHI, class Mode>
-__device__ void bp_prepare(const Ctx& c, int a, int tid, int team, BPSm<CHI, Mode>& sm) {
+__device__ void bp_prepare(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode>& sm) {
     using TS = typename Mode::TS;
     using CT = C<TS>;
-    constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H = CHI * CHI * CHI;
+    constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H2 = 2 * CHI * CHI * CHI;
     if (tid < 3) {
         const int4 ve = c.vert_edges[a];
         const int e = tid == 0 ? ve.x : (tid == 1 ? ve.y : ve.z);
@@ -544,9 +553,15 @@ __device__ void bp_prepare(const Ctx& c, int a, int tid, int team, BPSm<CHI, Mod
             sm.out_idx[tid] = sm.in_idx[tid] = -1;
         }
     }
-    const CT* Tg = (const CT*)c.T + (size_t)a * 2 * H;
-    for (int t = tid; t < 2 * H; t += TEAM) sm.T[t] = ldcg(Tg + t);
+    const CT* Tg = (const CT*)c.T + (size_t)a * H2;
+    for (int t = tid; t < H2; t += TEAM) sm.T[t] = ldcg(Tg + t);
     team_bar<TEAM>(team);
+    const CT* src = (const CT*)c.msg[cur];
+    for (int t = tid; t < 3 * CC; t += TEAM) {
+        const int k = t / CC, r = t % CC;
+        const int out = sm.out_idx[k];
+        sm.prev[k][r] = out >= 0 ? ldcg(src + (size_t)out * CC + r) : CT{(TS)0, (TS)0};
+    }
     if constexpr (Mode::mixed) {
         if (tid < 3 * CHI) {
             const int k = tid / CHI, j = tid % CHI;
@@ -568,10 +583,13 @@ template <int CHI, class Mode>
 __device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode>& sm) {
     using TS = typename Mode::TS;
     using CT = C<TS>;
-    constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H = CHI * CHI * CHI;
-    if (sm.cached != a) bp_prepare<CHI, Mode>(c, a, tid, team, sm);
+    constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H = CHI * CHI * CHI, H2 = 2 * H;
+    constexpr int S0 = CHI * CHI, S1 = CHI;   // strides of slots 0 and 1 (slot 2 has stride 1)
+    if (sm.cached != a) bp_prepare<CHI, Mode>(c, a, tid, team, cur, sm);
     const CT* src = (const CT*)c.msg[cur];
     CT* dst = (CT*)c.msg[cur ^ 1];
+    const CT z = CT{(TS)0, (TS)0};
+    // incoming messages
     for (int t = tid; t < 3 * CC; t += TEAM) {
         const int k = t / CC, r = t % CC;
         const int in = sm.in_idx[k];
@@ -579,113 +597,116 @@ __device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, BPS
             sm.min[k][r] = in >= 0 ? ldcg(src + (size_t)in * CC + r) : CT{(TS)(r == 0 ? 1 : 0), (TS)0};
         } else {
             const int j = r / CHI, jp = r % CHI;
-            const CT dv = in >= 0 ? ldcg(src + (size_t)in * CC + r) : CT{0.f, 0.f};
+            const CT dv = in >= 0 ? ldcg(src + (size_t)in * CC + r) : z;
             sm.din[k][r] = dv;
             sm.min[k][r] = CT{dv.x + ((j == jp) ? sm.m0f[k][j] : 0.f), dv.y};
         }
     }
     team_bar<TEAM>(team);
-    for (int s = 0; s < 3; ++s) {
-        if (sm.es[s] < 0) continue;
-        int o0, o1;
-        others_of(s, o0, o1);
-        const int ss = sstride<CHI>(s), s0 = sstride<CHI>(o0), s1 = sstride<CHI>(o1);
-        // P[i][a'][b][j] = sum_a T[i; a@o0, b@o1, j@s] x[a][a']   (FP64: x = m_o0; mixed: x = delta_o0)
-        const CT* x0 = Mode::mixed ? sm.din[o0] : sm.min[o0];
-        for (int t = tid; t < 2 * H; t += TEAM) {
-            const int i = t / H, ap = (t / CC) % CHI, b = (t / CHI) % CHI, j = t % CHI;
-            CT acc = CT{(TS)0, (TS)0};
-            for (int q = 0; q < CHI; ++q) acc = cfma(sm.T[i * H + q * s0 + b * s1 + j * ss], x0[q * CHI + ap], acc);
-            sm.P[t] = acc;
-        }
-        team_bar<TEAM>(team);
-        // Q[i][a'][b'][j] = sum_b P[i][a'][b][j] m_o1[b][b']  (+ mixed: m0_o0[a'] sum_b T[i; a'@o0, b@o1] delta_o1[b][b'])
-        for (int t = tid; t < 2 * H; t += TEAM) {
-            const int i = t / H, ap = (t / CC) % CHI, bp = (t / CHI) % CHI, j = t % CHI;
-            CT acc = CT{(TS)0, (TS)0};
-            for (int q = 0; q < CHI; ++q) acc = cfma(sm.P[i * H + ap * CC + q * CHI + j], sm.min[o1][q * CHI + bp], acc);
-            if constexpr (Mode::mixed) {
-                const TS w = sm.m0f[o0][ap];
-                if (w != (TS)0) {
-                    CT a2 = CT{(TS)0, (TS)0};
-                    for (int q = 0; q < CHI; ++q)
-                        a2 = cfma(sm.T[i * H + ap * s0 + q * s1 + j * ss], sm.din[o1][q * CHI + bp], a2);
-                    acc = acc + w * a2;
-                }
-            }
-            sm.Q[t] = acc;
-        }
-        team_bar<TEAM>(team);
-        // out[j][j'] = sum_{i,a',b'} Q[i][a'][b'][j] conj(T[i; a'@o0, b'@o1, j'@s]); the two
-        // physical indices go to the two halves of the team and are added at the end
-        if constexpr (2 * CC <= 32 && TEAM >= 2 * CC) {
-            const int i = tid / CC, t = tid % CC;
-            const int j = t / CHI, jp = t % CHI;
-            CT acc = CT{(TS)0, (TS)0};
-            if (tid < 2 * CC)
-                for (int ap = 0; ap < CHI; ++ap)
-                    for (int bp = 0; bp < CHI; ++bp)
-                        acc = cfmac(sm.T[i * H + ap * s0 + bp * s1 + jp * ss], sm.Q[i * H + ap * CC + bp * CHI + j], acc);
-            acc.x += __shfl_down_sync(0xffffffffu, acc.x, CC);
-            acc.y += __shfl_down_sync(0xffffffffu, acc.y, CC);
-            if (tid < CC) sm.mout[s][t] = acc;
-        } else {
-            for (int t = tid; t < CC; t += TEAM) {
-                const int j = t / CHI, jp = t % CHI;
-                CT acc = CT{(TS)0, (TS)0};
-                for (int i = 0; i < 2; ++i)
-                    for (int ap = 0; ap < CHI; ++ap)
-                        for (int bp = 0; bp < CHI; ++bp)
-                            acc = cfmac(sm.T[i * H + ap * s0 + bp * s1 + jp * ss], sm.Q[i * H + ap * CC + bp * CHI + j], acc);
-                sm.mout[s][t] = acc;
-            }
-        }
-        team_bar<TEAM>(team);
-    }
-    // unit trace, divided by the complex trace (reading R10); the trace and its
-    // reciprocal are formed in FP64.  Mixed: delta' = (D0 + Fd - m0 tr Fd) / (t0 + tr Fd).
-    if (tid < 3) {
-        if (sm.es[tid] >= 0) {
-            CT trs = CT{(TS)0, (TS)0};
-            for (int j = 0; j < CHI; ++j) trs = trs + sm.mout[tid][j * CHI + j];
-            cd tr = ccast<double>(trs);
-            if constexpr (Mode::mixed) {
-                sm.tau[tid] = trs;
-                tr = tr + sm.t0[tid];
-            }
-            const double n2 = norm2(tr);
-            const double in2 = n2 > 0.0 ? nr_rcp(n2) : 0.0;
-            sm.itr[tid] = ccast<TS>(cd{tr.x * in2, -tr.y * in2});
-        }
+    // first contractions along one slot: P_k[.., x@k, ..] = sum_q T[.., q@k, ..] y_k[q][x]
+    //   FP64: y = m (k = 0, 1); mixed: y = delta (k = 0, 1, 2)
+    constexpr int NP = BPSm<CHI, Mode>::NP;
+    for (int t = tid; t < NP * H2; t += TEAM) {
+        const int k = t / H2, e = t % H2;
+        const int j0 = (e / S0) % CHI, j1 = (e / S1) % CHI, j2 = e % CHI;
+        const int st = k == 0 ? S0 : (k == 1 ? S1 : 1);
+        const int x = k == 0 ? j0 : (k == 1 ? j1 : j2);
+        const int base = e - x * st;
+        const CT* y = Mode::mixed ? sm.din[k] : sm.min[k];
+        CT acc = z;
+#pragma unroll
+        for (int q = 0; q < CHI; ++q) acc = cfma(sm.T[base + q * st], y[q * CHI + x], acc);
+        sm.P[k][e] = acc;
     }
     team_bar<TEAM>(team);
+    // second contractions per outgoing slot s (natural layout, slot-s index = j):
+    //   Q_0[i][j][a][b] = sum_q P_1[i][j][a][q] m_2[q][b]  (+ m0_1[a] P_2[i][j][a][b])
+    //   Q_1[i][a][j][b] = sum_q P_0[i][a][j][q] m_2[q][b]  (+ m0_0[a] P_2[i][a][j][b])
+    //   Q_2[i][a][b][j] = sum_q P_0[i][a][q][j] m_1[q][b]  (+ m0_0[a] P_1[i][a][b][j])
+    for (int t = tid; t < 3 * H2; t += TEAM) {
+        const int s = t / H2, e = t % H2;
+        if (sm.es[s] < 0) continue;
+        const int j0 = (e / S0) % CHI, j1 = (e / S1) % CHI, j2 = e % CHI;
+        CT acc = z;
+        if (s == 2) {
+#pragma unroll
+            for (int q = 0; q < CHI; ++q) acc = cfma(sm.P[0][e - j1 * S1 + q * S1], sm.min[1][q * CHI + j1], acc);
+        } else {
+            const CT* Ps = (s == 0) ? sm.P[1] : sm.P[0];
+#pragma unroll
+            for (int q = 0; q < CHI; ++q) acc = cfma(Ps[e - j2 + q], sm.min[2][q * CHI + j2], acc);
+        }
+        if constexpr (Mode::mixed) {
+            const float w = (s == 0) ? sm.m0f[1][j1] : sm.m0f[0][j0];
+            const CT pe = (s == 2) ? sm.P[1][e] : sm.P[2][e];
+            acc = acc + w * pe;
+        }
+        sm.Q[s][e] = acc;
+    }
+    team_bar<TEAM>(team);
+    // overlaps with conj(T), one half per physical index: Fh[i][s][j][j']
+    for (int t = tid; t < 2 * 3 * CC; t += TEAM) {
+        const int i = t / (3 * CC), rem = t % (3 * CC);
+        const int s = rem / CC, r = rem % CC;
+        if (sm.es[s] < 0) continue;
+        const int j = r / CHI, jp = r % CHI;
+        const int ss = s == 0 ? S0 : (s == 1 ? S1 : 1);
+        const int so = s == 0 ? S1 : S0, st2 = s == 2 ? S1 : 1;   // strides of the two other slots
+        CT acc = z;
+#pragma unroll
+        for (int u = 0; u < CHI; ++u)
+#pragma unroll
+            for (int v = 0; v < CHI; ++v) {
+                const int off = i * H + u * so + v * st2;
+                acc = cfmac(sm.T[off + jp * ss], sm.Q[s][off + j * ss], acc);
+            }
+        sm.Fh[i][s][r] = acc;
+    }
+    team_bar<TEAM>(team);
+    // traces and their reciprocals in FP64 (reading R10: divide by the complex trace)
+    if (tid < 3 && sm.es[tid] >= 0) {
+        CT trs = z;
+        for (int j = 0; j < CHI; ++j) trs = trs + (sm.Fh[0][tid][j * CHI + j] + sm.Fh[1][tid][j * CHI + j]);
+        cd tr = ccast<double>(trs);
+        if constexpr (Mode::mixed) {
+            sm.tau[tid] = trs;
+            tr = tr + sm.t0[tid];
+        }
+        const double n2 = norm2(tr);
+        const double in2 = n2 > 0.0 ? nr_rcp(n2) : 0.0;
+        sm.itr[tid] = ccast<TS>(cd{tr.x * in2, -tr.y * in2});
+    }
+    team_bar<TEAM>(team);
+    // new messages; mixed: delta' = (D0 + Fd - m0 tr Fd) / (t0 + tr Fd)
     for (int t = tid; t < 3 * CC; t += TEAM) {
         const int k = t / CC, r = t % CC;
         const int out = sm.out_idx[k];
         if (out < 0) {
-            sm.D[k][r] = CT{(TS)0, (TS)0};
+            sm.D[k][r] = z;
             continue;
         }
-        const CT old = ldcg(src + (size_t)out * CC + r);
+        const CT f = sm.Fh[0][k][r] + sm.Fh[1][k][r];
         CT nv;
         if constexpr (!Mode::mixed) {
-            nv = sm.itr[k] * sm.mout[k][r];
+            nv = sm.itr[k] * f;
         } else {
             const int j = r / CHI, jp = r % CHI;
-            CT num = sm.D0f[k][r] + sm.mout[k][r];
+            CT num = sm.D0f[k][r] + f;
             if (j == jp) num = num - sm.m0f[k][j] * sm.tau[k];
             nv = sm.itr[k] * num;
         }
         dst[(size_t)out * CC + r] = nv;
-        sm.D[k][r] = nv - old;
+        sm.D[k][r] = nv - sm.prev[k][r];
+        sm.prev[k][r] = nv;
     }
     team_bar<TEAM>(team);
-    // trace norms ||m_new - m_old||_1 (singular values of the Hermitian difference)
+    // trace norms ||m_new - m_old||_1 = sum of singular values of the Hermitian difference
     constexpr int GJ = CC / 2;
     if (tid < 3 * GJ) {
         const int k = tid / GJ, g = tid % GJ;
         WarpGroup grp{group_mask<GJ>()};
-        jacobi_svd<CHI, TS>(sm.D[k], sm.DV[k], g, grp, group_mask<CHI>(), Mode::mixed ? (TS)1e-6 : (TS)1e-15, 60, true);
+        jacobi_svd<CHI, TS, WarpGroup, false>(sm.D[k], nullptr, g, grp, group_mask<CHI>(),
+                                               Mode::mixed ? (TS)1e-6 : (TS)1e-15, 60, false);
         if (g == 0) {
             TS sacc = (TS)0;
             for (int cc = 0; cc < CHI; ++cc) {

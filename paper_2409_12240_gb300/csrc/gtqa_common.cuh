@@ -146,12 +146,12 @@ __device__ __forceinline__ void round_robin_pair(int N, int step, int k, int& p,
     if (p > q) { int t = p; p = q; q = t; }
 }
 
-template <int N, typename R, typename Group>
+template <int N, typename R, typename Group, bool WITHV = true>
 __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pair_mask,
                           R tol, int max_sweeps, bool init_v, int* nrot = nullptr) {
     const int k = g / N;
     const int r = g % N;
-    if (init_v) {
+    if (WITHV && init_v) {
         V[(2 * k) * N + r] = C<R>{(R)((2 * k) == r), (R)0};
         V[(2 * k + 1) * N + r] = C<R>{(R)((2 * k + 1) == r), (R)0};
     }
@@ -184,9 +184,11 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
                 const C<R> sec = conj(se);
                 A[p * N + r] = c * ap - sec * aq;
                 A[q * N + r] = se * ap + c * aq;
-                const C<R> vp = V[p * N + r], vq = V[q * N + r];
-                V[p * N + r] = c * vp - sec * vq;
-                V[q * N + r] = se * vp + c * vq;
+                if constexpr (WITHV) {
+                    const C<R> vp = V[p * N + r], vq = V[q * N + r];
+                    V[p * N + r] = c * vp - sec * vq;
+                    V[q * N + r] = se * vp + c * vq;
+                }
                 rotated = 1;
                 if (nrot && r == 0) ++*nrot;
             }
