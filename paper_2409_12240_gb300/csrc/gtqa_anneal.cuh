@@ -580,7 +580,7 @@ __device__ void bp_prepare(const Ctx& c, int a, int tid, int team, int cur, BPSm
 }
 
 template <int CHI, class Mode>
-__device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode>& sm) {
+__device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, bool exact, BPSm<CHI, Mode>& sm) {
     using TS = typename Mode::TS;
     using CT = C<TS>;
     constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H = CHI * CHI * CHI, H2 = 2 * H;
@@ -700,9 +700,23 @@ __device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, BPS
         sm.prev[k][r] = nv;
     }
     team_bar<TEAM>(team);
-    // trace norms ||m_new - m_old||_1 = sum of singular values of the Hermitian difference
+    // distance of App. B: trace norms ||m_new - m_old||_1 (sum of singular values) when
+    // `exact`, else the Frobenius norms, a lower bound that suffices to continue
     constexpr int GJ = CC / 2;
-    if (tid < 3 * GJ) {
+    static_assert(3 * GJ <= TEAM && 3 * CHI <= 32 && 3 * CC <= TEAM, "BP team too small");
+    if (!exact) {
+        if (tid < 32) {
+            TS f2 = (TS)0;
+            if (tid < 3 * CHI) {
+                const int k = tid / CHI, cc = tid % CHI;
+#pragma unroll
+                for (int r = 0; r < CHI; ++r) f2 += norm2(sm.D[k][cc * CHI + r]);
+            }
+#pragma unroll
+            for (int o = 1; o < CHI; o <<= 1) f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+            if (tid < 3 * CHI && tid % CHI == 0) sm.dl[tid / CHI] = nr_sqrt(f2);
+        }
+    } else if (tid < 3 * GJ) {
         const int k = tid / GJ, g = tid % GJ;
         WarpGroup grp{group_mask<GJ>()};
         jacobi_svd<CHI, TS, WarpGroup, false>(sm.D[k], nullptr, g, grp, group_mask<CHI>(),
@@ -735,6 +749,50 @@ __device__ void bp_copy_vertex(const Ctx& c, int a, int tid, int TEAM, int cur) 
         const int u = c.edge_info[es[k]].x;
         const int out = 2 * es[k] + (a == u ? 0 : 1);
         for (int r = tid; r < CC; r += TEAM) dst[(size_t)out * CC + r] = ldcg(src + (size_t)out * CC + r);
+    }
+}
+
+// Exact distance of the sweep that wrote msg[cur_new] for the instances with need[b]
+// set: trace norms of new - old for every directed message, one group of CHI^2/2
+// threads per message (whole block, after a grid barrier).  Accumulates into ex[b].
+template <int CHI, class Mode>
+__device__ void bp_exact_pass(const Ctx& c, int cur_new, const int* need, C<typename Mode::TS>* scratch,
+                              double* bacc, double* ex) {
+    using TS = typename Mode::TS;
+    using CT = C<TS>;
+    constexpr int CC = CHI * CHI, GJ = CC / 2, TPB = Shape<CHI>::TPB, NG = TPB / GJ;
+    const int gi = threadIdx.x / GJ, g = threadIdx.x % GJ;
+    CT* Dm = scratch + gi * CC;
+    const CT* nw = (const CT*)c.msg[cur_new];
+    const CT* od = (const CT*)c.msg[cur_new ^ 1];
+    if (threadIdx.x == 0) *bacc = 0.0;
+    __syncthreads();
+    const WarpGroup grp{group_mask<GJ>()};
+    double mine = 0.0;
+    for (int mi = blockIdx.x * NG + gi; mi < 2 * c.m; mi += c.nblocks * NG) {
+        const int inst = c.vert_inst[c.edge_info[mi >> 1].x];
+        if (!need[inst]) continue;
+        for (int r = g; r < CC; r += GJ) Dm[r] = ldcg(nw + (size_t)mi * CC + r) - ldcg(od + (size_t)mi * CC + r);
+        jacobi_svd<CHI, TS, WarpGroup, false>(Dm, nullptr, g, grp, group_mask<CHI>(),
+                                               Mode::mixed ? (TS)1e-6 : (TS)1e-15, 60, false);
+        if (g == 0) {
+            TS sacc = (TS)0;
+            for (int cc = 0; cc < CHI; ++cc) {
+                TS n2 = (TS)0;
+                for (int r = 0; r < CHI; ++r) n2 += norm2(Dm[cc * CHI + r]);
+                sacc += nr_sqrt(n2);
+            }
+            if (c.B == 1) mine += (double)sacc;
+            else atomicAdd(ex + inst, (double)sacc);
+        }
+        grp.sync();
+    }
+    if (c.B == 1) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        if ((threadIdx.x & 31) == 0 && mine != 0.0) atomicAdd(bacc, mine);
+        __syncthreads();
+        if (threadIdx.x == 0 && *bacc != 0.0) atomicAdd(ex, *bacc);
     }
 }
 
@@ -922,7 +980,9 @@ template <int CHI, class Mode, unsigned PH>
 struct SmemSize {
     static constexpr int TPB = Shape<CHI>::TPB;
     static constexpr size_t gate = sizeof(GateSm<CHI>) * (TPB / Shape<CHI>::TG);
-    static constexpr size_t bp = sizeof(BPSm<CHI, Mode>) * (TPB / Shape<CHI>::TB) + 64 * sizeof(double);
+    // per-team caches, block sums (64 doubles), scratch of the exact-distance pass
+    static constexpr size_t bp = sizeof(BPSm<CHI, Mode>) * (TPB / Shape<CHI>::TB) + 64 * sizeof(double) +
+                                 sizeof(C<typename Mode::TS>) * 2 * TPB;
     static constexpr size_t rg = sizeof(RGSm<CHI>) * (TPB / Shape<CHI>::TR);
     static constexpr size_t rv =
         sizeof(C<typename Mode::TS>) * (4 * CHI * CHI * CHI + 3 * CHI * CHI) * (TPB / Shape<CHI>::TRV);
@@ -988,28 +1048,42 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                     c.inst_done[b] = 0;   // host-visible copy
                     c.inst_iters[b] = 0;
                     c.inst_dist[b] = 0.0;
-                    c.acc[b] = 0.0;
-                    c.acc[c.B + b] = 0.0;
-                    c.acc[2 * c.B + b] = 0.0;
+                    for (int q = 0; q < 6; ++q) c.acc[q * c.B + b] = 0.0;
                 }
                 if (!grid_sync(gb, nb, c.spin_limit)) return;
             }
             const int team = threadIdx.x / S::TB, tid = threadIdx.x % S::TB;
             const int tpb_teams = S::TPB / S::TB;
+            using CT_ = C<typename Mode::TS>;
             BPSm<CHI, Mode>& sm = reinterpret_cast<BPSm<CHI, Mode>*>(smem)[team];
             double* bsum = reinterpret_cast<double*>(smem + sizeof(BPSm<CHI, Mode>) * tpb_teams);
             // every block keeps its own copy of the per-instance state; all blocks take
             // identical decisions from the same accumulators, so one barrier per sweep suffices
+            // (two when a sweep's lower bound falls under the threshold and the exact
+            // distance is computed afterwards)
             int* done = reinterpret_cast<int*>(smem + SmemSize<CHI, Mode, PH>::value);
-            for (int b = threadIdx.x; b < c.B; b += S::TPB) done[b] = 0;
+            int* exnow = done + c.B;   // this sweep computes the exact distance inline
+            int* need = exnow + c.B;   // exact distance needed after the sweep
+            CT_* scratch = reinterpret_cast<CT_*>(bsum + 64);
+            for (int b = threadIdx.x; b < c.B; b += S::TPB) {
+                done[b] = 0;
+                exnow[b] = c.max_iter == 1;
+                need[b] = 0;
+            }
             if (tid == 0) sm.cached = -1;   // T and D0 changed in the init phase
             __syncthreads();
             const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * tpb_teams;
+            const double slack = Mode::mixed ? 1e-5 : 1e-12;   // rounding of the lower bound
             int it = 0;
             for (; it < c.max_iter; ++it) {
                 double* acc = c.acc + (size_t)(it % 3) * c.B;
                 double* acc_next = c.acc + (size_t)((it + 1) % 3) * c.B;
-                for (int b = blockIdx.x * S::TPB + threadIdx.x; b < c.B; b += c.nblocks * S::TPB) acc_next[b] = 0.0;
+                double* ex = c.acc + (size_t)(3 + it % 3) * c.B;
+                double* ex_next = c.acc + (size_t)(3 + (it + 1) % 3) * c.B;
+                for (int b = blockIdx.x * S::TPB + threadIdx.x; b < c.B; b += c.nblocks * S::TPB) {
+                    acc_next[b] = 0.0;
+                    ex_next[b] = 0.0;
+                }
                 double mine = 0.0;
                 for (int a = gteam; a < c.n; a += nt) {
                     const int inst = c.vert_inst[a];
@@ -1017,7 +1091,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                         bp_copy_vertex<CHI, Mode>(c, a, tid, S::TB, cur);
                         continue;
                     }
-                    const double d = bp_vertex<CHI, Mode>(c, a, tid, team, cur, sm);
+                    const double d = bp_vertex<CHI, Mode>(c, a, tid, team, cur, exnow[inst] != 0, sm);
                     if (c.B == 1) mine += d;
                     else if (tid == 0) atomicAdd(acc + inst, d);
                 }
@@ -1033,12 +1107,24 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 cur ^= 1;
                 if (!grid_sync(gb, nb, c.spin_limit)) return;
                 // stopping rule of App. B, per instance, evaluated identically by every block
-                int open_local = 0;
+                const bool last = it + 1 >= c.max_iter;
+                int open_local = 0, need_local = 0;
                 for (int b = threadIdx.x; b < c.B; b += S::TPB) {
                     if (done[b]) continue;
                     const double dsum = __ldcg(acc + b);
                     const int mb = c.inst_m[b];
-                    const bool fin = (mb == 0) || (dsum < c.tol * mb) || (it + 1 >= c.max_iter) || !(dsum == dsum);
+                    bool fin;
+                    if (mb == 0 || !(dsum == dsum)) {
+                        fin = true;
+                    } else if (exnow[b]) {
+                        fin = last || dsum < c.tol * mb;
+                    } else if (!last && dsum * (1.0 - slack) >= c.tol * mb) {
+                        fin = false;   // the exact distance is at least the bound
+                    } else {
+                        need[b] = 1;
+                        need_local = 1;
+                        continue;
+                    }
                     if (blockIdx.x == 0) {
                         c.inst_dist[b] = mb > 0 ? dsum * nr_rcp((double)mb) : 0.0;
                         c.inst_iters[b] = it + 1;
@@ -1046,6 +1132,28 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                     }
                     if (fin) done[b] = 1;
                     else open_local = 1;
+                    // the next sweep is exact inline when it is the last or when this
+                    // sweep came within a factor 3 of the threshold
+                    exnow[b] = (it + 2 >= c.max_iter) || dsum < 3.0 * c.tol * mb;
+                }
+                if (__syncthreads_or(need_local)) {
+                    bp_exact_pass<CHI, Mode>(c, cur, need, scratch, bsum + 32, ex);
+                    if (!grid_sync(gb, nb, c.spin_limit)) return;
+                    for (int b = threadIdx.x; b < c.B; b += S::TPB) {
+                        if (!need[b]) continue;
+                        need[b] = 0;
+                        const double dsum = __ldcg(ex + b);
+                        const int mb = c.inst_m[b];
+                        const bool fin = last || dsum < c.tol * mb || !(dsum == dsum);
+                        if (blockIdx.x == 0) {
+                            c.inst_dist[b] = dsum * nr_rcp((double)mb);
+                            c.inst_iters[b] = it + 1;
+                            if (fin) c.inst_done[b] = 1;
+                        }
+                        if (fin) done[b] = 1;
+                        else open_local = 1;
+                        exnow[b] = 1;
+                    }
                 }
                 if (!__syncthreads_or(open_local)) {
                     ++it;

@@ -444,7 +444,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
             delete s;
             return GTQA_ERR_UNSUPPORTED;
         }
-        s->smem[pk] = (base + (pk == PK_BP ? sizeof(int) * (size_t)B : 0) + 15) / 16 * 16;
+        s->smem[pk] = (base + (pk == PK_BP ? 3 * sizeof(int) * (size_t)B : 0) + 15) / 16 * 16;   // BP: 3 flags per instance
         const cudaError_t pe = phase_prepare(mixed(s), pk, s->CHI, s->smem[pk], &bps);
         if (pe != cudaSuccess || bps < 1) {
             cudaGetLastError();
@@ -495,7 +495,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         (rc = dalloc(s, &s->J, s->m)) || (rc = dalloc(s, &s->h, s->n)) || (rc = dalloc(s, &s->colour_edges, s->m)) ||
         (rc = dalloc(s, &s->colour_off, ncol + 1)) || (rc = dalloc(s, &s->last_colour, s->n)) ||
         (rc = dalloc(s, &s->iso, iso.size())) || (rc = dalloc(s, &s->inst_vbeg, B + 1)) ||
-        (rc = dalloc(s, &s->inst_m, B)) || (rc = dalloc(s, &s->acc, 3 * (size_t)B)) ||
+        (rc = dalloc(s, &s->inst_m, B)) || (rc = dalloc(s, &s->acc, 6 * (size_t)B)) ||
         (rc = dalloc(s, &s->inst_done, B)) || (rc = dalloc(s, &s->inst_iters, B)) ||
         (rc = dalloc(s, &s->inst_dist, B)) || (rc = dalloc(s, &s->stats, 4)) || (rc = dalloc(s, &s->ctl, 1)) ||
         (rc = dalloc(s, &s->rho, (size_t)s->n * 4)) || (rc = dalloc(s, &s->sign, s->n)) ||

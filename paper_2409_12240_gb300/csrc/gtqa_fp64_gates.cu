@@ -13,7 +13,7 @@ cudaError_t launch_t(const Ctx& c, size_t smem, cudaStream_t st) {
 }
 template <int CHI>
 cudaError_t prepare_t(size_t smem, int* bps) {
-    cudaError_t e = cudaFuncSetAttribute(gates_kernel<CHI, ModeFP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(gates_kernel<CHI, ModeFP64>, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, gates_kernel<CHI, ModeFP64>, Shape<CHI>::TPB, smem);
 }

@@ -26,8 +26,8 @@ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t kOffT = 0;                                                            // T [n][2][H] complex128
 constexpr size_t kOffMsg = align256(kOffT + sizeof(cd) * 2 * kH * (size_t)GTQA_STATIC_MAX_N);   // messages [2m][CC]
 constexpr size_t kOffCtl = align256(kOffMsg + sizeof(cd) * kCC * 2 * (size_t)GTQA_STATIC_MAX_M);
-constexpr size_t kOffAcc = align256(kOffCtl + sizeof(Control));                         // acc[3], dist[1]
-constexpr size_t kOffInt = align256(kOffAcc + sizeof(double) * 4);                      // done, iters, vbeg[2], m
+constexpr size_t kOffAcc = align256(kOffCtl + sizeof(Control));                         // acc[6], dist[1]
+constexpr size_t kOffInt = align256(kOffAcc + sizeof(double) * 7);                      // done, iters, vbeg[2], m
 constexpr size_t kOffVinst = align256(kOffInt + sizeof(int) * 8);                       // vert_inst [n] (zeros)
 constexpr size_t kBytes = align256(kOffVinst + sizeof(int) * (size_t)GTQA_STATIC_MAX_N);
 
@@ -52,7 +52,7 @@ int setup(int dev, void** addr, size_t* smem) {
         size_t base = 0;
         int tpb = 0, bps = 0;
         if (!bp_fp64_shape(kChi, &base, &tpb)) return GTQA_ERR_UNSUPPORTED;
-        const size_t sm = (base + sizeof(int) + 15) / 16 * 16;
+        const size_t sm = (base + 3 * sizeof(int) + 15) / 16 * 16;   // 3 flags of the one instance
         if (bp_fp64_prepare(kChi, sm, &bps) != cudaSuccess || bps < 1) {
             cudaGetLastError();
             return GTQA_ERR_CUDA;
@@ -100,7 +100,7 @@ extern "C" int gtqa_bp_static(int32_t n, int32_t m, const int32_t* vert_edges, c
     // array keeps the previous call's contents otherwise.
     const int ints[8] = {0, 0, 0, n, m, 0, 0, 0};   // done, iters, vbeg[0], vbeg[1], m
     if (cudaMemsetAsync(sc + kOffCtl, 0, sizeof(Control), st) != cudaSuccess ||
-        cudaMemsetAsync(sc + kOffAcc, 0, sizeof(double) * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(sc + kOffAcc, 0, sizeof(double) * 7, st) != cudaSuccess ||
         cudaMemcpyAsync(sc + kOffInt, ints, sizeof(ints), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(sc + kOffVinst, 0, sizeof(int) * (size_t)n, st) != cudaSuccess) {
         cudaGetLastError();
@@ -119,7 +119,7 @@ extern "C" int gtqa_bp_static(int32_t n, int32_t m, const int32_t* vert_edges, c
     c.inst_vbeg = reinterpret_cast<const int*>(sc + kOffInt) + 2;
     c.inst_m = reinterpret_cast<const int*>(sc + kOffInt) + 4;
     c.acc = reinterpret_cast<double*>(sc + kOffAcc);
-    c.inst_dist = reinterpret_cast<double*>(sc + kOffAcc) + 3;
+    c.inst_dist = reinterpret_cast<double*>(sc + kOffAcc) + 6;
     c.Gamma = const_cast<double*>(gamma);
     c.lam = const_cast<double*>(lambda);
     c.T = sc + kOffT;
