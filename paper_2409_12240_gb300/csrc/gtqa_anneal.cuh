@@ -241,9 +241,11 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
     // ---- SVD of M ----
     // FP64 mode: one-sided Jacobi in FP64 from V = I.
     // Mixed mode: Jacobi sweeps in FP32 on a copy of M give V32; one FP64 Newton-Schulz
-    // step V <- V (3I - V^H V)/2 makes it unitary to ~1e-14; the FP64 Jacobi then polishes
-    // W = M V (typically one sweep with rotations plus the confirming sweep).  The result
-    // is an FP64 SVD of M with a fraction of the FP64 instructions.
+    // step V <- V (3I - V^H V)/2 makes it unitary to ~1e-14, and W = M V (FP64) has
+    // columns orthogonal to the FP32 tolerance.  The singular values are W's column
+    // norms (exact up to second order in that tolerance, since V is unitary) and the
+    // left vectors W's normalised columns, accurate to about 1e-6 before they are
+    // rounded to complex64 storage.
     int nrot = 0, sweeps;
     auto svd64 = [&](bool init_v, double tol) {
         if constexpr (TEAM <= 32) {
@@ -261,10 +263,10 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
         team_bar<TEAM>(team);
         if constexpr (TEAM <= 32) {
             WarpGroup grp{group_mask<TEAM>()};
-            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true);
+            sweeps = jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true, &nrot);
         } else {
             TeamGroup<TEAM> grp{team, &sm.flag};
-            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true);
+            sweeps = jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true, &nrot);
         }
         team_bar<TEAM>(team);
         for (int t = tid; t < NM * NM; t += TEAM) sm.V[t] = ccast<double>(sm.V32[t]);
@@ -297,8 +299,6 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
             sm.M[t] = sm.G[t];
             sm.V[t] = sm.Vn[t];
         }
-        team_bar<TEAM>(team);
-        sweeps = svd64(false, 1e-13);
     }
     if (nrot) atomicAdd(&sm.nrot, nrot);
     team_bar<TEAM>(team);

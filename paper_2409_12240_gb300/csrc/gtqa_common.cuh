@@ -203,13 +203,16 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
 }
 
 // Rank of value i among n values, descending, ties by index (used to sort
-// singular values without data movement).
+// singular values without data movement).  A NaN ranks below every number, so the
+// ranks are a permutation of 0..n-1 whatever the values.
 template <typename R>
 __device__ __forceinline__ int desc_rank(const R* v, int n, int i) {
-    const R x = v[i];
+    const R x0 = v[i];
+    const R x = (x0 == x0) ? x0 : (R)-INFINITY;
     int rk = 0;
     for (int j = 0; j < n; ++j) {
-        const R y = v[j];
+        const R y0 = v[j];
+        const R y = (y0 == y0) ? y0 : (R)-INFINITY;
         rk += (y > x) || (y == x && j < i);
     }
     return rk;
