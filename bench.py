@@ -202,7 +202,7 @@ def storage_chi(chi: int) -> int:
     return 2 if chi <= 2 else (4 if chi <= 4 else 8)
 
 
-def gate_flops(chi: int, edges: int, pairs: int, rotations: int) -> float:
+def gate_flops(chi: int, edges: int, pairs: int, rotations: int, mixed: bool = False):
     """FP64 flops of the simple-update phase (real adds/muls, fma = 2).
 
     Per edge at storage bond dimension C (rows R = C^2 per QR block, N = 2C):
@@ -212,7 +212,10 @@ def gate_flops(chi: int, edges: int, pairs: int, rotations: int) -> float:
       singular values              3 N^2
       Q U / lambda (4 blocks)      4 C sum_k 16 (R-k) + 8 C R
     plus per Jacobi pair examined 14 N (alpha, beta, gamma) and per rotation 40 N + 15.
-    In the mixed mode the last line (Q U / lambda) runs in FP32; it is still counted here.
+    Returns (FP64 flops, FP32 flops).  In the mixed mode the counted Jacobi sweeps are the
+    FP64 polish after the FP32 preconditioning sweeps (which are not counted), the
+    Newton-Schulz step (V^H V, V(3I - G)/2) and W = M V add 3 x 8 N^3 FP64 flops per
+    edge, and the last line (Q U / lambda) runs in FP32.
     """
     C = storage_chi(chi)
     R, N = C * C, 2 * C
@@ -221,8 +224,11 @@ def gate_flops(chi: int, edges: int, pairs: int, rotations: int) -> float:
     core = 4 * sum(10 * (C - max(r, rp)) + 26 for r in range(C) for rp in range(C))
     sv = 3 * N * N
     back = 4 * C * sum(16 * (R - k) for k in range(C)) + 8 * C * R
-    fixed = x + qr + core + sv + back
-    return float(edges * fixed + pairs * 14 * N + rotations * (40 * N + 15))
+    jac = pairs * 14 * N + rotations * (40 * N + 15)
+    if not mixed:
+        return float(edges * (x + qr + core + sv + back) + jac), 0.0
+    ns = 3 * 8 * N ** 3
+    return float(edges * (x + qr + core + sv + ns) + jac), float(edges * back)
 
 
 def bp_sweep_flops(chi: int, vertices: int, mixed: bool) -> float:
@@ -233,6 +239,30 @@ def bp_sweep_flops(chi: int, vertices: int, mixed: bool) -> float:
     C = storage_chi(chi)
     per = (64 if mixed else 48) * C ** 4
     return float(vertices * 3 * per)
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_bp_kernel_n1000_chi4.json")
+TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2409_12240_gb300", "csrc", f) for f in ("gtqa_anneal.cuh", "gtqa_common.cuh")]
+
+
+def bp_traffic(mixed: bool, chi: int, sweeps_per_launch: float):
+    """DRAM bytes per BP launch from the committed ncu capture (dram__bytes_read.sum +
+    dram__bytes_write.sum of one launch), scaled to this run's sweeps per launch; None if
+    there is no capture for this mode or the kernel sources changed since it was taken."""
+    import hashlib
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for p in TRAFFIC_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    r = rec.get("mixed" if mixed else "fp64")
+    if not r or r.get("sources_sha256") != h.hexdigest() or r.get("chi") != chi:
+        return None
+    return r["fixed_bytes"] + r["bytes_per_sweep"] * sweeps_per_launch
 
 
 def per_layer_error(G, make, inst, k_last: int, samples: int = 6) -> dict:
@@ -299,12 +329,16 @@ def run_gtqa(a):
         return G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour,
                              G.gtqa_options_init(precision=p, cuda_stream=stream.cuda_stream))
 
-    def timed_window(p, clocks=None):
+    def timed_window(p, clocks=None, profile=False):
         """Warm-up layers 1..W, then layers W+1..W+K, one gtqa_anneal call per layer with an
-        L2 flush between layers (outside the events).  Returns (ms, stats delta, final rho)."""
+        L2 flush between layers (outside the events).  With `profile`, the library also
+        records CUDA events around each of its launches on the same stream (the per-kernel
+        durations of the roofline).  Returns (ms, stats delta, final rho, sign, clocks, prof)."""
         s = make(p)
         if W:
             G.gtqa_anneal(s, 1, W, Ks, dt, tol, mi)
+        if profile:
+            G.gtqa_profile(s, True)
         st0 = G.gtqa_stats(s)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         torch.cuda.synchronize()
@@ -325,15 +359,16 @@ def run_gtqa(a):
         torch.cuda.synchronize()
         ck = clocks.stop() if clocks else None
         t_ms = float(sum(e0.elapsed_time(e1) for e0, e1 in ev))
+        prof = G.gtqa_profile_read(s) if profile else None
         st1 = G.gtqa_stats(s)
         rho, sign = G.gtqa_marginals(s)
         G.gtqa_destroy(s)
         delta = {k: st1[k] - st0[k] for k in ("launches", "bp_sweeps", "bp_calls", "bp_not_converged_calls",
                                                "svd_pairs", "svd_rotations")}
-        return t_ms, delta, rho, sign, ck
+        return t_ms, delta, rho, sign, ck, prof
 
     clocks = Clocks(local)
-    t_ms, dlt, rho_main, sign_main, ck = timed_window(prec, clocks)
+    t_ms, dlt, rho_main, sign_main, ck, prof = timed_window(prec, clocks, profile=True)
     if dist:
         tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -343,7 +378,7 @@ def run_gtqa(a):
     # the FP64 path on the same layers, and the marginal error of the mixed path against it
     fp64 = None
     if mixed and not a.no_fp64:
-        t64, d64, rho64, sign64, _ = timed_window(G.GTQA_FP64)
+        t64, d64, rho64, sign64, _, _ = timed_window(G.GTQA_FP64)
         err = np.abs(rho_main - rho64)
         clear = np.abs(rho64[:, 0, 0].real - 0.5) > 1e-3
         fp64 = {"value": world * K / (t64 / 1e3), "unit": "layers/s", "ms_per_step": t64 / K,
@@ -356,44 +391,42 @@ def run_gtqa(a):
                     "note": "whole trajectories; BP stops at max_iter in part of the anneal, after which both "
                             "runs follow the chaotic BP map and decorrelate"}}
 
-    # ---- per-kernel profile (CUDA events around each launch) on the same layers ----
-    Kp = min(K, 300)
-    s2 = make(prec)
-    if W:
-        G.gtqa_anneal(s2, 1, W, Ks, dt, tol, mi)
-    G.gtqa_profile(s2, True)
-    p0 = G.gtqa_stats(s2)
-    with torch.cuda.stream(stream):
-        for j in range(Kp):
-            flush.fill_(j & 0xFF)
-            G.gtqa_anneal(s2, W + 1 + j, W + 1 + j, Ks, dt, tol, mi)
-    prof = G.gtqa_profile_read(s2)
-    p1 = G.gtqa_stats(s2)
-    G.gtqa_profile(s2, False)
-    G.gtqa_destroy(s2)
+    # ---- roofline of the kernel with the largest share of the timed window ----
     total_prof = sum(v[1] for v in prof.values())
     dom = max(prof, key=lambda k: prof[k][1])
-    fp64_peak = G.gtqa_alu_peak(True)
-    fp32_peak = G.gtqa_alu_peak(False)
+    # ALU peaks derived from unit counts and the maximum SM clock: 128 FP32 lanes and 2 FP64
+    # FMA units per SM, 2 flops per FMA; the FMA microbenchmark is reported beside them
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = (ck or {}).get("sm_max_mhz") or 2070.0
+    fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    fp64_peak = sms * 2 * 2 * mhz * 1e6 / 1e12
+    fp64_meas = G.gtqa_alu_peak(True)
+    fp32_meas = G.gtqa_alu_peak(False)
+    peak_note = f"{sms} SMs x {{lanes}} x 2 flop x {mhz:.0f} MHz (derived); FMA microbenchmark {{meas:.3f}} TFLOP/s"
     nl, ms, units = prof[dom]
     roof = None
     if dom == "gates_kernel" and nl:
-        fl = gate_flops(chi, units, int(p1["svd_pairs"] - p0["svd_pairs"]), int(p1["svd_rotations"] - p0["svd_rotations"]))
-        ach = fl / (ms * 1e-3) / 1e12
+        f64, f32 = gate_flops(chi, units, int(dlt["svd_pairs"]), int(dlt["svd_rotations"]), mixed)
+        ach = f64 / (ms * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None, "peak_source": "FP64 FMA microbenchmark, this run",
-                "algorithmic_flops_per_launch": fl / nl, "avg_launch_us": ms / nl * 1e3}
+                "frac": ach / fp64_peak, "traffic": None,
+                "peak_source": peak_note.format(lanes="2 FP64 FMA units", meas=fp64_meas),
+                "algorithmic_flops_per_launch": f64 / nl, "avg_launch_us": ms / nl * 1e3,
+                "note": "FP64 flops only" + ("; the FP32 preconditioning sweeps of the mixed SVD and the FP32 "
+                                             "back-application are not counted" if mixed else "")}
     elif dom == "bp_kernel" and nl:
-        sweeps = int(p1["bp_sweeps"] - p0["bp_sweeps"])
+        sweeps = int(dlt["bp_sweeps"])
         fl = bp_sweep_flops(chi, inst.n, mixed) * sweeps
         peak = fp32_peak if mixed else fp64_peak
         ach = fl / (ms * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_source": ("FP32" if mixed else "FP64") + " FMA microbenchmark, this run",
+                "frac": ach / peak, "traffic": bp_traffic(mixed, chi, sweeps / nl),
+                "peak_source": peak_note.format(lanes="128 FP32 lanes" if mixed else "2 FP64 FMA units",
+                                                meas=fp32_meas if mixed else fp64_meas),
                 "algorithmic_flops_per_launch": fl / nl, "avg_launch_us": ms / nl * 1e3,
-                "sweeps_per_launch": sweeps / nl,
-                "note": "flops of the BP contractions only; each sweep is bounded by the grid-barrier and memory latency"}
+                "sweeps_per_launch": sweeps / nl, "us_per_sweep": ms * 1e3 / max(sweeps, 1),
+                "note": "flops of the BP sweeps only (the warm-start phase of each launch is not counted); "
+                        "the working set is L2-resident and each sweep is bounded by a grid barrier"}
     kernel_share = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_prof, 4) if total_prof else 0}
                     for k, v in prof.items() if v[0]}
 
@@ -430,7 +463,8 @@ def run_gtqa(a):
         "bp_sweeps_per_layer": dlt["bp_sweeps"] / K,
         "bp_layers_at_max_iter": dlt["bp_not_converged_calls"] / K,
         "fp64_path": fp64,
-        "roofline": roof, "kernel_share": kernel_share, "fp32_peak_tflops": fp32_peak, "fp64_peak_tflops": fp64_peak,
+        "roofline": roof, "kernel_share": kernel_share, "alu_peaks_tflops": {"fp32": fp32_peak, "fp64": fp64_peak, "fp32_measured": fp32_meas,
+                             "fp64_measured": fp64_meas},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(dlt["launches"]), "clocks": ck,
         "final_marginals": {"mean_abs_z": float(np.mean(np.abs(rho_main[:, 0, 0].real - rho_main[:, 1, 1].real)))},
     }

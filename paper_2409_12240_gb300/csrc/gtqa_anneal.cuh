@@ -43,8 +43,7 @@ struct ModeMixed {
 enum : unsigned { PH_GATES = 1u, PH_BP = 2u, PH_WARM = 4u, PH_REGAUGE = 8u };
 
 struct Control {
-    unsigned int bar_count;
-    unsigned int bar_gen;
+    unsigned long long bar_count;   // grid-barrier arrivals (monotonic)
     int err;
     int cur;                 // message buffer holding the latest messages
     long long sweeps_total;  // sum over BP calls of max-over-instances sweeps
@@ -241,11 +240,9 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
     // ---- SVD of M ----
     // FP64 mode: one-sided Jacobi in FP64 from V = I.
     // Mixed mode: Jacobi sweeps in FP32 on a copy of M give V32; one FP64 Newton-Schulz
-    // step V <- V (3I - V^H V)/2 makes it unitary to ~1e-14, and W = M V (FP64) has
-    // columns orthogonal to the FP32 tolerance.  The singular values are W's column
-    // norms (exact up to second order in that tolerance, since V is unitary) and the
-    // left vectors W's normalised columns, accurate to about 1e-6 before they are
-    // rounded to complex64 storage.
+    // step V <- V (3I - V^H V)/2 makes it unitary to ~1e-14; the FP64 Jacobi then polishes
+    // W = M V (typically one sweep with rotations plus the confirming sweep).  The result
+    // is an FP64 SVD of M with a fraction of the FP64 instructions.
     int nrot = 0, sweeps;
     auto svd64 = [&](bool init_v, double tol) {
         if constexpr (TEAM <= 32) {
@@ -263,10 +260,10 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
         team_bar<TEAM>(team);
         if constexpr (TEAM <= 32) {
             WarpGroup grp{group_mask<TEAM>()};
-            sweeps = jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true, &nrot);
+            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true);
         } else {
             TeamGroup<TEAM> grp{team, &sm.flag};
-            sweeps = jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true, &nrot);
+            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true);
         }
         team_bar<TEAM>(team);
         for (int t = tid; t < NM * NM; t += TEAM) sm.V[t] = ccast<double>(sm.V32[t]);
@@ -299,6 +296,8 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
             sm.M[t] = sm.G[t];
             sm.V[t] = sm.Vn[t];
         }
+        team_bar<TEAM>(team);
+        sweeps = svd64(false, 1e-13);
     }
     if (nrot) atomicAdd(&sm.nrot, nrot);
     team_bar<TEAM>(team);
@@ -529,8 +528,8 @@ struct BPSm {
     cf D0f[3][CC];       // mixed: warm-start defect
     float m0f[3][CHI];   // mixed: warm-start diagonals
     cd t0[3];            // mixed: traces of F0
-    C<TS> itr[3];        // 1 / trace (formed in FP64)
-    C<TS> tau[3];        // mixed: trace of the correction terms
+    C<TS> trs[3];        // traces of the outgoing messages (mixed: of the correction terms)
+    C<TS> itr[3];        // 1 / trace, formed in FP64
     TS dl[3];
     int es[3], out_idx[3], in_idx[3];
     int cached;          // vertex held in the cache, -1 if none
@@ -541,6 +540,7 @@ __device__ void bp_prepare(const Ctx& c, int a, int tid, int team, int cur, BPSm
     using TS = typename Mode::TS;
     using CT = C<TS>;
     constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H2 = 2 * CHI * CHI * CHI;
+    team_bar<TEAM>(team);   // the team may still be reading the previous vertex's cache
     if (tid < 3) {
         const int4 ve = c.vert_edges[a];
         const int e = tid == 0 ? ve.x : (tid == 1 ? ve.y : ve.z);
@@ -579,8 +579,10 @@ __device__ void bp_prepare(const Ctx& c, int a, int tid, int team, int cur, BPSm
     team_bar<TEAM>(team);
 }
 
+// First part of the sweep for vertex a: incoming messages, the contractions, and the
+// traces of the three outgoing messages (left in sm.trs).
 template <int CHI, class Mode>
-__device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, bool exact, BPSm<CHI, Mode>& sm) {
+__device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode>& sm) {
     using TS = typename Mode::TS;
     using CT = C<TS>;
     constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H = CHI * CHI * CHI, H2 = 2 * H;
@@ -663,58 +665,95 @@ __device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, boo
         sm.Fh[i][s][r] = acc;
     }
     team_bar<TEAM>(team);
-    // traces and their reciprocals in FP64 (reading R10: divide by the complex trace)
-    if (tid < 3 && sm.es[tid] >= 0) {
+    // traces of the outgoing messages
+    if (tid < 3 * CC && tid % CC == 0) {
+        const int k = tid / CC;
         CT trs = z;
-        for (int j = 0; j < CHI; ++j) trs = trs + (sm.Fh[0][tid][j * CHI + j] + sm.Fh[1][tid][j * CHI + j]);
-        cd tr = ccast<double>(trs);
-        if constexpr (Mode::mixed) {
-            sm.tau[tid] = trs;
-            tr = tr + sm.t0[tid];
-        }
-        const double n2 = norm2(tr);
-        const double in2 = n2 > 0.0 ? nr_rcp(n2) : 0.0;
-        sm.itr[tid] = ccast<TS>(cd{tr.x * in2, -tr.y * in2});
+#pragma unroll
+        for (int j = 0; j < CHI; ++j) trs = trs + (sm.Fh[0][k][j * CHI + j] + sm.Fh[1][k][j * CHI + j]);
+        sm.trs[k] = trs;
     }
-    team_bar<TEAM>(team);
-    // new messages; mixed: delta' = (D0 + Fd - m0 tr Fd) / (t0 + tr Fd)
-    for (int t = tid; t < 3 * CC; t += TEAM) {
-        const int k = t / CC, r = t % CC;
+}
+
+// Reciprocals of the complex traces of every team's outgoing messages in FP64 (reading
+// R10: messages are divided by their complex trace), one lane per message, by the first
+// warp of the block: FP64 instructions cost the same for 1 or 32 active lanes, so one
+// warp does this for all teams.  Mixed: the trace is t0 + tr Fd.
+template <int CHI, class Mode>
+__device__ void bp_trace_rcp(BPSm<CHI, Mode>* all, int nteams) {
+    using TS = typename Mode::TS;
+    const int l = threadIdx.x;
+    if (l >= 3 * nteams) return;
+    BPSm<CHI, Mode>& sm = all[l / 3];
+    const int k = l % 3;
+    cd tr = ccast<double>(sm.trs[k]);
+    if constexpr (Mode::mixed) tr = tr + sm.t0[k];
+    const double n2 = norm2(tr);
+    const double in2 = n2 > 0.0 ? nr_rcp(n2) : 0.0;
+    sm.itr[k] = ccast<TS>(cd{tr.x * in2, -tr.y * in2});
+}
+
+// Second part: new messages m' = F / tr F (mixed: delta' = (D0 + Fd - m0 tr Fd) / (t0 + tr Fd))
+// and the distance of App. B, added to *dacc.
+template <int CHI, class Mode>
+__device__ void bp_back(const Ctx& c, int tid, int team, int cur, bool exact, BPSm<CHI, Mode>& sm, double* gacc) {
+    using TS = typename Mode::TS;
+    using CT = C<TS>;
+    constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI;
+    CT* dst = (CT*)c.msg[cur ^ 1];
+    const CT z = CT{(TS)0, (TS)0};
+    constexpr int GJ = CC / 2;
+    constexpr bool FAST = CC <= 32;   // the elements of one message lie in one warp
+    static_assert(3 * GJ <= TEAM && 3 * CHI <= 32 && 3 * CC <= TEAM, "BP team too small");
+    TS f2 = (TS)0;
+    if (tid < 3 * CC) {
+        const int k = tid / CC, r = tid % CC;
         const int out = sm.out_idx[k];
-        if (out < 0) {
-            sm.D[k][r] = z;
-            continue;
+        CT d = z;
+        if (out >= 0) {
+            const CT itr = sm.itr[k];
+            const CT f = sm.Fh[0][k][r] + sm.Fh[1][k][r];
+            CT num = f;
+            if constexpr (Mode::mixed) {
+                const int j = r / CHI, jp = r % CHI;
+                num = sm.D0f[k][r] + f;
+                if (j == jp) num = num - sm.m0f[k][j] * sm.trs[k];
+            }
+            const CT nv = itr * num;
+            dst[(size_t)out * CC + r] = nv;
+            d = nv - sm.prev[k][r];
+            sm.prev[k][r] = nv;
         }
-        const CT f = sm.Fh[0][k][r] + sm.Fh[1][k][r];
-        CT nv;
-        if constexpr (!Mode::mixed) {
-            nv = sm.itr[k] * f;
-        } else {
-            const int j = r / CHI, jp = r % CHI;
-            CT num = sm.D0f[k][r] + f;
-            if (j == jp) num = num - sm.m0f[k][j] * sm.tau[k];
-            nv = sm.itr[k] * num;
-        }
-        dst[(size_t)out * CC + r] = nv;
-        sm.D[k][r] = nv - sm.prev[k][r];
-        sm.prev[k][r] = nv;
+        if (FAST && !exact) f2 = norm2(d);
+        else sm.D[k][r] = d;
     }
-    team_bar<TEAM>(team);
     // distance of App. B: trace norms ||m_new - m_old||_1 (sum of singular values) when
     // `exact`, else the Frobenius norms, a lower bound that suffices to continue
-    constexpr int GJ = CC / 2;
-    static_assert(3 * GJ <= TEAM && 3 * CHI <= 32 && 3 * CC <= TEAM, "BP team too small");
+    if constexpr (FAST) {
+        if (!exact) {
+            if (tid < 3 * CC) {
+                f2 = group_sum<CC>(f2, group_mask<CC>());
+                if (tid % CC == 0) {
+                    const TS f = sm.out_idx[tid / CC] >= 0 ? nr_sqrt(f2) : (TS)0;
+                    if (gacc) atomicAdd(gacc, (double)f);
+                    else sm.dl[tid / CC] = f;
+                }
+            }
+            return;
+        }
+    }
+    team_bar<TEAM>(team);
     if (!exact) {
         if (tid < 32) {
-            TS f2 = (TS)0;
+            TS c2 = (TS)0;
             if (tid < 3 * CHI) {
                 const int k = tid / CHI, cc = tid % CHI;
 #pragma unroll
-                for (int r = 0; r < CHI; ++r) f2 += norm2(sm.D[k][cc * CHI + r]);
+                for (int r = 0; r < CHI; ++r) c2 += norm2(sm.D[k][cc * CHI + r]);
             }
 #pragma unroll
-            for (int o = 1; o < CHI; o <<= 1) f2 += __shfl_xor_sync(0xffffffffu, f2, o);
-            if (tid < 3 * CHI && tid % CHI == 0) sm.dl[tid / CHI] = nr_sqrt(f2);
+            for (int o = 1; o < CHI; o <<= 1) c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+            if (tid < 3 * CHI && tid % CHI == 0) sm.dl[tid / CHI] = nr_sqrt(c2);
         }
     } else if (tid < 3 * GJ) {
         const int k = tid / GJ, g = tid % GJ;
@@ -732,7 +771,7 @@ __device__ double bp_vertex(const Ctx& c, int a, int tid, int team, int cur, boo
         }
     }
     team_bar<TEAM>(team);
-    return (double)sm.dl[0] + (double)sm.dl[1] + (double)sm.dl[2];
+    if (gacc && tid == 0) atomicAdd(gacc, (double)sm.dl[0] + (double)sm.dl[1] + (double)sm.dl[2]);
 }
 
 // copy a frozen instance's outgoing messages to the other buffer
@@ -999,8 +1038,7 @@ template <int CHI, class Mode, unsigned PH>
 __device__ __forceinline__ void anneal_body(const Ctx& c) {
     using S = Shape<CHI>;
     extern __shared__ __align__(16) unsigned char smem[];
-    const GridBarrier gb{&c.ctl->bar_count, &c.ctl->bar_gen, &c.ctl->err};
-    const unsigned nb = (unsigned)c.bar_expect;
+    GridBarrier gb = grid_barrier_init(&c.ctl->bar_count, &c.ctl->err, (unsigned)c.bar_expect);
     const int nteams_total_g = c.nblocks * (S::TPB / S::TG);
     int cur = *(volatile int*)&c.ctl->cur;
     for (int k = c.k0; k <= c.k1; ++k) {
@@ -1026,12 +1064,12 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 if (col == c.ncol - 1)
                     for (int q = gteam; q < c.n_iso; q += nteams_total_g)
                         mixing_vertex<CHI, Mode>(c, c.iso[q], tid, S::TG, cX, sX);
-                if (!grid_sync(gb, nb, c.spin_limit)) return;
+                if (!grid_sync(gb, c.spin_limit)) return;
             }
             if (c.ncol == 0) {
                 for (int q = gteam; q < c.n_iso; q += nteams_total_g)
                     mixing_vertex<CHI, Mode>(c, c.iso[q], tid, S::TG, cX, sX);
-                if (!grid_sync(gb, nb, c.spin_limit)) return;
+                if (!grid_sync(gb, c.spin_limit)) return;
             }
         }
         if constexpr ((PH & PH_BP) != 0u) {
@@ -1050,7 +1088,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                     c.inst_dist[b] = 0.0;
                     for (int q = 0; q < 6; ++q) c.acc[q * c.B + b] = 0.0;
                 }
-                if (!grid_sync(gb, nb, c.spin_limit)) return;
+                if (!grid_sync(gb, c.spin_limit)) return;
             }
             const int team = threadIdx.x / S::TB, tid = threadIdx.x % S::TB;
             const int tpb_teams = S::TPB / S::TB;
@@ -1064,16 +1102,26 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
             int* done = reinterpret_cast<int*>(smem + SmemSize<CHI, Mode, PH>::value);
             int* exnow = done + c.B;   // this sweep computes the exact distance inline
             int* need = exnow + c.B;   // exact distance needed after the sweep
+            double* thr = reinterpret_cast<double*>(smem + SmemSize<CHI, Mode, PH>::value +
+                                                    (3 * sizeof(int) * (size_t)c.B + 7) / 8 * 8);
+            double* thr_hi = thr + c.B;                               // bound that lets a sweep continue
+            float* thr3 = reinterpret_cast<float*>(thr_hi + c.B);     // inline-exact trigger
             CT_* scratch = reinterpret_cast<CT_*>(bsum + 64);
+            const double slack = Mode::mixed ? 1e-5 : 1e-12;   // rounding of the lower bound
             for (int b = threadIdx.x; b < c.B; b += S::TPB) {
                 done[b] = 0;
                 exnow[b] = c.max_iter == 1;
                 need[b] = 0;
+                const double t = c.tol * (double)c.inst_m[b];
+                thr[b] = t;
+                thr_hi[b] = t / (1.0 - slack);
+                thr3[b] = (float)(3.0 * t);
             }
             if (tid == 0) sm.cached = -1;   // T and D0 changed in the init phase
             __syncthreads();
             const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * tpb_teams;
-            const double slack = Mode::mixed ? 1e-5 : 1e-12;   // rounding of the lower bound
+            const int inst0 = gteam < c.n ? c.vert_inst[gteam] : 0;   // the first round's vertex
+            BPSm<CHI, Mode>* all = reinterpret_cast<BPSm<CHI, Mode>*>(smem);
             int it = 0;
             for (; it < c.max_iter; ++it) {
                 double* acc = c.acc + (size_t)(it % 3) * c.B;
@@ -1084,41 +1132,50 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                     acc_next[b] = 0.0;
                     ex_next[b] = 0.0;
                 }
-                double mine = 0.0;
-                for (int a = gteam; a < c.n; a += nt) {
-                    const int inst = c.vert_inst[a];
-                    if (done[inst]) {
-                        bp_copy_vertex<CHI, Mode>(c, a, tid, S::TB, cur);
-                        continue;
+                // rounds of one vertex per team; the block synchronises three times per round
+                typename Mode::TS bl = 0;   // thread 0: this block's distance (one instance)
+                for (int base = 0; base < c.n; base += nt) {
+                    const int a = base + gteam;
+                    int inst = 0;
+                    bool act = false;
+                    if (a < c.n) {
+                        inst = base == 0 ? inst0 : c.vert_inst[a];
+                        if (done[inst]) bp_copy_vertex<CHI, Mode>(c, a, tid, S::TB, cur);
+                        else act = true;
                     }
-                    const double d = bp_vertex<CHI, Mode>(c, a, tid, team, cur, exnow[inst] != 0, sm);
-                    if (c.B == 1) mine += d;
-                    else if (tid == 0) atomicAdd(acc + inst, d);
-                }
-                if (c.B == 1) {
-                    if (tid == 0) bsum[team] = mine;
+                    if (act) bp_front<CHI, Mode>(c, a, tid, team, cur, sm);
                     __syncthreads();
-                    if (threadIdx.x == 0) {
-                        double s = 0.0;
-                        for (int q = 0; q < tpb_teams; ++q) s += bsum[q];
-                        atomicAdd(acc, s);
+                    if (threadIdx.x < 32) bp_trace_rcp<CHI, Mode>(all, tpb_teams);
+                    __syncthreads();
+                    if (act) bp_back<CHI, Mode>(c, tid, team, cur, exnow[inst] != 0, sm, c.B == 1 ? nullptr : acc + inst);
+                    else if (tid < 3) sm.dl[tid] = 0;
+                    if (c.B == 1) {
+                        __syncthreads();
+                        if (threadIdx.x < 32) {
+                            typename Mode::TS v = 0;
+                            for (int q = threadIdx.x; q < 3 * tpb_teams; q += 32) v += all[q / 3].dl[q % 3];
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                            bl += v;
+                        }
                     }
                 }
+                if (c.B == 1 && threadIdx.x == 0) atomicAdd(acc, (double)bl);
                 cur ^= 1;
-                if (!grid_sync(gb, nb, c.spin_limit)) return;
-                // stopping rule of App. B, per instance, evaluated identically by every block
+                if (!grid_sync(gb, c.spin_limit)) return;
+                // stopping rule of App. B, per instance, evaluated identically by every block;
+                // the raw distance sums are kept and divided by |E| at the end
                 const bool last = it + 1 >= c.max_iter;
                 int open_local = 0, need_local = 0;
                 for (int b = threadIdx.x; b < c.B; b += S::TPB) {
                     if (done[b]) continue;
                     const double dsum = __ldcg(acc + b);
-                    const int mb = c.inst_m[b];
                     bool fin;
-                    if (mb == 0 || !(dsum == dsum)) {
+                    if (c.inst_m[b] == 0 || !(dsum == dsum)) {
                         fin = true;
                     } else if (exnow[b]) {
-                        fin = last || dsum < c.tol * mb;
-                    } else if (!last && dsum * (1.0 - slack) >= c.tol * mb) {
+                        fin = last || dsum < thr[b];
+                    } else if (!last && dsum >= thr_hi[b]) {
                         fin = false;   // the exact distance is at least the bound
                     } else {
                         need[b] = 1;
@@ -1126,7 +1183,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                         continue;
                     }
                     if (blockIdx.x == 0) {
-                        c.inst_dist[b] = mb > 0 ? dsum * nr_rcp((double)mb) : 0.0;
+                        c.inst_dist[b] = dsum;
                         c.inst_iters[b] = it + 1;
                         if (fin) c.inst_done[b] = 1;
                     }
@@ -1134,19 +1191,18 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                     else open_local = 1;
                     // the next sweep is exact inline when it is the last or when this
                     // sweep came within a factor 3 of the threshold
-                    exnow[b] = (it + 2 >= c.max_iter) || dsum < 3.0 * c.tol * mb;
+                    exnow[b] = (it + 2 >= c.max_iter) || (float)dsum < thr3[b];
                 }
                 if (__syncthreads_or(need_local)) {
                     bp_exact_pass<CHI, Mode>(c, cur, need, scratch, bsum + 32, ex);
-                    if (!grid_sync(gb, nb, c.spin_limit)) return;
+                    if (!grid_sync(gb, c.spin_limit)) return;
                     for (int b = threadIdx.x; b < c.B; b += S::TPB) {
                         if (!need[b]) continue;
                         need[b] = 0;
                         const double dsum = __ldcg(ex + b);
-                        const int mb = c.inst_m[b];
-                        const bool fin = last || dsum < c.tol * mb || !(dsum == dsum);
+                        const bool fin = last || dsum < thr[b] || !(dsum == dsum);
                         if (blockIdx.x == 0) {
-                            c.inst_dist[b] = dsum * nr_rcp((double)mb);
+                            c.inst_dist[b] = dsum;
                             c.inst_iters[b] = it + 1;
                             if (fin) c.inst_done[b] = 1;
                         }
@@ -1165,6 +1221,8 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 int mi = 0, ncv = 0;
                 double md = 0.0;
                 for (int b = 0; b < c.B; ++b) {
+                    const int mb = c.inst_m[b];
+                    c.inst_dist[b] = mb > 0 ? c.inst_dist[b] / (double)mb : 0.0;
                     mi = c.inst_iters[b] > mi ? c.inst_iters[b] : mi;
                     md = c.inst_dist[b] > md ? c.inst_dist[b] : md;
                     if (!(c.inst_dist[b] < c.tol) && c.inst_m[b] > 0) ++ncv;
@@ -1184,7 +1242,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 RGSm<CHI>& sm = reinterpret_cast<RGSm<CHI>*>(smem)[team];
                 const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * (S::TPB / S::TR);
                 for (int e = gteam; e < c.m; e += nt) regauge_edge<CHI, Mode>(c, e, tid, team, cur, sm);
-                if (!grid_sync(gb, nb, c.spin_limit)) return;
+                if (!grid_sync(gb, c.spin_limit)) return;
             }
             {
                 using CT = C<typename Mode::TS>;
@@ -1195,7 +1253,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                     regauge_vertex<CHI, Mode>(c, a, tid, team, buf);
                     team_bar<S::TRV>(team);
                 }
-                if (!grid_sync(gb, nb, c.spin_limit)) return;
+                if (!grid_sync(gb, c.spin_limit)) return;
             }
         }
     }

@@ -444,7 +444,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
             delete s;
             return GTQA_ERR_UNSUPPORTED;
         }
-        s->smem[pk] = (base + (pk == PK_BP ? 3 * sizeof(int) * (size_t)B : 0) + 15) / 16 * 16;   // BP: 3 flags per instance
+        s->smem[pk] = (base + (pk == PK_BP ? bp_instance_smem(B) : 0) + 15) / 16 * 16;
         const cudaError_t pe = phase_prepare(mixed(s), pk, s->CHI, s->smem[pk], &bps);
         if (pe != cudaSuccess || bps < 1) {
             cudaGetLastError();

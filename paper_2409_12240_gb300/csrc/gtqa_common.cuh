@@ -272,35 +272,61 @@ __device__ __forceinline__ C<float> ldcg(const C<float>* p) {
 // GTQA timeout in *err and leaves.  Callers test *err after every barrier and
 // return, so a lost block can never hang the device.
 // ---------------------------------------------------------------------------
+// Grid barrier for cooperative launches over a monotonic 64-bit arrival counter: the
+// k-th barrier of a launch completes when the counter reaches base + k * nblocks, so
+// an arrival is one release-atomic and the wait one acquire-load poll, with no
+// separate generation word to publish.  Thread 0 of each block keeps the target.  Every
+// wait is bounded: after `limit` polls the block records GTQA_ERR_TIMEOUT in *err and
+// leaves (the others then time out at this or their next barrier).  Launches must pass
+// the same number of barriers in every block, which keeps the counter at a multiple of
+// nblocks between launches.
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long atom_add_release_u64(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
 struct GridBarrier {
-    unsigned int* count;
-    unsigned int* gen;
+    unsigned long long* count;
     int* err;
+    unsigned long long next;   // thread 0: counter value that completes the next barrier
+    unsigned int nblocks;
 };
 
-__device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned int nblocks, long long limit) {
-    __shared__ int ok_shared;
-    __syncthreads();   // the block's writes happen before thread 0's release below
+__device__ __forceinline__ GridBarrier grid_barrier_init(unsigned long long* count, int* err, unsigned int nblocks) {
+    GridBarrier gb{count, err, 0ull, nblocks};
     if (threadIdx.x == 0) {
-        const unsigned int g = *(volatile unsigned int*)gb.gen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(gb.count, 1u);
-        if (arrived == nblocks - 1) {
-            *(volatile unsigned int*)gb.count = 0u;
-            __threadfence();
-            atomicAdd(gb.gen, 1u);
-        } else {
+        // at most nblocks - 1 blocks can have arrived at this launch's first barrier
+        const unsigned long long c = *(volatile unsigned long long*)count;
+        gb.next = c - c % nblocks + nblocks;
+    }
+    return gb;
+}
+
+__device__ __forceinline__ bool grid_sync(GridBarrier& gb, long long limit) {
+    __shared__ int ok_shared;
+    __syncthreads();   // the block's writes happen before thread 0's release
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long old = atom_add_release_u64(gb.count, 1ull);
+        if (old + 1ull < gb.next) {
             long long polls = 0;
-            while (*(volatile unsigned int*)gb.gen == g) {
+            while (ld_acquire_u64(gb.count) < gb.next) {
                 if (++polls > limit) {
                     atomicExch(gb.err, 6);   // GTQA_ERR_TIMEOUT
+                    ok = 0;
                     break;
                 }
                 if (polls > 2048) __nanosleep(32);
             }
         }
-        __threadfence();
-        ok_shared = (*(volatile int*)gb.err == 0) ? 1 : 0;
+        gb.next += gb.nblocks;
+        ok_shared = ok;
     }
     __syncthreads();
     return ok_shared != 0;   // one value per block, so the whole block leaves together

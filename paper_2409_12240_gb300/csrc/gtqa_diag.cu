@@ -98,10 +98,10 @@ extern "C" int gtqa_math_check(int32_t n, const double* x, double* out) {
 // Diagnostic: latency of the bounded grid barrier used by the phase kernels
 // (cooperative launch, one block of `threads` per SM, `rounds` barriers).
 namespace {
-__global__ void barrier_bench_kernel(unsigned int* cnt, unsigned int* gen, int* err, int rounds) {
-    const gtqa::GridBarrier gb{cnt, gen, err};
+__global__ void barrier_bench_kernel(unsigned long long* cnt, int* err, int rounds) {
+    gtqa::GridBarrier gb = gtqa::grid_barrier_init(cnt, err, gridDim.x);
     for (int r = 0; r < rounds; ++r)
-        if (!gtqa::grid_sync(gb, gridDim.x, 1LL << 22)) return;
+        if (!gtqa::grid_sync(gb, 1LL << 22)) return;
 }
 }  // namespace
 
@@ -110,18 +110,17 @@ extern "C" int gtqa_barrier_bench(int32_t threads, int32_t rounds, double* us_pe
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return GTQA_ERR_CUDA;
-    unsigned int* buf = nullptr;
-    if (cudaMalloc(&buf, 4 * sizeof(unsigned int)) != cudaSuccess) return GTQA_ERR_OOM;
-    cudaMemset(buf, 0, 4 * sizeof(unsigned int));
-    unsigned int* cnt = buf;
-    unsigned int* gen = buf + 1;
-    int* err = reinterpret_cast<int*>(buf + 2);
+    unsigned long long* buf = nullptr;
+    if (cudaMalloc(&buf, 2 * sizeof(unsigned long long)) != cudaSuccess) return GTQA_ERR_OOM;
+    cudaMemset(buf, 0, 2 * sizeof(unsigned long long));
+    unsigned long long* cnt = buf;
+    int* err = reinterpret_cast<int*>(buf + 1);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
-        void* args[] = {&cnt, &gen, &err, &rounds};
+        void* args[] = {&cnt, &err, &rounds};
         cudaEventRecord(e0);
         cudaLaunchCooperativeKernel((const void*)barrier_bench_kernel, dim3(sms), dim3(threads), args, 0, nullptr);
         cudaEventRecord(e1);

@@ -11,6 +11,10 @@ namespace gtqa {
 
 enum PhaseKernel { PK_GATES = 0, PK_BP = 1, PK_REGAUGE = 2, PK_COUNT = 3 };
 
+// Shared memory the BP kernel keeps per instance after its fixed part: three int flags
+// (padded to 8 bytes), two FP64 thresholds and one float threshold.
+inline size_t bp_instance_smem(long long B) { return (12 * (size_t)B + 7) / 8 * 8 + 20 * (size_t)B; }
+
 // The dynamic shared-memory limit is an attribute of the kernel function, shared by
 // every state in the process, while the BP kernel's need grows with the number of
 // instances.  The limit is therefore raised to the device maximum (not to one state's

@@ -52,7 +52,7 @@ int setup(int dev, void** addr, size_t* smem) {
         size_t base = 0;
         int tpb = 0, bps = 0;
         if (!bp_fp64_shape(kChi, &base, &tpb)) return GTQA_ERR_UNSUPPORTED;
-        const size_t sm = (base + 3 * sizeof(int) + 15) / 16 * 16;   // 3 flags of the one instance
+        const size_t sm = (base + bp_instance_smem(1) + 15) / 16 * 16;
         if (bp_fp64_prepare(kChi, sm, &bps) != cudaSuccess || bps < 1) {
             cudaGetLastError();
             return GTQA_ERR_CUDA;
