@@ -17,7 +17,7 @@ Every step follows the paper's notation and order:
 * local-orthogonality residual R .............. App. C
 * reduced density matrices and read-out ....... Eq. (partial_dens), Eq. (bp_approx), Eq. (rounding_rule)
 * Trotterised annealing schedule .............. App. F, Eq. (discretizatoion)
-* per-gate fidelity estimate .................. Sec. III E, Eq. (gate_fidelity)
+* per-gate fidelity estimate .................. Sec. III D, Eq. (gate_fidelity)
 
 Readings taken where the paper is silent or ambiguous (each one is listed in the
 design notes of the repository):
