@@ -241,29 +241,33 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
     // FP64 mode: one-sided Jacobi in FP64 from V = I.
     // Mixed mode: Jacobi sweeps in FP32 on a copy of M give V32; one FP64 Newton-Schulz
     // step V <- V (3I - V^H V)/2 makes it unitary to ~1e-14; the FP64 Jacobi then polishes
-    // W = M V (typically one sweep with rotations plus the confirming sweep).  The result
-    // is an FP64 SVD of M with a fraction of the FP64 instructions.
+    // W = M V (typically two sweeps; the confirming sweep is skipped by the quadratic
+    // stop).  The result is an FP64 SVD of M with a fraction of the FP64 instructions.
     int nrot = 0, sweeps;
-    auto svd64 = [&](bool init_v, double tol) {
+    // FP32 rotation angles with FP64-exact rotations; the confirming sweep is skipped
+    // once a sweep's rotations are all below sqrt(tol) (quadratic convergence)
+    auto svd64 = [&](bool init_v, double tol, double quad) {
         if constexpr (TEAM <= 32) {
             WarpGroup grp{group_mask<TEAM>()};
-            return jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), tol, 60, init_v, &nrot);
+            return jacobi_svd<NM, double, WarpGroup, true, true>(sm.M, sm.V, tid, grp, group_mask<NM>(), tol, 60,
+                                                                 init_v, &nrot, quad);
         } else {
             TeamGroup<TEAM> grp{team, &sm.flag};
-            return jacobi_svd<NM, double>(sm.M, sm.V, tid, grp, group_mask<NM>(), tol, 60, init_v, &nrot);
+            return jacobi_svd<NM, double, TeamGroup<TEAM>, true, true>(sm.M, sm.V, tid, grp, group_mask<NM>(), tol,
+                                                                       60, init_v, &nrot, quad);
         }
     };
     if constexpr (!Mode::mixed) {
-        sweeps = svd64(true, 1e-15);
+        sweeps = svd64(true, 1e-15, 3e-8);
     } else {
         for (int t = tid; t < NM * NM; t += TEAM) sm.M32[t] = ccast<float>(sm.M[t]);
         team_bar<TEAM>(team);
         if constexpr (TEAM <= 32) {
             WarpGroup grp{group_mask<TEAM>()};
-            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true);
+            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true, nullptr, 1e-3f);
         } else {
             TeamGroup<TEAM> grp{team, &sm.flag};
-            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true);
+            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true, nullptr, 1e-3f);
         }
         team_bar<TEAM>(team);
         for (int t = tid; t < NM * NM; t += TEAM) sm.V[t] = ccast<double>(sm.V32[t]);
@@ -297,7 +301,7 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
             sm.V[t] = sm.Vn[t];
         }
         team_bar<TEAM>(team);
-        sweeps = svd64(false, 1e-13);
+        sweeps = svd64(false, 1e-13, 3e-7);
     }
     if (nrot) atomicAdd(&sm.nrot, nrot);
     team_bar<TEAM>(team);
@@ -758,8 +762,9 @@ __device__ void bp_back(const Ctx& c, int tid, int team, int cur, bool exact, BP
     } else if (tid < 3 * GJ) {
         const int k = tid / GJ, g = tid % GJ;
         WarpGroup grp{group_mask<GJ>()};
-        jacobi_svd<CHI, TS, WarpGroup, false>(sm.D[k], nullptr, g, grp, group_mask<CHI>(),
-                                               Mode::mixed ? (TS)1e-6 : (TS)1e-15, 60, false);
+        jacobi_svd<CHI, TS, WarpGroup, false, !Mode::mixed>(sm.D[k], nullptr, g, grp, group_mask<CHI>(),
+                                                             Mode::mixed ? (TS)1e-6 : (TS)1e-15, 60, false, nullptr,
+                                                             Mode::mixed ? (TS)1e-3 : (TS)3e-8);
         if (g == 0) {
             TS sacc = (TS)0;
             for (int cc = 0; cc < CHI; ++cc) {
@@ -812,8 +817,9 @@ __device__ void bp_exact_pass(const Ctx& c, int cur_new, const int* need, C<type
         const int inst = c.vert_inst[c.edge_info[mi >> 1].x];
         if (!need[inst]) continue;
         for (int r = g; r < CC; r += GJ) Dm[r] = ldcg(nw + (size_t)mi * CC + r) - ldcg(od + (size_t)mi * CC + r);
-        jacobi_svd<CHI, TS, WarpGroup, false>(Dm, nullptr, g, grp, group_mask<CHI>(),
-                                               Mode::mixed ? (TS)1e-6 : (TS)1e-15, 60, false);
+        jacobi_svd<CHI, TS, WarpGroup, false, !Mode::mixed>(Dm, nullptr, g, grp, group_mask<CHI>(),
+                                                             Mode::mixed ? (TS)1e-6 : (TS)1e-15, 60, false, nullptr,
+                                                             Mode::mixed ? (TS)1e-3 : (TS)3e-8);
         if (g == 0) {
             TS sacc = (TS)0;
             for (int cc = 0; cc < CHI; ++cc) {
@@ -882,7 +888,8 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
     {
         const int x = tid / GJ, g = tid % GJ;
         WarpGroup grp{group_mask<GJ>()};
-        jacobi_svd<CHI, double>(sm.Am[x], sm.Vm[x], g, grp, group_mask<CHI>(), 1e-15, 60, true);
+        jacobi_svd<CHI, double, WarpGroup, true, true>(sm.Am[x], sm.Vm[x], g, grp, group_mask<CHI>(), 1e-15, 60, true,
+                                                       nullptr, 3e-8);
     }
     team_bar<TEAM>(team);
     for (int t = tid; t < 2 * CHI; t += TEAM) {
@@ -925,7 +932,8 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
     team_bar<TEAM>(team);
     if (tid < GJ) {
         WarpGroup grp{group_mask<GJ>()};
-        jacobi_svd<CHI, double>(sm.M, sm.VM, tid, grp, group_mask<CHI>(), 1e-15, 60, true);
+        jacobi_svd<CHI, double, WarpGroup, true, true>(sm.M, sm.VM, tid, grp, group_mask<CHI>(), 1e-15, 60, true,
+                                                       nullptr, 3e-8);
     }
     team_bar<TEAM>(team);
     for (int cc = tid; cc < CHI; cc += TEAM) {

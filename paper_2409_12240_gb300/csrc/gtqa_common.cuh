@@ -146,9 +146,17 @@ __device__ __forceinline__ void round_robin_pair(int N, int step, int k, int& p,
     if (p > q) { int t = p; p = q; q = t; }
 }
 
-template <int N, typename R, typename Group, bool WITHV = true>
+// Options: WITHV = false skips the V updates (only the singular values are wanted).
+// F32ANGLE (R = double): the rotation angle t is solved in FP32 from the FP64 zeta, and c,
+// s and the phase e are then formed in FP64 from that t, so every rotation is unitary to
+// FP64 rounding and the FP64 orthogonality test decides convergence; only the size of
+// each step is FP32-accurate.  quad_tol > 0: a sweep whose examined pairs all have
+// |gamma| <= quad_tol sqrt(alpha beta) is the last one: with quadratic convergence the
+// next sweep would find |gamma| ~ quad_tol^2 sqrt(alpha beta) <= tol sqrt(alpha beta) (for
+// quad_tol^2 <= tol), so the confirming sweep is skipped.
+template <int N, typename R, typename Group, bool WITHV = true, bool F32ANGLE = false>
 __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pair_mask,
-                          R tol, int max_sweeps, bool init_v, int* nrot = nullptr) {
+                          R tol, int max_sweeps, bool init_v, int* nrot = nullptr, R quad_tol = (R)0) {
     const int k = g / N;
     const int r = g % N;
     if (WITHV && init_v) {
@@ -156,9 +164,11 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
         V[(2 * k + 1) * N + r] = C<R>{(R)((2 * k + 1) == r), (R)0};
     }
     grp.sync();
+    const R tol2 = tol * tol, quad2 = quad_tol * quad_tol;
+    const bool quad = quad_tol > (R)0;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
-        int rotated = 0;
+        int rotated = 0, big = 0;
         for (int step = 0; step < N - 1; ++step) {
             int p, q;
             round_robin_pair(N, step, k, p, q);
@@ -170,13 +180,23 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
             gam.x = group_sum<N>(gam.x, pair_mask);
             gam.y = group_sum<N>(gam.y, pair_mask);
             const R g2 = gam.x * gam.x + gam.y * gam.y;
-            if (g2 > (R)0 && g2 > (tol * tol) * (alpha * beta)) {
+            const R ab = alpha * beta;
+            if (g2 > (R)0 && g2 > tol2 * ab) {
+                if (g2 > quad2 * ab) big = 1;
                 const R rg = nr_rsqrt(g2);                      // 1 / |gamma|
                 const R zeta = (beta - alpha) * ((R)0.5 * rg);
-                const R az = fabs(zeta);
-                // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), the smaller root; 1/(2 zeta) for huge zeta
-                const R t = (zeta >= (R)0 ? (R)1 : (R)-1) *
-                            (az < (R)1e15 ? nr_rcp(az + nr_sqrt((R)1 + az * az)) : (R)0.5 * nr_rcp(az));
+                R t;
+                if constexpr (F32ANGLE) {
+                    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) in FP32; 1/(2 zeta) for huge zeta
+                    const float zf = (float)zeta, azf = fabsf(zf);
+                    const float tf = azf < 1e18f ? __frcp_rn(azf + sqrtf(fmaf(azf, azf, 1.f))) : 0.5f * __frcp_rn(azf);
+                    t = (R)(zf >= 0.f ? tf : -tf);
+                } else {
+                    const R az = fabs(zeta);
+                    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), the smaller root; 1/(2 zeta) for huge zeta
+                    t = (zeta >= (R)0 ? (R)1 : (R)-1) *
+                        (az < (R)1e15 ? nr_rcp(az + nr_sqrt((R)1 + az * az)) : (R)0.5 * nr_rcp(az));
+                }
                 const R c = nr_rsqrt((R)1 + t * t);
                 const R s = c * t;
                 const C<R> e = C<R>{gam.x * rg, gam.y * rg};
@@ -194,12 +214,12 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
             }
             grp.sync();
         }
-        if (!grp.any(rotated)) {
+        if (!grp.any(quad ? big : rotated)) {
             ++sweep;
             break;
         }
     }
-    return sweep;   // sweeps run, including the final one without rotations
+    return sweep;   // sweeps run, including the final one (without rotations unless quad_tol stopped it)
 }
 
 // Rank of value i among n values, descending, ties by index (used to sort
