@@ -521,9 +521,16 @@ template <int CHI, class Mode>
 struct BPSm {
     using TS = typename Mode::TS;
     static constexpr int H2 = 2 * CHI * CHI * CHI, CC = CHI * CHI, NP = Mode::mixed ? 3 : 2;
-    C<TS> T[H2];
-    C<TS> P[NP][H2];     // FP64: T x0 m0, T x1 m1; mixed: T x0 d0, T x1 d1, T x2 d2
-    C<TS> Q[3][H2];      // per outgoing slot
+    // F in two halves over the physical index (summed at use) unless the team is NPART lanes
+    // per (j, j') that split the (i, u) sum and meet by shuffles
+    static constexpr int NPART = Shape<CHI>::TB / CC;
+    static constexpr bool FSPLIT = !(Shape<CHI>::TB % CC == 0 && NPART <= 32 && (2 * CHI) % NPART == 0);
+    // T, P and Q in the natural index order [i][j0][j1][j2] with one padding element after
+    // every (i, j0) plane, so that a stride along slot 0 does not map to one bank
+    static constexpr int PS = CC + 1, H2P = 2 * CHI * PS;
+    C<TS> T[H2P];
+    C<TS> P[NP][H2P];    // FP64: T x0 m0, T x1 m1; mixed: T x0 d0, T x1 d1, T x2 d2
+    C<TS> Q[3][H2P];     // per outgoing slot
     C<TS> min[3][CC];    // incoming messages (mixed: m0 + delta)
     C<TS> din[3][CC];    // mixed: incoming delta
     C<TS> Fh[2][3][CC];  // the two physical-index halves of the outgoing messages
@@ -558,7 +565,7 @@ __device__ void bp_prepare(const Ctx& c, int a, int tid, int team, int cur, BPSm
         }
     }
     const CT* Tg = (const CT*)c.T + (size_t)a * H2;
-    for (int t = tid; t < H2; t += TEAM) sm.T[t] = ldcg(Tg + t);
+    for (int t = tid; t < H2; t += TEAM) sm.T[t + t / CC] = ldcg(Tg + t);
     team_bar<TEAM>(team);
     const CT* src = (const CT*)c.msg[cur];
     for (int t = tid; t < 3 * CC; t += TEAM) {
@@ -590,7 +597,8 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
     using TS = typename Mode::TS;
     using CT = C<TS>;
     constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H = CHI * CHI * CHI, H2 = 2 * H;
-    constexpr int S0 = CHI * CHI, S1 = CHI;   // strides of slots 0 and 1 (slot 2 has stride 1)
+    // strides in the padded shared-memory layout: slot 0, slot 1 (slot 2 has stride 1), i
+    constexpr int S0 = BPSm<CHI, Mode>::PS, S1 = CHI, HP = CHI * BPSm<CHI, Mode>::PS;
     if (sm.cached != a) bp_prepare<CHI, Mode>(c, a, tid, team, cur, sm);
     const CT* src = (const CT*)c.msg[cur];
     CT* dst = (CT*)c.msg[cur ^ 1];
@@ -612,61 +620,111 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
     // first contractions along one slot: P_k[.., x@k, ..] = sum_q T[.., q@k, ..] y_k[q][x]
     //   FP64: y = m (k = 0, 1); mixed: y = delta (k = 0, 1, 2)
     constexpr int NP = BPSm<CHI, Mode>::NP;
-    for (int t = tid; t < NP * H2; t += TEAM) {
-        const int k = t / H2, e = t % H2;
-        const int j0 = (e / S0) % CHI, j1 = (e / S1) % CHI, j2 = e % CHI;
-        const int st = k == 0 ? S0 : (k == 1 ? S1 : 1);
-        const int x = k == 0 ? j0 : (k == 1 ? j1 : j2);
-        const int base = e - x * st;
+    constexpr bool EVEN = H2 % TEAM == 0;   // whole tensors per team pass: slots fixed at compile time
+    auto slot_stride = [](int k) { return k == 0 ? S0 : (k == 1 ? S1 : 1); };
+    // e: natural index of an element, pe: its padded position
+    auto p_elem = [&](int k, int e) {
+        const int pe = e + e / CC;
+        const int st = slot_stride(k);
+        const int x = k == 0 ? (e / CC) % CHI : (k == 1 ? (e / CHI) % CHI : e % CHI);
+        const int base = pe - x * st;
         const CT* y = Mode::mixed ? sm.din[k] : sm.min[k];
         CT acc = z;
 #pragma unroll
         for (int q = 0; q < CHI; ++q) acc = cfma(sm.T[base + q * st], y[q * CHI + x], acc);
-        sm.P[k][e] = acc;
+        sm.P[k][pe] = acc;
+    };
+    if constexpr (EVEN) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+#pragma unroll
+            for (int w = 0; w < H2 / TEAM; ++w) p_elem(k, tid + w * TEAM);
+    } else {
+        for (int t = tid; t < NP * H2; t += TEAM) p_elem(t / H2, t % H2);
     }
     team_bar<TEAM>(team);
     // second contractions per outgoing slot s (natural layout, slot-s index = j):
     //   Q_0[i][j][a][b] = sum_q P_1[i][j][a][q] m_2[q][b]  (+ m0_1[a] P_2[i][j][a][b])
     //   Q_1[i][a][j][b] = sum_q P_0[i][a][j][q] m_2[q][b]  (+ m0_0[a] P_2[i][a][j][b])
     //   Q_2[i][a][b][j] = sum_q P_0[i][a][q][j] m_1[q][b]  (+ m0_0[a] P_1[i][a][b][j])
-    for (int t = tid; t < 3 * H2; t += TEAM) {
-        const int s = t / H2, e = t % H2;
-        if (sm.es[s] < 0) continue;
-        const int j0 = (e / S0) % CHI, j1 = (e / S1) % CHI, j2 = e % CHI;
+    auto q_elem = [&](int s, int e) {
+        const int pe = e + e / CC;
+        const int j0 = (e / CC) % CHI, j1 = (e / CHI) % CHI, j2 = e % CHI;
         CT acc = z;
         if (s == 2) {
 #pragma unroll
-            for (int q = 0; q < CHI; ++q) acc = cfma(sm.P[0][e - j1 * S1 + q * S1], sm.min[1][q * CHI + j1], acc);
+            for (int q = 0; q < CHI; ++q) acc = cfma(sm.P[0][pe - j1 * S1 + q * S1], sm.min[1][q * CHI + j1], acc);
         } else {
             const CT* Ps = (s == 0) ? sm.P[1] : sm.P[0];
 #pragma unroll
-            for (int q = 0; q < CHI; ++q) acc = cfma(Ps[e - j2 + q], sm.min[2][q * CHI + j2], acc);
+            for (int q = 0; q < CHI; ++q) acc = cfma(Ps[pe - j2 + q], sm.min[2][q * CHI + j2], acc);
         }
         if constexpr (Mode::mixed) {
             const float w = (s == 0) ? sm.m0f[1][j1] : sm.m0f[0][j0];
-            const CT pe = (s == 2) ? sm.P[1][e] : sm.P[2][e];
-            acc = acc + w * pe;
+            const CT pv = (s == 2) ? sm.P[1][pe] : sm.P[2][pe];
+            acc = acc + w * pv;
         }
-        sm.Q[s][e] = acc;
+        sm.Q[s][pe] = acc;
+    };
+    if constexpr (EVEN) {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            if (sm.es[s] < 0) continue;
+#pragma unroll
+            for (int w = 0; w < H2 / TEAM; ++w) q_elem(s, tid + w * TEAM);
+        }
+    } else {
+        for (int t = tid; t < 3 * H2; t += TEAM) {
+            const int s = t / H2;
+            if (sm.es[s] >= 0) q_elem(s, t % H2);
+        }
     }
     team_bar<TEAM>(team);
-    // overlaps with conj(T), one half per physical index: Fh[i][s][j][j']
-    for (int t = tid; t < 2 * 3 * CC; t += TEAM) {
-        const int i = t / (3 * CC), rem = t % (3 * CC);
-        const int s = rem / CC, r = rem % CC;
-        if (sm.es[s] < 0) continue;
+    // overlaps with conj(T): F_s[j][j'] = sum over (i, u@o0, v@o1) of Q_s[.., j@s] conj(T[.., j'@s])
+    if constexpr (BPSm<CHI, Mode>::FSPLIT) {
+        // one half of the sum per physical index i, added at use
+        for (int t = tid; t < 2 * 3 * CC; t += TEAM) {
+            const int i = t / (3 * CC), rem = t % (3 * CC);
+            const int s = rem / CC, r = rem % CC;
+            if (sm.es[s] < 0) continue;
+            const int j = r / CHI, jp = r % CHI;
+            const int ss = slot_stride(s);
+            const int so = s == 0 ? S1 : S0, st2 = s == 2 ? S1 : 1;   // strides of the two other slots
+            CT acc = z;
+#pragma unroll
+            for (int u = 0; u < CHI; ++u)
+#pragma unroll
+                for (int v = 0; v < CHI; ++v) {
+                    const int off = i * HP + u * so + v * st2;
+                    acc = cfmac(sm.T[off + jp * ss], sm.Q[s][off + j * ss], acc);
+                }
+            sm.Fh[i][s][r] = acc;
+        }
+    } else {
+        // lane = (j, j') * NPART + part; each part sums 2 CHI / NPART of the (i, u) pairs,
+        // then a shuffle sum over the NPART adjacent lanes
+        constexpr int NPART = BPSm<CHI, Mode>::NPART, PER = 2 * CHI / NPART;
+        const int r = tid / NPART, part = tid % NPART;
         const int j = r / CHI, jp = r % CHI;
-        const int ss = s == 0 ? S0 : (s == 1 ? S1 : 1);
-        const int so = s == 0 ? S1 : S0, st2 = s == 2 ? S1 : 1;   // strides of the two other slots
-        CT acc = z;
 #pragma unroll
-        for (int u = 0; u < CHI; ++u)
+        for (int s = 0; s < 3; ++s) {
+            if (sm.es[s] < 0) continue;
+            const int ss = slot_stride(s);
+            const int so = s == 0 ? S1 : S0, st2 = s == 2 ? S1 : 1;
+            CT acc = z;
 #pragma unroll
-            for (int v = 0; v < CHI; ++v) {
-                const int off = i * H + u * so + v * st2;
-                acc = cfmac(sm.T[off + jp * ss], sm.Q[s][off + j * ss], acc);
+            for (int h = 0; h < PER; ++h) {
+                const int cmb = part * PER + h, i = cmb / CHI, u = cmb % CHI;
+#pragma unroll
+                for (int v = 0; v < CHI; ++v) {
+                    const int off = i * HP + u * so + v * st2;
+                    acc = cfmac(sm.T[off + jp * ss], sm.Q[s][off + j * ss], acc);
+                }
             }
-        sm.Fh[i][s][r] = acc;
+            acc.x = group_sum<NPART>(acc.x, group_mask<NPART>());
+            acc.y = group_sum<NPART>(acc.y, group_mask<NPART>());
+            if (part == 0) sm.Fh[0][s][r] = acc;
+        }
     }
     team_bar<TEAM>(team);
     // traces of the outgoing messages
@@ -674,7 +732,9 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
         const int k = tid / CC;
         CT trs = z;
 #pragma unroll
-        for (int j = 0; j < CHI; ++j) trs = trs + (sm.Fh[0][k][j * CHI + j] + sm.Fh[1][k][j * CHI + j]);
+        for (int j = 0; j < CHI; ++j)
+            trs = trs + (BPSm<CHI, Mode>::FSPLIT ? sm.Fh[0][k][j * CHI + j] + sm.Fh[1][k][j * CHI + j]
+                                                  : sm.Fh[0][k][j * CHI + j]);
         sm.trs[k] = trs;
     }
 }
@@ -716,7 +776,7 @@ __device__ void bp_back(const Ctx& c, int tid, int team, int cur, bool exact, BP
         CT d = z;
         if (out >= 0) {
             const CT itr = sm.itr[k];
-            const CT f = sm.Fh[0][k][r] + sm.Fh[1][k][r];
+            const CT f = BPSm<CHI, Mode>::FSPLIT ? sm.Fh[0][k][r] + sm.Fh[1][k][r] : sm.Fh[0][k][r];
             CT num = f;
             if constexpr (Mode::mixed) {
                 const int j = r / CHI, jp = r % CHI;
