@@ -593,7 +593,8 @@ __device__ void bp_prepare(const Ctx& c, int a, int tid, int team, int cur, BPSm
 // First part of the sweep for vertex a: incoming messages, the contractions, and the
 // traces of the three outgoing messages (left in sm.trs).
 template <int CHI, class Mode>
-__device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode>& sm) {
+__device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode>& sm, bool have_pre,
+                         C<typename Mode::TS> pre) {
     using TS = typename Mode::TS;
     using CT = C<TS>;
     constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H = CHI * CHI * CHI, H2 = 2 * H;
@@ -603,15 +604,16 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
     const CT* src = (const CT*)c.msg[cur];
     CT* dst = (CT*)c.msg[cur ^ 1];
     const CT z = CT{(TS)0, (TS)0};
-    // incoming messages
+    // incoming messages (prefetched into `pre` by the caller when have_pre)
     for (int t = tid; t < 3 * CC; t += TEAM) {
         const int k = t / CC, r = t % CC;
         const int in = sm.in_idx[k];
+        const CT lv = in >= 0 ? (have_pre ? pre : ldcg(src + (size_t)in * CC + r)) : z;
         if constexpr (!Mode::mixed) {
-            sm.min[k][r] = in >= 0 ? ldcg(src + (size_t)in * CC + r) : CT{(TS)(r == 0 ? 1 : 0), (TS)0};
+            sm.min[k][r] = in >= 0 ? lv : CT{(TS)(r == 0 ? 1 : 0), (TS)0};
         } else {
             const int j = r / CHI, jp = r % CHI;
-            const CT dv = in >= 0 ? ldcg(src + (size_t)in * CC + r) : z;
+            const CT dv = lv;
             sm.din[k][r] = dv;
             sm.min[k][r] = CT{dv.x + ((j == jp) ? sm.m0f[k][j] : 0.f), dv.y};
         }
@@ -753,7 +755,8 @@ __device__ void bp_trace_rcp(BPSm<CHI, Mode>* all, int nteams) {
     cd tr = ccast<double>(sm.trs[k]);
     if constexpr (Mode::mixed) tr = tr + sm.t0[k];
     const double n2 = norm2(tr);
-    const double in2 = n2 > 0.0 ? nr_rcp(n2) : 0.0;
+    // the mixed mode rounds the result to FP32, so one Newton step (relative error ~2^-44) suffices
+    const double in2 = n2 > 0.0 ? (Mode::mixed ? nr_rcp1(n2) : nr_rcp(n2)) : 0.0;
     sm.itr[k] = ccast<TS>(cd{tr.x * in2, -tr.y * in2});
 }
 
@@ -1190,6 +1193,11 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
             const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * tpb_teams;
             const int inst0 = gteam < c.n ? c.vert_inst[gteam] : 0;   // the first round's vertex
             BPSm<CHI, Mode>* all = reinterpret_cast<BPSm<CHI, Mode>*>(smem);
+            bool have_pre = false;
+            CT_ pre = CT_{0, 0};
+            int* sflag = reinterpret_cast<int*>(bsum + 48);   // [2]: need | open << 1, per sweep parity
+            if (threadIdx.x == 0) sflag[0] = sflag[1] = 0;
+            __syncthreads();
             int it = 0;
             for (; it < c.max_iter; ++it) {
                 double* acc = c.acc + (size_t)(it % 3) * c.B;
@@ -1211,7 +1219,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                         if (done[inst]) bp_copy_vertex<CHI, Mode>(c, a, tid, S::TB, cur);
                         else act = true;
                     }
-                    if (act) bp_front<CHI, Mode>(c, a, tid, team, cur, sm);
+                    if (act) bp_front<CHI, Mode>(c, a, tid, team, cur, sm, base == 0 && have_pre, pre);
                     __syncthreads();
                     if (threadIdx.x < 32) bp_trace_rcp<CHI, Mode>(all, tpb_teams);
                     __syncthreads();
@@ -1231,6 +1239,14 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 if (c.B == 1 && threadIdx.x == 0) atomicAdd(acc, (double)bl);
                 cur ^= 1;
                 if (!grid_sync(gb, c.spin_limit)) return;
+                // the next sweep's incoming messages of this team's first vertex are loaded
+                // now, so that their latency overlaps the decision below
+                have_pre = false;
+                if (gteam < c.n && sm.cached == gteam && tid < 3 * CHI * CHI) {
+                    const int in = sm.in_idx[tid / (CHI * CHI)];
+                    if (in >= 0) pre = ldcg((const CT_*)c.msg[cur] + (size_t)in * CHI * CHI + tid % (CHI * CHI));
+                    have_pre = true;
+                }
                 // stopping rule of App. B, per instance, evaluated identically by every block;
                 // the raw distance sums are kept and divided by |E| at the end
                 const bool last = it + 1 >= c.max_iter;
@@ -1261,7 +1277,12 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                     // sweep came within a factor 3 of the threshold
                     exnow[b] = (it + 2 >= c.max_iter) || (float)dsum < thr3[b];
                 }
-                if (__syncthreads_or(need_local)) {
+                // one block barrier for both flags (a word per sweep parity, reset one sweep ahead)
+                if (need_local | open_local) atomicOr(&sflag[it & 1], need_local | (open_local << 1));
+                __syncthreads();
+                const int fl = sflag[it & 1];
+                if (threadIdx.x == 0) sflag[(it + 1) & 1] = 0;
+                if (fl & 1) {
                     bp_exact_pass<CHI, Mode>(c, cur, need, scratch, bsum + 32, ex);
                     if (!grid_sync(gb, c.spin_limit)) return;
                     for (int b = threadIdx.x; b < c.B; b += S::TPB) {
@@ -1278,8 +1299,11 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                         else open_local = 1;
                         exnow[b] = 1;
                     }
-                }
-                if (!__syncthreads_or(open_local)) {
+                    if (!__syncthreads_or(open_local)) {
+                        ++it;
+                        break;
+                    }
+                } else if (!(fl & 2)) {
                     ++it;
                     break;
                 }

@@ -102,6 +102,12 @@ __device__ __forceinline__ double nr_rcp(double x) {
     e = fma(-x, r, 1.0);
     return fma(r, e, r);
 }
+// one refinement step only: relative error ~2^-44, for results that are rounded to FP32
+__device__ __forceinline__ double nr_rcp1(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return fma(r, fma(-x, r, 1.0), r);
+}
 __device__ __forceinline__ double nr_rsqrt(double x) {
     double y;
     asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
