@@ -301,7 +301,13 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
             sm.V[t] = sm.Vn[t];
         }
         team_bar<TEAM>(team);
-        sweeps = svd64(false, 1e-13, 3e-7);
+        if constexpr (TEAM <= 32) {
+            WarpGroup grp{group_mask<TEAM>()};
+            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-13, 3e-7, 60, &nrot);
+        } else {
+            TeamGroup<TEAM> grp{team, &sm.flag};
+            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-13, 3e-7, 60, &nrot);
+        }
     }
     if (nrot) atomicAdd(&sm.nrot, nrot);
     team_bar<TEAM>(team);

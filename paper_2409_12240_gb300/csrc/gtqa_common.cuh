@@ -228,6 +228,101 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
     return sweep;   // sweeps run, including the final one (without rotations unless quad_tol stopped it)
 }
 
+// FP64 polish of a one-sided Jacobi SVD (same layout, pairing and rotations as
+// jacobi_svd<N, double>) for columns that are already nearly orthogonal, as after an
+// FP32 solve and an FP64 Newton-Schulz step.  Fewer FP64 instructions per step:
+//  * the squared column norms are kept in nrm[N] (shared) and, in steps whose rotations are all
+//    small, updated as alpha' = alpha - tau |gamma|^2 and beta' = beta + tau |gamma|^2 (the two
+//    eigenvalues of the pair's 2x2 Gram matrix) instead of two reductions per step; after a
+//    large rotation, where that update can cancel, they are recomputed;
+//  * the rotation is parametrised by tau = t / |gamma| = 2 sign(D) / (|D| + sqrt(D^2 + 4|gamma|^2)),
+//    D = beta - alpha, solved in FP32 on values scaled by an approximate 1/(alpha + beta);
+//    then t^2 = tau^2 |gamma|^2, c = 1/sqrt(1 + t^2) and s e = c tau gamma are formed in FP64,
+//    so c^2 + |s e|^2 = 1 to FP64 rounding whatever the error of tau, and the FP64
+//    orthogonality test alone decides convergence;
+//  * c = 1 - t^2/2 + 3t^4/8 when every pair of the group has t^2 < 1e-6 (the dropped terms are
+//    below 3.2e-19).
+// The quadratic stop of jacobi_svd applies (quad_tol).  Returns the sweeps run.
+template <int N, typename Group>
+__device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, const Group& grp, unsigned pair_mask,
+                             double tol, double quad_tol, int max_sweeps, int* nrot) {
+    using CD = C<double>;
+    const int k = g / N;
+    const int r = g % N;
+    {
+        const double n0 = group_sum<N>(norm2(A[(2 * k) * N + r]), pair_mask);
+        const double n1 = group_sum<N>(norm2(A[(2 * k + 1) * N + r]), pair_mask);
+        if (r == 0) {
+            nrm[2 * k] = n0;
+            nrm[2 * k + 1] = n1;
+        }
+    }
+    grp.sync();
+    const double tol2 = tol * tol, quad2 = quad_tol * quad_tol;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        int big = 0;
+        for (int step = 0; step < N - 1; ++step) {
+            int p, q;
+            round_robin_pair(N, step, k, p, q);
+            const CD ap = A[p * N + r], aq = A[q * N + r];
+            const double alpha = nrm[p], beta = nrm[q];
+            CD gam = cfmac(ap, aq, CD{0.0, 0.0});
+            gam.x = group_sum<N>(gam.x, pair_mask);
+            gam.y = group_sum<N>(gam.y, pair_mask);
+            const double g2 = gam.x * gam.x + gam.y * gam.y;
+            const double ab = alpha * beta;
+            const bool rot = g2 > 0.0 && g2 > tol2 * ab;
+            double tau = 0.0, t2 = 0.0;
+            if (rot) {
+                if (g2 > quad2 * ab) big = 1;
+                const double d = beta - alpha;
+                double rsc;
+                asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(rsc) : "d"(alpha + beta));
+                const float dn = (float)(d * rsc), gn = (float)(g2 * rsc * rsc);
+                const float tn = 2.f * __frcp_rn(fabsf(dn) + sqrtf(fmaf(dn, dn, 4.f * gn)));
+                tau = (double)(dn >= 0.f ? tn : -tn) * rsc;
+                t2 = tau * tau * g2;
+            }
+            const bool series = !grp.any(rot && !(t2 < 1e-6));
+            if (rot) {
+                const double c = series ? fma(t2, fma(0.375, t2, -0.5), 1.0) : nr_rsqrt(1.0 + t2);
+                const double ct = c * tau;
+                const CD se = CD{ct * gam.x, ct * gam.y};
+                const CD sec = conj(se);
+                A[p * N + r] = c * ap - sec * aq;
+                A[q * N + r] = se * ap + c * aq;
+                const CD vp = V[p * N + r], vq = V[q * N + r];
+                V[p * N + r] = c * vp - sec * vq;
+                V[q * N + r] = se * vp + c * vq;
+                if (r == 0 && nrot) ++*nrot;
+            }
+            if (series) {
+                if (rot && r == 0) {
+                    const double m = tau * g2;
+                    nrm[p] = alpha - m;
+                    nrm[q] = beta + m;
+                }
+            } else {
+                // a large rotation: the update alpha - tau |gamma|^2 can cancel, so the two
+                // norms are recomputed from the rotated columns
+                const double np = group_sum<N>(norm2(A[p * N + r]), pair_mask);
+                const double nq = group_sum<N>(norm2(A[q * N + r]), pair_mask);
+                if (r == 0) {
+                    nrm[p] = np;
+                    nrm[q] = nq;
+                }
+            }
+            grp.sync();
+        }
+        if (!grp.any(big)) {
+            ++sweep;
+            break;
+        }
+    }
+    return sweep;
+}
+
 // Rank of value i among n values, descending, ties by index (used to sort
 // singular values without data movement).  A NaN ranks below every number, so the
 // ranks are a permutation of 0..n-1 whatever the values.
