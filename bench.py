@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison run")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--ncu-case", type=int, default=None, metavar="K0",
+                   help="profiling case: anneal layers 1..K0, then one gates launch, one BP launch of 1 sweep "
+                        "and, from the same state, one of 21 sweeps (warm start, no regauge); no timing")
     p.add_argument("--budget", type=float, default=15.0, help=argparse.SUPPRESS)
     a = p.parse_args()
     if a.steps is None:
@@ -241,14 +244,15 @@ def bp_sweep_flops(chi: int, vertices: int, mixed: bool) -> float:
     return float(vertices * 3 * per)
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_bp_kernel_n1000_chi4.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_n1000_chi4.json")
 TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2409_12240_gb300", "csrc", f) for f in ("gtqa_anneal.cuh", "gtqa_common.cuh")]
 
 
-def bp_traffic(mixed: bool, chi: int, sweeps_per_launch: float):
-    """DRAM bytes per BP launch from the committed ncu capture (dram__bytes_read.sum +
-    dram__bytes_write.sum of one launch), scaled to this run's sweeps per launch; None if
-    there is no capture for this mode or the kernel sources changed since it was taken."""
+def kernel_traffic(kernel: str, mixed: bool, chi: int, sweeps_per_launch: float = 0.0):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the committed
+    ncu capture of `bench.py --ncu-case`; BP launches are scaled to this run's sweeps per launch
+    from the captured 1-sweep and 21-sweep launches.  None if there is no capture for this mode
+    or the kernel sources changed since it was taken."""
     import hashlib
     try:
         with open(TRAFFIC_FILE) as f:
@@ -260,9 +264,12 @@ def bp_traffic(mixed: bool, chi: int, sweeps_per_launch: float):
         with open(p, "rb") as f:
             h.update(f.read())
     r = rec.get("mixed" if mixed else "fp64")
-    if not r or r.get("sources_sha256") != h.hexdigest() or r.get("chi") != chi:
+    if not r or r.get("sources_sha256") != h.hexdigest() or r.get("chi") != chi or kernel not in r:
         return None
-    return r["fixed_bytes"] + r["bytes_per_sweep"] * sweeps_per_launch
+    k = r[kernel]
+    if kernel == "bp_kernel":
+        return k["fixed_bytes"] + k["bytes_per_sweep"] * sweeps_per_launch
+    return k["bytes_per_launch"]
 
 
 def per_layer_error(G, make, inst, k_last: int, samples: int = 6) -> dict:
@@ -409,7 +416,7 @@ def run_gtqa(a):
         f64, f32 = gate_flops(chi, units, int(dlt["svd_pairs"]), int(dlt["svd_rotations"]), mixed)
         ach = f64 / (ms * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None,
+                "frac": ach / fp64_peak, "traffic": kernel_traffic(dom, mixed, chi),
                 "peak_source": peak_note.format(lanes="2 FP64 FMA units", meas=fp64_meas),
                 "algorithmic_flops_per_launch": f64 / nl, "avg_launch_us": ms / nl * 1e3,
                 "note": "FP64 flops only" + ("; the FP32 preconditioning sweeps of the mixed SVD and the FP32 "
@@ -420,7 +427,7 @@ def run_gtqa(a):
         peak = fp32_peak if mixed else fp64_peak
         ach = fl / (ms * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": bp_traffic(mixed, chi, sweeps / nl),
+                "frac": ach / peak, "traffic": kernel_traffic(dom, mixed, chi, sweeps / nl),
                 "peak_source": peak_note.format(lanes="128 FP32 lanes" if mixed else "2 FP64 FMA units",
                                                 meas=fp32_meas if mixed else fp64_meas),
                 "algorithmic_flops_per_launch": fl / nl, "avg_launch_us": ms / nl * 1e3,
@@ -489,8 +496,34 @@ def run_reference(a):
     print(json.dumps(out))
 
 
+def ncu_case(a):
+    """A short run for ncu captures: the launches of interest come after 3 K0 warm-up launches
+    (gates, BP, regauge per layer); the gates launch is the (K0+1)-th gates_kernel, the two BP
+    launches the (K0+1)-th and (K0+2)-th bp_kernel."""
+    from paper_2409_12240_gb300 import gtqa as G
+    G.load(build_if_missing=True)
+    inst = instance()
+    prec = G.GTQA_MIXED if a.precision == "mixed" else G.GTQA_FP64
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, WL["chi"], inst.colour, G.gtqa_options_init(precision=prec))
+    try:
+        K0 = a.ncu_case
+        if K0 > 0:
+            G.gtqa_anneal(s, 1, K0, WL["K"], WL["dt"], WL["tol"], WL["max_iter"])
+        G.gtqa_trotter_layer(s, (K0 + 1) / WL["K"], WL["dt"])
+        Gm, L, M = G.gtqa_get_state(s)
+        G.gtqa_bp_sweep(s, 0.0, 1, G.GTQA_BP_WARM_START)
+        G.gtqa_set_state(s, Gm, L, M)
+        G.gtqa_bp_sweep(s, 0.0, 21, G.GTQA_BP_WARM_START)
+    finally:
+        G.gtqa_destroy(s)
+    print(json.dumps({"ncu_case": a.ncu_case, "precision": a.precision}))
+
+
 def main():
     a = parse()
+    if a.ncu_case is not None:
+        ncu_case(a)
+        return
     if a.oracle_sample:
         r = oracle_sampled_rate(a.warmup, a.steps, a.budget)
         print(json.dumps(r))
