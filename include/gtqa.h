@@ -164,6 +164,16 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
                 int32_t max_iter);
 
 /*
+ * Residual of the local-orthogonality condition of the Vidal gauge (App. C, the distance to
+ * the Vidal gauge): R = 1/(2|E|) sum_a sum_{b in da} || delta - sum Gamma_a Gamma_a^*
+ * prod_{c != b} lambda_ca^2 ||_1 with the trace norm, computed in FP64 on the device from the
+ * current Gamma and lambda.  delta is the identity on the bond indices with lambda > 0.
+ *   R_out  host double, written on success (0 for a graph without edges)
+ * Synchronises the stream.  GTQA_ERR_NUMERIC if the sum is NaN.
+ */
+int gtqa_residual(gtqa_state* s, double* R_out);
+
+/*
  * Single-qubit reduced density matrices rho_a = sum Gamma Gamma^* prod_b lambda_ba^2 / tr
  * (Eq. (partial_dens) with the environment of Eq. (bp_approx) from the warm-start
  * messages of the current Vidal-gauge state) and the read-out of Eq. (rounding_rule).

@@ -1400,4 +1400,58 @@ __global__ void marginals_kernel2(const C<typename Mode::TS>* Gamma, const doubl
     }
 }
 
+// Residual R of the local-orthogonality condition (App. C):
+//   R = 1/(2|E|) sum_a sum_{b in da} || delta - sum Gamma_a Gamma_a^* prod_{c != b} lambda_ca^2 ||_1,
+// one warp per (vertex, incident edge); delta is the identity on the bond indices with
+// lambda > 0 (the padded indices do not exist in the state).  The trace norm is the sum of
+// singular values of the C x C difference (FP64 Jacobi).  Adds the unnormalised sum to *out.
+template <int CHI, class Mode>
+__global__ void residual_kernel(const C<typename Mode::TS>* Gamma, const double* lam, const int4* vert_edges, int n,
+                                double* out) {
+    constexpr int H = CHI * CHI * CHI, CC = CHI * CHI, GJ = CC / 2 > 0 ? CC / 2 : 1, WPB = 8;
+    __shared__ cd Dsm[WPB][CC];
+    const int wib = threadIdx.x / 32, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * WPB + wib;
+    if (item >= 3 * n) return;
+    const int a = item / 3, s = item % 3;
+    const int4 ve = vert_edges[a];
+    const int es[3] = {ve.x, ve.y, ve.z};
+    if (es[s] < 0) return;
+    int o0, o1;
+    others_of(s, o0, o1);
+    const int ss = sstride<CHI>(s), s0 = sstride<CHI>(o0), s1 = sstride<CHI>(o1);
+    const C<typename Mode::TS>* g = Gamma + (size_t)a * 2 * H;
+    for (int r = lane; r < CC; r += 32) {
+        const int j = r / CHI, jp = r % CHI;
+        cd acc = cd{0.0, 0.0};
+        for (int i = 0; i < 2; ++i)
+            for (int u = 0; u < CHI; ++u) {
+                const double lu = lam_get(lam, CHI, es[o0], u);
+                for (int v = 0; v < CHI; ++v) {
+                    const double lv = lam_get(lam, CHI, es[o1], v);
+                    const int base = i * H + u * s0 + v * s1;
+                    const cd x = ccast<double>(g[base + j * ss]), y = ccast<double>(g[base + jp * ss]);
+                    acc = cfmac(y, (lu * lu * lv * lv) * x, acc);
+                }
+            }
+        const double act = (j == jp && lam_get(lam, CHI, es[s], j) > 0.0) ? 1.0 : 0.0;
+        Dsm[wib][r] = cd{act - acc.x, -acc.y};
+    }
+    __syncwarp();
+    if (lane < GJ) {
+        WarpGroup grp{group_mask<GJ>()};
+        jacobi_svd<CHI, double, WarpGroup, false>(Dsm[wib], nullptr, lane, grp, group_mask<CHI>(), 1e-15, 60, false);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        double sacc = 0.0;
+        for (int cc = 0; cc < CHI; ++cc) {
+            double n2 = 0.0;
+            for (int r = 0; r < CHI; ++r) n2 += norm2(Dsm[wib][cc * CHI + r]);
+            sacc += nr_sqrt(n2);
+        }
+        atomicAdd(out, sacc);
+    }
+}
+
 }  // namespace gtqa

@@ -51,6 +51,7 @@ struct gtqa_state {
     cd* rho = nullptr;
     int8_t* sign = nullptr;
     int* flags = nullptr;       // [0]: NaN in marginals
+    double* rbuf = nullptr;     // residual accumulator
     // host counters
     long long layers = 0, gates = 0, launches = 0;
     int sticky = GTQA_OK;
@@ -255,7 +256,7 @@ void free_state(gtqa_state* s) {
     void* ptrs[] = {s->Gamma, s->lam, s->T, s->msg[0], s->msg[1], s->D0, s->t0, s->X, s->edge_info,
                     s->vert_edges, s->vert_inst, s->J, s->h, s->colour_edges, s->colour_off, s->last_colour,
                     s->iso, s->inst_vbeg, s->inst_m, s->acc, s->inst_done, s->inst_iters, s->inst_dist,
-                    s->stats, s->ctl, s->rho, s->sign, s->flags};
+                    s->stats, s->ctl, s->rho, s->sign, s->flags, s->rbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : s->pending) {
@@ -499,7 +500,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         (rc = dalloc(s, &s->inst_done, B)) || (rc = dalloc(s, &s->inst_iters, B)) ||
         (rc = dalloc(s, &s->inst_dist, B)) || (rc = dalloc(s, &s->stats, 4)) || (rc = dalloc(s, &s->ctl, 1)) ||
         (rc = dalloc(s, &s->rho, (size_t)s->n * 4)) || (rc = dalloc(s, &s->sign, s->n)) ||
-        (rc = dalloc(s, &s->flags, 4))) {
+        (rc = dalloc(s, &s->flags, 4)) || (rc = dalloc(s, &s->rbuf, 1))) {
         free_state(s);
         return rc;
     }
@@ -668,6 +669,27 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
         s->gates += s->m;
     }
     return GTQA_OK;
+}
+
+int gtqa_residual(gtqa_state* s, double* R_out) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (!R_out) return GTQA_ERR_INVALID_ARG;
+    if (!cuda_ok(s, cudaMemsetAsync(s->rbuf, 0, sizeof(double), s->stream))) return GTQA_ERR_CUDA;
+    const cudaError_t e = mixed(s) ? residual_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream)
+                                   : residual_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->sticky = GTQA_ERR_CUDA;
+        return GTQA_ERR_CUDA;
+    }
+    s->launches += 1;
+    double sum = 0.0;
+    if (!cuda_ok(s, cudaMemcpyAsync(&sum, s->rbuf, sizeof(double), cudaMemcpyDeviceToHost, s->stream)) ||
+        !cuda_ok(s, cudaStreamSynchronize(s->stream)))
+        return GTQA_ERR_CUDA;
+    *R_out = s->m > 0 ? sum / (2.0 * (double)s->m) : 0.0;
+    return (sum == sum) ? GTQA_OK : GTQA_ERR_NUMERIC;
 }
 
 int gtqa_marginals(gtqa_state* s, double* rho_out, int8_t* sign_out) {

@@ -67,4 +67,23 @@ cudaError_t marginals_launch_fp64(int CHI, const void* G, const double* lam, con
     }
 }
 
+namespace {
+template <int CHI>
+cudaError_t resid_t(const void* G, const double* lam, const int4* ve, int n, double* out, cudaStream_t st) {
+    const int wpb = 8;
+    residual_kernel<CHI, ModeFP64><<<(3 * n + wpb - 1) / wpb, 32 * wpb, 0, st>>>((const C<typename ModeFP64::TS>*)G, lam, ve, n, out);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t residual_launch_fp64(int CHI, const void* G, const double* lam, const int4* ve, int n, double* out,
+                                  cudaStream_t st) {
+    switch (CHI) {
+        case 2: return resid_t<2>(G, lam, ve, n, out, st);
+        case 4: return resid_t<4>(G, lam, ve, n, out, st);
+        case 8: return resid_t<8>(G, lam, ve, n, out, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace gtqa

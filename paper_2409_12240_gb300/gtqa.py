@@ -36,7 +36,7 @@ EXPORTED = [
     "gtqa_regauge", "gtqa_anneal", "gtqa_marginals", "gtqa_stats", "gtqa_get_state", "gtqa_set_state", "gtqa_sizes",
     "gtqa_edge_colouring", "gtqa_strerror", "gtqa_destroy", "gtqa_profile", "gtqa_profile_read",
     "gtqa_profile_name", "gtqa_alu_peak", "gtqa_debug_barrier", "gtqa_math_check", "gtqa_bp_static",
-    "gtqa_barrier_bench",
+    "gtqa_barrier_bench", "gtqa_residual",
 ]
 KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_regauge": (I32, [P]),
         "gtqa_anneal": (I32, [P, I32, I32, I32, D, D, I32]),
         "gtqa_marginals": (I32, [P, P, P]),
+        "gtqa_residual": (I32, [P, ctypes.POINTER(D)]),
         "gtqa_stats": (I32, [P, ctypes.POINTER(gtqa_stats_t)]),
         "gtqa_get_state": (I32, [P, P, P, P]),
         "gtqa_set_state": (I32, [P, P, P, P]),
@@ -213,6 +214,13 @@ def gtqa_sizes(s: int) -> Tuple[int, int, int, int]:
     n, m, c, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().gtqa_sizes(s, ctypes.byref(n), ctypes.byref(m), ctypes.byref(c), ctypes.byref(k)), "gtqa_sizes")
     return int(n.value), int(m.value), int(c.value), int(k.value)
+
+
+def gtqa_residual(s: int) -> float:
+    """Local-orthogonality residual R of the current state (App. C)."""
+    r = ctypes.c_double()
+    _check(load().gtqa_residual(s, ctypes.byref(r)), "gtqa_residual")
+    return float(r.value)
 
 
 def gtqa_marginals(s: int, rho_out=None, sign_out=None):
