@@ -925,6 +925,12 @@ struct RGSm {
     double sig[CHI];
     int perm[CHI];
     double scal[2];
+    // mixed mode: scratch of the FP32-preconditioned SVDs
+    cf A32[2][CHI * CHI];
+    cf V32[2][CHI * CHI];
+    cd T1[2][CHI * CHI];
+    cd T2[2][CHI * CHI];
+    double nrm[2][CHI];
 };
 
 template <int CHI, class Mode>
@@ -955,10 +961,17 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
     }
     team_bar<TEAM>(team);
     {
+        // FP64 eigen-decompositions of the two Hermitian messages (the singular values of a
+        // Hermitian matrix are the moduli of its eigenvalues); the mixed mode takes the
+        // FP32-preconditioned path, whose result is FP64-accurate as well
         const int x = tid / GJ, g = tid % GJ;
         WarpGroup grp{group_mask<GJ>()};
-        jacobi_svd<CHI, double, WarpGroup, true, true>(sm.Am[x], sm.Vm[x], g, grp, group_mask<CHI>(), 1e-15, 60, true,
-                                                       nullptr, 3e-8);
+        if constexpr (Mode::mixed)
+            mixed_svd<CHI>(sm.Am[x], sm.Vm[x], sm.A32[x], sm.V32[x], sm.T1[x], sm.T2[x], sm.nrm[x], g, grp,
+                           group_mask<CHI>(), 1e-13, 3e-7, nullptr);
+        else
+            jacobi_svd<CHI, double, WarpGroup, true, true>(sm.Am[x], sm.Vm[x], g, grp, group_mask<CHI>(), 1e-15, 60, true,
+                                                           nullptr, 3e-8);
     }
     team_bar<TEAM>(team);
     for (int t = tid; t < 2 * CHI; t += TEAM) {
@@ -1001,8 +1014,12 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
     team_bar<TEAM>(team);
     if (tid < GJ) {
         WarpGroup grp{group_mask<GJ>()};
-        jacobi_svd<CHI, double, WarpGroup, true, true>(sm.M, sm.VM, tid, grp, group_mask<CHI>(), 1e-15, 60, true,
-                                                       nullptr, 3e-8);
+        if constexpr (Mode::mixed)
+            mixed_svd<CHI>(sm.M, sm.VM, sm.A32[0], sm.V32[0], sm.T1[0], sm.T2[0], sm.nrm[0], tid, grp,
+                           group_mask<CHI>(), 1e-13, 3e-7, nullptr);
+        else
+            jacobi_svd<CHI, double, WarpGroup, true, true>(sm.M, sm.VM, tid, grp, group_mask<CHI>(), 1e-15, 60, true,
+                                                           nullptr, 3e-8);
     }
     team_bar<TEAM>(team);
     for (int cc = tid; cc < CHI; cc += TEAM) {

@@ -323,6 +323,52 @@ __device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, con
     return sweep;
 }
 
+// FP64 SVD of an N x N complex matrix A (column-major, shared memory) by the mixed path:
+// one-sided Jacobi sweeps on an FP32 copy give V32; one FP64 Newton-Schulz step
+// V <- V (3I - V^H V)/2 makes V unitary to ~1e-14; W = A V (FP64) then goes through the
+// FP64 polish (jacobi_polish) to orthogonality `tol`.  On exit A holds U S (columns unsorted)
+// and V the right singular vectors, as after jacobi_svd<N, double>.  A32, V32 (N^2 complex
+// floats), T1, T2 (N^2 complex) and nrm (N) are scratch.  The group has N^2/2 lanes.
+template <int N, typename Group>
+__device__ int mixed_svd(C<double>* A, C<double>* V, C<float>* A32, C<float>* V32, C<double>* T1, C<double>* T2,
+                         double* nrm, int g, const Group& grp, unsigned pair_mask, double tol, double quad_tol,
+                         int* nrot) {
+    using CD = C<double>;
+    constexpr int NN = N * N, L = NN / 2;
+    for (int t = g; t < NN; t += L) A32[t] = ccast<float>(A[t]);
+    grp.sync();
+    jacobi_svd<N, float>(A32, V32, g, grp, pair_mask, 1e-6f, 40, true, nullptr, 1e-3f);
+    for (int t = g; t < NN; t += L) V[t] = ccast<double>(V32[t]);
+    grp.sync();
+    for (int t = g; t < NN; t += L) {   // T1 = V^H V
+        const int q = t / N, p = t % N;
+        CD acc = CD{0.0, 0.0};
+        for (int r = 0; r < N; ++r) acc = cfmac(V[p * N + r], V[q * N + r], acc);
+        T1[t] = acc;
+    }
+    grp.sync();
+    for (int t = g; t < NN; t += L) {   // T2 = V (1.5 I - 0.5 T1)
+        const int q = t / N, r = t % N;
+        CD acc = 1.5 * V[q * N + r];
+        for (int p = 0; p < N; ++p) acc = cfma(-0.5 * V[p * N + r], T1[q * N + p], acc);
+        T2[t] = acc;
+    }
+    grp.sync();
+    for (int t = g; t < NN; t += L) {   // T1 = A T2
+        const int q = t / N, r = t % N;
+        CD acc = CD{0.0, 0.0};
+        for (int p = 0; p < N; ++p) acc = cfma(A[p * N + r], T2[q * N + p], acc);
+        T1[t] = acc;
+    }
+    grp.sync();
+    for (int t = g; t < NN; t += L) {
+        A[t] = T1[t];
+        V[t] = T2[t];
+    }
+    grp.sync();
+    return jacobi_polish<N, Group>(A, V, nrm, g, grp, pair_mask, tol, quad_tol, 60, nrot);
+}
+
 // Rank of value i among n values, descending, ties by index (used to sort
 // singular values without data movement).  A NaN ranks below every number, so the
 // ranks are a permutation of 0..n-1 whatever the values.
