@@ -18,6 +18,7 @@ Every step follows the paper's notation and order:
 * reduced density matrices and read-out ....... Eq. (partial_dens), Eq. (bp_approx), Eq. (rounding_rule)
 * Trotterised annealing schedule .............. App. F, Eq. (discretizatoion)
 * per-gate fidelity estimate .................. Sec. III D, Eq. (gate_fidelity)
+* mean-field entanglement entropy, bipartition . Sec. III C, Eqs. (bipartition), (mean_field_schmidt), (apprx_entropy)
 
 Readings taken where the paper is silent or ambiguous (each one is listed in the
 design notes of the repository):
@@ -594,3 +595,60 @@ def messages_from_padded(st: VidalState, P: np.ndarray) -> Dict[Tuple[int, int],
         msgs[(e, 0)] = np.array(P[2 * e, :d, :d], dtype=np.complex128)
         msgs[(e, 1)] = np.array(P[2 * e + 1, :d, :d], dtype=np.complex128)
     return msgs
+
+
+# --------------------------------------------------------------------------
+# mean-field entanglement entropy over a bipartition (Sec. III C)
+# --------------------------------------------------------------------------
+def approx_entanglement_entropy(st: VidalState, cut) -> float:
+    """Eq. (apprx_entropy) with the mean-field Schmidt values of Eq. (mean_field_schmidt):
+    S* = - sum over the edges e of the cut of sum_j lambda_e[j]^2 log(lambda_e[j]^2).
+    `cut` is a boolean (or 0/1) array over the edges; zero entries of lambda add nothing."""
+    S = 0.0
+    for e in range(st.m):
+        if not cut[e]:
+            continue
+        for x in st.lam[e]:
+            p = float(x) * float(x)
+            if p > 0.0:
+                S -= p * np.log(p)
+    return S
+
+
+def spectral_bipartition(n: int, edges) -> Tuple[np.ndarray, np.ndarray, float]:
+    """Eq. (bipartition), A* = argmin |dA| / (|A| |Abar|), by spectral partitioning: the
+    eigenvector f of the second-smallest eigenvalue of the graph Laplacian D - A (dense
+    eigh), its sign fixed so that its entry of largest modulus (lowest vertex on ties) is
+    positive, vertices ordered by (f, id), and the prefix of that order with the smallest
+    ratio (the first one on ties).  Returns (side: True for A, cut: per edge, ratio)."""
+    edges = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    L = np.zeros((n, n))
+    for u, v in edges:
+        L[u, v] -= 1.0
+        L[v, u] -= 1.0
+        L[u, u] += 1.0
+        L[v, v] += 1.0
+    w, V = np.linalg.eigh(L)
+    f = V[:, 1].copy()
+    k = int(np.argmax(np.abs(f)))
+    if f[k] < 0:
+        f = -f
+    order = sorted(range(n), key=lambda a: (f[a], a))
+    inA = np.zeros(n, dtype=bool)
+    adj = [[] for _ in range(n)]
+    for u, v in edges:
+        adj[u].append(int(v))
+        adj[v].append(int(u))
+    cutsize, best, best_s = 0, np.inf, 1
+    for s in range(1, n):
+        u = order[s - 1]
+        inside = sum(1 for x in adj[u] if inA[x])
+        cutsize += len(adj[u]) - 2 * inside
+        inA[u] = True
+        r = cutsize / (s * (n - s))
+        if r < best:
+            best, best_s = r, s
+    side = np.zeros(n, dtype=bool)
+    side[order[:best_s]] = True
+    cut = side[edges[:, 0]] != side[edges[:, 1]]
+    return side, cut, float(best)

@@ -324,3 +324,59 @@ def trace_distance_band(seeds=(0, 1, 2), n: int = 14, T: float = 20.0, dt: float
                 tot += O.trace_norm(rho[a] - rhos[k - 1][a])
         errs.append(dt / (2 * T * n) * tot)
     return float(np.mean(errs))
+
+
+def tree_entropy_exact(seed: int, n: int = 10, K: int = 5, dt: float = 0.3) -> float:
+    """On a tree without truncation, lambda across an edge are the Schmidt values of that
+    edge's cut (Sec. II C), so the mean-field entropy of Eq. (apprx_entropy) for a one-edge
+    cut equals the von Neumann entropy of the exact state for that bipartition."""
+    inst = make_tree_instance(n, seed)
+    st = O.plus_state(inst.n, inst.edges)
+    psi, _ = SV.evolve(inst.n, inst.edges, inst.J, inst.h, K, dt)
+    for k in range(1, K + 1):
+        tZ, tX = O.schedule(k, K, dt)
+        st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 256, 1e-13, 100)
+    err = 0.0
+    for e in range(st.m):
+        side = _component(inst, e, int(inst.edges[e][0]))
+        sv = SV.schmidt_values(psi, side)
+        p = (sv / np.linalg.norm(sv)) ** 2
+        p = p[p > 1e-300]
+        s_exact = float(-(p * np.log(p)).sum())
+        cut = np.zeros(st.m, dtype=bool)
+        cut[e] = True
+        err = max(err, abs(O.approx_entanglement_entropy(st, cut) - s_exact))
+    return err
+
+
+def bipartition_closed_forms() -> float:
+    """Eq. (bipartition) on graphs whose best ratio cut is known: two 4-cliques joined by
+    one edge (the cliques, ratio 1/16) and the 12-cycle (two arcs of 6, ratio 2/36); the
+    spectral split must find them.  Returns the largest deviation of the ratio."""
+    err = 0.0
+    k4 = [(a, b) for a in range(4) for b in range(a + 1, 4)]
+    edges = np.array(k4 + [(a + 4, b + 4) for a, b in k4] + [(3, 4)])
+    side, cut, r = O.spectral_bipartition(8, edges)
+    err = max(err, abs(r - 1 / 16), float(abs(int(cut.sum()) - 1)))
+    err = max(err, float(len({bool(side[a]) for a in range(4)}) - 1))
+    ring = np.array([(a, (a + 1) % 12) for a in range(12)])
+    side, cut, r = O.spectral_bipartition(12, ring)
+    err = max(err, abs(r - 2 / 36), float(abs(int(cut.sum()) - 2)))
+    return float(err)
+
+
+def bipartition_against_brute_force(seed: int = 0, n: int = 12) -> float:
+    """The spectral split is a heuristic for Eq. (bipartition): on small random 3-regular
+    graphs its ratio is never below the exhaustive minimum over all 2^(n-1) - 1 splits, and
+    the reported cut and ratio are consistent with the returned sides."""
+    inst = make_instance(n, seed)
+    side, cut, r = O.spectral_bipartition(n, inst.edges)
+    e = inst.edges
+    best = np.inf
+    for mask in range(1, 2 ** (n - 1)):
+        s = np.array([(mask >> a) & 1 for a in range(n)], dtype=bool)
+        c = int((s[e[:, 0]] != s[e[:, 1]]).sum())
+        best = min(best, c / (s.sum() * (n - s.sum())))
+    consistent = abs(r - int(cut.sum()) / (side.sum() * (n - side.sum())))
+    below = max(0.0, best - r)
+    return float(max(consistent, below))

@@ -141,3 +141,22 @@ def test_trace_distance_error_in_paper_band():
     # Eq. (error), Fig. 4(b): 1e-3 .. a few 1e-2 for N = 14, T = 20, chi = 4 (sanity band)
     e = P.trace_distance_band(seeds=(0, 1))
     assert 1e-4 < e < 5e-2
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tree_one_edge_cut_entropy_is_exact(seed):
+    # Sec. III C, Eq. (apprx_entropy): exact for a one-edge cut of a tree (Sec. II C)
+    assert P.tree_entropy_exact(seed) < 1e-9
+
+
+def test_product_state_has_zero_entropy():
+    inst = make_instance(16, 0)
+    st = O.plus_state(inst.n, inst.edges)
+    assert O.approx_entanglement_entropy(st, np.ones(st.m, dtype=bool)) == 0.0
+
+
+def test_spectral_bipartition_closed_forms_and_brute_force():
+    # Eq. (bipartition): known optimal ratio cuts, and never better than the exhaustive optimum
+    assert P.bipartition_closed_forms() < 1e-12
+    for seed in range(3):
+        assert P.bipartition_against_brute_force(seed) < 1e-12
