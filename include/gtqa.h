@@ -164,6 +164,34 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
                 int32_t max_iter);
 
 /*
+ * Mean-field entanglement entropy of a bipartition (Sec. III C, Eq. (apprx_entropy) with the
+ * Schmidt values of Eq. (mean_field_schmidt)): S* = - sum over the cut edges e of
+ * sum_j lambda_e[j]^2 log(lambda_e[j]^2), computed on the device in FP64 from the current
+ * lambda.
+ *   cut    uint8 [m] (host or device): nonzero for the edges whose ends lie on different
+ *          sides (for a batched state, m counts the edges of all instances)
+ *   S_out  host double
+ * Synchronises the stream.  GTQA_ERR_NUMERIC if the sum is NaN.
+ */
+int gtqa_entropy(gtqa_state* s, const uint8_t* cut, double* S_out);
+
+/*
+ * The bipartition of Eq. (bipartition), A* = argmin |dA| / (|A| |Abar|), by spectral
+ * partitioning (host code): the eigenvector f of the second-smallest eigenvalue of the graph
+ * Laplacian D - A (Lanczos with full reorthogonalisation on the complement of the constant
+ * vector, at most 240 steps, so exact up to rounding for n <= 241; an approximation above),
+ * its sign fixed so that its entry of largest modulus is positive, the vertices ordered by
+ * (f, id), and the prefix of that order with the smallest ratio (the first one on ties).
+ *   n, m, edges  the graph (int32 [m][2], host)
+ *   side_out     uint8 [n], host: 1 for the vertices of A
+ *   cut_out      uint8 [m], host, nullable: 1 for the edges between A and Abar
+ *   ratio_out    host double, nullable: |dA| / (|A| |Abar|)
+ * No device work.  GTQA_ERR_INVALID_ARG for n < 2 or an edge out of range or a self-loop.
+ */
+int gtqa_spectral_bipartition(int32_t n, int32_t m, const int32_t* edges, uint8_t* side_out, uint8_t* cut_out,
+                              double* ratio_out);
+
+/*
  * Residual of the local-orthogonality condition of the Vidal gauge (App. C, the distance to
  * the Vidal gauge): R = 1/(2|E|) sum_a sum_{b in da} || delta - sum Gamma_a Gamma_a^*
  * prod_{c != b} lambda_ca^2 ||_1 with the trace norm, computed in FP64 on the device from the

@@ -51,7 +51,8 @@ struct gtqa_state {
     cd* rho = nullptr;
     int8_t* sign = nullptr;
     int* flags = nullptr;       // [0]: NaN in marginals
-    double* rbuf = nullptr;     // residual accumulator
+    double* rbuf = nullptr;     // residual / entropy accumulator
+    unsigned char* cutbuf = nullptr;   // entropy: per-edge cut mask
     // host counters
     long long layers = 0, gates = 0, launches = 0;
     int sticky = GTQA_OK;
@@ -256,7 +257,7 @@ void free_state(gtqa_state* s) {
     void* ptrs[] = {s->Gamma, s->lam, s->T, s->msg[0], s->msg[1], s->D0, s->t0, s->X, s->edge_info,
                     s->vert_edges, s->vert_inst, s->J, s->h, s->colour_edges, s->colour_off, s->last_colour,
                     s->iso, s->inst_vbeg, s->inst_m, s->acc, s->inst_done, s->inst_iters, s->inst_dist,
-                    s->stats, s->ctl, s->rho, s->sign, s->flags, s->rbuf};
+                    s->stats, s->ctl, s->rho, s->sign, s->flags, s->rbuf, s->cutbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : s->pending) {
@@ -500,7 +501,8 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         (rc = dalloc(s, &s->inst_done, B)) || (rc = dalloc(s, &s->inst_iters, B)) ||
         (rc = dalloc(s, &s->inst_dist, B)) || (rc = dalloc(s, &s->stats, 4)) || (rc = dalloc(s, &s->ctl, 1)) ||
         (rc = dalloc(s, &s->rho, (size_t)s->n * 4)) || (rc = dalloc(s, &s->sign, s->n)) ||
-        (rc = dalloc(s, &s->flags, 4)) || (rc = dalloc(s, &s->rbuf, 1))) {
+        (rc = dalloc(s, &s->flags, 4)) || (rc = dalloc(s, &s->rbuf, 1)) ||
+        (rc = dalloc(s, &s->cutbuf, std::max(s->m, 1)))) {
         free_state(s);
         return rc;
     }
@@ -576,6 +578,74 @@ int read_messages(gtqa_state* s, int cur, std::vector<cd>& out) {
             }
     }
     return GTQA_OK;
+}
+
+// Eq. (apprx_entropy): every thread adds -sum_j lambda^2 log lambda^2 of one cut edge.
+__global__ void entropy_kernel(const double* lam, const unsigned char* cut, int m, int chi, double* out) {
+    __shared__ double part[8];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (e < m && cut[e]) {
+        for (int j = 0; j < chi; ++j) {
+            const double p = lam[(size_t)e * chi + j] * lam[(size_t)e * chi + j];
+            if (p > 0.0) v -= p * log(p);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x / 32] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += part[w];
+        if (t != 0.0) atomicAdd(out, t);
+    }
+}
+
+// Smallest eigenpair of the symmetric tridiagonal matrix (a on the diagonal, b below it):
+// the eigenvalue by bisection on the Sturm count, the eigenvector by inverse iteration
+// with a tridiagonal (Thomas) solve.
+void tridiag_min_eigvec(const std::vector<double>& a, const std::vector<double>& b, std::vector<double>& y) {
+    const int k = (int)a.size();
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < k; ++i) {
+        const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    auto count_below = [&](double x) {   // eigenvalues < x (Sturm sequence)
+        int c = 0;
+        double q = a[0] - x;
+        if (q < 0) ++c;
+        for (int i = 1; i < k; ++i) {
+            const double d = q != 0.0 ? q : 1e-300;
+            q = a[i] - x - b[i - 1] * b[i - 1] / d;
+            if (q < 0) ++c;
+        }
+        return c;
+    };
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, std::fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (count_below(mid) >= 1) hi = mid; else lo = mid;
+    }
+    const double lam = lo - 1e-13 * std::max(1.0, std::fabs(lo));
+    y.assign(k, 1.0);
+    std::vector<double> d(k), r(k);
+    for (int pass = 0; pass < 4; ++pass) {   // (T - lam I) y_new = y
+        d[0] = a[0] - lam;
+        r[0] = y[0];
+        for (int i = 1; i < k; ++i) {
+            const double piv = d[i - 1] != 0.0 ? d[i - 1] : 1e-300;
+            const double f = b[i - 1] / piv;
+            d[i] = a[i] - lam - f * b[i - 1];
+            r[i] = y[i] - f * r[i - 1];
+        }
+        y[k - 1] = r[k - 1] / (d[k - 1] != 0.0 ? d[k - 1] : 1e-300);
+        for (int i = k - 2; i >= 0; --i) y[i] = (r[i] - b[i] * y[i + 1]) / (d[i] != 0.0 ? d[i] : 1e-300);
+        double nrm = 0.0;
+        for (double v : y) nrm += v * v;
+        nrm = std::sqrt(nrm);
+        for (double& v : y) v /= nrm;
+    }
 }
 
 }  // namespace
@@ -668,6 +738,138 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
         s->layers += 1;
         s->gates += s->m;
     }
+    return GTQA_OK;
+}
+
+int gtqa_entropy(gtqa_state* s, const uint8_t* cut, double* S_out) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (!S_out || (s->m > 0 && !cut)) return GTQA_ERR_INVALID_ARG;
+    if (s->m == 0) {
+        *S_out = 0.0;
+        return GTQA_OK;
+    }
+    if (!cuda_ok(s, cudaMemcpyAsync(s->cutbuf, cut, (size_t)s->m, cudaMemcpyDefault, s->stream)) ||
+        !cuda_ok(s, cudaMemsetAsync(s->rbuf, 0, sizeof(double), s->stream)))
+        return GTQA_ERR_CUDA;
+    entropy_kernel<<<(s->m + 255) / 256, 256, 0, s->stream>>>(s->lam, s->cutbuf, (int)s->m, s->CHI, s->rbuf);
+    if (!cuda_ok(s, cudaGetLastError())) return GTQA_ERR_CUDA;
+    s->launches += 1;
+    double v = 0.0;
+    if (!cuda_ok(s, cudaMemcpyAsync(&v, s->rbuf, sizeof(double), cudaMemcpyDeviceToHost, s->stream)) ||
+        !cuda_ok(s, cudaStreamSynchronize(s->stream)))
+        return GTQA_ERR_CUDA;
+    *S_out = v;
+    return (v == v) ? GTQA_OK : GTQA_ERR_NUMERIC;
+}
+
+int gtqa_spectral_bipartition(int32_t n, int32_t m, const int32_t* edges, uint8_t* side_out, uint8_t* cut_out,
+                              double* ratio_out) {
+    if (n < 2 || m < 0 || (m > 0 && !edges) || !side_out) return GTQA_ERR_INVALID_ARG;
+    std::vector<int> deg(n, 0);
+    for (int e = 0; e < m; ++e) {
+        const int u = edges[2 * e], v = edges[2 * e + 1];
+        if (u < 0 || v < 0 || u >= n || v >= n || u == v) return GTQA_ERR_INVALID_ARG;
+        ++deg[u];
+        ++deg[v];
+    }
+    std::vector<int> off(n + 1, 0), adj(2 * (size_t)m);
+    for (int a = 0; a < n; ++a) off[a + 1] = off[a] + deg[a];
+    {
+        std::vector<int> fill(off.begin(), off.end() - 1);
+        for (int e = 0; e < m; ++e) {
+            const int u = edges[2 * e], v = edges[2 * e + 1];
+            adj[fill[u]++] = v;
+            adj[fill[v]++] = u;
+        }
+    }
+    auto laplacian = [&](const std::vector<double>& x, std::vector<double>& y) {
+        for (int a = 0; a < n; ++a) {
+            double t = deg[a] * x[a];
+            for (int q = off[a]; q < off[a + 1]; ++q) t -= x[adj[q]];
+            y[a] = t;
+        }
+    };
+    auto project = [&](std::vector<double>& x) {   // remove the constant vector
+        double mean = 0.0;
+        for (double v : x) mean += v;
+        mean /= n;
+        for (double& v : x) v -= mean;
+    };
+    // Lanczos on L = D - A restricted to the complement of the constant vector, with full
+    // reorthogonalisation; the Krylov space is the whole complement for n <= 241
+    const int kmax = std::min(n - 1, 240);
+    std::vector<std::vector<double>> Q;
+    Q.reserve(kmax);
+    std::vector<double> al, be, w(n);
+    std::vector<double> q(n);
+    unsigned long long st = 0x9E3779B97F4A7C15ull;
+    for (int a = 0; a < n; ++a) {   // deterministic start vector (xorshift64)
+        st ^= st << 13;
+        st ^= st >> 7;
+        st ^= st << 17;
+        q[a] = (double)(st >> 11) / 9007199254740992.0 - 0.5;
+    }
+    project(q);
+    double nq = 0.0;
+    for (double v : q) nq += v * v;
+    nq = std::sqrt(nq);
+    if (!(nq > 0.0)) return GTQA_ERR_NUMERIC;
+    for (double& v : q) v /= nq;
+    for (int j = 0; j < kmax; ++j) {
+        Q.push_back(q);
+        laplacian(Q[j], w);
+        double aj = 0.0;
+        for (int a = 0; a < n; ++a) aj += Q[j][a] * w[a];
+        al.push_back(aj);
+        for (int pass = 0; pass < 2; ++pass) {
+            project(w);
+            for (int i = 0; i <= j; ++i) {
+                double c = 0.0;
+                for (int a = 0; a < n; ++a) c += Q[i][a] * w[a];
+                for (int a = 0; a < n; ++a) w[a] -= c * Q[i][a];
+            }
+        }
+        double bj = 0.0;
+        for (double v : w) bj += v * v;
+        bj = std::sqrt(bj);
+        if (j + 1 == kmax || bj < 1e-10 * std::max(1.0, std::fabs(aj))) break;
+        be.push_back(bj);
+        for (int a = 0; a < n; ++a) q[a] = w[a] / bj;
+    }
+    std::vector<double> y;
+    tridiag_min_eigvec(al, be, y);
+    std::vector<double> f(n, 0.0);
+    for (size_t i = 0; i < y.size(); ++i)
+        for (int a = 0; a < n; ++a) f[a] += y[i] * Q[i][a];
+    int big = 0;
+    for (int a = 1; a < n; ++a)
+        if (std::fabs(f[a]) > std::fabs(f[big])) big = a;
+    if (f[big] < 0)
+        for (double& v : f) v = -v;
+    std::vector<int> order(n);
+    for (int a = 0; a < n; ++a) order[a] = a;
+    std::sort(order.begin(), order.end(), [&](int x, int z) { return f[x] < f[z] || (f[x] == f[z] && x < z); });
+    std::vector<char> inA(n, 0);
+    long long cutsz = 0, best_s = 1;
+    double best = HUGE_VAL;
+    for (int sz = 1; sz < n; ++sz) {
+        const int u = order[sz - 1];
+        int inside = 0;
+        for (int qq = off[u]; qq < off[u + 1]; ++qq) inside += inA[adj[qq]];
+        cutsz += deg[u] - 2 * inside;
+        inA[u] = 1;
+        const double r = (double)cutsz / ((double)sz * (double)(n - sz));
+        if (r < best) {
+            best = r;
+            best_s = sz;
+        }
+    }
+    for (int a = 0; a < n; ++a) side_out[a] = 0;
+    for (long long i = 0; i < best_s; ++i) side_out[order[i]] = 1;
+    if (cut_out)
+        for (int e = 0; e < m; ++e) cut_out[e] = side_out[edges[2 * e]] != side_out[edges[2 * e + 1]];
+    if (ratio_out) *ratio_out = best;
     return GTQA_OK;
 }
 

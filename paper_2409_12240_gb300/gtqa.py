@@ -36,7 +36,7 @@ EXPORTED = [
     "gtqa_regauge", "gtqa_anneal", "gtqa_marginals", "gtqa_stats", "gtqa_get_state", "gtqa_set_state", "gtqa_sizes",
     "gtqa_edge_colouring", "gtqa_strerror", "gtqa_destroy", "gtqa_profile", "gtqa_profile_read",
     "gtqa_profile_name", "gtqa_alu_peak", "gtqa_debug_barrier", "gtqa_math_check", "gtqa_bp_static",
-    "gtqa_barrier_bench", "gtqa_residual",
+    "gtqa_barrier_bench", "gtqa_residual", "gtqa_entropy", "gtqa_spectral_bipartition",
 ]
 KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
@@ -90,6 +90,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_anneal": (I32, [P, I32, I32, I32, D, D, I32]),
         "gtqa_marginals": (I32, [P, P, P]),
         "gtqa_residual": (I32, [P, ctypes.POINTER(D)]),
+        "gtqa_entropy": (I32, [P, P, ctypes.POINTER(D)]),
+        "gtqa_spectral_bipartition": (I32, [I32, I32, P, P, P, ctypes.POINTER(D)]),
         "gtqa_stats": (I32, [P, ctypes.POINTER(gtqa_stats_t)]),
         "gtqa_get_state": (I32, [P, P, P, P]),
         "gtqa_set_state": (I32, [P, P, P, P]),
@@ -214,6 +216,26 @@ def gtqa_sizes(s: int) -> Tuple[int, int, int, int]:
     n, m, c, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().gtqa_sizes(s, ctypes.byref(n), ctypes.byref(m), ctypes.byref(c), ctypes.byref(k)), "gtqa_sizes")
     return int(n.value), int(m.value), int(c.value), int(k.value)
+
+
+def gtqa_entropy(s: int, cut) -> float:
+    """Mean-field entanglement entropy of the bipartition whose cut edges are marked in `cut`
+    (Sec. III C, Eq. (apprx_entropy))."""
+    c = np.ascontiguousarray(np.asarray(cut).astype(np.uint8))
+    v = ctypes.c_double()
+    _check(load().gtqa_entropy(s, c.ctypes.data, ctypes.byref(v)), "gtqa_entropy")
+    return float(v.value)
+
+
+def gtqa_spectral_bipartition(n: int, edges) -> Tuple[np.ndarray, np.ndarray, float]:
+    """Eq. (bipartition) by spectral partitioning: returns (side, cut, ratio)."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    side = np.zeros(int(n), dtype=np.uint8)
+    cut = np.zeros(e.shape[0], dtype=np.uint8)
+    r = ctypes.c_double()
+    _check(load().gtqa_spectral_bipartition(int(n), int(e.shape[0]), e.ctypes.data, side.ctypes.data,
+                                            cut.ctypes.data, ctypes.byref(r)), "gtqa_spectral_bipartition")
+    return side.astype(bool), cut.astype(bool), float(r.value)
 
 
 def gtqa_residual(s: int) -> float:

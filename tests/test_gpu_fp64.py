@@ -241,3 +241,32 @@ def test_residual_matches_oracle(precision, rel, atol):
         assert max(seen_after) < 1e-4 and all(x < y for x, y in zip(seen_after[2:], seen[2:])), (seen_after, seen)
     finally:
         G.gtqa_destroy(s)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision, tol", [(0, 1e-10), (1, 1e-5)])
+def test_entropy_of_spectral_cut_matches_oracle(precision, tol):
+    """Mean-field entanglement entropy (Sec. III C) of the spectral bipartition on the device
+    against the oracle's, after each of 6 layers."""
+    G = U.lib()
+    inst = make_instance(16, 2)
+    side, cut, ratio = G.gtqa_spectral_bipartition(inst.n, inst.edges)
+    _, cut_o, ratio_o = O.spectral_bipartition(inst.n, inst.edges)
+    assert abs(ratio - ratio_o) < 1e-12
+    K, dt, chi = 20, 0.3, 4
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour, G.gtqa_options_init(precision=precision))
+    try:
+        st = O.plus_state(inst.n, inst.edges)
+        assert G.gtqa_entropy(s, cut) == 0.0
+        seen = []
+        for k in range(1, 7):
+            G.gtqa_trotter_layer(s, k / K, dt)
+            G.gtqa_bp_sweep(s, 1e-12, 100)
+            tZ, tX = O.schedule(k, K, dt)
+            st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, chi, 1e-12, 100)
+            s_g, s_o = G.gtqa_entropy(s, cut), O.approx_entanglement_entropy(st, cut)
+            seen.append(s_o)
+            assert abs(s_g - s_o) < tol * max(1.0, s_o), (k, s_g, s_o)
+        assert max(seen) > 0.05   # the state is entangled across the cut by then
+    finally:
+        G.gtqa_destroy(s)
