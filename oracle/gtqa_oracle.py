@@ -19,6 +19,7 @@ Every step follows the paper's notation and order:
 * Trotterised annealing schedule .............. App. F, Eq. (discretizatoion)
 * per-gate fidelity estimate .................. Sec. III D, Eq. (gate_fidelity)
 * mean-field entanglement entropy, bipartition . Sec. III C, Eqs. (bipartition), (mean_field_schmidt), (apprx_entropy)
+* measurement sampling ........................ Sec. IV A, Eq. (projection)
 
 Readings taken where the paper is silent or ambiguous (each one is listed in the
 design notes of the repository):
@@ -652,3 +653,34 @@ def spectral_bipartition(n: int, edges) -> Tuple[np.ndarray, np.ndarray, float]:
     side[order[:best_s]] = True
     cut = side[edges[:, 0]] != side[edges[:, 1]]
     return side, cut, float(best)
+
+
+# --------------------------------------------------------------------------
+# measurement sampling for degenerate problems (Sec. IV A)
+# --------------------------------------------------------------------------
+def sample_bitstring(st: VidalState, order, u, tol: float, max_iter: int,
+                     eig_cutoff: float = EIG_CUTOFF, svd_cutoff: float = SVD_CUTOFF):
+    """BP-guided sampling of a bitstring (Sec. IV A), qubit by qubit in `order`:
+    (i) the outcome probabilities are the diagonal of the current reduced density matrix,
+    p(x_a = +1) = rho_a[0, 0] (Eq. (partial_dens) in the Vidal gauge, reading R8); the
+    outcome is +1 if u[k] < rho_a[0, 0] (u[k] uniform in [0, 1), passed in), else -1;
+    (ii) Gamma_a is projected on |x_a> (Eq. (projection)); (iii) the network is regauged: BP
+    from the warm start, then the Vidal gauge from the messages.
+    Returns (x, p, st): x[a] in {+1, -1}, p[k] the probability of the k-th outcome given the
+    previous ones, and the final state."""
+    x = np.zeros(st.n, dtype=np.int8)
+    p = np.zeros(len(order))
+    for k, a in enumerate(order):
+        rho = reduced_density_matrices(st)[a]
+        p0 = float(rho[0, 0].real)
+        xa = 1 if u[k] < p0 else -1
+        x[a] = xa
+        p[k] = p0 if xa == 1 else float(rho[1, 1].real)
+        i_keep = 0 if xa == 1 else 1
+        g = st.Gamma[a].copy()
+        g[1 - i_keep] = 0.0
+        st.Gamma[a] = g
+        T = symmetric_gauge(st)
+        msgs, _, _ = bp(st, T, reconstructed_messages(st), tol, max_iter)
+        st = vidal_gauge(st, T, msgs, eig_cutoff, svd_cutoff)
+    return x, p, st

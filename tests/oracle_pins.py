@@ -380,3 +380,22 @@ def bipartition_against_brute_force(seed: int = 0, n: int = 12) -> float:
     consistent = abs(r - int(cut.sum()) / (side.sum() * (n - side.sum())))
     below = max(0.0, best - r)
     return float(max(consistent, below))
+
+
+def tree_sampling_chain_rule(seed: int, n: int = 8, K: int = 4, dt: float = 0.4) -> float:
+    """Measurement sampling (Sec. IV A) on a tree without truncation: BP marginals are exact
+    (Sec. II B), so the product of the conditional probabilities of a sampled bitstring is
+    its exact Born probability |<x|psi>|^2 from the statevector.  Returns the relative error."""
+    inst = make_tree_instance(n, seed)
+    st = O.plus_state(inst.n, inst.edges)
+    psi, _ = SV.evolve(inst.n, inst.edges, inst.J, inst.h, K, dt)
+    for k in range(1, K + 1):
+        tZ, tX = O.schedule(k, K, dt)
+        st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 256, 1e-13, 100)
+    rng = np.random.default_rng(100 + seed)
+    order = rng.permutation(n).tolist()
+    u = rng.random(n)
+    x, p, _ = O.sample_bitstring(st, order, u, 1e-13, 100)
+    idx = tuple(0 if xa == 1 else 1 for xa in x)
+    born = abs(psi[idx]) ** 2 / np.sum(np.abs(psi) ** 2)
+    return float(abs(np.prod(p) - born) / born)

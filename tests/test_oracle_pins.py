@@ -160,3 +160,25 @@ def test_spectral_bipartition_closed_forms_and_brute_force():
     assert P.bipartition_closed_forms() < 1e-12
     for seed in range(3):
         assert P.bipartition_against_brute_force(seed) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tree_sampling_probabilities_are_born_probabilities(seed):
+    # Sec. IV A sampling with Eq. (projection) and regauging; exact on trees (Sec. II B)
+    assert P.tree_sampling_chain_rule(seed) < 1e-7   # BP after a projection converges to ~1e-9
+
+
+def test_sampling_a_product_state_follows_its_marginals():
+    # J = 0: the state stays a product, so each outcome's probability is the qubit's own marginal
+    inst = make_instance(12, 0, J="ferro", h_std=0.5)
+    J0 = np.zeros_like(inst.J)
+    st = O.plus_state(inst.n, inst.edges)
+    for k in range(1, 4):
+        tZ, tX = O.schedule(k, 4, 0.5)
+        st, _ = O.gtqa_layer(st, inst.colour, J0, inst.h, tZ, tX, 4, 1e-13, 100)
+    rho = O.reduced_density_matrices(st)
+    u = np.linspace(0.05, 0.95, inst.n)
+    x, p, _ = O.sample_bitstring(st, list(range(inst.n)), u, 1e-13, 100)
+    expect = np.where(u < rho[:, 0, 0].real, rho[:, 0, 0].real, rho[:, 1, 1].real)
+    assert np.abs(p - expect).max() < 1e-12
+    assert np.array_equal(x, np.where(u < rho[:, 0, 0].real, 1, -1))
