@@ -164,6 +164,24 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
                 int32_t max_iter);
 
 /*
+ * BP-guided measurement sampling of a bitstring (Sec. IV A), for problems whose solutions
+ * are degenerate so that the read-out of Eq. (rounding_rule) does not decide.  For each
+ * qubit a = order[q], q = 0..k-1, in turn: rho_a of the current Vidal-gauge state gives the
+ * outcome probabilities (p(+1) = rho_a[0,0]); the outcome is +1 if u[q] < rho_a[0,0], else -1;
+ * Gamma_a is projected on that outcome (Eq. (projection)); then BP runs from the warm start
+ * (tol, max_iter) and the network is regauged (App. D), as gtqa_bp_sweep with
+ * GTQA_BP_DEFAULT does.  The state is left in its post-measurement form.
+ *   k        number of qubits to sample (0 <= k <= n)
+ *   order    int32 [k], host: distinct vertices
+ *   u        float64 [k], host: the caller's uniform random numbers in [0, 1]
+ *   x_out    int8 [n], host: +1 / -1 for the sampled qubits, 0 for the others
+ *   p_out    float64 [k], host, nullable: the probability of each outcome given the earlier ones
+ * For a batched state every step regauges all instances.  Synchronises the stream once.
+ */
+int gtqa_sample(gtqa_state* s, int32_t k, const int32_t* order, const double* u, double tol, int32_t max_iter,
+                int8_t* x_out, double* p_out);
+
+/*
  * Mean-field entanglement entropy of a bipartition (Sec. III C, Eq. (apprx_entropy) with the
  * Schmidt values of Eq. (mean_field_schmidt)): S* = - sum over the cut edges e of
  * sum_j lambda_e[j]^2 log(lambda_e[j]^2), computed on the device in FP64 from the current

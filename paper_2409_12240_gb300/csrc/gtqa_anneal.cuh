@@ -1471,4 +1471,33 @@ __global__ void residual_kernel(const C<typename Mode::TS>* Gamma, const double*
     }
 }
 
+// One step of the measurement sampling of Sec. IV A for vertex a (one warp): rho_a as in
+// marginals_kernel2, the outcome x_a = +1 if u < rho_a[0,0] (else -1), its probability, and
+// the projection of Eq. (projection): the other physical component of Gamma_a is zeroed.
+template <int CHI, class Mode>
+__global__ void sample_kernel(C<typename Mode::TS>* Gamma, const double* lam, const int4* vert_edges, int a, double u,
+                              int step, int8_t* x_out, double* p_out) {
+    constexpr int H = CHI * CHI * CHI;
+    const int lane = threadIdx.x & 31;
+    const int4 ve = vert_edges[a];
+    C<typename Mode::TS>* g = Gamma + (size_t)a * 2 * H;
+    double r00 = 0.0, r11 = 0.0;
+    for (int r = lane; r < H; r += 32) {
+        const int j0 = r / (CHI * CHI), j1 = (r / CHI) % CHI, j2 = r % CHI;
+        const double l0 = lam_get(lam, CHI, ve.x, j0), l1 = lam_get(lam, CHI, ve.y, j1), l2 = lam_get(lam, CHI, ve.z, j2);
+        const double wgt = (l0 * l0) * (l1 * l1) * (l2 * l2);
+        r00 += wgt * norm2(ccast<double>(g[r]));
+        r11 += wgt * norm2(ccast<double>(g[H + r]));
+    }
+    r00 = group_sum<32>(r00, 0xffffffffu);
+    r11 = group_sum<32>(r11, 0xffffffffu);
+    const double p0 = r00 / (r00 + r11);
+    const int keep = u < p0 ? 0 : 1;
+    if (lane == 0) {
+        x_out[a] = keep == 0 ? 1 : -1;
+        p_out[step] = keep == 0 ? p0 : r11 / (r00 + r11);
+    }
+    for (int r = lane; r < H; r += 32) g[(1 - keep) * H + r] = C<typename Mode::TS>{0, 0};
+}
+
 }  // namespace gtqa

@@ -53,6 +53,8 @@ struct gtqa_state {
     int* flags = nullptr;       // [0]: NaN in marginals
     double* rbuf = nullptr;     // residual / entropy accumulator
     unsigned char* cutbuf = nullptr;   // entropy: per-edge cut mask
+    int8_t* xs = nullptr;       // sampling: outcomes [n]
+    double* ps = nullptr;       // sampling: outcome probabilities [n]
     // host counters
     long long layers = 0, gates = 0, launches = 0;
     int sticky = GTQA_OK;
@@ -257,7 +259,7 @@ void free_state(gtqa_state* s) {
     void* ptrs[] = {s->Gamma, s->lam, s->T, s->msg[0], s->msg[1], s->D0, s->t0, s->X, s->edge_info,
                     s->vert_edges, s->vert_inst, s->J, s->h, s->colour_edges, s->colour_off, s->last_colour,
                     s->iso, s->inst_vbeg, s->inst_m, s->acc, s->inst_done, s->inst_iters, s->inst_dist,
-                    s->stats, s->ctl, s->rho, s->sign, s->flags, s->rbuf, s->cutbuf};
+                    s->stats, s->ctl, s->rho, s->sign, s->flags, s->rbuf, s->cutbuf, s->xs, s->ps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : s->pending) {
@@ -502,7 +504,8 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         (rc = dalloc(s, &s->inst_dist, B)) || (rc = dalloc(s, &s->stats, 4)) || (rc = dalloc(s, &s->ctl, 1)) ||
         (rc = dalloc(s, &s->rho, (size_t)s->n * 4)) || (rc = dalloc(s, &s->sign, s->n)) ||
         (rc = dalloc(s, &s->flags, 4)) || (rc = dalloc(s, &s->rbuf, 1)) ||
-        (rc = dalloc(s, &s->cutbuf, std::max(s->m, 1)))) {
+        (rc = dalloc(s, &s->cutbuf, std::max(s->m, 1))) || (rc = dalloc(s, &s->xs, s->n)) ||
+        (rc = dalloc(s, &s->ps, s->n))) {
         free_state(s);
         return rc;
     }
@@ -708,6 +711,47 @@ int gtqa_bp_sweep(gtqa_state* s, double tol, int32_t max_iter, uint32_t flags, i
         return GTQA_ERR_NUMERIC;
     }
     return ctl.not_conv > 0 ? GTQA_ERR_NOT_CONVERGED : GTQA_OK;
+}
+
+int gtqa_sample(gtqa_state* s, int32_t k, const int32_t* order, const double* u, double tol, int32_t max_iter,
+                int8_t* x_out, double* p_out) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (k < 0 || k > s->n || (k > 0 && (!order || !u)) || !x_out || max_iter < 1 || !(tol >= 0.0))
+        return GTQA_ERR_INVALID_ARG;
+    std::vector<char> seen(s->n, 0);
+    for (int q = 0; q < k; ++q) {
+        if (order[q] < 0 || order[q] >= s->n || seen[order[q]] || !(u[q] >= 0.0 && u[q] <= 1.0))
+            return GTQA_ERR_INVALID_ARG;
+        seen[order[q]] = 1;
+    }
+    if (!cuda_ok(s, cudaMemsetAsync(s->xs, 0, (size_t)s->n, s->stream))) return GTQA_ERR_CUDA;
+    Ctx c = make_ctx(s);
+    c.phases = PH_BP | PH_WARM;
+    c.k0 = c.k1 = 0;
+    c.tol = tol;
+    c.max_iter = max_iter;
+    for (int q = 0; q < k; ++q) {
+        const cudaError_t e = mixed(s) ? sample_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, order[q], u[q], q,
+                                                             s->xs, s->ps, s->stream)
+                                       : sample_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, order[q], u[q], q,
+                                                            s->xs, s->ps, s->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->sticky = GTQA_ERR_CUDA;
+            return GTQA_ERR_CUDA;
+        }
+        s->launches += 1;
+        // the projection leaves the Vidal gauge: BP from the warm start, then the regauge
+        if ((rc = run(s, c, PK_BP, GTQA_K_BP, s->n)) || (rc = run(s, c, PK_REGAUGE, GTQA_K_REGAUGE, s->m))) return rc;
+    }
+    Control ctl;
+    if ((rc = read_ctl(s, &ctl))) return rc;
+    if (!cuda_ok(s, cudaMemcpyAsync(x_out, s->xs, (size_t)s->n, cudaMemcpyDeviceToHost, s->stream)) ||
+        (p_out && k > 0 && !cuda_ok(s, cudaMemcpyAsync(p_out, s->ps, sizeof(double) * k, cudaMemcpyDeviceToHost, s->stream))) ||
+        !cuda_ok(s, cudaStreamSynchronize(s->stream)))
+        return GTQA_ERR_CUDA;
+    return GTQA_OK;
 }
 
 int gtqa_regauge(gtqa_state* s) {

@@ -86,4 +86,23 @@ cudaError_t residual_launch_fp64(int CHI, const void* G, const double* lam, cons
     }
 }
 
+namespace {
+template <int CHI>
+cudaError_t sample_t(void* G, const double* lam, const int4* ve, int a, double u, int step, int8_t* x, double* p,
+                     cudaStream_t st) {
+    sample_kernel<CHI, ModeFP64><<<1, 32, 0, st>>>((C<typename ModeFP64::TS>*)G, lam, ve, a, u, step, x, p);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t sample_launch_fp64(int CHI, void* G, const double* lam, const int4* ve, int a, double u, int step,
+                                int8_t* x, double* p, cudaStream_t st) {
+    switch (CHI) {
+        case 2: return sample_t<2>(G, lam, ve, a, u, step, x, p, st);
+        case 4: return sample_t<4>(G, lam, ve, a, u, step, x, p, st);
+        case 8: return sample_t<8>(G, lam, ve, a, u, step, x, p, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace gtqa

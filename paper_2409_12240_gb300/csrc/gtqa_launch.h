@@ -44,6 +44,10 @@ GTQA_DECLARE_PHASE(mixed, bp)
 GTQA_DECLARE_PHASE(mixed, regauge)
 #undef GTQA_DECLARE_PHASE
 
+cudaError_t sample_launch_fp64(int CHI, void* Gamma, const double* lam, const int4* vert_edges, int a, double u,
+                               int step, int8_t* x, double* p, cudaStream_t st);
+cudaError_t sample_launch_mixed(int CHI, void* Gamma, const double* lam, const int4* vert_edges, int a, double u,
+                                int step, int8_t* x, double* p, cudaStream_t st);
 cudaError_t residual_launch_fp64(int CHI, const void* Gamma, const double* lam, const int4* vert_edges, int n,
                                  double* out, cudaStream_t st);
 cudaError_t residual_launch_mixed(int CHI, const void* Gamma, const double* lam, const int4* vert_edges, int n,

@@ -36,7 +36,7 @@ EXPORTED = [
     "gtqa_regauge", "gtqa_anneal", "gtqa_marginals", "gtqa_stats", "gtqa_get_state", "gtqa_set_state", "gtqa_sizes",
     "gtqa_edge_colouring", "gtqa_strerror", "gtqa_destroy", "gtqa_profile", "gtqa_profile_read",
     "gtqa_profile_name", "gtqa_alu_peak", "gtqa_debug_barrier", "gtqa_math_check", "gtqa_bp_static",
-    "gtqa_barrier_bench", "gtqa_residual", "gtqa_entropy", "gtqa_spectral_bipartition",
+    "gtqa_barrier_bench", "gtqa_residual", "gtqa_entropy", "gtqa_spectral_bipartition", "gtqa_sample",
 ]
 KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
@@ -91,6 +91,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_marginals": (I32, [P, P, P]),
         "gtqa_residual": (I32, [P, ctypes.POINTER(D)]),
         "gtqa_entropy": (I32, [P, P, ctypes.POINTER(D)]),
+        "gtqa_sample": (I32, [P, I32, P, P, D, I32, P, P]),
         "gtqa_spectral_bipartition": (I32, [I32, I32, P, P, P, ctypes.POINTER(D)]),
         "gtqa_stats": (I32, [P, ctypes.POINTER(gtqa_stats_t)]),
         "gtqa_get_state": (I32, [P, P, P, P]),
@@ -216,6 +217,18 @@ def gtqa_sizes(s: int) -> Tuple[int, int, int, int]:
     n, m, c, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().gtqa_sizes(s, ctypes.byref(n), ctypes.byref(m), ctypes.byref(c), ctypes.byref(k)), "gtqa_sizes")
     return int(n.value), int(m.value), int(c.value), int(k.value)
+
+
+def gtqa_sample(s: int, order, u, tol: float, max_iter: int) -> Tuple[np.ndarray, np.ndarray]:
+    """BP-guided measurement sampling (Sec. IV A); returns (x, p)."""
+    o = np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    n = gtqa_sizes(s)[0]
+    x = np.zeros(n, dtype=np.int8)
+    p = np.zeros(max(o.size, 1), dtype=np.float64)
+    _check(load().gtqa_sample(s, int(o.size), o.ctypes.data, uu.ctypes.data, float(tol), int(max_iter), x.ctypes.data,
+                              p.ctypes.data), "gtqa_sample")
+    return x, p[:o.size]
 
 
 def gtqa_entropy(s: int, cut) -> float:

@@ -270,3 +270,50 @@ def test_entropy_of_spectral_cut_matches_oracle(precision, tol):
         assert max(seen) > 0.05   # the state is entangled across the cut by then
     finally:
         G.gtqa_destroy(s)
+
+
+@pytest.mark.gpu
+def test_sampling_matches_oracle():
+    """BP-guided measurement sampling (Sec. IV A) on the degenerate MaxCut instance
+    (J = -1, h = 0): the same order and random numbers give the oracle's bitstring,
+    conditional probabilities and post-measurement marginals."""
+    G = U.lib()
+    inst = make_instance(12, 4, J="maxcut", h_std=0.0)
+    K, dt, chi, tol, mi = 10, 0.2, 4, 1e-12, 100
+    rng = np.random.default_rng(9)
+    order = rng.permutation(inst.n)
+    u = rng.random(inst.n)
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour)
+    try:
+        st = O.plus_state(inst.n, inst.edges)
+        for k in range(1, K + 1):
+            G.gtqa_trotter_layer(s, k / K, dt)
+            G.gtqa_bp_sweep(s, tol, mi)
+            tZ, tX = O.schedule(k, K, dt)
+            st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, chi, tol, mi)
+        x_g, p_g = G.gtqa_sample(s, order, u, tol, mi)
+        x_o, p_o, st = O.sample_bitstring(st, order.tolist(), u, tol, mi)
+        assert np.array_equal(x_g, x_o)
+        assert np.abs(p_g - p_o).max() < 1e-8, np.abs(p_g - p_o).max()
+        rho_g, _ = G.gtqa_marginals(s)
+        assert np.abs(rho_g - O.reduced_density_matrices(st)).max() < 1e-8
+    finally:
+        G.gtqa_destroy(s)
+
+
+@pytest.mark.gpu
+def test_mixed_sampling_gives_a_consistent_bitstring():
+    G = U.lib()
+    inst = make_instance(16, 5, J="maxcut", h_std=0.0)
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 4, inst.colour, G.gtqa_options_init(precision=G.GTQA_MIXED))
+    try:
+        G.gtqa_anneal(s, 1, 10, 10, 0.2, 1e-8, 100)
+        rng = np.random.default_rng(3)
+        order = rng.permutation(inst.n)
+        x, p = G.gtqa_sample(s, order, rng.random(inst.n), 1e-8, 100)
+        assert set(np.unique(x).tolist()) <= {-1, 1} and np.all(x != 0)
+        assert np.all((p > 0) & (p <= 1 + 1e-6))
+        rho, sign = G.gtqa_marginals(s)   # the post-measurement state is the sampled product state
+        assert np.array_equal(sign, x) and np.abs(np.abs(rho[:, 0, 0].real - 0.5) - 0.5).max() < 1e-4
+    finally:
+        G.gtqa_destroy(s)
