@@ -13,5 +13,8 @@ from .generators import (  # noqa: F401
     make_instance,
     make_tree_instance,
     make_batch,
+    heavy_hex_graph,
+    make_heavy_hex_instance,
+    random_gate_inputs,
     BASE_SEED,
 )

@@ -16,7 +16,7 @@ disjoint vertex pairs, so they commute and may run in one launch.
 from __future__ import annotations
 
 import dataclasses
-from typing import List, Optional
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -70,6 +70,31 @@ def random_tree(n: int, seed: int, max_degree: int = 3) -> np.ndarray:
         deg[k] += 1
     e = np.array(sorted(edges), dtype=np.int32).reshape(-1, 2)
     return e
+
+
+def heavy_hex_graph(rows: int, cols: int) -> Tuple[int, np.ndarray]:
+    """Heavy-hexagon lattice (the degree-2/3 qubit layout of Sec. V's loop study):
+    `rows` chains of `cols` vertices each, and between chains r and r+1 a bridge vertex
+    joined to both chains at every column c with c = 2 (r mod 2) (mod 4).  Bridges
+    above and below a chain sit at columns 2 apart, so every vertex has degree <= 3,
+    every cycle is even, and the shortest cycles (one hexagon: 4 + 4 chain edges, 2 + 2
+    bridge edges) have length 12.  Returns (n, sorted (m, 2) int32 edges)."""
+    if rows < 1 or cols < 1:
+        raise ValueError("rows and cols must be positive")
+    vid = lambda r, c: r * cols + c
+    n = rows * cols
+    edges = []
+    for r in range(rows):
+        for c in range(cols - 1):
+            edges.append((vid(r, c), vid(r, c + 1)))
+    for r in range(rows - 1):
+        for c in range(2 * (r % 2), cols, 4):
+            b = n
+            n += 1
+            edges.append((vid(r, c), b))
+            edges.append((vid(r + 1, c), b))
+    e = np.array(sorted((min(u, v), max(u, v)) for u, v in edges), dtype=np.int32).reshape(-1, 2)
+    return n, e
 
 
 def edge_colouring(n: int, edges: np.ndarray) -> np.ndarray:
@@ -237,6 +262,18 @@ def make_tree_instance(n: int, seed: int, h_std: float = 0.1, base: int = BASE_S
     return Instance(n, edges, Jv, hv, colour, int(seed), kind="tree")
 
 
+def make_heavy_hex_instance(rows: int, cols: int, seed: int, h_std: float = 0.1,
+                            base: int = BASE_SEED) -> Instance:
+    """Heavy-hexagon lattice with Gaussian J ~ N(0,1), h ~ N(0, h_std)."""
+    s = base + 2_000_000 + 3 * int(seed)
+    n, edges = heavy_hex_graph(rows, cols)
+    m = edges.shape[0]
+    Jv = _rng(s + 1).normal(0.0, 1.0, size=m)
+    hv = _rng(s + 2).normal(0.0, h_std, size=n) if h_std > 0 else np.zeros(n)
+    colour = edge_colouring(n, edges)
+    return Instance(n, edges, Jv, hv, colour, int(seed), kind="heavy_hex")
+
+
 def make_batch(B: int, seed: int = 0, n_lo: int = 50, n_hi: int = 1000) -> List[Instance]:
     """B random 3-regular instances with n uniform over even values in [n_lo, n_hi]."""
     rng = _rng(BASE_SEED + 7_000_000 + int(seed))
@@ -248,3 +285,22 @@ def random_messages_input(shape, seed: int) -> np.ndarray:
     """Seeded i.i.d. complex normal matrices (re, im ~ N(0,1)), for random BP starts."""
     rng = _rng(seed)
     return rng.normal(size=shape) + 1j * rng.normal(size=shape)
+
+
+def random_gate_inputs(n: int, m: int, k2: int, k1: int, seed: int):
+    """Seeded inputs for arbitrary-gate circuits: k2 two-qubit gates on uniformly drawn
+    edges (repeats allowed) and k1 one-qubit gates on uniformly drawn vertices, each a
+    Haar-distributed unitary (QR of a complex Gaussian matrix, phases of R's diagonal
+    divided out).  Returns (edge ids (k2,), U (k2, 4, 4), vertex ids (k1,), W (k1, 2, 2))."""
+    rng = _rng(BASE_SEED + 5_000_000 + int(seed))
+
+    def haar(d):
+        A = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+        Q, R = np.linalg.qr(A)
+        return Q * (np.diag(R) / np.abs(np.diag(R)))[None, :]
+
+    e = rng.integers(0, m, size=k2).astype(np.int32)
+    U = np.stack([haar(4) for _ in range(k2)]) if k2 else np.zeros((0, 4, 4), complex)
+    v = rng.integers(0, n, size=k1).astype(np.int32)
+    W = np.stack([haar(2) for _ in range(k1)]) if k1 else np.zeros((0, 2, 2), complex)
+    return e, U, v, W

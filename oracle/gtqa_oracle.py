@@ -20,6 +20,8 @@ Every step follows the paper's notation and order:
 * per-gate fidelity estimate .................. Sec. III D, Eq. (gate_fidelity)
 * mean-field entanglement entropy, bipartition . Sec. III C, Eqs. (bipartition), (mean_field_schmidt), (apprx_entropy)
 * measurement sampling ........................ Sec. IV A, Eq. (projection)
+* other product formulas, arbitrary gates ..... Sec. V (second-order and randomised formulas);
+                                                Sec. II D and App. E (any one- and two-qubit gate)
 
 Readings taken where the paper is silent or ambiguous (each one is listed in the
 design notes of the repository):
@@ -53,6 +55,16 @@ R8  Marginals: Eq. (partial_dens) with the environment of Eq. (bp_approx) built
     from the warm-start messages of the current Vidal-gauge state, i.e.
     rho_a = sum Gamma Gamma^* prod_b lambda_ba^2, divided by its trace.
 R9  Read-out tie rho_a[0,0] = 1/2 maps to -1 (literal "otherwise").
+R10 Product formulas beyond first order (the paper names them only as an
+    outlook, Sec. V): a layer is U_X(t_post) U_Z(t_Z) U_X(t_pre).  First order
+    (R1) is (t_pre, t_post) = (0, t_X); the second-order symmetric (Strang)
+    formula is (t_X/2, t_X/2) at the same tau_k; the randomised first-order
+    formula draws, per layer, the forward (0, t_X) or the reversed (t_X, 0)
+    ordering with probability 1/2 each (the caller supplies the draws).
+R11 Arbitrary two-qubit gate on edge e = {a, b} with a = edges[e][0]: a 4x4
+    matrix W[(i_a i_b), (i_a' i_b')] (row index 2 i_a + i_b), applied by the
+    same simple update as the Ising gate (App. E); gates are applied in the
+    order given.
 """
 from __future__ import annotations
 
@@ -236,10 +248,16 @@ def simple_update(st: VidalState, e: int, W: np.ndarray, chi: int,
 
 
 def trotter_layer(st: VidalState, colour: np.ndarray, J: np.ndarray, h: np.ndarray,
-                  t_Z: float, t_X: float, chi: int, svd_cutoff: float = SVD_CUTOFF) -> Dict[str, float]:
-    """U_X(t_X) U_Z(t_Z) of Eq. (discretizatoion): every edge gate of the
-    interaction layer (colour classes ascending, reading R2), then the mixing
+                  t_Z: float, t_X: float, chi: int, svd_cutoff: float = SVD_CUTOFF,
+                  t_X_pre: float = 0.0) -> Dict[str, float]:
+    """U_X(t_X) U_Z(t_Z) U_X(t_X_pre) of Eq. (discretizatoion) and reading R10: the
+    leading mixing gate on every qubit (skipped for t_X_pre = 0), every edge gate of
+    the interaction layer (colour classes ascending, reading R2), then the mixing
     gate on every qubit."""
+    if t_X_pre != 0.0:
+        Wp = mixing_gate(t_X_pre)
+        for a in range(st.n):
+            apply_single_qubit_gate(st, a, Wp)
     deg = [len(x) for x in st.inc]
     order = sorted(range(st.m), key=lambda e: (int(colour[e]), e))
     disc, logf = 0.0, 0.0
@@ -497,11 +515,21 @@ def objective(edges: np.ndarray, J: np.ndarray, h: np.ndarray, x: np.ndarray) ->
 # --------------------------------------------------------------------------
 def gtqa_layer(st: VidalState, colour, J, h, t_Z: float, t_X: float, chi: int,
                tol: float, max_iter: int, schedule: str = "flooding",
-               svd_cutoff: float = SVD_CUTOFF, eig_cutoff: float = EIG_CUTOFF) -> Tuple[VidalState, Dict]:
+               svd_cutoff: float = SVD_CUTOFF, eig_cutoff: float = EIG_CUTOFF,
+               t_X_pre: float = 0.0) -> Tuple[VidalState, Dict]:
     """One GTQA layer: Trotter layer (gates + truncation, mixing), then regauging
     by (i) symmetric split, (ii) BP from warm-start messages, (iii) Vidal gauge
     from the messages (Sec. II C)."""
-    info = trotter_layer(st, colour, J, h, t_Z, t_X, chi, svd_cutoff)
+    info = trotter_layer(st, colour, J, h, t_Z, t_X, chi, svd_cutoff, t_X_pre)
+    return regauge(st, tol, max_iter, schedule, svd_cutoff, eig_cutoff, info)
+
+
+def regauge(st: VidalState, tol: float, max_iter: int, schedule: str = "flooding",
+            svd_cutoff: float = SVD_CUTOFF, eig_cutoff: float = EIG_CUTOFF,
+            info: Optional[Dict] = None) -> Tuple[VidalState, Dict]:
+    """Sec. II C: symmetric split, BP from the warm-start messages, Vidal gauge from
+    the converged messages."""
+    info = {} if info is None else info
     T = symmetric_gauge(st)
     msgs, iters, hist = bp(st, T, reconstructed_messages(st), tol, max_iter, schedule)
     new = vidal_gauge(st, T, msgs, eig_cutoff, svd_cutoff)
@@ -509,17 +537,53 @@ def gtqa_layer(st: VidalState, colour, J, h, t_Z: float, t_X: float, chi: int,
     return new, info
 
 
+def product_formula(k: int, K: int, dt: float, order: int = 1, reverse: bool = False) -> Tuple[float, float, float]:
+    """Angles (t_X_pre, t_Z, t_X_post) of layer k under reading R10 (Sec. V).
+
+    order 1: (0, t_Z, t_X), or (t_X, t_Z, 0) when `reverse` (one draw of the randomised
+    first-order formula); order 2: the symmetric formula (t_X/2, t_Z, t_X/2).
+    """
+    t_Z, t_X = schedule(k, K, dt)
+    if order == 1:
+        return (t_X, t_Z, 0.0) if reverse else (0.0, t_Z, t_X)
+    if order == 2:
+        if reverse:
+            raise ValueError("the symmetric formula has no reversed form")
+        return 0.5 * t_X, t_Z, 0.5 * t_X
+    raise ValueError("order must be 1 or 2")
+
+
+def apply_gates(st: VidalState, gates: Sequence[Tuple[int, np.ndarray]], chi: int,
+                svd_cutoff: float = SVD_CUTOFF) -> Dict[str, float]:
+    """Reading R11: arbitrary two-qubit gates (edge e, 4x4 matrix) in the order given,
+    each by the simple update with truncation to chi (App. E)."""
+    disc, logf = 0.0, 0.0
+    for e, W in gates:
+        r = simple_update(st, int(e), np.asarray(W, dtype=np.complex128).reshape(2, 2, 2, 2), chi, svd_cutoff)
+        disc += r["discarded"]
+        logf += np.log(r["fidelity"]) if r["fidelity"] > 0 else -np.inf
+    return {"discarded": disc, "log_fidelity": logf}
+
+
+def apply_single_qubit_gates(st: VidalState, gates: Sequence[Tuple[int, np.ndarray]]) -> None:
+    """Sec. II D: one-qubit gates (vertex a, 2x2 matrix) in the order given."""
+    for a, W in gates:
+        apply_single_qubit_gate(st, int(a), np.asarray(W, dtype=np.complex128))
+
+
 def run(n: int, edges, J, h, colour, K: int, dt: float, chi: int, tol: float, max_iter: int,
         layers: Optional[int] = None, record: bool = False, state: Optional[VidalState] = None,
-        k0: int = 0):
+        k0: int = 0, order: int = 1, reverse: Optional[Sequence[bool]] = None):
     """Run layers k0+1 .. k0+layers (default all K) of the anneal from |+>^N
-    (or from `state`).  Returns the final state and per-layer info."""
+    (or from `state`) with the product formula of reading R10 (`reverse[i]` is the
+    draw of layer k0+1+i).  Returns the final state and per-layer info."""
     st = plus_state(n, np.asarray(edges)) if state is None else state
     infos = []
     last = K if layers is None else min(K, k0 + layers)
     for k in range(k0 + 1, last + 1):
-        t_Z, t_X = schedule(k, K, dt)
-        st, info = gtqa_layer(st, colour, J, h, t_Z, t_X, chi, tol, max_iter)
+        rev = bool(reverse[k - k0 - 1]) if reverse is not None else False
+        t_pre, t_Z, t_X = product_formula(k, K, dt, order, rev)
+        st, info = gtqa_layer(st, colour, J, h, t_Z, t_X, chi, tol, max_iter, t_X_pre=t_pre)
         if record:
             info["rho"] = reduced_density_matrices(st)
         info.pop("T", None)

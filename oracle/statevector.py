@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY (pins for the GTQA oracle; never used by the library).
 
 The circuit is Eq. (discretizatoion) of App. F with reading R1 of the oracle
 (layer k applies U_Z(dt*k/K) then U_X(dt*(1-k/K)), k = 1..K), starting from
-|+>^N (Sec. III A).  U_Z is the product of the commuting diagonal two-qubit gates
+|+>^N (Sec. III A); `evolve_split` takes any per-layer angles
+(t_X_pre, t_Z, t_X_post) (reading R10), and `apply_one` / `apply_two` apply
+arbitrary one- and two-qubit gates (reading R11).  U_Z is the product of the commuting diagonal two-qubit gates
 exp(-i t (J_ab Z_a Z_b + h_a/D_a Z_a + h_b/D_b Z_b)), U_X the product of
 exp(-i t X_a).  Qubit a is tensor axis a; |0> has Z eigenvalue +1 (x_a = +1,
 Sec. III A).
@@ -77,6 +79,35 @@ def evolve(n: int, edges, J, h, K: int, dt: float, layers: int | None = None,
         tau = k / K
         psi = psi * np.exp(-1j * dt * tau * E)
         psi = apply_mixing(psi, dt * (1.0 - tau))
+        if record:
+            rhos.append(all_rdm1(psi))
+    return psi, rhos
+
+
+def apply_one(psi: np.ndarray, a: int, W: np.ndarray) -> np.ndarray:
+    """psi'[.., i_a, ..] = sum_i' W[i_a, i'] psi[.., i', ..]."""
+    return np.moveaxis(np.tensordot(np.asarray(W), psi, axes=([1], [a])), 0, a)
+
+
+def apply_two(psi: np.ndarray, a: int, b: int, W: np.ndarray) -> np.ndarray:
+    """A 4x4 gate W[(i_a i_b), (i_a' i_b')] on qubits a and b."""
+    W4 = np.asarray(W).reshape(2, 2, 2, 2)
+    out = np.tensordot(W4, psi, axes=([2, 3], [a, b]))
+    return np.moveaxis(out, [0, 1], [a, b])
+
+
+def evolve_split(n: int, edges, J, h, angles, record: bool = True):
+    """Layers U_X(t_post) U_Z(t_Z) U_X(t_pre) for each (t_pre, t_Z, t_post) in `angles`.
+    Returns (psi, [rho per layer])."""
+    E = interaction_phase(n, edges, J, h)
+    psi = plus_state(n)
+    rhos: List[np.ndarray] = []
+    for t_pre, t_Z, t_post in angles:
+        if t_pre != 0.0:
+            psi = apply_mixing(psi, t_pre)
+        psi = psi * np.exp(-1j * t_Z * E)
+        if t_post != 0.0:
+            psi = apply_mixing(psi, t_post)
         if record:
             rhos.append(all_rdm1(psi))
     return psi, rhos

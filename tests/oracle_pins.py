@@ -399,3 +399,134 @@ def tree_sampling_chain_rule(seed: int, n: int = 8, K: int = 4, dt: float = 0.4)
     idx = tuple(0 if xa == 1 else 1 for xa in x)
     born = abs(psi[idx]) ** 2 / np.sum(np.abs(psi) ** 2)
     return float(abs(np.prod(p) - born) / born)
+
+
+# --------------------------------------------------------------------------
+# product formulas and arbitrary gates (Sec. V; Sec. II D, App. E)
+# --------------------------------------------------------------------------
+def _one_layer_error(n, edges, J, h, tau, dt, order, mode):
+    """Distance after one layer from |+>^n between the product formula and
+    expm(-i dt (tau H_Z + (1 - tau) H_X)).  mode "fwd"/"rev" compares states, mode "avg"
+    compares the density matrix averaged over the two orderings (randomised formula)."""
+    E = SV.interaction_phase(n, edges, J, h).reshape(-1)
+    ops = lambda P, q: np.kron(np.kron(np.eye(2 ** q), P), np.eye(2 ** (n - q - 1)))
+    HX = sum(ops(X, a) for a in range(n))
+    U = scipy.linalg.expm(-1j * dt * (tau * np.diag(E) + (1 - tau) * HX))
+    psi0 = np.full(2 ** n, 2 ** (-n / 2), dtype=complex)
+    exact = U @ psi0
+    K = 10
+    k = int(round(tau * K))
+    dt_l = dt
+
+    def layer(rev):
+        ang = O.product_formula(k, K, dt_l, order, rev)
+        psi, _ = SV.evolve_split(n, edges, J, h, [ang], record=False)
+        return psi.reshape(-1)
+
+    if mode == "avg":
+        pf, pr = layer(False), layer(True)
+        rho = 0.5 * (np.outer(pf, pf.conj()) + np.outer(pr, pr.conj()))
+        return float(np.linalg.norm(rho - np.outer(exact, exact.conj())))
+    psi = layer(mode == "rev")
+    return float(np.linalg.norm(psi - exact))
+
+
+def product_formula_orders(seed: int = 0) -> dict:
+    """Local error of one layer against the matrix exponential of the layer's
+    Hamiltonian (reading R10): the first-order formula (either ordering) errs by O(dt^2),
+    the symmetric formula and the average over the two first-order orderings (the
+    randomised formula, as a channel) by O(dt^3).  Returns e(dt)/e(dt/2) per formula
+    (about 4 and 8)."""
+    inst = make_instance(6, seed)
+    out = {}
+    for name, order, mode in (("first", 1, "fwd"), ("first_rev", 1, "rev"), ("second", 2, "fwd"),
+                              ("randomised", 1, "avg")):
+        e1 = _one_layer_error(inst.n, inst.edges, inst.J, inst.h, 0.4, 0.08, order, mode)
+        e2 = _one_layer_error(inst.n, inst.edges, inst.J, inst.h, 0.4, 0.04, order, mode)
+        out[name] = e1 / e2
+    return out
+
+
+def tree_product_formula_exact(seed: int, order: int, n: int = 10, K: int = 6, dt: float = 0.3) -> float:
+    """On a tree without truncation the GTQA marginals under the second-order or the
+    randomised first-order formula equal the exact ones layer by layer (Sec. II B, R10)."""
+    inst = make_tree_instance(n, seed)
+    rng = np.random.default_rng(seed + 99)
+    rev = [bool(x) for x in rng.integers(0, 2, size=K)] if order == 1 else [False] * K
+    angles = [O.product_formula(k, K, dt, order, rev[k - 1]) for k in range(1, K + 1)]
+    _, rhos = SV.evolve_split(inst.n, inst.edges, inst.J, inst.h, angles)
+    st = O.plus_state(inst.n, inst.edges)
+    err = 0.0
+    for k in range(1, K + 1):
+        t_pre, tZ, tX = angles[k - 1]
+        st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 256, 1e-13, 100, t_X_pre=t_pre)
+        err = max(err, float(np.abs(O.reduced_density_matrices(st) - rhos[k - 1]).max()))
+    return err
+
+
+def random_unitary(rng: np.random.Generator, d: int) -> np.ndarray:
+    """Haar-distributed d x d unitary (QR of a complex Gaussian matrix with the phases of
+    R's diagonal divided out)."""
+    A = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    Q, R = np.linalg.qr(A)
+    return Q * (np.diag(R) / np.abs(np.diag(R)))[None, :]
+
+
+def random_gate_list(rng: np.random.Generator, m: int, k: int):
+    """k gates on uniformly drawn edges (repeats allowed), Haar 4x4 unitaries."""
+    return [(int(rng.integers(m)), random_unitary(rng, 4)) for _ in range(k)]
+
+
+def general_gates_exact(seed: int = 0, n: int = 8, k: int = 14) -> dict:
+    """Arbitrary two- and one-qubit gates on a tree without truncation reproduce the
+    exact state (reading R11); after the regauge (exact BP on a tree) the marginals are
+    the exact ones."""
+    inst = make_tree_instance(n, seed)
+    rng = np.random.default_rng(seed + 7)
+    st = O.plus_state(inst.n, inst.edges)
+    psi = SV.plus_state(inst.n)
+    for rnd in range(2):
+        gates = random_gate_list(rng, inst.m, k)
+        singles = [(int(rng.integers(inst.n)), random_unitary(rng, 2)) for _ in range(n)]
+        O.apply_gates(st, gates, 256)
+        O.apply_single_qubit_gates(st, singles)
+        for e, W in gates:
+            a, b = (int(x) for x in inst.edges[e])
+            psi = SV.apply_two(psi, a, b, W)
+        for a, W in singles:
+            psi = SV.apply_one(psi, a, W)
+    state_err = _overlap_err(O.to_statevector(st), psi)
+    new, _ = O.regauge(st, 1e-13, 200)
+    rho_err = float(np.abs(O.reduced_density_matrices(new) - SV.all_rdm1(psi)).max())
+    return {"state": state_err, "rho": rho_err}
+
+
+def general_gate_truncation_fidelity(seed: int = 0, n: int = 10) -> float:
+    """On a tree in the Vidal gauge, one arbitrary gate followed by truncation to chi keeps
+    the optimal rank-chi Schmidt approximation: w, the discarded weight, is the weight of
+    the smallest exact Schmidt values across the edge, and |<psi|psi_trunc>|^2 = 1 - w
+    (Sec. II C, App. E, Eq. (gate_fidelity))."""
+    inst = make_tree_instance(n, seed)
+    rng = np.random.default_rng(seed + 3)
+    st = O.plus_state(inst.n, inst.edges)
+    O.apply_gates(st, random_gate_list(rng, inst.m, 3 * inst.m), 256)
+    st, _ = O.regauge(st, 1e-14, 300)
+    err = 0.0
+    for e in range(inst.m):
+        d = st.lam[e].size
+        if d < 2:
+            continue
+        W = random_unitary(rng, 4)
+        ref = O.VidalState(st.n, st.edges, st.inc, [g.copy() for g in st.Gamma], [l.copy() for l in st.lam])
+        O.apply_gates(ref, [(e, W)], 256)
+        cut = O.VidalState(st.n, st.edges, st.inc, [g.copy() for g in st.Gamma], [l.copy() for l in st.lam])
+        r = O.apply_gates(cut, [(e, W)], max(1, ref.lam[e].size - 1))
+        psi = O.to_statevector(ref)
+        a = psi.reshape(-1)
+        b = O.to_statevector(cut).reshape(-1)
+        ov = abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+        # the discarded weight is that of the smallest exact Schmidt values across e
+        sv = SV.schmidt_values(psi / np.linalg.norm(a), _component(inst, e, int(inst.edges[e][0])))
+        w_opt = float(np.sum(sv[ref.lam[e].size - 1:] ** 2))
+        err = max(err, abs(ov - (1.0 - r["discarded"])), abs(r["discarded"] - w_opt))
+    return float(err)

@@ -63,3 +63,54 @@ def test_batch_sizes_even_in_range():
     b = make_batch(8, seed=0)
     assert len(b) == 8
     assert all(50 <= x.n <= 1000 and x.n % 2 == 0 for x in b)
+
+
+@pytest.mark.parametrize("rows,cols", [(3, 9), (7, 15), (12, 27)])
+def test_heavy_hex_lattice_structure(rows, cols):
+    """Degree <= 3, connected, bipartite (all cycles even), shortest cycle 12."""
+    from instances import heavy_hex_graph
+    n, edges = heavy_hex_graph(rows, cols)
+    deg = np.bincount(edges.ravel(), minlength=n)
+    assert deg.max() <= 3 and deg.min() >= 1
+    adj = [[] for _ in range(n)]
+    for u, v in edges.tolist():
+        adj[u].append(v)
+        adj[v].append(u)
+    colour = -np.ones(n, dtype=int)
+    colour[0] = 0
+    queue = [0]
+    while queue:
+        u = queue.pop()
+        for v in adj[u]:
+            if colour[v] < 0:
+                colour[v] = 1 - colour[u]
+                queue.append(v)
+            assert colour[v] != colour[u]
+    assert (colour >= 0).all()
+    # girth by BFS from every vertex
+    girth = np.inf
+    for s in range(n):
+        dist = {s: 0}
+        parent = {s: -1}
+        q = [s]
+        for u in q:
+            for v in adj[u]:
+                if v not in dist:
+                    dist[v] = dist[u] + 1
+                    parent[v] = u
+                    q.append(v)
+                elif parent[u] != v:
+                    girth = min(girth, dist[u] + dist[v] + 1)
+    assert girth == 12
+    c = edge_colouring(n, edges)
+    assert check_colouring(n, edges, c)
+
+
+def test_random_gate_inputs_are_unitary_and_seeded():
+    from instances import random_gate_inputs
+    e, U, v, W = random_gate_inputs(10, 12, 20, 7, seed=3)
+    assert e.min() >= 0 and e.max() < 12 and v.min() >= 0 and v.max() < 10
+    assert np.abs(U @ np.conj(np.swapaxes(U, 1, 2)) - np.eye(4)).max() < 1e-12
+    assert np.abs(W @ np.conj(np.swapaxes(W, 1, 2)) - np.eye(2)).max() < 1e-12
+    e2, U2, _, _ = random_gate_inputs(10, 12, 20, 7, seed=3)
+    assert np.array_equal(e, e2) and np.array_equal(U, U2)

@@ -90,3 +90,56 @@ def test_wrong_symmetric_split_caught(monkeypatch):
         return T
     monkeypatch.setattr(O, "symmetric_gauge", bad)
     assert P.gtqa_tree_exact(0)["rho"] > 1e-6
+
+
+def test_lopsided_symmetric_formula_caught(monkeypatch):
+    orig = O.product_formula
+
+    def bad(k, K, dt, order=1, reverse=False):
+        p, z, q = orig(k, K, dt, order, reverse)
+        return (p, z, 2 * q) if order == 2 else (p, z, q)    # t_X/2 before, t_X after
+    monkeypatch.setattr(O, "product_formula", bad)
+    r = P.product_formula_orders(0)
+    assert not (7.0 < r["second"] < 9.0)
+
+
+def test_dropped_leading_mixing_caught(monkeypatch):
+    orig = O.trotter_layer
+
+    def bad(st, colour, J, h, t_Z, t_X, chi, svd_cutoff=O.SVD_CUTOFF, t_X_pre=0.0):
+        return orig(st, colour, J, h, t_Z, t_X, chi, svd_cutoff, 0.0)
+    monkeypatch.setattr(O, "trotter_layer", bad)
+    assert P.tree_product_formula_exact(0, 2) > 1e-6
+
+
+def test_transposed_two_qubit_gate_caught(monkeypatch):
+    orig = O.simple_update
+
+    def bad(st, e, W, chi, svd_cutoff=O.SVD_CUTOFF):
+        return orig(st, e, np.transpose(W, (2, 3, 0, 1)), chi, svd_cutoff)
+    monkeypatch.setattr(O, "simple_update", bad)
+    assert P.general_gates_exact(0)["state"] > 1e-6
+
+
+def test_swapped_gate_qubits_caught(monkeypatch):
+    orig = O.simple_update
+
+    def bad(st, e, W, chi, svd_cutoff=O.SVD_CUTOFF):
+        return orig(st, e, np.transpose(W, (1, 0, 3, 2)), chi, svd_cutoff)
+    monkeypatch.setattr(O, "simple_update", bad)
+    assert P.general_gates_exact(0)["state"] > 1e-6
+
+
+def test_truncation_keeping_the_smallest_values_caught(monkeypatch):
+    svd = np.linalg.svd
+
+    def bad_svd(a, *args, **kw):
+        r = svd(a, *args, **kw)
+        if isinstance(r, tuple) or hasattr(r, "U"):
+            U, s, Vh = r
+            k = int(np.sum(s > 1e-12 * s[0]))
+            idx = np.r_[np.arange(k)[::-1], np.arange(k, s.size)]
+            return U[:, idx], s[idx], Vh[idx, :]
+        return r
+    monkeypatch.setattr(O, "np", _np_with(svd=bad_svd))
+    assert P.general_gate_truncation_fidelity(0) > 1e-6

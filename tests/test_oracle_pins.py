@@ -182,3 +182,27 @@ def test_sampling_a_product_state_follows_its_marginals():
     expect = np.where(u < rho[:, 0, 0].real, rho[:, 0, 0].real, rho[:, 1, 1].real)
     assert np.abs(p - expect).max() < 1e-12
     assert np.array_equal(x, np.where(u < rho[:, 0, 0].real, 1, -1))
+
+
+def test_product_formula_error_orders():
+    r = P.product_formula_orders(0)
+    assert 3.5 < r["first"] < 4.5 and 3.5 < r["first_rev"] < 4.5, r
+    assert 7.0 < r["second"] < 9.0, r
+    assert 7.0 < r["randomised"] < 9.5, r
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tree_product_formulas_exact(order, seed):
+    assert P.tree_product_formula_exact(seed, order) < 1e-10
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_general_gates_exact_on_trees(seed):
+    r = P.general_gates_exact(seed)
+    assert r["state"] < 1e-10 and r["rho"] < 1e-10, r
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_general_gate_truncation_keeps_optimal_schmidt_approximation(seed):
+    assert P.general_gate_truncation_fidelity(seed) < 1e-10
