@@ -164,6 +164,61 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
                 int32_t max_iter);
 
 /*
+ * One Trotter layer in split form U_X(t_X_post) U_Z(t_Z) U_X(t_X_pre): the mixing gate
+ * exp(-i t_X_pre X) on every vertex, then every edge gate of U_Z(t_Z) by the simple update
+ * with truncation (App. E, App. D "Truncation"), then exp(-i t_X_post X) on every vertex
+ * (Sec. II D).  gtqa_trotter_layer(tau, dt) is (0, dt tau, dt (1 - tau)).  The building
+ * block of the product formulas beyond first order that Sec. V names.  Asynchronous.
+ * Returns GTQA_ERR_INVALID_ARG for a non-finite angle.
+ */
+int gtqa_trotter_split(gtqa_state* s, double t_Z, double t_X_pre, double t_X_post);
+
+#define GTQA_TROTTER_FIRST 1      /* U_X(t_X) U_Z(t_Z); reversed: U_Z(t_Z) U_X(t_X) */
+#define GTQA_TROTTER_SYMMETRIC 2  /* U_X(t_X/2) U_Z(t_Z) U_X(t_X/2), second order */
+
+/*
+ * gtqa_anneal with a choice of product formula (Sec. V: higher-order and randomised
+ * formulas).  Layer k (t_Z = dt k/K, t_X = dt (1 - k/K)) is gtqa_trotter_split with
+ *   GTQA_TROTTER_FIRST:     (t_X_pre, t_X_post) = (0, t_X), or (t_X, 0) when reverse is
+ *                           non-NULL and reverse[k - k_begin] != 0; drawing reverse[] as
+ *                           fair coin flips gives the randomised first-order formula;
+ *   GTQA_TROTTER_SYMMETRIC: (t_X/2, t_X/2); reverse must be NULL;
+ * followed by BP from the warm start and the regauge, as in gtqa_anneal.  reverse is a
+ * host array of k_end - k_begin + 1 bytes, read before the call returns.  Asynchronous.
+ * Returns GTQA_ERR_INVALID_ARG for a bad range, order, or a reverse array with the
+ * symmetric formula.
+ */
+int gtqa_anneal_ex(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double dt, double tol,
+                   int32_t max_iter, int32_t order, const uint8_t* reverse);
+
+/*
+ * Arbitrary two-qubit gates (Sec. II D, App. E): gate q acts on edge edge[q] = {u, v}, u and
+ * v its endpoints in the order given at creation, with the 4x4 complex matrix
+ * U[q][r][c] (r = 2 i_u + i_v, c = 2 i_u' + i_v'; host array of k x 16 complex128 as
+ * interleaved re, im pairs, row-major).  Each gate is a simple update of the edge's bond
+ * with truncation to chi (App. D "Truncation"); U need not be unitary.  Gates are applied in
+ * list order: the host packs them into launches of gates with disjoint endpoints, a gate
+ * going one launch after the latest earlier gate that shares a vertex with it, so the
+ * result is that of the sequential list.  QR and SVD in FP64 in both precision modes.
+ * Like gtqa_trotter_layer the call leaves the state out of the Vidal gauge: follow it with
+ * gtqa_bp_sweep(..., GTQA_BP_DEFAULT) before reading marginals.  The discarded weight and
+ * log-fidelity of each gate go to gtqa_stats.  Asynchronous; edge and U are read before
+ * the call returns.  Returns GTQA_ERR_INVALID_ARG for k < 0, an edge outside [0, m) (global
+ * ids in a batched state) or a non-finite entry.
+ */
+int gtqa_apply_gates(gtqa_state* s, int32_t k, const int32_t* edge, const double* U);
+
+/*
+ * Arbitrary one-qubit gates (Sec. II D): Gamma_a[i] <- sum_i' W[q][i][i'] Gamma_a[i'] for
+ * a = vertex[q], in list order (W: host array of k x 4 complex128, interleaved, row-major).
+ * Gates on one vertex are composed on the host, then one launch applies every vertex's
+ * product.  No truncation and no change of gauge class: the Vidal gauge is kept.
+ * Asynchronous; returns GTQA_ERR_INVALID_ARG for k < 0, a vertex outside [0, n) or a
+ * non-finite entry.
+ */
+int gtqa_apply_single_qubit_gates(gtqa_state* s, int32_t k, const int32_t* vertex, const double* W);
+
+/*
  * BP-guided measurement sampling of a bitstring (Sec. IV A), for problems whose solutions
  * are degenerate so that the read-out of Eq. (rounding_rule) does not decide.  For each
  * qubit a = order[q], q = 0..k-1, in turn: rho_a of the current Vidal-gauge state gives the

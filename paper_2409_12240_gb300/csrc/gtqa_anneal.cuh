@@ -4,7 +4,9 @@
 //   gates      for each colour class: simple update + truncation of every edge of
 //              that matching (App. E, App. D "Truncation"); the mixing gate
 //              exp(-i t_X X) (Sec. II D) is applied to a vertex right after its last
-//              gate of the layer.
+//              gate of the layer, and a leading mixing gate exp(-i t_pre X) (the
+//              second-order and reversed first-order product formulas of Sec. V)
+//              right before its first gate.
 //   bp init    T_a = Gamma_a prod lambda^{1/2} (Eq. (symmetric_gauge)); warm-start
 //              messages diag(lambda)/sum(lambda) (Eq. (reconstructed_messages)).
 //   bp sweeps  flooding update of every directed message, Eq. (local_consistency),
@@ -64,6 +66,7 @@ struct Ctx {
     const int* colour_edges;
     const int* colour_off;    // [ncol + 1]
     const int* last_colour;   // per vertex: colour of its last gate in a layer (-1: none)
+    const int* first_colour;  // per vertex: colour of its first gate in a layer (-1: none)
     const int* iso;           // vertices of degree 0
     int n_iso;
     int ncol;
@@ -92,6 +95,7 @@ struct Ctx {
     unsigned phases;
     int k0, k1, Ksched;       // layers k0..k1 with tau = k/Ksched; Ksched = 0: one layer at (tZ1, tX1)
     double dt, tZ1, tX1;
+    double tXpre1;            // Ksched = 0: leading mixing angle of the layer (0: none)
     int nblocks;
     int bar_expect;           // arrivals per grid barrier (= nblocks; larger only in the timeout test)
     long long spin_limit;
@@ -143,7 +147,7 @@ struct GateSm {
 
 template <int CHI, class Mode>
 __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& sm, double tZ, double cX, double sX,
-                          int colour) {
+                          int colour, bool pre, double cXp, double sXp) {
     using TS = typename Mode::TS;
     constexpr int NM = 2 * CHI, NR = CHI * CHI, G = NR / 2, TEAM = 2 * CHI * CHI;
     C<TS>* Gam = (C<TS>*)c.Gamma;
@@ -164,15 +168,22 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
     }
     for (int t = tid; t < CHI; t += TEAM) sm.lab[t] = __ldcg(c.lam + (size_t)e * CHI + t);
     team_bar<TEAM>(team);
-    for (int t = tid; t < 4 * CHI * NR; t += TEAM) {
-        const int blk = t / (CHI * NR), rem = t % (CHI * NR);
+    // both physical components of one element per thread, so that the leading mixing
+    // gate [[c, -i s], [-i s, c]] can act on a vertex before its first gate of the layer
+    for (int t = tid; t < 2 * CHI * NR; t += TEAM) {
+        const int x = t / (CHI * NR), rem = t % (CHI * NR);
         const int col = rem / NR, row = rem % NR;
-        const int x = blk >> 1, i = blk & 1;
-        const size_t off = (size_t)vtx[x] * (2 * CHI * CHI * CHI) + (size_t)i * CHI * CHI * CHI +
-                           col * sstride<CHI>(slot[x]) + (row / CHI) * sstride<CHI>(os[x][0]) +
-                           (row % CHI) * sstride<CHI>(os[x][1]);
-        const cd gv = ccast<double>(ldcg(Gam + off));
-        sm.X[blk][col][row] = sm.w[x][row] * gv;
+        const size_t off = (size_t)vtx[x] * (2 * CHI * CHI * CHI) + col * sstride<CHI>(slot[x]) +
+                           (row / CHI) * sstride<CHI>(os[x][0]) + (row % CHI) * sstride<CHI>(os[x][1]);
+        cd g0 = ccast<double>(ldcg(Gam + off));
+        cd g1 = ccast<double>(ldcg(Gam + off + CHI * CHI * CHI));
+        if (pre && c.first_colour[vtx[x]] == colour) {
+            const cd a0 = g0, a1 = g1;
+            g0 = cd{cXp * a0.x + sXp * a1.y, cXp * a0.y - sXp * a1.x};
+            g1 = cd{sXp * a0.y + cXp * a1.x, -sXp * a0.x + cXp * a1.y};
+        }
+        sm.X[2 * x][col][row] = sm.w[x][row] * g0;
+        sm.X[2 * x + 1][col][row] = sm.w[x][row] * g1;
     }
     team_bar<TEAM>(team);
 
@@ -1148,21 +1159,28 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
         double sX, cX;
         sincos(tX, &sX, &cX);
         if constexpr ((PH & PH_GATES) != 0u) {
+            const double tXp = c.Ksched > 0 ? 0.0 : c.tXpre1;
+            const bool pre = tXp != 0.0;
+            double sXp = 0.0, cXp = 1.0, sXi = sX, cXi = cX;
+            if (pre) {
+                sincos(tXp, &sXp, &cXp);
+                sincos(tX + tXp, &sXi, &cXi);   // vertices without gates: both mixing gates at once
+            }
             const int team = threadIdx.x / S::TG, tid = threadIdx.x % S::TG;
             GateSm<CHI>& sm = reinterpret_cast<GateSm<CHI>*>(smem)[team];
             const int gteam = team * c.nblocks + blockIdx.x;
             for (int col = 0; col < c.ncol; ++col) {
                 const int beg = c.colour_off[col], end = c.colour_off[col + 1];
                 for (int idx = beg + gteam; idx < end; idx += nteams_total_g)
-                    gate_edge<CHI, Mode>(c, c.colour_edges[idx], tid, team, sm, tZ, cX, sX, col);
+                    gate_edge<CHI, Mode>(c, c.colour_edges[idx], tid, team, sm, tZ, cX, sX, col, pre, cXp, sXp);
                 if (col == c.ncol - 1)
                     for (int q = gteam; q < c.n_iso; q += nteams_total_g)
-                        mixing_vertex<CHI, Mode>(c, c.iso[q], tid, S::TG, cX, sX);
+                        mixing_vertex<CHI, Mode>(c, c.iso[q], tid, S::TG, cXi, sXi);
                 if (!grid_sync(gb, c.spin_limit)) return;
             }
             if (c.ncol == 0) {
                 for (int q = gteam; q < c.n_iso; q += nteams_total_g)
-                    mixing_vertex<CHI, Mode>(c, c.iso[q], tid, S::TG, cX, sX);
+                    mixing_vertex<CHI, Mode>(c, c.iso[q], tid, S::TG, cXi, sXi);
                 if (!grid_sync(gb, c.spin_limit)) return;
             }
         }

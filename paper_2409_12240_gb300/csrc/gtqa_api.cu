@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -38,6 +39,7 @@ struct gtqa_state {
     int* colour_edges = nullptr;
     int* colour_off = nullptr;
     int* last_colour = nullptr;
+    int* first_colour = nullptr;
     int* iso = nullptr;
     int n_iso = 0;
     int* inst_vbeg = nullptr;
@@ -55,6 +57,13 @@ struct gtqa_state {
     unsigned char* cutbuf = nullptr;   // entropy: per-edge cut mask
     int8_t* xs = nullptr;       // sampling: outcomes [n]
     double* ps = nullptr;       // sampling: outcome probabilities [n]
+    int* gate_edge = nullptr;   // arbitrary gates: edge ids grouped by launch, and their matrices
+    cd* gate_U = nullptr;
+    size_t gate_cap = 0;
+    int* sq_vertex = nullptr;   // one-qubit gates: vertices and composed 2x2 matrices
+    cd* sq_W = nullptr;
+    size_t sq_cap = 0;
+    std::vector<int> h_edges;   // endpoints of every edge (2m), for host-side scheduling
     // host counters
     long long layers = 0, gates = 0, launches = 0;
     int sticky = GTQA_OK;
@@ -93,6 +102,21 @@ int dalloc(gtqa_state* s, T** p, size_t count) {
         s->sticky = GTQA_ERR_CUDA;
         return GTQA_ERR_CUDA;
     }
+    return GTQA_OK;
+}
+
+// Grow a pair of state-owned device buffers to hold `need` entries (contents dropped).
+template <typename A, typename B>
+int grow_pair(gtqa_state* s, A** a, B** b, size_t per_b, size_t& cap, size_t need) {
+    if (need <= cap) return GTQA_OK;
+    if (*a) cudaFree(*a);
+    if (*b) cudaFree(*b);
+    *a = nullptr;
+    *b = nullptr;
+    cap = 0;
+    int rc;
+    if ((rc = dalloc(s, a, need)) || (rc = dalloc(s, b, need * per_b))) return rc;
+    cap = need;
     return GTQA_OK;
 }
 
@@ -257,9 +281,10 @@ bool misra_gries(int n, int m, const int* edges, std::vector<int>& colour, int& 
 void free_state(gtqa_state* s) {
     if (!s) return;
     void* ptrs[] = {s->Gamma, s->lam, s->T, s->msg[0], s->msg[1], s->D0, s->t0, s->X, s->edge_info,
-                    s->vert_edges, s->vert_inst, s->J, s->h, s->colour_edges, s->colour_off, s->last_colour,
+                    s->vert_edges, s->vert_inst, s->J, s->h, s->colour_edges, s->colour_off, s->last_colour, s->first_colour,
                     s->iso, s->inst_vbeg, s->inst_m, s->acc, s->inst_done, s->inst_iters, s->inst_dist,
-                    s->stats, s->ctl, s->rho, s->sign, s->flags, s->rbuf, s->cutbuf, s->xs, s->ps};
+                    s->stats, s->ctl, s->rho, s->sign, s->flags, s->rbuf, s->cutbuf, s->xs, s->ps,
+                    s->gate_edge, s->gate_U, s->sq_vertex, s->sq_W};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : s->pending) {
@@ -281,6 +306,7 @@ Ctx make_ctx(const gtqa_state* s) {
     c.colour_edges = s->colour_edges;
     c.colour_off = s->colour_off;
     c.last_colour = s->last_colour;
+    c.first_colour = s->first_colour;
     c.iso = s->iso;
     c.n_iso = s->n_iso;
     c.ncol = s->ncol;
@@ -433,6 +459,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
     s->eig_cutoff = o.eig_cutoff > 0 ? o.eig_cutoff : 1e-13;
     s->ncol = ncol;
     s->h_inst_m = minst;
+    s->h_edges = ge;
     // launch shapes: one resident block per SM for each cooperative phase kernel
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -460,7 +487,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
     // slots: incident edges in ascending id; colour of each vertex's last gate
     std::vector<int4> vedges(N, make_int4(-1, -1, -1, 0));
     std::vector<int4> einfo(Mtot);
-    std::vector<int> lastc(N, -1);
+    std::vector<int> lastc(N, -1), firstc(N, -1);
     for (long long e = 0; e < Mtot; ++e) {
         int sl[2];
         for (int q = 0; q < 2; ++q) {
@@ -471,6 +498,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
             sl[q] = k;
             ve.w = k + 1;
             lastc[v] = std::max(lastc[v], gcol[e]);
+            firstc[v] = firstc[v] < 0 ? gcol[e] : std::min(firstc[v], gcol[e]);
         }
         einfo[e] = make_int4(ge[2 * e], ge[2 * e + 1], sl[0], sl[1]);
     }
@@ -498,6 +526,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         (rc = dalloc(s, &s->vert_edges, s->n)) || (rc = dalloc(s, &s->vert_inst, s->n)) ||
         (rc = dalloc(s, &s->J, s->m)) || (rc = dalloc(s, &s->h, s->n)) || (rc = dalloc(s, &s->colour_edges, s->m)) ||
         (rc = dalloc(s, &s->colour_off, ncol + 1)) || (rc = dalloc(s, &s->last_colour, s->n)) ||
+        (rc = dalloc(s, &s->first_colour, s->n)) ||
         (rc = dalloc(s, &s->iso, iso.size())) || (rc = dalloc(s, &s->inst_vbeg, B + 1)) ||
         (rc = dalloc(s, &s->inst_m, B)) || (rc = dalloc(s, &s->acc, 6 * (size_t)B)) ||
         (rc = dalloc(s, &s->inst_done, B)) || (rc = dalloc(s, &s->inst_iters, B)) ||
@@ -539,6 +568,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
               cuda_ok(s, cudaMemcpyAsync(s->colour_edges, cedges.data(), sizeof(int) * Mtot, cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->colour_off, coff.data(), sizeof(int) * (ncol + 1), cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->last_colour, lastc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st)) &&
+              cuda_ok(s, cudaMemcpyAsync(s->first_colour, firstc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st)) &&
               (iso.empty() || cuda_ok(s, cudaMemcpyAsync(s->iso, iso.data(), sizeof(int) * iso.size(), cudaMemcpyHostToDevice, st))) &&
               cuda_ok(s, cudaMemcpyAsync(s->inst_vbeg, vbeg.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->inst_m, minst.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st)) &&
@@ -690,6 +720,23 @@ int gtqa_trotter_layer(gtqa_state* s, double tau, double dt) {
     return GTQA_OK;
 }
 
+int gtqa_trotter_split(gtqa_state* s, double t_Z, double t_X_pre, double t_X_post) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (!std::isfinite(t_Z) || !std::isfinite(t_X_pre) || !std::isfinite(t_X_post)) return GTQA_ERR_INVALID_ARG;
+    Ctx c = make_ctx(s);
+    c.phases = PH_GATES;
+    c.k0 = c.k1 = 0;
+    c.Ksched = 0;
+    c.tZ1 = t_Z;
+    c.tX1 = t_X_post;
+    c.tXpre1 = t_X_pre;
+    if ((rc = run(s, c, PK_GATES, GTQA_K_TROTTER, s->m))) return rc;
+    s->layers += 1;
+    s->gates += s->m;
+    return GTQA_OK;
+}
+
 int gtqa_bp_sweep(gtqa_state* s, double tol, int32_t max_iter, uint32_t flags, int32_t* iters_out,
                   double* dist_out) {
     int rc = check_state(s);
@@ -754,6 +801,119 @@ int gtqa_sample(gtqa_state* s, int32_t k, const int32_t* order, const double* u,
     return GTQA_OK;
 }
 
+int gtqa_apply_gates(gtqa_state* s, int32_t k, const int32_t* edge, const double* U) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (k < 0 || (k > 0 && (!edge || !U))) return GTQA_ERR_INVALID_ARG;
+    for (int q = 0; q < k; ++q) {
+        if (edge[q] < 0 || edge[q] >= s->m) return GTQA_ERR_INVALID_ARG;
+        for (int t = 0; t < 32; ++t)
+            if (!std::isfinite(U[32 * (size_t)q + t])) return GTQA_ERR_INVALID_ARG;
+    }
+    if (k == 0) return GTQA_OK;
+    // As-soon-as-possible layering: a gate goes one launch after the latest earlier gate
+    // that shares a vertex with it, so gates of one launch have disjoint endpoints and
+    // every pair of gates sharing a vertex keeps its order.
+    std::vector<int> depth(s->n, 0), lay(k);
+    int nl = 0;
+    for (int q = 0; q < k; ++q) {
+        const int a = s->h_edges[2 * (size_t)edge[q]], b = s->h_edges[2 * (size_t)edge[q] + 1];
+        const int L = std::max(depth[a], depth[b]);
+        lay[q] = L;
+        depth[a] = depth[b] = L + 1;
+        nl = std::max(nl, L + 1);
+    }
+    std::vector<int> off(nl + 1, 0);
+    for (int q = 0; q < k; ++q) ++off[lay[q] + 1];
+    for (int L = 0; L < nl; ++L) off[L + 1] += off[L];
+    std::vector<int> fill(off.begin(), off.end() - 1), es(k);
+    std::vector<double> Us(32 * (size_t)k);
+    for (int q = 0; q < k; ++q) {
+        const int pos = fill[lay[q]]++;
+        es[pos] = edge[q];
+        std::memcpy(&Us[32 * (size_t)pos], U + 32 * (size_t)q, 32 * sizeof(double));
+    }
+    if ((rc = grow_pair(s, &s->gate_edge, &s->gate_U, 16, s->gate_cap, (size_t)k))) return rc;
+    if (!cuda_ok(s, cudaMemcpyAsync(s->gate_edge, es.data(), sizeof(int) * k, cudaMemcpyHostToDevice, s->stream)) ||
+        !cuda_ok(s, cudaMemcpyAsync(s->gate_U, Us.data(), sizeof(double) * Us.size(), cudaMemcpyHostToDevice, s->stream)))
+        return GTQA_ERR_CUDA;
+    for (int L = 0; L < nl; ++L) {
+        GenArgs a;
+        a.Gamma = s->Gamma;
+        a.lam = s->lam;
+        a.edge_info = s->edge_info;
+        a.vert_edges = s->vert_edges;
+        a.gate_edge = s->gate_edge + off[L];
+        a.gate_U = s->gate_U + 16 * (size_t)off[L];
+        a.count = off[L + 1] - off[L];
+        a.stats = s->stats;
+        a.chi = s->chi;
+        a.svd_cut = s->svd_cutoff;
+        const cudaError_t e = mixed(s) ? general_gates_launch_mixed(s->CHI, a, s->stream)
+                                       : general_gates_launch_fp64(s->CHI, a, s->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->sticky = GTQA_ERR_CUDA;
+            return GTQA_ERR_CUDA;
+        }
+        s->launches += 1;
+    }
+    s->gates += k;
+    return GTQA_OK;
+}
+
+int gtqa_apply_single_qubit_gates(gtqa_state* s, int32_t k, const int32_t* vertex, const double* W) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (k < 0 || (k > 0 && (!vertex || !W))) return GTQA_ERR_INVALID_ARG;
+    for (int q = 0; q < k; ++q) {
+        if (vertex[q] < 0 || vertex[q] >= s->n) return GTQA_ERR_INVALID_ARG;
+        for (int t = 0; t < 8; ++t)
+            if (!std::isfinite(W[8 * (size_t)q + t])) return GTQA_ERR_INVALID_ARG;
+    }
+    if (k == 0) return GTQA_OK;
+    // gates on one vertex compose in list order: W_total = W_last ... W_first
+    using cx = std::complex<double>;
+    std::vector<int> slot(s->n, -1), vs;
+    std::vector<cx> acc;
+    for (int q = 0; q < k; ++q) {
+        const int a = vertex[q];
+        if (slot[a] < 0) {
+            slot[a] = (int)vs.size();
+            vs.push_back(a);
+            acc.insert(acc.end(), {cx(1, 0), cx(0, 0), cx(0, 0), cx(1, 0)});
+        }
+        cx* T = &acc[4 * (size_t)slot[a]];
+        const double* w = W + 8 * (size_t)q;
+        const cx w00(w[0], w[1]), w01(w[2], w[3]), w10(w[4], w[5]), w11(w[6], w[7]);
+        const cx t00 = w00 * T[0] + w01 * T[2], t01 = w00 * T[1] + w01 * T[3];
+        const cx t10 = w10 * T[0] + w11 * T[2], t11 = w10 * T[1] + w11 * T[3];
+        T[0] = t00;
+        T[1] = t01;
+        T[2] = t10;
+        T[3] = t11;
+    }
+    const int cnt = (int)vs.size();
+    std::vector<double> Wd(8 * (size_t)cnt);
+    for (size_t t = 0; t < 4 * (size_t)cnt; ++t) {
+        Wd[2 * t] = acc[t].real();
+        Wd[2 * t + 1] = acc[t].imag();
+    }
+    if ((rc = grow_pair(s, &s->sq_vertex, &s->sq_W, 4, s->sq_cap, (size_t)cnt))) return rc;
+    if (!cuda_ok(s, cudaMemcpyAsync(s->sq_vertex, vs.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s->stream)) ||
+        !cuda_ok(s, cudaMemcpyAsync(s->sq_W, Wd.data(), sizeof(double) * Wd.size(), cudaMemcpyHostToDevice, s->stream)))
+        return GTQA_ERR_CUDA;
+    const cudaError_t e = mixed(s) ? single_gates_launch_mixed(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream)
+                                   : single_gates_launch_fp64(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->sticky = GTQA_ERR_CUDA;
+        return GTQA_ERR_CUDA;
+    }
+    s->launches += 1;
+    return GTQA_OK;
+}
+
 int gtqa_regauge(gtqa_state* s) {
     int rc = check_state(s);
     if (rc) return rc;
@@ -776,6 +936,41 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
     c.max_iter = max_iter;
     for (int k = k_begin; k <= k_end; ++k) {
         c.k0 = c.k1 = k;
+        if ((rc = run(s, c, PK_GATES, GTQA_K_TROTTER, s->m)) || (rc = run(s, c, PK_BP, GTQA_K_BP, s->n)) ||
+            (rc = run(s, c, PK_REGAUGE, GTQA_K_REGAUGE, s->m)))
+            return rc;
+        s->layers += 1;
+        s->gates += s->m;
+    }
+    return GTQA_OK;
+}
+
+int gtqa_anneal_ex(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double dt, double tol,
+                   int32_t max_iter, int32_t order, const uint8_t* reverse) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (K < 1 || k_begin < 1 || k_end < k_begin || k_end > K || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1 ||
+        (order != GTQA_TROTTER_FIRST && order != GTQA_TROTTER_SYMMETRIC) ||
+        (order == GTQA_TROTTER_SYMMETRIC && reverse))
+        return GTQA_ERR_INVALID_ARG;
+    Ctx c = make_ctx(s);
+    c.phases = PH_GATES | PH_BP | PH_WARM | PH_REGAUGE;
+    c.Ksched = 0;
+    c.tol = tol;
+    c.max_iter = max_iter;
+    for (int k = k_begin; k <= k_end; ++k) {
+        // the layer's angles are formed here, as in the oracle's product_formula
+        const double tau = (double)k / (double)K, tZ = dt * tau, tX = dt * (1.0 - tau);
+        const bool rev = reverse && reverse[k - k_begin];
+        c.k0 = c.k1 = k;
+        c.tZ1 = tZ;
+        if (order == GTQA_TROTTER_SYMMETRIC) {
+            c.tXpre1 = 0.5 * tX;
+            c.tX1 = 0.5 * tX;
+        } else {
+            c.tXpre1 = rev ? tX : 0.0;
+            c.tX1 = rev ? 0.0 : tX;
+        }
         if ((rc = run(s, c, PK_GATES, GTQA_K_TROTTER, s->m)) || (rc = run(s, c, PK_BP, GTQA_K_BP, s->n)) ||
             (rc = run(s, c, PK_REGAUGE, GTQA_K_REGAUGE, s->m)))
             return rc;

@@ -499,4 +499,21 @@ __device__ __forceinline__ bool grid_sync(GridBarrier& gb, long long limit) {
     return ok_shared != 0;   // one value per block, so the whole block leaves together
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel function, shared by
+// every state in the process, while the BP kernel's need grows with the number of
+// instances.  The limit is therefore raised to the device maximum (not to one state's
+// need), so that states of different sizes can launch the same kernel in any order.
+template <class K>
+inline cudaError_t raise_smem_limit(K kernel, size_t smem) {
+    int dev = 0, mx = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const size_t avail = (size_t)mx > fa.sharedSizeBytes ? (size_t)mx - fa.sharedSizeBytes : 0;
+    if (smem > avail) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail);
+}
+
 }  // namespace gtqa

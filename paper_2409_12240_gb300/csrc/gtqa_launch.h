@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "gtqa_anneal.cuh"
+#include "gtqa_general.cuh"
 
 namespace gtqa {
 
@@ -14,23 +15,6 @@ enum PhaseKernel { PK_GATES = 0, PK_BP = 1, PK_REGAUGE = 2, PK_COUNT = 3 };
 // Shared memory the BP kernel keeps per instance after its fixed part: three int flags
 // (padded to 8 bytes), two FP64 thresholds and one float threshold.
 inline size_t bp_instance_smem(long long B) { return (12 * (size_t)B + 7) / 8 * 8 + 20 * (size_t)B; }
-
-// The dynamic shared-memory limit is an attribute of the kernel function, shared by
-// every state in the process, while the BP kernel's need grows with the number of
-// instances.  The limit is therefore raised to the device maximum (not to one state's
-// need), so that states of different sizes can launch the same kernel in any order.
-template <class K>
-inline cudaError_t raise_smem_limit(K kernel, size_t smem) {
-    int dev = 0, mx = 0;
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
-    if (e != cudaSuccess) return e;
-    const size_t avail = (size_t)mx > fa.sharedSizeBytes ? (size_t)mx - fa.sharedSizeBytes : 0;
-    if (smem > avail) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail);
-}
 
 #define GTQA_DECLARE_PHASE(MODE, PHASE)                                                                 \
     bool PHASE##_##MODE##_shape(int CHI, size_t* smem_base, int* tpb);                                  \
@@ -56,6 +40,12 @@ cudaError_t marginals_launch_fp64(int CHI, const void* Gamma, const double* lam,
                                   cd* rho, int8_t* sign, int* flag, cudaStream_t st);
 cudaError_t marginals_launch_mixed(int CHI, const void* Gamma, const double* lam, const int4* vert_edges, int n,
                                    cd* rho, int8_t* sign, int* flag, cudaStream_t st);
+
+cudaError_t general_gates_launch_fp64(int CHI, const GenArgs& a, cudaStream_t st);
+cudaError_t general_gates_launch_mixed(int CHI, const GenArgs& a, cudaStream_t st);
+cudaError_t single_gates_launch_fp64(int CHI, void* Gamma, const int* vertex, const cd* W, int count, cudaStream_t st);
+cudaError_t single_gates_launch_mixed(int CHI, void* Gamma, const int* vertex, const cd* W, int count,
+                                      cudaStream_t st);
 
 inline bool phase_shape(bool mixed, int pk, int CHI, size_t* sb, int* tpb) {
     switch (pk) {

@@ -31,12 +31,16 @@ GTQA_BP_WARM_START = 1
 GTQA_BP_REGAUGE = 2
 GTQA_BP_DEFAULT = 3
 
+GTQA_TROTTER_FIRST = 1
+GTQA_TROTTER_SYMMETRIC = 2
+
 EXPORTED = [
     "gtqa_options_init", "gtqa_create", "gtqa_create_batch", "gtqa_trotter_layer", "gtqa_bp_sweep",
     "gtqa_regauge", "gtqa_anneal", "gtqa_marginals", "gtqa_stats", "gtqa_get_state", "gtqa_set_state", "gtqa_sizes",
     "gtqa_edge_colouring", "gtqa_strerror", "gtqa_destroy", "gtqa_profile", "gtqa_profile_read",
     "gtqa_profile_name", "gtqa_alu_peak", "gtqa_debug_barrier", "gtqa_math_check", "gtqa_bp_static",
     "gtqa_barrier_bench", "gtqa_residual", "gtqa_entropy", "gtqa_spectral_bipartition", "gtqa_sample",
+    "gtqa_trotter_split", "gtqa_anneal_ex", "gtqa_apply_gates", "gtqa_apply_single_qubit_gates",
 ]
 KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
@@ -88,6 +92,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_bp_sweep": (I32, [P, D, I32, U32, ctypes.POINTER(I32), ctypes.POINTER(D)]),
         "gtqa_regauge": (I32, [P]),
         "gtqa_anneal": (I32, [P, I32, I32, I32, D, D, I32]),
+        "gtqa_trotter_split": (I32, [P, D, D, D]),
+        "gtqa_anneal_ex": (I32, [P, I32, I32, I32, D, D, I32, I32, P]),
+        "gtqa_apply_gates": (I32, [P, I32, P, P]),
+        "gtqa_apply_single_qubit_gates": (I32, [P, I32, P, P]),
         "gtqa_marginals": (I32, [P, P, P]),
         "gtqa_residual": (I32, [P, ctypes.POINTER(D)]),
         "gtqa_entropy": (I32, [P, P, ctypes.POINTER(D)]),
@@ -211,6 +219,41 @@ def gtqa_anneal(s: int, k_begin: int, k_end: int, K: int, dt: float, tol: float,
     """Layers k_begin..k_end of the K-layer anneal in one persistent launch (asynchronous)."""
     _check(load().gtqa_anneal(s, int(k_begin), int(k_end), int(K), float(dt), float(tol), int(max_iter)),
            "gtqa_anneal")
+
+
+def gtqa_trotter_split(s: int, t_Z: float, t_X_pre: float, t_X_post: float) -> None:
+    """One layer U_X(t_X_post) U_Z(t_Z) U_X(t_X_pre) (asynchronous)."""
+    _check(load().gtqa_trotter_split(s, float(t_Z), float(t_X_pre), float(t_X_post)), "gtqa_trotter_split")
+
+
+def gtqa_anneal_ex(s: int, k_begin: int, k_end: int, K: int, dt: float, tol: float, max_iter: int,
+                   order: int = GTQA_TROTTER_FIRST, reverse=None) -> None:
+    """gtqa_anneal with the first-order (optionally reversed per layer) or symmetric formula."""
+    rv = None if reverse is None else np.ascontiguousarray(np.asarray(reverse, dtype=np.uint8))
+    if rv is not None and rv.size != k_end - k_begin + 1:
+        raise ValueError("reverse needs one entry per layer")
+    _check(load().gtqa_anneal_ex(s, int(k_begin), int(k_end), int(K), float(dt), float(tol), int(max_iter),
+                                 int(order), rv.ctypes.data if rv is not None else None), "gtqa_anneal_ex")
+
+
+def gtqa_apply_gates(s: int, edge, U) -> None:
+    """Arbitrary two-qubit gates, U[q] a 4x4 complex matrix on edge[q] (asynchronous)."""
+    e = np.ascontiguousarray(np.asarray(edge, dtype=np.int32).reshape(-1))
+    u = np.ascontiguousarray(np.asarray(U, dtype=np.complex128).reshape(-1, 4, 4))
+    if u.shape[0] != e.size:
+        raise ValueError("one 4x4 matrix per gate")
+    _check(load().gtqa_apply_gates(s, int(e.size), e.ctypes.data if e.size else None,
+                                   u.ctypes.data if e.size else None), "gtqa_apply_gates")
+
+
+def gtqa_apply_single_qubit_gates(s: int, vertex, W) -> None:
+    """Arbitrary one-qubit gates, W[q] a 2x2 complex matrix on vertex[q] (asynchronous)."""
+    v = np.ascontiguousarray(np.asarray(vertex, dtype=np.int32).reshape(-1))
+    w = np.ascontiguousarray(np.asarray(W, dtype=np.complex128).reshape(-1, 2, 2))
+    if w.shape[0] != v.size:
+        raise ValueError("one 2x2 matrix per gate")
+    _check(load().gtqa_apply_single_qubit_gates(s, int(v.size), v.ctypes.data if v.size else None,
+                                                w.ctypes.data if v.size else None), "gtqa_apply_single_qubit_gates")
 
 
 def gtqa_sizes(s: int) -> Tuple[int, int, int, int]:
