@@ -55,13 +55,13 @@ R8  Marginals: Eq. (partial_dens) with the environment of Eq. (bp_approx) built
     from the warm-start messages of the current Vidal-gauge state, i.e.
     rho_a = sum Gamma Gamma^* prod_b lambda_ba^2, divided by its trace.
 R9  Read-out tie rho_a[0,0] = 1/2 maps to -1 (literal "otherwise").
-R10 Product formulas beyond first order (the paper names them only as an
+R13 Product formulas beyond first order (the paper names them only as an
     outlook, Sec. V): a layer is U_X(t_post) U_Z(t_Z) U_X(t_pre).  First order
     (R1) is (t_pre, t_post) = (0, t_X); the second-order symmetric (Strang)
     formula is (t_X/2, t_X/2) at the same tau_k; the randomised first-order
     formula draws, per layer, the forward (0, t_X) or the reversed (t_X, 0)
     ordering with probability 1/2 each (the caller supplies the draws).
-R11 Arbitrary two-qubit gate on edge e = {a, b} with a = edges[e][0]: a 4x4
+R14 Arbitrary two-qubit gate on edge e = {a, b} with a = edges[e][0]: a 4x4
     matrix W[(i_a i_b), (i_a' i_b')] (row index 2 i_a + i_b), applied by the
     same simple update as the Ising gate (App. E); gates are applied in the
     order given.
@@ -250,7 +250,7 @@ def simple_update(st: VidalState, e: int, W: np.ndarray, chi: int,
 def trotter_layer(st: VidalState, colour: np.ndarray, J: np.ndarray, h: np.ndarray,
                   t_Z: float, t_X: float, chi: int, svd_cutoff: float = SVD_CUTOFF,
                   t_X_pre: float = 0.0) -> Dict[str, float]:
-    """U_X(t_X) U_Z(t_Z) U_X(t_X_pre) of Eq. (discretizatoion) and reading R10: the
+    """U_X(t_X) U_Z(t_Z) U_X(t_X_pre) of Eq. (discretizatoion) and reading R13: the
     leading mixing gate on every qubit (skipped for t_X_pre = 0), every edge gate of
     the interaction layer (colour classes ascending, reading R2), then the mixing
     gate on every qubit."""
@@ -538,7 +538,7 @@ def regauge(st: VidalState, tol: float, max_iter: int, schedule: str = "flooding
 
 
 def product_formula(k: int, K: int, dt: float, order: int = 1, reverse: bool = False) -> Tuple[float, float, float]:
-    """Angles (t_X_pre, t_Z, t_X_post) of layer k under reading R10 (Sec. V).
+    """Angles (t_X_pre, t_Z, t_X_post) of layer k under reading R13 (Sec. V).
 
     order 1: (0, t_Z, t_X), or (t_X, t_Z, 0) when `reverse` (one draw of the randomised
     first-order formula); order 2: the symmetric formula (t_X/2, t_Z, t_X/2).
@@ -555,7 +555,7 @@ def product_formula(k: int, K: int, dt: float, order: int = 1, reverse: bool = F
 
 def apply_gates(st: VidalState, gates: Sequence[Tuple[int, np.ndarray]], chi: int,
                 svd_cutoff: float = SVD_CUTOFF) -> Dict[str, float]:
-    """Reading R11: arbitrary two-qubit gates (edge e, 4x4 matrix) in the order given,
+    """Reading R14: arbitrary two-qubit gates (edge e, 4x4 matrix) in the order given,
     each by the simple update with truncation to chi (App. E)."""
     disc, logf = 0.0, 0.0
     for e, W in gates:
@@ -575,7 +575,7 @@ def run(n: int, edges, J, h, colour, K: int, dt: float, chi: int, tol: float, ma
         layers: Optional[int] = None, record: bool = False, state: Optional[VidalState] = None,
         k0: int = 0, order: int = 1, reverse: Optional[Sequence[bool]] = None):
     """Run layers k0+1 .. k0+layers (default all K) of the anneal from |+>^N
-    (or from `state`) with the product formula of reading R10 (`reverse[i]` is the
+    (or from `state`) with the product formula of reading R13 (`reverse[i]` is the
     draw of layer k0+1+i).  Returns the final state and per-layer info."""
     st = plus_state(n, np.asarray(edges)) if state is None else state
     infos = []

@@ -5,8 +5,8 @@ TEST INFRASTRUCTURE ONLY (pins for the GTQA oracle; never used by the library).
 The circuit is Eq. (discretizatoion) of App. F with reading R1 of the oracle
 (layer k applies U_Z(dt*k/K) then U_X(dt*(1-k/K)), k = 1..K), starting from
 |+>^N (Sec. III A); `evolve_split` takes any per-layer angles
-(t_X_pre, t_Z, t_X_post) (reading R10), and `apply_one` / `apply_two` apply
-arbitrary one- and two-qubit gates (reading R11).  U_Z is the product of the commuting diagonal two-qubit gates
+(t_X_pre, t_Z, t_X_post) (reading R13), and `apply_one` / `apply_two` apply
+arbitrary one- and two-qubit gates (reading R14).  U_Z is the product of the commuting diagonal two-qubit gates
 exp(-i t (J_ab Z_a Z_b + h_a/D_a Z_a + h_b/D_b Z_b)), U_X the product of
 exp(-i t X_a).  Qubit a is tensor axis a; |0> has Z eigenvalue +1 (x_a = +1,
 Sec. III A).

@@ -433,7 +433,7 @@ def _one_layer_error(n, edges, J, h, tau, dt, order, mode):
 
 def product_formula_orders(seed: int = 0) -> dict:
     """Local error of one layer against the matrix exponential of the layer's
-    Hamiltonian (reading R10): the first-order formula (either ordering) errs by O(dt^2),
+    Hamiltonian (reading R13): the first-order formula (either ordering) errs by O(dt^2),
     the symmetric formula and the average over the two first-order orderings (the
     randomised formula, as a channel) by O(dt^3).  Returns e(dt)/e(dt/2) per formula
     (about 4 and 8)."""
@@ -449,7 +449,7 @@ def product_formula_orders(seed: int = 0) -> dict:
 
 def tree_product_formula_exact(seed: int, order: int, n: int = 10, K: int = 6, dt: float = 0.3) -> float:
     """On a tree without truncation the GTQA marginals under the second-order or the
-    randomised first-order formula equal the exact ones layer by layer (Sec. II B, R10)."""
+    randomised first-order formula equal the exact ones layer by layer (Sec. II B, R13)."""
     inst = make_tree_instance(n, seed)
     rng = np.random.default_rng(seed + 99)
     rev = [bool(x) for x in rng.integers(0, 2, size=K)] if order == 1 else [False] * K
@@ -479,7 +479,7 @@ def random_gate_list(rng: np.random.Generator, m: int, k: int):
 
 def general_gates_exact(seed: int = 0, n: int = 8, k: int = 14) -> dict:
     """Arbitrary two- and one-qubit gates on a tree without truncation reproduce the
-    exact state (reading R11); after the regauge (exact BP on a tree) the marginals are
+    exact state (reading R14); after the regauge (exact BP on a tree) the marginals are
     the exact ones."""
     inst = make_tree_instance(n, seed)
     rng = np.random.default_rng(seed + 7)
