@@ -2,7 +2,7 @@
 """Throughput of the GTQA hot path: Trotter layers per second on one GB300.
 
 Workload (the single-instance annealing run): seeded random 3-regular graph with
-n = 1000 vertices (m = 1500 edges, Misra-Gries 4-colour matching schedule),
+n = 1000 vertices (m = 1500 edges, 3-colour matching schedule from a Kempe-chain edge colouring),
 J_ab ~ N(0, 1), h_a ~ N(0, 0.1), bond dimension chi = 4, linear schedule over
 K = 3200 Trotter layers with dt = 0.2, BP tolerance 1e-8 (at most 100 sweeps).
 One step = one full annealing layer: every edge gate with truncation, the mixing
@@ -31,7 +31,7 @@ if ROOT not in sys.path:
 
 METRIC = "Trotter layers/sec at n=1000, chi=4 (mixed vs FP64 GPU) at stated marginal error"
 WL = dict(n=1000, seed=0, chi=4, K=3200, dt=0.2, tol=1e-8, max_iter=100)
-WORKLOAD_NAME = ("random 3-regular n=1000 (m=1500, 4-colour schedule), J~N(0,1), h~N(0,0.1), "
+WORKLOAD_NAME = ("random 3-regular n=1000 (m=1500, 3-colour schedule), J~N(0,1), h~N(0,0.1), "
                  "chi=4, K=3200 layers, dt=0.2, BP tol 1e-8, max 100 sweeps")
 L2_FLUSH_BYTES = 256 << 20
 

@@ -298,7 +298,9 @@ int gtqa_set_state(gtqa_state* s, const double* gamma, const double* lambda, con
 /* Sizes: total vertices and edges, storage bond dimension CHI, number of colours. */
 int gtqa_sizes(const gtqa_state* s, int64_t* n, int64_t* m, int32_t* chi_storage, int32_t* n_colours);
 
-/* Host-only: the library's Misra-Gries edge colouring (<= Delta + 1 colours). */
+/* Host-only: the edge colouring gtqa_create uses when colour is NULL: Delta colours by a
+ * seeded Kempe-chain search when it succeeds (almost all random cubic graphs, trees,
+ * heavy-hexagon lattices), else Misra-Gries (<= Delta + 1 colours).  Deterministic. */
 int gtqa_edge_colouring(int32_t n, int32_t m, const int32_t* edges, int32_t* colour_out,
                         int32_t* n_colours_out);
 

@@ -9,6 +9,8 @@ from .generators import (  # noqa: F401
     random_regular_graph,
     random_tree,
     edge_colouring,
+    delta_edge_colouring,
+    misra_gries_colouring,
     check_colouring,
     make_instance,
     make_tree_instance,

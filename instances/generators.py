@@ -97,7 +97,100 @@ def heavy_hex_graph(rows: int, cols: int) -> Tuple[int, np.ndarray]:
     return n, e
 
 
-def edge_colouring(n: int, edges: np.ndarray) -> np.ndarray:
+def edge_colouring(n: int, edges: np.ndarray, seed: int = 0) -> np.ndarray:
+    """Proper edge colouring, each colour class a matching: Delta colours when the Kempe-chain
+    search below finds them (almost all random cubic graphs, trees and heavy-hexagon lattices
+    are Delta-edge-colourable), else Misra-Gries with at most Delta + 1.  Fewer colours means
+    fewer sequential gate phases per layer.  Returns an int32 array colour[e]."""
+    col = delta_edge_colouring(n, edges, seed)
+    return col if col is not None else misra_gries_colouring(n, edges)
+
+
+def delta_edge_colouring(n: int, edges: np.ndarray, seed: int = 0,
+                         max_steps: Optional[int] = None) -> Optional[np.ndarray]:
+    """Try to colour the edges with Delta = max degree colours; None if the search gives up.
+
+    Edges are coloured in a seeded random order.  An edge {u, v} takes a colour free at both
+    ends if there is one.  Otherwise, with a free at u and b free at v, the a/b Kempe chain that
+    starts at v is swapped, which frees a at v, unless the chain ends at u (it would close an
+    odd cycle with {u, v}).  In that case a random Kempe component through u or v is swapped,
+    which keeps the colouring proper, and the edge is tried again.  The search gives up after
+    max_steps attempts (default 200 m + 1000)."""
+    edges = np.asarray(edges, dtype=np.int64)
+    m = int(edges.shape[0])
+    if m == 0:
+        return np.zeros(0, dtype=np.int32)
+    D = int(np.bincount(edges.ravel(), minlength=n).max())
+    if D == 1:
+        return np.zeros(m, dtype=np.int32)
+    rng = _rng(BASE_SEED + 9_000_000 + int(seed))
+    E = edges.tolist()
+    at = np.full((n, D), -1, dtype=np.int64)     # edge of colour c at vertex v
+    col = np.full(m, -1, dtype=np.int64)
+
+    def other(f, x):
+        return E[f][0] if E[f][1] == x else E[f][1]
+
+    def recolour(fs, a, b):
+        for f in fs:
+            p, q = E[f]
+            at[p, col[f]] = -1
+            at[q, col[f]] = -1
+        for f in fs:
+            col[f] = b if col[f] == a else a
+            p, q = E[f]
+            at[p, col[f]] = f
+            at[q, col[f]] = f
+
+    def component(x, a, b):
+        comp, seen, stack, visited = [], set(), [x], {x}
+        while stack:
+            y = stack.pop()
+            for c in (a, b):
+                f = int(at[y, c])
+                if f >= 0 and f not in seen:
+                    seen.add(f)
+                    comp.append(f)
+                    z = other(f, y)
+                    if z not in visited:
+                        visited.add(z)
+                        stack.append(z)
+        return comp
+
+    steps, limit = 0, (max_steps if max_steps is not None else 200 * m + 1000)
+    for e in rng.permutation(m).tolist():
+        u, v = E[e]
+        while True:
+            steps += 1
+            if steps > limit:
+                return None
+            fu = [c for c in range(D) if at[u, c] < 0]
+            fv = [c for c in range(D) if at[v, c] < 0]
+            common = [c for c in fu if c in fv]
+            if common:
+                c = common[int(rng.integers(len(common)))]
+                break
+            a = fu[int(rng.integers(len(fu)))]
+            b = fv[int(rng.integers(len(fv)))]
+            path, x, cc = [], v, a
+            while at[x, cc] >= 0:
+                f = int(at[x, cc])
+                path.append(f)
+                x = other(f, x)
+                cc = b if cc == a else a
+            if x != u:
+                recolour(path, a, b)
+                c = a
+                break
+            p, q = (int(t) for t in rng.choice(D, size=2, replace=False))
+            recolour(component((u, v)[int(rng.integers(2))], p, q), p, q)
+        col[e] = c
+        at[u, c] = e
+        at[v, c] = e
+    return col.astype(np.int32)
+
+
+def misra_gries_colouring(n: int, edges: np.ndarray) -> np.ndarray:
     """Proper edge colouring with at most Delta+1 colours (Misra-Gries).
 
     Returns an int32 array colour[e]; edges sharing a vertex get different

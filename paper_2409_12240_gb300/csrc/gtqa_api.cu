@@ -177,6 +177,130 @@ void prof_collect(gtqa_state* s) {
     s->pending.clear();
 }
 
+// Edge colouring with Delta colours by a seeded Kempe-chain search (same scheme as the
+// input generators): edges in a random order; an edge {u, v} takes a colour free at both
+// ends, else the a/b chain from v (a free at u, b free at v) is swapped unless it ends at u,
+// else a random Kempe component through u or v is swapped and the edge is tried again.
+// Returns false after max_steps attempts (the graph may need Delta + 1 colours).
+bool delta_colouring(int n, int m, const int* edges, std::vector<int>& colour, int& ncol) {
+    ncol = 0;
+    colour.assign(m, 0);
+    if (m == 0) return true;
+    std::vector<int> deg(n, 0);
+    for (int e = 0; e < m; ++e) {
+        deg[edges[2 * e]]++;
+        deg[edges[2 * e + 1]]++;
+    }
+    int D = 0;
+    for (int v = 0; v < n; ++v) D = deg[v] > D ? deg[v] : D;
+    if (D <= 1) {
+        ncol = 1;
+        return true;
+    }
+    unsigned long long rs = 0x9e3779b97f4a7c15ull;
+    auto rnd = [&](int k) {   // splitmix64, reduced to [0, k)
+        rs += 0x9e3779b97f4a7c15ull;
+        unsigned long long z = rs;
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        return (int)(z % (unsigned long long)k);
+    };
+    std::vector<int> at((size_t)n * D, -1), col(m, -1), order(m);
+    for (int e = 0; e < m; ++e) order[e] = e;
+    for (int e = m - 1; e > 0; --e) std::swap(order[e], order[rnd(e + 1)]);
+    auto other = [&](int f, int x) { return edges[2 * f] == x ? edges[2 * f + 1] : edges[2 * f]; };
+    auto recolour = [&](const std::vector<int>& fs, int a, int b) {
+        for (int f : fs) {
+            at[(size_t)edges[2 * f] * D + col[f]] = -1;
+            at[(size_t)edges[2 * f + 1] * D + col[f]] = -1;
+        }
+        for (int f : fs) {
+            col[f] = col[f] == a ? b : a;
+            at[(size_t)edges[2 * f] * D + col[f]] = f;
+            at[(size_t)edges[2 * f + 1] * D + col[f]] = f;
+        }
+    };
+    std::vector<int> path, stack, fu, fv, common;
+    std::vector<char> fseen(m, 0), vseen(n, 0);
+    const long long limit = 200LL * m + 1000;
+    long long steps = 0;
+    for (int e : order) {
+        const int u = edges[2 * e], v = edges[2 * e + 1];
+        int c = -1;
+        while (c < 0) {
+            if (++steps > limit) return false;
+            fu.clear();
+            fv.clear();
+            common.clear();
+            for (int k = 0; k < D; ++k) {
+                if (at[(size_t)u * D + k] < 0) fu.push_back(k);
+                if (at[(size_t)v * D + k] < 0) fv.push_back(k);
+            }
+            for (int k : fu)
+                if (std::find(fv.begin(), fv.end(), k) != fv.end()) common.push_back(k);
+            if (!common.empty()) {
+                c = common[rnd((int)common.size())];
+                break;
+            }
+            const int a = fu[rnd((int)fu.size())], b = fv[rnd((int)fv.size())];
+            path.clear();
+            int x = v, cc = a;
+            while (at[(size_t)x * D + cc] >= 0) {
+                const int f = at[(size_t)x * D + cc];
+                path.push_back(f);
+                x = other(f, x);
+                cc = cc == a ? b : a;
+            }
+            if (x != u) {
+                recolour(path, a, b);
+                c = a;
+                break;
+            }
+            // the whole p/q component through u or v
+            const int p = rnd(D);
+            int q = rnd(D - 1);
+            if (q >= p) ++q;
+            path.clear();
+            stack.assign(1, rnd(2) ? u : v);
+            vseen[stack[0]] = 1;
+            std::vector<int> touched(1, stack[0]);
+            while (!stack.empty()) {
+                const int y = stack.back();
+                stack.pop_back();
+                for (int k : {p, q}) {
+                    const int f = at[(size_t)y * D + k];
+                    if (f >= 0 && !fseen[f]) {
+                        fseen[f] = 1;
+                        path.push_back(f);
+                        const int z = other(f, y);
+                        if (!vseen[z]) {
+                            vseen[z] = 1;
+                            touched.push_back(z);
+                            stack.push_back(z);
+                        }
+                    }
+                }
+            }
+            for (int f : path) fseen[f] = 0;
+            for (int z : touched) vseen[z] = 0;
+            recolour(path, p, q);
+        }
+        col[e] = c;
+        at[(size_t)u * D + c] = e;
+        at[(size_t)v * D + c] = e;
+    }
+    colour = col;
+    ncol = D;
+    return true;
+}
+
+// Fewest colours the library can find: Delta by delta_colouring, else Misra-Gries.
+bool misra_gries(int n, int m, const int* edges, std::vector<int>& colour, int& ncol);
+bool edge_colouring(int n, int m, const int* edges, std::vector<int>& colour, int& ncol) {
+    return delta_colouring(n, m, edges, colour, ncol) || misra_gries(n, m, edges, colour, ncol);
+}
+
 // Misra-Gries proper edge colouring with at most Delta + 1 colours.
 bool misra_gries(int n, int m, const int* edges, std::vector<int>& colour, int& ncol) {
     std::vector<int> deg(n, 0);
@@ -428,7 +552,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
             } else {
                 std::vector<int> col;
                 int nc = 0;
-                if (!misra_gries(n[b], m[b], edges + 2 * eoff, col, nc)) return GTQA_ERR_INVALID_ARG;
+                if (!edge_colouring(n[b], m[b], edges + 2 * eoff, col, nc)) return GTQA_ERR_INVALID_ARG;
                 for (int e = 0; e < m[b]; ++e) gcol[eoff + e] = col[e];
             }
             voff += n[b];
@@ -1285,7 +1409,7 @@ int gtqa_edge_colouring(int32_t n, int32_t m, const int32_t* edges, int32_t* col
     }
     std::vector<int> col;
     int nc = 0;
-    if (!misra_gries(n, m, edges, col, nc)) return GTQA_ERR_INVALID_ARG;
+    if (!edge_colouring(n, m, edges, col, nc)) return GTQA_ERR_INVALID_ARG;
     for (int e = 0; e < m; ++e) colour_out[e] = col[e];
     if (n_colours_out) *n_colours_out = nc;
     return GTQA_OK;

@@ -83,3 +83,29 @@ def test_null_handles_are_rejected(G):
     assert lib.gtqa_trotter_layer(None, 0.5, 0.1) == G.GTQA_ERR_INVALID_ARG
     assert lib.gtqa_regauge(None) == G.GTQA_ERR_INVALID_ARG
     lib.gtqa_destroy(None)
+
+
+def test_library_colouring_uses_delta_colours_when_it_can(G):
+    """Random cubic graphs (n up to 100000), trees and heavy-hex lattices get 3 colours; the
+    Petersen graph and a cubic graph with a bridge (both class 2) fall back to Misra-Gries
+    with 4."""
+    from instances import heavy_hex_graph, random_tree
+    for n, seed in ((50, 1), (1000, 3), (100000, 2)):
+        e = random_regular_graph(n, 3, seed)
+        col, k = G.gtqa_edge_colouring(n, e)
+        assert k == 3 and check_colouring(n, e, col)
+    e = random_regular_graph(16, 3, 0)     # has the bridge {4, 5}
+    col, k = G.gtqa_edge_colouring(16, e)
+    assert k == 4 and check_colouring(16, e, col)
+    t = random_tree(60, 4)
+    col, k = G.gtqa_edge_colouring(60, t)
+    assert k == 3 and check_colouring(60, t, col)
+    nh, eh = heavy_hex_graph(7, 15)
+    col, k = G.gtqa_edge_colouring(nh, eh)
+    assert k == 3 and check_colouring(nh, eh, col)
+    outer = [(i, (i + 1) % 5) for i in range(5)]
+    inner = [(5 + i, 5 + (i + 2) % 5) for i in range(5)]
+    spokes = [(i, i + 5) for i in range(5)]
+    pe = np.array(sorted((min(a, b), max(a, b)) for a, b in outer + inner + spokes), dtype=np.int32)
+    col, k = G.gtqa_edge_colouring(10, pe)
+    assert k == 4 and check_colouring(10, pe, col)

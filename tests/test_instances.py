@@ -114,3 +114,28 @@ def test_random_gate_inputs_are_unitary_and_seeded():
     assert np.abs(W @ np.conj(np.swapaxes(W, 1, 2)) - np.eye(2)).max() < 1e-12
     e2, U2, _, _ = random_gate_inputs(10, 12, 20, 7, seed=3)
     assert np.array_equal(e, e2) and np.array_equal(U, U2)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_delta_colouring_of_cubic_graphs_trees_and_heavy_hex(seed):
+    """The Kempe-chain search finds Delta = 3 colours on random cubic graphs (n = 1000),
+    trees and heavy-hex lattices, and the result is a proper colouring."""
+    from instances import delta_edge_colouring, make_heavy_hex_instance
+    for inst in (make_instance(1000, seed), make_tree_instance(40, seed), make_heavy_hex_instance(4, 11, seed)):
+        assert check_colouring(inst.n, inst.edges, inst.colour)
+        assert inst.n_colours == 3
+        col = delta_edge_colouring(inst.n, inst.edges, seed=seed + 1)
+        assert col is not None and check_colouring(inst.n, inst.edges, col) and col.max() == 2
+
+
+def test_delta_colouring_gives_up_on_the_petersen_graph():
+    """The Petersen graph is cubic but needs 4 colours: the search gives up and edge_colouring
+    falls back to Misra-Gries."""
+    from instances import delta_edge_colouring
+    outer = [(i, (i + 1) % 5) for i in range(5)]
+    inner = [(5 + i, 5 + (i + 2) % 5) for i in range(5)]
+    spokes = [(i, i + 5) for i in range(5)]
+    edges = np.array(sorted((min(a, b), max(a, b)) for a, b in outer + inner + spokes), dtype=np.int32)
+    assert delta_edge_colouring(10, edges, max_steps=3000) is None
+    col = edge_colouring(10, edges)
+    assert check_colouring(10, edges, col) and col.max() == 3
