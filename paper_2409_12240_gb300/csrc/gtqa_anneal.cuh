@@ -128,7 +128,7 @@ template <int CHI>
 struct GateSm {
     cd X[4][CHI][CHI * CHI];   // [block][col][row]: (a,0) (a,1) (b,0) (b,1); reused for staging
     cd vk[4][CHI];
-    double tau[4][CHI];
+    double tau[4][CHI];        // square roots of the reflector coefficients
     cd M[4 * CHI * CHI];
     cd V[4 * CHI * CHI];
     cd G[4 * CHI * CHI];       // mixed: V^H V, then M V
@@ -141,6 +141,7 @@ struct GateSm {
     cd ph[4];
     int perm[2 * CHI];
     int keep;
+    unsigned relmask;          // mixed: columns that decide the polish's stop
     int flag;
     int nrot;
 };
@@ -203,7 +204,8 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
         const double ra = a2 > 0.0 ? nr_rsqrt(a2) : 0.0;
         const double axkk = a2 * ra;
         const cd ph = a2 > 0.0 ? cd{xkk.x * ra, xkk.y * ra} : cd{1.0, 0.0};
-        const double tau = nrm > 0.0 ? nr_rcp(nrm * (nrm + axkk)) : 0.0;
+        const double stau = nrm > 0.0 ? nr_rsqrt(nrm * (nrm + axkk)) : 0.0;   // sqrt(tau)
+        const double tau = stau * stau;
         const cd vkk = (axkk + nrm) * ph;
         const cd v0 = (r0 == k) ? vkk : x0;
         const cd v1 = x1;
@@ -221,7 +223,7 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
         if (r0 == k) Xk[k] = (-nrm) * ph;
         if (l == 0) {
             sm.vk[blk][k] = vkk;
-            sm.tau[blk][k] = tau;
+            sm.tau[blk][k] = stau;
         }
         __syncwarp(gm);
     }
@@ -314,10 +316,12 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
         team_bar<TEAM>(team);
         if constexpr (TEAM <= 32) {
             WarpGroup grp{group_mask<TEAM>()};
-            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-13, 3e-7, 60, &nrot);
+            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-13, 3e-7, 60, &nrot,
+                                       c.chi, &sm.relmask);
         } else {
             TeamGroup<TEAM> grp{team, &sm.flag};
-            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-13, 3e-7, 60, &nrot);
+            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-13, 3e-7, 60, &nrot,
+                                       c.chi, &sm.relmask);
         }
     }
     if (nrot) atomicAdd(&sm.nrot, nrot);
@@ -330,31 +334,28 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
     team_bar<TEAM>(team);
     for (int cc = tid; cc < NM; cc += TEAM) sm.perm[desc_rank(sm.sig, NM, cc)] = cc;
     team_bar<TEAM>(team);
-    if (tid == 0) {
+    if (tid < NM) {   // lane r holds the r-th largest singular value
+        const unsigned mk = group_mask<NM>();
+        const double sv = sm.sig[sm.perm[tid]];
         const double smax = sm.sig[sm.perm[0]];
-        int cnt = 0;
-        double tot = 0.0;
-        for (int r = 0; r < NM; ++r) {
-            const double s = sm.sig[sm.perm[r]];
-            tot += s * s;
-            cnt += (s > c.svd_cut * smax) ? 1 : 0;
-        }
+        const int cnt = __popc(__ballot_sync(mk, sv > c.svd_cut * smax));
         int keep = cnt < c.chi ? cnt : c.chi;
         if (keep < 1) keep = 1;
-        double kept = 0.0, drop = 0.0;
-        for (int r = 0; r < NM; ++r) {
-            const double s = sm.sig[sm.perm[r]];
-            if (r < keep) kept += s * s; else drop += s * s;
-        }
+        const double s2 = sv * sv;
+        const double kept = group_sum<NM>(tid < keep ? s2 : 0.0, mk);
+        const double drop = group_sum<NM>(tid < keep ? 0.0 : s2, mk);
         const double inv = kept > 0.0 ? nr_rsqrt(kept) : 0.0;
-        for (int r = 0; r < CHI; ++r) c.lam[(size_t)e * CHI + r] = (r < keep) ? sm.sig[sm.perm[r]] * inv : 0.0;
-        const double disc = tot > 0.0 ? drop * nr_rcp(tot) : 0.0;
-        atomicAdd(&c.stats[0], disc);
-        // log of the gate fidelity (1 - disc)^2, Eq. (gate_fidelity); a float log in the mixed mode
-        atomicAdd(&c.stats[1], Mode::mixed ? 2.0 * (double)log1pf(-(float)disc) : 2.0 * log1p(-disc));
-        atomicAdd(&c.stats[2], (double)sweeps * (NM - 1) * (NM / 2));
-        atomicAdd(&c.stats[3], (double)sm.nrot);
-        sm.keep = keep;
+        if (tid < CHI) c.lam[(size_t)e * CHI + tid] = (tid < keep) ? sv * inv : 0.0;
+        if (tid == 0) {
+            const double tot = kept + drop;
+            const double disc = tot > 0.0 ? drop * nr_rcp(tot) : 0.0;
+            atomicAdd(&c.stats[0], disc);
+            // log of the gate fidelity (1 - disc)^2, Eq. (gate_fidelity); a float log in the mixed mode
+            atomicAdd(&c.stats[1], Mode::mixed ? 2.0 * (double)log1pf(-(float)disc) : 2.0 * log1p(-disc));
+            atomicAdd(&c.stats[2], (double)sweeps * (NM - 1) * (NM / 2));
+            atomicAdd(&c.stats[3], (double)sm.nrot);
+            sm.keep = keep;
+        }
     }
     team_bar<TEAM>(team);
     const int keep = sm.keep;
@@ -378,7 +379,7 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
     // H_k = I - tau v v^H is applied as I - u u^H with u = sqrt(tau) v (|u| = sqrt 2), so
     // neither factor over- or underflows when the reflector is tiny (matters in float).
     for (int k = CHI - 1; k >= 0; --k) {
-        const double st = nr_sqrt(sm.tau[blk][k]);
+        const double st = sm.tau[blk][k];
         const C<RB> v0 = ccast<RB>(st * ((r0 == k) ? sm.vk[blk][k] : ((r0 > k) ? sm.X[blk][k][r0] : cd{0.0, 0.0})));
         const C<RB> v1 = ccast<RB>(st * sm.X[blk][k][r1]);
 #pragma unroll

@@ -242,10 +242,19 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
 //    orthogonality test alone decides convergence;
 //  * c = 1 - t^2/2 + 3t^4/8 when every pair of the group has t^2 < 1e-6 (the dropped terms are
 //    below 3.2e-19).
-// The quadratic stop of jacobi_svd applies (quad_tol).  Returns the sweeps run.
+// The quadratic stop of jacobi_svd applies (quad_tol).
+// keep_rank < N (the caller keeps at most keep_rank singular triplets, as in the truncation of
+// App. D): only pairs that touch a column among the keep_rank largest (with a margin: norms
+// within a factor 4 of the keep_rank-th largest at entry count) decide the quadratic stop, and
+// a pair of such a column p with a smaller one q is judged by |gamma| against alpha_p (the
+// size of the rotation of the kept column) rather than sqrt(alpha_p beta_q).  The kept
+// columns then converge as with keep_rank = N, while rotations among discarded columns, which
+// leave the kept subspace unchanged, no longer force a confirming sweep.  Every pair is still
+// rotated in each sweep that runs.  Returns the sweeps run.
 template <int N, typename Group>
 __device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, const Group& grp, unsigned pair_mask,
-                             double tol, double quad_tol, int max_sweeps, int* nrot) {
+                             double tol, double quad_tol, int max_sweeps, int* nrot, int keep_rank = N,
+                             unsigned* relmask = nullptr) {
     using CD = C<double>;
     const int k = g / N;
     const int r = g % N;
@@ -258,6 +267,25 @@ __device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, con
         }
     }
     grp.sync();
+    const bool partial = keep_rank < N && relmask != nullptr;
+    if (partial) {
+        if (g == 0) *relmask = 0u;
+        grp.sync();
+        if (g < N) {
+            // the keep_rank-th largest norm, then every column within a factor 4 of it
+            const double x = nrm[g];
+            int above = 0;
+            for (int j = 0; j < N; ++j) above += (nrm[j] > x) || (nrm[j] == x && j < g);
+            if (above == keep_rank - 1) {
+                const double thr = 0.25 * x;
+                unsigned mask = 0u;
+                for (int j = 0; j < N; ++j) mask |= (nrm[j] >= thr) ? (1u << j) : 0u;
+                *relmask = mask;
+            }
+        }
+        grp.sync();
+    }
+    const unsigned rel = partial ? *relmask : 0xffffffffu;
     const double tol2 = tol * tol, quad2 = quad_tol * quad_tol;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
@@ -275,7 +303,13 @@ __device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, con
             const bool rot = g2 > 0.0 && g2 > tol2 * ab;
             double tau = 0.0, t2 = 0.0;
             if (rot) {
-                if (g2 > quad2 * ab) big = 1;
+                const bool rp = (rel >> p) & 1u, rq = (rel >> q) & 1u;
+                if (rp && rq) {
+                    if (g2 > quad2 * ab) big = 1;
+                } else if (rp || rq) {
+                    const double mx = alpha > beta ? alpha : beta;
+                    if (g2 > quad2 * mx * mx) big = 1;
+                }
                 const double d = beta - alpha;
                 double rsc;
                 asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(rsc) : "d"(alpha + beta));
