@@ -344,10 +344,11 @@ def make_instance(n: int, seed: int, d: int = 3, J: str = "gauss", h_std: float 
     return Instance(n, edges, Jv.astype(np.float64), hv.astype(np.float64), colour, int(seed))
 
 
-def make_tree_instance(n: int, seed: int, h_std: float = 0.1, base: int = BASE_SEED) -> Instance:
-    """Random tree (max degree 3) with Gaussian J ~ N(0,1), h ~ N(0, h_std)."""
-    s = base + 1_000_000 + 3 * int(seed)
-    edges = random_tree(n, s)
+def make_tree_instance(n: int, seed: int, h_std: float = 0.1, base: int = BASE_SEED,
+                       max_degree: int = 3) -> Instance:
+    """Random tree (max degree 3, or max_degree) with Gaussian J ~ N(0,1), h ~ N(0, h_std)."""
+    s = base + 1_000_000 + 3 * int(seed) + (0 if max_degree == 3 else 100_000 * max_degree)
+    edges = random_tree(n, s, max_degree)
     m = edges.shape[0]
     Jv = _rng(s + 1).normal(0.0, 1.0, size=m)
     hv = _rng(s + 2).normal(0.0, h_std, size=n) if h_std > 0 else np.zeros(n)

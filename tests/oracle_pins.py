@@ -73,11 +73,12 @@ def gates_exact_without_truncation(inst: Instance, layers: int = 2, dt: float = 
     return _overlap_err(O.to_statevector(st), psi)
 
 
-def gtqa_tree_exact(seed: int, n: int = 10, K: int = 6, dt: float = 0.3) -> dict:
+def gtqa_tree_exact(seed: int, n: int = 10, K: int = 6, dt: float = 0.3, max_degree: int = 3) -> dict:
     """On trees BP is exact (Sec. II B), so GTQA marginals without truncation equal
     the exact ones at every layer; lambda equals the edge-cut Schmidt values
-    (Sec. II C); the contracted network equals the exact state."""
-    inst = make_tree_instance(n, seed)
+    (Sec. II C); the contracted network equals the exact state.  max_degree = 4 exercises
+    vertex tensors with four bonds (the 4-regular graphs of Sec. V)."""
+    inst = make_tree_instance(n, seed, max_degree=max_degree)
     st = O.plus_state(inst.n, inst.edges)
     psi, rhos = SV.evolve(inst.n, inst.edges, inst.J, inst.h, K, dt)
     rho_err = 0.0

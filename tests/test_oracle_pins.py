@@ -206,3 +206,12 @@ def test_general_gates_exact_on_trees(seed):
 @pytest.mark.parametrize("seed", [0, 1])
 def test_general_gate_truncation_keeps_optimal_schmidt_approximation(seed):
     assert P.general_gate_truncation_fidelity(seed) < 1e-10
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_gtqa_exact_on_degree_four_trees(seed):
+    import numpy as np
+    from instances import make_tree_instance
+    assert np.bincount(make_tree_instance(10, seed, max_degree=4).edges.ravel()).max() == 4
+    r = P.gtqa_tree_exact(seed, max_degree=4)
+    assert r["rho"] < 1e-10 and r["lam"] < 1e-10 and r["state"] < 1e-10, r
