@@ -47,7 +47,7 @@ extern "C" {
 #endif
 
 #define GTQA_OK 0
-#define GTQA_ERR_INVALID_ARG 1   /* bad size, index, degree > 3, duplicate edge, bad colouring, NaN input */
+#define GTQA_ERR_INVALID_ARG 1   /* bad size, index, degree > 4, duplicate edge, bad colouring, NaN input */
 #define GTQA_ERR_NOT_CONVERGED 2 /* BP hit max_iter before dist/|E| < tol; state and outputs valid */
 #define GTQA_ERR_NUMERIC 3       /* NaN or Inf detected on the device */
 #define GTQA_ERR_OOM 4           /* device allocation failed */
@@ -105,14 +105,19 @@ void gtqa_options_init(gtqa_options* opt);
 /*
  * Create the state |+>^N (all bond dimensions 1, Sec. III A) of one problem instance.
  *   n, m       vertices and edges
- *   edges      host int32 [m][2]; 0 <= u, v < n, u != v, no repeated pair, degree <= 3
+ *   edges      host int32 [m][2]; 0 <= u, v < n, u != v, no repeated pair, degree <= 4
  *   colour     host int32 [m] proper edge colouring (each colour a matching), or NULL
- *              for the library's own Misra-Gries colouring (<= Delta + 1 colours).
+ *              for the library's own (gtqa_edge_colouring).
  *              Gates run colour by colour, ascending (the paper leaves the order open).
  *   J, h       host float64 couplings [m] and fields [n] of Eq. (objective_function)
  *   chi        maximal bond dimension, 1 <= chi <= 8
  *   opt        options or NULL for defaults
  *   out        receives the new state; *out is NULL on failure
+ * Graphs with a vertex of degree 4 (the random 4-regular graphs of Sec. V) get vertex tensors
+ * with four bonds, Gamma [n][2][CHI]^4, and plain per-phase kernels.  Such a state needs the
+ * FP64 precision, one instance and chi <= 4: anything else returns GTQA_ERR_UNSUPPORTED.
+ * gtqa_sample and gtqa_residual return GTQA_ERR_UNSUPPORTED on it; every other call works
+ * as documented.  Its BP reads the distance on the host after every sweep.
  */
 int gtqa_create(int32_t n, int32_t m, const int32_t* edges, const int32_t* colour,
                 const double* J, const double* h, int32_t chi,
@@ -294,6 +299,10 @@ int gtqa_stats(gtqa_state* s, gtqa_stats_t* out);
  */
 int gtqa_get_state(gtqa_state* s, double* gamma_out, double* lambda_out, double* messages_out);
 int gtqa_set_state(gtqa_state* s, const double* gamma, const double* lambda, const double* messages);
+
+/* Number of bonds per vertex tensor: 3, or 4 for a graph with a degree-4 vertex (Gamma is
+ * then [n][2][CHI][CHI][CHI][CHI] in gtqa_get_state / gtqa_set_state). */
+int gtqa_max_degree(const gtqa_state* s, int32_t* D_out);
 
 /* Sizes: total vertices and edges, storage bond dimension CHI, number of colours. */
 int gtqa_sizes(const gtqa_state* s, int64_t* n, int64_t* m, int32_t* chi_storage, int32_t* n_colours);

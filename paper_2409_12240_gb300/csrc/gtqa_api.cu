@@ -64,6 +64,13 @@ struct gtqa_state {
     cd* sq_W = nullptr;
     size_t sq_cap = 0;
     std::vector<int> h_edges;   // endpoints of every edge (2m), for host-side scheduling
+    // degree-4 graphs: slots per vertex, all vertex ids, host copies for the gate phases
+    int D = 3;
+    int4* vslots4 = nullptr;
+    int* allv = nullptr;
+    std::vector<int> h_deg, h_cedges, h_coff;
+    std::vector<double> h_J, h_h;
+    int cur4 = 0;               // message buffer holding the latest messages (degree 4)
     // host counters
     long long layers = 0, gates = 0, launches = 0;
     int sticky = GTQA_OK;
@@ -129,7 +136,9 @@ int storage_chi(int chi) {
 
 bool mixed(const gtqa_state* s) { return s->precision == GTQA_MIXED; }
 size_t elem_bytes(const gtqa_state* s) { return mixed(s) ? sizeof(cf) : sizeof(cd); }
-size_t gamma_elems(const gtqa_state* s) { return (size_t)s->n * 2 * s->CHI * s->CHI * s->CHI; }
+size_t gamma_elems(const gtqa_state* s) {
+    return (size_t)s->n * 2 * s->CHI * s->CHI * s->CHI * (s->D == 4 ? s->CHI : 1);
+}
 size_t msg_elems(const gtqa_state* s) { return (size_t)s->m * 2 * s->CHI * s->CHI; }
 
 cudaEvent_t prof_event(gtqa_state* s) {
@@ -408,7 +417,7 @@ void free_state(gtqa_state* s) {
                     s->vert_edges, s->vert_inst, s->J, s->h, s->colour_edges, s->colour_off, s->last_colour, s->first_colour,
                     s->iso, s->inst_vbeg, s->inst_m, s->acc, s->inst_done, s->inst_iters, s->inst_dist,
                     s->stats, s->ctl, s->rho, s->sign, s->flags, s->rbuf, s->cutbuf, s->xs, s->ps,
-                    s->gate_edge, s->gate_U, s->sq_vertex, s->sq_W};
+                    s->gate_edge, s->gate_U, s->sq_vertex, s->sq_W, s->vslots4, s->allv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : s->pending) {
@@ -533,7 +542,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
                 keys.push_back(a * n[b] + c);
                 ge[2 * (eoff + e)] = (int)(u + voff);
                 ge[2 * (eoff + e) + 1] = (int)(v + voff);
-                if (++deg[u + voff] > 3 || ++deg[v + voff] > 3) return GTQA_ERR_INVALID_ARG;
+                if (++deg[u + voff] > 4 || ++deg[v + voff] > 4) return GTQA_ERR_INVALID_ARG;
             }
             std::vector<long long> sk = keys;
             std::sort(sk.begin(), sk.end());
@@ -570,8 +579,14 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
             ncol = gcol[e] + 1 > ncol ? gcol[e] + 1 : ncol;
         }
     }
+    // vertex degree 4 (Sec. V's 4-regular graphs): the plain degree-4 kernels, FP64, one
+    // instance, CHI <= 4
+    int Dmax = 0;
+    for (long long v = 0; v < N; ++v) Dmax = std::max(Dmax, deg[v]);
+    if (Dmax == 4 && (B != 1 || o.precision != GTQA_FP64 || storage_chi(chi) > 4)) return GTQA_ERR_UNSUPPORTED;
     gtqa_state* s = new (std::nothrow) gtqa_state();
     if (!s) return GTQA_ERR_OOM;
+    s->D = Dmax == 4 ? 4 : 3;
     s->B = B;
     s->n = (int)N;
     s->m = (int)Mtot;
@@ -609,7 +624,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
     }
     s->nblocks = sms;
     // slots: incident edges in ascending id; colour of each vertex's last gate
-    std::vector<int4> vedges(N, make_int4(-1, -1, -1, 0));
+    std::vector<int4> vedges(N, make_int4(-1, -1, -1, 0)), v4(N, make_int4(-1, -1, -1, -1));
     std::vector<int4> einfo(Mtot);
     std::vector<int> lastc(N, -1), firstc(N, -1);
     for (long long e = 0; e < Mtot; ++e) {
@@ -618,7 +633,9 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
             const int v = ge[2 * e + q];
             int4& ve = vedges[v];
             const int k = ve.w;
-            if (k == 0) ve.x = (int)e; else if (k == 1) ve.y = (int)e; else ve.z = (int)e;
+            if (k == 0) ve.x = (int)e; else if (k == 1) ve.y = (int)e; else if (k == 2) ve.z = (int)e;
+            int4& w4 = v4[v];
+            if (k == 0) w4.x = (int)e; else if (k == 1) w4.y = (int)e; else if (k == 2) w4.z = (int)e; else w4.w = (int)e;
             sl[q] = k;
             ve.w = k + 1;
             lastc[v] = std::max(lastc[v], gcol[e]);
@@ -639,6 +656,13 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
             if (gcol[e] == c) cedges.push_back((int)e);
     }
     coff[ncol] = (int)cedges.size();
+    if (s->D == 4) {
+        s->h_cedges = cedges;
+        s->h_coff = coff;
+        s->h_J.assign(J ? J : (const double*)nullptr, J ? J + Mtot : (const double*)nullptr);
+        s->h_h.assign(h, h + N);
+        s->h_deg.assign(deg.begin(), deg.end());
+    }
     const int CHI = s->CHI;
     const size_t gel = gamma_elems(s), mel = msg_elems(s), eb = elem_bytes(s);
     int rc = GTQA_OK;
@@ -658,12 +682,23 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         (rc = dalloc(s, &s->rho, (size_t)s->n * 4)) || (rc = dalloc(s, &s->sign, s->n)) ||
         (rc = dalloc(s, &s->flags, 4)) || (rc = dalloc(s, &s->rbuf, 1)) ||
         (rc = dalloc(s, &s->cutbuf, std::max(s->m, 1))) || (rc = dalloc(s, &s->xs, s->n)) ||
-        (rc = dalloc(s, &s->ps, s->n))) {
+        (rc = dalloc(s, &s->ps, s->n)) || (s->D == 4 && (rc = dalloc(s, &s->vslots4, s->n))) ||
+        (s->D == 4 && (rc = dalloc(s, &s->allv, s->n)))) {
         free_state(s);
         return rc;
     }
+    if (s->D == 4) {
+        std::vector<int> all(N);
+        for (long long a = 0; a < N; ++a) all[a] = (int)a;
+        if (!cuda_ok(s, cudaMemcpyAsync(s->vslots4, v4.data(), sizeof(int4) * N, cudaMemcpyHostToDevice, s->stream)) ||
+            !cuda_ok(s, cudaMemcpyAsync(s->allv, all.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s->stream)) ||
+            !cuda_ok(s, cudaStreamSynchronize(s->stream))) {
+            free_state(s);
+            return GTQA_ERR_CUDA;
+        }
+    }
     // |+>^N: Gamma[a][i][0][0][0] = 1/sqrt(2); lambda_e = (1, 0, ...)
-    const size_t H = (size_t)CHI * CHI * CHI;
+    const size_t H = (size_t)CHI * CHI * CHI * (s->D == 4 ? CHI : 1);
     std::vector<unsigned char> g0(gel * eb, 0);
     for (long long a = 0; a < N; ++a) {
         for (int i = 0; i < 2; ++i) {
@@ -805,6 +840,159 @@ void tridiag_min_eigvec(const std::vector<double>& a, const std::vector<double>&
     }
 }
 
+// ---------------------------------------------------------------------------
+// degree-4 graphs: host orchestration of the plain kernels of gtqa_deg4.cuh
+// ---------------------------------------------------------------------------
+D4Args d4_args(gtqa_state* s, int cur) {
+    D4Args a;
+    a.Gamma = s->Gamma;
+    a.T = s->T;
+    a.lam = s->lam;
+    a.msg_cur = s->msg[cur];
+    a.msg_nxt = s->msg[cur ^ 1];
+    a.X = s->X;
+    a.vslots = s->vslots4;
+    a.edge_info = s->edge_info;
+    a.n = s->n;
+    a.m = s->m;
+    a.acc = s->acc;
+    a.warm = 0;
+    return a;
+}
+
+int d4_fail(gtqa_state* s) {
+    cudaGetLastError();
+    s->sticky = GTQA_ERR_CUDA;
+    return GTQA_ERR_CUDA;
+}
+
+// exp(-i t X) on every vertex (Sec. II D)
+int d4_mixing(gtqa_state* s, double t) {
+    if (t == 0.0 || s->n == 0) return GTQA_OK;
+    std::vector<double> W(8 * (size_t)s->n);
+    const double c = std::cos(t), sn = std::sin(t);
+    for (int a = 0; a < s->n; ++a) {
+        double* w = &W[8 * (size_t)a];
+        w[0] = c; w[1] = 0.0; w[2] = 0.0; w[3] = -sn;
+        w[4] = 0.0; w[5] = -sn; w[6] = c; w[7] = 0.0;
+    }
+    int rc;
+    if ((rc = grow_pair(s, &s->sq_vertex, &s->sq_W, 4, s->sq_cap, (size_t)s->n))) return rc;
+    if (!cuda_ok(s, cudaMemcpyAsync(s->sq_W, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, s->stream)))
+        return GTQA_ERR_CUDA;
+    if (d4_single_gates_launch(s->CHI, s->Gamma, s->allv, s->sq_W, s->n, s->stream) != cudaSuccess) return d4_fail(s);
+    s->launches += 1;
+    return GTQA_OK;
+}
+
+// Edge gates of U_Z(t_Z) by colour class (App. F; App. E through the whole-side update).
+int d4_interaction(gtqa_state* s, double tZ) {
+    const int m = s->m;
+    if (m == 0) return GTQA_OK;
+    std::vector<double> U(32 * (size_t)m, 0.0);
+    for (int q = 0; q < m; ++q) {
+        const int e = s->h_cedges[q];
+        const int a = s->h_edges[2 * (size_t)e], b = s->h_edges[2 * (size_t)e + 1];
+        const double ha = s->h_h[a] / s->h_deg[a], hb = s->h_h[b] / s->h_deg[b], Je = s->h_J.empty() ? 0.0 : s->h_J[e];
+        for (int ia = 0; ia < 2; ++ia)
+            for (int ib = 0; ib < 2; ++ib) {
+                const double za = 1.0 - 2.0 * ia, zb = 1.0 - 2.0 * ib;
+                const double ph = -tZ * (Je * za * zb + ha * za + hb * zb);
+                const int d = 2 * ia + ib;
+                U[32 * (size_t)q + 2 * (4 * d + d)] = std::cos(ph);
+                U[32 * (size_t)q + 2 * (4 * d + d) + 1] = std::sin(ph);
+            }
+    }
+    int rc;
+    if ((rc = grow_pair(s, &s->gate_edge, &s->gate_U, 16, s->gate_cap, (size_t)m))) return rc;
+    if (!cuda_ok(s, cudaMemcpyAsync(s->gate_U, U.data(), sizeof(double) * U.size(), cudaMemcpyHostToDevice, s->stream)))
+        return GTQA_ERR_CUDA;
+    for (int c = 0; c < s->ncol; ++c) {
+        GenArgs g;
+        g.Gamma = s->Gamma;
+        g.lam = s->lam;
+        g.edge_info = s->edge_info;
+        g.vert_edges = s->vslots4;
+        g.gate_edge = s->colour_edges + s->h_coff[c];
+        g.gate_U = s->gate_U + 16 * (size_t)s->h_coff[c];
+        g.count = s->h_coff[c + 1] - s->h_coff[c];
+        g.stats = s->stats;
+        g.chi = s->chi;
+        g.svd_cut = s->svd_cutoff;
+        if (d4_general_gates_launch(s->CHI, g, s->stream) != cudaSuccess) return d4_fail(s);
+        s->launches += 1;
+    }
+    return GTQA_OK;
+}
+
+int d4_trotter(gtqa_state* s, double tZ, double tXpre, double tXpost) {
+    int rc;
+    if ((rc = d4_mixing(s, tXpre)) || (rc = d4_interaction(s, tZ)) || (rc = d4_mixing(s, tXpost))) return rc;
+    s->layers += 1;
+    s->gates += s->m;
+    return GTQA_OK;
+}
+
+int d4_regauge(gtqa_state* s) {
+    Ctx c = make_ctx(s);
+    if (d4_regauge_launch(s->CHI, c, s->cur4, d4_args(s, s->cur4), s->stream) != cudaSuccess) return d4_fail(s);
+    s->launches += 2;
+    return GTQA_OK;
+}
+
+// Flooding BP (App. B): one launch per sweep; the host reads the trace-norm distance after
+// each sweep and stops after the sweep where dist/|E| < tol, or after max_iter sweeps.
+int d4_bp(gtqa_state* s, double tol, int max_iter, uint32_t flags, int32_t* iters_out, double* dist_out) {
+    int cur = s->cur4;
+    D4Args a = d4_args(s, cur);
+    a.warm = (flags & GTQA_BP_WARM_START) ? 1 : 0;
+    a.msg_nxt = s->msg[cur];   // the init kernel writes the warm start where the first sweep reads
+    if (s->n > 0 && d4_bp_init_launch(s->CHI, a, s->stream) != cudaSuccess) return d4_fail(s);
+    s->launches += 1;
+    int it = 0;
+    double dist = 0.0;
+    bool conv = false;
+    for (; it < max_iter;) {
+        if (!cuda_ok(s, cudaMemsetAsync(s->acc, 0, sizeof(double), s->stream))) return GTQA_ERR_CUDA;
+        D4Args w = d4_args(s, cur);
+        if (d4_bp_sweep_launch(s->CHI, w, s->stream) != cudaSuccess) return d4_fail(s);
+        s->launches += 1;
+        double acc = 0.0;
+        if (!cuda_ok(s, cudaMemcpyAsync(&acc, s->acc, sizeof(double), cudaMemcpyDeviceToHost, s->stream)) ||
+            !cuda_ok(s, cudaStreamSynchronize(s->stream)))
+            return GTQA_ERR_CUDA;
+        cur ^= 1;
+        ++it;
+        dist = s->m > 0 ? acc / s->m : 0.0;
+        if (!(dist == dist)) {
+            s->sticky = GTQA_ERR_NUMERIC;
+            return GTQA_ERR_NUMERIC;
+        }
+        if (dist < tol) {
+            conv = true;
+            break;
+        }
+    }
+    s->cur4 = cur;
+    Control ctl;
+    int rc;
+    if ((rc = read_ctl(s, &ctl))) return rc;
+    ctl.cur = cur;
+    ctl.last_iters = it;
+    ctl.last_dist = dist;
+    ctl.not_conv = conv ? 0 : 1;
+    ctl.sweeps_total += it;
+    ctl.bp_calls += 1;
+    ctl.nc_calls += conv ? 0 : 1;
+    if (!cuda_ok(s, cudaMemcpyAsync(s->ctl, &ctl, sizeof(Control), cudaMemcpyHostToDevice, s->stream)) ||
+        !cuda_ok(s, cudaStreamSynchronize(s->stream)))
+        return GTQA_ERR_CUDA;
+    if (iters_out) *iters_out = it;
+    if (dist_out) *dist_out = dist;
+    if ((flags & GTQA_BP_REGAUGE) && (rc = d4_regauge(s))) return rc;
+    return conv ? GTQA_OK : GTQA_ERR_NOT_CONVERGED;
+}
+
 }  // namespace
 
 extern "C" {
@@ -832,6 +1020,7 @@ int gtqa_trotter_layer(gtqa_state* s, double tau, double dt) {
     int rc = check_state(s);
     if (rc) return rc;
     if (!std::isfinite(tau) || !std::isfinite(dt)) return GTQA_ERR_INVALID_ARG;
+    if (s->D == 4) return d4_trotter(s, dt * tau, 0.0, dt * (1.0 - tau));
     Ctx c = make_ctx(s);
     c.phases = PH_GATES;
     c.k0 = c.k1 = 0;
@@ -848,6 +1037,7 @@ int gtqa_trotter_split(gtqa_state* s, double t_Z, double t_X_pre, double t_X_pos
     int rc = check_state(s);
     if (rc) return rc;
     if (!std::isfinite(t_Z) || !std::isfinite(t_X_pre) || !std::isfinite(t_X_post)) return GTQA_ERR_INVALID_ARG;
+    if (s->D == 4) return d4_trotter(s, t_Z, t_X_pre, t_X_post);
     Ctx c = make_ctx(s);
     c.phases = PH_GATES;
     c.k0 = c.k1 = 0;
@@ -866,6 +1056,7 @@ int gtqa_bp_sweep(gtqa_state* s, double tol, int32_t max_iter, uint32_t flags, i
     int rc = check_state(s);
     if (rc) return rc;
     if (max_iter < 1 || !(tol >= 0.0) || (flags & ~3u)) return GTQA_ERR_INVALID_ARG;
+    if (s->D == 4) return d4_bp(s, tol, max_iter, flags, iters_out, dist_out);
     Ctx c = make_ctx(s);
     c.phases = PH_BP | ((flags & GTQA_BP_WARM_START) ? PH_WARM : 0u);
     c.k0 = c.k1 = 0;
@@ -888,6 +1079,7 @@ int gtqa_sample(gtqa_state* s, int32_t k, const int32_t* order, const double* u,
                 int8_t* x_out, double* p_out) {
     int rc = check_state(s);
     if (rc) return rc;
+    if (s->D == 4) return GTQA_ERR_UNSUPPORTED;
     if (k < 0 || k > s->n || (k > 0 && (!order || !u)) || !x_out || max_iter < 1 || !(tol >= 0.0))
         return GTQA_ERR_INVALID_ARG;
     std::vector<char> seen(s->n, 0);
@@ -966,15 +1158,16 @@ int gtqa_apply_gates(gtqa_state* s, int32_t k, const int32_t* edge, const double
         a.Gamma = s->Gamma;
         a.lam = s->lam;
         a.edge_info = s->edge_info;
-        a.vert_edges = s->vert_edges;
+        a.vert_edges = s->D == 4 ? s->vslots4 : s->vert_edges;
         a.gate_edge = s->gate_edge + off[L];
         a.gate_U = s->gate_U + 16 * (size_t)off[L];
         a.count = off[L + 1] - off[L];
         a.stats = s->stats;
         a.chi = s->chi;
         a.svd_cut = s->svd_cutoff;
-        const cudaError_t e = mixed(s) ? general_gates_launch_mixed(s->CHI, a, s->stream)
-                                       : general_gates_launch_fp64(s->CHI, a, s->stream);
+        const cudaError_t e = s->D == 4   ? d4_general_gates_launch(s->CHI, a, s->stream)
+                              : mixed(s) ? general_gates_launch_mixed(s->CHI, a, s->stream)
+                                         : general_gates_launch_fp64(s->CHI, a, s->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             s->sticky = GTQA_ERR_CUDA;
@@ -1027,8 +1220,9 @@ int gtqa_apply_single_qubit_gates(gtqa_state* s, int32_t k, const int32_t* verte
     if (!cuda_ok(s, cudaMemcpyAsync(s->sq_vertex, vs.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s->stream)) ||
         !cuda_ok(s, cudaMemcpyAsync(s->sq_W, Wd.data(), sizeof(double) * Wd.size(), cudaMemcpyHostToDevice, s->stream)))
         return GTQA_ERR_CUDA;
-    const cudaError_t e = mixed(s) ? single_gates_launch_mixed(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream)
-                                   : single_gates_launch_fp64(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream);
+    const cudaError_t e = s->D == 4 ? d4_single_gates_launch(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream)
+                          : mixed(s) ? single_gates_launch_mixed(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream)
+                                     : single_gates_launch_fp64(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         s->sticky = GTQA_ERR_CUDA;
@@ -1041,6 +1235,7 @@ int gtqa_apply_single_qubit_gates(gtqa_state* s, int32_t k, const int32_t* verte
 int gtqa_regauge(gtqa_state* s) {
     int rc = check_state(s);
     if (rc) return rc;
+    if (s->D == 4) return d4_regauge(s);
     Ctx c = make_ctx(s);
     c.phases = PH_REGAUGE;
     c.k0 = c.k1 = 0;
@@ -1052,6 +1247,15 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
     if (rc) return rc;
     if (K < 1 || k_begin < 1 || k_end < k_begin || k_end > K || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1)
         return GTQA_ERR_INVALID_ARG;
+    if (s->D == 4) {
+        for (int k = k_begin; k <= k_end; ++k) {
+            const double tau = (double)k / (double)K;
+            if ((rc = d4_trotter(s, dt * tau, 0.0, dt * (1.0 - tau)))) return rc;
+            rc = d4_bp(s, tol, max_iter, GTQA_BP_DEFAULT, nullptr, nullptr);
+            if (rc && rc != GTQA_ERR_NOT_CONVERGED) return rc;
+        }
+        return GTQA_OK;
+    }
     Ctx c = make_ctx(s);
     c.phases = PH_GATES | PH_BP | PH_WARM | PH_REGAUGE;
     c.Ksched = K;
@@ -1077,6 +1281,18 @@ int gtqa_anneal_ex(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, dou
         (order != GTQA_TROTTER_FIRST && order != GTQA_TROTTER_SYMMETRIC) ||
         (order == GTQA_TROTTER_SYMMETRIC && reverse))
         return GTQA_ERR_INVALID_ARG;
+    if (s->D == 4) {
+        for (int k = k_begin; k <= k_end; ++k) {
+            const double tau = (double)k / (double)K, tZ = dt * tau, tX = dt * (1.0 - tau);
+            const bool rev = reverse && reverse[k - k_begin];
+            const double pre = order == GTQA_TROTTER_SYMMETRIC ? 0.5 * tX : (rev ? tX : 0.0);
+            const double post = order == GTQA_TROTTER_SYMMETRIC ? 0.5 * tX : (rev ? 0.0 : tX);
+            if ((rc = d4_trotter(s, tZ, pre, post))) return rc;
+            rc = d4_bp(s, tol, max_iter, GTQA_BP_DEFAULT, nullptr, nullptr);
+            if (rc && rc != GTQA_ERR_NOT_CONVERGED) return rc;
+        }
+        return GTQA_OK;
+    }
     Ctx c = make_ctx(s);
     c.phases = PH_GATES | PH_BP | PH_WARM | PH_REGAUGE;
     c.Ksched = 0;
@@ -1239,6 +1455,7 @@ int gtqa_spectral_bipartition(int32_t n, int32_t m, const int32_t* edges, uint8_
 int gtqa_residual(gtqa_state* s, double* R_out) {
     int rc = check_state(s);
     if (rc) return rc;
+    if (s->D == 4) return GTQA_ERR_UNSUPPORTED;
     if (!R_out) return GTQA_ERR_INVALID_ARG;
     if (!cuda_ok(s, cudaMemsetAsync(s->rbuf, 0, sizeof(double), s->stream))) return GTQA_ERR_CUDA;
     const cudaError_t e = mixed(s) ? residual_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream)
@@ -1263,10 +1480,13 @@ int gtqa_marginals(gtqa_state* s, double* rho_out, int8_t* sign_out) {
     if (!rho_out) return GTQA_ERR_INVALID_ARG;
     {
         ProfScope ps(s, GTQA_K_MARGINALS, s->n);
-        const cudaError_t e = mixed(s) ? marginals_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho,
-                                                                s->sign, s->flags, s->stream)
-                                       : marginals_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho,
-                                                               s->sign, s->flags, s->stream);
+        const cudaError_t e =
+            s->D == 4 ? d4_marginals_launch(s->CHI, (const cd*)s->Gamma, s->lam, s->vslots4, s->n, s->rho, s->sign,
+                                            s->flags, s->stream)
+            : mixed(s) ? marginals_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho, s->sign,
+                                                s->flags, s->stream)
+                       : marginals_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho, s->sign,
+                                               s->flags, s->stream);
         if (!cuda_ok(s, e)) return GTQA_ERR_CUDA;
         s->launches += 1;
     }
@@ -1389,6 +1609,12 @@ int gtqa_set_state(gtqa_state* s, const double* gamma, const double* lambda, con
     if (!cuda_ok(s, cudaMemcpyAsync(s->lam, L.data(), L.size() * sizeof(double), cudaMemcpyHostToDevice, st)) ||
         !cuda_ok(s, cudaStreamSynchronize(st)))
         return GTQA_ERR_CUDA;
+    return GTQA_OK;
+}
+
+int gtqa_max_degree(const gtqa_state* s, int32_t* D_out) {
+    if (!s || !D_out) return GTQA_ERR_INVALID_ARG;
+    *D_out = s->D;
     return GTQA_OK;
 }
 

@@ -5,9 +5,9 @@ namespace gtqa {
 
 cudaError_t general_gates_launch_fp64(int CHI, const GenArgs& a, cudaStream_t st) {
     switch (CHI) {
-        case 2: return general_gates_launch_t<2, ModeFP64>(a, st);
-        case 4: return general_gates_launch_t<4, ModeFP64>(a, st);
-        case 8: return general_gates_launch_t<8, ModeFP64>(a, st);
+        case 2: return general_gates_launch_t<2, 3, ModeFP64>(a, st);
+        case 4: return general_gates_launch_t<4, 3, ModeFP64>(a, st);
+        case 8: return general_gates_launch_t<8, 3, ModeFP64>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -15,9 +15,9 @@ cudaError_t general_gates_launch_fp64(int CHI, const GenArgs& a, cudaStream_t st
 cudaError_t single_gates_launch_fp64(int CHI, void* Gamma, const int* vertex, const cd* W, int count,
                                       cudaStream_t st) {
     switch (CHI) {
-        case 2: return single_gates_launch_t<2, ModeFP64>(Gamma, vertex, W, count, st);
-        case 4: return single_gates_launch_t<4, ModeFP64>(Gamma, vertex, W, count, st);
-        case 8: return single_gates_launch_t<8, ModeFP64>(Gamma, vertex, W, count, st);
+        case 2: return single_gates_launch_t<2, 3, ModeFP64>(Gamma, vertex, W, count, st);
+        case 4: return single_gates_launch_t<4, 3, ModeFP64>(Gamma, vertex, W, count, st);
+        case 8: return single_gates_launch_t<8, 3, ModeFP64>(Gamma, vertex, W, count, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -13,7 +13,8 @@
 //   Gamma~_b[i_b][k][J] = (Q_b conj V)[(J), (i_b, k)] / w_b[J],
 // so that Theta' = Q_a M Q_b^T is the gate applied to the two-site tensor of App. E.
 // One team of (4 CHI)^2 / 2 threads (the Jacobi layout) per gate; one launch per set of
-// gates with disjoint endpoints.
+// gates with disjoint endpoints.  D is the number of bond slots per vertex tensor (3, or 4 for
+// degree-4 graphs, where J runs over CHI^3 values); slot k has stride CHI^(D-1-k).
 #pragma once
 
 #include "gtqa_anneal.cuh"
@@ -24,7 +25,7 @@ struct GenArgs {
     void* Gamma;
     double* lam;
     const int4* edge_info;
-    const int4* vert_edges;
+    const int4* vert_edges;   // slots of each vertex (x, y, z, and w when D = 4; -1 phantom)
     const int* gate_edge;     // edge of each gate of this launch
     const cd* gate_U;         // [gates][4][4], row 2 i_a + i_b, column 2 i_a' + i_b'
     int count;                // gates in this launch
@@ -33,39 +34,43 @@ struct GenArgs {
     double svd_cut;
 };
 
-template <int CHI>
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+template <int CHI, int D = 3>
 struct GenShape {
-    static constexpr int NR = CHI * CHI;     // rows of A_x
+    static constexpr int NR = ipow(CHI, D - 1);   // rows of A_x
     static constexpr int NC = 2 * CHI;       // columns of A_x: (i, j)
     static constexpr int NM = 4 * CHI;       // order of the core matrix
     static constexpr int G = NR / 2;         // lanes per Householder group (two rows each)
     static constexpr int TEAM = NM * NM / 2; // Jacobi layout: NM/2 pairs x NM rows
 };
 
-template <int CHI>
+template <int CHI, int D = 3>
 struct GenSm {
-    cd X[2][GenShape<CHI>::NC][GenShape<CHI>::NR];   // [side][column (i, j)][row J]; reflectors after the QR
-    cd vk[2][GenShape<CHI>::NC];
-    double tau[2][GenShape<CHI>::NC];
-    cd M[GenShape<CHI>::NM * GenShape<CHI>::NM];
-    cd V[GenShape<CHI>::NM * GenShape<CHI>::NM];
+    using S = GenShape<CHI, D>;
+    cd X[2][S::NC][S::NR];   // [side][column (i, j)][row J]; reflectors after the QR
+    cd vk[2][S::NC];
+    double tau[2][S::NC];
+    cd M[S::NM * S::NM];
+    cd V[S::NM * S::NM];
     cd U[16];
-    double w[2][GenShape<CHI>::NR];
+    double w[2][S::NR];
     double lab[CHI];
-    double sig[GenShape<CHI>::NM];
-    int perm[GenShape<CHI>::NM];
+    double sig[S::NM];
+    int perm[S::NM];
     int keep;
     int flag;
     int nrot;
 };
 
-template <int CHI, class Mode>
-__global__ void __launch_bounds__(GenShape<CHI>::TEAM, 1) general_gates_kernel(GenArgs c) {
+template <int CHI, int D, class Mode>
+__global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kernel(GenArgs c) {
     using TS = typename Mode::TS;
-    using S = GenShape<CHI>;
-    constexpr int NR = S::NR, NC = S::NC, NM = S::NM, G = S::G, TEAM = S::TEAM;
+    using S = GenShape<CHI, D>;
+    constexpr int NR = S::NR, NC = S::NC, NM = S::NM, G = S::G, TEAM = S::TEAM, HV = ipow(CHI, D);
+    static_assert(G <= 32, "a Householder group must fit in one warp");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GenSm<CHI>& sm = *reinterpret_cast<GenSm<CHI>*>(smem_raw);
+    GenSm<CHI, D>& sm = *reinterpret_cast<GenSm<CHI, D>*>(smem_raw);
     const int g = threadIdx.x;
     if (blockIdx.x >= (unsigned)c.count) return;   // uniform per block
     auto bar = [&]() {
@@ -77,17 +82,36 @@ __global__ void __launch_bounds__(GenShape<CHI>::TEAM, 1) general_gates_kernel(G
     const int4 ei = c.edge_info[e];
     const int vtx[2] = {ei.x, ei.y};
     const int slot[2] = {ei.z, ei.w};
-    int oe[2][2], os[2][2];
+    // the D - 1 other slots of each side in ascending order; J = sum_m o_m CHI^(D-2-m)
+    int oe[2][D - 1], ost[2][D - 1];
     for (int x = 0; x < 2; ++x) {
         const int4 ve = c.vert_edges[vtx[x]];
-        const int es[3] = {ve.x, ve.y, ve.z};
-        others_of(slot[x], os[x][0], os[x][1]);
-        oe[x][0] = es[os[x][0]];
-        oe[x][1] = es[os[x][1]];
+        const int es[4] = {ve.x, ve.y, ve.z, D == 4 ? ve.w : -1};
+        int m = 0;
+        for (int k = 0; k < D; ++k)
+            if (k != slot[x]) {
+                oe[x][m] = es[k];
+                ost[x][m] = ipow(CHI, D - 1 - k);
+                ++m;
+            }
     }
+    auto joff = [&](int x, int J) {   // offset of the other-slot index J inside a vertex tensor
+        size_t off = 0;
+        for (int m = D - 2; m >= 0; --m) {
+            off += (size_t)(J % CHI) * ost[x][m];
+            J /= CHI;
+        }
+        return off;
+    };
     for (int t = g; t < 2 * NR; t += TEAM) {
-        const int x = t / NR, J = t % NR;
-        sm.w[x][J] = lam_get(c.lam, CHI, oe[x][0], J / CHI) * lam_get(c.lam, CHI, oe[x][1], J % CHI);
+        const int x = t / NR;
+        int J = t % NR;
+        double w = 1.0;
+        for (int m = D - 2; m >= 0; --m) {
+            w *= lam_get(c.lam, CHI, oe[x][m], J % CHI);
+            J /= CHI;
+        }
+        sm.w[x][t % NR] = w;
     }
     for (int t = g; t < CHI; t += TEAM) sm.lab[t] = __ldcg(c.lam + (size_t)e * CHI + t);
     for (int t = g; t < 16; t += TEAM) sm.U[t] = c.gate_U[(size_t)blockIdx.x * 16 + t];
@@ -96,9 +120,8 @@ __global__ void __launch_bounds__(GenShape<CHI>::TEAM, 1) general_gates_kernel(G
         const int x = t / (NC * NR), rem = t % (NC * NR);
         const int col = rem / NR, row = rem % NR;
         const int i = col / CHI, j = col % CHI;
-        const size_t off = (size_t)vtx[x] * (2 * CHI * CHI * CHI) + (size_t)i * CHI * CHI * CHI +
-                           j * sstride<CHI>(slot[x]) + (row / CHI) * sstride<CHI>(os[x][0]) +
-                           (row % CHI) * sstride<CHI>(os[x][1]);
+        const size_t off = (size_t)vtx[x] * (2 * HV) + (size_t)i * HV + (size_t)j * ipow(CHI, D - 1 - slot[x]) +
+                           joff(x, row);
         sm.X[x][col][row] = sm.w[x][row] * ccast<double>(ldcg(Gam + off));
     }
     bar();
@@ -264,23 +287,23 @@ __global__ void __launch_bounds__(GenShape<CHI>::TEAM, 1) general_gates_kernel(G
         }
         const double w0 = sm.w[x][r0], w1 = sm.w[x][r1];
         const double iw0 = w0 > 0.0 ? nr_rcp(w0) : 0.0, iw1 = w1 > 0.0 ? nr_rcp(w1) : 0.0;
-        const size_t base = (size_t)vtx[x] * (2 * CHI * CHI * CHI) + (size_t)i * CHI * CHI * CHI;
-        const size_t o0 = (r0 / CHI) * sstride<CHI>(os[x][0]) + (r0 % CHI) * sstride<CHI>(os[x][1]);
-        const size_t o1 = (r1 / CHI) * sstride<CHI>(os[x][0]) + (r1 % CHI) * sstride<CHI>(os[x][1]);
+        const size_t base = (size_t)vtx[x] * (2 * HV) + (size_t)i * HV;
+        const size_t o0 = joff(x, r0), o1 = joff(x, r1);
+        const size_t ss = ipow(CHI, D - 1 - slot[x]);
 #pragma unroll
         for (int cc = 0; cc < CHI; ++cc) {
-            Gam[base + cc * sstride<CHI>(slot[x]) + o0] = ccast<TS>(iw0 * E0[cc]);
-            Gam[base + cc * sstride<CHI>(slot[x]) + o1] = ccast<TS>(iw1 * E1[cc]);
+            Gam[base + cc * ss + o0] = ccast<TS>(iw0 * E0[cc]);
+            Gam[base + cc * ss + o1] = ccast<TS>(iw1 * E1[cc]);
         }
     }
 }
 
 // One-qubit gates: Gamma~_a[i] = sum_i' W[i][i'] Gamma_a[i'] (Sec. II D); one block per gate,
 // all gates of a launch on distinct vertices.
-template <int CHI, class Mode>
+template <int CHI, int D, class Mode>
 __global__ void single_gates_kernel(void* Gamma, const int* vertex, const cd* W, int count) {
     using TS = typename Mode::TS;
-    constexpr int H = CHI * CHI * CHI;
+    constexpr int H = ipow(CHI, D);
     const int q = blockIdx.x;
     if (q >= count) return;
     C<TS>* gm = (C<TS>*)Gamma + (size_t)vertex[q] * 2 * H;
@@ -292,24 +315,24 @@ __global__ void single_gates_kernel(void* Gamma, const int* vertex, const cd* W,
     }
 }
 
-template <int CHI, class Mode>
+template <int CHI, int D, class Mode>
 cudaError_t general_gates_launch_t(const GenArgs& a, cudaStream_t st) {
-    constexpr size_t smem = sizeof(GenSm<CHI>);
+    constexpr size_t smem = sizeof(GenSm<CHI, D>);
     static bool attr_set = false;   // the attribute is per function; setting it twice is harmless
     if (!attr_set) {
-        const cudaError_t e = raise_smem_limit(general_gates_kernel<CHI, Mode>, smem);
+        const cudaError_t e = raise_smem_limit(general_gates_kernel<CHI, D, Mode>, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     if (a.count <= 0) return cudaSuccess;
-    general_gates_kernel<CHI, Mode><<<a.count, GenShape<CHI>::TEAM, smem, st>>>(a);
+    general_gates_kernel<CHI, D, Mode><<<a.count, GenShape<CHI, D>::TEAM, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int CHI, class Mode>
+template <int CHI, int D, class Mode>
 cudaError_t single_gates_launch_t(void* Gamma, const int* vertex, const cd* W, int count, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
-    single_gates_kernel<CHI, Mode><<<count, 64, 0, st>>>(Gamma, vertex, W, count);
+    single_gates_kernel<CHI, D, Mode><<<count, 64, 0, st>>>(Gamma, vertex, W, count);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 
 #include "gtqa_anneal.cuh"
 #include "gtqa_general.cuh"
+#include "gtqa_deg4.cuh"
 
 namespace gtqa {
 
@@ -46,6 +47,15 @@ cudaError_t general_gates_launch_mixed(int CHI, const GenArgs& a, cudaStream_t s
 cudaError_t single_gates_launch_fp64(int CHI, void* Gamma, const int* vertex, const cd* W, int count, cudaStream_t st);
 cudaError_t single_gates_launch_mixed(int CHI, void* Gamma, const int* vertex, const cd* W, int count,
                                       cudaStream_t st);
+
+// degree-4 graphs (FP64 mode, CHI in {2, 4})
+cudaError_t d4_bp_init_launch(int CHI, const D4Args& a, cudaStream_t st);
+cudaError_t d4_bp_sweep_launch(int CHI, const D4Args& a, cudaStream_t st);
+cudaError_t d4_regauge_launch(int CHI, const Ctx& c, int cur, const D4Args& a, cudaStream_t st);
+cudaError_t d4_marginals_launch(int CHI, const cd* Gamma, const double* lam, const int4* vslots, int n, cd* rho,
+                                int8_t* sign, int* flag, cudaStream_t st);
+cudaError_t d4_general_gates_launch(int CHI, const GenArgs& a, cudaStream_t st);
+cudaError_t d4_single_gates_launch(int CHI, void* Gamma, const int* vertex, const cd* W, int count, cudaStream_t st);
 
 inline bool phase_shape(bool mixed, int pk, int CHI, size_t* sb, int* tpb) {
     switch (pk) {

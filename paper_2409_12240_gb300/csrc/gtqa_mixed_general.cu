@@ -5,9 +5,9 @@ namespace gtqa {
 
 cudaError_t general_gates_launch_mixed(int CHI, const GenArgs& a, cudaStream_t st) {
     switch (CHI) {
-        case 2: return general_gates_launch_t<2, ModeMixed>(a, st);
-        case 4: return general_gates_launch_t<4, ModeMixed>(a, st);
-        case 8: return general_gates_launch_t<8, ModeMixed>(a, st);
+        case 2: return general_gates_launch_t<2, 3, ModeMixed>(a, st);
+        case 4: return general_gates_launch_t<4, 3, ModeMixed>(a, st);
+        case 8: return general_gates_launch_t<8, 3, ModeMixed>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -15,9 +15,9 @@ cudaError_t general_gates_launch_mixed(int CHI, const GenArgs& a, cudaStream_t s
 cudaError_t single_gates_launch_mixed(int CHI, void* Gamma, const int* vertex, const cd* W, int count,
                                       cudaStream_t st) {
     switch (CHI) {
-        case 2: return single_gates_launch_t<2, ModeMixed>(Gamma, vertex, W, count, st);
-        case 4: return single_gates_launch_t<4, ModeMixed>(Gamma, vertex, W, count, st);
-        case 8: return single_gates_launch_t<8, ModeMixed>(Gamma, vertex, W, count, st);
+        case 2: return single_gates_launch_t<2, 3, ModeMixed>(Gamma, vertex, W, count, st);
+        case 4: return single_gates_launch_t<4, 3, ModeMixed>(Gamma, vertex, W, count, st);
+        case 8: return single_gates_launch_t<8, 3, ModeMixed>(Gamma, vertex, W, count, st);
         default: return cudaErrorInvalidValue;
     }
 }

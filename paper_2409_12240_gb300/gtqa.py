@@ -41,6 +41,7 @@ EXPORTED = [
     "gtqa_profile_name", "gtqa_alu_peak", "gtqa_debug_barrier", "gtqa_math_check", "gtqa_bp_static",
     "gtqa_barrier_bench", "gtqa_residual", "gtqa_entropy", "gtqa_spectral_bipartition", "gtqa_sample",
     "gtqa_trotter_split", "gtqa_anneal_ex", "gtqa_apply_gates", "gtqa_apply_single_qubit_gates",
+    "gtqa_max_degree",
 ]
 KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
@@ -96,6 +97,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_anneal_ex": (I32, [P, I32, I32, I32, D, D, I32, I32, P]),
         "gtqa_apply_gates": (I32, [P, I32, P, P]),
         "gtqa_apply_single_qubit_gates": (I32, [P, I32, P, P]),
+        "gtqa_max_degree": (I32, [P, ctypes.POINTER(I32)]),
         "gtqa_marginals": (I32, [P, P, P]),
         "gtqa_residual": (I32, [P, ctypes.POINTER(D)]),
         "gtqa_entropy": (I32, [P, P, ctypes.POINTER(D)]),
@@ -318,10 +320,17 @@ def gtqa_stats(s: int) -> dict:
     return {k: getattr(st, k) for k, _ in gtqa_stats_t._fields_}
 
 
+def gtqa_max_degree(s: int) -> int:
+    D = ctypes.c_int32()
+    _check(load().gtqa_max_degree(s, ctypes.byref(D)), "gtqa_max_degree")
+    return int(D.value)
+
+
 def gtqa_get_state(s: int):
-    """(Gamma (n,2,CHI,CHI,CHI) complex128, lambda (m,CHI), messages (2m,CHI,CHI) complex128)."""
+    """(Gamma (n,2,CHI,...,CHI) complex128 with one CHI per bond slot, lambda (m,CHI),
+    messages (2m,CHI,CHI) complex128)."""
     n, m, C, _ = gtqa_sizes(s)
-    G = np.zeros((n, 2, C, C, C), dtype=np.complex128)
+    G = np.zeros((n, 2) + (C,) * gtqa_max_degree(s), dtype=np.complex128)
     L = np.zeros((m, C), dtype=np.float64)
     Mg = np.zeros((2 * m, C, C), dtype=np.complex128)
     _check(load().gtqa_get_state(s, _ptr(G)[0], _ptr(L)[0], _ptr(Mg)[0]), "gtqa_get_state")

@@ -64,9 +64,13 @@ def test_invalid_graphs_rejected_on_host(G):
     assert _rc(G, 4, [[0, 0]], [1.0], h, 4)[0] == G.GTQA_ERR_INVALID_ARG
     # duplicate edge
     assert _rc(G, 4, [[0, 1], [1, 0]], [1.0, 1.0], h, 4)[0] == G.GTQA_ERR_INVALID_ARG
-    # degree 4
-    star = [[0, 1], [0, 2], [0, 3], [0, 4]]
-    assert _rc(G, 5, star, np.ones(4), np.zeros(5), 4)[0] == G.GTQA_ERR_INVALID_ARG
+    # degree 5
+    star = [[0, 1], [0, 2], [0, 3], [0, 4], [0, 5]]
+    assert _rc(G, 6, star, np.ones(5), np.zeros(6), 4)[0] == G.GTQA_ERR_INVALID_ARG
+    # degree 4 needs FP64 and chi <= 4 (checked before any device work)
+    star4 = star[:4]
+    assert _rc(G, 5, star4, np.ones(4), np.zeros(5), 4, precision=G.GTQA_MIXED)[0] == G.GTQA_ERR_UNSUPPORTED
+    assert _rc(G, 5, star4, np.ones(4), np.zeros(5), 8)[0] == G.GTQA_ERR_UNSUPPORTED
     # out of range vertex
     assert _rc(G, 4, [[0, 7]], [1.0], h, 4)[0] == G.GTQA_ERR_INVALID_ARG
     # colouring that is not a matching

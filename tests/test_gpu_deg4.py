@@ -1,0 +1,144 @@
+"""GPU parity on graphs with degree-4 vertices (the random 4-regular graphs of Sec. V): the
+plain degree-4 kernels (FP64) against the oracle, layer by layer (bar 1e-10 on marginals
+and lambda), for annealing layers, product formulas and arbitrary gates."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import gpu_util as U
+from instances import make_instance, make_tree_instance, random_gate_inputs
+from oracle import gtqa_oracle as O
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def _create(G, inst, chi):
+    return G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour, G.gtqa_options_init(precision=G.GTQA_FP64))
+
+
+def _compare(G, s, st):
+    rho_g, sign_g = G.gtqa_marginals(s)
+    rho_o = O.reduced_density_matrices(st)
+    _, Lg, _ = G.gtqa_get_state(s)
+    _, Lo = O.to_padded(st, Lg.shape[1], degree=4)
+    return float(np.abs(rho_g - rho_o).max()), float(np.abs(Lg - Lo).max())
+
+
+@pytest.mark.parametrize("chi", [2, 4])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_four_regular_layers_match_oracle(chi, seed):
+    """n = 10, 4-regular, J ~ N(0,1), h ~ N(0, 0.1), K = 20, dt = 0.1: six layers of gates, BP
+    from the warm start (tol 1e-12) and the regauge."""
+    G = U.lib()
+    inst = make_instance(10, seed, d=4)
+    K, dt, tol, mi = 20, 0.1, 1e-12, 300
+    s = _create(G, inst, chi)
+    st = O.plus_state(inst.n, inst.edges)
+    try:
+        assert G.gtqa_max_degree(s) == 4
+        for k in range(1, 7):
+            G.gtqa_trotter_layer(s, k / K, dt)
+            it_g, _, conv = G.gtqa_bp_sweep(s, tol, mi)
+            tZ, tX = O.schedule(k, K, dt)
+            st, info = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, chi, tol, mi)
+            assert abs(it_g - info["bp_iters"]) <= 1, (it_g, info["bp_iters"])
+            e_rho, e_lam = _compare(G, s, st)
+            assert e_rho < TOL and e_lam < TOL, (k, e_rho, e_lam)
+    finally:
+        G.gtqa_destroy(s)
+
+
+@pytest.mark.parametrize("kind", ["tree", "spider"])
+def test_degree_four_trees_match_oracle(kind):
+    """Trees with degree-4 vertices (mixed degrees 1..4, phantom slots) against the oracle.
+    The spider (a degree-4 centre, one leg of length 2) has Schmidt rank <= 4 across every
+    edge, so at chi = 4 nothing is truncated and both equal the exact marginals (BP is exact on
+    trees)."""
+    from instances import Instance
+    from oracle import statevector as SV
+    G = U.lib()
+    if kind == "tree":
+        inst = make_tree_instance(10, 2, max_degree=4)
+    else:
+        rng = np.random.default_rng(7)
+        edges = np.array([[0, 1], [0, 2], [0, 3], [0, 4], [4, 5]], dtype=np.int32)
+        inst = Instance(6, edges, rng.normal(size=5), rng.normal(0, 0.1, size=6),
+                        np.array([0, 1, 2, 3, 0], dtype=np.int32), 7, kind="spider")
+    K, dt, chi = 6, 0.3, 4
+    _, rhos = SV.evolve(inst.n, inst.edges, inst.J, inst.h, K, dt)
+    s = _create(G, inst, chi)
+    st = O.plus_state(inst.n, inst.edges)
+    try:
+        for k in range(1, K + 1):
+            G.gtqa_trotter_layer(s, k / K, dt)
+            G.gtqa_bp_sweep(s, 1e-13, 100)
+            tZ, tX = O.schedule(k, K, dt)
+            st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, chi, 1e-13, 100)
+            e_rho, e_lam = _compare(G, s, st)
+            assert e_rho < TOL and e_lam < TOL, (k, e_rho, e_lam)
+        if kind == "spider":
+            rho_g, _ = G.gtqa_marginals(s)
+            assert np.abs(rho_g - rhos[K - 1]).max() < 1e-9
+    finally:
+        G.gtqa_destroy(s)
+
+
+def test_four_regular_anneal_symmetric_formula_and_gates():
+    """gtqa_anneal_ex (symmetric formula) and then arbitrary gates with BP and the regauge on a
+    4-regular graph, against the oracle."""
+    G = U.lib()
+    inst = make_instance(12, 3, d=4)
+    K, dt, chi, tol, mi = 20, 0.1, 4, 1e-12, 300
+    s = _create(G, inst, chi)
+    st = O.plus_state(inst.n, inst.edges)
+    try:
+        G.gtqa_anneal_ex(s, 1, 4, K, dt, tol, mi, G.GTQA_TROTTER_SYMMETRIC)
+        for k in range(1, 5):
+            t_pre, tZ, tX = O.product_formula(k, K, dt, 2)
+            st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, chi, tol, mi, t_X_pre=t_pre)
+        e_rho, e_lam = _compare(G, s, st)
+        assert e_rho < TOL and e_lam < TOL, (e_rho, e_lam)
+        e, Uq, v, W = random_gate_inputs(inst.n, inst.m, inst.m, inst.n, seed=21)
+        G.gtqa_apply_gates(s, e, Uq)
+        G.gtqa_apply_single_qubit_gates(s, v, W)
+        G.gtqa_bp_sweep(s, tol, mi)
+        O.apply_gates(st, list(zip(e.tolist(), Uq)), chi)
+        O.apply_single_qubit_gates(st, list(zip(v.tolist(), W)))
+        st, _ = O.regauge(st, tol, mi)
+        e_rho, e_lam = _compare(G, s, st)
+        assert e_rho < TOL and e_lam < TOL, (e_rho, e_lam)
+        stats = G.gtqa_stats(s)
+        assert stats["bp_calls"] == 5 and stats["layers"] == 4
+    finally:
+        G.gtqa_destroy(s)
+
+
+def test_four_regular_unsupported_calls_and_state_round_trip():
+    G = U.lib()
+    inst = make_instance(10, 4, d=4)
+    s = _create(G, inst, 4)
+    try:
+        G.gtqa_anneal(s, 1, 2, 10, 0.2, 1e-10, 100)
+        lib = G.load()
+        x = np.zeros(inst.n, dtype=np.int8)
+        order = np.arange(inst.n, dtype=np.int32)
+        u = np.full(inst.n, 0.5)
+        assert lib.gtqa_sample(s, inst.n, order.ctypes.data, u.ctypes.data, 1e-8, 10, x.ctypes.data, None) == \
+            G.GTQA_ERR_UNSUPPORTED
+        import ctypes
+        R = ctypes.c_double()
+        assert lib.gtqa_residual(s, ctypes.byref(R)) == G.GTQA_ERR_UNSUPPORTED
+        Gm, L, M = G.gtqa_get_state(s)
+        assert Gm.shape == (inst.n, 2, 4, 4, 4, 4)
+        rho0, _ = G.gtqa_marginals(s)
+        G.gtqa_set_state(s, Gm, L, M)
+        rho1, _ = G.gtqa_marginals(s)
+        assert np.array_equal(rho0, rho1)
+        # the entropy of a cut needs lambda only and works on degree-4 states
+        cut = np.zeros(inst.m, dtype=np.uint8)
+        cut[0] = 1
+        assert G.gtqa_entropy(s, cut) >= 0.0
+    finally:
+        G.gtqa_destroy(s)
