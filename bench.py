@@ -307,6 +307,17 @@ def per_layer_error(G, make, inst, k_last: int, samples: int = 6) -> dict:
 # ---------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------
+def replica_throughput(t_ms: float, K: int, world: int, dist=None, device: str = "cpu"):
+    """Whole-job throughput of `world` independent replicas that each ran K layers: the slowest
+    rank's time (max over ranks), and value = world * K layers / that time."""
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([t_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    return t_ms, world * K / (t_ms / 1e3)
+
+
 def run_gtqa(a):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -376,11 +387,7 @@ def run_gtqa(a):
 
     clocks = Clocks(local)
     t_ms, dlt, rho_main, sign_main, ck, prof = timed_window(prec, clocks, profile=True)
-    if dist:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * K / (t_ms / 1e3)
+    t_ms, value = replica_throughput(t_ms, K, world, dist, "cuda")
 
     # the FP64 path on the same layers, and the marginal error of the mixed path against it
     fp64 = None
