@@ -169,6 +169,37 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
                 int32_t max_iter);
 
 /*
+ * Autotuner of the launch shapes.  Each of the three phase kernels (gates, BP, regauge) is a
+ * persistent cooperative launch of `grid` blocks, one per SM at most.  For each kernel in turn,
+ * gtqa_autotune times one launch of the layer (tau, dt) with BP to (tol, max_iter) from the
+ * state's current contents.  It tries each candidate grid: all SMs, 7/8 ... 1/2 of them, and
+ * the fewest blocks that cover the kernel's work in one round of teams.  The earlier phases of
+ * the layer run untimed first, so that each kernel sees its real inputs.  The median of three
+ * runs decides, and the fastest grid is kept for the state.  The state's contents and
+ * statistics are restored afterwards.  grid_out (nullable, 3 ints) receives the chosen grid
+ * sizes.  Results do not depend on the grid, except for the rounding order of the BP distance
+ * sum.  Synchronises.  Returns GTQA_ERR_UNSUPPORTED for a degree-4 state.
+ */
+int gtqa_autotune(gtqa_state* s, double tau, double dt, double tol, int32_t max_iter, int32_t* grid_out);
+
+/* Set the grid sizes (blocks of the gates, BP and regauge kernels, each 1..number of SMs), for
+ * example to apply gtqa_autotune's choice from another state of the same shape. */
+int gtqa_set_grid(gtqa_state* s, const int32_t* grid);
+
+/*
+ * gtqa_anneal replayed from a CUDA graph: the three launches of every layer k_begin..k_end are
+ * captured once (on a private stream, with profiling events off) into a graph that the state
+ * keeps, and the graph is launched on the state's stream.  A later call with the same
+ * arguments relaunches the kept graph without capturing again; different arguments replace
+ * it.  The results are those of gtqa_anneal with the same arguments, bit for bit.  Graphs
+ * save the host-side launch cost; the device work is unchanged.  Asynchronous.  Returns
+ * GTQA_ERR_UNSUPPORTED if the launches could not be captured (nothing is launched and the
+ * state stays usable) or for a degree-4 state, and GTQA_ERR_INVALID_ARG as gtqa_anneal.
+ */
+int gtqa_anneal_graph(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double dt, double tol,
+                      int32_t max_iter);
+
+/*
  * One Trotter layer in split form U_X(t_X_post) U_Z(t_Z) U_X(t_X_pre): the mixing gate
  * exp(-i t_X_pre X) on every vertex, then every edge gate of U_Z(t_Z) by the simple update
  * with truncation (App. E, App. D "Truncation"), then exp(-i t_X_post X) on every vertex

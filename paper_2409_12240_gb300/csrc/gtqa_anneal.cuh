@@ -45,7 +45,8 @@ struct ModeMixed {
 enum : unsigned { PH_GATES = 1u, PH_BP = 2u, PH_WARM = 4u, PH_REGAUGE = 8u };
 
 struct Control {
-    unsigned long long bar_count;   // grid-barrier arrivals (monotonic)
+    unsigned long long bar_count;   // grid-barrier arrivals (monotonic), a multiple of the grid between launches
+    unsigned long long bar_pk[3];   // the same, one counter per phase kernel (each kernel keeps its grid size)
     int err;
     int cur;                 // message buffer holding the latest messages
     long long sweeps_total;  // sum over BP calls of max-over-instances sweeps
@@ -87,6 +88,7 @@ struct Ctx {
     double* inst_dist;
     double* stats;            // discarded weight, log fidelity, SVD pairs, SVD rotations
     Control* ctl;
+    unsigned long long* bar;  // barrier counter of this launch (null: ctl->bar_count)
     // parameters
     int chi;
     double svd_cut, eig_cut;
@@ -1144,7 +1146,7 @@ template <int CHI, class Mode, unsigned PH>
 __device__ __forceinline__ void anneal_body(const Ctx& c) {
     using S = Shape<CHI>;
     extern __shared__ __align__(16) unsigned char smem[];
-    GridBarrier gb = grid_barrier_init(&c.ctl->bar_count, &c.ctl->err, (unsigned)c.bar_expect);
+    GridBarrier gb = grid_barrier_init(c.bar ? c.bar : &c.ctl->bar_count, &c.ctl->err, (unsigned)c.bar_expect);
     const int nteams_total_g = c.nblocks * (S::TPB / S::TG);
     int cur = *(volatile int*)&c.ctl->cur;
     for (int k = c.k0; k <= c.k1; ++k) {

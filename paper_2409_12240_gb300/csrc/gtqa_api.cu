@@ -71,11 +71,17 @@ struct gtqa_state {
     std::vector<int> h_deg, h_cedges, h_coff;
     std::vector<double> h_J, h_h;
     int cur4 = 0;               // message buffer holding the latest messages (degree 4)
+    // gtqa_anneal_graph: the captured launches of one layer range, and what they were captured for
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int gk0 = 0, gk1 = 0, gK = 0, gmi = 0;
+    double gdt = 0.0, gtol = 0.0;
     // host counters
     long long layers = 0, gates = 0, launches = 0;
     int sticky = GTQA_OK;
     long long spin_limit = 1LL << 22;   // polls per grid barrier before GTQA_ERR_TIMEOUT (about a second)
     int bar_extra = 0;                  // test hook: extra arrivals the barrier waits for
+    int grid[PK_COUNT] = {0, 0, 0};     // persistent blocks per phase kernel (gtqa_autotune)
     // optional profiler (per launch class)
     bool prof_on = false;
     struct Pending { int kind; cudaEvent_t a, b; long long units; };
@@ -413,6 +419,8 @@ bool misra_gries(int n, int m, const int* edges, std::vector<int>& colour, int& 
 
 void free_state(gtqa_state* s) {
     if (!s) return;
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->graph) cudaGraphDestroy(s->graph);
     void* ptrs[] = {s->Gamma, s->lam, s->T, s->msg[0], s->msg[1], s->D0, s->t0, s->X, s->edge_info,
                     s->vert_edges, s->vert_inst, s->J, s->h, s->colour_edges, s->colour_off, s->last_colour, s->first_colour,
                     s->iso, s->inst_vbeg, s->inst_m, s->acc, s->inst_done, s->inst_iters, s->inst_dist,
@@ -472,8 +480,15 @@ Ctx make_ctx(const gtqa_state* s) {
 }
 
 // One cooperative launch of a phase kernel.
-int run(gtqa_state* s, const Ctx& c, int pk, int kind, long long units) {
+int run(gtqa_state* s, const Ctx& c0, int pk, int kind, long long units) {
     cudaError_t e;
+    Ctx c = c0;
+    c.nblocks = s->grid[pk];
+    c.bar_expect = s->grid[pk] + s->bar_extra;
+    // each phase kernel counts its barrier arrivals separately, so that the counter stays a
+    // multiple of that kernel's grid size between its launches (gtqa_set_grid and the
+    // autotuner zero it when the size changes)
+    c.bar = &s->ctl->bar_pk[pk];
     {
         ProfScope ps(s, kind, units);
         e = phase_launch(mixed(s), pk, s->CHI, c, s->smem[pk], s->stream);
@@ -623,6 +638,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         }
     }
     s->nblocks = sms;
+    for (int pk = 0; pk < PK_COUNT; ++pk) s->grid[pk] = sms;
     // slots: incident edges in ascending id; colour of each vertex's last gate
     std::vector<int4> vedges(N, make_int4(-1, -1, -1, 0)), v4(N, make_int4(-1, -1, -1, -1));
     std::vector<int4> einfo(Mtot);
@@ -993,6 +1009,42 @@ int d4_bp(gtqa_state* s, double tol, int max_iter, uint32_t flags, int32_t* iter
     return conv ? GTQA_OK : GTQA_ERR_NOT_CONVERGED;
 }
 
+// The three phase launches of layers k_begin..k_end (gtqa_anneal's body).
+int anneal_launches(gtqa_state* s, int k_begin, int k_end, int K, double dt, double tol, int max_iter) {
+    int rc;
+    Ctx c = make_ctx(s);
+    c.phases = PH_GATES | PH_BP | PH_WARM | PH_REGAUGE;
+    c.Ksched = K;
+    c.dt = dt;
+    c.tol = tol;
+    c.max_iter = max_iter;
+    for (int k = k_begin; k <= k_end; ++k) {
+        c.k0 = c.k1 = k;
+        if ((rc = run(s, c, PK_GATES, GTQA_K_TROTTER, s->m)) || (rc = run(s, c, PK_BP, GTQA_K_BP, s->n)) ||
+            (rc = run(s, c, PK_REGAUGE, GTQA_K_REGAUGE, s->m)))
+            return rc;
+        s->layers += 1;
+        s->gates += s->m;
+    }
+    return GTQA_OK;
+}
+
+// Work teams per block of each phase kernel (the regauge counts its edge teams).
+template <int CHI>
+int teams_per_block_t(int pk) {
+    using S = Shape<CHI>;
+    return pk == PK_GATES ? S::TPB / S::TG : (pk == PK_BP ? S::TPB / S::TB : S::TPB / S::TR);
+}
+int teams_per_block(int pk, int CHI) {
+    return CHI == 2 ? teams_per_block_t<2>(pk) : (CHI == 4 ? teams_per_block_t<4>(pk) : teams_per_block_t<8>(pk));
+}
+
+// Zero the per-kernel barrier counters (stream-ordered, between launches).
+int zero_barriers(gtqa_state* s) {
+    Control* c = s->ctl;
+    return cuda_ok(s, cudaMemsetAsync(&c->bar_pk[0], 0, sizeof(c->bar_pk), s->stream)) ? GTQA_OK : GTQA_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1030,6 +1082,119 @@ int gtqa_trotter_layer(gtqa_state* s, double tau, double dt) {
     if ((rc = run(s, c, PK_GATES, GTQA_K_TROTTER, s->m))) return rc;
     s->layers += 1;
     s->gates += s->m;
+    return GTQA_OK;
+}
+
+int gtqa_set_grid(gtqa_state* s, const int32_t* grid) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (!grid) return GTQA_ERR_INVALID_ARG;
+    for (int pk = 0; pk < PK_COUNT; ++pk)
+        if (grid[pk] < 1 || grid[pk] > s->nblocks) return GTQA_ERR_INVALID_ARG;
+    for (int pk = 0; pk < PK_COUNT; ++pk) s->grid[pk] = grid[pk];
+    return zero_barriers(s);
+}
+
+int gtqa_autotune(gtqa_state* s, double tau, double dt, double tol, int32_t max_iter, int32_t* grid_out) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (!std::isfinite(tau) || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1) return GTQA_ERR_INVALID_ARG;
+    if (s->D == 4) return GTQA_ERR_UNSUPPORTED;
+    // snapshot of everything a layer writes, restored before every timed launch and at the end
+    struct Buf { void* p; size_t bytes; std::vector<unsigned char> h; };
+    const size_t gel = gamma_elems(s), mel = msg_elems(s), eb = elem_bytes(s);
+    std::vector<Buf> bufs = {{s->Gamma, gel * eb, {}}, {s->T, gel * eb, {}}, {s->lam, sizeof(double) * s->m * s->CHI, {}},
+                             {s->msg[0], mel * eb, {}}, {s->msg[1], mel * eb, {}},
+                             {s->X, sizeof(cd) * s->m * 2 * s->CHI * s->CHI, {}},
+                             {s->D0, mixed(s) ? sizeof(cf) * mel : 0, {}}, {s->t0, mixed(s) ? sizeof(cd) * 2 * s->m : 0, {}},
+                             {s->stats, sizeof(double) * 4, {}}, {s->ctl, sizeof(Control), {}},
+                             {s->acc, sizeof(double) * 6 * s->B, {}}, {s->inst_done, sizeof(int) * s->B, {}},
+                             {s->inst_iters, sizeof(int) * s->B, {}}, {s->inst_dist, sizeof(double) * s->B, {}}};
+    for (auto& b : bufs) {
+        b.h.resize(b.bytes);
+        if (b.bytes && !cuda_ok(s, cudaMemcpyAsync(b.h.data(), b.p, b.bytes, cudaMemcpyDeviceToHost, s->stream)))
+            return GTQA_ERR_CUDA;
+    }
+    if (!cuda_ok(s, cudaStreamSynchronize(s->stream))) return GTQA_ERR_CUDA;
+    // the restored control block holds barrier counts of the snapshot's grid sizes: zero them
+    auto restore = [&]() {
+        for (auto& b : bufs)
+            if (b.bytes && !cuda_ok(s, cudaMemcpyAsync(b.p, b.h.data(), b.bytes, cudaMemcpyHostToDevice, s->stream)))
+                return false;
+        return zero_barriers(s) == GTQA_OK;
+    };
+    const long long layers = s->layers, gates = s->gates, launches = s->launches;
+    const bool prof = s->prof_on;
+    s->prof_on = false;
+    Ctx c = make_ctx(s);
+    c.k0 = c.k1 = 0;
+    c.Ksched = 0;
+    c.tZ1 = dt * tau;
+    c.tX1 = dt * (1.0 - tau);
+    c.tol = tol;
+    c.max_iter = max_iter;
+    // work units per phase kernel and teams per block: candidates are all SMs, fewer blocks in
+    // steps of 1/8, and the fewest blocks that still cover the work in one round
+    const int full = s->nblocks;
+    const long long units[PK_COUNT] = {s->m, s->n, s->m};
+    const int tpb_teams[PK_COUNT] = {teams_per_block(PK_GATES, s->CHI), teams_per_block(PK_BP, s->CHI),
+                                     teams_per_block(PK_REGAUGE, s->CHI)};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!cuda_ok(s, cudaEventCreate(&e0)) || !cuda_ok(s, cudaEventCreate(&e1))) return GTQA_ERR_CUDA;
+    int best[PK_COUNT];
+    rc = GTQA_OK;
+    for (int pk = 0; pk < PK_COUNT && rc == GTQA_OK; ++pk) {
+        std::vector<int> cand;
+        for (int q = 8; q >= 4; --q) cand.push_back(std::max(1, full * q / 8));
+        const long long one_round = (units[pk] + tpb_teams[pk] - 1) / std::max(1, tpb_teams[pk]);
+        if (one_round >= 1 && one_round < full) cand.push_back((int)one_round);
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        double tbest = 1e300;
+        best[pk] = s->grid[pk];
+        const int keep = s->grid[pk];
+        for (int g : cand) {
+            s->grid[pk] = g;
+            std::vector<float> ts;
+            for (int rep = 0; rep < 3 && rc == GTQA_OK; ++rep) {
+                if (!restore()) { rc = GTQA_ERR_CUDA; break; }
+                // the phases before the timed one, untimed, so that it sees its real inputs
+                Ctx ci = c;
+                ci.phases = PH_GATES;
+                if (pk >= PK_BP && (rc = run(s, ci, PK_GATES, GTQA_K_TROTTER, s->m))) break;
+                ci.phases = PH_BP | PH_WARM;
+                if (pk >= PK_REGAUGE && (rc = run(s, ci, PK_BP, GTQA_K_BP, s->n))) break;
+                ci.phases = pk == PK_GATES ? PH_GATES : (pk == PK_BP ? (PH_BP | PH_WARM) : PH_REGAUGE);
+                cudaEventRecord(e0, s->stream);
+                if ((rc = run(s, ci, pk, pk, units[pk]))) break;
+                cudaEventRecord(e1, s->stream);
+                float ms = 0.f;
+                if (!cuda_ok(s, cudaEventSynchronize(e1)) || !cuda_ok(s, cudaEventElapsedTime(&ms, e0, e1))) {
+                    rc = GTQA_ERR_CUDA;
+                    break;
+                }
+                ts.push_back(ms);
+            }
+            if (rc != GTQA_OK) break;
+            std::sort(ts.begin(), ts.end());
+            if (ts[ts.size() / 2] < tbest) {
+                tbest = ts[ts.size() / 2];
+                best[pk] = g;
+            }
+        }
+        s->grid[pk] = rc == GTQA_OK ? best[pk] : keep;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const bool ok = restore() && cuda_ok(s, cudaStreamSynchronize(s->stream));
+    s->layers = layers;
+    s->gates = gates;
+    s->launches = launches;
+    s->prof_on = prof;
+    if (rc != GTQA_OK) return rc;
+    if (!ok) return GTQA_ERR_CUDA;
+    if (grid_out)
+        for (int pk = 0; pk < PK_COUNT; ++pk) grid_out[pk] = s->grid[pk];
     return GTQA_OK;
 }
 
@@ -1256,20 +1421,65 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
         }
         return GTQA_OK;
     }
-    Ctx c = make_ctx(s);
-    c.phases = PH_GATES | PH_BP | PH_WARM | PH_REGAUGE;
-    c.Ksched = K;
-    c.dt = dt;
-    c.tol = tol;
-    c.max_iter = max_iter;
-    for (int k = k_begin; k <= k_end; ++k) {
-        c.k0 = c.k1 = k;
-        if ((rc = run(s, c, PK_GATES, GTQA_K_TROTTER, s->m)) || (rc = run(s, c, PK_BP, GTQA_K_BP, s->n)) ||
-            (rc = run(s, c, PK_REGAUGE, GTQA_K_REGAUGE, s->m)))
-            return rc;
-        s->layers += 1;
-        s->gates += s->m;
+    return anneal_launches(s, k_begin, k_end, K, dt, tol, max_iter);
+}
+
+int gtqa_anneal_graph(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double dt, double tol,
+                      int32_t max_iter) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (K < 1 || k_begin < 1 || k_end < k_begin || k_end > K || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1)
+        return GTQA_ERR_INVALID_ARG;
+    if (s->D == 4) return GTQA_ERR_UNSUPPORTED;
+    const bool same = s->gexec && s->gk0 == k_begin && s->gk1 == k_end && s->gK == K && s->gdt == dt &&
+                      s->gtol == tol && s->gmi == max_iter;
+    if (!same) {
+        if (s->gexec) cudaGraphExecDestroy(s->gexec);
+        if (s->graph) cudaGraphDestroy(s->graph);
+        s->gexec = nullptr;
+        s->graph = nullptr;
+        // capture on a private stream (the state's own stream may be the legacy default stream),
+        // with the per-launch profiling events off
+        cudaStream_t cs = nullptr;
+        if (!cuda_ok(s, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) return GTQA_ERR_CUDA;
+        const cudaStream_t own = s->stream;
+        const bool prof = s->prof_on;
+        const long long layers = s->layers, gates = s->gates, launches = s->launches;
+        s->stream = cs;
+        s->prof_on = false;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        int lrc = e == cudaSuccess ? anneal_launches(s, k_begin, k_end, K, dt, tol, max_iter) : GTQA_ERR_CUDA;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cs, &g) : e;
+        s->stream = own;
+        s->prof_on = prof;
+        s->layers = layers;
+        s->gates = gates;
+        s->launches = launches;
+        cudaStreamDestroy(cs);
+        if (lrc == GTQA_OK && e2 == cudaSuccess && g) e = cudaGraphInstantiate(&s->gexec, g, 0);
+        else e = e2 != cudaSuccess ? e2 : cudaErrorUnknown;
+        if (e != cudaSuccess || lrc != GTQA_OK) {
+            if (g) cudaGraphDestroy(g);
+            s->gexec = nullptr;
+            cudaGetLastError();
+            // a failed capture leaves the state usable: nothing was launched
+            if (s->sticky == GTQA_ERR_CUDA) s->sticky = GTQA_OK;
+            return GTQA_ERR_UNSUPPORTED;
+        }
+        s->graph = g;
+        s->gk0 = k_begin;
+        s->gk1 = k_end;
+        s->gK = K;
+        s->gdt = dt;
+        s->gtol = tol;
+        s->gmi = max_iter;
     }
+    if (!cuda_ok(s, cudaGraphLaunch(s->gexec, s->stream))) return GTQA_ERR_CUDA;
+    const long long L = (long long)k_end - k_begin + 1;
+    s->layers += L;
+    s->gates += L * s->m;
+    s->launches += 3 * L;
     return GTQA_OK;
 }
 

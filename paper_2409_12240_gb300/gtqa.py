@@ -41,7 +41,7 @@ EXPORTED = [
     "gtqa_profile_name", "gtqa_alu_peak", "gtqa_debug_barrier", "gtqa_math_check", "gtqa_bp_static",
     "gtqa_barrier_bench", "gtqa_residual", "gtqa_entropy", "gtqa_spectral_bipartition", "gtqa_sample",
     "gtqa_trotter_split", "gtqa_anneal_ex", "gtqa_apply_gates", "gtqa_apply_single_qubit_gates",
-    "gtqa_max_degree",
+    "gtqa_max_degree", "gtqa_anneal_graph", "gtqa_autotune", "gtqa_set_grid",
 ]
 KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
@@ -93,6 +93,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_bp_sweep": (I32, [P, D, I32, U32, ctypes.POINTER(I32), ctypes.POINTER(D)]),
         "gtqa_regauge": (I32, [P]),
         "gtqa_anneal": (I32, [P, I32, I32, I32, D, D, I32]),
+        "gtqa_anneal_graph": (I32, [P, I32, I32, I32, D, D, I32]),
+        "gtqa_autotune": (I32, [P, D, D, D, I32, P]),
+        "gtqa_set_grid": (I32, [P, P]),
         "gtqa_trotter_split": (I32, [P, D, D, D]),
         "gtqa_anneal_ex": (I32, [P, I32, I32, I32, D, D, I32, I32, P]),
         "gtqa_apply_gates": (I32, [P, I32, P, P]),
@@ -256,6 +259,25 @@ def gtqa_apply_single_qubit_gates(s: int, vertex, W) -> None:
         raise ValueError("one 2x2 matrix per gate")
     _check(load().gtqa_apply_single_qubit_gates(s, int(v.size), v.ctypes.data if v.size else None,
                                                 w.ctypes.data if v.size else None), "gtqa_apply_single_qubit_gates")
+
+
+def gtqa_anneal_graph(s: int, k_begin: int, k_end: int, K: int, dt: float, tol: float, max_iter: int) -> None:
+    """gtqa_anneal replayed from a CUDA graph captured once per argument set (asynchronous)."""
+    _check(load().gtqa_anneal_graph(s, int(k_begin), int(k_end), int(K), float(dt), float(tol), int(max_iter)),
+           "gtqa_anneal_graph")
+
+
+def gtqa_autotune(s: int, tau: float, dt: float, tol: float, max_iter: int) -> Tuple[int, int, int]:
+    """Time each phase kernel's candidate grid sizes on the current state; keep and return the
+    fastest (gates, BP, regauge)."""
+    g = np.zeros(3, dtype=np.int32)
+    _check(load().gtqa_autotune(s, float(tau), float(dt), float(tol), int(max_iter), g.ctypes.data), "gtqa_autotune")
+    return int(g[0]), int(g[1]), int(g[2])
+
+
+def gtqa_set_grid(s: int, grid) -> None:
+    g = np.ascontiguousarray(np.asarray(grid, dtype=np.int32))
+    _check(load().gtqa_set_grid(s, g.ctypes.data), "gtqa_set_grid")
 
 
 def gtqa_sizes(s: int) -> Tuple[int, int, int, int]:

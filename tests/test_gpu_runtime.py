@@ -90,3 +90,70 @@ def test_newton_refined_reciprocal_and_roots_match_cuda():
     for a, b in ((0, 1), (2, 3), (4, 5)):
         rel = np.abs(out[:, a] - out[:, b]) / np.abs(out[:, b])
         assert rel.max() < 4 * np.finfo(float).eps, (a, rel.max())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_anneal_from_a_cuda_graph_matches_direct_launches(precision):
+    """gtqa_anneal_graph (layers captured once into a CUDA graph) gives the state of gtqa_anneal,
+    bit for bit, for a first range, a replay of a new range, and a batched state."""
+    import numpy as np
+    from instances import make_batch, make_instance
+    G = U.lib()
+    K, dt, tol, mi = 200, 0.2, 1e-8, 100
+    for kind in ("single", "batch"):
+        out = []
+        for graph in (False, True):
+            opt = G.gtqa_options_init(precision=precision)
+            if kind == "single":
+                inst = make_instance(200, 5)
+                s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 4, inst.colour, opt)
+            else:
+                insts = make_batch(6, seed=3, n_lo=50, n_hi=120)
+                s = G.gtqa_create_batch([x.n for x in insts], [x.edges for x in insts], [x.J for x in insts],
+                                        [x.h for x in insts], 4, [x.colour for x in insts], opt)
+            try:
+                for k0, k1 in ((1, 8), (9, 20)):
+                    if graph:
+                        G.gtqa_anneal_graph(s, k0, k1, K, dt, tol, mi)
+                    else:
+                        G.gtqa_anneal(s, k0, k1, K, dt, tol, mi)
+                out.append((G.gtqa_get_state(s), G.gtqa_marginals(s)[0], G.gtqa_stats(s)))
+            finally:
+                G.gtqa_destroy(s)
+        (sa, ra, ta), (sb, rb, tb) = out
+        for a, b in zip(sa, sb):
+            assert np.array_equal(a, b), kind
+        assert np.array_equal(ra, rb)
+        assert ta["layers"] == tb["layers"] == 20 and ta["bp_calls"] == tb["bp_calls"] == 20
+
+
+def test_autotune_restores_the_state_and_keeps_results():
+    """gtqa_autotune leaves the state and statistics as they were, keeps grid sizes within the SM
+    count, and the layers it then runs give the results of the default grid (FP64, bitwise on
+    lambda and marginals)."""
+    import numpy as np
+    from instances import make_instance
+    G = U.lib()
+    inst = make_instance(1000, 0)
+    K, dt, tol, mi = 3200, 0.2, 1e-10, 100
+    res = []
+    for tune in (False, True):
+        s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 4, inst.colour, G.gtqa_options_init(precision=0))
+        try:
+            G.gtqa_anneal(s, 1, 30, K, dt, tol, mi)
+            before = G.gtqa_get_state(s)
+            st0 = G.gtqa_stats(s)
+            if tune:
+                grid = G.gtqa_autotune(s, 31 / K, dt, tol, mi)
+                assert all(1 <= g <= 152 for g in grid), grid
+                after = G.gtqa_get_state(s)
+                for a, b in zip(before, after):
+                    assert np.array_equal(a, b)
+                st1 = G.gtqa_stats(s)
+                for k in ("layers", "gates", "bp_calls", "bp_sweeps", "discarded_weight"):
+                    assert st0[k] == st1[k], k
+            G.gtqa_anneal(s, 31, 40, K, dt, tol, mi)
+            res.append((G.gtqa_get_state(s)[1], G.gtqa_marginals(s)[0]))
+        finally:
+            G.gtqa_destroy(s)
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
