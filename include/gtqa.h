@@ -245,6 +245,16 @@ int gtqa_anneal_ex(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, dou
 int gtqa_apply_gates(gtqa_state* s, int32_t k, const int32_t* edge, const double* U);
 
 /*
+ * Host-only: the launch layering gtqa_apply_gates uses for a gate list.  layer_out[q] is the
+ * launch of gate q: one after the latest earlier gate sharing a vertex with it (0 if none).
+ * Gates of one launch have disjoint endpoints, and gates sharing a vertex keep their order.
+ * n_layers_out (nullable) receives the number of launches.  edges: host int32 [m][2]; edge:
+ * host int32 [k], each in [0, m).
+ */
+int gtqa_gate_layers(int32_t n, int32_t m, const int32_t* edges, int32_t k, const int32_t* edge, int32_t* layer_out,
+                     int32_t* n_layers_out);
+
+/*
  * Arbitrary one-qubit gates (Sec. II D): Gamma_a[i] <- sum_i' W[q][i][i'] Gamma_a[i'] for
  * a = vertex[q], in list order (W: host array of k x 4 complex128, interleaved, row-major).
  * Gates on one vertex are composed on the host, then one launch applies every vertex's

@@ -1045,6 +1045,22 @@ int zero_barriers(gtqa_state* s) {
     return cuda_ok(s, cudaMemsetAsync(&c->bar_pk[0], 0, sizeof(c->bar_pk), s->stream)) ? GTQA_OK : GTQA_ERR_CUDA;
 }
 
+// As-soon-as-possible layering of a gate list: a gate goes one launch after the latest earlier
+// gate that shares a vertex with it, so gates of one launch have disjoint endpoints and every
+// pair of gates sharing a vertex keeps its order.  Returns the number of launches.
+int gate_layers(int n, const int* edges, int k, const int32_t* edge, int32_t* layer) {
+    std::vector<int> depth(n, 0);
+    int nl = 0;
+    for (int q = 0; q < k; ++q) {
+        const int a = edges[2 * (size_t)edge[q]], b = edges[2 * (size_t)edge[q] + 1];
+        const int L = std::max(depth[a], depth[b]);
+        layer[q] = L;
+        depth[a] = depth[b] = L + 1;
+        nl = std::max(nl, L + 1);
+    }
+    return nl;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1292,18 +1308,8 @@ int gtqa_apply_gates(gtqa_state* s, int32_t k, const int32_t* edge, const double
             if (!std::isfinite(U[32 * (size_t)q + t])) return GTQA_ERR_INVALID_ARG;
     }
     if (k == 0) return GTQA_OK;
-    // As-soon-as-possible layering: a gate goes one launch after the latest earlier gate
-    // that shares a vertex with it, so gates of one launch have disjoint endpoints and
-    // every pair of gates sharing a vertex keeps its order.
-    std::vector<int> depth(s->n, 0), lay(k);
-    int nl = 0;
-    for (int q = 0; q < k; ++q) {
-        const int a = s->h_edges[2 * (size_t)edge[q]], b = s->h_edges[2 * (size_t)edge[q] + 1];
-        const int L = std::max(depth[a], depth[b]);
-        lay[q] = L;
-        depth[a] = depth[b] = L + 1;
-        nl = std::max(nl, L + 1);
-    }
+    std::vector<int> lay(k);
+    const int nl = gate_layers(s->n, s->h_edges.data(), k, edge, lay.data());
     std::vector<int> off(nl + 1, 0);
     for (int q = 0; q < k; ++q) ++off[lay[q] + 1];
     for (int L = 0; L < nl; ++L) off[L + 1] += off[L];
@@ -1819,6 +1825,19 @@ int gtqa_set_state(gtqa_state* s, const double* gamma, const double* lambda, con
     if (!cuda_ok(s, cudaMemcpyAsync(s->lam, L.data(), L.size() * sizeof(double), cudaMemcpyHostToDevice, st)) ||
         !cuda_ok(s, cudaStreamSynchronize(st)))
         return GTQA_ERR_CUDA;
+    return GTQA_OK;
+}
+
+int gtqa_gate_layers(int32_t n, int32_t m, const int32_t* edges, int32_t k, const int32_t* edge, int32_t* layer_out,
+                     int32_t* n_layers_out) {
+    if (n < 1 || m < 0 || k < 0 || (m > 0 && !edges) || (k > 0 && (!edge || !layer_out))) return GTQA_ERR_INVALID_ARG;
+    for (int e = 0; e < m; ++e)
+        if (edges[2 * e] < 0 || edges[2 * e] >= n || edges[2 * e + 1] < 0 || edges[2 * e + 1] >= n)
+            return GTQA_ERR_INVALID_ARG;
+    for (int q = 0; q < k; ++q)
+        if (edge[q] < 0 || edge[q] >= m) return GTQA_ERR_INVALID_ARG;
+    const int nl = gate_layers(n, edges, k, edge, layer_out);
+    if (n_layers_out) *n_layers_out = nl;
     return GTQA_OK;
 }
 

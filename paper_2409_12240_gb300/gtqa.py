@@ -41,7 +41,7 @@ EXPORTED = [
     "gtqa_profile_name", "gtqa_alu_peak", "gtqa_debug_barrier", "gtqa_math_check", "gtqa_bp_static",
     "gtqa_barrier_bench", "gtqa_residual", "gtqa_entropy", "gtqa_spectral_bipartition", "gtqa_sample",
     "gtqa_trotter_split", "gtqa_anneal_ex", "gtqa_apply_gates", "gtqa_apply_single_qubit_gates",
-    "gtqa_max_degree", "gtqa_anneal_graph", "gtqa_autotune", "gtqa_set_grid",
+    "gtqa_max_degree", "gtqa_anneal_graph", "gtqa_autotune", "gtqa_set_grid", "gtqa_gate_layers",
 ]
 KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
@@ -96,6 +96,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_anneal_graph": (I32, [P, I32, I32, I32, D, D, I32]),
         "gtqa_autotune": (I32, [P, D, D, D, I32, P]),
         "gtqa_set_grid": (I32, [P, P]),
+        "gtqa_gate_layers": (I32, [I32, I32, P, I32, P, P, ctypes.POINTER(I32)]),
         "gtqa_trotter_split": (I32, [P, D, D, D]),
         "gtqa_anneal_ex": (I32, [P, I32, I32, I32, D, D, I32, I32, P]),
         "gtqa_apply_gates": (I32, [P, I32, P, P]),
@@ -278,6 +279,17 @@ def gtqa_autotune(s: int, tau: float, dt: float, tol: float, max_iter: int) -> T
 def gtqa_set_grid(s: int, grid) -> None:
     g = np.ascontiguousarray(np.asarray(grid, dtype=np.int32))
     _check(load().gtqa_set_grid(s, g.ctypes.data), "gtqa_set_grid")
+
+
+def gtqa_gate_layers(n: int, edges, edge) -> Tuple[np.ndarray, int]:
+    """Host-only: (launch of each gate, number of launches) of gtqa_apply_gates' layering."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    g = np.ascontiguousarray(np.asarray(edge, dtype=np.int32).reshape(-1))
+    lay = np.zeros(max(g.size, 1), dtype=np.int32)
+    nl = ctypes.c_int32()
+    _check(load().gtqa_gate_layers(int(n), int(e.shape[0]), e.ctypes.data, int(g.size), g.ctypes.data, lay.ctypes.data,
+                                   ctypes.byref(nl)), "gtqa_gate_layers")
+    return lay[:g.size], int(nl.value)
 
 
 def gtqa_sizes(s: int) -> Tuple[int, int, int, int]:

@@ -7,7 +7,7 @@ import re
 import numpy as np
 import pytest
 
-from instances import check_colouring, make_instance, random_regular_graph
+from instances import check_colouring, edge_colouring, make_instance, random_regular_graph
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -113,3 +113,29 @@ def test_library_colouring_uses_delta_colours_when_it_can(G):
     pe = np.array(sorted((min(a, b), max(a, b)) for a, b in outer + inner + spokes), dtype=np.int32)
     col, k = G.gtqa_edge_colouring(10, pe)
     assert k == 4 and check_colouring(10, pe, col)
+
+
+def test_gate_layering_keeps_order_and_disjointness(G):
+    """gtqa_apply_gates' launch layering: gates of one launch have disjoint endpoints, two gates
+    sharing a vertex keep their list order, and each gate sits one launch after its latest
+    predecessor on a shared vertex (so the layering is as shallow as the order allows)."""
+    from instances import random_gate_inputs
+    n = 40
+    e = random_regular_graph(n, 3, 4)
+    gate_e, _, _, _ = random_gate_inputs(n, e.shape[0], 400, 0, seed=9)
+    lay, nl = G.gtqa_gate_layers(n, e, gate_e)
+    assert nl == lay.max() + 1
+    depth = np.zeros(n, dtype=int)
+    for q, ed in enumerate(gate_e.tolist()):
+        a, b = e[ed]
+        assert lay[q] == max(depth[a], depth[b])
+        depth[a] = depth[b] = lay[q] + 1
+    for L in range(nl):
+        verts = e[gate_e[lay == L]].ravel()
+        assert np.unique(verts).size == verts.size
+    # one colour class of a proper colouring is a single launch
+    col = edge_colouring(n, e)
+    lay1, nl1 = G.gtqa_gate_layers(n, e, np.nonzero(col == 0)[0])
+    assert nl1 == 1 and (lay1 == 0).all()
+    with pytest.raises(Exception):
+        G.gtqa_gate_layers(n, e, [e.shape[0]])
