@@ -110,14 +110,16 @@ void gtqa_options_init(gtqa_options* opt);
  *              for the library's own (gtqa_edge_colouring).
  *              Gates run colour by colour, ascending (the paper leaves the order open).
  *   J, h       host float64 couplings [m] and fields [n] of Eq. (objective_function)
- *   chi        maximal bond dimension, 1 <= chi <= 8
+ *   chi        maximal bond dimension, 1 <= chi <= 16 (storage 2, 4, 8 or 16)
  *   opt        options or NULL for defaults
  *   out        receives the new state; *out is NULL on failure
  * Graphs with a vertex of degree 4 (the random 4-regular graphs of Sec. V) get vertex tensors
- * with four bonds, Gamma [n][2][CHI]^4, and plain per-phase kernels.  Such a state needs the
- * FP64 precision, one instance and chi <= 4: anything else returns GTQA_ERR_UNSUPPORTED.
- * gtqa_sample and gtqa_residual return GTQA_ERR_UNSUPPORTED on it; every other call works
- * as documented.  Its BP reads the distance on the host after every sweep.
+ * with four bonds, Gamma [n][2][CHI]^4; 8 < chi <= 16 gets storage bond dimension 16.  Both run
+ * on plain per-phase kernels and need the FP64 precision and one instance; degree 4 needs
+ * chi <= 4.  Anything else returns GTQA_ERR_UNSUPPORTED.  On such a state gtqa_sample,
+ * gtqa_residual, gtqa_autotune and gtqa_anneal_graph return GTQA_ERR_UNSUPPORTED, and so does
+ * gtqa_apply_gates at chi > 8; every other call works as documented.  Its BP reads the
+ * distance on the host after every sweep.
  */
 int gtqa_create(int32_t n, int32_t m, const int32_t* edges, const int32_t* colour,
                 const double* J, const double* h, int32_t chi,

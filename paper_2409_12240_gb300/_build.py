@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["gtqa_api.cu", "gtqa_fp64_gates.cu", "gtqa_fp64_bp.cu", "gtqa_fp64_regauge.cu",
            "gtqa_mixed_gates.cu", "gtqa_mixed_bp.cu", "gtqa_mixed_regauge.cu", "gtqa_diag.cu",
            "gtqa_static.cu", "gtqa_fp64_general.cu", "gtqa_mixed_general.cu",
-           "gtqa_deg4.cu"]
+           "gtqa_plain.cu"]
 
 
 def _nvcc() -> str:

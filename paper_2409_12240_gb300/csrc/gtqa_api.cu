@@ -66,6 +66,9 @@ struct gtqa_state {
     std::vector<int> h_edges;   // endpoints of every edge (2m), for host-side scheduling
     // degree-4 graphs: slots per vertex, all vertex ids, host copies for the gate phases
     int D = 3;
+    bool plain = false;         // degree 4 or CHI = 16: the plain kernels
+    cd* pscratch = nullptr;     // plain path: per-block tensor buffers in global memory
+    cd* dm = nullptr;           // plain path: new - old of every message of a sweep
     int4* vslots4 = nullptr;
     int* allv = nullptr;
     std::vector<int> h_deg, h_cedges, h_coff;
@@ -137,6 +140,7 @@ int storage_chi(int chi) {
     if (chi <= 2) return 2;
     if (chi <= 4) return 4;
     if (chi <= 8) return 8;
+    if (chi <= 16) return 16;
     return 0;
 }
 
@@ -425,7 +429,7 @@ void free_state(gtqa_state* s) {
                     s->vert_edges, s->vert_inst, s->J, s->h, s->colour_edges, s->colour_off, s->last_colour, s->first_colour,
                     s->iso, s->inst_vbeg, s->inst_m, s->acc, s->inst_done, s->inst_iters, s->inst_dist,
                     s->stats, s->ctl, s->rho, s->sign, s->flags, s->rbuf, s->cutbuf, s->xs, s->ps,
-                    s->gate_edge, s->gate_U, s->sq_vertex, s->sq_W, s->vslots4, s->allv};
+                    s->gate_edge, s->gate_U, s->sq_vertex, s->sq_W, s->vslots4, s->allv, s->pscratch, s->dm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& p : s->pending) {
@@ -594,14 +598,18 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
             ncol = gcol[e] + 1 > ncol ? gcol[e] + 1 : ncol;
         }
     }
-    // vertex degree 4 (Sec. V's 4-regular graphs): the plain degree-4 kernels, FP64, one
-    // instance, CHI <= 4
+    // vertex degree 4 (Sec. V's 4-regular graphs) or storage bond dimension 16: the plain
+    // kernels, FP64, one instance
     int Dmax = 0;
     for (long long v = 0; v < N; ++v) Dmax = std::max(Dmax, deg[v]);
-    if (Dmax == 4 && (B != 1 || o.precision != GTQA_FP64 || storage_chi(chi) > 4)) return GTQA_ERR_UNSUPPORTED;
+    const int Dst = Dmax == 4 ? 4 : 3;
+    const bool plain = Dst == 4 || storage_chi(chi) == 16;
+    if (plain && (B != 1 || o.precision != GTQA_FP64 || !plain_supported(storage_chi(chi), Dst)))
+        return GTQA_ERR_UNSUPPORTED;
     gtqa_state* s = new (std::nothrow) gtqa_state();
     if (!s) return GTQA_ERR_OOM;
-    s->D = Dmax == 4 ? 4 : 3;
+    s->D = Dst;
+    s->plain = plain;
     s->B = B;
     s->n = (int)N;
     s->m = (int)Mtot;
@@ -622,7 +630,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         delete s;
         return GTQA_ERR_CUDA;
     }
-    for (int pk = 0; pk < PK_COUNT; ++pk) {
+    for (int pk = 0; pk < PK_COUNT && !s->plain; ++pk) {
         size_t base = 0;
         int tpb = 0, bps = 0;
         if (!phase_shape(mixed(s), pk, s->CHI, &base, &tpb)) {
@@ -672,7 +680,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
             if (gcol[e] == c) cedges.push_back((int)e);
     }
     coff[ncol] = (int)cedges.size();
-    if (s->D == 4) {
+    if (s->plain) {
         s->h_cedges = cedges;
         s->h_coff = coff;
         s->h_J.assign(J ? J : (const double*)nullptr, J ? J + Mtot : (const double*)nullptr);
@@ -698,12 +706,14 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         (rc = dalloc(s, &s->rho, (size_t)s->n * 4)) || (rc = dalloc(s, &s->sign, s->n)) ||
         (rc = dalloc(s, &s->flags, 4)) || (rc = dalloc(s, &s->rbuf, 1)) ||
         (rc = dalloc(s, &s->cutbuf, std::max(s->m, 1))) || (rc = dalloc(s, &s->xs, s->n)) ||
-        (rc = dalloc(s, &s->ps, s->n)) || (s->D == 4 && (rc = dalloc(s, &s->vslots4, s->n))) ||
-        (s->D == 4 && (rc = dalloc(s, &s->allv, s->n)))) {
+        (rc = dalloc(s, &s->ps, s->n)) || (s->plain && (rc = dalloc(s, &s->vslots4, s->n))) ||
+        (s->plain && (rc = dalloc(s, &s->allv, s->n))) ||
+        (s->plain && (rc = dalloc(s, &s->pscratch, plain_scratch_entries(s->CHI, s->D, s->n, s->m)))) ||
+        (s->plain && (rc = dalloc(s, &s->dm, (size_t)2 * s->m * CHI * CHI)))) {
         free_state(s);
         return rc;
     }
-    if (s->D == 4) {
+    if (s->plain) {
         std::vector<int> all(N);
         for (long long a = 0; a < N; ++a) all[a] = (int)a;
         if (!cuda_ok(s, cudaMemcpyAsync(s->vslots4, v4.data(), sizeof(int4) * N, cudaMemcpyHostToDevice, s->stream)) ||
@@ -859,14 +869,16 @@ void tridiag_min_eigvec(const std::vector<double>& a, const std::vector<double>&
 // ---------------------------------------------------------------------------
 // degree-4 graphs: host orchestration of the plain kernels of gtqa_deg4.cuh
 // ---------------------------------------------------------------------------
-D4Args d4_args(gtqa_state* s, int cur) {
-    D4Args a;
+PlainArgs d4_args(gtqa_state* s, int cur) {
+    PlainArgs a;
     a.Gamma = s->Gamma;
     a.T = s->T;
     a.lam = s->lam;
     a.msg_cur = s->msg[cur];
     a.msg_nxt = s->msg[cur ^ 1];
     a.X = s->X;
+    a.dm = s->dm;
+    a.scratch = s->pscratch;
     a.vslots = s->vslots4;
     a.edge_info = s->edge_info;
     a.n = s->n;
@@ -896,7 +908,8 @@ int d4_mixing(gtqa_state* s, double t) {
     if ((rc = grow_pair(s, &s->sq_vertex, &s->sq_W, 4, s->sq_cap, (size_t)s->n))) return rc;
     if (!cuda_ok(s, cudaMemcpyAsync(s->sq_W, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, s->stream)))
         return GTQA_ERR_CUDA;
-    if (d4_single_gates_launch(s->CHI, s->Gamma, s->allv, s->sq_W, s->n, s->stream) != cudaSuccess) return d4_fail(s);
+    if (plain_single_gates_launch(s->CHI, s->D, s->Gamma, s->allv, s->sq_W, s->n, s->stream) != cudaSuccess)
+        return d4_fail(s);
     s->launches += 1;
     return GTQA_OK;
 }
@@ -924,18 +937,36 @@ int d4_interaction(gtqa_state* s, double tZ) {
     if (!cuda_ok(s, cudaMemcpyAsync(s->gate_U, U.data(), sizeof(double) * U.size(), cudaMemcpyHostToDevice, s->stream)))
         return GTQA_ERR_CUDA;
     for (int c = 0; c < s->ncol; ++c) {
-        GenArgs g;
-        g.Gamma = s->Gamma;
-        g.lam = s->lam;
-        g.edge_info = s->edge_info;
-        g.vert_edges = s->vslots4;
-        g.gate_edge = s->colour_edges + s->h_coff[c];
-        g.gate_U = s->gate_U + 16 * (size_t)s->h_coff[c];
-        g.count = s->h_coff[c + 1] - s->h_coff[c];
-        g.stats = s->stats;
-        g.chi = s->chi;
-        g.svd_cut = s->svd_cutoff;
-        if (d4_general_gates_launch(s->CHI, g, s->stream) != cudaSuccess) return d4_fail(s);
+        cudaError_t e;
+        if (s->CHI == 16) {
+            Gate16Args g;
+            g.Gamma = s->Gamma;
+            g.lam = s->lam;
+            g.edge_info = s->edge_info;
+            g.vslots = s->vslots4;
+            g.gate_edge = s->colour_edges + s->h_coff[c];
+            g.gate_U = s->gate_U + 16 * (size_t)s->h_coff[c];
+            g.scratch = s->pscratch;
+            g.count = s->h_coff[c + 1] - s->h_coff[c];
+            g.stats = s->stats;
+            g.chi = s->chi;
+            g.svd_cut = s->svd_cutoff;
+            e = ising16_gates_launch(g, s->stream);
+        } else {
+            GenArgs g;
+            g.Gamma = s->Gamma;
+            g.lam = s->lam;
+            g.edge_info = s->edge_info;
+            g.vert_edges = s->vslots4;
+            g.gate_edge = s->colour_edges + s->h_coff[c];
+            g.gate_U = s->gate_U + 16 * (size_t)s->h_coff[c];
+            g.count = s->h_coff[c + 1] - s->h_coff[c];
+            g.stats = s->stats;
+            g.chi = s->chi;
+            g.svd_cut = s->svd_cutoff;
+            e = plain_general_gates_launch(s->CHI, s->D, g, s->stream);
+        }
+        if (e != cudaSuccess) return d4_fail(s);
         s->launches += 1;
     }
     return GTQA_OK;
@@ -950,8 +981,9 @@ int d4_trotter(gtqa_state* s, double tZ, double tXpre, double tXpost) {
 }
 
 int d4_regauge(gtqa_state* s) {
-    Ctx c = make_ctx(s);
-    if (d4_regauge_launch(s->CHI, c, s->cur4, d4_args(s, s->cur4), s->stream) != cudaSuccess) return d4_fail(s);
+    if (plain_regauge_launch(s->CHI, s->D, d4_args(s, s->cur4), (const cd*)s->msg[s->cur4], s->eig_cutoff,
+                             s->svd_cutoff, s->stream) != cudaSuccess)
+        return d4_fail(s);
     s->launches += 2;
     return GTQA_OK;
 }
@@ -960,19 +992,19 @@ int d4_regauge(gtqa_state* s) {
 // each sweep and stops after the sweep where dist/|E| < tol, or after max_iter sweeps.
 int d4_bp(gtqa_state* s, double tol, int max_iter, uint32_t flags, int32_t* iters_out, double* dist_out) {
     int cur = s->cur4;
-    D4Args a = d4_args(s, cur);
+    PlainArgs a = d4_args(s, cur);
     a.warm = (flags & GTQA_BP_WARM_START) ? 1 : 0;
     a.msg_nxt = s->msg[cur];   // the init kernel writes the warm start where the first sweep reads
-    if (s->n > 0 && d4_bp_init_launch(s->CHI, a, s->stream) != cudaSuccess) return d4_fail(s);
+    if (s->n > 0 && plain_bp_init_launch(s->CHI, s->D, a, s->stream) != cudaSuccess) return d4_fail(s);
     s->launches += 1;
     int it = 0;
     double dist = 0.0;
     bool conv = false;
     for (; it < max_iter;) {
         if (!cuda_ok(s, cudaMemsetAsync(s->acc, 0, sizeof(double), s->stream))) return GTQA_ERR_CUDA;
-        D4Args w = d4_args(s, cur);
-        if (d4_bp_sweep_launch(s->CHI, w, s->stream) != cudaSuccess) return d4_fail(s);
-        s->launches += 1;
+        PlainArgs w = d4_args(s, cur);
+        if (plain_bp_sweep_launch(s->CHI, s->D, w, s->stream) != cudaSuccess) return d4_fail(s);
+        s->launches += 2;
         double acc = 0.0;
         if (!cuda_ok(s, cudaMemcpyAsync(&acc, s->acc, sizeof(double), cudaMemcpyDeviceToHost, s->stream)) ||
             !cuda_ok(s, cudaStreamSynchronize(s->stream)))
@@ -1088,7 +1120,7 @@ int gtqa_trotter_layer(gtqa_state* s, double tau, double dt) {
     int rc = check_state(s);
     if (rc) return rc;
     if (!std::isfinite(tau) || !std::isfinite(dt)) return GTQA_ERR_INVALID_ARG;
-    if (s->D == 4) return d4_trotter(s, dt * tau, 0.0, dt * (1.0 - tau));
+    if (s->plain) return d4_trotter(s, dt * tau, 0.0, dt * (1.0 - tau));
     Ctx c = make_ctx(s);
     c.phases = PH_GATES;
     c.k0 = c.k1 = 0;
@@ -1115,7 +1147,7 @@ int gtqa_autotune(gtqa_state* s, double tau, double dt, double tol, int32_t max_
     int rc = check_state(s);
     if (rc) return rc;
     if (!std::isfinite(tau) || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1) return GTQA_ERR_INVALID_ARG;
-    if (s->D == 4) return GTQA_ERR_UNSUPPORTED;
+    if (s->plain) return GTQA_ERR_UNSUPPORTED;
     // snapshot of everything a layer writes, restored before every timed launch and at the end
     struct Buf { void* p; size_t bytes; std::vector<unsigned char> h; };
     const size_t gel = gamma_elems(s), mel = msg_elems(s), eb = elem_bytes(s);
@@ -1218,7 +1250,7 @@ int gtqa_trotter_split(gtqa_state* s, double t_Z, double t_X_pre, double t_X_pos
     int rc = check_state(s);
     if (rc) return rc;
     if (!std::isfinite(t_Z) || !std::isfinite(t_X_pre) || !std::isfinite(t_X_post)) return GTQA_ERR_INVALID_ARG;
-    if (s->D == 4) return d4_trotter(s, t_Z, t_X_pre, t_X_post);
+    if (s->plain) return d4_trotter(s, t_Z, t_X_pre, t_X_post);
     Ctx c = make_ctx(s);
     c.phases = PH_GATES;
     c.k0 = c.k1 = 0;
@@ -1237,7 +1269,7 @@ int gtqa_bp_sweep(gtqa_state* s, double tol, int32_t max_iter, uint32_t flags, i
     int rc = check_state(s);
     if (rc) return rc;
     if (max_iter < 1 || !(tol >= 0.0) || (flags & ~3u)) return GTQA_ERR_INVALID_ARG;
-    if (s->D == 4) return d4_bp(s, tol, max_iter, flags, iters_out, dist_out);
+    if (s->plain) return d4_bp(s, tol, max_iter, flags, iters_out, dist_out);
     Ctx c = make_ctx(s);
     c.phases = PH_BP | ((flags & GTQA_BP_WARM_START) ? PH_WARM : 0u);
     c.k0 = c.k1 = 0;
@@ -1260,7 +1292,7 @@ int gtqa_sample(gtqa_state* s, int32_t k, const int32_t* order, const double* u,
                 int8_t* x_out, double* p_out) {
     int rc = check_state(s);
     if (rc) return rc;
-    if (s->D == 4) return GTQA_ERR_UNSUPPORTED;
+    if (s->plain) return GTQA_ERR_UNSUPPORTED;
     if (k < 0 || k > s->n || (k > 0 && (!order || !u)) || !x_out || max_iter < 1 || !(tol >= 0.0))
         return GTQA_ERR_INVALID_ARG;
     std::vector<char> seen(s->n, 0);
@@ -1301,6 +1333,7 @@ int gtqa_sample(gtqa_state* s, int32_t k, const int32_t* order, const double* u,
 int gtqa_apply_gates(gtqa_state* s, int32_t k, const int32_t* edge, const double* U) {
     int rc = check_state(s);
     if (rc) return rc;
+    if (s->plain && s->CHI == 16) return GTQA_ERR_UNSUPPORTED;   // a 64 x 64 core per gate
     if (k < 0 || (k > 0 && (!edge || !U))) return GTQA_ERR_INVALID_ARG;
     for (int q = 0; q < k; ++q) {
         if (edge[q] < 0 || edge[q] >= s->m) return GTQA_ERR_INVALID_ARG;
@@ -1329,14 +1362,14 @@ int gtqa_apply_gates(gtqa_state* s, int32_t k, const int32_t* edge, const double
         a.Gamma = s->Gamma;
         a.lam = s->lam;
         a.edge_info = s->edge_info;
-        a.vert_edges = s->D == 4 ? s->vslots4 : s->vert_edges;
+        a.vert_edges = s->plain ? s->vslots4 : s->vert_edges;
         a.gate_edge = s->gate_edge + off[L];
         a.gate_U = s->gate_U + 16 * (size_t)off[L];
         a.count = off[L + 1] - off[L];
         a.stats = s->stats;
         a.chi = s->chi;
         a.svd_cut = s->svd_cutoff;
-        const cudaError_t e = s->D == 4   ? d4_general_gates_launch(s->CHI, a, s->stream)
+        const cudaError_t e = s->plain    ? plain_general_gates_launch(s->CHI, s->D, a, s->stream)
                               : mixed(s) ? general_gates_launch_mixed(s->CHI, a, s->stream)
                                          : general_gates_launch_fp64(s->CHI, a, s->stream);
         if (e != cudaSuccess) {
@@ -1391,7 +1424,8 @@ int gtqa_apply_single_qubit_gates(gtqa_state* s, int32_t k, const int32_t* verte
     if (!cuda_ok(s, cudaMemcpyAsync(s->sq_vertex, vs.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s->stream)) ||
         !cuda_ok(s, cudaMemcpyAsync(s->sq_W, Wd.data(), sizeof(double) * Wd.size(), cudaMemcpyHostToDevice, s->stream)))
         return GTQA_ERR_CUDA;
-    const cudaError_t e = s->D == 4 ? d4_single_gates_launch(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream)
+    const cudaError_t e = s->plain ? plain_single_gates_launch(s->CHI, s->D, s->Gamma, s->sq_vertex, s->sq_W, cnt,
+                                                               s->stream)
                           : mixed(s) ? single_gates_launch_mixed(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream)
                                      : single_gates_launch_fp64(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream);
     if (e != cudaSuccess) {
@@ -1406,7 +1440,7 @@ int gtqa_apply_single_qubit_gates(gtqa_state* s, int32_t k, const int32_t* verte
 int gtqa_regauge(gtqa_state* s) {
     int rc = check_state(s);
     if (rc) return rc;
-    if (s->D == 4) return d4_regauge(s);
+    if (s->plain) return d4_regauge(s);
     Ctx c = make_ctx(s);
     c.phases = PH_REGAUGE;
     c.k0 = c.k1 = 0;
@@ -1418,7 +1452,7 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
     if (rc) return rc;
     if (K < 1 || k_begin < 1 || k_end < k_begin || k_end > K || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1)
         return GTQA_ERR_INVALID_ARG;
-    if (s->D == 4) {
+    if (s->plain) {
         for (int k = k_begin; k <= k_end; ++k) {
             const double tau = (double)k / (double)K;
             if ((rc = d4_trotter(s, dt * tau, 0.0, dt * (1.0 - tau)))) return rc;
@@ -1436,7 +1470,7 @@ int gtqa_anneal_graph(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, 
     if (rc) return rc;
     if (K < 1 || k_begin < 1 || k_end < k_begin || k_end > K || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1)
         return GTQA_ERR_INVALID_ARG;
-    if (s->D == 4) return GTQA_ERR_UNSUPPORTED;
+    if (s->plain) return GTQA_ERR_UNSUPPORTED;
     const bool same = s->gexec && s->gk0 == k_begin && s->gk1 == k_end && s->gK == K && s->gdt == dt &&
                       s->gtol == tol && s->gmi == max_iter;
     if (!same) {
@@ -1497,7 +1531,7 @@ int gtqa_anneal_ex(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, dou
         (order != GTQA_TROTTER_FIRST && order != GTQA_TROTTER_SYMMETRIC) ||
         (order == GTQA_TROTTER_SYMMETRIC && reverse))
         return GTQA_ERR_INVALID_ARG;
-    if (s->D == 4) {
+    if (s->plain) {
         for (int k = k_begin; k <= k_end; ++k) {
             const double tau = (double)k / (double)K, tZ = dt * tau, tX = dt * (1.0 - tau);
             const bool rev = reverse && reverse[k - k_begin];
@@ -1671,7 +1705,7 @@ int gtqa_spectral_bipartition(int32_t n, int32_t m, const int32_t* edges, uint8_
 int gtqa_residual(gtqa_state* s, double* R_out) {
     int rc = check_state(s);
     if (rc) return rc;
-    if (s->D == 4) return GTQA_ERR_UNSUPPORTED;
+    if (s->plain) return GTQA_ERR_UNSUPPORTED;
     if (!R_out) return GTQA_ERR_INVALID_ARG;
     if (!cuda_ok(s, cudaMemsetAsync(s->rbuf, 0, sizeof(double), s->stream))) return GTQA_ERR_CUDA;
     const cudaError_t e = mixed(s) ? residual_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream)
@@ -1697,8 +1731,8 @@ int gtqa_marginals(gtqa_state* s, double* rho_out, int8_t* sign_out) {
     {
         ProfScope ps(s, GTQA_K_MARGINALS, s->n);
         const cudaError_t e =
-            s->D == 4 ? d4_marginals_launch(s->CHI, (const cd*)s->Gamma, s->lam, s->vslots4, s->n, s->rho, s->sign,
-                                            s->flags, s->stream)
+            s->plain ? plain_marginals_launch(s->CHI, s->D, (const cd*)s->Gamma, s->lam, s->vslots4, s->n, s->rho,
+                                              s->sign, s->flags, s->stream)
             : mixed(s) ? marginals_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho, s->sign,
                                                 s->flags, s->stream)
                        : marginals_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho, s->sign,

@@ -1,0 +1,641 @@
+// The plain path: graph tensor networks whose vertex tensors are too large or have too many
+// bonds for the persistent kernels.  Two shapes are built: degree 4 with CHI <= 4 (the random
+// 4-regular graphs of Sec. V) and degree 3 with CHI = 16 (the largest bond dimension of the
+// chi sweep).  Complex128 throughout (the FP64 precision mode), one instance.
+//
+// Layout: Gamma and T are [n][2][CHI]^D (slot k = k-th incident edge in ascending id, stride
+// CHI^(D-1-k); phantom slots of vertices with fewer edges have dimension 1 with lambda = e_0);
+// lambda [m][CHI]; messages [2m][CHI][CHI] as in the persistent path.
+// The steps are those of the persistent path, in plain launches:
+//   gates    degree 4: general_gates_kernel<CHI, 4> with the diagonal Ising gate (App. E);
+//            CHI = 16: ising16_gate_kernel, the per-physical-index QR-reduced simple update
+//            with a 2 CHI x 2 CHI core (App. E, App. D "Truncation"); one launch per colour
+//            class; mixing gates through single_gates_kernel (Sec. II D);
+//   bp       T = Gamma prod lambda^{1/2} (Eq. (symmetric_gauge)), warm start
+//            diag(lambda)/sum(lambda) (Eq. (reconstructed_messages)); per flooding sweep of
+//            Eq. (local_consistency) one launch over vertices and one over messages for the
+//            exact trace-norm distance (App. B); the host reads the distance after every sweep;
+//   regauge  per edge the Vidal gauge transforms from the two messages (App. D "Vidal gauge
+//            finding"), then per vertex the transforms applied to T;
+//   marginals  Eq. (partial_dens) with the environment of Eq. (bp_approx).
+#pragma once
+
+#include "gtqa_general.cuh"
+
+namespace gtqa {
+
+struct PlainArgs {
+    void* Gamma;
+    void* T;
+    double* lam;
+    const void* msg_cur;      // incoming and previous outgoing messages
+    void* msg_nxt;            // new outgoing messages
+    cd* X;                    // regauge transforms [m][2][CHI^2]
+    cd* dm;                   // [2m][CHI^2]: new - old of every outgoing message of a sweep
+    cd* scratch;              // per-block tensor buffers when shared memory is too small
+    const int4* vslots;       // slots per vertex (x, y, z, w; -1 phantom)
+    const int4* edge_info;    // (u, v, slot at u, slot at v)
+    int n, m;
+    double* acc;              // distance accumulator (one double)
+    int warm;
+};
+
+template <int CHI, int D>
+struct PlainShape {
+    static constexpr int H = ipow(CHI, D), H2 = 2 * H, CC = CHI * CHI;
+    static constexpr int NT = 16 * CC < 1024 ? 16 * CC : 1024;    // threads of the sweep kernel
+    static constexpr int TPO = NT / CC;                           // threads per message entry
+    static constexpr bool SMEM = 3 * H2 * 16 <= 48 * 1024;        // tensor buffers in shared memory
+    static constexpr size_t scratch_per_block = SMEM ? 0 : (size_t)3 * H2;   // complex entries
+};
+
+__device__ __forceinline__ int plain_slot_edge(const int4& v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+// T = Gamma prod_k lambda_k^{1/2}; with warm, the vertex's outgoing messages are set to
+// diag(lambda)/sum(lambda) in msg_nxt (the buffer the first sweep reads).  One block per vertex.
+template <int CHI, int D>
+__global__ void plain_bp_init_kernel(PlainArgs a) {
+    using S = PlainShape<CHI, D>;
+    const int v = blockIdx.x;
+    __shared__ double sq[D][CHI], m0[D][CHI];
+    const int4 sl = a.vslots[v];
+    if (threadIdx.x < D * CHI) {
+        const int k = threadIdx.x / CHI, j = threadIdx.x % CHI;
+        const int e = plain_slot_edge(sl, k);
+        const double lj = lam_get(a.lam, CHI, e, j);
+        sq[k][j] = sqrt(lj);
+        double s = 0.0;
+        for (int q = 0; q < CHI; ++q) s += lam_get(a.lam, CHI, e, q);
+        m0[k][j] = s > 0.0 ? lj / s : 0.0;
+    }
+    __syncthreads();
+    const cd* g = (const cd*)a.Gamma + (size_t)v * S::H2;
+    cd* T = (cd*)a.T + (size_t)v * S::H2;
+    for (int t = threadIdx.x; t < S::H2; t += blockDim.x) {
+        int r = t % S::H;
+        double f = 1.0;
+        for (int k = D - 1; k >= 0; --k) {
+            f *= sq[k][r % CHI];
+            r /= CHI;
+        }
+        T[t] = f * g[t];
+    }
+    if (a.warm) {
+        cd* out = (cd*)a.msg_nxt;
+        for (int t = threadIdx.x; t < D * S::CC; t += blockDim.x) {
+            const int k = t / S::CC, r = t % S::CC;
+            const int e = plain_slot_edge(sl, k);
+            if (e < 0) continue;
+            const int o = 2 * e + (a.edge_info[e].x == v ? 0 : 1);
+            const int j = r / CHI, jp = r % CHI;
+            out[(size_t)o * S::CC + r] = cd{j == jp ? m0[k][j] : 0.0, 0.0};
+        }
+    }
+}
+
+// One flooding sweep for one vertex: every outgoing message
+//   m_{v->b}[j][j'] = sum T[.., j@s, ..] conj(T[.., j'@s, ..]) prod_{o != s} m_o[x_o][x'_o]
+// (Eq. (local_consistency)), divided by its complex trace; new - old goes to dm for the
+// trace-norm kernel.
+template <int CHI, int D>
+__global__ void __launch_bounds__(PlainShape<CHI, D>::NT) plain_bp_sweep_kernel(PlainArgs a) {
+    using S = PlainShape<CHI, D>;
+    constexpr int H2 = S::H2, CC = S::CC, NT = S::NT, TPO = S::TPO;
+    extern __shared__ __align__(16) unsigned char plain_smem[];
+    cd* min = reinterpret_cast<cd*>(plain_smem);   // [D][CC]
+    cd* F = min + D * CC;                          // [CC]
+    cd* T;
+    cd* P0;
+    cd* P1;
+    if constexpr (S::SMEM) {
+        T = F + CC;
+        P0 = T + H2;
+        P1 = P0 + H2;
+    } else {
+        T = a.scratch + (size_t)blockIdx.x * S::scratch_per_block;
+        P0 = T + H2;
+        P1 = P0 + H2;
+    }
+    __shared__ int es[4], in_idx[4], out_idx[4];
+    __shared__ cd itr;
+    const int v = blockIdx.x, tid = threadIdx.x;
+    const cd* src_msg = (const cd*)a.msg_cur;
+    cd* dst_msg = (cd*)a.msg_nxt;
+    if (tid < D) {
+        const int e = plain_slot_edge(a.vslots[v], tid);
+        es[tid] = e;
+        if (e >= 0) {
+            const bool first = a.edge_info[e].x == v;
+            out_idx[tid] = 2 * e + (first ? 0 : 1);
+            in_idx[tid] = 2 * e + (first ? 1 : 0);
+        } else {
+            out_idx[tid] = in_idx[tid] = -1;
+        }
+    }
+    for (int t = tid; t < H2; t += NT) T[t] = ((const cd*)a.T)[(size_t)v * H2 + t];
+    __syncthreads();
+    for (int t = tid; t < D * CC; t += NT) {
+        const int k = t / CC, r = t % CC;
+        min[t] = in_idx[k] >= 0 ? src_msg[(size_t)in_idx[k] * CC + r] : cd{r == 0 ? 1.0 : 0.0, 0.0};
+    }
+    __syncthreads();
+    for (int s = 0; s < D; ++s) {
+        if (es[s] < 0) continue;   // uniform: es is shared
+        const cd* src = T;
+        cd* dst = P0;
+        for (int o = 0; o < D; ++o) {
+            if (o == s) continue;
+            const int so = ipow(CHI, D - 1 - o);
+            for (int t = tid; t < H2; t += NT) {
+                const int x = (t / so) % CHI, base = t - x * so;
+                cd acc = cd{0.0, 0.0};
+#pragma unroll 4
+                for (int q = 0; q < CHI; ++q) acc = cfma(src[base + q * so], min[o * CC + q * CHI + x], acc);
+                dst[t] = acc;
+            }
+            __syncthreads();
+            src = dst;
+            dst = (dst == P0) ? P1 : P0;
+        }
+        // F[j][j'] = sum over the entries with slot-s index j of conj(T[.. j' ..]) src[.. j ..]
+        const int ss = ipow(CHI, D - 1 - s);
+        constexpr int NTERM = H2 / CHI;
+        for (int rr = tid / TPO; rr < CC; rr += NT / TPO) {
+            const int part = tid % TPO;
+            const int j = rr / CHI, jp = rr % CHI;
+            cd f = cd{0.0, 0.0};
+            for (int q = part; q < NTERM; q += TPO) {
+                const int t = (q / ss) * (ss * CHI) + (q % ss);
+                f = cfmac(T[t + jp * ss], src[t + j * ss], f);
+            }
+            f.x = group_sum<TPO>(f.x, group_mask<TPO>());
+            f.y = group_sum<TPO>(f.y, group_mask<TPO>());
+            if (part == 0) F[rr] = f;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            cd tr = cd{0.0, 0.0};
+            for (int q = 0; q < CHI; ++q) tr = tr + F[q * CHI + q];
+            const double d = tr.x * tr.x + tr.y * tr.y;
+            itr = d > 0.0 ? cd{tr.x / d, -tr.y / d} : cd{0.0, 0.0};
+        }
+        __syncthreads();
+        for (int r = tid; r < CC; r += NT) {
+            const cd mn = F[r] * itr;
+            const cd mo = src_msg[(size_t)out_idx[s] * CC + r];
+            dst_msg[(size_t)out_idx[s] * CC + r] = mn;
+            a.dm[(size_t)out_idx[s] * CC + r] = mn - mo;
+        }
+        __syncthreads();
+    }
+}
+
+// Trace norm (sum of singular values, one-sided Jacobi in FP64) of every directed message's
+// new - old; block = CHI^2 / 2 threads, one message per block; the sum goes to *acc.
+template <int CHI>
+__global__ void plain_trace_norm_kernel(const cd* dm, double* acc) {
+    constexpr int CC = CHI * CHI;
+    __shared__ cd A[CC];
+    __shared__ double tn;
+    __shared__ int flag;
+    const int g = threadIdx.x;
+    for (int t = g; t < CC; t += blockDim.x) A[t] = dm[(size_t)blockIdx.x * CC + t];
+    if (g == 0) tn = 0.0;
+    __syncthreads();
+    BlockGroup grp{&flag};
+    jacobi_svd<CHI, double, BlockGroup, false>(A, nullptr, g, grp, group_mask<CHI>(), 1e-15, 60, false);
+    __syncthreads();
+    if (g < CHI) {
+        double c2 = 0.0;
+        for (int r = 0; r < CHI; ++r) c2 += norm2(A[g * CHI + r]);
+        atomicAdd(&tn, sqrt(c2));
+    }
+    __syncthreads();
+    if (g == 0) atomicAdd(acc, tn);
+}
+
+// Vidal gauge finding, edge part (App. D "Vidal gauge finding"), FP64, block = CHI^2 / 2
+// threads: Hermitian eigen-decompositions of m_{a->b} and m_{b->a} (as SVDs; signs from
+// v^H A v), principal square roots and pseudo-inverse square roots, the SVD of
+// M = (m_{a->b}^{1/2})^T m_{b->a}^{1/2}, lambda = S/||S||, X_a = conj(m_{a->b}^{-1/2}) U ||S||^{1/2}
+// and X_b = conj(m_{b->a}^{-1/2}) V^* ||S||^{1/2}.
+template <int CHI>
+__global__ void plain_regauge_edge_kernel(const cd* msg, double* lam, cd* X, double eig_cut, double svd_cut) {
+    constexpr int CC = CHI * CHI;
+    __shared__ cd Am[2][CC], Vm[2][CC], sqm[2][CC], isq[2][CC], M[CC], VM[CC];
+    __shared__ double w[2][CHI], sig[CHI], scal[2];
+    __shared__ int perm[CHI], flag;
+    const int e = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+    BlockGroup grp{&flag};
+    for (int t = tid; t < 2 * CC; t += NT) {
+        const int x = t / CC, r = t % CC;
+        const int row = r % CHI, col = r / CHI;
+        const cd* mm = msg + (size_t)(2 * e + x) * CC;
+        const cd v = mm[row * CHI + col], vt = mm[col * CHI + row];
+        Am[x][col * CHI + row] = cd{0.5 * (v.x + vt.x), 0.5 * (v.y - vt.y)};
+    }
+    __syncthreads();
+    for (int x = 0; x < 2; ++x)
+        jacobi_svd<CHI, double, BlockGroup, true, true>(Am[x], Vm[x], tid, grp, group_mask<CHI>(), 1e-15, 60, true,
+                                                        nullptr, 3e-8);
+    __syncthreads();
+    for (int t = tid; t < 2 * CHI; t += NT) {
+        const int x = t / CHI, k = t % CHI;
+        double n2 = 0.0, sg = 0.0;
+        for (int r = 0; r < CHI; ++r) {
+            const cd av = Am[x][k * CHI + r], vv = Vm[x][k * CHI + r];
+            n2 += norm2(av);
+            sg += vv.x * av.x + vv.y * av.y;
+        }
+        const double wv = nr_sqrt(n2);
+        w[x][k] = sg >= 0.0 ? wv : -wv;
+    }
+    __syncthreads();
+    for (int t = tid; t < 2 * CC; t += NT) {
+        const int x = t / CC, r = t % CC;
+        const int j = r / CHI, jp = r % CHI;
+        double wmax = 0.0;
+        for (int k = 0; k < CHI; ++k) wmax = fmax(wmax, w[x][k]);
+        cd s1 = cd{0.0, 0.0}, s2 = cd{0.0, 0.0};
+        for (int k = 0; k < CHI; ++k) {
+            const double wk = w[x][k];
+            if (!(wk > eig_cut * wmax)) continue;
+            const double is = nr_rsqrt(wk);
+            const double sq = wk * is;
+            const cd vv = Vm[x][k * CHI + j] * conj(Vm[x][k * CHI + jp]);
+            s1 = cfma(cd{sq, 0.0}, vv, s1);
+            s2 = cfma(cd{is, 0.0}, vv, s2);
+        }
+        sqm[x][r] = s1;
+        isq[x][r] = s2;
+    }
+    __syncthreads();
+    for (int t = tid; t < CC; t += NT) {
+        const int k = t % CHI, l = t / CHI;
+        cd acc = cd{0.0, 0.0};
+        for (int j = 0; j < CHI; ++j) acc = cfma(sqm[0][j * CHI + k], sqm[1][j * CHI + l], acc);
+        M[l * CHI + k] = acc;
+    }
+    __syncthreads();
+    jacobi_svd<CHI, double, BlockGroup, true, true>(M, VM, tid, grp, group_mask<CHI>(), 1e-15, 60, true, nullptr, 3e-8);
+    __syncthreads();
+    for (int cc = tid; cc < CHI; cc += NT) {
+        double n2 = 0.0;
+        for (int r = 0; r < CHI; ++r) n2 += norm2(M[cc * CHI + r]);
+        sig[cc] = nr_sqrt(n2);
+    }
+    __syncthreads();
+    for (int cc = tid; cc < CHI; cc += NT) perm[desc_rank(sig, CHI, cc)] = cc;
+    __syncthreads();
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int cc = 0; cc < CHI; ++cc) tot += sig[cc] * sig[cc];
+        const double nrm = nr_sqrt(tot);
+        scal[0] = nrm;
+        scal[1] = nr_sqrt(nrm);
+        const double inrm = nrm > 0.0 ? nr_rcp(nrm) : 0.0;
+        const double smax = sig[perm[0]];
+        for (int r = 0; r < CHI; ++r) {
+            const double s = sig[perm[r]];
+            lam[(size_t)e * CHI + r] = (nrm > 0.0 && s > svd_cut * smax) ? s * inrm : 0.0;
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < 2 * CC; t += NT) {
+        const int x = t / CC, r = t % CC;
+        const int jpp = r / CHI, j = r % CHI;
+        const int pc = perm[j];
+        const double s = sig[pc];
+        cd acc = cd{0.0, 0.0};
+        const bool kept = scal[0] > 0.0 && s > svd_cut * sig[perm[0]];
+        if (kept) {
+            for (int jp = 0; jp < CHI; ++jp) {
+                const cd u = (x == 0) ? nr_rcp(s) * M[pc * CHI + jp] : conj(VM[pc * CHI + jp]);
+                acc = cfma(isq[x][jp * CHI + jpp], u, acc);
+            }
+            acc = scal[1] * acc;
+        }
+        X[((size_t)e * 2 + x) * CC + r] = acc;
+    }
+}
+
+// Vidal gauge finding, vertex part: Gamma[.., j@k, ..] = sum_q T[.., q@k, ..] X_k[q][j] for every
+// slot (X of the edge, from this vertex's side; identity on phantom slots).
+template <int CHI, int D>
+__global__ void plain_regauge_vertex_kernel(PlainArgs a) {
+    using S = PlainShape<CHI, D>;
+    constexpr int H2 = S::H2, CC = S::CC;
+    extern __shared__ __align__(16) unsigned char plain_smem[];
+    cd* Xs = reinterpret_cast<cd*>(plain_smem);   // [D][CC]
+    cd* b0;
+    cd* b1;
+    if constexpr (S::SMEM) {
+        b0 = Xs + D * CC;
+        b1 = b0 + H2;
+    } else {
+        b0 = a.scratch + (size_t)blockIdx.x * S::scratch_per_block;
+        b1 = b0 + H2;
+    }
+    const int v = blockIdx.x;
+    const int4 sl = a.vslots[v];
+    for (int t = threadIdx.x; t < H2; t += blockDim.x) b0[t] = ((const cd*)a.T)[(size_t)v * H2 + t];
+    for (int t = threadIdx.x; t < D * CC; t += blockDim.x) {
+        const int k = t / CC, r = t % CC;
+        const int e = plain_slot_edge(sl, k);
+        if (e >= 0) {
+            const int side = a.edge_info[e].x == v ? 0 : 1;
+            Xs[t] = a.X[((size_t)e * 2 + side) * CC + r];
+        } else {
+            Xs[t] = cd{(r / CHI == r % CHI) ? 1.0 : 0.0, 0.0};
+        }
+    }
+    __syncthreads();
+    cd* cur = b0;
+    cd* nxt = b1;
+    for (int k = 0; k < D; ++k) {
+        const int st = ipow(CHI, D - 1 - k);
+        for (int t = threadIdx.x; t < H2; t += blockDim.x) {
+            const int jk = (t / st) % CHI, base = t - jk * st;
+            cd acc = cd{0.0, 0.0};
+            for (int q = 0; q < CHI; ++q) acc = cfma(cur[base + q * st], Xs[k * CC + q * CHI + jk], acc);
+            nxt[t] = acc;
+        }
+        __syncthreads();
+        cd* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    cd* g = (cd*)a.Gamma + (size_t)v * H2;
+    for (int t = threadIdx.x; t < H2; t += blockDim.x) g[t] = cur[t];
+}
+
+// rho_a = sum_J Gamma[i, J] conj(Gamma[i', J]) prod_k lambda_k[j_k]^2 / trace (Eqs. (partial_dens),
+// (bp_approx)); read-out +1 if rho_a[0][0] > 1/2 (Eq. (rounding_rule)).  One warp per vertex.
+template <int CHI, int D>
+__global__ void plain_marginals_kernel(const cd* Gamma, const double* lam, const int4* vslots, int n, cd* rho,
+                                       int8_t* sign, int* nan_flag) {
+    constexpr int H = PlainShape<CHI, D>::H;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int v = warp;
+    const int4 sl = vslots[v];
+    cd acc[4] = {cd{0, 0}, cd{0, 0}, cd{0, 0}, cd{0, 0}};
+    for (int r = lane; r < H; r += 32) {
+        int rem = r;
+        double wgt = 1.0;
+        for (int k = D - 1; k >= 0; --k) {
+            const double l = lam_get(lam, CHI, plain_slot_edge(sl, k), rem % CHI);
+            wgt *= l * l;
+            rem /= CHI;
+        }
+        const cd g0 = Gamma[(size_t)v * 2 * H + r], g1 = Gamma[(size_t)v * 2 * H + H + r];
+        acc[0] = cfmac(g0, wgt * g0, acc[0]);
+        acc[1] = cfmac(g1, wgt * g0, acc[1]);
+        acc[2] = cfmac(g0, wgt * g1, acc[2]);
+        acc[3] = cfmac(g1, wgt * g1, acc[3]);
+    }
+    for (int q = 0; q < 4; ++q) {
+        acc[q].x = group_sum<32>(acc[q].x, 0xffffffffu);
+        acc[q].y = group_sum<32>(acc[q].y, 0xffffffffu);
+    }
+    if (lane == 0) {
+        const double tr = acc[0].x + acc[3].x;
+        const double it = 1.0 / tr;
+        for (int q = 0; q < 4; ++q) rho[(size_t)v * 4 + q] = it * acc[q];
+        if (sign) sign[v] = (acc[0].x * it > 0.5) ? 1 : -1;
+        if (!(tr == tr) || tr == 0.0) atomicOr(nan_flag, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CHI = 16, degree 3: the simple update of a diagonal gate (App. E) in QR-reduced form, one
+// block of 512 threads per edge.  The four blocks A_{x,i}[J, j] = w_x[J] Gamma_x[i][j][J]
+// (CHI^2 x CHI) live in global scratch; each gets a Householder QR from a group of 128 threads
+// (two rows each) whose sums go through shared memory.  The core
+//   M[(i_a r), (i_b r')] = U[(i_a i_b), (i_a i_b)] sum_j R_{a,i_a}[r, j] lambda_j R_{b,i_b}[r', j]
+// (2 CHI x 2 CHI) has the same singular values as Theta; FP64 one-sided Jacobi (512 threads),
+// truncation to chi as in App. D "Truncation", and the new Gamma from the reflectors.
+// ---------------------------------------------------------------------------
+struct Gate16Args {
+    void* Gamma;
+    double* lam;
+    const int4* edge_info;
+    const int4* vslots;
+    const int* gate_edge;
+    const cd* gate_U;         // [gates][16], diagonal used
+    cd* scratch;              // [gates in launch][4][CHI][CHI^2]
+    int count;
+    double* stats;
+    int chi;
+    double svd_cut;
+};
+
+template <int CHI>
+struct Gate16Sm {
+    static constexpr int NM = 2 * CHI, NR = CHI * CHI;
+    cd M[NM * NM];
+    cd V[NM * NM];
+    cd vk[4][CHI];
+    double st[4][CHI];        // square roots of the reflector coefficients
+    double w[2][NR];
+    double lab[CHI];
+    cd ph[4];
+    double sig[NM];
+    int perm[NM];
+    cd red[4][4][CHI];        // [group][warp][value] partial sums
+    int keep, flag, nrot;
+};
+
+// sum over the 128 threads of group grp of vals[0..nv) (complex), returned to every thread;
+// red is [4 warps][nv]; named barrier 1 + grp
+template <int NV>
+__device__ __forceinline__ void group128_sum(cd (&vals)[NV], int nv, cd (*red)[16], int grp) {
+    const int lane = threadIdx.x & 31, wig = (threadIdx.x / 32) & 3;
+    for (int q = 0; q < nv; ++q) {
+        vals[q].x = group_sum<32>(vals[q].x, 0xffffffffu);
+        vals[q].y = group_sum<32>(vals[q].y, 0xffffffffu);
+        if (lane == 0) red[wig][q] = vals[q];
+    }
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
+    for (int q = 0; q < nv; ++q) vals[q] = red[0][q] + red[1][q] + red[2][q] + red[3][q];
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
+}
+
+template <int CHI>
+__global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
+    constexpr int NM = 2 * CHI, NR = CHI * CHI, H = CHI * CHI * CHI, RPT = NR / 128;
+    static_assert(NR == 2 * 128, "the 128-thread groups hold two rows each");
+    __shared__ Gate16Sm<CHI> sm;
+    const int tid = threadIdx.x;
+    const int e = c.gate_edge[blockIdx.x];
+    const int4 ei = c.edge_info[e];
+    const int vtx[2] = {ei.x, ei.y};
+    const int slot[2] = {ei.z, ei.w};
+    int oe[2][2], os[2][2];
+    for (int x = 0; x < 2; ++x) {
+        const int4 ve = c.vslots[vtx[x]];
+        const int es[3] = {ve.x, ve.y, ve.z};
+        others_of(slot[x], os[x][0], os[x][1]);
+        oe[x][0] = es[os[x][0]];
+        oe[x][1] = es[os[x][1]];
+    }
+    cd* Xg = c.scratch + (size_t)blockIdx.x * 4 * CHI * NR;   // [blk][col][row]
+    cd* Gam = (cd*)c.Gamma;
+    for (int t = tid; t < 2 * NR; t += 512) {
+        const int x = t / NR, J = t % NR;
+        sm.w[x][J] = lam_get(c.lam, CHI, oe[x][0], J / CHI) * lam_get(c.lam, CHI, oe[x][1], J % CHI);
+    }
+    for (int t = tid; t < CHI; t += 512) sm.lab[t] = c.lam[(size_t)e * CHI + t];
+    if (tid < 4) sm.ph[tid] = c.gate_U[(size_t)blockIdx.x * 16 + 5 * tid];
+    if (tid == 0) sm.nrot = 0;
+    __syncthreads();
+    for (int t = tid; t < 4 * CHI * NR; t += 512) {
+        const int blk = t / (CHI * NR), rem = t % (CHI * NR);
+        const int col = rem / NR, row = rem % NR;
+        const int x = blk >> 1, i = blk & 1;
+        const size_t off = (size_t)vtx[x] * 2 * H + (size_t)i * H + col * sstride<CHI>(slot[x]) +
+                           (row / CHI) * sstride<CHI>(os[x][0]) + (row % CHI) * sstride<CHI>(os[x][1]);
+        Xg[((size_t)blk * CHI + col) * NR + row] = sm.w[x][row] * Gam[off];
+    }
+    __syncthreads();
+    // ---- Householder QR of the four blocks, 128 threads per block, rows l and l + 128 ----
+    const int blk = tid / 128, l = tid % 128;
+    cd* Xb = Xg + (size_t)blk * CHI * NR;
+    for (int k = 0; k < CHI; ++k) {
+        cd* Xk = Xb + (size_t)k * NR;
+        const cd z = cd{0.0, 0.0};
+        cd x0 = (l >= k) ? Xk[l] : z;
+        cd x1 = Xk[l + 128];
+        cd nv[1] = {cd{norm2(x0) + norm2(x1), 0.0}};
+        group128_sum<1>(nv, 1, sm.red[blk], blk);
+        const double nrm = nr_sqrt(nv[0].x);
+        const cd xkk = Xk[k];
+        const double a2 = norm2(xkk);
+        const double ra = a2 > 0.0 ? nr_rsqrt(a2) : 0.0;
+        const double axkk = a2 * ra;
+        const cd ph = a2 > 0.0 ? cd{xkk.x * ra, xkk.y * ra} : cd{1.0, 0.0};
+        const double stau = nrm > 0.0 ? nr_rsqrt(nrm * (nrm + axkk)) : 0.0;
+        const double tau = stau * stau;
+        const cd vkk = (axkk + nrm) * ph;
+        const cd v0 = (l == k) ? vkk : x0;
+        const cd v1 = x1;
+        cd d[CHI];
+#pragma unroll
+        for (int cc = 0; cc < CHI; ++cc) {
+            d[cc] = z;
+            if (cc > k) {
+                const cd* Xc = Xb + (size_t)cc * NR;
+                d[cc] = cfmac(v0, Xc[l], cfmac(v1, Xc[l + 128], z));
+            }
+        }
+        group128_sum<CHI>(d, CHI, sm.red[blk], blk);
+#pragma unroll
+        for (int cc = 0; cc < CHI; ++cc) {
+            if (cc <= k) continue;
+            cd* Xc = Xb + (size_t)cc * NR;
+            const cd td = tau * d[cc];
+            if (l >= k) Xc[l] = Xc[l] - v0 * td;
+            Xc[l + 128] = Xc[l + 128] - v1 * td;
+        }
+        if (l == k) Xk[k] = (-nrm) * ph;
+        if (l == 0) {
+            sm.vk[blk][k] = vkk;
+            sm.st[blk][k] = stau;
+        }
+        asm volatile("bar.sync %0, 128;" ::"r"(1 + blk) : "memory");
+    }
+    __syncthreads();
+    // ---- core M (column-major NM x NM) with the diagonal gate ----
+    for (int t = tid; t < NM * NM; t += 512) {
+        const int col = t / NM, row = t % NM;
+        const int ia = row / CHI, r = row % CHI, ib = col / CHI, rp = col % CHI;
+        const cd* Ra = Xg + (size_t)ia * CHI * NR;          // block (a, ia)
+        const cd* Rb = Xg + (size_t)(2 + ib) * CHI * NR;    // block (b, ib)
+        cd acc = cd{0.0, 0.0};
+        const int j0 = r > rp ? r : rp;
+        for (int j = j0; j < CHI; ++j) acc = cfma(sm.lab[j] * Ra[(size_t)j * NR + r], Rb[(size_t)j * NR + rp], acc);
+        sm.M[t] = sm.ph[2 * ia + ib] * acc;
+    }
+    __syncthreads();
+    int nrot = 0;
+    BlockGroup grp{&sm.flag};
+    const int sweeps = jacobi_svd<NM, double, BlockGroup, true, true>(sm.M, sm.V, tid, grp, group_mask<NM>(), 1e-15, 60,
+                                                                      true, &nrot, 3e-8);
+    if (nrot) atomicAdd(&sm.nrot, nrot);
+    __syncthreads();
+    for (int cc = tid; cc < NM; cc += 512) {
+        double s2 = 0.0;
+        for (int r = 0; r < NM; ++r) s2 += norm2(sm.M[cc * NM + r]);
+        sm.sig[cc] = nr_sqrt(s2);
+    }
+    __syncthreads();
+    for (int cc = tid; cc < NM; cc += 512) sm.perm[desc_rank(sm.sig, NM, cc)] = cc;
+    __syncthreads();
+    if (tid < NM) {   // lane r holds the r-th largest singular value (NM = 32: one warp)
+        const unsigned mk = group_mask<NM>();
+        const double sv = sm.sig[sm.perm[tid]];
+        const double smax = sm.sig[sm.perm[0]];
+        const int cnt = __popc(__ballot_sync(mk, sv > c.svd_cut * smax));
+        int keep = cnt < c.chi ? cnt : c.chi;
+        if (keep < 1) keep = 1;
+        const double s2 = sv * sv;
+        const double kept = group_sum<NM>(tid < keep ? s2 : 0.0, mk);
+        const double drop = group_sum<NM>(tid < keep ? 0.0 : s2, mk);
+        const double inv = kept > 0.0 ? nr_rsqrt(kept) : 0.0;
+        if (tid < CHI) c.lam[(size_t)e * CHI + tid] = (tid < keep) ? sv * inv : 0.0;
+        if (tid == 0) {
+            const double tot = kept + drop;
+            const double disc = tot > 0.0 ? drop * nr_rcp(tot) : 0.0;
+            atomicAdd(&c.stats[0], disc);
+            atomicAdd(&c.stats[1], 2.0 * log1p(-disc));   // Eq. (gate_fidelity)
+            atomicAdd(&c.stats[2], (double)sweeps * (NM - 1) * (NM / 2));
+            atomicAdd(&c.stats[3], (double)sm.nrot);
+            sm.keep = keep;
+        }
+    }
+    __syncthreads();
+    const int keep = sm.keep;
+    // ---- new Gamma: the reflectors of each block applied to U (side a) / V^* (side b) ----
+    const int x = blk >> 1, i = blk & 1;
+    cd E0[CHI], E1[CHI];
+#pragma unroll
+    for (int cc = 0; cc < CHI; ++cc) {
+        E0[cc] = cd{0.0, 0.0};
+        E1[cc] = cd{0.0, 0.0};
+        if (l < CHI && cc < keep) {
+            const int pc = sm.perm[cc];
+            const int row = i * CHI + l;
+            E0[cc] = (x == 0) ? nr_rcp(sm.sig[pc]) * sm.M[pc * NM + row] : conj(sm.V[pc * NM + row]);
+        }
+    }
+    for (int k = CHI - 1; k >= 0; --k) {
+        const double st = sm.st[blk][k];
+        const cd* Xk = Xb + (size_t)k * NR;
+        const cd v0 = st * ((l == k) ? sm.vk[blk][k] : ((l > k) ? Xk[l] : cd{0.0, 0.0}));
+        const cd v1 = st * Xk[l + 128];
+        cd d[CHI];
+#pragma unroll
+        for (int cc = 0; cc < CHI; ++cc) d[cc] = cfmac(v0, E0[cc], cfmac(v1, E1[cc], cd{0.0, 0.0}));
+        group128_sum<CHI>(d, CHI, sm.red[blk], blk);
+#pragma unroll
+        for (int cc = 0; cc < CHI; ++cc) {
+            E0[cc] = E0[cc] - v0 * d[cc];
+            E1[cc] = E1[cc] - v1 * d[cc];
+        }
+    }
+    const double w0 = sm.w[x][l], w1 = sm.w[x][l + 128];
+    const double iw0 = w0 > 0.0 ? nr_rcp(w0) : 0.0, iw1 = w1 > 0.0 ? nr_rcp(w1) : 0.0;
+    const size_t base = (size_t)vtx[x] * 2 * H + (size_t)i * H;
+    const size_t o0 = (l / CHI) * sstride<CHI>(os[x][0]) + (l % CHI) * sstride<CHI>(os[x][1]);
+    const size_t o1 = ((l + 128) / CHI) * sstride<CHI>(os[x][0]) + ((l + 128) % CHI) * sstride<CHI>(os[x][1]);
+#pragma unroll
+    for (int cc = 0; cc < CHI; ++cc) {
+        Gam[base + cc * sstride<CHI>(slot[x]) + o0] = iw0 * E0[cc];
+        Gam[base + cc * sstride<CHI>(slot[x]) + o1] = iw1 * E1[cc];
+    }
+    (void)RPT;
+}
+
+}  // namespace gtqa

@@ -71,6 +71,10 @@ def test_invalid_graphs_rejected_on_host(G):
     star4 = star[:4]
     assert _rc(G, 5, star4, np.ones(4), np.zeros(5), 4, precision=G.GTQA_MIXED)[0] == G.GTQA_ERR_UNSUPPORTED
     assert _rc(G, 5, star4, np.ones(4), np.zeros(5), 8)[0] == G.GTQA_ERR_UNSUPPORTED
+    # chi 9..16 (storage 16) needs FP64 and degree <= 3
+    assert _rc(G, 4, [[0, 1]], [1.0], h, 16, precision=G.GTQA_MIXED)[0] == G.GTQA_ERR_UNSUPPORTED
+    assert _rc(G, 5, star4, np.ones(4), np.zeros(5), 12)[0] == G.GTQA_ERR_UNSUPPORTED
+    assert _rc(G, 4, [[0, 1]], [1.0], h, 17)[0] == G.GTQA_ERR_UNSUPPORTED
     # out of range vertex
     assert _rc(G, 4, [[0, 7]], [1.0], h, 4)[0] == G.GTQA_ERR_INVALID_ARG
     # colouring that is not a matching
