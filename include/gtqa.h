@@ -60,6 +60,10 @@ extern "C" {
 #define GTQA_MIXED 1  /* complex64 tensors and BP contractions; FP64 QR/SVD, gauge roots, normalisation.
                          Messages are held as m0 + delta: m0 = diag(lambda)/sum(lambda) (exact),
                          delta in complex64; get/set_state convert to and from complex128. */
+#define GTQA_C64 2    /* complex64 with every step in FP32, including the QR/SVD, gauge roots and
+                       * normalisation (a reference point for the precision split; plain kernels,
+                       * one instance, degree 3 with chi <= 8 or degree 4 with chi <= 4; default
+                       * cut-offs 1e-7 on singular values and 1e-6 on message eigenvalues) */
 
 /* flags of gtqa_bp_sweep */
 #define GTQA_BP_WARM_START 1u  /* start from m_{a->b} = diag(lambda_ab)/sum(lambda_ab) (Eq. reconstructed_messages) */

@@ -35,11 +35,19 @@ namespace gtqa {
 
 struct ModeFP64 {
     using TS = double;   // storage of Gamma, T, messages
+    using RC = double;   // arithmetic of the SVDs, QRs and gauge roots
     static constexpr bool mixed = false;
 };
 struct ModeMixed {
     using TS = float;
+    using RC = double;
     static constexpr bool mixed = true;
+};
+// every step in complex64 / FP32 (a reference point for the precision split; plain kernels only)
+struct ModeC64 {
+    using TS = float;
+    using RC = float;
+    static constexpr bool mixed = false;
 };
 
 enum : unsigned { PH_GATES = 1u, PH_BP = 2u, PH_WARM = 4u, PH_REGAUGE = 8u };

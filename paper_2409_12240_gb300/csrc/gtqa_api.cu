@@ -145,7 +145,9 @@ int storage_chi(int chi) {
 }
 
 bool mixed(const gtqa_state* s) { return s->precision == GTQA_MIXED; }
-size_t elem_bytes(const gtqa_state* s) { return mixed(s) ? sizeof(cf) : sizeof(cd); }
+bool f32(const gtqa_state* s) { return s->precision == GTQA_C64; }
+bool f32store(const gtqa_state* s) { return s->precision != GTQA_FP64; }
+size_t elem_bytes(const gtqa_state* s) { return f32store(s) ? sizeof(cf) : sizeof(cd); }
 size_t gamma_elems(const gtqa_state* s) {
     return (size_t)s->n * 2 * s->CHI * s->CHI * s->CHI * (s->D == 4 ? s->CHI : 1);
 }
@@ -532,7 +534,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
     gtqa_options o;
     gtqa_options_init(&o);
     if (opt) o = *opt;
-    if (o.precision != GTQA_FP64 && o.precision != GTQA_MIXED) return GTQA_ERR_UNSUPPORTED;
+    if (o.precision != GTQA_FP64 && o.precision != GTQA_MIXED && o.precision != GTQA_C64) return GTQA_ERR_UNSUPPORTED;
     if (o.reserved0 != 0) return GTQA_ERR_INVALID_ARG;
     long long N = 0, Mtot = 0;
     for (int b = 0; b < B; ++b) {
@@ -603,8 +605,9 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
     int Dmax = 0;
     for (long long v = 0; v < N; ++v) Dmax = std::max(Dmax, deg[v]);
     const int Dst = Dmax == 4 ? 4 : 3;
-    const bool plain = Dst == 4 || storage_chi(chi) == 16;
-    if (plain && (B != 1 || o.precision != GTQA_FP64 || !plain_supported(storage_chi(chi), Dst)))
+    const bool c64 = o.precision == GTQA_C64;
+    const bool plain = Dst == 4 || storage_chi(chi) == 16 || c64;
+    if (plain && (B != 1 || o.precision == GTQA_MIXED || !plain_supported(storage_chi(chi), Dst, c64)))
         return GTQA_ERR_UNSUPPORTED;
     gtqa_state* s = new (std::nothrow) gtqa_state();
     if (!s) return GTQA_ERR_OOM;
@@ -617,8 +620,9 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
     s->CHI = storage_chi(chi);
     s->precision = o.precision;
     s->stream = (cudaStream_t)o.cuda_stream;
-    s->svd_cutoff = o.svd_cutoff > 0 ? o.svd_cutoff : 1e-14;
-    s->eig_cutoff = o.eig_cutoff > 0 ? o.eig_cutoff : 1e-13;
+    // relative cut-offs: FP64 defaults, FP32-sized ones in the complex64 mode
+    s->svd_cutoff = o.svd_cutoff > 0 ? o.svd_cutoff : (c64 ? 1e-7 : 1e-14);
+    s->eig_cutoff = o.eig_cutoff > 0 ? o.eig_cutoff : (c64 ? 1e-6 : 1e-13);
     s->ncol = ncol;
     s->h_inst_m = minst;
     s->h_edges = ge;
@@ -729,7 +733,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
     for (long long a = 0; a < N; ++a) {
         for (int i = 0; i < 2; ++i) {
             const size_t idx = a * 2 * H + i * H;
-            if (mixed(s)) reinterpret_cast<cf*>(g0.data())[idx] = cf{(float)M_SQRT1_2, 0.f};
+            if (f32store(s)) reinterpret_cast<cf*>(g0.data())[idx] = cf{(float)M_SQRT1_2, 0.f};
             else reinterpret_cast<cd*>(g0.data())[idx] = cd{M_SQRT1_2, 0.0};
         }
     }
@@ -773,10 +777,18 @@ int read_messages(gtqa_state* s, int cur, std::vector<cd>& out) {
     const size_t mel = msg_elems(s);
     const int CC = s->CHI * s->CHI;
     out.assign(mel, cd{0.0, 0.0});
-    if (!mixed(s)) {
+    if (!f32store(s)) {
         if (!cuda_ok(s, cudaMemcpyAsync(out.data(), s->msg[cur], mel * sizeof(cd), cudaMemcpyDeviceToHost, s->stream)))
             return GTQA_ERR_CUDA;
         return cuda_ok(s, cudaStreamSynchronize(s->stream)) ? GTQA_OK : GTQA_ERR_CUDA;
+    }
+    if (f32(s)) {
+        std::vector<cf> d(mel);
+        if (!cuda_ok(s, cudaMemcpyAsync(d.data(), s->msg[cur], mel * sizeof(cf), cudaMemcpyDeviceToHost, s->stream)) ||
+            !cuda_ok(s, cudaStreamSynchronize(s->stream)))
+            return GTQA_ERR_CUDA;
+        for (size_t i = 0; i < mel; ++i) out[i] = cd{(double)d[i].x, (double)d[i].y};
+        return GTQA_OK;
     }
     std::vector<cf> d(mel);
     std::vector<double> L((size_t)s->m * s->CHI);
@@ -908,7 +920,7 @@ int d4_mixing(gtqa_state* s, double t) {
     if ((rc = grow_pair(s, &s->sq_vertex, &s->sq_W, 4, s->sq_cap, (size_t)s->n))) return rc;
     if (!cuda_ok(s, cudaMemcpyAsync(s->sq_W, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, s->stream)))
         return GTQA_ERR_CUDA;
-    if (plain_single_gates_launch(s->CHI, s->D, s->Gamma, s->allv, s->sq_W, s->n, s->stream) != cudaSuccess)
+    if (plain_single_gates_launch(s->CHI, s->D, f32(s), s->Gamma, s->allv, s->sq_W, s->n, s->stream) != cudaSuccess)
         return d4_fail(s);
     s->launches += 1;
     return GTQA_OK;
@@ -938,7 +950,7 @@ int d4_interaction(gtqa_state* s, double tZ) {
         return GTQA_ERR_CUDA;
     for (int c = 0; c < s->ncol; ++c) {
         cudaError_t e;
-        if (s->CHI == 16) {
+        if (s->CHI == 16 && !f32(s)) {
             Gate16Args g;
             g.Gamma = s->Gamma;
             g.lam = s->lam;
@@ -964,7 +976,7 @@ int d4_interaction(gtqa_state* s, double tZ) {
             g.stats = s->stats;
             g.chi = s->chi;
             g.svd_cut = s->svd_cutoff;
-            e = plain_general_gates_launch(s->CHI, s->D, g, s->stream);
+            e = plain_general_gates_launch(s->CHI, s->D, f32(s), g, s->stream);
         }
         if (e != cudaSuccess) return d4_fail(s);
         s->launches += 1;
@@ -981,7 +993,7 @@ int d4_trotter(gtqa_state* s, double tZ, double tXpre, double tXpost) {
 }
 
 int d4_regauge(gtqa_state* s) {
-    if (plain_regauge_launch(s->CHI, s->D, d4_args(s, s->cur4), (const cd*)s->msg[s->cur4], s->eig_cutoff,
+    if (plain_regauge_launch(s->CHI, s->D, f32(s), d4_args(s, s->cur4), s->msg[s->cur4], s->eig_cutoff,
                              s->svd_cutoff, s->stream) != cudaSuccess)
         return d4_fail(s);
     s->launches += 2;
@@ -995,7 +1007,7 @@ int d4_bp(gtqa_state* s, double tol, int max_iter, uint32_t flags, int32_t* iter
     PlainArgs a = d4_args(s, cur);
     a.warm = (flags & GTQA_BP_WARM_START) ? 1 : 0;
     a.msg_nxt = s->msg[cur];   // the init kernel writes the warm start where the first sweep reads
-    if (s->n > 0 && plain_bp_init_launch(s->CHI, s->D, a, s->stream) != cudaSuccess) return d4_fail(s);
+    if (s->n > 0 && plain_bp_init_launch(s->CHI, s->D, f32(s), a, s->stream) != cudaSuccess) return d4_fail(s);
     s->launches += 1;
     int it = 0;
     double dist = 0.0;
@@ -1003,7 +1015,7 @@ int d4_bp(gtqa_state* s, double tol, int max_iter, uint32_t flags, int32_t* iter
     for (; it < max_iter;) {
         if (!cuda_ok(s, cudaMemsetAsync(s->acc, 0, sizeof(double), s->stream))) return GTQA_ERR_CUDA;
         PlainArgs w = d4_args(s, cur);
-        if (plain_bp_sweep_launch(s->CHI, s->D, w, s->stream) != cudaSuccess) return d4_fail(s);
+        if (plain_bp_sweep_launch(s->CHI, s->D, f32(s), w, s->stream) != cudaSuccess) return d4_fail(s);
         s->launches += 2;
         double acc = 0.0;
         if (!cuda_ok(s, cudaMemcpyAsync(&acc, s->acc, sizeof(double), cudaMemcpyDeviceToHost, s->stream)) ||
@@ -1369,7 +1381,7 @@ int gtqa_apply_gates(gtqa_state* s, int32_t k, const int32_t* edge, const double
         a.stats = s->stats;
         a.chi = s->chi;
         a.svd_cut = s->svd_cutoff;
-        const cudaError_t e = s->plain    ? plain_general_gates_launch(s->CHI, s->D, a, s->stream)
+        const cudaError_t e = s->plain    ? plain_general_gates_launch(s->CHI, s->D, f32(s), a, s->stream)
                               : mixed(s) ? general_gates_launch_mixed(s->CHI, a, s->stream)
                                          : general_gates_launch_fp64(s->CHI, a, s->stream);
         if (e != cudaSuccess) {
@@ -1424,8 +1436,8 @@ int gtqa_apply_single_qubit_gates(gtqa_state* s, int32_t k, const int32_t* verte
     if (!cuda_ok(s, cudaMemcpyAsync(s->sq_vertex, vs.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s->stream)) ||
         !cuda_ok(s, cudaMemcpyAsync(s->sq_W, Wd.data(), sizeof(double) * Wd.size(), cudaMemcpyHostToDevice, s->stream)))
         return GTQA_ERR_CUDA;
-    const cudaError_t e = s->plain ? plain_single_gates_launch(s->CHI, s->D, s->Gamma, s->sq_vertex, s->sq_W, cnt,
-                                                               s->stream)
+    const cudaError_t e = s->plain ? plain_single_gates_launch(s->CHI, s->D, f32(s), s->Gamma, s->sq_vertex, s->sq_W,
+                                                               cnt, s->stream)
                           : mixed(s) ? single_gates_launch_mixed(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream)
                                      : single_gates_launch_fp64(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream);
     if (e != cudaSuccess) {
@@ -1731,7 +1743,7 @@ int gtqa_marginals(gtqa_state* s, double* rho_out, int8_t* sign_out) {
     {
         ProfScope ps(s, GTQA_K_MARGINALS, s->n);
         const cudaError_t e =
-            s->plain ? plain_marginals_launch(s->CHI, s->D, (const cd*)s->Gamma, s->lam, s->vslots4, s->n, s->rho,
+            s->plain ? plain_marginals_launch(s->CHI, s->D, f32(s), s->Gamma, s->lam, s->vslots4, s->n, s->rho,
                                               s->sign, s->flags, s->stream)
             : mixed(s) ? marginals_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho, s->sign,
                                                 s->flags, s->stream)
@@ -1787,7 +1799,7 @@ int gtqa_get_state(gtqa_state* s, double* gamma_out, double* lambda_out, double*
     const cudaStream_t st = s->stream;
     const size_t gel = gamma_elems(s), mel = msg_elems(s);
     if (gamma_out) {
-        if (!mixed(s)) {
+        if (!f32store(s)) {
             if (!cuda_ok(s, cudaMemcpyAsync(gamma_out, s->Gamma, gel * sizeof(cd), cudaMemcpyDefault, st)))
                 return GTQA_ERR_CUDA;
         } else {
@@ -1833,9 +1845,17 @@ int gtqa_set_state(gtqa_state* s, const double* gamma, const double* lambda, con
         return GTQA_ERR_CUDA;
     for (double x : L)
         if (!(x >= 0.0) || !std::isfinite(x)) return GTQA_ERR_INVALID_ARG;
-    if (!mixed(s)) {
+    if (!f32store(s)) {
         if (!cuda_ok(s, cudaMemcpyAsync(s->Gamma, g.data(), gel * sizeof(cd), cudaMemcpyHostToDevice, st)) ||
             !cuda_ok(s, cudaMemcpyAsync(s->msg[ctl.cur], mm.data(), mel * sizeof(cd), cudaMemcpyHostToDevice, st)))
+            return GTQA_ERR_CUDA;
+    } else if (f32(s)) {
+        std::vector<cf> gf(gel), mf(mel);
+        for (size_t i = 0; i < gel; ++i) gf[i] = cf{(float)g[i].x, (float)g[i].y};
+        for (size_t i = 0; i < mel; ++i) mf[i] = cf{(float)mm[i].x, (float)mm[i].y};
+        if (!cuda_ok(s, cudaMemcpyAsync(s->Gamma, gf.data(), gel * sizeof(cf), cudaMemcpyHostToDevice, st)) ||
+            !cuda_ok(s, cudaMemcpyAsync(s->msg[ctl.cur], mf.data(), mel * sizeof(cf), cudaMemcpyHostToDevice, st)) ||
+            !cuda_ok(s, cudaStreamSynchronize(st)))
             return GTQA_ERR_CUDA;
     } else {
         std::vector<cf> gf(gel), df(mel);

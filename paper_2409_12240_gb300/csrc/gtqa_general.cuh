@@ -45,18 +45,18 @@ struct GenShape {
     static constexpr int TEAM = NM * NM / 2; // Jacobi layout: NM/2 pairs x NM rows
 };
 
-template <int CHI, int D = 3>
+template <int CHI, int D = 3, typename R = double>
 struct GenSm {
     using S = GenShape<CHI, D>;
-    cd X[2][S::NC][S::NR];   // [side][column (i, j)][row J]; reflectors after the QR
-    cd vk[2][S::NC];
-    double tau[2][S::NC];
-    cd M[S::NM * S::NM];
-    cd V[S::NM * S::NM];
-    cd U[16];
-    double w[2][S::NR];
-    double lab[CHI];
-    double sig[S::NM];
+    C<R> X[2][S::NC][S::NR];   // [side][column (i, j)][row J]; reflectors after the QR
+    C<R> vk[2][S::NC];
+    R tau[2][S::NC];
+    C<R> M[S::NM * S::NM];
+    C<R> V[S::NM * S::NM];
+    C<R> U[16];
+    R w[2][S::NR];
+    R lab[CHI];
+    R sig[S::NM];
     int perm[S::NM];
     int keep;
     int flag;
@@ -66,11 +66,14 @@ struct GenSm {
 template <int CHI, int D, class Mode>
 __global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kernel(GenArgs c) {
     using TS = typename Mode::TS;
+    using R = typename Mode::RC;   // FP64, or FP32 in the complex64 mode
+    using CR = C<R>;
+    constexpr bool R64 = sizeof(R) == 8;
     using S = GenShape<CHI, D>;
     constexpr int NR = S::NR, NC = S::NC, NM = S::NM, G = S::G, TEAM = S::TEAM, HV = ipow(CHI, D);
     static_assert(G <= 32, "a Householder group must fit in one warp");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GenSm<CHI, D>& sm = *reinterpret_cast<GenSm<CHI, D>*>(smem_raw);
+    GenSm<CHI, D, R>& sm = *reinterpret_cast<GenSm<CHI, D, R>*>(smem_raw);
     const int g = threadIdx.x;
     if (blockIdx.x >= (unsigned)c.count) return;   // uniform per block
     auto bar = [&]() {
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kerne
     for (int t = g; t < 2 * NR; t += TEAM) {
         const int x = t / NR;
         int J = t % NR;
-        double w = 1.0;
+        R w = 1.0;
         for (int m = D - 2; m >= 0; --m) {
             w *= lam_get(c.lam, CHI, oe[x][m], J % CHI);
             J /= CHI;
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kerne
         sm.w[x][t % NR] = w;
     }
     for (int t = g; t < CHI; t += TEAM) sm.lab[t] = __ldcg(c.lam + (size_t)e * CHI + t);
-    for (int t = g; t < 16; t += TEAM) sm.U[t] = c.gate_U[(size_t)blockIdx.x * 16 + t];
+    for (int t = g; t < 16; t += TEAM) sm.U[t] = ccast<R>(c.gate_U[(size_t)blockIdx.x * 16 + t]);
     bar();
     for (int t = g; t < 2 * NC * NR; t += TEAM) {
         const int x = t / (NC * NR), rem = t % (NC * NR);
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kerne
         const int i = col / CHI, j = col % CHI;
         const size_t off = (size_t)vtx[x] * (2 * HV) + (size_t)i * HV + (size_t)j * ipow(CHI, D - 1 - slot[x]) +
                            joff(x, row);
-        sm.X[x][col][row] = sm.w[x][row] * ccast<double>(ldcg(Gam + off));
+        sm.X[x][col][row] = sm.w[x][row] * ccast<R>(ldcg(Gam + off));
     }
     bar();
 
@@ -133,28 +136,28 @@ __global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kerne
         const int x = g / G;
         const unsigned gm = group_mask<G>();
         for (int k = 0; k < NC; ++k) {
-            cd* Xk = sm.X[x][k];
-            const cd z = cd{0.0, 0.0};
-            const cd x0 = (r0 >= k) ? Xk[r0] : z;
-            const cd x1 = (r1 >= k) ? Xk[r1] : z;
-            const double nrm2 = group_sum<G>(norm2(x0) + norm2(x1), gm);
-            const cd xkk = Xk[k];
-            const double nrm = nr_sqrt(nrm2);
-            const double a2 = norm2(xkk);
-            const double ra = a2 > 0.0 ? nr_rsqrt(a2) : 0.0;
-            const double axkk = a2 * ra;
-            const cd ph = a2 > 0.0 ? cd{xkk.x * ra, xkk.y * ra} : cd{1.0, 0.0};
-            const double tau = nrm > 0.0 ? nr_rcp(nrm * (nrm + axkk)) : 0.0;
-            const cd vkk = (axkk + nrm) * ph;
-            const cd v0 = (r0 == k) ? vkk : x0;
-            const cd v1 = (r1 == k) ? vkk : x1;
+            CR* Xk = sm.X[x][k];
+            const CR z = CR{(R)0, (R)0};
+            const CR x0 = (r0 >= k) ? Xk[r0] : z;
+            const CR x1 = (r1 >= k) ? Xk[r1] : z;
+            const R nrm2 = group_sum<G>(norm2(x0) + norm2(x1), gm);
+            const CR xkk = Xk[k];
+            const R nrm = nr_sqrt(nrm2);
+            const R a2 = norm2(xkk);
+            const R ra = a2 > 0.0 ? nr_rsqrt(a2) : 0.0;
+            const R axkk = a2 * ra;
+            const CR ph = a2 > 0.0 ? CR{xkk.x * ra, xkk.y * ra} : CR{(R)1, (R)0};
+            const R tau = nrm > 0.0 ? nr_rcp(nrm * (nrm + axkk)) : 0.0;
+            const CR vkk = (axkk + nrm) * ph;
+            const CR v0 = (r0 == k) ? vkk : x0;
+            const CR v1 = (r1 == k) ? vkk : x1;
             for (int cc = k + 1; cc < NC; ++cc) {
-                cd* Xc = sm.X[x][cc];
-                const cd y0 = Xc[r0], y1 = Xc[r1];
-                cd d = cfmac(v0, y0, cfmac(v1, y1, z));
+                CR* Xc = sm.X[x][cc];
+                const CR y0 = Xc[r0], y1 = Xc[r1];
+                CR d = cfmac(v0, y0, cfmac(v1, y1, z));
                 d.x = group_sum<G>(d.x, gm);
                 d.y = group_sum<G>(d.y, gm);
-                const cd td = tau * d;
+                const CR td = tau * d;
                 if (r0 >= k) Xc[r0] = y0 - v0 * td;
                 if (r1 >= k) Xc[r1] = y1 - v1 * td;
             }
@@ -173,12 +176,12 @@ __global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kerne
     // ---- core matrix M (column-major NM x NM): the gate on the two R factors ----
     for (int t = g; t < NC * NC; t += TEAM) {
         const int r = t % NC, rp = t / NC;
-        cd B[2][2];
+        CR B[2][2];
 #pragma unroll
         for (int ia = 0; ia < 2; ++ia)
 #pragma unroll
             for (int ib = 0; ib < 2; ++ib) {
-                cd acc = cd{0.0, 0.0};
+                CR acc = CR{(R)0, (R)0};
                 for (int j = 0; j < CHI; ++j) {
                     const int ca = ia * CHI + j, cb = ib * CHI + j;
                     if (r <= ca && rp <= cb) acc = cfma(sm.lab[j] * sm.X[0][ca][r], sm.X[1][cb][rp], acc);
@@ -189,8 +192,8 @@ __global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kerne
         for (int ia = 0; ia < 2; ++ia)
 #pragma unroll
             for (int ib = 0; ib < 2; ++ib) {
-                const cd* u = sm.U + (2 * ia + ib) * 4;
-                cd acc = u[0] * B[0][0];
+                const CR* u = sm.U + (2 * ia + ib) * 4;
+                CR acc = u[0] * B[0][0];
                 acc = cfma(u[1], B[0][1], acc);
                 acc = cfma(u[2], B[1][0], acc);
                 acc = cfma(u[3], B[1][1], acc);
@@ -204,17 +207,17 @@ __global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kerne
     int nrot = 0, sweeps;
     if constexpr (TEAM <= 32) {
         WarpGroup grp{group_mask<TEAM>()};
-        sweeps = jacobi_svd<NM, double, WarpGroup, true, true>(sm.M, sm.V, g, grp, group_mask<NM>(), 1e-15, 60, true,
-                                                               &nrot, 3e-8);
+        sweeps = jacobi_svd<NM, R, WarpGroup, true, R64>(sm.M, sm.V, g, grp, group_mask<NM>(), (R)(R64 ? 1e-15 : 1e-6), 60, true,
+                                                               &nrot, (R)(R64 ? 3e-8 : 1e-3));
     } else {
         BlockGroup grp{&sm.flag};
-        sweeps = jacobi_svd<NM, double, BlockGroup, true, true>(sm.M, sm.V, g, grp, group_mask<NM>(), 1e-15, 60, true,
-                                                                &nrot, 3e-8);
+        sweeps = jacobi_svd<NM, R, BlockGroup, true, R64>(sm.M, sm.V, g, grp, group_mask<NM>(), (R)(R64 ? 1e-15 : 1e-6), 60, true,
+                                                                &nrot, (R)(R64 ? 3e-8 : 1e-3));
     }
     if (nrot) atomicAdd(&sm.nrot, nrot);
     bar();
     for (int cc = g; cc < NM; cc += TEAM) {
-        double s2 = 0.0;
+        R s2 = 0.0;
         for (int r = 0; r < NM; ++r) s2 += norm2(sm.M[cc * NM + r]);
         sm.sig[cc] = nr_sqrt(s2);
     }
@@ -222,24 +225,24 @@ __global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kerne
     for (int cc = g; cc < NM; cc += TEAM) sm.perm[desc_rank(sm.sig, NM, cc)] = cc;
     bar();
     if (g == 0) {
-        const double smax = sm.sig[sm.perm[0]];
+        const R smax = sm.sig[sm.perm[0]];
         int cnt = 0;
-        double tot = 0.0;
+        R tot = 0.0;
         for (int r = 0; r < NM; ++r) {
-            const double s = sm.sig[sm.perm[r]];
+            const R s = sm.sig[sm.perm[r]];
             tot += s * s;
             cnt += (s > c.svd_cut * smax) ? 1 : 0;
         }
         int keep = cnt < c.chi ? cnt : c.chi;
         if (keep < 1) keep = 1;
-        double kept = 0.0, drop = 0.0;
+        R kept = 0.0, drop = 0.0;
         for (int r = 0; r < NM; ++r) {
-            const double s = sm.sig[sm.perm[r]];
+            const R s = sm.sig[sm.perm[r]];
             if (r < keep) kept += s * s; else drop += s * s;
         }
-        const double inv = kept > 0.0 ? nr_rsqrt(kept) : 0.0;
+        const R inv = kept > 0.0 ? nr_rsqrt(kept) : 0.0;
         for (int r = 0; r < CHI; ++r) c.lam[(size_t)e * CHI + r] = (r < keep) ? sm.sig[sm.perm[r]] * inv : 0.0;
-        const double disc = tot > 0.0 ? drop * nr_rcp(tot) : 0.0;
+        const R disc = tot > 0.0 ? drop * nr_rcp(tot) : 0.0;
         atomicAdd(&c.stats[0], disc);
         atomicAdd(&c.stats[1], 2.0 * log1p(-disc));   // Eq. (gate_fidelity)
         atomicAdd(&c.stats[2], (double)sweeps * (NM - 1) * (NM / 2));
@@ -253,14 +256,14 @@ __global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kerne
     if (g < 4 * G) {
         const int blk = g / G, x = blk >> 1, i = blk & 1;
         const unsigned gm = group_mask<G>();
-        cd E0[CHI], E1[CHI];
+        CR E0[CHI], E1[CHI];
 #pragma unroll
         for (int cc = 0; cc < CHI; ++cc) {
-            E0[cc] = cd{0.0, 0.0};
-            E1[cc] = cd{0.0, 0.0};
+            E0[cc] = CR{(R)0, (R)0};
+            E1[cc] = CR{(R)0, (R)0};
             if (cc < keep) {
                 const int pc = sm.perm[cc];
-                const double is = sm.sig[pc] > 0.0 ? nr_rcp(sm.sig[pc]) : 0.0;
+                const R is = sm.sig[pc] > 0.0 ? nr_rcp(sm.sig[pc]) : 0.0;
                 if (r0 < NC) {
                     const int row = i * NC + r0;
                     E0[cc] = (x == 0) ? is * sm.M[pc * NM + row] : conj(sm.V[pc * NM + row]);
@@ -273,20 +276,20 @@ __global__ void __launch_bounds__(GenShape<CHI, D>::TEAM, 1) general_gates_kerne
         }
         // H_k = I - tau v v^H applied as I - u u^H with u = sqrt(tau) v, last reflector first
         for (int k = NC - 1; k >= 0; --k) {
-            const double st = nr_sqrt(sm.tau[x][k]);
-            const cd v0 = st * ((r0 == k) ? sm.vk[x][k] : ((r0 > k) ? sm.X[x][k][r0] : cd{0.0, 0.0}));
-            const cd v1 = st * ((r1 == k) ? sm.vk[x][k] : ((r1 > k) ? sm.X[x][k][r1] : cd{0.0, 0.0}));
+            const R st = nr_sqrt(sm.tau[x][k]);
+            const CR v0 = st * ((r0 == k) ? sm.vk[x][k] : ((r0 > k) ? sm.X[x][k][r0] : CR{(R)0, (R)0}));
+            const CR v1 = st * ((r1 == k) ? sm.vk[x][k] : ((r1 > k) ? sm.X[x][k][r1] : CR{(R)0, (R)0}));
 #pragma unroll
             for (int cc = 0; cc < CHI; ++cc) {
-                cd d = cfmac(v0, E0[cc], cfmac(v1, E1[cc], cd{0.0, 0.0}));
+                CR d = cfmac(v0, E0[cc], cfmac(v1, E1[cc], CR{(R)0, (R)0}));
                 d.x = group_sum<G>(d.x, gm);
                 d.y = group_sum<G>(d.y, gm);
                 E0[cc] = E0[cc] - v0 * d;
                 E1[cc] = E1[cc] - v1 * d;
             }
         }
-        const double w0 = sm.w[x][r0], w1 = sm.w[x][r1];
-        const double iw0 = w0 > 0.0 ? nr_rcp(w0) : 0.0, iw1 = w1 > 0.0 ? nr_rcp(w1) : 0.0;
+        const R w0 = sm.w[x][r0], w1 = sm.w[x][r1];
+        const R iw0 = w0 > 0.0 ? nr_rcp(w0) : 0.0, iw1 = w1 > 0.0 ? nr_rcp(w1) : 0.0;
         const size_t base = (size_t)vtx[x] * (2 * HV) + (size_t)i * HV;
         const size_t o0 = joff(x, r0), o1 = joff(x, r1);
         const size_t ss = ipow(CHI, D - 1 - slot[x]);
@@ -317,7 +320,7 @@ __global__ void single_gates_kernel(void* Gamma, const int* vertex, const cd* W,
 
 template <int CHI, int D, class Mode>
 cudaError_t general_gates_launch_t(const GenArgs& a, cudaStream_t st) {
-    constexpr size_t smem = sizeof(GenSm<CHI, D>);
+    constexpr size_t smem = sizeof(GenSm<CHI, D, typename Mode::RC>);
     static bool attr_set = false;   // the attribute is per function; setting it twice is harmless
     if (!attr_set) {
         const cudaError_t e = raise_smem_limit(general_gates_kernel<CHI, D, Mode>, smem);

@@ -1,7 +1,9 @@
 // The plain path: graph tensor networks whose vertex tensors are too large or have too many
-// bonds for the persistent kernels.  Two shapes are built: degree 4 with CHI <= 4 (the random
-// 4-regular graphs of Sec. V) and degree 3 with CHI = 16 (the largest bond dimension of the
-// chi sweep).  Complex128 throughout (the FP64 precision mode), one instance.
+// bonds for the persistent kernels, or that run every step in FP32.  Shapes built: degree 4
+// with CHI <= 4 (the random 4-regular graphs of Sec. V) and degree 3 with CHI = 16 (the largest
+// bond dimension of the chi sweep), in complex128 (the FP64 precision mode); degree 3 with
+// CHI <= 8 and degree 4 with CHI <= 4 in complex64 with every step in FP32 (the complex64 mode,
+// R = float).  One instance.
 //
 // Layout: Gamma and T are [n][2][CHI]^D (slot k = k-th incident edge in ascending id, stride
 // CHI^(D-1-k); phantom slots of vertices with fewer edges have dimension 1 with lambda = e_0);
@@ -30,9 +32,9 @@ struct PlainArgs {
     double* lam;
     const void* msg_cur;      // incoming and previous outgoing messages
     void* msg_nxt;            // new outgoing messages
-    cd* X;                    // regauge transforms [m][2][CHI^2]
-    cd* dm;                   // [2m][CHI^2]: new - old of every outgoing message of a sweep
-    cd* scratch;              // per-block tensor buffers when shared memory is too small
+    void* X;                  // regauge transforms [m][2][CHI^2]
+    void* dm;                 // [2m][CHI^2]: new - old of every outgoing message of a sweep
+    void* scratch;            // per-block tensor buffers when shared memory is too small
     const int4* vslots;       // slots per vertex (x, y, z, w; -1 phantom)
     const int4* edge_info;    // (u, v, slot at u, slot at v)
     int n, m;
@@ -40,12 +42,12 @@ struct PlainArgs {
     int warm;
 };
 
-template <int CHI, int D>
+template <int CHI, int D, typename R = double>
 struct PlainShape {
     static constexpr int H = ipow(CHI, D), H2 = 2 * H, CC = CHI * CHI;
     static constexpr int NT = 16 * CC < 1024 ? 16 * CC : 1024;    // threads of the sweep kernel
     static constexpr int TPO = NT / CC;                           // threads per message entry
-    static constexpr bool SMEM = 3 * H2 * 16 <= 48 * 1024;        // tensor buffers in shared memory
+    static constexpr bool SMEM = 3 * H2 * (int)sizeof(C<R>) <= 48 * 1024;   // tensor buffers in shared memory
     static constexpr size_t scratch_per_block = SMEM ? 0 : (size_t)3 * H2;   // complex entries
 };
 
@@ -55,27 +57,27 @@ __device__ __forceinline__ int plain_slot_edge(const int4& v, int k) {
 
 // T = Gamma prod_k lambda_k^{1/2}; with warm, the vertex's outgoing messages are set to
 // diag(lambda)/sum(lambda) in msg_nxt (the buffer the first sweep reads).  One block per vertex.
-template <int CHI, int D>
+template <int CHI, int D, typename R>
 __global__ void plain_bp_init_kernel(PlainArgs a) {
-    using S = PlainShape<CHI, D>;
+    using S = PlainShape<CHI, D, R>;
     const int v = blockIdx.x;
-    __shared__ double sq[D][CHI], m0[D][CHI];
+    __shared__ R sq[D][CHI], m0[D][CHI];
     const int4 sl = a.vslots[v];
     if (threadIdx.x < D * CHI) {
         const int k = threadIdx.x / CHI, j = threadIdx.x % CHI;
         const int e = plain_slot_edge(sl, k);
-        const double lj = lam_get(a.lam, CHI, e, j);
+        const R lj = lam_get(a.lam, CHI, e, j);
         sq[k][j] = sqrt(lj);
-        double s = 0.0;
+        R s = 0.0;
         for (int q = 0; q < CHI; ++q) s += lam_get(a.lam, CHI, e, q);
         m0[k][j] = s > 0.0 ? lj / s : 0.0;
     }
     __syncthreads();
-    const cd* g = (const cd*)a.Gamma + (size_t)v * S::H2;
-    cd* T = (cd*)a.T + (size_t)v * S::H2;
+    const C<R>* g = (const C<R>*)a.Gamma + (size_t)v * S::H2;
+    C<R>* T = (C<R>*)a.T + (size_t)v * S::H2;
     for (int t = threadIdx.x; t < S::H2; t += blockDim.x) {
         int r = t % S::H;
-        double f = 1.0;
+        R f = 1.0;
         for (int k = D - 1; k >= 0; --k) {
             f *= sq[k][r % CHI];
             r /= CHI;
@@ -83,14 +85,14 @@ __global__ void plain_bp_init_kernel(PlainArgs a) {
         T[t] = f * g[t];
     }
     if (a.warm) {
-        cd* out = (cd*)a.msg_nxt;
+        C<R>* out = (C<R>*)a.msg_nxt;
         for (int t = threadIdx.x; t < D * S::CC; t += blockDim.x) {
             const int k = t / S::CC, r = t % S::CC;
             const int e = plain_slot_edge(sl, k);
             if (e < 0) continue;
             const int o = 2 * e + (a.edge_info[e].x == v ? 0 : 1);
             const int j = r / CHI, jp = r % CHI;
-            out[(size_t)o * S::CC + r] = cd{j == jp ? m0[k][j] : 0.0, 0.0};
+            out[(size_t)o * S::CC + r] = C<R>{j == jp ? m0[k][j] : (R)0, (R)0};
         }
     }
 }
@@ -99,30 +101,30 @@ __global__ void plain_bp_init_kernel(PlainArgs a) {
 //   m_{v->b}[j][j'] = sum T[.., j@s, ..] conj(T[.., j'@s, ..]) prod_{o != s} m_o[x_o][x'_o]
 // (Eq. (local_consistency)), divided by its complex trace; new - old goes to dm for the
 // trace-norm kernel.
-template <int CHI, int D>
-__global__ void __launch_bounds__(PlainShape<CHI, D>::NT) plain_bp_sweep_kernel(PlainArgs a) {
-    using S = PlainShape<CHI, D>;
+template <int CHI, int D, typename R>
+__global__ void __launch_bounds__(PlainShape<CHI, D, R>::NT) plain_bp_sweep_kernel(PlainArgs a) {
+    using S = PlainShape<CHI, D, R>;
     constexpr int H2 = S::H2, CC = S::CC, NT = S::NT, TPO = S::TPO;
     extern __shared__ __align__(16) unsigned char plain_smem[];
-    cd* min = reinterpret_cast<cd*>(plain_smem);   // [D][CC]
-    cd* F = min + D * CC;                          // [CC]
-    cd* T;
-    cd* P0;
-    cd* P1;
+    C<R>* min = reinterpret_cast<C<R>*>(plain_smem);   // [D][CC]
+    C<R>* F = min + D * CC;                          // [CC]
+    C<R>* T;
+    C<R>* P0;
+    C<R>* P1;
     if constexpr (S::SMEM) {
         T = F + CC;
         P0 = T + H2;
         P1 = P0 + H2;
     } else {
-        T = a.scratch + (size_t)blockIdx.x * S::scratch_per_block;
+        T = (C<R>*)a.scratch + (size_t)blockIdx.x * S::scratch_per_block;
         P0 = T + H2;
         P1 = P0 + H2;
     }
     __shared__ int es[4], in_idx[4], out_idx[4];
-    __shared__ cd itr;
+    __shared__ C<R> itr;
     const int v = blockIdx.x, tid = threadIdx.x;
-    const cd* src_msg = (const cd*)a.msg_cur;
-    cd* dst_msg = (cd*)a.msg_nxt;
+    const C<R>* src_msg = (const C<R>*)a.msg_cur;
+    C<R>* dst_msg = (C<R>*)a.msg_nxt;
     if (tid < D) {
         const int e = plain_slot_edge(a.vslots[v], tid);
         es[tid] = e;
@@ -134,23 +136,23 @@ __global__ void __launch_bounds__(PlainShape<CHI, D>::NT) plain_bp_sweep_kernel(
             out_idx[tid] = in_idx[tid] = -1;
         }
     }
-    for (int t = tid; t < H2; t += NT) T[t] = ((const cd*)a.T)[(size_t)v * H2 + t];
+    for (int t = tid; t < H2; t += NT) T[t] = ((const C<R>*)a.T)[(size_t)v * H2 + t];
     __syncthreads();
     for (int t = tid; t < D * CC; t += NT) {
         const int k = t / CC, r = t % CC;
-        min[t] = in_idx[k] >= 0 ? src_msg[(size_t)in_idx[k] * CC + r] : cd{r == 0 ? 1.0 : 0.0, 0.0};
+        min[t] = in_idx[k] >= 0 ? src_msg[(size_t)in_idx[k] * CC + r] : C<R>{(R)(r == 0 ? 1 : 0), (R)0};
     }
     __syncthreads();
     for (int s = 0; s < D; ++s) {
         if (es[s] < 0) continue;   // uniform: es is shared
-        const cd* src = T;
-        cd* dst = P0;
+        const C<R>* src = T;
+        C<R>* dst = P0;
         for (int o = 0; o < D; ++o) {
             if (o == s) continue;
             const int so = ipow(CHI, D - 1 - o);
             for (int t = tid; t < H2; t += NT) {
                 const int x = (t / so) % CHI, base = t - x * so;
-                cd acc = cd{0.0, 0.0};
+                C<R> acc = C<R>{(R)0, (R)0};
 #pragma unroll 4
                 for (int q = 0; q < CHI; ++q) acc = cfma(src[base + q * so], min[o * CC + q * CHI + x], acc);
                 dst[t] = acc;
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(PlainShape<CHI, D>::NT) plain_bp_sweep_kernel(
         for (int rr = tid / TPO; rr < CC; rr += NT / TPO) {
             const int part = tid % TPO;
             const int j = rr / CHI, jp = rr % CHI;
-            cd f = cd{0.0, 0.0};
+            C<R> f = C<R>{(R)0, (R)0};
             for (int q = part; q < NTERM; q += TPO) {
                 const int t = (q / ss) * (ss * CHI) + (q % ss);
                 f = cfmac(T[t + jp * ss], src[t + j * ss], f);
@@ -176,17 +178,17 @@ __global__ void __launch_bounds__(PlainShape<CHI, D>::NT) plain_bp_sweep_kernel(
         }
         __syncthreads();
         if (tid == 0) {
-            cd tr = cd{0.0, 0.0};
+            C<R> tr = C<R>{(R)0, (R)0};
             for (int q = 0; q < CHI; ++q) tr = tr + F[q * CHI + q];
-            const double d = tr.x * tr.x + tr.y * tr.y;
-            itr = d > 0.0 ? cd{tr.x / d, -tr.y / d} : cd{0.0, 0.0};
+            const R d = tr.x * tr.x + tr.y * tr.y;
+            itr = d > 0.0 ? C<R>{tr.x / d, -tr.y / d} : C<R>{(R)0, (R)0};
         }
         __syncthreads();
         for (int r = tid; r < CC; r += NT) {
-            const cd mn = F[r] * itr;
-            const cd mo = src_msg[(size_t)out_idx[s] * CC + r];
+            const C<R> mn = F[r] * itr;
+            const C<R> mo = src_msg[(size_t)out_idx[s] * CC + r];
             dst_msg[(size_t)out_idx[s] * CC + r] = mn;
-            a.dm[(size_t)out_idx[s] * CC + r] = mn - mo;
+            ((C<R>*)a.dm)[(size_t)out_idx[s] * CC + r] = mn - mo;
         }
         __syncthreads();
     }
@@ -194,21 +196,22 @@ __global__ void __launch_bounds__(PlainShape<CHI, D>::NT) plain_bp_sweep_kernel(
 
 // Trace norm (sum of singular values, one-sided Jacobi in FP64) of every directed message's
 // new - old; block = CHI^2 / 2 threads, one message per block; the sum goes to *acc.
-template <int CHI>
-__global__ void plain_trace_norm_kernel(const cd* dm, double* acc) {
+template <int CHI, typename R>
+__global__ void plain_trace_norm_kernel(const C<R>* dm, double* acc) {
     constexpr int CC = CHI * CHI;
-    __shared__ cd A[CC];
-    __shared__ double tn;
+    __shared__ C<R> A[CC];
+    __shared__ R tn;
     __shared__ int flag;
     const int g = threadIdx.x;
     for (int t = g; t < CC; t += blockDim.x) A[t] = dm[(size_t)blockIdx.x * CC + t];
     if (g == 0) tn = 0.0;
     __syncthreads();
     BlockGroup grp{&flag};
-    jacobi_svd<CHI, double, BlockGroup, false>(A, nullptr, g, grp, group_mask<CHI>(), 1e-15, 60, false);
+    jacobi_svd<CHI, R, BlockGroup, false>(A, nullptr, g, grp, group_mask<CHI>(), (R)(sizeof(R) == 8 ? 1e-15 : 1e-6), 60,
+                                          false);
     __syncthreads();
     if (g < CHI) {
-        double c2 = 0.0;
+        R c2 = 0.0;
         for (int r = 0; r < CHI; ++r) c2 += norm2(A[g * CHI + r]);
         atomicAdd(&tn, sqrt(c2));
     }
@@ -221,52 +224,53 @@ __global__ void plain_trace_norm_kernel(const cd* dm, double* acc) {
 // v^H A v), principal square roots and pseudo-inverse square roots, the SVD of
 // M = (m_{a->b}^{1/2})^T m_{b->a}^{1/2}, lambda = S/||S||, X_a = conj(m_{a->b}^{-1/2}) U ||S||^{1/2}
 // and X_b = conj(m_{b->a}^{-1/2}) V^* ||S||^{1/2}.
-template <int CHI>
-__global__ void plain_regauge_edge_kernel(const cd* msg, double* lam, cd* X, double eig_cut, double svd_cut) {
+template <int CHI, typename R>
+__global__ void plain_regauge_edge_kernel(const C<R>* msg, double* lam, C<R>* X, double eig_cut, double svd_cut) {
     constexpr int CC = CHI * CHI;
-    __shared__ cd Am[2][CC], Vm[2][CC], sqm[2][CC], isq[2][CC], M[CC], VM[CC];
-    __shared__ double w[2][CHI], sig[CHI], scal[2];
+    __shared__ C<R> Am[2][CC], Vm[2][CC], sqm[2][CC], isq[2][CC], M[CC], VM[CC];
+    __shared__ R w[2][CHI], sig[CHI], scal[2];
     __shared__ int perm[CHI], flag;
     const int e = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
     BlockGroup grp{&flag};
     for (int t = tid; t < 2 * CC; t += NT) {
         const int x = t / CC, r = t % CC;
         const int row = r % CHI, col = r / CHI;
-        const cd* mm = msg + (size_t)(2 * e + x) * CC;
-        const cd v = mm[row * CHI + col], vt = mm[col * CHI + row];
-        Am[x][col * CHI + row] = cd{0.5 * (v.x + vt.x), 0.5 * (v.y - vt.y)};
+        const C<R>* mm = msg + (size_t)(2 * e + x) * CC;
+        const C<R> v = mm[row * CHI + col], vt = mm[col * CHI + row];
+        Am[x][col * CHI + row] = C<R>{(R)0.5 * (v.x + vt.x), (R)0.5 * (v.y - vt.y)};
     }
     __syncthreads();
     for (int x = 0; x < 2; ++x)
-        jacobi_svd<CHI, double, BlockGroup, true, true>(Am[x], Vm[x], tid, grp, group_mask<CHI>(), 1e-15, 60, true,
-                                                        nullptr, 3e-8);
+        jacobi_svd<CHI, R, BlockGroup, true, sizeof(R) == 8>(Am[x], Vm[x], tid, grp, group_mask<CHI>(),
+                                                                  (R)(sizeof(R) == 8 ? 1e-15 : 1e-6), 60, true, nullptr,
+                                                                  (R)(sizeof(R) == 8 ? 3e-8 : 1e-3));
     __syncthreads();
     for (int t = tid; t < 2 * CHI; t += NT) {
         const int x = t / CHI, k = t % CHI;
-        double n2 = 0.0, sg = 0.0;
+        R n2 = 0.0, sg = 0.0;
         for (int r = 0; r < CHI; ++r) {
-            const cd av = Am[x][k * CHI + r], vv = Vm[x][k * CHI + r];
+            const C<R> av = Am[x][k * CHI + r], vv = Vm[x][k * CHI + r];
             n2 += norm2(av);
             sg += vv.x * av.x + vv.y * av.y;
         }
-        const double wv = nr_sqrt(n2);
+        const R wv = nr_sqrt(n2);
         w[x][k] = sg >= 0.0 ? wv : -wv;
     }
     __syncthreads();
     for (int t = tid; t < 2 * CC; t += NT) {
         const int x = t / CC, r = t % CC;
         const int j = r / CHI, jp = r % CHI;
-        double wmax = 0.0;
+        R wmax = 0.0;
         for (int k = 0; k < CHI; ++k) wmax = fmax(wmax, w[x][k]);
-        cd s1 = cd{0.0, 0.0}, s2 = cd{0.0, 0.0};
+        C<R> s1 = C<R>{(R)0, (R)0}, s2 = C<R>{(R)0, (R)0};
         for (int k = 0; k < CHI; ++k) {
-            const double wk = w[x][k];
+            const R wk = w[x][k];
             if (!(wk > eig_cut * wmax)) continue;
-            const double is = nr_rsqrt(wk);
-            const double sq = wk * is;
-            const cd vv = Vm[x][k * CHI + j] * conj(Vm[x][k * CHI + jp]);
-            s1 = cfma(cd{sq, 0.0}, vv, s1);
-            s2 = cfma(cd{is, 0.0}, vv, s2);
+            const R is = nr_rsqrt(wk);
+            const R sq = wk * is;
+            const C<R> vv = Vm[x][k * CHI + j] * conj(Vm[x][k * CHI + jp]);
+            s1 = cfma(C<R>{sq, (R)0}, vv, s1);
+            s2 = cfma(C<R>{is, (R)0}, vv, s2);
         }
         sqm[x][r] = s1;
         isq[x][r] = s2;
@@ -274,15 +278,17 @@ __global__ void plain_regauge_edge_kernel(const cd* msg, double* lam, cd* X, dou
     __syncthreads();
     for (int t = tid; t < CC; t += NT) {
         const int k = t % CHI, l = t / CHI;
-        cd acc = cd{0.0, 0.0};
+        C<R> acc = C<R>{(R)0, (R)0};
         for (int j = 0; j < CHI; ++j) acc = cfma(sqm[0][j * CHI + k], sqm[1][j * CHI + l], acc);
         M[l * CHI + k] = acc;
     }
     __syncthreads();
-    jacobi_svd<CHI, double, BlockGroup, true, true>(M, VM, tid, grp, group_mask<CHI>(), 1e-15, 60, true, nullptr, 3e-8);
+    jacobi_svd<CHI, R, BlockGroup, true, sizeof(R) == 8>(M, VM, tid, grp, group_mask<CHI>(),
+                                                         (R)(sizeof(R) == 8 ? 1e-15 : 1e-6), 60, true, nullptr,
+                                                         (R)(sizeof(R) == 8 ? 3e-8 : 1e-3));
     __syncthreads();
     for (int cc = tid; cc < CHI; cc += NT) {
-        double n2 = 0.0;
+        R n2 = 0.0;
         for (int r = 0; r < CHI; ++r) n2 += norm2(M[cc * CHI + r]);
         sig[cc] = nr_sqrt(n2);
     }
@@ -290,15 +296,15 @@ __global__ void plain_regauge_edge_kernel(const cd* msg, double* lam, cd* X, dou
     for (int cc = tid; cc < CHI; cc += NT) perm[desc_rank(sig, CHI, cc)] = cc;
     __syncthreads();
     if (tid == 0) {
-        double tot = 0.0;
+        R tot = 0.0;
         for (int cc = 0; cc < CHI; ++cc) tot += sig[cc] * sig[cc];
-        const double nrm = nr_sqrt(tot);
+        const R nrm = nr_sqrt(tot);
         scal[0] = nrm;
         scal[1] = nr_sqrt(nrm);
-        const double inrm = nrm > 0.0 ? nr_rcp(nrm) : 0.0;
-        const double smax = sig[perm[0]];
+        const R inrm = nrm > 0.0 ? nr_rcp(nrm) : 0.0;
+        const R smax = sig[perm[0]];
         for (int r = 0; r < CHI; ++r) {
-            const double s = sig[perm[r]];
+            const R s = sig[perm[r]];
             lam[(size_t)e * CHI + r] = (nrm > 0.0 && s > svd_cut * smax) ? s * inrm : 0.0;
         }
     }
@@ -307,12 +313,12 @@ __global__ void plain_regauge_edge_kernel(const cd* msg, double* lam, cd* X, dou
         const int x = t / CC, r = t % CC;
         const int jpp = r / CHI, j = r % CHI;
         const int pc = perm[j];
-        const double s = sig[pc];
-        cd acc = cd{0.0, 0.0};
+        const R s = sig[pc];
+        C<R> acc = C<R>{(R)0, (R)0};
         const bool kept = scal[0] > 0.0 && s > svd_cut * sig[perm[0]];
         if (kept) {
             for (int jp = 0; jp < CHI; ++jp) {
-                const cd u = (x == 0) ? nr_rcp(s) * M[pc * CHI + jp] : conj(VM[pc * CHI + jp]);
+                const C<R> u = (x == 0) ? nr_rcp(s) * M[pc * CHI + jp] : conj(VM[pc * CHI + jp]);
                 acc = cfma(isq[x][jp * CHI + jpp], u, acc);
             }
             acc = scal[1] * acc;
@@ -323,60 +329,60 @@ __global__ void plain_regauge_edge_kernel(const cd* msg, double* lam, cd* X, dou
 
 // Vidal gauge finding, vertex part: Gamma[.., j@k, ..] = sum_q T[.., q@k, ..] X_k[q][j] for every
 // slot (X of the edge, from this vertex's side; identity on phantom slots).
-template <int CHI, int D>
+template <int CHI, int D, typename R>
 __global__ void plain_regauge_vertex_kernel(PlainArgs a) {
-    using S = PlainShape<CHI, D>;
+    using S = PlainShape<CHI, D, R>;
     constexpr int H2 = S::H2, CC = S::CC;
     extern __shared__ __align__(16) unsigned char plain_smem[];
-    cd* Xs = reinterpret_cast<cd*>(plain_smem);   // [D][CC]
-    cd* b0;
-    cd* b1;
+    C<R>* Xs = reinterpret_cast<C<R>*>(plain_smem);   // [D][CC]
+    C<R>* b0;
+    C<R>* b1;
     if constexpr (S::SMEM) {
         b0 = Xs + D * CC;
         b1 = b0 + H2;
     } else {
-        b0 = a.scratch + (size_t)blockIdx.x * S::scratch_per_block;
+        b0 = (C<R>*)a.scratch + (size_t)blockIdx.x * S::scratch_per_block;
         b1 = b0 + H2;
     }
     const int v = blockIdx.x;
     const int4 sl = a.vslots[v];
-    for (int t = threadIdx.x; t < H2; t += blockDim.x) b0[t] = ((const cd*)a.T)[(size_t)v * H2 + t];
+    for (int t = threadIdx.x; t < H2; t += blockDim.x) b0[t] = ((const C<R>*)a.T)[(size_t)v * H2 + t];
     for (int t = threadIdx.x; t < D * CC; t += blockDim.x) {
         const int k = t / CC, r = t % CC;
         const int e = plain_slot_edge(sl, k);
         if (e >= 0) {
             const int side = a.edge_info[e].x == v ? 0 : 1;
-            Xs[t] = a.X[((size_t)e * 2 + side) * CC + r];
+            Xs[t] = ((const C<R>*)a.X)[((size_t)e * 2 + side) * CC + r];
         } else {
-            Xs[t] = cd{(r / CHI == r % CHI) ? 1.0 : 0.0, 0.0};
+            Xs[t] = C<R>{(R)((r / CHI == r % CHI) ? 1 : 0), (R)0};
         }
     }
     __syncthreads();
-    cd* cur = b0;
-    cd* nxt = b1;
+    C<R>* cur = b0;
+    C<R>* nxt = b1;
     for (int k = 0; k < D; ++k) {
         const int st = ipow(CHI, D - 1 - k);
         for (int t = threadIdx.x; t < H2; t += blockDim.x) {
             const int jk = (t / st) % CHI, base = t - jk * st;
-            cd acc = cd{0.0, 0.0};
+            C<R> acc = C<R>{(R)0, (R)0};
             for (int q = 0; q < CHI; ++q) acc = cfma(cur[base + q * st], Xs[k * CC + q * CHI + jk], acc);
             nxt[t] = acc;
         }
         __syncthreads();
-        cd* tmp = cur;
+        C<R>* tmp = cur;
         cur = nxt;
         nxt = tmp;
     }
-    cd* g = (cd*)a.Gamma + (size_t)v * H2;
+    C<R>* g = (C<R>*)a.Gamma + (size_t)v * H2;
     for (int t = threadIdx.x; t < H2; t += blockDim.x) g[t] = cur[t];
 }
 
 // rho_a = sum_J Gamma[i, J] conj(Gamma[i', J]) prod_k lambda_k[j_k]^2 / trace (Eqs. (partial_dens),
 // (bp_approx)); read-out +1 if rho_a[0][0] > 1/2 (Eq. (rounding_rule)).  One warp per vertex.
-template <int CHI, int D>
-__global__ void plain_marginals_kernel(const cd* Gamma, const double* lam, const int4* vslots, int n, cd* rho,
+template <int CHI, int D, typename R>
+__global__ void plain_marginals_kernel(const C<R>* Gamma, const double* lam, const int4* vslots, int n, cd* rho,
                                        int8_t* sign, int* nan_flag) {
-    constexpr int H = PlainShape<CHI, D>::H;
+    constexpr int H = PlainShape<CHI, D, R>::H;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x & 31;
     if (warp >= n) return;
     const int v = warp;
@@ -390,7 +396,7 @@ __global__ void plain_marginals_kernel(const cd* Gamma, const double* lam, const
             wgt *= l * l;
             rem /= CHI;
         }
-        const cd g0 = Gamma[(size_t)v * 2 * H + r], g1 = Gamma[(size_t)v * 2 * H + H + r];
+        const cd g0 = ccast<double>(Gamma[(size_t)v * 2 * H + r]), g1 = ccast<double>(Gamma[(size_t)v * 2 * H + H + r]);
         acc[0] = cfmac(g0, wgt * g0, acc[0]);
         acc[1] = cfmac(g1, wgt * g0, acc[1]);
         acc[2] = cfmac(g0, wgt * g1, acc[2]);

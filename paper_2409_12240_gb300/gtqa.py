@@ -26,6 +26,7 @@ GTQA_ERR_UNSUPPORTED = 7
 
 GTQA_FP64 = 0
 GTQA_MIXED = 1
+GTQA_C64 = 2
 
 GTQA_BP_WARM_START = 1
 GTQA_BP_REGAUGE = 2
