@@ -74,3 +74,24 @@ def test_c64_rejected_shapes():
     # chi 16 has no complex64 kernels
     assert lib.gtqa_create(inst.n, inst.m, e.ctypes.data, None, J.ctypes.data, hh.ctypes.data, 16, ctypes.byref(opt),
                            ctypes.byref(h)) == G.GTQA_ERR_UNSUPPORTED
+
+
+def test_c64_on_a_four_regular_graph_follows_the_oracle():
+    """The complex64 mode on the degree-4 plain kernels (n = 10, chi = 4): within 1e-4 of the
+    oracle after 6 layers."""
+    G = U.lib()
+    inst = make_instance(10, 2, d=4)
+    K, dt, tol, mi = 20, 0.1, 1e-6, 100
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 4, inst.colour, G.gtqa_options_init(precision=G.GTQA_C64))
+    st = O.plus_state(inst.n, inst.edges)
+    try:
+        assert G.gtqa_max_degree(s) == 4
+        for k in range(1, 7):
+            G.gtqa_trotter_layer(s, k / K, dt)
+            G.gtqa_bp_sweep(s, tol, mi)
+            tZ, tX = O.schedule(k, K, dt)
+            st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 4, 1e-12, 200)
+        rho_g, _ = G.gtqa_marginals(s)
+        assert np.abs(rho_g - O.reduced_density_matrices(st)).max() < 1e-4
+    finally:
+        G.gtqa_destroy(s)

@@ -67,3 +67,31 @@ def test_chi16_anneal_symmetric_formula_and_unsupported_calls():
         assert np.isfinite(G.gtqa_marginals(s)[0]).all()
     finally:
         G.gtqa_destroy(s)
+
+
+def test_chi16_single_qubit_gates_and_entropy():
+    """One-qubit gates on a chi = 16 state equal the oracle's (then BP and the regauge), and the
+    entropy of a cut (lambda only) matches the oracle's."""
+    from instances import random_gate_inputs
+    G = U.lib()
+    inst = make_instance(12, 1)
+    K, dt, tol, mi = 20, 0.3, 1e-12, 300
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 16, inst.colour, G.gtqa_options_init(precision=G.GTQA_FP64))
+    st = O.plus_state(inst.n, inst.edges)
+    try:
+        G.gtqa_anneal(s, 1, 4, K, dt, tol, mi)
+        for k in range(1, 5):
+            tZ, tX = O.schedule(k, K, dt)
+            st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 16, tol, mi)
+        _, _, v, W = random_gate_inputs(inst.n, inst.m, 0, 2 * inst.n, seed=31)
+        G.gtqa_apply_single_qubit_gates(s, v, W)
+        G.gtqa_bp_sweep(s, tol, mi)
+        O.apply_single_qubit_gates(st, list(zip(v.tolist(), W)))
+        st, _ = O.regauge(st, tol, mi)
+        rho_g, _ = G.gtqa_marginals(s)
+        assert np.abs(rho_g - O.reduced_density_matrices(st)).max() < TOL
+        cut = np.zeros(inst.m, dtype=np.uint8)
+        cut[: inst.m // 3] = 1
+        assert abs(G.gtqa_entropy(s, cut) - O.approx_entanglement_entropy(st, cut.astype(bool))) < 1e-9
+    finally:
+        G.gtqa_destroy(s)
