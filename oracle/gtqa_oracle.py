@@ -20,6 +20,7 @@ Every step follows the paper's notation and order:
 * per-gate fidelity estimate .................. Sec. III D, Eq. (gate_fidelity)
 * mean-field entanglement entropy, bipartition . Sec. III C, Eqs. (bipartition), (mean_field_schmidt), (apprx_entropy)
 * measurement sampling ........................ Sec. IV A, Eq. (projection)
+* regauge only when R is large ................ Sec. II C, App. C (reading R15)
 * other product formulas, arbitrary gates ..... Sec. V (second-order and randomised formulas);
                                                 Sec. II D and App. E (any one- and two-qubit gate)
 
@@ -61,6 +62,10 @@ R13 Product formulas beyond first order (the paper names them only as an
     formula is (t_X/2, t_X/2) at the same tau_k; the randomised first-order
     formula draws, per layer, the forward (0, t_X) or the reversed (t_X, 0)
     ordering with probability 1/2 each (the caller supplies the draws).
+R15 Regauge policy (Sec. II C: the paper regauges occasionally, when R grows too
+    large): after the Trotter layer, R of App. C is evaluated, and the symmetric
+    split, BP and Vidal gauge finding run only if R > r_threshold.  A negative
+    threshold regauges every layer (R1-R14).
 R14 Arbitrary two-qubit gate on edge e = {a, b} with a = edges[e][0]: a 4x4
     matrix W[(i_a i_b), (i_a' i_b')] (row index 2 i_a + i_b), applied by the
     same simple update as the Ising gate (App. E); gates are applied in the
@@ -590,6 +595,26 @@ def run(n: int, edges, J, h, colour, K: int, dt: float, chi: int, tol: float, ma
         if not record:
             info.pop("messages", None)
         infos.append(info)
+    return st, infos
+
+
+def run_with_regauge_policy(n: int, edges, J, h, colour, K: int, dt: float, chi: int, tol: float,
+                            max_iter: int, r_threshold: float, layers: Optional[int] = None,
+                            state: Optional[VidalState] = None, k0: int = 0):
+    """Reading R15: layers k0+1 .. k0+layers of the anneal (R1), each followed by the
+    regauge of Sec. II C only when the residual R of App. C exceeds r_threshold.
+    Returns the final state and per-layer {"R", "regauged"}."""
+    st = plus_state(n, np.asarray(edges)) if state is None else state
+    infos = []
+    last = K if layers is None else min(K, k0 + layers)
+    for k in range(k0 + 1, last + 1):
+        t_Z, t_X = schedule(k, K, dt)
+        trotter_layer(st, colour, J, h, t_Z, t_X, chi)
+        R = local_orthogonality_residual(st)
+        done = R > r_threshold
+        if done:
+            st, _ = regauge(st, tol, max_iter)
+        infos.append({"R": R, "regauged": done})
     return st, infos
 
 

@@ -531,3 +531,43 @@ def general_gate_truncation_fidelity(seed: int = 0, n: int = 10) -> float:
         w_opt = float(np.sum(sv[ref.lam[e].size - 1:] ** 2))
         err = max(err, abs(ov - (1.0 - r["discarded"])), abs(r["discarded"] - w_opt))
     return float(err)
+
+
+def regauge_policy_on_trees(seed: int = 0, n: int = 10, K: int = 6, dt: float = 0.3) -> dict:
+    """Reading R15 on a tree without truncation: the simple update is exact there (Sec. II B-C),
+    so a policy that never regauges (infinite threshold) still gives the exact marginals at
+    every layer, and so does one that always regauges."""
+    inst = make_tree_instance(n, seed)
+    _, rhos = SV.evolve(inst.n, inst.edges, inst.J, inst.h, K, dt)
+    out = {}
+    for name, thr in (("never", np.inf), ("always", -1.0)):
+        st = None
+        err = 0.0
+        regauged = 0
+        for k in range(1, K + 1):
+            st, infos = O.run_with_regauge_policy(inst.n, inst.edges, inst.J, inst.h, inst.colour, K, dt, 256, 1e-13,
+                                                  100, thr, layers=1, state=st, k0=k - 1)
+            regauged += sum(i["regauged"] for i in infos)
+            err = max(err, float(np.abs(O.reduced_density_matrices(st) - rhos[k - 1]).max()))
+        out[name] = {"regauged": regauged, "rho": err}
+    return out
+
+
+def regauge_policy_on_loopy_graphs(seed: int = 0, n: int = 16, K: int = 20, dt: float = 0.1, chi: int = 4) -> dict:
+    """On a loopy graph with truncation: a negative threshold regauges every layer and is the
+    every-layer run (reading R1); an infinite one never regauges; at an intermediate threshold
+    exactly the layers whose R exceeds it are regauged."""
+    inst = make_instance(n, seed)
+    layers = 6
+    args = (inst.n, inst.edges, inst.J, inst.h, inst.colour, K, dt, chi, 1e-12, 100)
+    st_a, infos_a = O.run_with_regauge_policy(*args, -1.0, layers=layers)
+    st_b, _ = O.run(*args, layers=layers)
+    _, infos_c = O.run_with_regauge_policy(*args, np.inf, layers=layers)
+    Rs = sorted(i["R"] for i in infos_a)
+    thr = 0.5 * (Rs[len(Rs) // 2 - 1] + Rs[len(Rs) // 2])
+    _, infos_d = O.run_with_regauge_policy(*args, thr, layers=layers)
+    return {"all_regauged": all(i["regauged"] for i in infos_a),
+            "rho": float(np.abs(O.reduced_density_matrices(st_a) - O.reduced_density_matrices(st_b)).max()),
+            "none_regauged": not any(i["regauged"] for i in infos_c),
+            "threshold_rule": all(i["regauged"] == (i["R"] > thr) for i in infos_d),
+            "some_skipped": 0 < sum(i["regauged"] for i in infos_d) < layers}

@@ -215,3 +215,16 @@ def test_gtqa_exact_on_degree_four_trees(seed):
     assert np.bincount(make_tree_instance(10, seed, max_degree=4).edges.ravel()).max() == 4
     r = P.gtqa_tree_exact(seed, max_degree=4)
     assert r["rho"] < 1e-10 and r["lam"] < 1e-10 and r["state"] < 1e-10, r
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_regauge_policy_on_trees_stays_exact(seed):
+    r = P.regauge_policy_on_trees(seed)
+    assert r["never"]["regauged"] == 0 and r["never"]["rho"] < 1e-10, r
+    assert r["always"]["regauged"] == 6 and r["always"]["rho"] < 1e-10, r
+
+
+def test_regauge_policy_on_loopy_graphs():
+    r = P.regauge_policy_on_loopy_graphs(0)
+    assert r["all_regauged"] and r["rho"] == 0.0 and r["none_regauged"], r
+    assert r["threshold_rule"] and r["some_skipped"], r
