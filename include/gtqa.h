@@ -193,6 +193,24 @@ int gtqa_autotune(gtqa_state* s, double tau, double dt, double tol, int32_t max_
 int gtqa_set_grid(gtqa_state* s, const int32_t* grid);
 
 /*
+ * gtqa_anneal with the paper's occasional regauging (Sec. II C: the Vidal gauge is restored
+ * when the local-orthogonality residual R of App. C grows too large).  After each layer's gates
+ * R is evaluated on the device (as gtqa_residual, normalised by 2|E|; for a batch, over all
+ * instances together).  BP from the warm start and Vidal gauge finding then run only if
+ * R > r_threshold; otherwise they are skipped on the device, with no host synchronisation,
+ * and the state keeps its simple-update gauge.  A negative threshold regauges every layer, as
+ * gtqa_anneal does.  Skipped layers leave gtqa_stats' last-BP fields unchanged;
+ * gtqa_regauge_counts reports how many layers were regauged and skipped.  Asynchronous.
+ * Returns GTQA_ERR_INVALID_ARG as gtqa_anneal or for a NaN threshold, and
+ * GTQA_ERR_UNSUPPORTED on a plain-path state (degree 4, chi > 8, complex64 mode).
+ */
+int gtqa_anneal_policy(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double dt, double tol,
+                       int32_t max_iter, double r_threshold);
+
+/* Layers regauged and skipped by gtqa_anneal_policy since creation.  Synchronises. */
+int gtqa_regauge_counts(gtqa_state* s, int64_t* regauged, int64_t* skipped);
+
+/*
  * gtqa_anneal replayed from a CUDA graph: the three launches of every layer k_begin..k_end are
  * captured once (on a private stream, with profiling events off) into a graph that the state
  * keeps, and the graph is launched on the state's stream.  A later call with the same

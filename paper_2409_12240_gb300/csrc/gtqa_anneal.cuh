@@ -63,6 +63,8 @@ struct Control {
     double last_dist;        // max over instances of the final dist/|E|
     long long bp_calls;
     long long nc_calls;      // BP calls in which some instance hit max_iter
+    long long regauged;      // regauge-policy layers: regauged (BP and gauge finding ran)
+    long long reg_skipped;   // and skipped (R at or below the threshold)
 };
 
 struct Ctx {
@@ -106,6 +108,8 @@ struct Ctx {
     int k0, k1, Ksched;       // layers k0..k1 with tau = k/Ksched; Ksched = 0: one layer at (tZ1, tX1)
     double dt, tZ1, tX1;
     double tXpre1;            // Ksched = 0: leading mixing angle of the layer (0: none)
+    const double* rgate;      // regauge policy: the residual sum of this layer (null: always regauge)
+    double rthr_sum;          // BP and regauge run only if *rgate > rthr_sum
     int nblocks;
     int bar_expect;           // arrivals per grid barrier (= nblocks; larger only in the timeout test)
     long long spin_limit;
@@ -1195,7 +1199,11 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 if (!grid_sync(gb, c.spin_limit)) return;
             }
         }
+        // regauge policy (Sec. II C): BP and gauge finding only when R exceeds the threshold;
+        // every block reads the same value, so the whole grid takes the same branch
+        const bool skip_regauge = c.rgate && !(__ldcg(c.rgate) > c.rthr_sum);
         if constexpr ((PH & PH_BP) != 0u) {
+            if (skip_regauge) continue;
             {
                 const int team = threadIdx.x / S::TV, tid = threadIdx.x % S::TV;
                 const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * (S::TPB / S::TV);
@@ -1381,6 +1389,11 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
             }
         }
         if constexpr ((PH & PH_REGAUGE) != 0u) {
+            if (c.rgate && blockIdx.x == 0 && threadIdx.x == 0) {
+                if (skip_regauge) ++c.ctl->reg_skipped;
+                else ++c.ctl->regauged;
+            }
+            if (skip_regauge) continue;
             {
                 const int team = threadIdx.x / S::TR, tid = threadIdx.x % S::TR;
                 RGSm<CHI>& sm = reinterpret_cast<RGSm<CHI>*>(smem)[team];

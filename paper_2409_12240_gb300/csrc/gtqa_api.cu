@@ -1476,6 +1476,57 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
     return anneal_launches(s, k_begin, k_end, K, dt, tol, max_iter);
 }
 
+int gtqa_anneal_policy(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double dt, double tol,
+                       int32_t max_iter, double r_threshold) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (K < 1 || k_begin < 1 || k_end < k_begin || k_end > K || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1 ||
+        std::isnan(r_threshold))
+        return GTQA_ERR_INVALID_ARG;
+    if (s->plain) return GTQA_ERR_UNSUPPORTED;
+    Ctx c = make_ctx(s);
+    c.Ksched = K;
+    c.dt = dt;
+    c.tol = tol;
+    c.max_iter = max_iter;
+    for (int k = k_begin; k <= k_end; ++k) {
+        c.k0 = c.k1 = k;
+        c.phases = PH_GATES;
+        c.rgate = nullptr;
+        if ((rc = run(s, c, PK_GATES, GTQA_K_TROTTER, s->m))) return rc;
+        // R of App. C (unnormalised sum over the 2m directed bonds) on the device
+        if (!cuda_ok(s, cudaMemsetAsync(s->rbuf, 0, sizeof(double), s->stream))) return GTQA_ERR_CUDA;
+        const cudaError_t e =
+            mixed(s) ? residual_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream)
+                     : residual_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->sticky = GTQA_ERR_CUDA;
+            return GTQA_ERR_CUDA;
+        }
+        s->launches += 1;
+        c.rgate = s->rbuf;
+        c.rthr_sum = r_threshold * 2.0 * (double)s->m;
+        c.phases = PH_BP | PH_WARM;
+        if ((rc = run(s, c, PK_BP, GTQA_K_BP, s->n))) return rc;
+        c.phases = PH_REGAUGE;
+        if ((rc = run(s, c, PK_REGAUGE, GTQA_K_REGAUGE, s->m))) return rc;
+        s->layers += 1;
+        s->gates += s->m;
+    }
+    return GTQA_OK;
+}
+
+int gtqa_regauge_counts(gtqa_state* s, int64_t* regauged, int64_t* skipped) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    Control ctl;
+    if ((rc = read_ctl(s, &ctl))) return rc;
+    if (regauged) *regauged = ctl.regauged;
+    if (skipped) *skipped = ctl.reg_skipped;
+    return GTQA_OK;
+}
+
 int gtqa_anneal_graph(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double dt, double tol,
                       int32_t max_iter) {
     int rc = check_state(s);

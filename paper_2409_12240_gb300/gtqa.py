@@ -43,6 +43,7 @@ EXPORTED = [
     "gtqa_barrier_bench", "gtqa_residual", "gtqa_entropy", "gtqa_spectral_bipartition", "gtqa_sample",
     "gtqa_trotter_split", "gtqa_anneal_ex", "gtqa_apply_gates", "gtqa_apply_single_qubit_gates",
     "gtqa_max_degree", "gtqa_anneal_graph", "gtqa_autotune", "gtqa_set_grid", "gtqa_gate_layers",
+    "gtqa_anneal_policy", "gtqa_regauge_counts",
 ]
 KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
@@ -95,6 +96,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_regauge": (I32, [P]),
         "gtqa_anneal": (I32, [P, I32, I32, I32, D, D, I32]),
         "gtqa_anneal_graph": (I32, [P, I32, I32, I32, D, D, I32]),
+        "gtqa_anneal_policy": (I32, [P, I32, I32, I32, D, D, I32, D]),
+        "gtqa_regauge_counts": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "gtqa_autotune": (I32, [P, D, D, D, I32, P]),
         "gtqa_set_grid": (I32, [P, P]),
         "gtqa_gate_layers": (I32, [I32, I32, P, I32, P, P, ctypes.POINTER(I32)]),
@@ -291,6 +294,19 @@ def gtqa_gate_layers(n: int, edges, edge) -> Tuple[np.ndarray, int]:
     _check(load().gtqa_gate_layers(int(n), int(e.shape[0]), e.ctypes.data, int(g.size), g.ctypes.data, lay.ctypes.data,
                                    ctypes.byref(nl)), "gtqa_gate_layers")
     return lay[:g.size], int(nl.value)
+
+
+def gtqa_anneal_policy(s: int, k_begin: int, k_end: int, K: int, dt: float, tol: float, max_iter: int,
+                       r_threshold: float) -> None:
+    """gtqa_anneal, regauging only the layers whose residual R exceeds r_threshold."""
+    _check(load().gtqa_anneal_policy(s, int(k_begin), int(k_end), int(K), float(dt), float(tol), int(max_iter),
+                                     float(r_threshold)), "gtqa_anneal_policy")
+
+
+def gtqa_regauge_counts(s: int) -> Tuple[int, int]:
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().gtqa_regauge_counts(s, ctypes.byref(a), ctypes.byref(b)), "gtqa_regauge_counts")
+    return int(a.value), int(b.value)
 
 
 def gtqa_sizes(s: int) -> Tuple[int, int, int, int]:
