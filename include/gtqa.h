@@ -73,10 +73,12 @@ extern "C" {
 typedef struct gtqa_state gtqa_state;
 
 typedef struct gtqa_options {
-    int32_t precision;   /* GTQA_FP64 or GTQA_MIXED */
+    int32_t precision;   /* GTQA_FP64, GTQA_MIXED or GTQA_C64 */
     int32_t reserved0;   /* must be 0 */
-    double svd_cutoff;   /* singular values <= svd_cutoff * s_0 are dropped; <= 0 selects 1e-14 */
-    double eig_cutoff;   /* message eigenvalues <= eig_cutoff * w_max count as zero; <= 0 selects 1e-13 */
+    double svd_cutoff;   /* singular values <= svd_cutoff * s_0 are dropped; <= 0 selects the
+                            precision's default: 1e-14, or 1e-7 for GTQA_C64 */
+    double eig_cutoff;   /* message eigenvalues <= eig_cutoff * w_max count as zero; <= 0 selects
+                            1e-13, or 1e-6 for GTQA_C64 */
     void* cuda_stream;   /* cudaStream_t for all work; NULL selects the legacy default stream */
 } gtqa_options;
 
@@ -118,12 +120,14 @@ void gtqa_options_init(gtqa_options* opt);
  *   opt        options or NULL for defaults
  *   out        receives the new state; *out is NULL on failure
  * Graphs with a vertex of degree 4 (the random 4-regular graphs of Sec. V) get vertex tensors
- * with four bonds, Gamma [n][2][CHI]^4; 8 < chi <= 16 gets storage bond dimension 16.  Both run
- * on plain per-phase kernels and need the FP64 precision and one instance; degree 4 needs
- * chi <= 4.  Anything else returns GTQA_ERR_UNSUPPORTED.  On such a state gtqa_sample,
- * gtqa_residual, gtqa_autotune and gtqa_anneal_graph return GTQA_ERR_UNSUPPORTED, and so does
+ * with four bonds, Gamma [n][2][CHI]^4; 8 < chi <= 16 gets storage bond dimension 16.  These
+ * states, and every state in the GTQA_C64 precision, run on plain per-phase kernels and hold
+ * one instance.  The shapes built there are: FP64 with degree 4 and chi <= 4, or degree 3 and
+ * 8 < chi <= 16; GTQA_C64 with degree 3 and chi <= 8, or degree 4 and chi <= 4.  Anything else
+ * returns GTQA_ERR_UNSUPPORTED.  On a plain-path state gtqa_autotune and gtqa_anneal_graph
+ * return GTQA_ERR_UNSUPPORTED (there is no persistent launch to tune or capture), and so does
  * gtqa_apply_gates at chi > 8; every other call works as documented.  Its BP reads the
- * distance on the host after every sweep.
+ * distance on the host after every sweep, and gtqa_anneal_policy reads R on the host.
  */
 int gtqa_create(int32_t n, int32_t m, const int32_t* edges, const int32_t* colour,
                 const double* J, const double* h, int32_t chi,
@@ -184,7 +188,7 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
  * runs decides, and the fastest grid is kept for the state.  The state's contents and
  * statistics are restored afterwards.  grid_out (nullable, 3 ints) receives the chosen grid
  * sizes.  Results do not depend on the grid, except for the rounding order of the BP distance
- * sum.  Synchronises.  Returns GTQA_ERR_UNSUPPORTED for a degree-4 state.
+ * sum.  Synchronises.  Returns GTQA_ERR_UNSUPPORTED for a plain-path state (gtqa_create).
  */
 int gtqa_autotune(gtqa_state* s, double tau, double dt, double tol, int32_t max_iter, int32_t* grid_out);
 
@@ -201,8 +205,10 @@ int gtqa_set_grid(gtqa_state* s, const int32_t* grid);
  * and the state keeps its simple-update gauge.  A negative threshold regauges every layer, as
  * gtqa_anneal does.  Skipped layers leave gtqa_stats' last-BP fields unchanged;
  * gtqa_regauge_counts reports how many layers were regauged and skipped.  Asynchronous.
- * Returns GTQA_ERR_INVALID_ARG as gtqa_anneal or for a NaN threshold, and
- * GTQA_ERR_UNSUPPORTED on a plain-path state (degree 4, chi > 8, complex64 mode).
+ * On a plain-path state (gtqa_create) the host reads R after the gates of every layer and
+ * launches BP and the regauge only when R > r_threshold; that loop synchronises once per layer
+ * and returns GTQA_ERR_NUMERIC if R is NaN.
+ * Returns GTQA_ERR_INVALID_ARG as gtqa_anneal or for a NaN threshold.
  */
 int gtqa_anneal_policy(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double dt, double tol,
                        int32_t max_iter, double r_threshold);

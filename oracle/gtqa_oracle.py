@@ -600,7 +600,8 @@ def run(n: int, edges, J, h, colour, K: int, dt: float, chi: int, tol: float, ma
 
 def run_with_regauge_policy(n: int, edges, J, h, colour, K: int, dt: float, chi: int, tol: float,
                             max_iter: int, r_threshold: float, layers: Optional[int] = None,
-                            state: Optional[VidalState] = None, k0: int = 0):
+                            state: Optional[VidalState] = None, k0: int = 0,
+                            svd_cutoff: float = SVD_CUTOFF):
     """Reading R15: layers k0+1 .. k0+layers of the anneal (R1), each followed by the
     regauge of Sec. II C only when the residual R of App. C exceeds r_threshold.
     Returns the final state and per-layer {"R", "regauged"}."""
@@ -609,11 +610,11 @@ def run_with_regauge_policy(n: int, edges, J, h, colour, K: int, dt: float, chi:
     last = K if layers is None else min(K, k0 + layers)
     for k in range(k0 + 1, last + 1):
         t_Z, t_X = schedule(k, K, dt)
-        trotter_layer(st, colour, J, h, t_Z, t_X, chi)
+        trotter_layer(st, colour, J, h, t_Z, t_X, chi, svd_cutoff)
         R = local_orthogonality_residual(st)
         done = R > r_threshold
         if done:
-            st, _ = regauge(st, tol, max_iter)
+            st, _ = regauge(st, tol, max_iter, svd_cutoff=svd_cutoff)
         infos.append({"R": R, "regauged": done})
     return st, infos
 

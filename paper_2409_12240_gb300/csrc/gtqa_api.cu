@@ -1053,6 +1053,53 @@ int d4_bp(gtqa_state* s, double tol, int max_iter, uint32_t flags, int32_t* iter
     return conv ? GTQA_OK : GTQA_ERR_NOT_CONVERGED;
 }
 
+// Unnormalised residual sum of App. C over the 2m directed bonds, added to s->rbuf.
+cudaError_t residual_launch(gtqa_state* s) {
+    if (s->plain)
+        return plain_residual_launch(s->CHI, s->D, f32(s), s->Gamma, s->lam, s->vslots4, s->n, s->rbuf, s->stream);
+    return mixed(s) ? residual_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream)
+                    : residual_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream);
+}
+
+// The regauge policy (Sec. II C) on the plain path: after the gates of each layer the host
+// reads R; BP from the warm start and the regauge run only when R > r_threshold.
+int d4_anneal_policy(gtqa_state* s, int k_begin, int k_end, int K, double dt, double tol, int max_iter,
+                     double r_threshold) {
+    int rc;
+    long long reg = 0, skip = 0;
+    const double thr_sum = r_threshold * 2.0 * (double)s->m;
+    for (int k = k_begin; k <= k_end; ++k) {
+        const double tau = (double)k / (double)K;
+        if ((rc = d4_trotter(s, dt * tau, 0.0, dt * (1.0 - tau)))) return rc;
+        if (!cuda_ok(s, cudaMemsetAsync(s->rbuf, 0, sizeof(double), s->stream))) return GTQA_ERR_CUDA;
+        if (residual_launch(s) != cudaSuccess) return d4_fail(s);
+        s->launches += 1;
+        double sum = 0.0;
+        if (!cuda_ok(s, cudaMemcpyAsync(&sum, s->rbuf, sizeof(double), cudaMemcpyDeviceToHost, s->stream)) ||
+            !cuda_ok(s, cudaStreamSynchronize(s->stream)))
+            return GTQA_ERR_CUDA;
+        if (!(sum == sum)) {
+            s->sticky = GTQA_ERR_NUMERIC;
+            return GTQA_ERR_NUMERIC;
+        }
+        if (sum > thr_sum) {
+            rc = d4_bp(s, tol, max_iter, GTQA_BP_DEFAULT, nullptr, nullptr);
+            if (rc && rc != GTQA_ERR_NOT_CONVERGED) return rc;
+            ++reg;
+        } else {
+            ++skip;
+        }
+    }
+    Control ctl;
+    if ((rc = read_ctl(s, &ctl))) return rc;
+    ctl.regauged += reg;
+    ctl.reg_skipped += skip;
+    if (!cuda_ok(s, cudaMemcpyAsync(s->ctl, &ctl, sizeof(Control), cudaMemcpyHostToDevice, s->stream)) ||
+        !cuda_ok(s, cudaStreamSynchronize(s->stream)))
+        return GTQA_ERR_CUDA;
+    return GTQA_OK;
+}
+
 // The three phase launches of layers k_begin..k_end (gtqa_anneal's body).
 int anneal_launches(gtqa_state* s, int k_begin, int k_end, int K, double dt, double tol, int max_iter) {
     int rc;
@@ -1113,8 +1160,8 @@ void gtqa_options_init(gtqa_options* opt) {
     if (!opt) return;
     std::memset(opt, 0, sizeof(*opt));
     opt->precision = GTQA_FP64;
-    opt->svd_cutoff = 1e-14;
-    opt->eig_cutoff = 1e-13;
+    opt->svd_cutoff = 0.0;   // the precision's default (gtqa_create)
+    opt->eig_cutoff = 0.0;
     opt->cuda_stream = nullptr;
 }
 
@@ -1304,7 +1351,6 @@ int gtqa_sample(gtqa_state* s, int32_t k, const int32_t* order, const double* u,
                 int8_t* x_out, double* p_out) {
     int rc = check_state(s);
     if (rc) return rc;
-    if (s->plain) return GTQA_ERR_UNSUPPORTED;
     if (k < 0 || k > s->n || (k > 0 && (!order || !u)) || !x_out || max_iter < 1 || !(tol >= 0.0))
         return GTQA_ERR_INVALID_ARG;
     std::vector<char> seen(s->n, 0);
@@ -1319,7 +1365,16 @@ int gtqa_sample(gtqa_state* s, int32_t k, const int32_t* order, const double* u,
     c.k0 = c.k1 = 0;
     c.tol = tol;
     c.max_iter = max_iter;
-    for (int q = 0; q < k; ++q) {
+    for (int q = 0; q < k && s->plain; ++q) {
+        if (plain_sample_launch(s->CHI, s->D, f32(s), s->Gamma, s->lam, s->vslots4, order[q], u[q], q, s->xs, s->ps,
+                                s->stream) != cudaSuccess)
+            return d4_fail(s);
+        s->launches += 1;
+        // the projection leaves the Vidal gauge: BP from the warm start, then the regauge
+        rc = d4_bp(s, tol, max_iter, GTQA_BP_WARM_START | GTQA_BP_REGAUGE, nullptr, nullptr);
+        if (rc && rc != GTQA_ERR_NOT_CONVERGED) return rc;
+    }
+    for (int q = 0; q < k && !s->plain; ++q) {
         const cudaError_t e = mixed(s) ? sample_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, order[q], u[q], q,
                                                              s->xs, s->ps, s->stream)
                                        : sample_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, order[q], u[q], q,
@@ -1483,7 +1538,7 @@ int gtqa_anneal_policy(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K,
     if (K < 1 || k_begin < 1 || k_end < k_begin || k_end > K || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1 ||
         std::isnan(r_threshold))
         return GTQA_ERR_INVALID_ARG;
-    if (s->plain) return GTQA_ERR_UNSUPPORTED;
+    if (s->plain) return d4_anneal_policy(s, k_begin, k_end, K, dt, tol, max_iter, r_threshold);
     Ctx c = make_ctx(s);
     c.Ksched = K;
     c.dt = dt;
@@ -1496,9 +1551,7 @@ int gtqa_anneal_policy(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K,
         if ((rc = run(s, c, PK_GATES, GTQA_K_TROTTER, s->m))) return rc;
         // R of App. C (unnormalised sum over the 2m directed bonds) on the device
         if (!cuda_ok(s, cudaMemsetAsync(s->rbuf, 0, sizeof(double), s->stream))) return GTQA_ERR_CUDA;
-        const cudaError_t e =
-            mixed(s) ? residual_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream)
-                     : residual_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream);
+        const cudaError_t e = residual_launch(s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             s->sticky = GTQA_ERR_CUDA;
@@ -1768,11 +1821,9 @@ int gtqa_spectral_bipartition(int32_t n, int32_t m, const int32_t* edges, uint8_
 int gtqa_residual(gtqa_state* s, double* R_out) {
     int rc = check_state(s);
     if (rc) return rc;
-    if (s->plain) return GTQA_ERR_UNSUPPORTED;
     if (!R_out) return GTQA_ERR_INVALID_ARG;
     if (!cuda_ok(s, cudaMemsetAsync(s->rbuf, 0, sizeof(double), s->stream))) return GTQA_ERR_CUDA;
-    const cudaError_t e = mixed(s) ? residual_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream)
-                                   : residual_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream);
+    const cudaError_t e = residual_launch(s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         s->sticky = GTQA_ERR_CUDA;

@@ -59,6 +59,10 @@ cudaError_t plain_regauge_launch(int CHI, int D, bool f32, const PlainArgs& a, c
                                  double svd_cut, cudaStream_t st);
 cudaError_t plain_marginals_launch(int CHI, int D, bool f32, const void* Gamma, const double* lam, const int4* vslots,
                                    int n, cd* rho, int8_t* sign, int* flag, cudaStream_t st);
+cudaError_t plain_residual_launch(int CHI, int D, bool f32, const void* Gamma, const double* lam, const int4* vslots,
+                                  int n, double* out, cudaStream_t st);
+cudaError_t plain_sample_launch(int CHI, int D, bool f32, void* Gamma, const double* lam, const int4* vslots, int a,
+                                double u, int step, int8_t* x, double* p, cudaStream_t st);
 cudaError_t plain_general_gates_launch(int CHI, int D, bool f32, const GenArgs& a, cudaStream_t st);
 cudaError_t plain_single_gates_launch(int CHI, int D, bool f32, void* Gamma, const int* vertex, const cd* W, int count,
                                       cudaStream_t st);

@@ -53,6 +53,18 @@ cudaError_t marg_t(const void* G, const double* lam, const int4* vs, int n, cd* 
                                                                                 flag);
     return cudaGetLastError();
 }
+template <int CHI, int D, typename R>
+cudaError_t resid_t(const void* G, const double* lam, const int4* vs, int n, double* out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    plain_residual_kernel<CHI, D, R><<<n * D, PlainShape<CHI, D, R>::CC / 2, 0, st>>>((const C<R>*)G, lam, vs, out);
+    return cudaGetLastError();
+}
+template <int CHI, int D, typename R>
+cudaError_t sample_t(void* G, const double* lam, const int4* vs, int a, double u, int step, int8_t* x, double* p,
+                     cudaStream_t st) {
+    plain_sample_kernel<CHI, D, R><<<1, 32, 0, st>>>((C<R>*)G, lam, vs, a, u, step, x, p);
+    return cudaGetLastError();
+}
 }  // namespace
 
 // CALL(CHI, D, R) for every built shape
@@ -101,6 +113,18 @@ cudaError_t plain_regauge_launch(int CHI, int D, bool f32, const PlainArgs& a, c
 cudaError_t plain_marginals_launch(int CHI, int D, bool f32, const void* G, const double* lam, const int4* vs, int n,
                                    cd* rho, int8_t* sign, int* flag, cudaStream_t st) {
 #define C_(c, d, r) marg_t<c, d, r>(G, lam, vs, n, rho, sign, flag, st)
+    GTQA_PLAIN_DISPATCH(C_)
+#undef C_
+}
+cudaError_t plain_residual_launch(int CHI, int D, bool f32, const void* G, const double* lam, const int4* vs, int n,
+                                  double* out, cudaStream_t st) {
+#define C_(c, d, r) resid_t<c, d, r>(G, lam, vs, n, out, st)
+    GTQA_PLAIN_DISPATCH(C_)
+#undef C_
+}
+cudaError_t plain_sample_launch(int CHI, int D, bool f32, void* G, const double* lam, const int4* vs, int a, double u,
+                                int step, int8_t* x, double* p, cudaStream_t st) {
+#define C_(c, d, r) sample_t<c, d, r>(G, lam, vs, a, u, step, x, p, st)
     GTQA_PLAIN_DISPATCH(C_)
 #undef C_
 }

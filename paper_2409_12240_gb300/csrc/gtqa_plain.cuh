@@ -415,6 +415,99 @@ __global__ void plain_marginals_kernel(const C<R>* Gamma, const double* lam, con
     }
 }
 
+// Residual R of the local-orthogonality condition (App. C) on the plain layout: one block of
+// max(CHI^2/2, 1) threads per (vertex, slot) item whose slot holds a bond,
+//   D_k[j, j'] = delta_{j j'} [lambda_k[j] > 0] - sum_{i, J \ j_k} Gamma[i, J(j)] conj(Gamma[i, J(j')])
+//                prod_{l != k} lambda_l[j_l]^2
+// in FP64 (complex64 Gamma is widened), then its trace norm (FP64 one-sided Jacobi), added to
+// *out.  The caller divides the sum by 2|E|.
+template <int CHI, int D, typename R>
+__global__ void plain_residual_kernel(const C<R>* Gamma, const double* lam, const int4* vslots, double* out) {
+    constexpr int H = PlainShape<CHI, D, R>::H, CC = CHI * CHI, NO = H / CHI;
+    __shared__ cd A[CC];
+    __shared__ double tn;
+    __shared__ int flag;
+    const int v = blockIdx.x / D, k = blockIdx.x % D;
+    const int4 sl = vslots[v];
+    const int ek = plain_slot_edge(sl, k);
+    if (ek < 0) return;   // a phantom slot: the whole block leaves
+    const int g = threadIdx.x;
+    const C<R>* gv = Gamma + (size_t)v * 2 * H;
+    int sk = 1;   // stride of slot k, CHI^(D-1-k)
+    for (int l = D - 1; l > k; --l) sk *= CHI;
+    for (int r = g; r < CC; r += blockDim.x) {
+        const int j = r / CHI, jp = r % CHI;
+        cd acc = cd{0.0, 0.0};
+        for (int q = 0; q < NO; ++q) {
+            // q runs over the indices of the other slots (last slot fastest)
+            int rem = q, base = 0, stride = 1;
+            double w = 1.0;
+            for (int l = D - 1; l >= 0; --l) {
+                if (l != k) {
+                    const int idx = rem % CHI;
+                    rem /= CHI;
+                    const double lv = lam_get(lam, CHI, plain_slot_edge(sl, l), idx);
+                    w *= lv * lv;
+                    base += idx * stride;
+                }
+                stride *= CHI;
+            }
+            for (int i = 0; i < 2; ++i) {
+                const cd x = ccast<double>(gv[i * H + base + j * sk]), y = ccast<double>(gv[i * H + base + jp * sk]);
+                acc = cfmac(y, w * x, acc);
+            }
+        }
+        const double act = (j == jp && lam_get(lam, CHI, ek, j) > 0.0) ? 1.0 : 0.0;
+        A[r] = cd{act - acc.x, -acc.y};
+    }
+    if (g == 0) tn = 0.0;
+    __syncthreads();
+    BlockGroup grp{&flag};
+    jacobi_svd<CHI, double, BlockGroup, false>(A, nullptr, g, grp, group_mask<CHI>(), 1e-15, 60, false);
+    __syncthreads();
+    if (g < CHI) {
+        double c2 = 0.0;
+        for (int r = 0; r < CHI; ++r) c2 += norm2(A[g * CHI + r]);
+        atomicAdd(&tn, sqrt(c2));
+    }
+    __syncthreads();
+    if (g == 0) atomicAdd(out, tn);
+}
+
+// One step of the measurement sampling of Sec. IV A on the plain layout (one warp, vertex a):
+// p0 = rho_a[0][0] as in plain_marginals_kernel, the outcome x_a = +1 if u < p0 (else -1) and its
+// probability, then the projection of Eq. (projection): the other physical component of
+// Gamma_a is zeroed.
+template <int CHI, int D, typename R>
+__global__ void plain_sample_kernel(C<R>* Gamma, const double* lam, const int4* vslots, int a, double u, int step,
+                                    int8_t* x_out, double* p_out) {
+    constexpr int H = PlainShape<CHI, D, R>::H;
+    const int lane = threadIdx.x & 31;
+    const int4 sl = vslots[a];
+    C<R>* g = Gamma + (size_t)a * 2 * H;
+    double r00 = 0.0, r11 = 0.0;
+    for (int r = lane; r < H; r += 32) {
+        int rem = r;
+        double wgt = 1.0;
+        for (int k = D - 1; k >= 0; --k) {
+            const double l = lam_get(lam, CHI, plain_slot_edge(sl, k), rem % CHI);
+            wgt *= l * l;
+            rem /= CHI;
+        }
+        r00 += wgt * norm2(ccast<double>(g[r]));
+        r11 += wgt * norm2(ccast<double>(g[H + r]));
+    }
+    r00 = group_sum<32>(r00, 0xffffffffu);
+    r11 = group_sum<32>(r11, 0xffffffffu);
+    const double p0 = r00 / (r00 + r11);
+    const int keep = u < p0 ? 0 : 1;
+    if (lane == 0) {
+        x_out[a] = keep == 0 ? 1 : -1;
+        p_out[step] = keep == 0 ? p0 : r11 / (r00 + r11);
+    }
+    for (int r = lane; r < H; r += 32) g[(1 - keep) * H + r] = C<R>{(R)0, (R)0};
+}
+
 // ---------------------------------------------------------------------------
 // CHI = 16, degree 3: the simple update of a diagonal gate (App. E) in QR-reduced form, one
 // block of 512 threads per edge.  The four blocks A_{x,i}[J, j] = w_x[J] Gamma_x[i][j][J]

@@ -75,3 +75,26 @@ def run_pair(inst, chi, K, dt, tol, max_iter, layers, precision=0, check_every=1
     finally:
         G.gtqa_destroy(s)
     return out
+
+
+def star_state(Gg, Lg, Mg, edges, inc, a):
+    """The star of vertex a (a and its neighbours, a's edges in slot order) as an oracle state
+    with a's Gamma and the messages into a; the neighbours' tensors are not used."""
+    es = inc[a]
+    nb = [int(edges[e][1] if edges[e][0] == a else edges[e][0]) for e in es]
+    k = len(es)
+    star_edges = np.array([[0, q + 1] for q in range(k)], dtype=np.int64)
+    C = Gg.shape[2]
+    Gs = np.zeros((k + 1,) + Gg.shape[1:], dtype=np.complex128)
+    Gs[0] = Gg[a]
+    Gs[1:, :, 0, 0, 0] = 1.0
+    Ls = np.stack([Lg[e] for e in es])
+    st = O.from_padded(k + 1, star_edges, Gs, Ls)
+    msgs = {}
+    for q, e in enumerate(es):
+        d = st.lam[q].size
+        inward = 2 * e + (0 if edges[e][0] == nb[q] else 1)    # m_{nb -> a}
+        outward = 2 * e + (0 if edges[e][0] == a else 1)      # m_{a -> nb}
+        msgs[(q, 1)] = np.array(Mg[inward, :d, :d])
+        msgs[(q, 0)] = np.array(Mg[outward, :d, :d])
+    return st, msgs

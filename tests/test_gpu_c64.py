@@ -42,7 +42,8 @@ def test_c64_layers_follow_the_oracle(chi):
 def test_c64_against_fp64_next_to_mixed(chi):
     """n = 1000, Gaussian J and h ~ N(0, 0.1), 12 layers of a 1000-layer schedule (dt = 0.2),
     tol 1e-8: the complex64 mode's per-vertex marginal error against the FP64 path stays below
-    5e-3, and the mixed mode is at least as accurate (the reason for its FP64 stages)."""
+    5e-5 (it reached 1.4e-3 at chi = 8 when FP32-noise singular values were kept), and the mixed
+    mode is at least as accurate (the reason for its FP64 stages)."""
     G = U.lib()
     inst = make_instance(1000, 1, J="gauss", h_std=0.1)
     K, dt, tol, mi, layers = 1000, 0.2, 1e-8, 100, 12
@@ -57,7 +58,7 @@ def test_c64_against_fp64_next_to_mixed(chi):
     e_c64 = float(np.abs(rho[G.GTQA_C64] - rho[G.GTQA_FP64]).max())
     e_mix = float(np.abs(rho[G.GTQA_MIXED] - rho[G.GTQA_FP64]).max())
     print(f"chi={chi}: max |rho - rho_fp64| complex64 {e_c64:.3e}, mixed {e_mix:.3e}")
-    assert e_c64 < 5e-3, e_c64
+    assert e_c64 < 5e-5, e_c64
     assert e_mix <= e_c64 + 1e-12, (e_mix, e_c64)
 
 

@@ -95,3 +95,37 @@ def test_chi16_single_qubit_gates_and_entropy():
         assert abs(G.gtqa_entropy(s, cut) - O.approx_entanglement_entropy(st, cut.astype(bool))) < 1e-9
     finally:
         G.gtqa_destroy(s)
+
+
+def test_chi16_n1000_properties_and_sampled_oracle_checks():
+    """chi = 16 at n = 1000 (Gaussian J, h ~ N(0, 0.1), 4 layers of a 1000-layer schedule,
+    dt = 0.2, FP64): marginals are unit-trace Hermitian PSD, and after the gates of layer 5 and
+    a warm-start BP to 1e-12 the messages of sampled vertices satisfy Eq. (local_consistency) as
+    evaluated by the oracle from the device's tensors and incoming messages."""
+    G = U.lib()
+    inst = make_instance(1000, 1)
+    K, dt, tol, mi = 1000, 0.2, 1e-12, 200
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 16, inst.colour, G.gtqa_options_init(precision=G.GTQA_FP64))
+    try:
+        G.gtqa_anneal(s, 1, 4, K, dt, tol, mi)
+        rho, _ = G.gtqa_marginals(s)
+        tr = rho[:, 0, 0].real + rho[:, 1, 1].real
+        assert np.abs(tr - 1).max() < 1e-12
+        assert np.abs(rho - np.conj(np.swapaxes(rho, 1, 2))).max() < 1e-12
+        assert np.linalg.eigvalsh(rho).min() > -1e-12
+        G.gtqa_trotter_layer(s, 5 / K, dt)
+        it, dist, conv = G.gtqa_bp_sweep(s, tol, mi, G.GTQA_BP_WARM_START)
+        assert conv, (it, dist)
+        Gg, Lg, Mg = G.gtqa_get_state(s)
+    finally:
+        G.gtqa_destroy(s)
+    assert Lg.shape[1] == 16   # the bond storage of the chi = 16 kernels
+    inc = O.incidence(inst.n, inst.edges)
+    rng = np.random.default_rng(12)
+    for a in rng.choice(inst.n, size=12, replace=False):
+        st, msgs = U.star_state(Gg, Lg, Mg, inst.edges, inc, int(a))
+        T = O.symmetric_gauge(st)
+        for q in range(len(inc[a])):
+            upd = O.message_update(st, T, msgs, 0, q)
+            upd = upd / np.trace(upd)
+            assert np.abs(upd - msgs[(q, 0)]).max() < 1e-8, (int(a), q, np.abs(upd - msgs[(q, 0)]).max())

@@ -1,6 +1,6 @@
 """GPU parity at the shapes of the other workloads: the batched uneven configuration
 (256 instances, n uniform over even values in [50, 1000], chi = 4, dt = 0.05), the
-bond-dimension sweep at n = 1000 (chi in {2, 4, 8}, Gaussian and ferromagnetic
+bond-dimension sweep at n = 1000 (chi in {2, 4, 8}, Gaussian, ferromagnetic and MaxCut
 couplings, FP64 against mixed), and the n = 100000, chi = 8 scale configuration
 (properties and oracle-computed local checks on sampled vertices)."""
 from __future__ import annotations
@@ -62,12 +62,13 @@ def test_batched_uneven_instances_match_single_runs_and_oracle():
 
 
 @pytest.mark.parametrize("chi", [2, 4, 8])
-@pytest.mark.parametrize("J", ["ferro", "gauss"])
+@pytest.mark.parametrize("J", ["ferro", "maxcut", "gauss"])
 def test_chi_sweep_mixed_against_fp64(chi, J):
-    """n = 1000: J = +1, h = 0 (degenerate) and Gaussian J, h; the mixed path against the FP64
-    path, per vertex, after 12 layers of a 1000-layer schedule (dt = 0.2)."""
+    """n = 1000: J = +1 or J = -1 (the MaxCut couplings of Sec. IV A) with h = 0, both
+    degenerate, and Gaussian J, h; the mixed path against the FP64 path, per vertex, after 12
+    layers of a 1000-layer schedule (dt = 0.2)."""
     G = U.lib()
-    inst = make_instance(1000, 1, J=J, h_std=0.0 if J == "ferro" else 0.1)
+    inst = make_instance(1000, 1, J=J, h_std=0.1 if J == "gauss" else 0.0)
     K, dt, tol, mi, layers = 1000, 0.2, 1e-8, 100, 12
     rho = {}
     for prec in (G.GTQA_FP64, G.GTQA_MIXED):
@@ -81,29 +82,6 @@ def test_chi_sweep_mixed_against_fp64(chi, J):
     assert err < 1e-4, err
     if J == "gauss":
         assert _clear_signs_equal(rho[G.GTQA_MIXED], rho[G.GTQA_FP64])
-
-
-def _star(Gg, Lg, Mg, edges, inc, a):
-    """The star of vertex a (a and its neighbours, a's edges in slot order) as an oracle state
-    with a's Gamma and the messages into a; the neighbours' tensors are not used."""
-    es = inc[a]
-    nb = [int(edges[e][1] if edges[e][0] == a else edges[e][0]) for e in es]
-    k = len(es)
-    star_edges = np.array([[0, q + 1] for q in range(k)], dtype=np.int64)
-    C = Gg.shape[2]
-    Gs = np.zeros((k + 1,) + Gg.shape[1:], dtype=np.complex128)
-    Gs[0] = Gg[a]
-    Gs[1:, :, 0, 0, 0] = 1.0
-    Ls = np.stack([Lg[e] for e in es])
-    st = O.from_padded(k + 1, star_edges, Gs, Ls)
-    msgs = {}
-    for q, e in enumerate(es):
-        d = st.lam[q].size
-        inward = 2 * e + (0 if edges[e][0] == nb[q] else 1)    # m_{nb -> a}
-        outward = 2 * e + (0 if edges[e][0] == a else 1)      # m_{a -> nb}
-        msgs[(q, 1)] = np.array(Mg[inward, :d, :d])
-        msgs[(q, 0)] = np.array(Mg[outward, :d, :d])
-    return st, msgs
 
 
 def test_scale_n100000_chi8_properties_and_sampled_oracle_checks():
@@ -132,7 +110,7 @@ def test_scale_n100000_chi8_properties_and_sampled_oracle_checks():
     inc = O.incidence(inst.n, inst.edges)
     rng = np.random.default_rng(11)
     for a in rng.choice(inst.n, size=16, replace=False):
-        st, msgs = _star(Gg, Lg, Mg, inst.edges, inc, int(a))
+        st, msgs = U.star_state(Gg, Lg, Mg, inst.edges, inc, int(a))
         T = O.symmetric_gauge(st)
         for q in range(len(inc[a])):
             upd = O.message_update(st, T, msgs, 0, q)

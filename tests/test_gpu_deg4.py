@@ -122,14 +122,9 @@ def test_four_regular_unsupported_calls_and_state_round_trip():
     try:
         G.gtqa_anneal(s, 1, 2, 10, 0.2, 1e-10, 100)
         lib = G.load()
-        x = np.zeros(inst.n, dtype=np.int8)
-        order = np.arange(inst.n, dtype=np.int32)
-        u = np.full(inst.n, 0.5)
-        assert lib.gtqa_sample(s, inst.n, order.ctypes.data, u.ctypes.data, 1e-8, 10, x.ctypes.data, None) == \
-            G.GTQA_ERR_UNSUPPORTED
-        import ctypes
-        R = ctypes.c_double()
-        assert lib.gtqa_residual(s, ctypes.byref(R)) == G.GTQA_ERR_UNSUPPORTED
+        # no persistent launch to tune or capture on the plain path
+        assert lib.gtqa_autotune(s, 0.5, 0.2, 1e-8, 10, None) == G.GTQA_ERR_UNSUPPORTED
+        assert lib.gtqa_anneal_graph(s, 3, 4, 10, 0.2, 1e-10, 100) == G.GTQA_ERR_UNSUPPORTED
         Gm, L, M = G.gtqa_get_state(s)
         assert Gm.shape == (inst.n, 2, 4, 4, 4, 4)
         rho0, _ = G.gtqa_marginals(s)
