@@ -39,6 +39,18 @@ def test_strerror_codes(G):
     assert G.strerror(99) == "unknown error code"
 
 
+def test_options_init_selects_the_precision_default_cutoffs(G):
+    """The initialiser leaves both cut-offs at 0, which gtqa_create reads as the precision's own
+    default (1e-14 / 1e-13, or 1e-7 / 1e-6 in the complex64 mode); writing the FP64 values there
+    made complex64 states keep FP32-noise singular values."""
+    o = G.gtqa_options()
+    G.load().gtqa_options_init(ctypes.byref(o))
+    assert o.precision == G.GTQA_FP64 and o.svd_cutoff == 0.0 and o.eig_cutoff == 0.0
+    assert o.cuda_stream is None
+    o2 = G.gtqa_options_init(precision=G.GTQA_C64, svd_cutoff=1e-6)
+    assert o2.precision == G.GTQA_C64 and o2.svd_cutoff == 1e-6 and o2.eig_cutoff == 0.0
+
+
 @pytest.mark.parametrize("n,seed", [(16, 0), (50, 1), (1000, 2)])
 def test_library_colouring_is_proper(G, n, seed):
     e = random_regular_graph(n, 3, seed)
