@@ -19,7 +19,10 @@
 //            exact trace-norm distance (App. B); the host reads the distance after every sweep;
 //   regauge  per edge the Vidal gauge transforms from the two messages (App. D "Vidal gauge
 //            finding"), then per vertex the transforms applied to T;
-//   marginals  Eq. (partial_dens) with the environment of Eq. (bp_approx).
+//   marginals  Eq. (partial_dens) with the environment of Eq. (bp_approx);
+//   residual   R of App. C per (vertex, slot), FP64 trace norms (the regauge policy of
+//              Sec. II C reads it on the host);
+//   sampling   the projection step of Sec. IV A for one vertex, then BP and the regauge.
 #pragma once
 
 #include "gtqa_general.cuh"
