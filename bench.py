@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison run")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--ncu-scale", type=int, default=None, metavar="N",
+                   help="short run of the chi = 8 scale configuration's shape at n = N for ncu: five "
+                        "layers, then one gates, one BP (10 sweeps) and one regauge launch")
     p.add_argument("--ncu-case", type=int, default=None, metavar="K0",
                    help="profiling case: anneal layers 1..K0, then one gates launch, one BP launch of 1 sweep "
                         "and, from the same state, one of 21 sweeps (warm start, no regauge); no timing")
@@ -550,10 +553,34 @@ def ncu_case(a):
     print(json.dumps({"ncu_case": a.ncu_case, "precision": a.precision}))
 
 
+def ncu_scale(a):
+    """The shape of the n = 100000, chi = 8 configuration (random 3-regular, seed 2, J ~ N(0,1),
+    h ~ N(0, 0.1), mixed, K = 500, dt = 0.05) at n = a.ncu_scale: layers 1..5 (15 launches), then
+    the gates of layer 6, a 10-sweep BP launch from the warm start and a regauge launch."""
+    from paper_2409_12240_gb300 import gtqa as G
+    from instances import make_instance
+    G.load(build_if_missing=True)
+    inst = make_instance(a.ncu_scale, 2)
+    K, dt, tol, mi = 500, 0.05, 1e-8, 100
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 8, inst.colour, G.gtqa_options_init(precision=G.GTQA_MIXED))
+    try:
+        G.gtqa_anneal(s, 1, 5, K, dt, tol, mi)
+        G.gtqa_trotter_layer(s, 6 / K, dt)
+        G.gtqa_bp_sweep(s, 0.0, 10, G.GTQA_BP_WARM_START)
+        G.gtqa_regauge(s)
+        G.gtqa_marginals(s)
+    finally:
+        G.gtqa_destroy(s)
+    print(json.dumps({"ncu_scale": a.ncu_scale, "chi": 8, "precision": "mixed"}))
+
+
 def main():
     a = parse()
     if a.ncu_case is not None:
         ncu_case(a)
+        return
+    if a.ncu_scale is not None:
+        ncu_scale(a)
         return
     if a.oracle_sample:
         r = oracle_sampled_rate(a.warmup, a.steps, a.budget)
