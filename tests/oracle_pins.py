@@ -571,3 +571,29 @@ def regauge_policy_on_loopy_graphs(seed: int = 0, n: int = 16, K: int = 20, dt: 
             "none_regauged": not any(i["regauged"] for i in infos_c),
             "threshold_rule": all(i["regauged"] == (i["R"] > thr) for i in infos_d),
             "some_skipped": 0 < sum(i["regauged"] for i in infos_d) < layers}
+
+
+def residual_closed_form() -> float:
+    """R of App. C on a hand-built 3-vertex path 0 - 1 - 2 (edges e0 = (0, 1), e1 = (1, 2)) whose
+    value follows by hand.  lambda_e0 = (cos 0.3, sin 0.3), lambda_e1 = (cos 0.7, sin 0.7);
+    Gamma_0[i, j0] = diag(sqrt(1 + 0.05), sqrt(1 - 0.02)); Gamma_2 = identity; Gamma_1[i, j0, j1]
+    = delta(i, j0) c[j1].  Per directed bond the matrix sum_rest Gamma Gamma^* prod_{other} lambda^2
+    is: at vertex 0, diag(1.05, 0.98) (trace norm of I minus it: 0.07); at vertex 2, I (0); at
+    vertex 1 on e0, s I with s = |c0|^2 cos^2 0.7 + |c1|^2 sin^2 0.7 (2 |1 - s|); at vertex 1 on
+    e1, c c^H, since sum_i lambda_e0[i]^2 = 1 (eigenvalues |c|^2 and 0, so |1 - |c|^2| + 1).
+    R divides the sum by 2|E| = 4.  Returns |oracle R - closed form|."""
+    a, b = 0.3, 0.7
+    c = np.array([0.8 + 0.1j, 0.3 - 0.4j])
+    edges = np.array([[0, 1], [1, 2]], dtype=np.int64)
+    inc = O.incidence(3, edges)
+    G0 = np.diag([np.sqrt(1.05), np.sqrt(0.98)]).astype(np.complex128)
+    G2 = np.eye(2, dtype=np.complex128)
+    G1 = np.zeros((2, 2, 2), dtype=np.complex128)
+    for i in range(2):
+        G1[i, i, :] = c
+    lam = [np.array([np.cos(a), np.sin(a)]), np.array([np.cos(b), np.sin(b)])]
+    st = O.VidalState(3, edges, inc, [G0, G1, G2], lam)
+    s = abs(c[0]) ** 2 * np.cos(b) ** 2 + abs(c[1]) ** 2 * np.sin(b) ** 2
+    c2 = float(np.sum(np.abs(c) ** 2))
+    closed = (0.07 + 0.0 + 2 * abs(1 - s) + abs(1 - c2) + 1.0) / 4.0
+    return abs(O.local_orthogonality_residual(st) - closed)

@@ -143,3 +143,21 @@ def test_truncation_keeping_the_smallest_values_caught(monkeypatch):
         return r
     monkeypatch.setattr(O, "np", _np_with(svd=bad_svd))
     assert P.general_gate_truncation_fidelity(0) > 1e-6
+
+
+def test_frobenius_instead_of_trace_norm_in_residual_caught(monkeypatch):
+    """R of App. C uses the trace norm; a Frobenius norm leaves R = 0 after the regauge but
+    changes the closed-form value."""
+    monkeypatch.setattr(O, "trace_norm", lambda A: float(np.linalg.norm(A)))
+    assert P.residual_closed_form() > 1e-3
+
+
+def test_lambda_instead_of_lambda_squared_in_residual_caught(monkeypatch):
+    """Weighting the other slots by lambda instead of lambda^2 (App. C)."""
+    orig = O._scale_slot
+
+    def bad(t, slot, vec):
+        return orig(t, slot, np.sqrt(np.abs(vec)))
+    monkeypatch.setattr(O, "_scale_slot", bad)
+    assert P.residual_closed_form() > 1e-3
+

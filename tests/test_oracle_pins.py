@@ -84,6 +84,10 @@ def test_warm_start_is_fixed_point_after_regauge():
     assert P.warm_start_fixed_point() < 1e-10
 
 
+def test_residual_closed_form():
+    assert P.residual_closed_form() < 1e-14
+
+
 def test_residual_zero_after_regauge():
     # App. C-D: the Vidal gauge from converged messages has R = 0
     assert P.residual_after_regauge() < 1e-9
