@@ -307,7 +307,8 @@ int gtqa_apply_single_qubit_gates(gtqa_state* s, int32_t k, const int32_t* verte
  *   u        float64 [k], host: the caller's uniform random numbers in [0, 1]
  *   x_out    int8 [n], host: +1 / -1 for the sampled qubits, 0 for the others
  *   p_out    float64 [k], host, nullable: the probability of each outcome given the earlier ones
- * For a batched state every step regauges all instances.  Synchronises the stream once.
+ * For a batched state every step regauges all instances.  Synchronises the stream once (on a
+ * plain-path state, see gtqa_create, also after every BP sweep).
  */
 int gtqa_sample(gtqa_state* s, int32_t k, const int32_t* order, const double* u, double tol, int32_t max_iter,
                 int8_t* x_out, double* p_out);
