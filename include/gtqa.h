@@ -62,7 +62,7 @@ extern "C" {
                          delta in complex64; get/set_state convert to and from complex128. */
 #define GTQA_C64 2    /* complex64 with every step in FP32, including the QR/SVD, gauge roots and
                        * normalisation (a reference point for the precision split; plain kernels,
-                       * one instance, degree 3 with chi <= 8 or degree 4 with chi <= 4; default
+                       * one instance, degree 3 with chi <= 16 or degree 4 with chi <= 4; default
                        * cut-offs 1e-7 on singular values and 1e-6 on message eigenvalues) */
 
 /* flags of gtqa_bp_sweep */
@@ -123,7 +123,7 @@ void gtqa_options_init(gtqa_options* opt);
  * with four bonds, Gamma [n][2][CHI]^4; 8 < chi <= 16 gets storage bond dimension 16.  These
  * states, and every state in the GTQA_C64 precision, run on plain per-phase kernels and hold
  * one instance.  The shapes built there are: FP64 with degree 4 and chi <= 4, or degree 3 and
- * 8 < chi <= 16; GTQA_C64 with degree 3 and chi <= 8, or degree 4 and chi <= 4.  Anything else
+ * 8 < chi <= 16; GTQA_C64 with degree 3 and chi <= 16, or degree 4 and chi <= 4.  Anything else
  * returns GTQA_ERR_UNSUPPORTED.  On a plain-path state gtqa_autotune and gtqa_anneal_graph
  * return GTQA_ERR_UNSUPPORTED (there is no persistent launch to tune or capture), and so does
  * gtqa_apply_gates at chi > 8; every other call works as documented.  Its BP reads the

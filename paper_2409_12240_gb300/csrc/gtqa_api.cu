@@ -950,7 +950,7 @@ int d4_interaction(gtqa_state* s, double tZ) {
         return GTQA_ERR_CUDA;
     for (int c = 0; c < s->ncol; ++c) {
         cudaError_t e;
-        if (s->CHI == 16 && !f32(s)) {
+        if (s->CHI == 16) {
             Gate16Args g;
             g.Gamma = s->Gamma;
             g.lam = s->lam;
@@ -963,7 +963,7 @@ int d4_interaction(gtqa_state* s, double tZ) {
             g.stats = s->stats;
             g.chi = s->chi;
             g.svd_cut = s->svd_cutoff;
-            e = ising16_gates_launch(g, s->stream);
+            e = ising16_gates_launch(g, f32(s), s->stream);
         } else {
             GenArgs g;
             g.Gamma = s->Gamma;

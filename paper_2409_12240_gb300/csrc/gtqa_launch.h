@@ -50,7 +50,7 @@ cudaError_t single_gates_launch_mixed(int CHI, void* Gamma, const int* vertex, c
                                       cudaStream_t st);
 
 // the plain path: FP64 (degree 4 with CHI in {2, 4}, degree 3 with CHI = 16) and the complex64
-// mode (f32: degree 3 with CHI in {2, 4, 8}, degree 4 with CHI in {2, 4})
+// mode (f32: degree 3 with CHI in {2, 4, 8, 16}, degree 4 with CHI in {2, 4})
 bool plain_supported(int CHI, int D, bool f32);
 size_t plain_scratch_entries(int CHI, int D, int n, int m);
 cudaError_t plain_bp_init_launch(int CHI, int D, bool f32, const PlainArgs& a, cudaStream_t st);
@@ -66,7 +66,7 @@ cudaError_t plain_sample_launch(int CHI, int D, bool f32, void* Gamma, const dou
 cudaError_t plain_general_gates_launch(int CHI, int D, bool f32, const GenArgs& a, cudaStream_t st);
 cudaError_t plain_single_gates_launch(int CHI, int D, bool f32, void* Gamma, const int* vertex, const cd* W, int count,
                                       cudaStream_t st);
-cudaError_t ising16_gates_launch(const Gate16Args& a, cudaStream_t st);
+cudaError_t ising16_gates_launch(const Gate16Args& a, bool f32, cudaStream_t st);
 
 inline bool phase_shape(bool mixed, int pk, int CHI, size_t* sb, int* tpb) {
     switch (pk) {

@@ -1,5 +1,5 @@
 // Plain-path kernel instantiations.  FP64: degree 4 with CHI in {2, 4}, degree 3 with CHI = 16.
-// Complex64 mode (every step in FP32): degree 3 with CHI in {2, 4, 8}, degree 4 with CHI in {2, 4}.
+// Complex64 mode (every step in FP32): degree 3 with CHI in {2, 4, 8, 16}, degree 4 with CHI in {2, 4}.
 #include "gtqa_launch.h"
 
 namespace gtqa {
@@ -77,6 +77,7 @@ cudaError_t sample_t(void* G, const double* lam, const int4* vs, int a, double u
         if (D == 3 && CHI == 2) return CALL(2, 3, float);                      \
         if (D == 3 && CHI == 4) return CALL(4, 3, float);                      \
         if (D == 3 && CHI == 8) return CALL(8, 3, float);                      \
+        if (D == 3 && CHI == 16) return CALL(16, 3, float);                    \
         if (D == 4 && CHI == 2) return CALL(2, 4, float);                      \
         if (D == 4 && CHI == 4) return CALL(4, 4, float);                      \
     }                                                                          \
@@ -84,7 +85,7 @@ cudaError_t sample_t(void* G, const double* lam, const int4* vs, int a, double u
 
 bool plain_supported(int CHI, int D, bool f32) {
     if (!f32) return (D == 4 && (CHI == 2 || CHI == 4)) || (D == 3 && CHI == 16);
-    return (D == 3 && (CHI == 2 || CHI == 4 || CHI == 8)) || (D == 4 && (CHI == 2 || CHI == 4));
+    return (D == 3 && (CHI == 2 || CHI == 4 || CHI == 8 || CHI == 16)) || (D == 4 && (CHI == 2 || CHI == 4));
 }
 
 size_t plain_scratch_entries(int CHI, int D, int n, int m) {
@@ -151,14 +152,16 @@ cudaError_t plain_single_gates_launch(int CHI, int D, bool f32, void* G, const i
         if (D == 3 && CHI == 2) return single_gates_launch_t<2, 3, ModeC64>(G, v, W, count, st);
         if (D == 3 && CHI == 4) return single_gates_launch_t<4, 3, ModeC64>(G, v, W, count, st);
         if (D == 3 && CHI == 8) return single_gates_launch_t<8, 3, ModeC64>(G, v, W, count, st);
+        if (D == 3 && CHI == 16) return single_gates_launch_t<16, 3, ModeC64>(G, v, W, count, st);
         if (D == 4 && CHI == 2) return single_gates_launch_t<2, 4, ModeC64>(G, v, W, count, st);
         if (D == 4 && CHI == 4) return single_gates_launch_t<4, 4, ModeC64>(G, v, W, count, st);
     }
     return cudaErrorInvalidValue;
 }
-cudaError_t ising16_gates_launch(const Gate16Args& a, cudaStream_t st) {
+cudaError_t ising16_gates_launch(const Gate16Args& a, bool f32, cudaStream_t st) {
     if (a.count <= 0) return cudaSuccess;
-    ising16_gate_kernel<16><<<a.count, 512, 0, st>>>(a);
+    if (f32) ising16_gate_kernel<16, float><<<a.count, 512, 0, st>>>(a);
+    else ising16_gate_kernel<16, double><<<a.count, 512, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -2,8 +2,8 @@
 // bonds for the persistent kernels, or that run every step in FP32.  Shapes built: degree 4
 // with CHI <= 4 (the random 4-regular graphs of Sec. V) and degree 3 with CHI = 16 (the largest
 // bond dimension of the chi sweep), in complex128 (the FP64 precision mode); degree 3 with
-// CHI <= 8 and degree 4 with CHI <= 4 in complex64 with every step in FP32 (the complex64 mode,
-// R = float).  One instance.
+// CHI <= 8 or CHI = 16 and degree 4 with CHI <= 4 in complex64 with every step in FP32 (the
+// complex64 mode, R = float).  One instance.
 //
 // Layout: Gamma and T are [n][2][CHI]^D (slot k = k-th incident edge in ascending id, stride
 // CHI^(D-1-k); phantom slots of vertices with fewer edges have dimension 1 with lambda = e_0);
@@ -517,7 +517,7 @@ __global__ void plain_sample_kernel(C<R>* Gamma, const double* lam, const int4* 
 // (CHI^2 x CHI) live in global scratch; each gets a Householder QR from a group of 128 threads
 // (two rows each) whose sums go through shared memory.  The core
 //   M[(i_a r), (i_b r')] = U[(i_a i_b), (i_a i_b)] sum_j R_{a,i_a}[r, j] lambda_j R_{b,i_b}[r', j]
-// (2 CHI x 2 CHI) has the same singular values as Theta; FP64 one-sided Jacobi (512 threads),
+// (2 CHI x 2 CHI) has the same singular values as Theta; one-sided Jacobi (512 threads),
 // truncation to chi as in App. D "Truncation", and the new Gamma from the reflectors.
 // ---------------------------------------------------------------------------
 struct Gate16Args {
@@ -534,26 +534,27 @@ struct Gate16Args {
     double svd_cut;
 };
 
-template <int CHI>
+template <int CHI, typename R>
 struct Gate16Sm {
+    using CR = C<R>;
     static constexpr int NM = 2 * CHI, NR = CHI * CHI;
-    cd M[NM * NM];
-    cd V[NM * NM];
-    cd vk[4][CHI];
-    double st[4][CHI];        // square roots of the reflector coefficients
-    double w[2][NR];
-    double lab[CHI];
-    cd ph[4];
-    double sig[NM];
+    CR M[NM * NM];
+    CR V[NM * NM];
+    CR vk[4][CHI];
+    R st[4][CHI];             // square roots of the reflector coefficients
+    R w[2][NR];
+    R lab[CHI];
+    CR ph[4];
+    R sig[NM];
     int perm[NM];
-    cd red[4][4][CHI];        // [group][warp][value] partial sums
+    CR red[4][4][CHI];        // [group][warp][value] partial sums
     int keep, flag, nrot;
 };
 
 // sum over the 128 threads of group grp of vals[0..nv) (complex), returned to every thread;
 // red is [4 warps][nv]; named barrier 1 + grp
-template <int NV>
-__device__ __forceinline__ void group128_sum(cd (&vals)[NV], int nv, cd (*red)[16], int grp) {
+template <int NV, typename CR>
+__device__ __forceinline__ void group128_sum(CR (&vals)[NV], int nv, CR (*red)[16], int grp) {
     const int lane = threadIdx.x & 31, wig = (threadIdx.x / 32) & 3;
     for (int q = 0; q < nv; ++q) {
         vals[q].x = group_sum<32>(vals[q].x, 0xffffffffu);
@@ -565,11 +566,15 @@ __device__ __forceinline__ void group128_sum(cd (&vals)[NV], int nv, cd (*red)[1
     asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
 }
 
-template <int CHI>
+// R = double: the FP64 precision mode; R = float: the complex64 mode (QR, Jacobi SVD and the
+// new Gamma in FP32, Gamma stored in complex64; lambda is written as float64).
+template <int CHI, typename R>
 __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
-    constexpr int NM = 2 * CHI, NR = CHI * CHI, H = CHI * CHI * CHI, RPT = NR / 128;
+    using CR = C<R>;
+    constexpr bool R64 = sizeof(R) == 8;
+    constexpr int NM = 2 * CHI, NR = CHI * CHI, H = CHI * CHI * CHI;
     static_assert(NR == 2 * 128, "the 128-thread groups hold two rows each");
-    __shared__ Gate16Sm<CHI> sm;
+    __shared__ Gate16Sm<CHI, R> sm;
     const int tid = threadIdx.x;
     const int e = c.gate_edge[blockIdx.x];
     const int4 ei = c.edge_info[e];
@@ -583,14 +588,14 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
         oe[x][0] = es[os[x][0]];
         oe[x][1] = es[os[x][1]];
     }
-    cd* Xg = c.scratch + (size_t)blockIdx.x * 4 * CHI * NR;   // [blk][col][row]
-    cd* Gam = (cd*)c.Gamma;
+    CR* Xg = reinterpret_cast<CR*>(c.scratch) + (size_t)blockIdx.x * 4 * CHI * NR;   // [blk][col][row]
+    CR* Gam = (CR*)c.Gamma;
     for (int t = tid; t < 2 * NR; t += 512) {
         const int x = t / NR, J = t % NR;
-        sm.w[x][J] = lam_get(c.lam, CHI, oe[x][0], J / CHI) * lam_get(c.lam, CHI, oe[x][1], J % CHI);
+        sm.w[x][J] = (R)(lam_get(c.lam, CHI, oe[x][0], J / CHI) * lam_get(c.lam, CHI, oe[x][1], J % CHI));
     }
-    for (int t = tid; t < CHI; t += 512) sm.lab[t] = c.lam[(size_t)e * CHI + t];
-    if (tid < 4) sm.ph[tid] = c.gate_U[(size_t)blockIdx.x * 16 + 5 * tid];
+    for (int t = tid; t < CHI; t += 512) sm.lab[t] = (R)c.lam[(size_t)e * CHI + t];
+    if (tid < 4) sm.ph[tid] = ccast<R>(c.gate_U[(size_t)blockIdx.x * 16 + 5 * tid]);
     if (tid == 0) sm.nrot = 0;
     __syncthreads();
     for (int t = tid; t < 4 * CHI * NR; t += 512) {
@@ -604,31 +609,31 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
     __syncthreads();
     // ---- Householder QR of the four blocks, 128 threads per block, rows l and l + 128 ----
     const int blk = tid / 128, l = tid % 128;
-    cd* Xb = Xg + (size_t)blk * CHI * NR;
+    CR* Xb = Xg + (size_t)blk * CHI * NR;
     for (int k = 0; k < CHI; ++k) {
-        cd* Xk = Xb + (size_t)k * NR;
-        const cd z = cd{0.0, 0.0};
-        cd x0 = (l >= k) ? Xk[l] : z;
-        cd x1 = Xk[l + 128];
-        cd nv[1] = {cd{norm2(x0) + norm2(x1), 0.0}};
+        CR* Xk = Xb + (size_t)k * NR;
+        const CR z = CR{(R)0, (R)0};
+        CR x0 = (l >= k) ? Xk[l] : z;
+        CR x1 = Xk[l + 128];
+        CR nv[1] = {CR{norm2(x0) + norm2(x1), (R)0}};
         group128_sum<1>(nv, 1, sm.red[blk], blk);
-        const double nrm = nr_sqrt(nv[0].x);
-        const cd xkk = Xk[k];
-        const double a2 = norm2(xkk);
-        const double ra = a2 > 0.0 ? nr_rsqrt(a2) : 0.0;
-        const double axkk = a2 * ra;
-        const cd ph = a2 > 0.0 ? cd{xkk.x * ra, xkk.y * ra} : cd{1.0, 0.0};
-        const double stau = nrm > 0.0 ? nr_rsqrt(nrm * (nrm + axkk)) : 0.0;
-        const double tau = stau * stau;
-        const cd vkk = (axkk + nrm) * ph;
-        const cd v0 = (l == k) ? vkk : x0;
-        const cd v1 = x1;
-        cd d[CHI];
+        const R nrm = nr_sqrt(nv[0].x);
+        const CR xkk = Xk[k];
+        const R a2 = norm2(xkk);
+        const R ra = a2 > (R)0 ? nr_rsqrt(a2) : (R)0;
+        const R axkk = a2 * ra;
+        const CR ph = a2 > (R)0 ? CR{xkk.x * ra, xkk.y * ra} : CR{(R)1, (R)0};
+        const R stau = nrm > (R)0 ? nr_rsqrt(nrm * (nrm + axkk)) : (R)0;
+        const R tau = stau * stau;
+        const CR vkk = (axkk + nrm) * ph;
+        const CR v0 = (l == k) ? vkk : x0;
+        const CR v1 = x1;
+        CR d[CHI];
 #pragma unroll
         for (int cc = 0; cc < CHI; ++cc) {
             d[cc] = z;
             if (cc > k) {
-                const cd* Xc = Xb + (size_t)cc * NR;
+                const CR* Xc = Xb + (size_t)cc * NR;
                 d[cc] = cfmac(v0, Xc[l], cfmac(v1, Xc[l + 128], z));
             }
         }
@@ -636,8 +641,8 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
 #pragma unroll
         for (int cc = 0; cc < CHI; ++cc) {
             if (cc <= k) continue;
-            cd* Xc = Xb + (size_t)cc * NR;
-            const cd td = tau * d[cc];
+            CR* Xc = Xb + (size_t)cc * NR;
+            const CR td = tau * d[cc];
             if (l >= k) Xc[l] = Xc[l] - v0 * td;
             Xc[l + 128] = Xc[l + 128] - v1 * td;
         }
@@ -653,9 +658,9 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
     for (int t = tid; t < NM * NM; t += 512) {
         const int col = t / NM, row = t % NM;
         const int ia = row / CHI, r = row % CHI, ib = col / CHI, rp = col % CHI;
-        const cd* Ra = Xg + (size_t)ia * CHI * NR;          // block (a, ia)
-        const cd* Rb = Xg + (size_t)(2 + ib) * CHI * NR;    // block (b, ib)
-        cd acc = cd{0.0, 0.0};
+        const CR* Ra = Xg + (size_t)ia * CHI * NR;          // block (a, ia)
+        const CR* Rb = Xg + (size_t)(2 + ib) * CHI * NR;    // block (b, ib)
+        CR acc = CR{(R)0, (R)0};
         const int j0 = r > rp ? r : rp;
         for (int j = j0; j < CHI; ++j) acc = cfma(sm.lab[j] * Ra[(size_t)j * NR + r], Rb[(size_t)j * NR + rp], acc);
         sm.M[t] = sm.ph[2 * ia + ib] * acc;
@@ -663,12 +668,13 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
     __syncthreads();
     int nrot = 0;
     BlockGroup grp{&sm.flag};
-    const int sweeps = jacobi_svd<NM, double, BlockGroup, true, true>(sm.M, sm.V, tid, grp, group_mask<NM>(), 1e-15, 60,
-                                                                      true, &nrot, 3e-8);
+    const int sweeps = jacobi_svd<NM, R, BlockGroup, true, R64>(sm.M, sm.V, tid, grp, group_mask<NM>(),
+                                                                (R)(R64 ? 1e-15 : 1e-6), 60, true, &nrot,
+                                                                (R)(R64 ? 3e-8 : 1e-3));
     if (nrot) atomicAdd(&sm.nrot, nrot);
     __syncthreads();
     for (int cc = tid; cc < NM; cc += 512) {
-        double s2 = 0.0;
+        R s2 = (R)0;
         for (int r = 0; r < NM; ++r) s2 += norm2(sm.M[cc * NM + r]);
         sm.sig[cc] = nr_sqrt(s2);
     }
@@ -677,21 +683,21 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
     __syncthreads();
     if (tid < NM) {   // lane r holds the r-th largest singular value (NM = 32: one warp)
         const unsigned mk = group_mask<NM>();
-        const double sv = sm.sig[sm.perm[tid]];
-        const double smax = sm.sig[sm.perm[0]];
-        const int cnt = __popc(__ballot_sync(mk, sv > c.svd_cut * smax));
+        const R sv = sm.sig[sm.perm[tid]];
+        const R smax = sm.sig[sm.perm[0]];
+        const int cnt = __popc(__ballot_sync(mk, sv > (R)c.svd_cut * smax));
         int keep = cnt < c.chi ? cnt : c.chi;
         if (keep < 1) keep = 1;
-        const double s2 = sv * sv;
-        const double kept = group_sum<NM>(tid < keep ? s2 : 0.0, mk);
-        const double drop = group_sum<NM>(tid < keep ? 0.0 : s2, mk);
-        const double inv = kept > 0.0 ? nr_rsqrt(kept) : 0.0;
-        if (tid < CHI) c.lam[(size_t)e * CHI + tid] = (tid < keep) ? sv * inv : 0.0;
+        const R s2 = sv * sv;
+        const R kept = group_sum<NM>(tid < keep ? s2 : (R)0, mk);
+        const R drop = group_sum<NM>(tid < keep ? (R)0 : s2, mk);
+        const R inv = kept > (R)0 ? nr_rsqrt(kept) : (R)0;
+        if (tid < CHI) c.lam[(size_t)e * CHI + tid] = (tid < keep) ? (double)(sv * inv) : 0.0;
         if (tid == 0) {
-            const double tot = kept + drop;
-            const double disc = tot > 0.0 ? drop * nr_rcp(tot) : 0.0;
-            atomicAdd(&c.stats[0], disc);
-            atomicAdd(&c.stats[1], 2.0 * log1p(-disc));   // Eq. (gate_fidelity)
+            const R tot = kept + drop;
+            const R disc = tot > (R)0 ? drop * nr_rcp(tot) : (R)0;
+            atomicAdd(&c.stats[0], (double)disc);
+            atomicAdd(&c.stats[1], 2.0 * log1p(-(double)disc));   // Eq. (gate_fidelity)
             atomicAdd(&c.stats[2], (double)sweeps * (NM - 1) * (NM / 2));
             atomicAdd(&c.stats[3], (double)sm.nrot);
             sm.keep = keep;
@@ -701,11 +707,11 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
     const int keep = sm.keep;
     // ---- new Gamma: the reflectors of each block applied to U (side a) / V^* (side b) ----
     const int x = blk >> 1, i = blk & 1;
-    cd E0[CHI], E1[CHI];
+    CR E0[CHI], E1[CHI];
 #pragma unroll
     for (int cc = 0; cc < CHI; ++cc) {
-        E0[cc] = cd{0.0, 0.0};
-        E1[cc] = cd{0.0, 0.0};
+        E0[cc] = CR{(R)0, (R)0};
+        E1[cc] = CR{(R)0, (R)0};
         if (l < CHI && cc < keep) {
             const int pc = sm.perm[cc];
             const int row = i * CHI + l;
@@ -713,13 +719,13 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
         }
     }
     for (int k = CHI - 1; k >= 0; --k) {
-        const double st = sm.st[blk][k];
-        const cd* Xk = Xb + (size_t)k * NR;
-        const cd v0 = st * ((l == k) ? sm.vk[blk][k] : ((l > k) ? Xk[l] : cd{0.0, 0.0}));
-        const cd v1 = st * Xk[l + 128];
-        cd d[CHI];
+        const R st = sm.st[blk][k];
+        const CR* Xk = Xb + (size_t)k * NR;
+        const CR v0 = st * ((l == k) ? sm.vk[blk][k] : ((l > k) ? Xk[l] : CR{(R)0, (R)0}));
+        const CR v1 = st * Xk[l + 128];
+        CR d[CHI];
 #pragma unroll
-        for (int cc = 0; cc < CHI; ++cc) d[cc] = cfmac(v0, E0[cc], cfmac(v1, E1[cc], cd{0.0, 0.0}));
+        for (int cc = 0; cc < CHI; ++cc) d[cc] = cfmac(v0, E0[cc], cfmac(v1, E1[cc], CR{(R)0, (R)0}));
         group128_sum<CHI>(d, CHI, sm.red[blk], blk);
 #pragma unroll
         for (int cc = 0; cc < CHI; ++cc) {
@@ -727,8 +733,8 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
             E1[cc] = E1[cc] - v1 * d[cc];
         }
     }
-    const double w0 = sm.w[x][l], w1 = sm.w[x][l + 128];
-    const double iw0 = w0 > 0.0 ? nr_rcp(w0) : 0.0, iw1 = w1 > 0.0 ? nr_rcp(w1) : 0.0;
+    const R w0 = sm.w[x][l], w1 = sm.w[x][l + 128];
+    const R iw0 = w0 > (R)0 ? nr_rcp(w0) : (R)0, iw1 = w1 > (R)0 ? nr_rcp(w1) : (R)0;
     const size_t base = (size_t)vtx[x] * 2 * H + (size_t)i * H;
     const size_t o0 = (l / CHI) * sstride<CHI>(os[x][0]) + (l % CHI) * sstride<CHI>(os[x][1]);
     const size_t o1 = ((l + 128) / CHI) * sstride<CHI>(os[x][0]) + ((l + 128) % CHI) * sstride<CHI>(os[x][1]);
@@ -737,7 +743,6 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
         Gam[base + cc * sstride<CHI>(slot[x]) + o0] = iw0 * E0[cc];
         Gam[base + cc * sstride<CHI>(slot[x]) + o1] = iw1 * E1[cc];
     }
-    (void)RPT;
 }
 
 }  // namespace gtqa

@@ -62,19 +62,47 @@ def test_c64_against_fp64_next_to_mixed(chi):
     assert e_mix <= e_c64 + 1e-12, (e_mix, e_c64)
 
 
-def test_c64_rejected_shapes():
+def test_mixed_chi16_rejected():
     G = U.lib()
     inst = make_instance(16, 0)
     lib = G.load()
     import ctypes
-    opt = G.gtqa_options_init(precision=G.GTQA_C64)
+    opt = G.gtqa_options_init(precision=G.GTQA_MIXED)
     h = ctypes.c_void_p()
     e = np.ascontiguousarray(inst.edges, dtype=np.int32)
     J = np.ascontiguousarray(inst.J)
     hh = np.ascontiguousarray(inst.h)
-    # chi 16 has no complex64 kernels
+    # chi 16 runs on the plain kernels, which have the FP64 and complex64 modes only
     assert lib.gtqa_create(inst.n, inst.m, e.ctypes.data, None, J.ctypes.data, hh.ctypes.data, 16, ctypes.byref(opt),
                            ctypes.byref(h)) == G.GTQA_ERR_UNSUPPORTED
+
+
+def test_c64_chi16_follows_the_oracle():
+    """The complex64 mode at chi = 16 (FP32 QR, 32 x 32 Jacobi SVD and BP): n = 12, 3-regular,
+    K = 20, dt = 0.3, 6 layers (bonds reach 16), within 1e-4 of the oracle on marginals and
+    lambda."""
+    G = U.lib()
+    inst = make_instance(12, 6)
+    K, dt, tol, mi = 20, 0.3, 1e-6, 100
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 16, inst.colour, G.gtqa_options_init(precision=G.GTQA_C64))
+    st = O.plus_state(inst.n, inst.edges)
+    try:
+        n, m, C, _ = G.gtqa_sizes(s)
+        assert C == 16
+        for k in range(1, 7):
+            G.gtqa_trotter_layer(s, k / K, dt)
+            G.gtqa_bp_sweep(s, tol, mi)
+            tZ, tX = O.schedule(k, K, dt)
+            st, _ = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, 16, 1e-12, 200)
+        rho_g, _ = G.gtqa_marginals(s)
+        _, Lg, _ = G.gtqa_get_state(s)
+        _, Lo = O.to_padded(st, 16)
+        e_rho = float(np.abs(rho_g - O.reduced_density_matrices(st)).max())
+        e_lam = float(np.abs(Lg - Lo).max())
+        print(f"complex64 chi=16: marginals {e_rho:.2e}, lambda {e_lam:.2e}")
+        assert e_rho < 1e-4 and e_lam < 1e-4, (e_rho, e_lam)
+    finally:
+        G.gtqa_destroy(s)
 
 
 def test_c64_on_a_four_regular_graph_follows_the_oracle():
