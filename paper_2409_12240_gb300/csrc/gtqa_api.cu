@@ -146,6 +146,11 @@ int storage_chi(int chi) {
 
 bool mixed(const gtqa_state* s) { return s->precision == GTQA_MIXED; }
 bool f32(const gtqa_state* s) { return s->precision == GTQA_C64; }
+// precision selector of the plain kernels: 0 FP64, 1 mixed, 2 complex64
+int pm(const gtqa_state* s) { return s->precision == GTQA_FP64 ? 0 : (s->precision == GTQA_MIXED ? 1 : 2); }
+// messages held as the absolute m in complex64 (complex64 mode, and the mixed mode on the plain
+// path); the persistent mixed path holds m - m0 instead
+bool abs32(const gtqa_state* s) { return f32(s) || (s->precision == GTQA_MIXED && s->plain); }
 bool f32store(const gtqa_state* s) { return s->precision != GTQA_FP64; }
 size_t elem_bytes(const gtqa_state* s) { return f32store(s) ? sizeof(cf) : sizeof(cd); }
 size_t gamma_elems(const gtqa_state* s) {
@@ -600,14 +605,15 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
             ncol = gcol[e] + 1 > ncol ? gcol[e] + 1 : ncol;
         }
     }
-    // vertex degree 4 (Sec. V's 4-regular graphs) or storage bond dimension 16: the plain
-    // kernels, FP64, one instance
+    // vertex degree 4 (Sec. V's 4-regular graphs), storage bond dimension 16 or the complex64
+    // mode: the plain kernels, one instance
     int Dmax = 0;
     for (long long v = 0; v < N; ++v) Dmax = std::max(Dmax, deg[v]);
     const int Dst = Dmax == 4 ? 4 : 3;
     const bool c64 = o.precision == GTQA_C64;
     const bool plain = Dst == 4 || storage_chi(chi) == 16 || c64;
-    if (plain && (B != 1 || o.precision == GTQA_MIXED || !plain_supported(storage_chi(chi), Dst, c64)))
+    const int pmode = o.precision == GTQA_FP64 ? 0 : (o.precision == GTQA_MIXED ? 1 : 2);
+    if (plain && (B != 1 || !plain_supported(storage_chi(chi), Dst, pmode)))
         return GTQA_ERR_UNSUPPORTED;
     gtqa_state* s = new (std::nothrow) gtqa_state();
     if (!s) return GTQA_ERR_OOM;
@@ -782,7 +788,7 @@ int read_messages(gtqa_state* s, int cur, std::vector<cd>& out) {
             return GTQA_ERR_CUDA;
         return cuda_ok(s, cudaStreamSynchronize(s->stream)) ? GTQA_OK : GTQA_ERR_CUDA;
     }
-    if (f32(s)) {
+    if (abs32(s)) {
         std::vector<cf> d(mel);
         if (!cuda_ok(s, cudaMemcpyAsync(d.data(), s->msg[cur], mel * sizeof(cf), cudaMemcpyDeviceToHost, s->stream)) ||
             !cuda_ok(s, cudaStreamSynchronize(s->stream)))
@@ -920,7 +926,7 @@ int d4_mixing(gtqa_state* s, double t) {
     if ((rc = grow_pair(s, &s->sq_vertex, &s->sq_W, 4, s->sq_cap, (size_t)s->n))) return rc;
     if (!cuda_ok(s, cudaMemcpyAsync(s->sq_W, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, s->stream)))
         return GTQA_ERR_CUDA;
-    if (plain_single_gates_launch(s->CHI, s->D, f32(s), s->Gamma, s->allv, s->sq_W, s->n, s->stream) != cudaSuccess)
+    if (plain_single_gates_launch(s->CHI, s->D, pm(s), s->Gamma, s->allv, s->sq_W, s->n, s->stream) != cudaSuccess)
         return d4_fail(s);
     s->launches += 1;
     return GTQA_OK;
@@ -963,7 +969,7 @@ int d4_interaction(gtqa_state* s, double tZ) {
             g.stats = s->stats;
             g.chi = s->chi;
             g.svd_cut = s->svd_cutoff;
-            e = ising16_gates_launch(g, f32(s), s->stream);
+            e = ising16_gates_launch(g, pm(s), s->stream);
         } else {
             GenArgs g;
             g.Gamma = s->Gamma;
@@ -976,7 +982,7 @@ int d4_interaction(gtqa_state* s, double tZ) {
             g.stats = s->stats;
             g.chi = s->chi;
             g.svd_cut = s->svd_cutoff;
-            e = plain_general_gates_launch(s->CHI, s->D, f32(s), g, s->stream);
+            e = plain_general_gates_launch(s->CHI, s->D, pm(s), g, s->stream);
         }
         if (e != cudaSuccess) return d4_fail(s);
         s->launches += 1;
@@ -993,7 +999,7 @@ int d4_trotter(gtqa_state* s, double tZ, double tXpre, double tXpost) {
 }
 
 int d4_regauge(gtqa_state* s) {
-    if (plain_regauge_launch(s->CHI, s->D, f32(s), d4_args(s, s->cur4), s->msg[s->cur4], s->eig_cutoff,
+    if (plain_regauge_launch(s->CHI, s->D, pm(s), d4_args(s, s->cur4), s->msg[s->cur4], s->eig_cutoff,
                              s->svd_cutoff, s->stream) != cudaSuccess)
         return d4_fail(s);
     s->launches += 2;
@@ -1007,7 +1013,7 @@ int d4_bp(gtqa_state* s, double tol, int max_iter, uint32_t flags, int32_t* iter
     PlainArgs a = d4_args(s, cur);
     a.warm = (flags & GTQA_BP_WARM_START) ? 1 : 0;
     a.msg_nxt = s->msg[cur];   // the init kernel writes the warm start where the first sweep reads
-    if (s->n > 0 && plain_bp_init_launch(s->CHI, s->D, f32(s), a, s->stream) != cudaSuccess) return d4_fail(s);
+    if (s->n > 0 && plain_bp_init_launch(s->CHI, s->D, pm(s), a, s->stream) != cudaSuccess) return d4_fail(s);
     s->launches += 1;
     int it = 0;
     double dist = 0.0;
@@ -1015,7 +1021,7 @@ int d4_bp(gtqa_state* s, double tol, int max_iter, uint32_t flags, int32_t* iter
     for (; it < max_iter;) {
         if (!cuda_ok(s, cudaMemsetAsync(s->acc, 0, sizeof(double), s->stream))) return GTQA_ERR_CUDA;
         PlainArgs w = d4_args(s, cur);
-        if (plain_bp_sweep_launch(s->CHI, s->D, f32(s), w, s->stream) != cudaSuccess) return d4_fail(s);
+        if (plain_bp_sweep_launch(s->CHI, s->D, pm(s), w, s->stream) != cudaSuccess) return d4_fail(s);
         s->launches += 2;
         double acc = 0.0;
         if (!cuda_ok(s, cudaMemcpyAsync(&acc, s->acc, sizeof(double), cudaMemcpyDeviceToHost, s->stream)) ||
@@ -1056,7 +1062,7 @@ int d4_bp(gtqa_state* s, double tol, int max_iter, uint32_t flags, int32_t* iter
 // Unnormalised residual sum of App. C over the 2m directed bonds, added to s->rbuf.
 cudaError_t residual_launch(gtqa_state* s) {
     if (s->plain)
-        return plain_residual_launch(s->CHI, s->D, f32(s), s->Gamma, s->lam, s->vslots4, s->n, s->rbuf, s->stream);
+        return plain_residual_launch(s->CHI, s->D, pm(s), s->Gamma, s->lam, s->vslots4, s->n, s->rbuf, s->stream);
     return mixed(s) ? residual_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream)
                     : residual_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream);
 }
@@ -1366,7 +1372,7 @@ int gtqa_sample(gtqa_state* s, int32_t k, const int32_t* order, const double* u,
     c.tol = tol;
     c.max_iter = max_iter;
     for (int q = 0; q < k && s->plain; ++q) {
-        if (plain_sample_launch(s->CHI, s->D, f32(s), s->Gamma, s->lam, s->vslots4, order[q], u[q], q, s->xs, s->ps,
+        if (plain_sample_launch(s->CHI, s->D, pm(s), s->Gamma, s->lam, s->vslots4, order[q], u[q], q, s->xs, s->ps,
                                 s->stream) != cudaSuccess)
             return d4_fail(s);
         s->launches += 1;
@@ -1436,7 +1442,7 @@ int gtqa_apply_gates(gtqa_state* s, int32_t k, const int32_t* edge, const double
         a.stats = s->stats;
         a.chi = s->chi;
         a.svd_cut = s->svd_cutoff;
-        const cudaError_t e = s->plain    ? plain_general_gates_launch(s->CHI, s->D, f32(s), a, s->stream)
+        const cudaError_t e = s->plain    ? plain_general_gates_launch(s->CHI, s->D, pm(s), a, s->stream)
                               : mixed(s) ? general_gates_launch_mixed(s->CHI, a, s->stream)
                                          : general_gates_launch_fp64(s->CHI, a, s->stream);
         if (e != cudaSuccess) {
@@ -1491,7 +1497,7 @@ int gtqa_apply_single_qubit_gates(gtqa_state* s, int32_t k, const int32_t* verte
     if (!cuda_ok(s, cudaMemcpyAsync(s->sq_vertex, vs.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s->stream)) ||
         !cuda_ok(s, cudaMemcpyAsync(s->sq_W, Wd.data(), sizeof(double) * Wd.size(), cudaMemcpyHostToDevice, s->stream)))
         return GTQA_ERR_CUDA;
-    const cudaError_t e = s->plain ? plain_single_gates_launch(s->CHI, s->D, f32(s), s->Gamma, s->sq_vertex, s->sq_W,
+    const cudaError_t e = s->plain ? plain_single_gates_launch(s->CHI, s->D, pm(s), s->Gamma, s->sq_vertex, s->sq_W,
                                                                cnt, s->stream)
                           : mixed(s) ? single_gates_launch_mixed(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream)
                                      : single_gates_launch_fp64(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream);
@@ -1845,7 +1851,7 @@ int gtqa_marginals(gtqa_state* s, double* rho_out, int8_t* sign_out) {
     {
         ProfScope ps(s, GTQA_K_MARGINALS, s->n);
         const cudaError_t e =
-            s->plain ? plain_marginals_launch(s->CHI, s->D, f32(s), s->Gamma, s->lam, s->vslots4, s->n, s->rho,
+            s->plain ? plain_marginals_launch(s->CHI, s->D, pm(s), s->Gamma, s->lam, s->vslots4, s->n, s->rho,
                                               s->sign, s->flags, s->stream)
             : mixed(s) ? marginals_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho, s->sign,
                                                 s->flags, s->stream)
@@ -1951,7 +1957,7 @@ int gtqa_set_state(gtqa_state* s, const double* gamma, const double* lambda, con
         if (!cuda_ok(s, cudaMemcpyAsync(s->Gamma, g.data(), gel * sizeof(cd), cudaMemcpyHostToDevice, st)) ||
             !cuda_ok(s, cudaMemcpyAsync(s->msg[ctl.cur], mm.data(), mel * sizeof(cd), cudaMemcpyHostToDevice, st)))
             return GTQA_ERR_CUDA;
-    } else if (f32(s)) {
+    } else if (abs32(s)) {
         std::vector<cf> gf(gel), mf(mel);
         for (size_t i = 0; i < gel; ++i) gf[i] = cf{(float)g[i].x, (float)g[i].y};
         for (size_t i = 0; i < mel; ++i) mf[i] = cf{(float)mm[i].x, (float)mm[i].y};

@@ -49,24 +49,25 @@ cudaError_t single_gates_launch_fp64(int CHI, void* Gamma, const int* vertex, co
 cudaError_t single_gates_launch_mixed(int CHI, void* Gamma, const int* vertex, const cd* W, int count,
                                       cudaStream_t st);
 
-// the plain path: FP64 (degree 4 with CHI in {2, 4}, degree 3 with CHI = 16) and the complex64
-// mode (f32: degree 3 with CHI in {2, 4, 8, 16}, degree 4 with CHI in {2, 4})
-bool plain_supported(int CHI, int D, bool f32);
+// the plain path; pm selects the precision: 0 FP64, 1 mixed (degree 4 with CHI in {2, 4},
+// degree 3 with CHI = 16 for both) or 2 complex64 (degree 3 with CHI in {2, 4, 8, 16}, degree 4
+// with CHI in {2, 4})
+bool plain_supported(int CHI, int D, int pm);
 size_t plain_scratch_entries(int CHI, int D, int n, int m);
-cudaError_t plain_bp_init_launch(int CHI, int D, bool f32, const PlainArgs& a, cudaStream_t st);
-cudaError_t plain_bp_sweep_launch(int CHI, int D, bool f32, const PlainArgs& a, cudaStream_t st);
-cudaError_t plain_regauge_launch(int CHI, int D, bool f32, const PlainArgs& a, const void* msg, double eig_cut,
+cudaError_t plain_bp_init_launch(int CHI, int D, int pm, const PlainArgs& a, cudaStream_t st);
+cudaError_t plain_bp_sweep_launch(int CHI, int D, int pm, const PlainArgs& a, cudaStream_t st);
+cudaError_t plain_regauge_launch(int CHI, int D, int pm, const PlainArgs& a, const void* msg, double eig_cut,
                                  double svd_cut, cudaStream_t st);
-cudaError_t plain_marginals_launch(int CHI, int D, bool f32, const void* Gamma, const double* lam, const int4* vslots,
+cudaError_t plain_marginals_launch(int CHI, int D, int pm, const void* Gamma, const double* lam, const int4* vslots,
                                    int n, cd* rho, int8_t* sign, int* flag, cudaStream_t st);
-cudaError_t plain_residual_launch(int CHI, int D, bool f32, const void* Gamma, const double* lam, const int4* vslots,
+cudaError_t plain_residual_launch(int CHI, int D, int pm, const void* Gamma, const double* lam, const int4* vslots,
                                   int n, double* out, cudaStream_t st);
-cudaError_t plain_sample_launch(int CHI, int D, bool f32, void* Gamma, const double* lam, const int4* vslots, int a,
+cudaError_t plain_sample_launch(int CHI, int D, int pm, void* Gamma, const double* lam, const int4* vslots, int a,
                                 double u, int step, int8_t* x, double* p, cudaStream_t st);
-cudaError_t plain_general_gates_launch(int CHI, int D, bool f32, const GenArgs& a, cudaStream_t st);
-cudaError_t plain_single_gates_launch(int CHI, int D, bool f32, void* Gamma, const int* vertex, const cd* W, int count,
+cudaError_t plain_general_gates_launch(int CHI, int D, int pm, const GenArgs& a, cudaStream_t st);
+cudaError_t plain_single_gates_launch(int CHI, int D, int pm, void* Gamma, const int* vertex, const cd* W, int count,
                                       cudaStream_t st);
-cudaError_t ising16_gates_launch(const Gate16Args& a, bool f32, cudaStream_t st);
+cudaError_t ising16_gates_launch(const Gate16Args& a, int pm, cudaStream_t st);
 
 inline bool phase_shape(bool mixed, int pk, int CHI, size_t* sb, int* tpb) {
     switch (pk) {

@@ -60,18 +60,18 @@ __device__ __forceinline__ int plain_slot_edge(const int4& v, int k) {
 
 // T = Gamma prod_k lambda_k^{1/2}; with warm, the vertex's outgoing messages are set to
 // diag(lambda)/sum(lambda) in msg_nxt (the buffer the first sweep reads).  One block per vertex.
-template <int CHI, int D, typename R>
+template <int CHI, int D, typename R, typename RC = R>
 __global__ void plain_bp_init_kernel(PlainArgs a) {
     using S = PlainShape<CHI, D, R>;
     const int v = blockIdx.x;
-    __shared__ R sq[D][CHI], m0[D][CHI];
+    __shared__ RC sq[D][CHI], m0[D][CHI];
     const int4 sl = a.vslots[v];
     if (threadIdx.x < D * CHI) {
         const int k = threadIdx.x / CHI, j = threadIdx.x % CHI;
         const int e = plain_slot_edge(sl, k);
-        const R lj = lam_get(a.lam, CHI, e, j);
+        const RC lj = lam_get(a.lam, CHI, e, j);
         sq[k][j] = sqrt(lj);
-        R s = 0.0;
+        RC s = 0.0;
         for (int q = 0; q < CHI; ++q) s += lam_get(a.lam, CHI, e, q);
         m0[k][j] = s > 0.0 ? lj / s : 0.0;
     }
@@ -80,12 +80,12 @@ __global__ void plain_bp_init_kernel(PlainArgs a) {
     C<R>* T = (C<R>*)a.T + (size_t)v * S::H2;
     for (int t = threadIdx.x; t < S::H2; t += blockDim.x) {
         int r = t % S::H;
-        R f = 1.0;
+        RC f = 1.0;
         for (int k = D - 1; k >= 0; --k) {
             f *= sq[k][r % CHI];
             r /= CHI;
         }
-        T[t] = f * g[t];
+        T[t] = ccast<R>(f * ccast<RC>(g[t]));
     }
     if (a.warm) {
         C<R>* out = (C<R>*)a.msg_nxt;
@@ -95,7 +95,7 @@ __global__ void plain_bp_init_kernel(PlainArgs a) {
             if (e < 0) continue;
             const int o = 2 * e + (a.edge_info[e].x == v ? 0 : 1);
             const int j = r / CHI, jp = r % CHI;
-            out[(size_t)o * S::CC + r] = C<R>{j == jp ? m0[k][j] : (R)0, (R)0};
+            out[(size_t)o * S::CC + r] = C<R>{j == jp ? (R)m0[k][j] : (R)0, (R)0};
         }
     }
 }
@@ -104,7 +104,9 @@ __global__ void plain_bp_init_kernel(PlainArgs a) {
 //   m_{v->b}[j][j'] = sum T[.., j@s, ..] conj(T[.., j'@s, ..]) prod_{o != s} m_o[x_o][x'_o]
 // (Eq. (local_consistency)), divided by its complex trace; new - old goes to dm for the
 // trace-norm kernel.
-template <int CHI, int D, typename R>
+// R is the storage and contraction type; RC the type of the trace and the normalisation
+// (FP64 in the mixed mode).
+template <int CHI, int D, typename R, typename RC = R>
 __global__ void __launch_bounds__(PlainShape<CHI, D, R>::NT) plain_bp_sweep_kernel(PlainArgs a) {
     using S = PlainShape<CHI, D, R>;
     constexpr int H2 = S::H2, CC = S::CC, NT = S::NT, TPO = S::TPO;
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(PlainShape<CHI, D, R>::NT) plain_bp_sweep_kern
         P1 = P0 + H2;
     }
     __shared__ int es[4], in_idx[4], out_idx[4];
-    __shared__ C<R> itr;
+    __shared__ C<RC> itr;
     const int v = blockIdx.x, tid = threadIdx.x;
     const C<R>* src_msg = (const C<R>*)a.msg_cur;
     C<R>* dst_msg = (C<R>*)a.msg_nxt;
@@ -181,17 +183,17 @@ __global__ void __launch_bounds__(PlainShape<CHI, D, R>::NT) plain_bp_sweep_kern
         }
         __syncthreads();
         if (tid == 0) {
-            C<R> tr = C<R>{(R)0, (R)0};
-            for (int q = 0; q < CHI; ++q) tr = tr + F[q * CHI + q];
-            const R d = tr.x * tr.x + tr.y * tr.y;
-            itr = d > 0.0 ? C<R>{tr.x / d, -tr.y / d} : C<R>{(R)0, (R)0};
+            C<RC> tr = C<RC>{(RC)0, (RC)0};
+            for (int q = 0; q < CHI; ++q) tr = tr + ccast<RC>(F[q * CHI + q]);
+            const RC d = tr.x * tr.x + tr.y * tr.y;
+            itr = d > 0.0 ? C<RC>{tr.x / d, -tr.y / d} : C<RC>{(RC)0, (RC)0};
         }
         __syncthreads();
         for (int r = tid; r < CC; r += NT) {
-            const C<R> mn = F[r] * itr;
-            const C<R> mo = src_msg[(size_t)out_idx[s] * CC + r];
-            dst_msg[(size_t)out_idx[s] * CC + r] = mn;
-            ((C<R>*)a.dm)[(size_t)out_idx[s] * CC + r] = mn - mo;
+            const C<RC> mn = ccast<RC>(F[r]) * itr;
+            const C<RC> mo = ccast<RC>(src_msg[(size_t)out_idx[s] * CC + r]);
+            dst_msg[(size_t)out_idx[s] * CC + r] = ccast<R>(mn);
+            ((C<R>*)a.dm)[(size_t)out_idx[s] * CC + r] = ccast<R>(mn - mo);
         }
         __syncthreads();
     }
@@ -199,22 +201,22 @@ __global__ void __launch_bounds__(PlainShape<CHI, D, R>::NT) plain_bp_sweep_kern
 
 // Trace norm (sum of singular values, one-sided Jacobi in FP64) of every directed message's
 // new - old; block = CHI^2 / 2 threads, one message per block; the sum goes to *acc.
-template <int CHI, typename R>
+template <int CHI, typename R, typename RC = R>
 __global__ void plain_trace_norm_kernel(const C<R>* dm, double* acc) {
     constexpr int CC = CHI * CHI;
-    __shared__ C<R> A[CC];
-    __shared__ R tn;
+    __shared__ C<RC> A[CC];
+    __shared__ RC tn;
     __shared__ int flag;
     const int g = threadIdx.x;
-    for (int t = g; t < CC; t += blockDim.x) A[t] = dm[(size_t)blockIdx.x * CC + t];
+    for (int t = g; t < CC; t += blockDim.x) A[t] = ccast<RC>(dm[(size_t)blockIdx.x * CC + t]);
     if (g == 0) tn = 0.0;
     __syncthreads();
     BlockGroup grp{&flag};
-    jacobi_svd<CHI, R, BlockGroup, false>(A, nullptr, g, grp, group_mask<CHI>(), (R)(sizeof(R) == 8 ? 1e-15 : 1e-6), 60,
-                                          false);
+    jacobi_svd<CHI, RC, BlockGroup, false>(A, nullptr, g, grp, group_mask<CHI>(), (RC)(sizeof(RC) == 8 ? 1e-15 : 1e-6),
+                                           60, false);
     __syncthreads();
     if (g < CHI) {
-        R c2 = 0.0;
+        RC c2 = 0.0;
         for (int r = 0; r < CHI; ++r) c2 += norm2(A[g * CHI + r]);
         atomicAdd(&tn, sqrt(c2));
     }
@@ -227,11 +229,11 @@ __global__ void plain_trace_norm_kernel(const C<R>* dm, double* acc) {
 // v^H A v), principal square roots and pseudo-inverse square roots, the SVD of
 // M = (m_{a->b}^{1/2})^T m_{b->a}^{1/2}, lambda = S/||S||, X_a = conj(m_{a->b}^{-1/2}) U ||S||^{1/2}
 // and X_b = conj(m_{b->a}^{-1/2}) V^* ||S||^{1/2}.
-template <int CHI, typename R>
+template <int CHI, typename R, typename RC = R>
 __global__ void plain_regauge_edge_kernel(const C<R>* msg, double* lam, C<R>* X, double eig_cut, double svd_cut) {
     constexpr int CC = CHI * CHI;
-    __shared__ C<R> Am[2][CC], Vm[2][CC], sqm[2][CC], isq[2][CC], M[CC], VM[CC];
-    __shared__ R w[2][CHI], sig[CHI], scal[2];
+    __shared__ C<RC> Am[2][CC], Vm[2][CC], sqm[2][CC], isq[2][CC], M[CC], VM[CC];
+    __shared__ RC w[2][CHI], sig[CHI], scal[2];
     __shared__ int perm[CHI], flag;
     const int e = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
     BlockGroup grp{&flag};
@@ -239,41 +241,41 @@ __global__ void plain_regauge_edge_kernel(const C<R>* msg, double* lam, C<R>* X,
         const int x = t / CC, r = t % CC;
         const int row = r % CHI, col = r / CHI;
         const C<R>* mm = msg + (size_t)(2 * e + x) * CC;
-        const C<R> v = mm[row * CHI + col], vt = mm[col * CHI + row];
-        Am[x][col * CHI + row] = C<R>{(R)0.5 * (v.x + vt.x), (R)0.5 * (v.y - vt.y)};
+        const C<RC> v = ccast<RC>(mm[row * CHI + col]), vt = ccast<RC>(mm[col * CHI + row]);
+        Am[x][col * CHI + row] = C<RC>{(RC)0.5 * (v.x + vt.x), (RC)0.5 * (v.y - vt.y)};
     }
     __syncthreads();
     for (int x = 0; x < 2; ++x)
-        jacobi_svd<CHI, R, BlockGroup, true, sizeof(R) == 8>(Am[x], Vm[x], tid, grp, group_mask<CHI>(),
-                                                                  (R)(sizeof(R) == 8 ? 1e-15 : 1e-6), 60, true, nullptr,
-                                                                  (R)(sizeof(R) == 8 ? 3e-8 : 1e-3));
+        jacobi_svd<CHI, RC, BlockGroup, true, sizeof(RC) == 8>(Am[x], Vm[x], tid, grp, group_mask<CHI>(),
+                                                                  (RC)(sizeof(RC) == 8 ? 1e-15 : 1e-6), 60, true, nullptr,
+                                                                  (RC)(sizeof(RC) == 8 ? 3e-8 : 1e-3));
     __syncthreads();
     for (int t = tid; t < 2 * CHI; t += NT) {
         const int x = t / CHI, k = t % CHI;
-        R n2 = 0.0, sg = 0.0;
+        RC n2 = 0.0, sg = 0.0;
         for (int r = 0; r < CHI; ++r) {
-            const C<R> av = Am[x][k * CHI + r], vv = Vm[x][k * CHI + r];
+            const C<RC> av = Am[x][k * CHI + r], vv = Vm[x][k * CHI + r];
             n2 += norm2(av);
             sg += vv.x * av.x + vv.y * av.y;
         }
-        const R wv = nr_sqrt(n2);
+        const RC wv = nr_sqrt(n2);
         w[x][k] = sg >= 0.0 ? wv : -wv;
     }
     __syncthreads();
     for (int t = tid; t < 2 * CC; t += NT) {
         const int x = t / CC, r = t % CC;
         const int j = r / CHI, jp = r % CHI;
-        R wmax = 0.0;
+        RC wmax = 0.0;
         for (int k = 0; k < CHI; ++k) wmax = fmax(wmax, w[x][k]);
-        C<R> s1 = C<R>{(R)0, (R)0}, s2 = C<R>{(R)0, (R)0};
+        C<RC> s1 = C<RC>{(RC)0, (RC)0}, s2 = C<RC>{(RC)0, (RC)0};
         for (int k = 0; k < CHI; ++k) {
-            const R wk = w[x][k];
+            const RC wk = w[x][k];
             if (!(wk > eig_cut * wmax)) continue;
-            const R is = nr_rsqrt(wk);
-            const R sq = wk * is;
-            const C<R> vv = Vm[x][k * CHI + j] * conj(Vm[x][k * CHI + jp]);
-            s1 = cfma(C<R>{sq, (R)0}, vv, s1);
-            s2 = cfma(C<R>{is, (R)0}, vv, s2);
+            const RC is = nr_rsqrt(wk);
+            const RC sq = wk * is;
+            const C<RC> vv = Vm[x][k * CHI + j] * conj(Vm[x][k * CHI + jp]);
+            s1 = cfma(C<RC>{sq, (RC)0}, vv, s1);
+            s2 = cfma(C<RC>{is, (RC)0}, vv, s2);
         }
         sqm[x][r] = s1;
         isq[x][r] = s2;
@@ -281,17 +283,17 @@ __global__ void plain_regauge_edge_kernel(const C<R>* msg, double* lam, C<R>* X,
     __syncthreads();
     for (int t = tid; t < CC; t += NT) {
         const int k = t % CHI, l = t / CHI;
-        C<R> acc = C<R>{(R)0, (R)0};
+        C<RC> acc = C<RC>{(RC)0, (RC)0};
         for (int j = 0; j < CHI; ++j) acc = cfma(sqm[0][j * CHI + k], sqm[1][j * CHI + l], acc);
         M[l * CHI + k] = acc;
     }
     __syncthreads();
-    jacobi_svd<CHI, R, BlockGroup, true, sizeof(R) == 8>(M, VM, tid, grp, group_mask<CHI>(),
-                                                         (R)(sizeof(R) == 8 ? 1e-15 : 1e-6), 60, true, nullptr,
-                                                         (R)(sizeof(R) == 8 ? 3e-8 : 1e-3));
+    jacobi_svd<CHI, RC, BlockGroup, true, sizeof(RC) == 8>(M, VM, tid, grp, group_mask<CHI>(),
+                                                         (RC)(sizeof(RC) == 8 ? 1e-15 : 1e-6), 60, true, nullptr,
+                                                         (RC)(sizeof(RC) == 8 ? 3e-8 : 1e-3));
     __syncthreads();
     for (int cc = tid; cc < CHI; cc += NT) {
-        R n2 = 0.0;
+        RC n2 = 0.0;
         for (int r = 0; r < CHI; ++r) n2 += norm2(M[cc * CHI + r]);
         sig[cc] = nr_sqrt(n2);
     }
@@ -299,15 +301,15 @@ __global__ void plain_regauge_edge_kernel(const C<R>* msg, double* lam, C<R>* X,
     for (int cc = tid; cc < CHI; cc += NT) perm[desc_rank(sig, CHI, cc)] = cc;
     __syncthreads();
     if (tid == 0) {
-        R tot = 0.0;
+        RC tot = 0.0;
         for (int cc = 0; cc < CHI; ++cc) tot += sig[cc] * sig[cc];
-        const R nrm = nr_sqrt(tot);
+        const RC nrm = nr_sqrt(tot);
         scal[0] = nrm;
         scal[1] = nr_sqrt(nrm);
-        const R inrm = nrm > 0.0 ? nr_rcp(nrm) : 0.0;
-        const R smax = sig[perm[0]];
+        const RC inrm = nrm > 0.0 ? nr_rcp(nrm) : 0.0;
+        const RC smax = sig[perm[0]];
         for (int r = 0; r < CHI; ++r) {
-            const R s = sig[perm[r]];
+            const RC s = sig[perm[r]];
             lam[(size_t)e * CHI + r] = (nrm > 0.0 && s > svd_cut * smax) ? s * inrm : 0.0;
         }
     }
@@ -316,17 +318,17 @@ __global__ void plain_regauge_edge_kernel(const C<R>* msg, double* lam, C<R>* X,
         const int x = t / CC, r = t % CC;
         const int jpp = r / CHI, j = r % CHI;
         const int pc = perm[j];
-        const R s = sig[pc];
-        C<R> acc = C<R>{(R)0, (R)0};
+        const RC s = sig[pc];
+        C<RC> acc = C<RC>{(RC)0, (RC)0};
         const bool kept = scal[0] > 0.0 && s > svd_cut * sig[perm[0]];
         if (kept) {
             for (int jp = 0; jp < CHI; ++jp) {
-                const C<R> u = (x == 0) ? nr_rcp(s) * M[pc * CHI + jp] : conj(VM[pc * CHI + jp]);
+                const C<RC> u = (x == 0) ? nr_rcp(s) * M[pc * CHI + jp] : conj(VM[pc * CHI + jp]);
                 acc = cfma(isq[x][jp * CHI + jpp], u, acc);
             }
             acc = scal[1] * acc;
         }
-        X[((size_t)e * 2 + x) * CC + r] = acc;
+        X[((size_t)e * 2 + x) * CC + r] = ccast<R>(acc);
     }
 }
 
@@ -566,9 +568,11 @@ __device__ __forceinline__ void group128_sum(CR (&vals)[NV], int nv, CR (*red)[1
     asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
 }
 
-// R = double: the FP64 precision mode; R = float: the complex64 mode (QR, Jacobi SVD and the
-// new Gamma in FP32, Gamma stored in complex64; lambda is written as float64).
-template <int CHI, typename R>
+// TS is the storage type of Gamma, R the arithmetic type: (double, double) is the FP64
+// precision mode, (float, float) the complex64 mode (QR, Jacobi SVD and the new Gamma in FP32)
+// and (float, double) the mixed mode (FP64 QR and SVD on complex64 Gamma).  lambda is always
+// written as float64.
+template <int CHI, typename TS, typename R>
 __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
     using CR = C<R>;
     constexpr bool R64 = sizeof(R) == 8;
@@ -589,7 +593,7 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
         oe[x][1] = es[os[x][1]];
     }
     CR* Xg = reinterpret_cast<CR*>(c.scratch) + (size_t)blockIdx.x * 4 * CHI * NR;   // [blk][col][row]
-    CR* Gam = (CR*)c.Gamma;
+    C<TS>* Gam = (C<TS>*)c.Gamma;
     for (int t = tid; t < 2 * NR; t += 512) {
         const int x = t / NR, J = t % NR;
         sm.w[x][J] = (R)(lam_get(c.lam, CHI, oe[x][0], J / CHI) * lam_get(c.lam, CHI, oe[x][1], J % CHI));
@@ -604,7 +608,7 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
         const int x = blk >> 1, i = blk & 1;
         const size_t off = (size_t)vtx[x] * 2 * H + (size_t)i * H + col * sstride<CHI>(slot[x]) +
                            (row / CHI) * sstride<CHI>(os[x][0]) + (row % CHI) * sstride<CHI>(os[x][1]);
-        Xg[((size_t)blk * CHI + col) * NR + row] = sm.w[x][row] * Gam[off];
+        Xg[((size_t)blk * CHI + col) * NR + row] = sm.w[x][row] * ccast<R>(Gam[off]);
     }
     __syncthreads();
     // ---- Householder QR of the four blocks, 128 threads per block, rows l and l + 128 ----
@@ -740,8 +744,8 @@ __global__ void __launch_bounds__(512, 1) ising16_gate_kernel(Gate16Args c) {
     const size_t o1 = ((l + 128) / CHI) * sstride<CHI>(os[x][0]) + ((l + 128) % CHI) * sstride<CHI>(os[x][1]);
 #pragma unroll
     for (int cc = 0; cc < CHI; ++cc) {
-        Gam[base + cc * sstride<CHI>(slot[x]) + o0] = iw0 * E0[cc];
-        Gam[base + cc * sstride<CHI>(slot[x]) + o1] = iw1 * E1[cc];
+        Gam[base + cc * sstride<CHI>(slot[x]) + o0] = ccast<TS>(iw0 * E0[cc]);
+        Gam[base + cc * sstride<CHI>(slot[x]) + o1] = ccast<TS>(iw1 * E1[cc]);
     }
 }
 

@@ -79,12 +79,11 @@ def test_invalid_graphs_rejected_on_host(G):
     # degree 5
     star = [[0, 1], [0, 2], [0, 3], [0, 4], [0, 5]]
     assert _rc(G, 6, star, np.ones(5), np.zeros(6), 4)[0] == G.GTQA_ERR_INVALID_ARG
-    # degree 4 needs FP64 and chi <= 4 (checked before any device work)
+    # degree 4 needs chi <= 4 in every precision (checked before any device work)
     star4 = star[:4]
-    assert _rc(G, 5, star4, np.ones(4), np.zeros(5), 4, precision=G.GTQA_MIXED)[0] == G.GTQA_ERR_UNSUPPORTED
-    assert _rc(G, 5, star4, np.ones(4), np.zeros(5), 8)[0] == G.GTQA_ERR_UNSUPPORTED
-    # chi 9..16 (storage 16) needs FP64 and degree <= 3
-    assert _rc(G, 4, [[0, 1]], [1.0], h, 16, precision=G.GTQA_MIXED)[0] == G.GTQA_ERR_UNSUPPORTED
+    for prec in (G.GTQA_FP64, G.GTQA_MIXED, G.GTQA_C64):
+        assert _rc(G, 5, star4, np.ones(4), np.zeros(5), 8, precision=prec)[0] == G.GTQA_ERR_UNSUPPORTED
+    # chi 9..16 (storage 16) needs degree <= 3
     assert _rc(G, 5, star4, np.ones(4), np.zeros(5), 12)[0] == G.GTQA_ERR_UNSUPPORTED
     assert _rc(G, 4, [[0, 1]], [1.0], h, 17)[0] == G.GTQA_ERR_UNSUPPORTED
     # out of range vertex

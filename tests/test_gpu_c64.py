@@ -62,19 +62,20 @@ def test_c64_against_fp64_next_to_mixed(chi):
     assert e_mix <= e_c64 + 1e-12, (e_mix, e_c64)
 
 
-def test_mixed_chi16_rejected():
+def test_unsupported_plain_shapes_rejected():
+    """Degree 4 runs on the plain kernels up to chi = 4 in every precision."""
     G = U.lib()
-    inst = make_instance(16, 0)
+    inst = make_instance(10, 0, d=4)
     lib = G.load()
     import ctypes
-    opt = G.gtqa_options_init(precision=G.GTQA_MIXED)
-    h = ctypes.c_void_p()
     e = np.ascontiguousarray(inst.edges, dtype=np.int32)
     J = np.ascontiguousarray(inst.J)
     hh = np.ascontiguousarray(inst.h)
-    # chi 16 runs on the plain kernels, which have the FP64 and complex64 modes only
-    assert lib.gtqa_create(inst.n, inst.m, e.ctypes.data, None, J.ctypes.data, hh.ctypes.data, 16, ctypes.byref(opt),
-                           ctypes.byref(h)) == G.GTQA_ERR_UNSUPPORTED
+    for prec in (G.GTQA_FP64, G.GTQA_MIXED, G.GTQA_C64):
+        opt = G.gtqa_options_init(precision=prec)
+        h = ctypes.c_void_p()
+        assert lib.gtqa_create(inst.n, inst.m, e.ctypes.data, None, J.ctypes.data, hh.ctypes.data, 8,
+                               ctypes.byref(opt), ctypes.byref(h)) == G.GTQA_ERR_UNSUPPORTED
 
 
 def test_c64_chi16_follows_the_oracle():
