@@ -1,9 +1,11 @@
 // The plain path: graph tensor networks whose vertex tensors are too large or have too many
 // bonds for the persistent kernels, or that run every step in FP32.  Shapes built: degree 4
 // with CHI <= 4 (the random 4-regular graphs of Sec. V) and degree 3 with CHI = 16 (the largest
-// bond dimension of the chi sweep), in complex128 (the FP64 precision mode); degree 3 with
-// CHI <= 8 or CHI = 16 and degree 4 with CHI <= 4 in complex64 with every step in FP32 (the
-// complex64 mode, R = float).  One instance.
+// bond dimension of the chi sweep), in complex128 (the FP64 precision mode, R = RC = double) and
+// in the mixed mode (complex64 storage and contractions, R = float, with the normalisation,
+// trace norms, regauge and the CHI = 16 gate's QR/SVD in RC = double); degree 3 with CHI <= 8 or
+// CHI = 16 and degree 4 with CHI <= 4 in complex64 with every step in FP32 (the complex64 mode,
+// R = RC = float).  One instance.  The messages hold m itself in every mode.
 //
 // Layout: Gamma and T are [n][2][CHI]^D (slot k = k-th incident edge in ascending id, stride
 // CHI^(D-1-k); phantom slots of vertices with fewer edges have dimension 1 with lambda = e_0);
