@@ -148,9 +148,9 @@ bool mixed(const gtqa_state* s) { return s->precision == GTQA_MIXED; }
 bool f32(const gtqa_state* s) { return s->precision == GTQA_C64; }
 // precision selector of the plain kernels: 0 FP64, 1 mixed, 2 complex64
 int pm(const gtqa_state* s) { return s->precision == GTQA_FP64 ? 0 : (s->precision == GTQA_MIXED ? 1 : 2); }
-// messages held as the absolute m in complex64 (complex64 mode, and the mixed mode on the plain
-// path); the persistent mixed path holds m - m0 instead
-bool abs32(const gtqa_state* s) { return f32(s) || (s->precision == GTQA_MIXED && s->plain); }
+// messages held as the absolute m in complex64 (the complex64 mode); the mixed mode holds
+// m - m0 on both paths
+bool abs32(const gtqa_state* s) { return f32(s); }
 bool f32store(const gtqa_state* s) { return s->precision != GTQA_FP64; }
 size_t elem_bytes(const gtqa_state* s) { return f32store(s) ? sizeof(cf) : sizeof(cd); }
 size_t gamma_elems(const gtqa_state* s) {
@@ -903,6 +903,8 @@ PlainArgs d4_args(gtqa_state* s, int cur) {
     a.m = s->m;
     a.acc = s->acc;
     a.warm = 0;
+    a.D0 = s->D0;
+    a.t0 = s->t0;
     return a;
 }
 

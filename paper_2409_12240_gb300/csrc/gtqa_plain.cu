@@ -7,10 +7,12 @@
 namespace gtqa {
 
 namespace {
-template <int CHI, int D, typename R>
+template <int CHI, int D, typename R, typename RC>
 size_t sweep_smem() {
     using S = PlainShape<CHI, D, R>;
-    return sizeof(C<R>) * ((D + 1) * S::CC + (S::SMEM ? 3 * S::H2 : 0));
+    // the mixed mode adds m0 and delta of the incoming messages
+    const int mix = sizeof(R) != sizeof(RC) ? 2 * D * S::CC : 0;
+    return sizeof(C<R>) * ((D + 1) * S::CC + (S::SMEM ? 3 * S::H2 : 0) + mix);
 }
 template <int CHI, int D, typename R>
 size_t vertex_smem() {
@@ -27,7 +29,7 @@ template <int CHI, int D, typename R, typename RC>
 cudaError_t sweep_t(const PlainArgs& a, cudaStream_t st) {
     using S = PlainShape<CHI, D, R>;
     if (a.n > 0) {
-        plain_bp_sweep_kernel<CHI, D, R, RC><<<a.n, S::NT, sweep_smem<CHI, D, R>(), st>>>(a);
+        plain_bp_sweep_kernel<CHI, D, R, RC><<<a.n, S::NT, sweep_smem<CHI, D, R, RC>(), st>>>(a);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

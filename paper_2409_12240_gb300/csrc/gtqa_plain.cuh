@@ -45,6 +45,8 @@ struct PlainArgs {
     int n, m;
     double* acc;              // distance accumulator (one double)
     int warm;
+    void* D0;                 // mixed mode: [2m][CHI^2] warm-start defect F(m0) - tr F(m0) m0 (storage type)
+    cd* t0;                   // mixed mode: [2m] tr F(m0)
 };
 
 template <int CHI, int D, typename R = double>
@@ -89,7 +91,9 @@ __global__ void plain_bp_init_kernel(PlainArgs a) {
         }
         T[t] = ccast<R>(f * ccast<RC>(g[t]));
     }
+    constexpr bool MIX = sizeof(R) != sizeof(RC);
     if (a.warm) {
+        // the mixed mode holds delta = m - m0, which the warm start sets to 0
         C<R>* out = (C<R>*)a.msg_nxt;
         for (int t = threadIdx.x; t < D * S::CC; t += blockDim.x) {
             const int k = t / S::CC, r = t % S::CC;
@@ -97,7 +101,58 @@ __global__ void plain_bp_init_kernel(PlainArgs a) {
             if (e < 0) continue;
             const int o = 2 * e + (a.edge_info[e].x == v ? 0 : 1);
             const int j = r / CHI, jp = r % CHI;
-            out[(size_t)o * S::CC + r] = C<R>{j == jp ? (R)m0[k][j] : (R)0, (R)0};
+            out[(size_t)o * S::CC + r] = C<R>{(!MIX && j == jp) ? (R)m0[k][j] : (R)0, (R)0};
+        }
+    }
+    if constexpr (MIX) {
+        // F0 = F(m0) of every outgoing message in RC from the stored T (so that F(m0 + delta) =
+        // F0 + F_delta holds for the T the sweeps contract), kept as D0 = F0 - tr(F0) m0 and t0
+        __shared__ C<RC> F0[D][S::CC];
+        __shared__ C<RC> tr0[D];
+        __syncthreads();   // this block's T is written
+        constexpr int NO = S::H / CHI;
+        for (int t = threadIdx.x; t < D * S::CC; t += blockDim.x) {
+            const int k = t / S::CC, r = t % S::CC;
+            if (plain_slot_edge(sl, k) < 0) continue;
+            const int j = r / CHI, jp = r % CHI;
+            int sk = 1;
+            for (int l = D - 1; l > k; --l) sk *= CHI;
+            C<RC> f = C<RC>{(RC)0, (RC)0};
+            for (int i = 0; i < 2; ++i)
+                for (int q = 0; q < NO; ++q) {
+                    int rem = q, base = 0, stride = 1;
+                    RC w = 1.0;
+                    for (int l = D - 1; l >= 0; --l) {
+                        if (l != k) {
+                            const int idx = rem % CHI;
+                            rem /= CHI;
+                            w *= m0[l][idx];
+                            base += idx * stride;
+                        }
+                        stride *= CHI;
+                    }
+                    const C<RC> x = ccast<RC>(T[i * S::H + base + j * sk]), y = ccast<RC>(T[i * S::H + base + jp * sk]);
+                    f = cfmac(y, w * x, f);
+                }
+            F0[k][r] = f;
+        }
+        __syncthreads();
+        if (threadIdx.x < D) {
+            C<RC> tr = C<RC>{(RC)0, (RC)0};
+            for (int j = 0; j < CHI; ++j) tr = tr + F0[threadIdx.x][j * CHI + j];
+            tr0[threadIdx.x] = tr;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < D * S::CC; t += blockDim.x) {
+            const int k = t / S::CC, r = t % S::CC;
+            const int e = plain_slot_edge(sl, k);
+            if (e < 0) continue;
+            const int o = 2 * e + (a.edge_info[e].x == v ? 0 : 1);
+            const int j = r / CHI, jp = r % CHI;
+            C<RC> d = F0[k][r];
+            if (j == jp) d = d - m0[k][j] * tr0[k];
+            ((C<R>*)a.D0)[(size_t)o * S::CC + r] = ccast<R>(d);
+            if (r == 0) a.t0[o] = ccast<double>(tr0[k]);
         }
     }
 }
@@ -129,6 +184,13 @@ __global__ void __launch_bounds__(PlainShape<CHI, D, R>::NT) plain_bp_sweep_kern
     }
     __shared__ int es[4], in_idx[4], out_idx[4];
     __shared__ C<RC> itr;
+    // mixed mode (the delta form of the persistent path): the messages hold delta = m - m0 with
+    // m0 = diag(lambda)/sum(lambda); mz and md hold m0 and delta of the incoming messages
+    constexpr bool MIX = sizeof(R) != sizeof(RC);
+    C<R>* mz = min + (D + 1) * CC + (S::SMEM ? 3 * H2 : 0);   // [D][CC], mixed mode only
+    C<R>* md = mz + D * CC;                                  // [D][CC], mixed mode only
+    __shared__ RC m0d[D][CHI];
+    __shared__ C<RC> tau;
     const int v = blockIdx.x, tid = threadIdx.x;
     const C<R>* src_msg = (const C<R>*)a.msg_cur;
     C<R>* dst_msg = (C<R>*)a.msg_nxt;
@@ -143,13 +205,94 @@ __global__ void __launch_bounds__(PlainShape<CHI, D, R>::NT) plain_bp_sweep_kern
             out_idx[tid] = in_idx[tid] = -1;
         }
     }
+    if (MIX && tid < D * CHI) {
+        const int k = tid / CHI, j = tid % CHI;
+        const int e = plain_slot_edge(a.vslots[v], k);
+        RC sum = 0.0;
+        for (int q = 0; q < CHI; ++q) sum += lam_get(a.lam, CHI, e, q);
+        m0d[k][j] = sum > 0.0 ? lam_get(a.lam, CHI, e, j) / sum : 0.0;
+    }
     for (int t = tid; t < H2; t += NT) T[t] = ((const C<R>*)a.T)[(size_t)v * H2 + t];
     __syncthreads();
     for (int t = tid; t < D * CC; t += NT) {
         const int k = t / CC, r = t % CC;
-        min[t] = in_idx[k] >= 0 ? src_msg[(size_t)in_idx[k] * CC + r] : C<R>{(R)(r == 0 ? 1 : 0), (R)0};
+        if constexpr (MIX) {
+            const int j = r / CHI, jp = r % CHI;
+            const C<R> dv = in_idx[k] >= 0 ? src_msg[(size_t)in_idx[k] * CC + r] : C<R>{(R)0, (R)0};
+            const C<R> zv = C<R>{j == jp ? (R)m0d[k][j] : (R)0, (R)0};
+            md[t] = dv;
+            mz[t] = zv;
+            min[t] = zv + dv;
+        } else {
+            min[t] = in_idx[k] >= 0 ? src_msg[(size_t)in_idx[k] * CC + r] : C<R>{(R)(r == 0 ? 1 : 0), (R)0};
+        }
     }
     __syncthreads();
+    if constexpr (MIX) {
+        // F(m0 + delta) - F(m0) telescoped over the other slots o_1 < o_2 < ...: chain c takes
+        // m0 on the slots before its own, delta on its own and m after it (FP32 contractions);
+        // then delta' = (D0 + F_delta - m0 tr F_delta) / (t0 + tr F_delta) in RC
+        for (int s = 0; s < D; ++s) {
+            if (es[s] < 0) continue;   // uniform: es is shared
+            const int ss = ipow(CHI, D - 1 - s);
+            constexpr int NTERM = H2 / CHI;
+            for (int c = 0; c < D - 1; ++c) {
+                const C<R>* src = T;
+                C<R>* dst = P0;
+                int i = 0;
+                for (int o = 0; o < D; ++o) {
+                    if (o == s) continue;
+                    const C<R>* mo = (i < c ? mz : (i == c ? md : min)) + o * CC;
+                    ++i;
+                    const int so = ipow(CHI, D - 1 - o);
+                    for (int t = tid; t < H2; t += NT) {
+                        const int x = (t / so) % CHI, base = t - x * so;
+                        C<R> acc = C<R>{(R)0, (R)0};
+#pragma unroll 4
+                        for (int q = 0; q < CHI; ++q) acc = cfma(src[base + q * so], mo[q * CHI + x], acc);
+                        dst[t] = acc;
+                    }
+                    __syncthreads();
+                    src = dst;
+                    dst = (dst == P0) ? P1 : P0;
+                }
+                for (int rr = tid / TPO; rr < CC; rr += NT / TPO) {
+                    const int part = tid % TPO;
+                    const int j = rr / CHI, jp = rr % CHI;
+                    C<R> f = C<R>{(R)0, (R)0};
+                    for (int q = part; q < NTERM; q += TPO) {
+                        const int t = (q / ss) * (ss * CHI) + (q % ss);
+                        f = cfmac(T[t + jp * ss], src[t + j * ss], f);
+                    }
+                    f.x = group_sum<TPO>(f.x, group_mask<TPO>());
+                    f.y = group_sum<TPO>(f.y, group_mask<TPO>());
+                    if (part == 0) F[rr] = c == 0 ? f : F[rr] + f;
+                }
+                __syncthreads();
+            }
+            const int out = out_idx[s];
+            if (tid == 0) {
+                C<RC> tr = C<RC>{(RC)0, (RC)0};
+                for (int q = 0; q < CHI; ++q) tr = tr + ccast<RC>(F[q * CHI + q]);
+                tau = tr;
+                const C<RC> den = a.t0[out] + tr;
+                const RC d = den.x * den.x + den.y * den.y;
+                itr = d > 0.0 ? C<RC>{den.x / d, -den.y / d} : C<RC>{(RC)0, (RC)0};
+            }
+            __syncthreads();
+            for (int r = tid; r < CC; r += NT) {
+                const int j = r / CHI, jp = r % CHI;
+                C<RC> num = ccast<RC>(((const C<R>*)a.D0)[(size_t)out * CC + r]) + ccast<RC>(F[r]);
+                if (j == jp) num = num - m0d[s][j] * tau;
+                const C<RC> dn = num * itr;
+                const C<RC> dold = ccast<RC>(src_msg[(size_t)out * CC + r]);
+                dst_msg[(size_t)out * CC + r] = ccast<R>(dn);
+                ((C<R>*)a.dm)[(size_t)out * CC + r] = ccast<R>(dn - dold);
+            }
+            __syncthreads();
+        }
+        return;
+    }
     for (int s = 0; s < D; ++s) {
         if (es[s] < 0) continue;   // uniform: es is shared
         const C<R>* src = T;
@@ -239,11 +382,25 @@ __global__ void plain_regauge_edge_kernel(const C<R>* msg, double* lam, C<R>* X,
     __shared__ int perm[CHI], flag;
     const int e = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
     BlockGroup grp{&flag};
+    // mixed mode: the messages hold delta = m - m0, m0 = diag(lambda_e)/sum(lambda_e) (read before
+    // this kernel overwrites lambda_e)
+    constexpr bool MIX = sizeof(R) != sizeof(RC);
+    __shared__ RC m0e[CHI];
+    if (MIX && tid < CHI) {
+        RC sum = 0.0;
+        for (int q = 0; q < CHI; ++q) sum += lam[(size_t)e * CHI + q];
+        m0e[tid] = sum > 0.0 ? lam[(size_t)e * CHI + tid] / sum : 0.0;
+    }
+    if (MIX) __syncthreads();
     for (int t = tid; t < 2 * CC; t += NT) {
         const int x = t / CC, r = t % CC;
         const int row = r % CHI, col = r / CHI;
         const C<R>* mm = msg + (size_t)(2 * e + x) * CC;
-        const C<RC> v = ccast<RC>(mm[row * CHI + col]), vt = ccast<RC>(mm[col * CHI + row]);
+        C<RC> v = ccast<RC>(mm[row * CHI + col]), vt = ccast<RC>(mm[col * CHI + row]);
+        if (MIX && row == col) {
+            v.x += m0e[row];
+            vt.x += m0e[row];
+        }
         Am[x][col * CHI + row] = C<RC>{(RC)0.5 * (v.x + vt.x), (RC)0.5 * (v.y - vt.y)};
     }
     __syncthreads();
