@@ -59,8 +59,7 @@ extern "C" {
 #define GTQA_FP64 0   /* complex128 everywhere */
 #define GTQA_MIXED 1  /* complex64 tensors and BP contractions; FP64 QR/SVD, gauge roots, normalisation.
                          Messages are held as m0 + delta: m0 = diag(lambda)/sum(lambda) (exact),
-                         delta in complex64 (plain-path states, see gtqa_create: m in complex64);
-                         get/set_state convert to and from complex128. */
+                         delta in complex64; get/set_state convert to and from complex128. */
 #define GTQA_C64 2    /* complex64 with every step in FP32, including the QR/SVD, gauge roots and
                        * normalisation (a reference point for the precision split; plain kernels,
                        * one instance, degree 3 with chi <= 16 or degree 4 with chi <= 4; default
@@ -125,8 +124,7 @@ void gtqa_options_init(gtqa_options* opt);
  * states, and every state in the GTQA_C64 precision, run on plain per-phase kernels and hold
  * one instance.  The shapes built there are: FP64 and GTQA_MIXED with degree 4 and chi <= 4, or
  * degree 3 and 8 < chi <= 16; GTQA_C64 with degree 3 and chi <= 16, or degree 4 and chi <= 4.
- * On the plain path GTQA_MIXED holds the messages as m itself in complex64 (not as m0 + delta),
- * so the BP distance has an FP32 floor near 1e-7 per message.  Anything else
+ * Anything else
  * returns GTQA_ERR_UNSUPPORTED.  On a plain-path state gtqa_autotune and gtqa_anneal_graph
  * return GTQA_ERR_UNSUPPORTED (there is no persistent launch to tune or capture), and so does
  * gtqa_apply_gates at chi > 8; every other call works as documented.  Its BP reads the
