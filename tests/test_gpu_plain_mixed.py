@@ -1,6 +1,7 @@
-"""The mixed precision on the plain path (degree-4 graphs and chi = 16): complex64 Gamma, T and
-messages with FP32 contractions; FP64 QR/SVD in the gates, FP64 message normalisation and trace
-norms, FP64 eigen-decompositions and SVD in the regauge.  Against the oracle (1e-4 on marginals
+"""The mixed precision on the plain path (degree-4 graphs and chi = 16): complex64 Gamma and T,
+messages held as delta = m - m0 in complex64 with FP32 contractions of the delta terms; FP64
+QR/SVD in the gates, FP64 warm-start defect, normalisation and trace norms, FP64
+eigen-decompositions and SVD in the regauge.  Against the oracle (1e-4 on marginals
 and lambda, as for the persistent mixed path), against the FP64 plain path, the state round trip,
 and the residual kernel on a mixed state against the oracle's R of that state."""
 from __future__ import annotations
@@ -51,8 +52,8 @@ def test_plain_mixed_follows_the_oracle(case):
 
 def test_plain_mixed_state_round_trip_and_residual():
     """get_state / set_state reproduce the marginals bit for bit on a mixed plain state (the
-    messages are held as the absolute m in complex64), and the residual kernel equals the
-    oracle's R of the device's own state."""
+    messages are returned as m0 + delta in complex128, with unit trace), and the residual kernel
+    equals the oracle's R of the device's own state."""
     G = U.lib()
     inst = make_instance(10, 4, d=4)
     s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 4, inst.colour, G.gtqa_options_init(precision=G.GTQA_MIXED))
