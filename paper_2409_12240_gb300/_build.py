@@ -17,10 +17,13 @@ CSRC = os.path.join(PKG_DIR, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_PATH = os.path.join(PKG_DIR, "libgtqa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gtqa_api.cu", "gtqa_fp64_gates.cu", "gtqa_fp64_bp.cu", "gtqa_fp64_regauge.cu",
-           "gtqa_mixed_gates.cu", "gtqa_mixed_bp.cu", "gtqa_mixed_regauge.cu", "gtqa_diag.cu",
-           "gtqa_static.cu", "gtqa_fp64_general.cu", "gtqa_mixed_general.cu",
-           "gtqa_plain.cu"]
+# (source, object name, extra defines): gtqa_units.cu is compiled once per precision mode
+# and kernel family, so the eight instantiation sets build in parallel
+_UNIT_NAMES = ("gates", "bp", "regauge", "general")
+SOURCES = [("gtqa_api.cu", "gtqa_api", []), ("gtqa_diag.cu", "gtqa_diag", []),
+           ("gtqa_static.cu", "gtqa_static", []), ("gtqa_plain.cu", "gtqa_plain", [])] + [
+    ("gtqa_units.cu", f"gtqa_{mode.lower()[4:]}_{name}", [f"-DGTQA_UNIT_MODE={mode}", f"-DGTQA_UNIT={u}"])
+    for mode in ("ModeFP64", "ModeMixed") for u, name in enumerate(_UNIT_NAMES)]
 
 
 def _nvcc() -> str:
@@ -50,10 +53,10 @@ def build(force: bool = False, verbose: bool = False, extra: Optional[List[str]]
     nvcc = _nvcc()
     objs = []
     procs = []
-    for src in SOURCES:
-        obj = os.path.join(PKG_DIR, "_build", src.replace(".cu", ".o"))
+    for src, name, defs in SOURCES:
+        obj = os.path.join(PKG_DIR, "_build", name + ".o")
         os.makedirs(os.path.dirname(obj), exist_ok=True)
-        cmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+        cmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, *defs,
                "-c", os.path.join(CSRC, src), "-o", obj] + (extra or [])
         if verbose:
             print(" ".join(cmd))

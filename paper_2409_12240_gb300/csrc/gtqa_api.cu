@@ -1065,8 +1065,8 @@ int d4_bp(gtqa_state* s, double tol, int max_iter, uint32_t flags, int32_t* iter
 cudaError_t residual_launch(gtqa_state* s) {
     if (s->plain)
         return plain_residual_launch(s->CHI, s->D, pm(s), s->Gamma, s->lam, s->vslots4, s->n, s->rbuf, s->stream);
-    return mixed(s) ? residual_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream)
-                    : residual_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream);
+    return mixed(s) ? AuxUnit<ModeMixed>::residual(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream)
+                    : AuxUnit<ModeFP64>::residual(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rbuf, s->stream);
 }
 
 // The regauge policy (Sec. II C) on the plain path: after the gates of each layer the host
@@ -1383,9 +1383,9 @@ int gtqa_sample(gtqa_state* s, int32_t k, const int32_t* order, const double* u,
         if (rc && rc != GTQA_ERR_NOT_CONVERGED) return rc;
     }
     for (int q = 0; q < k && !s->plain; ++q) {
-        const cudaError_t e = mixed(s) ? sample_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, order[q], u[q], q,
+        const cudaError_t e = mixed(s) ? AuxUnit<ModeMixed>::sample(s->CHI, s->Gamma, s->lam, s->vert_edges, order[q], u[q], q,
                                                              s->xs, s->ps, s->stream)
-                                       : sample_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, order[q], u[q], q,
+                                       : AuxUnit<ModeFP64>::sample(s->CHI, s->Gamma, s->lam, s->vert_edges, order[q], u[q], q,
                                                             s->xs, s->ps, s->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -1445,8 +1445,8 @@ int gtqa_apply_gates(gtqa_state* s, int32_t k, const int32_t* edge, const double
         a.chi = s->chi;
         a.svd_cut = s->svd_cutoff;
         const cudaError_t e = s->plain    ? plain_general_gates_launch(s->CHI, s->D, pm(s), a, s->stream)
-                              : mixed(s) ? general_gates_launch_mixed(s->CHI, a, s->stream)
-                                         : general_gates_launch_fp64(s->CHI, a, s->stream);
+                              : mixed(s) ? GeneralUnit<ModeMixed>::gates(s->CHI, a, s->stream)
+                                         : GeneralUnit<ModeFP64>::gates(s->CHI, a, s->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             s->sticky = GTQA_ERR_CUDA;
@@ -1501,8 +1501,8 @@ int gtqa_apply_single_qubit_gates(gtqa_state* s, int32_t k, const int32_t* verte
         return GTQA_ERR_CUDA;
     const cudaError_t e = s->plain ? plain_single_gates_launch(s->CHI, s->D, pm(s), s->Gamma, s->sq_vertex, s->sq_W,
                                                                cnt, s->stream)
-                          : mixed(s) ? single_gates_launch_mixed(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream)
-                                     : single_gates_launch_fp64(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream);
+                          : mixed(s) ? GeneralUnit<ModeMixed>::single(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream)
+                                     : GeneralUnit<ModeFP64>::single(s->CHI, s->Gamma, s->sq_vertex, s->sq_W, cnt, s->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         s->sticky = GTQA_ERR_CUDA;
@@ -1855,9 +1855,9 @@ int gtqa_marginals(gtqa_state* s, double* rho_out, int8_t* sign_out) {
         const cudaError_t e =
             s->plain ? plain_marginals_launch(s->CHI, s->D, pm(s), s->Gamma, s->lam, s->vslots4, s->n, s->rho,
                                               s->sign, s->flags, s->stream)
-            : mixed(s) ? marginals_launch_mixed(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho, s->sign,
+            : mixed(s) ? AuxUnit<ModeMixed>::marginals(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho, s->sign,
                                                 s->flags, s->stream)
-                       : marginals_launch_fp64(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho, s->sign,
+                       : AuxUnit<ModeFP64>::marginals(s->CHI, s->Gamma, s->lam, s->vert_edges, s->n, s->rho, s->sign,
                                                s->flags, s->stream);
         if (!cuda_ok(s, e)) return GTQA_ERR_CUDA;
         s->launches += 1;

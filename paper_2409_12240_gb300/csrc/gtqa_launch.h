@@ -1,5 +1,5 @@
-// Host-side launchers of the annealing kernels.  One translation unit per
-// (precision mode, phase kernel) so the six instantiation sets compile in parallel.
+// Host-side launchers of the annealing kernels and the dispatch on precision mode and
+// phase kernel.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -18,36 +18,35 @@ enum PhaseKernel { PK_GATES = 0, PK_BP = 1, PK_REGAUGE = 2, PK_COUNT = 3 };
 // (padded to 8 bytes), two FP64 thresholds and one float threshold.
 inline size_t bp_instance_smem(long long B) { return (12 * (size_t)B + 7) / 8 * 8 + 20 * (size_t)B; }
 
-#define GTQA_DECLARE_PHASE(MODE, PHASE)                                                                 \
-    bool PHASE##_##MODE##_shape(int CHI, size_t* smem_base, int* tpb);                                  \
-    cudaError_t PHASE##_##MODE##_prepare(int CHI, size_t smem, int* blocks_per_sm);                      \
-    cudaError_t PHASE##_##MODE##_launch(int CHI, const Ctx& c, size_t smem, cudaStream_t st);
-GTQA_DECLARE_PHASE(fp64, gates)
-GTQA_DECLARE_PHASE(fp64, bp)
-GTQA_DECLARE_PHASE(fp64, regauge)
-GTQA_DECLARE_PHASE(mixed, gates)
-GTQA_DECLARE_PHASE(mixed, bp)
-GTQA_DECLARE_PHASE(mixed, regauge)
-#undef GTQA_DECLARE_PHASE
+// Launchers of the persistent phase kernels of one precision mode.  The definitions
+// (gtqa_units.cuh) are compiled only in gtqa_units.cu, which the build compiles once per
+// (mode, phase) with an explicit instantiation, so the instantiation sets build in
+// parallel; every other unit links against them.
+template <class Mode, int PK>
+struct PhaseUnit {
+    static bool shape(int CHI, size_t* smem_base, int* tpb);
+    static cudaError_t prepare(int CHI, size_t smem, int* blocks_per_sm);
+    static cudaError_t launch(int CHI, const Ctx& c, size_t smem, cudaStream_t st);
+};
 
-cudaError_t sample_launch_fp64(int CHI, void* Gamma, const double* lam, const int4* vert_edges, int a, double u,
-                               int step, int8_t* x, double* p, cudaStream_t st);
-cudaError_t sample_launch_mixed(int CHI, void* Gamma, const double* lam, const int4* vert_edges, int a, double u,
-                                int step, int8_t* x, double* p, cudaStream_t st);
-cudaError_t residual_launch_fp64(int CHI, const void* Gamma, const double* lam, const int4* vert_edges, int n,
-                                 double* out, cudaStream_t st);
-cudaError_t residual_launch_mixed(int CHI, const void* Gamma, const double* lam, const int4* vert_edges, int n,
-                                  double* out, cudaStream_t st);
-cudaError_t marginals_launch_fp64(int CHI, const void* Gamma, const double* lam, const int4* vert_edges, int n,
-                                  cd* rho, int8_t* sign, int* flag, cudaStream_t st);
-cudaError_t marginals_launch_mixed(int CHI, const void* Gamma, const double* lam, const int4* vert_edges, int n,
-                                   cd* rho, int8_t* sign, int* flag, cudaStream_t st);
+// Marginals, residual and measurement-sampling kernels of one mode (instantiated in the
+// gates unit of that mode).
+template <class Mode>
+struct AuxUnit {
+    static cudaError_t marginals(int CHI, const void* Gamma, const double* lam, const int4* vert_edges, int n, cd* rho,
+                                 int8_t* sign, int* flag, cudaStream_t st);
+    static cudaError_t residual(int CHI, const void* Gamma, const double* lam, const int4* vert_edges, int n,
+                                double* out, cudaStream_t st);
+    static cudaError_t sample(int CHI, void* Gamma, const double* lam, const int4* vert_edges, int a, double u,
+                              int step, int8_t* x, double* p, cudaStream_t st);
+};
 
-cudaError_t general_gates_launch_fp64(int CHI, const GenArgs& a, cudaStream_t st);
-cudaError_t general_gates_launch_mixed(int CHI, const GenArgs& a, cudaStream_t st);
-cudaError_t single_gates_launch_fp64(int CHI, void* Gamma, const int* vertex, const cd* W, int count, cudaStream_t st);
-cudaError_t single_gates_launch_mixed(int CHI, void* Gamma, const int* vertex, const cd* W, int count,
-                                      cudaStream_t st);
+// Arbitrary two-qubit and one-qubit gate kernels of one mode (degree 3).
+template <class Mode>
+struct GeneralUnit {
+    static cudaError_t gates(int CHI, const GenArgs& a, cudaStream_t st);
+    static cudaError_t single(int CHI, void* Gamma, const int* vertex, const cd* W, int count, cudaStream_t st);
+};
 
 // the plain path; pm selects the precision: 0 FP64, 1 mixed (degree 4 with CHI in {2, 4},
 // degree 3 with CHI = 16 for both) or 2 complex64 (degree 3 with CHI in {2, 4, 8, 16}, degree 4
@@ -71,23 +70,32 @@ cudaError_t ising16_gates_launch(const Gate16Args& a, int pm, cudaStream_t st);
 
 inline bool phase_shape(bool mixed, int pk, int CHI, size_t* sb, int* tpb) {
     switch (pk) {
-        case PK_GATES: return mixed ? gates_mixed_shape(CHI, sb, tpb) : gates_fp64_shape(CHI, sb, tpb);
-        case PK_BP: return mixed ? bp_mixed_shape(CHI, sb, tpb) : bp_fp64_shape(CHI, sb, tpb);
-        default: return mixed ? regauge_mixed_shape(CHI, sb, tpb) : regauge_fp64_shape(CHI, sb, tpb);
+        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::shape(CHI, sb, tpb)
+                                    : PhaseUnit<ModeFP64, PK_GATES>::shape(CHI, sb, tpb);
+        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::shape(CHI, sb, tpb)
+                                 : PhaseUnit<ModeFP64, PK_BP>::shape(CHI, sb, tpb);
+        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::shape(CHI, sb, tpb)
+                              : PhaseUnit<ModeFP64, PK_REGAUGE>::shape(CHI, sb, tpb);
     }
 }
 inline cudaError_t phase_prepare(bool mixed, int pk, int CHI, size_t smem, int* bps) {
     switch (pk) {
-        case PK_GATES: return mixed ? gates_mixed_prepare(CHI, smem, bps) : gates_fp64_prepare(CHI, smem, bps);
-        case PK_BP: return mixed ? bp_mixed_prepare(CHI, smem, bps) : bp_fp64_prepare(CHI, smem, bps);
-        default: return mixed ? regauge_mixed_prepare(CHI, smem, bps) : regauge_fp64_prepare(CHI, smem, bps);
+        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::prepare(CHI, smem, bps)
+                                    : PhaseUnit<ModeFP64, PK_GATES>::prepare(CHI, smem, bps);
+        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::prepare(CHI, smem, bps)
+                                 : PhaseUnit<ModeFP64, PK_BP>::prepare(CHI, smem, bps);
+        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::prepare(CHI, smem, bps)
+                              : PhaseUnit<ModeFP64, PK_REGAUGE>::prepare(CHI, smem, bps);
     }
 }
 inline cudaError_t phase_launch(bool mixed, int pk, int CHI, const Ctx& c, size_t smem, cudaStream_t st) {
     switch (pk) {
-        case PK_GATES: return mixed ? gates_mixed_launch(CHI, c, smem, st) : gates_fp64_launch(CHI, c, smem, st);
-        case PK_BP: return mixed ? bp_mixed_launch(CHI, c, smem, st) : bp_fp64_launch(CHI, c, smem, st);
-        default: return mixed ? regauge_mixed_launch(CHI, c, smem, st) : regauge_fp64_launch(CHI, c, smem, st);
+        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::launch(CHI, c, smem, st)
+                                    : PhaseUnit<ModeFP64, PK_GATES>::launch(CHI, c, smem, st);
+        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::launch(CHI, c, smem, st)
+                                 : PhaseUnit<ModeFP64, PK_BP>::launch(CHI, c, smem, st);
+        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::launch(CHI, c, smem, st)
+                              : PhaseUnit<ModeFP64, PK_REGAUGE>::launch(CHI, c, smem, st);
     }
 }
 

@@ -51,9 +51,9 @@ int setup(int dev, void** addr, size_t* smem) {
         }
         size_t base = 0;
         int tpb = 0, bps = 0;
-        if (!bp_fp64_shape(kChi, &base, &tpb)) return GTQA_ERR_UNSUPPORTED;
+        if (!PhaseUnit<ModeFP64, PK_BP>::shape(kChi, &base, &tpb)) return GTQA_ERR_UNSUPPORTED;
         const size_t sm = (base + bp_instance_smem(1) + 15) / 16 * 16;
-        if (bp_fp64_prepare(kChi, sm, &bps) != cudaSuccess || bps < 1) {
+        if (PhaseUnit<ModeFP64, PK_BP>::prepare(kChi, sm, &bps) != cudaSuccess || bps < 1) {
             cudaGetLastError();
             return GTQA_ERR_CUDA;
         }
@@ -132,7 +132,7 @@ extern "C" int gtqa_bp_static(int32_t n, int32_t m, const int32_t* vert_edges, c
     c.nblocks = sms;
     c.bar_expect = sms;
     c.spin_limit = 1LL << 22;
-    if (bp_fp64_launch(kChi, c, smem, st) != cudaSuccess) {
+    if (PhaseUnit<ModeFP64, PK_BP>::launch(kChi, c, smem, st) != cudaSuccess) {
         cudaGetLastError();
         return GTQA_ERR_CUDA;
     }
