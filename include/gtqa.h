@@ -96,6 +96,10 @@ typedef struct gtqa_stats_t {
     int64_t launches;        /* kernels launched by the library since creation */
     int64_t bp_calls;        /* BP runs since creation (one per layer in gtqa_anneal) */
     int64_t bp_not_converged_calls; /* BP runs in which some instance reached max_iter */
+    int64_t bp_exact_passes; /* separate passes computing the exact trace-norm distance of a sweep
+                                (persistent path: when a sweep's lower bound falls under tol) */
+    int64_t regauge_svd_sweeps; /* Jacobi sweeps of the regauge's eigen-decompositions and SVDs
+                                   (persistent path; work counter) */
 } gtqa_stats_t;
 
 /* kernels timed by the optional profiler (gtqa_profile) */
@@ -369,6 +373,13 @@ int gtqa_stats(gtqa_state* s, gtqa_stats_t* out);
  * layouts above; any pointer may be NULL to skip that array) or overwrite it (set:
  * every pointer required; lambda must be >= 0 and zero exactly beyond each bond's
  * dimension).  Used to start the library and a reference from identical states.
+ * Messages are those of the last BP run, in the gauge that run saw: the gates and the
+ * regauge change Gamma and lambda but not the messages.  In GTQA_MIXED the device holds
+ * delta = m - diag(lambda)/sum(lambda) and get_state returns diag(lambda)/sum(lambda) + delta
+ * with the current lambda; after gates or a regauge that sum is re-based on the new lambda
+ * and is not the message of any BP run (the stale messages of the other modes are not
+ * either).  A BP run without GTQA_BP_WARM_START continues from these values; runs with the
+ * warm start (gtqa_anneal and the default flags) do not read them.
  */
 int gtqa_get_state(gtqa_state* s, double* gamma_out, double* lambda_out, double* messages_out);
 int gtqa_set_state(gtqa_state* s, const double* gamma, const double* lambda, const double* messages);
@@ -452,10 +463,14 @@ int gtqa_barrier_bench(int32_t threads, int32_t rounds, double* us_per_barrier);
  * file-scope device array of about 5.5 MiB that every GPU loading the library holds
  * until the process exits.  n > GTQA_STATIC_MAX_N or m > GTQA_STATIC_MAX_M, host
  * pointers, or bad sizes return GTQA_ERR_INVALID_ARG before any device work.  The
- * first call on a device looks up the array's address and sets the kernel's shared
- * memory limit; make that first call before any stream capture.  All calls share the
- * one array: calls that overlap on the GPU (other streams, other threads) race.
- * Synchronises the stream.  Returns GTQA_ERR_NOT_CONVERGED when max_iter was reached.
+ * contents of vert_edges and edge_info are checked by a small kernel before BP runs
+ * (degree 0..3, edge ids in [0, m), slots that agree between the two arrays, -1 past the
+ * degree); a violation returns GTQA_ERR_INVALID_ARG and BP does not run.  Every call
+ * looks up the array's device address (cudaGetSymbolAddress, which allocates nothing)
+ * and sets the BP kernel's shared-memory limit, so calls remain valid after a device
+ * reset.  All calls share the one array: calls that overlap on the GPU (other streams,
+ * other threads) race.  Synchronises the stream.  Returns GTQA_ERR_NOT_CONVERGED when
+ * max_iter was reached.
  */
 #define GTQA_STATIC_CHI 4
 #define GTQA_STATIC_MAX_N 2048

@@ -65,6 +65,7 @@ struct Control {
     long long nc_calls;      // BP calls in which some instance hit max_iter
     long long regauged;      // regauge-policy layers: regauged (BP and gauge finding ran)
     long long reg_skipped;   // and skipped (R at or below the threshold)
+    long long exact_passes;  // separate exact-distance passes (bp_exact_pass) run by BP
 };
 
 struct Ctx {
@@ -96,7 +97,7 @@ struct Ctx {
     int* inst_done;
     int* inst_iters;
     double* inst_dist;
-    double* stats;            // discarded weight, log fidelity, SVD pairs, SVD rotations
+    double* stats;            // discarded weight, log fidelity, gate SVD pairs and rotations, regauge SVD sweeps
     Control* ctl;
     unsigned long long* bar;  // barrier counter of this launch (null: ctl->bar_count)
     // parameters
@@ -992,12 +993,14 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
         // FP32-preconditioned path, whose result is FP64-accurate as well
         const int x = tid / GJ, g = tid % GJ;
         WarpGroup grp{group_mask<GJ>()};
+        int sw;
         if constexpr (Mode::mixed)
-            mixed_svd<CHI>(sm.Am[x], sm.Vm[x], sm.A32[x], sm.V32[x], sm.T1[x], sm.T2[x], sm.nrm[x], g, grp,
-                           group_mask<CHI>(), 1e-13, 3e-7, nullptr);
+            sw = mixed_svd<CHI>(sm.Am[x], sm.Vm[x], sm.A32[x], sm.V32[x], sm.T1[x], sm.T2[x], sm.nrm[x], g, grp,
+                                group_mask<CHI>(), 1e-13, 3e-7, nullptr);
         else
-            jacobi_svd<CHI, double, WarpGroup, true, true>(sm.Am[x], sm.Vm[x], g, grp, group_mask<CHI>(), 1e-15, 60, true,
-                                                           nullptr, 3e-8);
+            sw = jacobi_svd<CHI, double, WarpGroup, true, true>(sm.Am[x], sm.Vm[x], g, grp, group_mask<CHI>(), 1e-15, 60,
+                                                                true, nullptr, 3e-8);
+        if (g == 0) atomicAdd(&c.stats[4], (double)sw);
     }
     team_bar<TEAM>(team);
     for (int t = tid; t < 2 * CHI; t += TEAM) {
@@ -1040,12 +1043,14 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
     team_bar<TEAM>(team);
     if (tid < GJ) {
         WarpGroup grp{group_mask<GJ>()};
+        int sw;
         if constexpr (Mode::mixed)
-            mixed_svd<CHI>(sm.M, sm.VM, sm.A32[0], sm.V32[0], sm.T1[0], sm.T2[0], sm.nrm[0], tid, grp,
-                           group_mask<CHI>(), 1e-13, 3e-7, nullptr);
+            sw = mixed_svd<CHI>(sm.M, sm.VM, sm.A32[0], sm.V32[0], sm.T1[0], sm.T2[0], sm.nrm[0], tid, grp,
+                                group_mask<CHI>(), 1e-13, 3e-7, nullptr);
         else
-            jacobi_svd<CHI, double, WarpGroup, true, true>(sm.M, sm.VM, tid, grp, group_mask<CHI>(), 1e-15, 60, true,
-                                                           nullptr, 3e-8);
+            sw = jacobi_svd<CHI, double, WarpGroup, true, true>(sm.M, sm.VM, tid, grp, group_mask<CHI>(), 1e-15, 60, true,
+                                                                nullptr, 3e-8);
+        if (tid == 0) atomicAdd(&c.stats[4], (double)sw);
     }
     team_bar<TEAM>(team);
     for (int cc = tid; cc < CHI; cc += TEAM) {
@@ -1343,6 +1348,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 const int fl = sflag[it & 1];
                 if (threadIdx.x == 0) sflag[(it + 1) & 1] = 0;
                 if (fl & 1) {
+                    if (blockIdx.x == 0 && threadIdx.x == 0) ++c.ctl->exact_passes;
                     bp_exact_pass<CHI, Mode>(c, cur, need, scratch, bsum + 32, ex);
                     if (!grid_sync(gb, c.spin_limit)) return;
                     for (int b = threadIdx.x; b < c.B; b += S::TPB) {

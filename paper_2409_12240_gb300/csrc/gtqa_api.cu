@@ -48,7 +48,8 @@ struct gtqa_state {
     int* inst_done = nullptr;
     int* inst_iters = nullptr;
     double* inst_dist = nullptr;
-    double* stats = nullptr;    // discarded weight, log fidelity, SVD pairs, SVD rotations
+    double* stats = nullptr;    // [kStats]: discarded weight, log fidelity, gate SVD pairs, gate SVD rotations,
+                                // regauge SVD sweeps
     Control* ctl = nullptr;
     cd* rho = nullptr;
     int8_t* sign = nullptr;
@@ -96,6 +97,8 @@ struct gtqa_state {
 };
 
 namespace {
+
+constexpr int kStats = 8;   // entries of the device statistics buffer (five in use)
 
 bool cuda_ok(gtqa_state* s, cudaError_t e) {
     if (e != cudaSuccess) {
@@ -712,7 +715,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         (rc = dalloc(s, &s->iso, iso.size())) || (rc = dalloc(s, &s->inst_vbeg, B + 1)) ||
         (rc = dalloc(s, &s->inst_m, B)) || (rc = dalloc(s, &s->acc, 6 * (size_t)B)) ||
         (rc = dalloc(s, &s->inst_done, B)) || (rc = dalloc(s, &s->inst_iters, B)) ||
-        (rc = dalloc(s, &s->inst_dist, B)) || (rc = dalloc(s, &s->stats, 4)) || (rc = dalloc(s, &s->ctl, 1)) ||
+        (rc = dalloc(s, &s->inst_dist, B)) || (rc = dalloc(s, &s->stats, kStats)) || (rc = dalloc(s, &s->ctl, 1)) ||
         (rc = dalloc(s, &s->rho, (size_t)s->n * 4)) || (rc = dalloc(s, &s->sign, s->n)) ||
         (rc = dalloc(s, &s->flags, 4)) || (rc = dalloc(s, &s->rbuf, 1)) ||
         (rc = dalloc(s, &s->cutbuf, std::max(s->m, 1))) || (rc = dalloc(s, &s->xs, s->n)) ||
@@ -767,7 +770,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
               (iso.empty() || cuda_ok(s, cudaMemcpyAsync(s->iso, iso.data(), sizeof(int) * iso.size(), cudaMemcpyHostToDevice, st))) &&
               cuda_ok(s, cudaMemcpyAsync(s->inst_vbeg, vbeg.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->inst_m, minst.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st)) &&
-              cuda_ok(s, cudaMemsetAsync(s->stats, 0, sizeof(double) * 4, st)) &&
+              cuda_ok(s, cudaMemsetAsync(s->stats, 0, sizeof(double) * kStats, st)) &&
               cuda_ok(s, cudaMemcpyAsync(s->ctl, &ctl0, sizeof(Control), cudaMemcpyHostToDevice, st)) &&
               cuda_ok(s, cudaMemsetAsync(s->flags, 0, sizeof(int) * 4, st)) && cuda_ok(s, cudaStreamSynchronize(st));
     if (!ok) {
@@ -1222,7 +1225,7 @@ int gtqa_autotune(gtqa_state* s, double tau, double dt, double tol, int32_t max_
                              {s->msg[0], mel * eb, {}}, {s->msg[1], mel * eb, {}},
                              {s->X, sizeof(cd) * s->m * 2 * s->CHI * s->CHI, {}},
                              {s->D0, mixed(s) ? sizeof(cf) * mel : 0, {}}, {s->t0, mixed(s) ? sizeof(cd) * 2 * s->m : 0, {}},
-                             {s->stats, sizeof(double) * 4, {}}, {s->ctl, sizeof(Control), {}},
+                             {s->stats, sizeof(double) * kStats, {}}, {s->ctl, sizeof(Control), {}},
                              {s->acc, sizeof(double) * 6 * s->B, {}}, {s->inst_done, sizeof(int) * s->B, {}},
                              {s->inst_iters, sizeof(int) * s->B, {}}, {s->inst_dist, sizeof(double) * s->B, {}}};
     for (auto& b : bufs) {
@@ -1879,7 +1882,7 @@ int gtqa_marginals(gtqa_state* s, double* rho_out, int8_t* sign_out) {
 
 int gtqa_stats(gtqa_state* s, gtqa_stats_t* out) {
     if (!s || !out) return GTQA_ERR_INVALID_ARG;
-    double st[4] = {0.0, 0.0, 0.0, 0.0};
+    double st[kStats] = {};
     Control ctl;
     if (!cuda_ok(s, cudaMemcpyAsync(st, s->stats, sizeof(st), cudaMemcpyDeviceToHost, s->stream)) ||
         !cuda_ok(s, cudaMemcpyAsync(&ctl, s->ctl, sizeof(ctl), cudaMemcpyDeviceToHost, s->stream)) ||
@@ -1898,6 +1901,8 @@ int gtqa_stats(gtqa_state* s, gtqa_stats_t* out) {
     out->launches = s->launches;
     out->bp_calls = ctl.bp_calls;
     out->bp_not_converged_calls = ctl.nc_calls;
+    out->bp_exact_passes = ctl.exact_passes;
+    out->regauge_svd_sweeps = (int64_t)st[4];
     return ctl.err ? ctl.err : GTQA_OK;
 }
 

@@ -7,7 +7,8 @@
 // CHI = 16 and degree 4 with CHI <= 4 in complex64 with every step in FP32 (the complex64 mode,
 // R = RC = float).  One instance.  The messages hold m itself in FP64 and complex64 and, as on
 // the persistent path, delta = m - m0 with m0 = diag(lambda)/sum(lambda) in the mixed mode
-// (BP contracts only the delta terms in FP32 against the FP64 warm-start defect D0).
+// (BP contracts only the delta terms in FP32; the warm-start defect D0 is computed in FP64 and
+// stored in complex64, its trace t0 in complex128).
 //
 // Layout: Gamma and T are [n][2][CHI]^D (slot k = k-th incident edge in ascending id, stride
 // CHI^(D-1-k); phantom slots of vertices with fewer edges have dimension 1 with lambda = e_0);

@@ -12,7 +12,6 @@
 #include "gtqa_launch.h"
 
 #include <cstring>
-#include <mutex>
 
 using namespace gtqa;
 
@@ -34,35 +33,62 @@ constexpr size_t kBytes = align256(kOffVinst + sizeof(int) * (size_t)GTQA_STATIC
 // Every GPU that loads this library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_bp_scratch[kBytes];
 
-std::mutex g_mutex;
-void* g_addr[64] = {};
-size_t g_smem[64] = {};
-
-// One-time set-up per device (with that device current): the device address of the
-// scratch array and the shared-memory opt-in of the BP kernel.
-int setup(int dev, void** addr, size_t* smem) {
-    if (dev < 0 || dev >= 64) return GTQA_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_bp_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return GTQA_ERR_CUDA;
-        }
-        size_t base = 0;
-        int tpb = 0, bps = 0;
-        if (!PhaseUnit<ModeFP64, PK_BP>::shape(kChi, &base, &tpb)) return GTQA_ERR_UNSUPPORTED;
-        const size_t sm = (base + bp_instance_smem(1) + 15) / 16 * 16;
-        if (PhaseUnit<ModeFP64, PK_BP>::prepare(kChi, sm, &bps) != cudaSuccess || bps < 1) {
-            cudaGetLastError();
-            return GTQA_ERR_CUDA;
-        }
-        g_addr[dev] = p;
-        g_smem[dev] = sm;
+// Set-up on every call, with the caller's device current: the device address of the
+// scratch array (cudaGetSymbolAddress, which allocates nothing) and the BP kernel's
+// shared-memory opt-in.  Neither is cached, so a call after a device reset (which reloads
+// the module and drops the kernel attribute) still sees the live array and limit.
+int setup(void** addr, size_t* smem) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_bp_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return GTQA_ERR_CUDA;
     }
-    *addr = g_addr[dev];
-    *smem = g_smem[dev];
+    size_t base = 0;
+    int tpb = 0, bps = 0;
+    if (!PhaseUnit<ModeFP64, PK_BP>::shape(kChi, &base, &tpb)) return GTQA_ERR_UNSUPPORTED;
+    const size_t sm = (base + bp_instance_smem(1) + 15) / 16 * 16;
+    if (PhaseUnit<ModeFP64, PK_BP>::prepare(kChi, sm, &bps) != cudaSuccess || bps < 1) {
+        cudaGetLastError();
+        return GTQA_ERR_CUDA;
+    }
+    *addr = p;
+    *smem = sm;
     return GTQA_OK;
+}
+
+// Checks the caller's index arrays before BP follows them: every vertex has degree 0..3,
+// its slots below the degree hold edge ids in [0, m) whose endpoint and slot entries
+// name that vertex and slot, and the slots past the degree hold -1; every edge joins two
+// distinct vertices in [0, n) with slots in 0..2 that list the edge.  Any violation sets
+// *bad.  Only indices already checked to be in range are followed.
+__global__ void check_graph(const int4* ve, const int4* ei, int n, int m, int* bad) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    bool ok = true;
+    if (t < n) {
+        const int4 v = ve[t];
+        const int es[3] = {v.x, v.y, v.z};
+        ok = v.w >= 0 && v.w <= 3;
+        for (int k = 0; k < 3 && ok; ++k) {
+            if (k >= v.w) {
+                ok = es[k] == -1;
+            } else if (es[k] < 0 || es[k] >= m) {
+                ok = false;
+            } else {
+                const int4 x = ei[es[k]];
+                ok = (x.x == t && x.z == k) || (x.y == t && x.w == k);
+            }
+        }
+    } else if (t < n + m) {
+        const int e = t - n;
+        const int4 x = ei[e];
+        ok = x.x >= 0 && x.x < n && x.y >= 0 && x.y < n && x.x != x.y && x.z >= 0 && x.z < 3 && x.w >= 0 && x.w < 3;
+        if (ok) {
+            const int4 a = ve[x.x], b = ve[x.y];
+            const int sa[3] = {a.x, a.y, a.z}, sb[3] = {b.x, b.y, b.z};
+            ok = sa[x.z] == e && sb[x.w] == e;
+        }
+    }
+    if (!ok) atomicOr(bad, 1);
 }
 
 bool device_accessible(const void* p) {
@@ -92,13 +118,13 @@ extern "C" int gtqa_bp_static(int32_t n, int32_t m, const int32_t* vert_edges, c
     }
     void* base = nullptr;
     size_t smem = 0;
-    int rc = setup(dev, &base, &smem);
+    int rc = setup(&base, &smem);
     if (rc) return rc;
     unsigned char* sc = static_cast<unsigned char*>(base);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // Per-call initialisation of the parts that must start at zero or hold sizes; the
     // array keeps the previous call's contents otherwise.
-    const int ints[8] = {0, 0, 0, n, m, 0, 0, 0};   // done, iters, vbeg[0], vbeg[1], m
+    const int ints[8] = {0, 0, 0, n, m, 0, 0, 0};   // done, iters, vbeg[0], vbeg[1], m, index check flag
     if (cudaMemsetAsync(sc + kOffCtl, 0, sizeof(Control), st) != cudaSuccess ||
         cudaMemsetAsync(sc + kOffAcc, 0, sizeof(double) * 7, st) != cudaSuccess ||
         cudaMemcpyAsync(sc + kOffInt, ints, sizeof(ints), cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -106,6 +132,18 @@ extern "C" int gtqa_bp_static(int32_t n, int32_t m, const int32_t* vert_edges, c
         cudaGetLastError();
         return GTQA_ERR_CUDA;
     }
+    // the index arrays are checked on the device before the BP kernel reads through them
+    int* bad = reinterpret_cast<int*>(sc + kOffInt) + 5;
+    int hbad = 0;
+    check_graph<<<(n + m + 255) / 256, 256, 0, st>>>(reinterpret_cast<const int4*>(vert_edges),
+                                                     reinterpret_cast<const int4*>(edge_info), n, m, bad);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return GTQA_ERR_CUDA;
+    }
+    if (hbad) return GTQA_ERR_INVALID_ARG;
     Ctx c;
     std::memset(&c, 0, sizeof(c));
     c.edge_info = reinterpret_cast<const int4*>(edge_info);
