@@ -6,9 +6,15 @@ n = 1000 vertices (m = 1500 edges, 3-colour matching schedule from a Kempe-chain
 J_ab ~ N(0, 1), h_a ~ N(0, 0.1), bond dimension chi = 4, linear schedule over
 K = 3200 Trotter layers with dt = 0.2, BP tolerance 1e-8 (at most 100 sweeps).
 One step = one full annealing layer: every edge gate with truncation, the mixing
-layer, flooding BP to tolerance from the warm start, and Vidal-gauge finding.
+layer, flooding BP to tolerance from the warm start, and Vidal-gauge finding, replayed
+from the library's one-layer CUDA graph.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+Every run walks the whole anneal (layers 1..K).  With --steps S < K - W the S timed layers
+are spread evenly over W+1..K (the layers between them run untimed), so a short run samples
+the early, middle and late anneal alike; with S = K - W (the default) every layer after the
+warm-up is timed.
+
+    python bench.py [--gpus N] [--steps S] [--warmup W] [--precision fp64|mixed]
     python bench.py --impl reference ...     # the CPU oracle on the same workload
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs its own replica of
@@ -17,14 +23,17 @@ the workload (no collective on the data path) and the slowest rank's time counts
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import shutil
 import subprocess
 import sys
+import tempfile
 import time
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
-from typing import Tuple
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -34,10 +43,15 @@ METRIC = "Trotter layers/sec at n=1000, chi=4 (mixed vs FP64 GPU) at stated marg
 WL = dict(n=1000, seed=0, chi=4, K=3200, dt=0.2, tol=1e-8, max_iter=100)
 WORKLOAD_NAME = ("random 3-regular n=1000 (m=1500, 3-colour schedule), J~N(0,1), h~N(0,0.1), "
                  "chi=4, K=3200 layers, dt=0.2, BP tol 1e-8, max 100 sweeps")
+# the batched configuration: 256 instances with n uniform over even values in [50, 1000]
+BATCH_WL = dict(B=256, seed=0, chi=4, K=400, dt=0.05, tol=1e-8, max_iter=100)
+# the scale configuration: n = 100000, chi = 8
+SCALE_WL = dict(n=100000, seed=2, chi=8, K=500, dt=0.05, tol=1e-8, max_iter=100, warm=5, steps=10)
+SNAPSHOTS = (800, 1600, 2400, 3200)
 L2_FLUSH_BYTES = 256 << 20
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=None)
@@ -46,22 +60,41 @@ def parse():
     p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison run")
+    p.add_argument("--no-whole", action="store_true", help="skip the perturbed FP64 anneals of the whole-anneal report")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched legs")
+    p.add_argument("--no-scale", action="store_true", help="skip the n = 100000, chi = 8 leg")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     p.add_argument("--ncu-scale", type=int, default=None, metavar="N",
                    help="short run of the chi = 8 scale configuration's shape at n = N for ncu: five "
                         "layers, then one gates, one BP (10 sweeps) and one regauge launch")
     p.add_argument("--ncu-case", type=int, default=None, metavar="K0",
                    help="profiling case: anneal layers 1..K0, then one gates launch, one BP launch of 1 sweep "
                         "and, from the same state, one of 21 sweeps (warm start, no regauge); no timing")
-    p.add_argument("--budget", type=float, default=15.0, help=argparse.SUPPRESS)
-    a = p.parse_args()
+    p.add_argument("--budget", type=float, default=20.0, help=argparse.SUPPRESS)
+    a = p.parse_args(argv)
+    a.warmup = max(0, a.warmup)
     if a.steps is None:
         a.steps = WL["K"] - a.warmup
-    a.warmup = max(0, a.warmup)
-    if a.warmup + a.steps > WL["K"]:
-        a.steps = max(1, WL["K"] - a.warmup)
+    a.steps = max(1, min(a.steps, WL["K"] - a.warmup))
     return a
+
+
+def sample_layers(W: int, S: int, K: int) -> List[int]:
+    """The S timed layers: all of W+1..K when S = K - W, else S layers spread evenly over
+    W+1..K (first and last included)."""
+    if S >= K - W:
+        return list(range(W + 1, K + 1))
+    if S == 1:
+        return [K]
+    return sorted({W + 1 + int(round(i * (K - W - 1) / (S - 1))) for i in range(S)})
+
+
+def spread(xs: Sequence[int], k: int) -> List[int]:
+    """At most k entries of xs, evenly spaced, first and last included."""
+    if len(xs) <= k:
+        return list(xs)
+    return sorted({xs[int(i)] for i in np.linspace(0, len(xs) - 1, k).round()})
 
 
 def instance():
@@ -69,40 +102,47 @@ def instance():
     return make_instance(WL["n"], WL["seed"])
 
 
-# ---------------------------------------------------------------------------
-# CPU oracle, timed on a bounded sample of the workload
-# ---------------------------------------------------------------------------
-def oracle_sampled_rate(W: int, K: int, budget_s: float) -> dict:
-    """Layers/s of the CPU oracle on this workload.
+def energy(inst, x) -> float:
+    """Objective E(x) = sum J_ab x_a x_b + sum h_a x_a of the read-out (the annealer maximises it)."""
+    x = np.asarray(x, dtype=np.float64)
+    return float(np.sum(inst.J * x[inst.edges[:, 0]] * x[inst.edges[:, 1]]) + np.sum(inst.h * x))
 
-    W full oracle layers (k = 1..W) are run first.  Each of the K steps then times a
-    fraction f of one layer's per-unit work with the oracle's own functions: the gates
-    of f*m edges (in schedule order), the mixing gate on the matching share of
-    vertices, the symmetric split of the touched vertices, s BP message updates of
-    the 2 f m directed messages of those edges (s = sweeps the last full layer used),
-    and the per-edge Vidal-gauge step of those edges.  value = sum of fractions /
-    sum of times.  f is chosen so the K steps take about budget_s seconds.
+
+def compare_marginals(rho, sign, rho_ref, sign_ref) -> dict:
+    """max / mean |rho - rho_ref| and the sign agreement over the vertices whose reference
+    marginal is clear of the read-out tie (|rho00 - 1/2| > 1e-3); null when none is."""
+    err = np.abs(rho - rho_ref)
+    clear = np.abs(rho_ref[:, 0, 0].real - 0.5) > 1e-3
+    agree = float(np.mean(sign[clear] == sign_ref[clear])) if clear.any() else None
+    return {"max_abs": float(err.max()), "mean_abs": float(err.mean()), "sign_agreement": agree,
+            "clear_vertices": int(clear.sum())}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle, timed on a bounded sample of the same layers
+# ---------------------------------------------------------------------------
+def oracle_sampled_rate(steps: Sequence[dict], budget_s: float) -> dict:
+    """Layers/s of the CPU oracle on sampled layers of this workload.
+
+    Each step is one layer k from a given state (Gamma, lambda after layer k-1) with that
+    layer's BP sweep count s.  A step times a fraction f = q/m of the layer's per-unit work
+    with the oracle's own functions: the gates of q edges (in schedule order, from a rotating
+    offset), the mixing gate on the matching share of vertices, the symmetric split of the
+    touched vertices, s BP message updates of the 2q directed messages of those edges, and the
+    per-edge Vidal-gauge step of those edges.  q is sized by a short calibration step so that
+    every step takes about budget_s / len(steps) seconds.  The layer's time is estimated as
+    t / f, and value = steps / sum of the estimated layer times.
     """
     from oracle import gtqa_oracle as O
     inst = instance()
     n, m = inst.n, inst.m
-    st = O.plus_state(n, inst.edges)
-    deg = [len(x) for x in st.inc]
-    t_layer, s_ref = None, 1
-    for k in range(1, max(W, 1) + 1):
-        tZ, tX = O.schedule(k, WL["K"], WL["dt"])
-        t0 = time.perf_counter()
-        st, info = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, WL["chi"], WL["tol"], WL["max_iter"])
-        t_layer = time.perf_counter() - t0
-        s_ref = max(1, int(info["bp_iters"]))
-    f = min(1.0, budget_s / (K * t_layer))
-    q = max(1, int(round(f * m)))
     order = sorted(range(m), key=lambda e: (int(inst.colour[e]), e))
-    tot_t, tot_units = 0.0, 0.0
-    for j in range(K):
-        k = min(WL["K"], max(W, 1) + 1 + j)
+    per_step = budget_s / max(1, len(steps))
+
+    def one(st, k, s_k, off, q):
         tZ, tX = O.schedule(k, WL["K"], WL["dt"])
-        sel = [order[(j * q + i) % m] for i in range(q)]
+        deg = [len(x) for x in st.inc]
+        sel = [order[(off + i) % m] for i in range(q)]
         verts = sorted({int(x) for e in sel for x in inst.edges[e]})
         t0 = time.perf_counter()
         for e in sel:
@@ -121,7 +161,7 @@ def oracle_sampled_rate(W: int, K: int, budget_s: float) -> dict:
                 msgs[(e, 0)] = mm
                 msgs[(e, 1)] = mm
         new = {}
-        for _ in range(s_ref):
+        for _ in range(max(1, s_k)):
             for e in sel:
                 for a in (int(inst.edges[e][0]), int(inst.edges[e][1])):
                     key = O.directed(st, a, e)
@@ -132,24 +172,71 @@ def oracle_sampled_rate(W: int, K: int, budget_s: float) -> dict:
         view = O.VidalState(st.n, st.edges, st.inc, dict(T), {e: st.lam[e] for a in verts for e in st.inc[a]})
         for e in sel:
             O.vidal_gauge_edge(view, e, new)
-        tot_t += time.perf_counter() - t0
-        tot_units += q / m
-    return {"value": tot_units / tot_t, "unit": "layers/s", "cores": 1, "kind": "oracle",
-            "sample": (f"{max(W, 1)} full oracle layers from |+>, then {K} steps each timing {q} of {m} edges' "
-                       f"gate, {s_ref} BP update(s) of their {2 * q} directed messages, symmetric split, mixing "
-                       f"and regauge (fraction {q / m:.4f} of a layer per step), scaled to whole layers"),
-            "seconds": tot_t}
+        return time.perf_counter() - t0
+
+    est, qs, tot = [], [], 0.0
+    for j, sp in enumerate(steps):
+        q0 = 4   # calibration on a fresh copy of the state, then the timed step
+        tc = one(sp["state"](), sp["k"], sp["sweeps"], 0, q0)
+        q = int(min(m, max(1, round(q0 * per_step / max(tc, 1e-6)))))
+        t = one(sp["state"](), sp["k"], sp["sweeps"], (j * 97) % m, q)
+        est.append(t * m / q)
+        qs.append(q)
+        tot += t
+    return {"value": len(steps) / sum(est), "unit": "layers/s", "cores": 1, "kind": "oracle",
+            "seconds": tot, "edges_per_step": qs,
+            "layers": [int(sp["k"]) for sp in steps], "sweeps": [int(sp["sweeps"]) for sp in steps]}
 
 
-def cpu_baseline_subprocess(W: int, budget: float) -> dict:
+def cpu_sample_subprocess(path: str, budget: float) -> dict:
+    """Runs the oracle timing in a child process with BLAS threads pinned to 1."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    env.pop("WORLD_SIZE", None)
-    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample", "--warmup", str(W),
-           "--steps", "20", "--budget", str(budget)]
-    r = subprocess.run(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, timeout=900)
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        env.pop(k, None)
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample", path, "--budget", str(budget)]
+    r = subprocess.run(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, timeout=1200)
     if r.returncode != 0:
         return {"value": None, "error": r.stderr.decode(errors="replace")[-400:]}
     return json.loads(r.stdout.decode().strip().splitlines()[-1])
+
+
+def oracle_sample_main(path: str, budget: float) -> dict:
+    """Child-process entry: the sampled layers' states were saved by the FP64 GPU run."""
+    from oracle import gtqa_oracle as O
+    inst = instance()
+    with open(os.path.join(path, "layers.json")) as f:
+        meta = json.load(f)
+    steps = []
+    for k, s_k in zip(meta["layers"], meta["sweeps"]):
+        z = np.load(os.path.join(path, f"state_{k}.npz"))
+        G_, L_ = z["G"], z["L"]
+        steps.append({"k": k, "sweeps": s_k, "state": (lambda G_=G_, L_=L_: O.from_padded(inst.n, inst.edges, G_, L_))})
+    r = oracle_sampled_rate(steps, budget)
+    r["sample"] = (f"{len(steps)} layers spread over the anneal ({meta['layers'][0]}..{meta['layers'][-1]}), each from "
+                   f"the FP64 GPU state after the previous layer with its own BP sweep count "
+                   f"(mean {np.mean(meta['sweeps']):.1f}); per layer a fraction of the edges' gates, BP updates of "
+                   f"their directed messages, symmetric split, mixing and regauge, scaled to whole layers")
+    return r
+
+
+def oracle_own_states_rate(W: int, layers: Sequence[int], budget: float) -> dict:
+    """The reference arm: the oracle anneals layers 1..W itself (no GPU), and every timed step
+    is a sampled layer k from that state with the sweep count of the oracle's own layer W."""
+    from oracle import gtqa_oracle as O
+    inst = instance()
+    st = O.plus_state(inst.n, inst.edges)
+    s_ref = 1
+    for k in range(1, max(W, 1) + 1):
+        tZ, tX = O.schedule(k, WL["K"], WL["dt"])
+        st, info = O.gtqa_layer(st, inst.colour, inst.J, inst.h, tZ, tX, WL["chi"], WL["tol"], WL["max_iter"])
+        s_ref = max(1, int(info["bp_iters"]))
+    G_, L_ = O.to_padded(st, 4)
+    steps = [{"k": k, "sweeps": s_ref, "state": (lambda: O.from_padded(inst.n, inst.edges, G_, L_))} for k in layers]
+    r = oracle_sampled_rate(steps, budget)
+    r["sample"] = (f"{max(W, 1)} full oracle layers from |+>, then {len(steps)} steps at the sampled layers "
+                   f"{layers[0]}..{layers[-1]} from that state with its BP sweep count ({s_ref}); per step a fraction "
+                   f"of the edges' gates, BP updates, symmetric split, mixing and regauge, scaled to whole layers")
+    return r
 
 
 # ---------------------------------------------------------------------------
@@ -203,14 +290,14 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per unit (flop counts of the variant that runs)
+# algorithmic and executed work per unit
 # ---------------------------------------------------------------------------
 def storage_chi(chi: int) -> int:
     return 2 if chi <= 2 else (4 if chi <= 4 else 8)
 
 
 def gate_flops(chi: int, edges: int, pairs: int, rotations: int, mixed: bool = False):
-    """FP64 flops of the simple-update phase (real adds/muls, fma = 2).
+    """FP64 flops of the simple-update phase as executed (real adds/muls, fma = 2).
 
     Per edge at storage bond dimension C (rows R = C^2 per QR block, N = 2C):
       X = Gamma * lambda products  8C^3 + 2C^2
@@ -241,10 +328,14 @@ def gate_flops(chi: int, edges: int, pairs: int, rotations: int, mixed: bool = F
 def bp_sweep_flops(chi: int, vertices: int, mixed: bool) -> float:
     """Algorithmic flops of one flooding sweep (Eq. local_consistency) over `vertices` vertices
     of degree 3: per directed message 3 contractions of 2 chi^4 complex MACs = 48 chi^4 real
-    flops (the per-message figure of the method; FP32 in the mixed mode).  The mixed kernel
-    executes 4 contractions per message (64 chi^4, the delta-form update) and replaces the
-    per-message FP64 trace-norm eigen-decomposition by a bound; neither difference is counted."""
+    flops (the per-message figure of the method; FP32 in the mixed mode)."""
     return float(vertices * 3 * 48 * chi ** 4)
+
+
+def bp_sweep_flops_executed(chi: int, vertices: int, mixed: bool) -> float:
+    """Flops the BP kernel issues per sweep: the mixed kernel contracts the delta form
+    (4 contractions, 64 chi^4 per message, FP32); the FP64 kernel the 48 chi^4 of the method."""
+    return float(vertices * 3 * (64 if mixed else 48) * chi ** 4)
 
 
 def edge_gate_flops(chi: int) -> Tuple[float, float]:
@@ -260,6 +351,30 @@ def edge_gate_flops(chi: int) -> Tuple[float, float]:
     return float(tot), float(0.95 * tot)
 
 
+def regauge_edge_flops(chi: int) -> Tuple[float, float]:
+    """Algorithmic flops of the Vidal-gauge step of one edge (a7), in complex MACs of 8 flops:
+    two chi x chi Hermitian eigen-decompositions and one chi x chi SVD by one-sided Jacobi with
+    vectors (11 n per pair, 7.5 sweeps of n (n - 1) / 2 pairs each, n = chi), the square roots and
+    inverse square roots (2 x 2 chi^3), M (chi^3), the two transforms X (2 chi^3), all FP64; and
+    the two bond transforms applied to the vertex tensors (2 x 2 chi^4, FP32 in the mixed mode).
+    Returns (total, FP64 part)."""
+    n = chi
+    jac = 11 * n * (n * (n - 1) / 2) * 7.5
+    f64 = 8 * (3 * jac + 4 * chi ** 3 + chi ** 3 + 2 * chi ** 3)
+    return float(f64 + 8 * 4 * chi ** 4), float(f64)
+
+
+def regauge_flops_executed(chi: int, edges: int, svd_sweeps: int, mixed: bool) -> float:
+    """FP64 flops the regauge kernel issues: per counted Jacobi sweep (FP64 sweeps, or the FP64
+    polish sweeps of the mixed mode) (N - 1) N / 2 pairs of 14 N + 40 N + 15 flops at N = C;
+    per edge the Hermitian parts, roots, M and X (7 C^3 complex MACs), and in the mixed mode the
+    three Newton-Schulz steps and products (3 x 3 x 8 C^3)."""
+    C = storage_chi(chi)
+    per_sweep = (C - 1) * C / 2 * (54 * C + 15)
+    fixed = 8 * 7 * C ** 3 + (3 * 3 * 8 * C ** 3 if mixed else 0)
+    return float(svd_sweeps * per_sweep + edges * fixed)
+
+
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_n1000_chi4.json")
 TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2409_12240_gb300", "csrc", f) for f in ("gtqa_anneal.cuh", "gtqa_common.cuh")]
 
@@ -269,7 +384,6 @@ def kernel_traffic(kernel: str, mixed: bool, chi: int, sweeps_per_launch: float 
     ncu capture of `bench.py --ncu-case`; BP launches are scaled to this run's sweeps per launch
     from the captured 1-sweep and 21-sweep launches.  None if there is no capture for this mode
     or the kernel sources changed since it was taken."""
-    import hashlib
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)
@@ -285,39 +399,73 @@ def kernel_traffic(kernel: str, mixed: bool, chi: int, sweeps_per_launch: float 
     k = r[kernel]
     if kernel == "bp_kernel":
         return k["fixed_bytes"] + k["bytes_per_sweep"] * sweeps_per_launch
-    return k["bytes_per_launch"]
+    return k.get("bytes_per_launch")
 
 
-def per_layer_error(G, make, inst, k_last: int, samples: int = 6) -> dict:
-    """Marginal error introduced by one mixed-precision layer: at sampled layers k the
-    FP64 state after layer k-1 is loaded into a mixed and an FP64 state, layer k runs in
-    both, and max |rho_mixed - rho_fp64| over vertices is recorded."""
-    Ks, dt, tol, mi = WL["K"], WL["dt"], WL["tol"], WL["max_iter"]
-    ks = sorted({max(2, int(round(k_last * (i + 1) / samples))) for i in range(samples)})
-    ref = make(G.GTQA_FP64)
-    out, done = {}, 0
-    try:
-        for k in ks:
-            G.gtqa_anneal(ref, done + 1, k - 1, Ks, dt, tol, mi)
-            done = k - 1
-            Gm, L, Mg = G.gtqa_get_state(ref)
-            errs = []
-            rhos = []
-            for p in (G.GTQA_MIXED, G.GTQA_FP64):
-                s = make(p)
-                G.gtqa_set_state(s, Gm, L, Mg)
-                G.gtqa_anneal(s, k, k, Ks, dt, tol, mi)
-                rhos.append(G.gtqa_marginals(s))
-                G.gtqa_destroy(s)
-            (rm, sm_), (rf, sf) = rhos
-            clear = np.abs(rf[:, 0, 0].real - 0.5) > 1e-3
-            out[str(k)] = {"max_abs": float(np.abs(rm - rf).max()),
-                           "sign_agreement": float(np.mean(sm_[clear] == sf[clear]))}
-    finally:
-        G.gtqa_destroy(ref)
-    return {"max_abs": max(v["max_abs"] for v in out.values()),
-            "min_sign_agreement": min(v["sign_agreement"] for v in out.values()), "samples": out,
-            "note": "one layer in each mode from the same FP64 state at layer k-1"}
+class Peaks:
+    """ALU peaks derived from unit counts and the maximum SM clock (128 FP32 lanes and two FP64
+    FMA units per SM, 2 flops per FMA); the FMA microbenchmark is reported beside them."""
+
+    def __init__(self, G, sms: int, mhz: float):
+        self.sms, self.mhz = sms, mhz
+        self.fp32 = sms * 128 * 2 * mhz * 1e6 / 1e12
+        self.fp64 = sms * 2 * 2 * mhz * 1e6 / 1e12
+        self.fp64_meas = G.gtqa_alu_peak(True)
+        self.fp32_meas = G.gtqa_alu_peak(False)
+
+    def note(self, fp64: bool) -> str:
+        lanes, meas = ("2 FP64 FMA units", self.fp64_meas) if fp64 else ("128 FP32 lanes", self.fp32_meas)
+        return f"{self.sms} SMs x {lanes} x 2 flop x {self.mhz:.0f} MHz (derived); FMA microbenchmark {meas:.3f} TFLOP/s"
+
+
+def rooflines(prof: dict, dlt: dict, chi: int, n: int, m: int, mixed: bool, peaks: Peaks, traffic: bool) -> dict:
+    """Roofline objects of the three phase kernels from the library's per-launch CUDA events
+    (prof: {kernel: (launches, total ms, units)}) and the statistics over the same launches."""
+    out = {}
+    C = storage_chi(chi)
+    for kname, (nl, ms, units) in prof.items():
+        if not nl or kname not in ("gates_kernel", "bp_kernel", "regauge_kernel"):
+            continue
+        sec = ms * 1e-3
+        if kname == "gates_kernel":
+            _, f64e = edge_gate_flops(chi)
+            alg = f64e * units
+            exe = gate_flops(chi, units, int(dlt["svd_pairs"]), int(dlt["svd_rotations"]), mixed)[0]
+            peak, fp64 = peaks.fp64, True
+            unit_count = "edges per launch x the FP64 part (95 %) of the edge gate's algorithmic flops"
+            note = ("the mixed path runs the SVD's preconditioning sweeps in FP32, so it executes fewer FP64 flops "
+                    "than it is credited with" if mixed else "FP64 throughout")
+            tr = kernel_traffic(kname, mixed, chi) if traffic else None
+        elif kname == "bp_kernel":
+            sweeps = int(dlt["bp_sweeps"])
+            alg = bp_sweep_flops(chi, n, mixed) * sweeps
+            exe = bp_sweep_flops_executed(C, n, mixed) * sweeps
+            fp64 = not mixed
+            peak = peaks.fp32 if mixed else peaks.fp64
+            unit_count = "sweeps x 3n directed messages x 48 chi^4 flops"
+            note = ("flops of the BP sweeps only (the warm-start phase of each launch is not counted); the working "
+                    "set is L2-resident and each sweep ends in a grid barrier")
+            tr = kernel_traffic(kname, mixed, chi, sweeps / nl) if traffic else None
+        else:
+            _, f64e = regauge_edge_flops(chi)
+            alg = f64e * units
+            exe = regauge_flops_executed(chi, units, int(dlt["regauge_svd_sweeps"]), mixed)
+            peak, fp64 = peaks.fp64, True
+            unit_count = "edges per launch x the FP64 part of the Vidal-gauge step's algorithmic flops"
+            note = ("eigen-decompositions, SVD and roots in FP64 (the mixed mode's FP32 preconditioning sweeps are "
+                    "not counted as executed FP64)")
+            tr = kernel_traffic(kname, mixed, chi) if traffic else None
+        ach = alg / sec / 1e12
+        ex = exe / sec / 1e12
+        o = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+             "traffic": tr, "peak_source": peaks.note(fp64), "algorithmic_flops_per_launch": alg / nl,
+             "avg_launch_us": ms / nl * 1e3, "launches": nl, "unit_count": unit_count,
+             "executed_flops_per_launch": exe / nl, "executed_tflops": ex, "executed_frac": ex / peak, "note": note}
+        if kname == "bp_kernel":
+            o["sweeps_per_launch"] = int(dlt["bp_sweeps"]) / nl
+            o["us_per_sweep"] = ms * 1e3 / max(int(dlt["bp_sweeps"]), 1)
+        out[kname] = o
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -332,6 +480,83 @@ def replica_throughput(t_ms: float, K: int, world: int, dist=None, device: str =
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_ms = float(tt.item())
     return t_ms, world * K / (t_ms / 1e3)
+
+
+STAT_KEYS = ("launches", "bp_sweeps", "bp_calls", "bp_not_converged_calls", "svd_pairs", "svd_rotations",
+             "bp_exact_passes", "regauge_svd_sweeps")
+
+
+def walk(G, s, K: int, dt: float, tol: float, mi: int, timed: Sequence[int], stream, flush,
+         snaps: Sequence[int] = (), save_before: Sequence[int] = (), profile: bool = False, clocks=None,
+         dist=None, state_dir: Optional[str] = None) -> dict:
+    """Layers 1..K of one anneal through gtqa_anneal_graph.  Every layer in `timed` is bracketed
+    by CUDA events on the library's stream, after an L2 flush that lies outside the events; the
+    layers between timed ones run untimed.  With `profile`, the library's per-phase events of
+    the timed layers are summed (the roofline's kernel durations).  Returns the timed
+    milliseconds, statistics and profile deltas over the timed layers, per-timed-layer sweeps,
+    marginals at the snapshot layers, and (into state_dir) the state before given layers."""
+    import torch
+    timed = sorted(set(int(k) for k in timed))
+    tset, sset, bset = set(timed), set(snaps), set(save_before)
+    marks = sorted(tset | sset | bset)
+    ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in timed}
+    dsum = {k: 0 for k in STAT_KEYS}
+    psum: Dict[str, list] = {}
+    per_layer = {}
+    snap_out = {}
+    if profile:
+        G.gtqa_profile(s, True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    k = 1
+    with torch.cuda.stream(stream):
+        for e in marks:
+            if e > k:
+                G.gtqa_anneal_graph(s, k, e - 1, K, dt, tol, mi)
+            if e in bset and state_dir:
+                Gm, L, _ = G.gtqa_get_state(s)
+                np.savez(os.path.join(state_dir, f"state_{e}.npz"), G=Gm, L=L)
+            if e in tset:
+                st0 = G.gtqa_stats(s)
+                p0 = G.gtqa_profile_read(s) if profile else None
+                flush.fill_(e & 0xFF)
+                ev[e][0].record(stream)
+                G.gtqa_anneal_graph(s, e, e, K, dt, tol, mi)
+                ev[e][1].record(stream)
+                st1 = G.gtqa_stats(s)
+                for key in STAT_KEYS:
+                    dsum[key] += st1[key] - st0[key]
+                per_layer[e] = {"sweeps": st1["bp_sweeps"] - st0["bp_sweeps"],
+                                "max_iter": st1["bp_not_converged_calls"] - st0["bp_not_converged_calls"]}
+                if profile:
+                    p1 = G.gtqa_profile_read(s)
+                    for kn in p1:
+                        a0 = psum.setdefault(kn, [0, 0.0, 0])
+                        a0[0] += p1[kn][0] - p0[kn][0]
+                        a0[1] += p1[kn][1] - p0[kn][1]
+                        a0[2] += p1[kn][2] - p0[kn][2]
+            else:
+                G.gtqa_anneal_graph(s, e, e, K, dt, tol, mi)
+            if e in sset:
+                snap_out[e] = G.gtqa_marginals(s)
+            k = e + 1
+        if k <= K:
+            G.gtqa_anneal_graph(s, k, K, K, dt, tol, mi)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop() if clocks else None
+    if profile:
+        G.gtqa_profile(s, False)
+    t_ms = float(sum(ev[k][0].elapsed_time(ev[k][1]) for k in timed))
+    rho, sign = G.gtqa_marginals(s)
+    return {"t_ms": t_ms, "stats": dsum, "prof": {kn: tuple(v) for kn, v in psum.items()}, "per_layer": per_layer,
+            "snaps": snap_out, "rho": rho, "sign": sign, "clocks": ck}
 
 
 def run_gtqa(a):
@@ -349,129 +574,67 @@ def run_gtqa(a):
     mixed = a.precision == "mixed"
     prec = G.GTQA_MIXED if mixed else G.GTQA_FP64
     inst = instance()
-    W, K = a.warmup, a.steps
+    W, S = a.warmup, a.steps
     Ks, dt, tol, mi, chi = WL["K"], WL["dt"], WL["tol"], WL["max_iter"], WL["chi"]
-
-    cpu = None
-    if rank == 0 and world == 1 and not a.no_cpu:
-        cpu = cpu_baseline_subprocess(W, a.budget)
-
+    timed = sample_layers(W, S, Ks)
+    S = len(timed)
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    props = torch.cuda.get_device_properties(local)
 
-    def make(p):
-        return G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour,
+    def make(p, J=None, inst_=None):
+        x = inst_ or inst
+        return G.gtqa_create(x.n, x.edges, x.J if J is None else J, x.h, chi, x.colour,
                              G.gtqa_options_init(precision=p, cuda_stream=stream.cuda_stream))
 
-    def timed_window(p, clocks=None, profile=False):
-        """Warm-up layers 1..W, then layers W+1..W+K, one gtqa_anneal call per layer with an
-        L2 flush between layers (outside the events).  With `profile`, the library also
-        records CUDA events around each of its launches on the same stream (the per-kernel
-        durations of the roofline).  Returns (ms, stats delta, final rho, sign, clocks, prof)."""
-        s = make(p)
-        if W:
-            G.gtqa_anneal(s, 1, W, Ks, dt, tol, mi)
-        if profile:
-            G.gtqa_profile(s, True)
-        st0 = G.gtqa_stats(s)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-        with torch.cuda.stream(stream):
-            for j in range(K):
-                flush.fill_(j & 0xFF)
-                ev[j][0].record(stream)
-                G.gtqa_anneal(s, W + 1 + j, W + 1 + j, Ks, dt, tol, mi)
-                ev[j][1].record(stream)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        ck = clocks.stop() if clocks else None
-        t_ms = float(sum(e0.elapsed_time(e1) for e0, e1 in ev))
-        prof = G.gtqa_profile_read(s) if profile else None
-        st1 = G.gtqa_stats(s)
-        rho, sign = G.gtqa_marginals(s)
-        G.gtqa_destroy(s)
-        delta = {k: st1[k] - st0[k] for k in ("launches", "bp_sweeps", "bp_calls", "bp_not_converged_calls",
-                                               "svd_pairs", "svd_rotations")}
-        return t_ms, delta, rho, sign, ck, prof
-
+    # ---- the timed run of the chosen precision ----
     clocks = Clocks(local)
-    t_ms, dlt, rho_main, sign_main, ck, prof = timed_window(prec, clocks, profile=True)
-    t_ms, value = replica_throughput(t_ms, K, world, dist, "cuda")
-
-    # the FP64 path on the same layers, and the marginal error of the mixed path against it
-    fp64 = None
-    if mixed and not a.no_fp64:
-        t64, d64, rho64, sign64, _, _ = timed_window(G.GTQA_FP64)
-        err = np.abs(rho_main - rho64)
-        clear = np.abs(rho64[:, 0, 0].real - 0.5) > 1e-3
-        fp64 = {"value": world * K / (t64 / 1e3), "unit": "layers/s", "ms_per_step": t64 / K,
-                "bp_sweeps_per_layer": d64["bp_sweeps"] / K,
-                "speedup_mixed_over_fp64": t64 / t_ms,
-                "marginal_error_per_layer": per_layer_error(G, make, inst, W + K),
-                "trajectory_divergence_at_last_layer": {
-                    "max_abs": float(err.max()), "mean_abs": float(err.mean()),
-                    "sign_agreement": float(np.mean(sign_main[clear] == sign64[clear])), "at_layer": W + K,
-                    "note": "whole trajectories; BP stops at max_iter in part of the anneal, after which both "
-                            "runs follow the chaotic BP map and decorrelate"}}
-
-    # ---- roofline of the kernel with the largest share of the timed window ----
-    total_prof = sum(v[1] for v in prof.values())
-    dom = max(prof, key=lambda k: prof[k][1])
-    # ALU peaks derived from unit counts and the maximum SM clock: 128 FP32 lanes and 2 FP64
-    # FMA units per SM, 2 flops per FMA; the FMA microbenchmark is reported beside them
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    s = make(prec)
+    main = walk(G, s, Ks, dt, tol, mi, timed, stream, flush, snaps=SNAPSHOTS, profile=True, clocks=clocks, dist=dist)
+    G.gtqa_destroy(s)
+    t_ms, value = replica_throughput(main["t_ms"], S, world, dist, "cuda")
+    ck = main["clocks"]
     mhz = (ck or {}).get("sm_max_mhz") or 2070.0
-    fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
-    fp64_peak = sms * 2 * 2 * mhz * 1e6 / 1e12
-    fp64_meas = G.gtqa_alu_peak(True)
-    fp32_meas = G.gtqa_alu_peak(False)
-    peak_note = f"{sms} SMs x {{lanes}} x 2 flop x {mhz:.0f} MHz (derived); FMA microbenchmark {{meas:.3f}} TFLOP/s"
-    def roofline_of(kname):
-        nl, ms, units = prof[kname]
-        if not nl:
-            return None
-        if kname == "gates_kernel":
-            _, f64e = edge_gate_flops(chi)
-            f64 = f64e * units
-            ach = f64 / (ms * 1e-3) / 1e12
-            return {"kernel": kname, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": ach / fp64_peak, "traffic": kernel_traffic(kname, mixed, chi),
-                    "peak_source": peak_note.format(lanes="2 FP64 FMA units", meas=fp64_meas),
-                    "algorithmic_flops_per_launch": f64 / nl, "avg_launch_us": ms / nl * 1e3,
-                    "unit_count": "edges per launch x the FP64 part (95 %) of the edge gate's algorithmic flops",
-                    "executed_fp64_flops_per_launch": gate_flops(chi, units, int(dlt["svd_pairs"]),
-                                                                 int(dlt["svd_rotations"]), mixed)[0] / nl,
-                    "note": "the mixed path runs the SVD's preconditioning sweeps in FP32, so it executes fewer "
-                            "FP64 flops than it is credited with; the frac is against the FP64 peak"}
-        if kname == "bp_kernel":
-            sweeps = int(dlt["bp_sweeps"])
-            fl = bp_sweep_flops(chi, inst.n, mixed) * sweeps
-            peak = fp32_peak if mixed else fp64_peak
-            ach = fl / (ms * 1e-3) / 1e12
-            return {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": kernel_traffic(kname, mixed, chi, sweeps / nl),
-                    "peak_source": peak_note.format(lanes="128 FP32 lanes" if mixed else "2 FP64 FMA units",
-                                                    meas=fp32_meas if mixed else fp64_meas),
-                    "algorithmic_flops_per_launch": fl / nl, "avg_launch_us": ms / nl * 1e3,
-                    "sweeps_per_launch": sweeps / nl, "us_per_sweep": ms * 1e3 / max(sweeps, 1),
-                    "unit_count": "sweeps x 3n directed messages x 48 chi^4 flops",
-                    "note": "flops of the BP sweeps only (the warm-start phase of each launch is not counted); "
-                            "the working set is L2-resident and each sweep is bounded by a grid barrier"}
-        return None
+    peaks = Peaks(G, props.multi_processor_count, mhz)
+    roofs = rooflines(main["prof"], main["stats"], chi, inst.n, inst.m, mixed, peaks, traffic=True)
+    total_prof = sum(v[1] for v in main["prof"].values())
+    dom = max(roofs, key=lambda kn: main["prof"][kn][1])
+    kernel_share = {kn: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_prof, 4) if total_prof else 0}
+                    for kn, v in main["prof"].items() if v[0]}
 
-    roof = roofline_of(dom)
-    roof_other = {k: roofline_of(k) for k in ("gates_kernel", "bp_kernel") if k != dom and k in prof}
-    kernel_share = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total_prof, 4) if total_prof else 0}
-                    for k, v in prof.items() if v[0]}
+    # ---- the FP64 path on the same layers; its states before a few sampled layers feed the
+    # per-layer error and the CPU baseline ----
+    err_layers = spread(timed, 6)
+    cpu_layers = spread(timed, 20)
+    state_dir = tempfile.mkdtemp(prefix="gtqa_bench_")
+    fp64 = None
+    whole = None
+    cpu = None
+    try:
+        run64 = None
+        if mixed and not a.no_fp64:
+            s = make(G.GTQA_FP64)
+            run64 = walk(G, s, Ks, dt, tol, mi, timed, stream, flush, snaps=SNAPSHOTS,
+                         save_before=sorted(set(err_layers) | set(cpu_layers)), profile=True, state_dir=state_dir)
+            G.gtqa_destroy(s)
+            r64 = rooflines(run64["prof"], run64["stats"], chi, inst.n, inst.m, False, peaks, traffic=True)
+            per = per_layer_error(G, make, err_layers, state_dir)
+            fp64 = {"value": world * S / (run64["t_ms"] / 1e3), "unit": "layers/s", "ms_per_step": run64["t_ms"] / S,
+                    "bp_sweeps_per_layer": run64["stats"]["bp_sweeps"] / S,
+                    "bp_layers_at_max_iter": run64["stats"]["bp_not_converged_calls"] / S,
+                    "speedup_mixed_over_fp64": run64["t_ms"] / main["t_ms"],
+                    "marginal_error_per_layer": per, "roofline": r64,
+                    "note": "the same timed layers on the FP64 path"}
+            if not a.no_whole:
+                whole = whole_anneal(G, make, inst, main, run64, stream, flush, props.multi_processor_count)
+        if rank == 0 and world == 1 and not a.no_cpu and run64 is not None:
+            with open(os.path.join(state_dir, "layers.json"), "w") as f:
+                json.dump({"layers": cpu_layers, "sweeps": [int(run64["per_layer"][k]["sweeps"]) for k in cpu_layers]}, f)
+            cpu = cpu_sample_subprocess(state_dir, a.budget)
+    finally:
+        shutil.rmtree(state_dir, ignore_errors=True)
 
-    # ---- end to end through the public API with host buffers ----
+    # ---- end to end through the public API with host buffers: the whole anneal ----
     e2e = None
     if not a.no_e2e:
         rho_h = torch.empty((inst.n, 2, 2), dtype=torch.complex128, pin_memory=True).numpy()
@@ -480,38 +643,195 @@ def run_gtqa(a):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s3 = make(prec)
-        for j in range(K):
-            G.gtqa_anneal(s3, j + 1, j + 1, Ks, dt, tol, mi)
+        for k in range(1, Ks + 1):
+            G.gtqa_anneal_graph(s3, k, k, Ks, dt, tol, mi)
             G.gtqa_marginals(s3, rho_h, sign_h)
         G.gtqa_destroy(s3)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
-        e2e = {"value": world * K / t_e2e, "unit": "layers/s", "h2d_bytes_per_step": h2d / K,
+        e2e = {"value": world * Ks / t_e2e, "unit": "layers/s", "h2d_bytes_per_step": h2d / Ks,
                "d2h_bytes_per_step": rho_h.nbytes + sign_h.nbytes,
-               "note": "create from host arrays, layers 1..K each followed by marginals into pinned host buffers, destroy"}
+               "note": "create from host arrays, every layer 1..K (CUDA-graph replay) followed by the marginals "
+                       "and read-out into pinned host buffers, destroy; wall clock"}
+
+    batch = None if a.no_batch else batched_legs(G, stream, flush, peaks, W, S, fp64)
+    scale = None if a.no_scale else scale_leg(G, stream, flush, peaks, fp64)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
+    nl = S
     out = {
-        "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world, "steps": S, "warmup": W,
+        "ms_per_step": t_ms / S, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64/f64" if mixed else "c128/f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "precision": a.precision, "layers_timed": [W + 1, W + K],
-                   "l2": "flushed between timed layers (256 MiB write, outside the timed events)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "bp_sweeps_per_layer": dlt["bp_sweeps"] / K,
-        "bp_layers_at_max_iter": dlt["bp_not_converged_calls"] / K,
-        "fp64_path": fp64,
-        "roofline": roof, "roofline_other_kernels": roof_other, "kernel_share": kernel_share, "alu_peaks_tflops": {"fp32": fp32_peak, "fp64": fp64_peak, "fp32_measured": fp32_meas,
-                             "fp64_measured": fp64_meas},
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(dlt["launches"]), "clocks": ck,
-        "final_marginals": {"mean_abs_z": float(np.mean(np.abs(rho_main[:, 0, 0].real - rho_main[:, 1, 1].real)))},
+        "config": config_dict(a, timed, world),
+        "bp_sweeps_per_layer": main["stats"]["bp_sweeps"] / nl,
+        "bp_layers_at_max_iter": main["stats"]["bp_not_converged_calls"] / nl,
+        "bp_exact_passes": main["stats"]["bp_exact_passes"],
+        "fp64_path": fp64, "whole_anneal": whole,
+        "roofline": roofs[dom], "roofline_other_kernels": {k: v for k, v in roofs.items() if k != dom},
+        "kernel_share": kernel_share,
+        "alu_peaks_tflops": {"fp32": peaks.fp32, "fp64": peaks.fp64, "fp32_measured": peaks.fp32_meas,
+                             "fp64_measured": peaks.fp64_meas},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(main["stats"]["launches"]), "clocks": ck,
+        "batched": batch, "scale": scale,
+        "final_marginals": {"mean_abs_z": float(np.mean(np.abs(main["rho"][:, 0, 0].real - main["rho"][:, 1, 1].real))),
+                            "E": energy(inst, main["sign"])},
     }
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def config_dict(a, timed, world) -> dict:
+    return {"workload": WORKLOAD_NAME, "precision": a.precision,
+            "layers_timed": {"count": len(timed), "first": timed[0], "last": timed[-1],
+                             "spread": len(timed) < WL["K"] - a.warmup},
+            "l2": "flushed before every timed layer (256 MiB write, outside the timed events)",
+            "launch": "one CUDA-graph replay per layer (gates, BP, regauge)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+def per_layer_error(G, make, layers: Sequence[int], state_dir: str) -> dict:
+    """Marginal error introduced by one mixed-precision layer: at the given layers k the FP64
+    state after layer k-1 is loaded into a mixed and an FP64 state, layer k runs in both, and
+    max |rho_mixed - rho_fp64| over vertices is recorded with the sign agreement."""
+    Ks, dt, tol, mi = WL["K"], WL["dt"], WL["tol"], WL["max_iter"]
+    out = {}
+    for k in layers:
+        z = np.load(os.path.join(state_dir, f"state_{k}.npz"))
+        res = []
+        for p in (G.GTQA_MIXED, G.GTQA_FP64):
+            s = make(p)
+            n_, m_, C_, _ = G.gtqa_sizes(s)
+            G.gtqa_set_state(s, z["G"], z["L"], np.zeros((2 * m_, C_, C_), dtype=np.complex128))
+            G.gtqa_anneal(s, k, k, Ks, dt, tol, mi)
+            res.append(G.gtqa_marginals(s))
+            G.gtqa_destroy(s)
+        (rm, sm_), (rf, sf) = res
+        out[str(k)] = compare_marginals(rm, sm_, rf, sf)
+    agrees = [v["sign_agreement"] for v in out.values() if v["sign_agreement"] is not None]
+    return {"max_abs": max(v["max_abs"] for v in out.values()),
+            "min_sign_agreement": min(agrees) if agrees else None, "samples": out,
+            "note": "one layer in each mode from the same FP64 state at layer k-1"}
+
+
+def whole_anneal(G, make, inst, main, run64, stream, flush, sms: int) -> dict:
+    """The read-out over the whole anneal: the mixed run and FP64 runs whose inputs differ at
+    rounding level (every J_ab moved by one ulp; every J_ab scaled by 1 + 2^-24 xi with seeded
+    signs xi, the size of complex64 rounding; another grid size of the persistent kernels,
+    which reorders nothing and must give identical results), each against the FP64 run at
+    layers 800, 1600, 2400 and 3200, with the objective E(x) of each final read-out."""
+    Ks, dt, tol, mi = WL["K"], WL["dt"], WL["tol"], WL["max_iter"]
+    rng = np.random.default_rng(2409122400 + 77)
+    runs = {"fp64_J_plus_1ulp": dict(J=np.nextafter(inst.J, np.inf)),
+            "fp64_J_rel_2^-24": dict(J=inst.J * (1.0 + 2.0 ** -24 * rng.choice([-1.0, 1.0], size=inst.m))),
+            "fp64_grid_7/8": dict(grid=max(1, sms * 7 // 8))}
+    snaps = {"mixed": main["snaps"], "fp64": run64["snaps"]}
+    finals = {"mixed": main["sign"], "fp64": run64["sign"]}
+    for name, kw in runs.items():
+        s = make(G.GTQA_FP64, J=kw.get("J"))
+        if "grid" in kw:
+            G.gtqa_set_grid(s, [kw["grid"]] * 3)
+        r = walk(G, s, Ks, dt, tol, mi, [], stream, flush, snaps=SNAPSHOTS)
+        G.gtqa_destroy(s)
+        snaps[name] = r["snaps"]
+        finals[name] = r["sign"]
+    out = {"reference": "fp64", "E_fp64": energy(inst, finals["fp64"]), "runs": {}}
+    for name in snaps:
+        if name == "fp64":
+            continue
+        d = {"E": energy(inst, finals[name])}
+        for k in SNAPSHOTS:
+            rho, sg = snaps[name][k]
+            rf, sf = snaps["fp64"][k]
+            d[str(k)] = compare_marginals(rho, sg, rf, sf)
+        out["runs"][name] = d
+    Es = [out["E_fp64"]] + [v["E"] for k, v in out["runs"].items() if k.startswith("fp64")]
+    out["fp64_E_range"] = [min(Es), max(Es)]
+    out["mixed_E_within_fp64_range"] = bool(min(Es) <= out["runs"]["mixed"]["E"] <= max(Es))
+    out["note"] = ("BP reaches max_iter without converging in most late-anneal layers; there the state follows an "
+                   "unstable map, so the read-out depends on rounding-level differences of the inputs")
+    return out
+
+
+def batched_legs(G, stream, flush, peaks: Peaks, W: int, S: int, fp64) -> dict:
+    """Mixed batched throughput, instance-layers/s, with the FP64 single-instance rate beside it:
+    (a) 16 seeded n = 1000 instances of the single-instance workload's shape in one batched
+    state; (b) the batched configuration (256 instances, n uniform over even values in
+    [50, 1000], K = 400, dt = 0.05).  Both anneal through CUDA-graph replays with S timed layers
+    spread over the anneal as in the main run."""
+    from instances import make_batch, make_instance
+    out = {}
+    legs = {"16x_n1000": ([make_instance(1000, s_) for s_ in range(16)], WL["K"], WL["dt"], WL["tol"], WL["max_iter"]),
+            "256_uneven": (make_batch(BATCH_WL["B"], seed=BATCH_WL["seed"]), BATCH_WL["K"], BATCH_WL["dt"],
+                           BATCH_WL["tol"], BATCH_WL["max_iter"])}
+    for name, (insts, K, dt, tol, mi) in legs.items():
+        s = G.gtqa_create_batch([x.n for x in insts], [x.edges for x in insts], [x.J for x in insts],
+                                [x.h for x in insts], 4, [x.colour for x in insts],
+                                G.gtqa_options_init(precision=G.GTQA_MIXED, cuda_stream=stream.cuda_stream))
+        timed = sample_layers(min(W, K - 1), min(S, K - min(W, K - 1)), K)
+        r = walk(G, s, K, dt, tol, mi, timed, stream, flush, profile=True)
+        G.gtqa_destroy(s)
+        N = sum(x.n for x in insts)
+        M = sum(x.m for x in insts)
+        roofs = rooflines(r["prof"], r["stats"], 4, N, M, True, peaks, traffic=False)
+        dom = max(roofs, key=lambda kn: r["prof"][kn][1])
+        L = len(timed)
+        out[name] = {"instances": len(insts), "vertices": N, "edges": M, "K": K, "dt": dt,
+                     "layers_timed": {"count": L, "first": timed[0], "last": timed[-1]},
+                     "instance_layers_per_s": len(insts) * L / (r["t_ms"] / 1e3),
+                     "batch_layers_per_s": L / (r["t_ms"] / 1e3), "ms_per_layer": r["t_ms"] / L,
+                     "bp_sweeps_per_layer": r["stats"]["bp_sweeps"] / L,
+                     "fp64_single_instance_layers_per_s": (fp64 or {}).get("value"),
+                     "roofline": roofs[dom], "roofline_other_kernels": {k: v for k, v in roofs.items() if k != dom}}
+    return out
+
+
+def scale_leg(G, stream, flush, peaks: Peaks, fp64) -> dict:
+    """The scale configuration (n = 100000, m = 150000, chi = 8, mixed, K = 500, dt = 0.05),
+    HBM-resident: layers 1..5 untimed, layers 6..15 timed (the whole anneal takes minutes)."""
+    from instances import make_instance
+    w = SCALE_WL
+    inst = make_instance(w["n"], w["seed"])
+    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, w["chi"], inst.colour,
+                      G.gtqa_options_init(precision=G.GTQA_MIXED, cuda_stream=stream.cuda_stream))
+    timed = list(range(w["warm"] + 1, w["warm"] + w["steps"] + 1))
+    G.gtqa_anneal_graph(s, 1, w["warm"], w["K"], w["dt"], w["tol"], w["max_iter"])
+    r = walk_range(G, s, w, timed, stream, flush)
+    G.gtqa_destroy(s)
+    roofs = rooflines(r["prof"], r["stats"], w["chi"], inst.n, inst.m, True, peaks, traffic=False)
+    dom = max(roofs, key=lambda kn: r["prof"][kn][1])
+    L = len(timed)
+    return {"n": inst.n, "m": inst.m, "chi": w["chi"], "K": w["K"], "dt": w["dt"],
+            "layers_timed": {"count": L, "first": timed[0], "last": timed[-1]},
+            "layers_per_s": L / (r["t_ms"] / 1e3), "ms_per_layer": r["t_ms"] / L,
+            "bp_sweeps_per_layer": r["stats"]["bp_sweeps"] / L,
+            "roofline": roofs[dom], "roofline_other_kernels": {k: v for k, v in roofs.items() if k != dom}}
+
+
+def walk_range(G, s, w, timed, stream, flush) -> dict:
+    """Times consecutive layers `timed` (already annealed up to timed[0] - 1) with per-layer
+    CUDA events and the library's per-phase events."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in timed]
+    G.gtqa_profile(s, True)
+    st0 = G.gtqa_stats(s)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for j, k in enumerate(timed):
+            flush.fill_(k & 0xFF)
+            ev[j][0].record(stream)
+            G.gtqa_anneal_graph(s, k, k, w["K"], w["dt"], w["tol"], w["max_iter"])
+            ev[j][1].record(stream)
+    torch.cuda.synchronize()
+    prof = G.gtqa_profile_read(s)
+    st1 = G.gtqa_stats(s)
+    G.gtqa_profile(s, False)
+    return {"t_ms": float(sum(e0.elapsed_time(e1) for e0, e1 in ev)), "prof": prof,
+            "stats": {k: st1[k] - st0[k] for k in STAT_KEYS}}
 
 
 def run_reference(a):
@@ -519,17 +839,16 @@ def run_reference(a):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
-    W, K = a.warmup, a.steps
-    r = oracle_sampled_rate(W, K, budget_s=120.0)
+    W = a.warmup
+    timed = sample_layers(W, a.steps, WL["K"])
+    r = oracle_own_states_rate(W, timed, budget=120.0)
     out = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": "layers/s", "n_gpus": world,
-           "steps": K, "warmup": W, "ms_per_step": 1e3 / r["value"], "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "c128/f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD_NAME, "precision": "fp64 (CPU oracle)", "layers_timed": [W + 1, W + K]},
+           "steps": len(timed), "warmup": W, "ms_per_step": 1e3 / r["value"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128/f64", "data": "synthetic",
+           "config": config_dict(a, timed, world),
            "cpu_baseline": {"value": r["value"], "unit": "layers/s", "cores": 1, "kind": "oracle", "sample": r["sample"]},
            "e2e": {"value": r["value"], "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
-
-
 def ncu_case(a):
     """A short run for ncu captures: the launches of interest come after 3 K0 warm-up launches
     (gates, BP, regauge per layer); the gates launch is the (K0+1)-th gates_kernel, the two BP
@@ -583,8 +902,7 @@ def main():
         ncu_scale(a)
         return
     if a.oracle_sample:
-        r = oracle_sampled_rate(a.warmup, a.steps, a.budget)
-        print(json.dumps(r))
+        print(json.dumps(oracle_sample_main(a.oracle_sample, a.budget)))
         return
     if a.impl == "reference":
         run_reference(a)

@@ -222,14 +222,20 @@ int gtqa_anneal_policy(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K,
 int gtqa_regauge_counts(gtqa_state* s, int64_t* regauged, int64_t* skipped);
 
 /*
- * gtqa_anneal replayed from a CUDA graph: the three launches of every layer k_begin..k_end are
- * captured once (on a private stream, with profiling events off) into a graph that the state
- * keeps, and the graph is launched on the state's stream.  A later call with the same
- * arguments relaunches the kept graph without capturing again; different arguments replace
- * it.  The results are those of gtqa_anneal with the same arguments, bit for bit.  Graphs
- * save the host-side launch cost; the device work is unchanged.  Asynchronous.  Returns
- * GTQA_ERR_UNSUPPORTED if the launches could not be captured (nothing is launched and the
- * state stays usable) or for a degree-4 state, and GTQA_ERR_INVALID_ARG as gtqa_anneal.
+ * gtqa_anneal replayed from a CUDA graph: the three launches of one layer (gates, BP,
+ * regauge) are captured once (on a private stream) into a graph that the state keeps.  The
+ * captured layer reads its index k from a device word, and its regauge launch stores k + 1,
+ * so layers k_begin..k_end are one small kernel that sets k_begin followed by one graph launch
+ * per layer on the state's stream.  The graph is kept for later calls with the same K, dt,
+ * tol and max_iter (any layer range) and the same profiling setting; other values replace it.
+ * The results are those of gtqa_anneal with the same arguments, bit for bit; the graph saves
+ * the host-side launch cost and the device work is unchanged.  The graph carries events
+ * between its three launches; with the profiler on (gtqa_profile) each replay is timed into
+ * the gates, BP and regauge classes, its events being read before the next replay (a
+ * multi-layer call then waits for each layer before launching the next) or by
+ * gtqa_profile_read.  Otherwise asynchronous.  Returns GTQA_ERR_UNSUPPORTED if the launches could not be captured
+ * (nothing is launched and the state stays usable) or for a degree-4 state, and
+ * GTQA_ERR_INVALID_ARG as gtqa_anneal.
  */
 int gtqa_anneal_graph(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double dt, double tol,
                       int32_t max_iter);

@@ -107,6 +107,8 @@ struct Ctx {
     int max_iter;
     unsigned phases;
     int k0, k1, Ksched;       // layers k0..k1 with tau = k/Ksched; Ksched = 0: one layer at (tZ1, tX1)
+    int* kdev;                // non-null: one layer, k read from *kdev; the regauge phase stores k + 1
+                              // (CUDA-graph replays of one captured layer advance through the anneal)
     double dt, tZ1, tX1;
     double tXpre1;            // Ksched = 0: leading mixing angle of the layer (0: none)
     const double* rgate;      // regauge policy: the residual sum of this layer (null: always regauge)
@@ -1166,7 +1168,8 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
     GridBarrier gb = grid_barrier_init(c.bar ? c.bar : &c.ctl->bar_count, &c.ctl->err, (unsigned)c.bar_expect);
     const int nteams_total_g = c.nblocks * (S::TPB / S::TG);
     int cur = *(volatile int*)&c.ctl->cur;
-    for (int k = c.k0; k <= c.k1; ++k) {
+    const int kb = c.kdev ? *(volatile int*)c.kdev : c.k0, ke = c.kdev ? kb : c.k1;
+    for (int k = kb; k <= ke; ++k) {
         double tZ, tX;
         if (c.Ksched > 0) {
             const double tau = (double)k / (double)c.Ksched;
@@ -1419,6 +1422,9 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 if (!grid_sync(gb, c.spin_limit)) return;
             }
         }
+        // every block read *kdev at entry, before the barriers above
+        if constexpr ((PH & PH_REGAUGE) != 0u)
+            if (c.kdev && blockIdx.x == 0 && threadIdx.x == 0) *c.kdev = k + 1;
     }
 }
 

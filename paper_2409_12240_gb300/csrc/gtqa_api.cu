@@ -75,11 +75,15 @@ struct gtqa_state {
     std::vector<int> h_deg, h_cedges, h_coff;
     std::vector<double> h_J, h_h;
     int cur4 = 0;               // message buffer holding the latest messages (degree 4)
-    // gtqa_anneal_graph: the captured launches of one layer range, and what they were captured for
+    // gtqa_anneal_graph: one captured layer (gates, BP, regauge) whose layer index is read from
+    // *kdev, and what it was captured for; with profiling on, events between the launches
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    int gk0 = 0, gk1 = 0, gK = 0, gmi = 0;
+    int* kdev = nullptr;
+    int gK = 0, gmi = 0;
     double gdt = 0.0, gtol = 0.0;
+    bool gpending = false;      // a profiled replay whose events are not read yet
+    cudaEvent_t gev[4] = {nullptr, nullptr, nullptr, nullptr};
     // host counters
     long long layers = 0, gates = 0, launches = 0;
     int sticky = GTQA_OK;
@@ -192,7 +196,27 @@ struct ProfScope {
     }
 };
 
+// Adds the phase times of the last profiled graph replay (gtqa_anneal_graph) to the profiler's
+// classes; waits for that replay.  Returns false on a CUDA error.
+bool graph_collect(gtqa_state* s) {
+    if (!s->gpending) return true;
+    s->gpending = false;
+    float ms[3];
+    if (!cuda_ok(s, cudaEventSynchronize(s->gev[3]))) return false;
+    for (int q = 0; q < 3; ++q)
+        if (!cuda_ok(s, cudaEventElapsedTime(&ms[q], s->gev[q], s->gev[q + 1]))) return false;
+    const int kinds[3] = {GTQA_K_TROTTER, GTQA_K_BP, GTQA_K_REGAUGE};
+    const long long units[3] = {s->m, s->n, s->m};
+    for (int q = 0; q < 3; ++q) {
+        s->prof_ms[kinds[q]] += ms[q];
+        s->prof_launches[kinds[q]] += 1;
+        s->prof_units[kinds[q]] += units[q];
+    }
+    return true;
+}
+
 void prof_collect(gtqa_state* s) {
+    graph_collect(s);
     for (auto& p : s->pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
@@ -435,7 +459,9 @@ void free_state(gtqa_state* s) {
     if (!s) return;
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
     if (s->graph) cudaGraphDestroy(s->graph);
-    void* ptrs[] = {s->Gamma, s->lam, s->T, s->msg[0], s->msg[1], s->D0, s->t0, s->X, s->edge_info,
+    for (cudaEvent_t e : s->gev)
+        if (e) cudaEventDestroy(e);
+    void* ptrs[] = {s->kdev, s->Gamma, s->lam, s->T, s->msg[0], s->msg[1], s->D0, s->t0, s->X, s->edge_info,
                     s->vert_edges, s->vert_inst, s->J, s->h, s->colour_edges, s->colour_off, s->last_colour, s->first_colour,
                     s->iso, s->inst_vbeg, s->inst_m, s->acc, s->inst_done, s->inst_iters, s->inst_dist,
                     s->stats, s->ctl, s->rho, s->sign, s->flags, s->rbuf, s->cutbuf, s->xs, s->ps,
@@ -449,6 +475,9 @@ void free_state(gtqa_state* s) {
     for (cudaEvent_t e : s->pool) cudaEventDestroy(e);
     delete s;
 }
+
+// stores the first layer index of a run of graph replays (gtqa_anneal_graph)
+__global__ void set_layer_kernel(int* kdev, int k) { *kdev = k; }
 
 Ctx make_ctx(const gtqa_state* s) {
     Ctx c;
@@ -715,7 +744,7 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         (rc = dalloc(s, &s->iso, iso.size())) || (rc = dalloc(s, &s->inst_vbeg, B + 1)) ||
         (rc = dalloc(s, &s->inst_m, B)) || (rc = dalloc(s, &s->acc, 6 * (size_t)B)) ||
         (rc = dalloc(s, &s->inst_done, B)) || (rc = dalloc(s, &s->inst_iters, B)) ||
-        (rc = dalloc(s, &s->inst_dist, B)) || (rc = dalloc(s, &s->stats, kStats)) || (rc = dalloc(s, &s->ctl, 1)) ||
+        (rc = dalloc(s, &s->inst_dist, B)) || (rc = dalloc(s, &s->stats, kStats)) || (rc = dalloc(s, &s->ctl, 1)) || (rc = dalloc(s, &s->kdev, 1)) ||
         (rc = dalloc(s, &s->rho, (size_t)s->n * 4)) || (rc = dalloc(s, &s->sign, s->n)) ||
         (rc = dalloc(s, &s->flags, 4)) || (rc = dalloc(s, &s->rbuf, 1)) ||
         (rc = dalloc(s, &s->cutbuf, std::max(s->m, 1))) || (rc = dalloc(s, &s->xs, s->n)) ||
@@ -1598,30 +1627,46 @@ int gtqa_anneal_graph(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, 
     if (K < 1 || k_begin < 1 || k_end < k_begin || k_end > K || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1)
         return GTQA_ERR_INVALID_ARG;
     if (s->plain) return GTQA_ERR_UNSUPPORTED;
-    const bool same = s->gexec && s->gk0 == k_begin && s->gk1 == k_end && s->gK == K && s->gdt == dt &&
-                      s->gtol == tol && s->gmi == max_iter;
+    const bool same = s->gexec && s->gK == K && s->gdt == dt && s->gtol == tol && s->gmi == max_iter;
     if (!same) {
+        if (!graph_collect(s)) return GTQA_ERR_CUDA;
         if (s->gexec) cudaGraphExecDestroy(s->gexec);
         if (s->graph) cudaGraphDestroy(s->graph);
         s->gexec = nullptr;
         s->graph = nullptr;
-        // capture on a private stream (the state's own stream may be the legacy default stream),
-        // with the per-launch profiling events off
+        const bool prof = s->prof_on;
+        for (cudaEvent_t& e : s->gev)
+            if (!e && !cuda_ok(s, cudaEventCreate(&e))) return GTQA_ERR_CUDA;
+        // capture on a private stream (the state's own stream may be the legacy default stream)
         cudaStream_t cs = nullptr;
         if (!cuda_ok(s, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) return GTQA_ERR_CUDA;
         const cudaStream_t own = s->stream;
-        const bool prof = s->prof_on;
-        const long long layers = s->layers, gates = s->gates, launches = s->launches;
+        const long long launches = s->launches;
         s->stream = cs;
-        s->prof_on = false;
+        s->prof_on = false;   // the library's per-launch events are replaced by the graph's own
+        Ctx c = make_ctx(s);
+        c.phases = PH_GATES | PH_BP | PH_WARM | PH_REGAUGE;
+        c.Ksched = K;
+        c.dt = dt;
+        c.tol = tol;
+        c.max_iter = max_iter;
+        c.kdev = s->kdev;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        int lrc = e == cudaSuccess ? anneal_launches(s, k_begin, k_end, K, dt, tol, max_iter) : GTQA_ERR_CUDA;
+        int lrc = e == cudaSuccess ? GTQA_OK : GTQA_ERR_CUDA;
+        const int pks[3] = {PK_GATES, PK_BP, PK_REGAUGE};
+        const long long units[3] = {s->m, s->n, s->m};
+        // external event nodes around the three launches: every replay re-records them, and they
+        // are read when the profiler is on
+        for (int q = 0; q < 3 && lrc == GTQA_OK; ++q) {
+            if (cudaEventRecordWithFlags(s->gev[q], cs, cudaEventRecordExternal) != cudaSuccess) lrc = GTQA_ERR_CUDA;
+            if (lrc == GTQA_OK) lrc = run(s, c, pks[q], pks[q], units[q]);
+        }
+        if (lrc == GTQA_OK && cudaEventRecordWithFlags(s->gev[3], cs, cudaEventRecordExternal) != cudaSuccess)
+            lrc = GTQA_ERR_CUDA;
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cs, &g) : e;
         s->stream = own;
         s->prof_on = prof;
-        s->layers = layers;
-        s->gates = gates;
         s->launches = launches;
         cudaStreamDestroy(cs);
         if (lrc == GTQA_OK && e2 == cudaSuccess && g) e = cudaGraphInstantiate(&s->gexec, g, 0);
@@ -1635,18 +1680,24 @@ int gtqa_anneal_graph(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, 
             return GTQA_ERR_UNSUPPORTED;
         }
         s->graph = g;
-        s->gk0 = k_begin;
-        s->gk1 = k_end;
         s->gK = K;
         s->gdt = dt;
         s->gtol = tol;
         s->gmi = max_iter;
     }
-    if (!cuda_ok(s, cudaGraphLaunch(s->gexec, s->stream))) return GTQA_ERR_CUDA;
-    const long long L = (long long)k_end - k_begin + 1;
-    s->layers += L;
-    s->gates += L * s->m;
-    s->launches += 3 * L;
+    // the captured layer reads its index from *kdev and its regauge stores the next one
+    set_layer_kernel<<<1, 1, 0, s->stream>>>(s->kdev, k_begin);
+    if (!cuda_ok(s, cudaGetLastError())) return GTQA_ERR_CUDA;
+    s->launches += 1;
+    for (int k = k_begin; k <= k_end; ++k) {
+        // each replay re-records the events: a profiled replay's are read before the next one
+        if (!graph_collect(s)) return GTQA_ERR_CUDA;
+        if (!cuda_ok(s, cudaGraphLaunch(s->gexec, s->stream))) return GTQA_ERR_CUDA;
+        s->layers += 1;
+        s->gates += s->m;
+        s->launches += 3;
+        s->gpending = s->prof_on;
+    }
     return GTQA_OK;
 }
 

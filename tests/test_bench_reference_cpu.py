@@ -22,3 +22,17 @@ def test_reference_arm_prints_the_contract_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_timed_layers_spread_over_the_anneal():
+    """A short run samples the whole anneal (first and last layer included); the default run
+    times every layer after the warm-up."""
+    sys.path.insert(0, ROOT)
+    import bench
+    L = bench.sample_layers(5, 20, 3200)
+    assert len(L) == 20 and L[0] == 6 and L[-1] == 3200 and L == sorted(set(L))
+    assert max(b - a for a, b in zip(L, L[1:])) - min(b - a for a, b in zip(L, L[1:])) <= 1
+    assert bench.sample_layers(3, 3197, 3200) == list(range(4, 3201))
+    assert bench.sample_layers(3, 1, 3200) == [3200]
+    assert bench.spread(list(range(100)), 5) == [0, 25, 50, 74, 99]
+    assert bench.spread([1, 2, 3], 5) == [1, 2, 3]

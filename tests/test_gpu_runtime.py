@@ -127,6 +127,40 @@ def test_anneal_from_a_cuda_graph_matches_direct_launches(precision):
         assert ta["layers"] == tb["layers"] == 20 and ta["bp_calls"] == tb["bp_calls"] == 20
 
 
+def test_profiled_graph_replays_time_each_phase_and_keep_results():
+    """With the profiler on, every graph replay is timed into the gates, BP and regauge classes
+    (one launch of each per layer) and the state stays that of direct launches, bit for bit."""
+    import numpy as np
+    from instances import make_instance
+    G = U.lib()
+    inst = make_instance(200, 6)
+    K, dt, tol, mi = 200, 0.2, 1e-8, 100
+    out = []
+    for graph in (False, True):
+        s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 4, inst.colour, G.gtqa_options_init(precision=1))
+        try:
+            G.gtqa_anneal(s, 1, 5, K, dt, tol, mi)
+            G.gtqa_profile(s, True)
+            if graph:
+                G.gtqa_anneal_graph(s, 6, 17, K, dt, tol, mi)
+            else:
+                G.gtqa_anneal(s, 6, 17, K, dt, tol, mi)
+            prof = G.gtqa_profile_read(s)
+            G.gtqa_profile(s, False)
+            G.gtqa_anneal_graph(s, 18, 20, K, dt, tol, mi) if graph else G.gtqa_anneal(s, 18, 20, K, dt, tol, mi)
+            out.append((G.gtqa_get_state(s), prof))
+        finally:
+            G.gtqa_destroy(s)
+    (sa, pa), (sb, pb) = out
+    for a, b in zip(sa, sb):
+        assert np.array_equal(a, b)
+    for name in ("gates_kernel", "bp_kernel", "regauge_kernel"):
+        assert pa[name][0] == pb[name][0] == 12, (name, pa[name], pb[name])
+        assert pb[name][1] > 0.0 and pa[name][2] == pb[name][2]
+        # the same device work, timed by events around the launches or between graph nodes
+        assert 0.5 < pb[name][1] / pa[name][1] < 2.0, (name, pa[name], pb[name])
+
+
 def test_autotune_restores_the_state_and_keeps_results():
     """gtqa_autotune leaves the state and statistics as they were, keeps grid sizes within the SM
     count, and the layers it then runs give the results of the default grid (FP64, bitwise on
