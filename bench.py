@@ -72,6 +72,9 @@ def parse(argv=None):
                    help="profiling case: anneal layers 1..K0, then one gates launch, one BP launch of 1 sweep "
                         "and, from the same state, one of 21 sweeps (warm start, no regauge); no timing")
     p.add_argument("--budget", type=float, default=20.0, help=argparse.SUPPRESS)
+    p.add_argument("--bp-study", action="store_true",
+                   help="no timing: BP sweeps per layer over the anneal, sweep-by-sweep traces at three late "
+                        "layers, and the same anneal with h ~ N(0, 1)")
     a = p.parse_args(argv)
     a.warmup = max(0, a.warmup)
     if a.steps is None:
@@ -338,30 +341,42 @@ def bp_sweep_flops_executed(chi: int, vertices: int, mixed: bool) -> float:
     return float(vertices * 3 * (64 if mixed else 48) * chi ** 4)
 
 
-def edge_gate_flops(chi: int) -> Tuple[float, float]:
-    """Algorithmic flops of one edge gate with truncation (a2-a3), in complex MACs of 8 flops:
-    two Householder QRs of the (2 chi^2) x (2 chi) side matrices (2 m n^2 - 2/3 n^3 each), the
-    core M (2 (2 chi)^3), a one-sided Jacobi SVD of order n = 2 chi with V (11 n per pair, 7.5
-    sweeps of n (n - 1) / 2 pairs), the two Q applications (2 chi (m n - n^2 / 2) each), plus
-    about 50 chi^3 flops of gate and lambda scaling.  Returns (total, FP64 part = 95 %)."""
+def _cmac_jacobi(n: int, sweeps: float = 7.5) -> float:
+    """Complex MACs of a one-sided Jacobi SVD of order n with vectors: 11 n per pair, n (n - 1) / 2
+    pairs per sweep, 7.5 sweeps (the per-unit figure of the method's cost table)."""
+    return 11 * n * (n * (n - 1) / 2) * sweeps
+
+
+def edge_gate_flops(chi: int, mixed: bool) -> Tuple[float, float]:
+    """Algorithmic (FP64, FP32) flops of one edge gate with truncation (a2-a3) in the variant that
+    runs, from complex MACs of 8 flops: two Householder QRs of the (2 chi^2) x (2 chi) side
+    matrices (2 m n^2 - 2/3 n^3 each) and the core M (2 (2 chi)^3), FP64; the one-sided Jacobi SVD
+    of order n = 2 chi (FP64, or FP32 sweeps in the mixed mode, which then adds the FP64
+    Newton-Schulz step and W = M V, 3 n^3, and two FP64 polish sweeps); the two Q applications (2 chi (m n - n^2 / 2) each; FP32 in the mixed mode);
+    and about 50 chi^3 flops of gate and lambda scaling (FP64)."""
     m, n = 2 * chi * chi, 2 * chi
-    cmac = 2 * (2 * m * n * n - 2 * n ** 3 / 3) + 2 * n ** 3 + 11 * n * (n * (n - 1) / 2) * 7.5 \
-        + 2 * 2 * chi * (m * n - n * n / 2)
-    tot = 8 * cmac + 50 * chi ** 3
-    return float(tot), float(0.95 * tot)
+    qr_core = 2 * (2 * m * n * n - 2 * n ** 3 / 3) + 2 * n ** 3
+    jac = _cmac_jacobi(n)
+    apply_q = 2 * 2 * chi * (m * n - n * n / 2)
+    if not mixed:
+        return float(8 * (qr_core + jac + apply_q) + 50 * chi ** 3), 0.0
+    return float(8 * (qr_core + 3 * n ** 3 + _cmac_jacobi(n, 2.0)) + 50 * chi ** 3), float(8 * (jac + apply_q))
 
 
-def regauge_edge_flops(chi: int) -> Tuple[float, float]:
-    """Algorithmic flops of the Vidal-gauge step of one edge (a7), in complex MACs of 8 flops:
-    two chi x chi Hermitian eigen-decompositions and one chi x chi SVD by one-sided Jacobi with
-    vectors (11 n per pair, 7.5 sweeps of n (n - 1) / 2 pairs each, n = chi), the square roots and
-    inverse square roots (2 x 2 chi^3), M (chi^3), the two transforms X (2 chi^3), all FP64; and
-    the two bond transforms applied to the vertex tensors (2 x 2 chi^4, FP32 in the mixed mode).
-    Returns (total, FP64 part)."""
+def regauge_edge_flops(chi: int, mixed: bool) -> Tuple[float, float]:
+    """Algorithmic (FP64, FP32) flops of the Vidal-gauge step of one edge (a7), from complex MACs:
+    two chi x chi Hermitian eigen-decompositions and one chi x chi SVD by one-sided Jacobi (FP64,
+    or FP32 sweeps plus the FP64 Newton-Schulz step and two FP64 polish sweeps each, in the mixed
+    mode); the square roots
+    and inverse square roots (4 chi^3), M (chi^3) and the two transforms X (2 chi^3), FP64; the
+    two bond transforms applied to the vertex tensors (2 x 2 chi^4; FP32 in the mixed mode)."""
     n = chi
-    jac = 11 * n * (n * (n - 1) / 2) * 7.5
-    f64 = 8 * (3 * jac + 4 * chi ** 3 + chi ** 3 + 2 * chi ** 3)
-    return float(f64 + 8 * 4 * chi ** 4), float(f64)
+    jac = 3 * _cmac_jacobi(n)
+    fixed = 4 * n ** 3 + n ** 3 + 2 * n ** 3
+    apply_g = 2 * 2 * chi ** 4
+    if not mixed:
+        return float(8 * (jac + fixed + apply_g)), 0.0
+    return float(8 * (fixed + 3 * (3 * n ** 3 + _cmac_jacobi(n, 2.0)))), float(8 * (jac + apply_g))
 
 
 def regauge_flops_executed(chi: int, edges: int, svd_sweeps: int, mixed: bool) -> float:
@@ -420,7 +435,12 @@ class Peaks:
 
 def rooflines(prof: dict, dlt: dict, chi: int, n: int, m: int, mixed: bool, peaks: Peaks, traffic: bool) -> dict:
     """Roofline objects of the three phase kernels from the library's per-launch CUDA events
-    (prof: {kernel: (launches, total ms, units)}) and the statistics over the same launches."""
+    (prof: {kernel: (launches, total ms, units)}) and the statistics over the same launches.
+
+    Each kernel's algorithmic work is split by the pipe it runs on in this precision mode (the
+    variant that runs): its roofline time is max(F64 / P64, F32 / P32), and `frac` is that time
+    over the measured time, reported as achieved / peak of the binding pipe.  The path is
+    CUDA-core arithmetic on an L2-resident working set (bound "alu")."""
     out = {}
     C = storage_chi(chi)
     for kname, (nl, ms, units) in prof.items():
@@ -428,44 +448,51 @@ def rooflines(prof: dict, dlt: dict, chi: int, n: int, m: int, mixed: bool, peak
             continue
         sec = ms * 1e-3
         if kname == "gates_kernel":
-            _, f64e = edge_gate_flops(chi)
-            alg = f64e * units
-            exe = gate_flops(chi, units, int(dlt["svd_pairs"]), int(dlt["svd_rotations"]), mixed)[0]
-            peak, fp64 = peaks.fp64, True
-            unit_count = "edges per launch x the FP64 part (95 %) of the edge gate's algorithmic flops"
-            note = ("the mixed path runs the SVD's preconditioning sweeps in FP32, so it executes fewer FP64 flops "
-                    "than it is credited with" if mixed else "FP64 throughout")
+            f64u, f32u = edge_gate_flops(chi, mixed)
+            f64, f32 = f64u * units, f32u * units
+            exe64 = gate_flops(chi, units, int(dlt["svd_pairs"]), int(dlt["svd_rotations"]), mixed)[0]
+            unit_count = "edges per launch x the edge gate's algorithmic flops, split by pipe"
             tr = kernel_traffic(kname, mixed, chi) if traffic else None
         elif kname == "bp_kernel":
             sweeps = int(dlt["bp_sweeps"])
-            alg = bp_sweep_flops(chi, n, mixed) * sweeps
-            exe = bp_sweep_flops_executed(C, n, mixed) * sweeps
-            fp64 = not mixed
-            peak = peaks.fp32 if mixed else peaks.fp64
-            unit_count = "sweeps x 3n directed messages x 48 chi^4 flops"
-            note = ("flops of the BP sweeps only (the warm-start phase of each launch is not counted); the working "
-                    "set is L2-resident and each sweep ends in a grid barrier")
+            fl = bp_sweep_flops(chi, n, mixed) * sweeps
+            norm64 = 20.0 * 3 * n * sweeps   # the FP64 trace reciprocals
+            f64, f32 = (norm64, fl) if mixed else (fl + norm64, 0.0)
+            exe64 = norm64 if mixed else bp_sweep_flops_executed(C, n, False) * sweeps
+            unit_count = "sweeps x 3n directed messages x 48 chi^4 flops (+ the FP64 normalisation)"
             tr = kernel_traffic(kname, mixed, chi, sweeps / nl) if traffic else None
         else:
-            _, f64e = regauge_edge_flops(chi)
-            alg = f64e * units
-            exe = regauge_flops_executed(chi, units, int(dlt["regauge_svd_sweeps"]), mixed)
-            peak, fp64 = peaks.fp64, True
-            unit_count = "edges per launch x the FP64 part of the Vidal-gauge step's algorithmic flops"
-            note = ("eigen-decompositions, SVD and roots in FP64 (the mixed mode's FP32 preconditioning sweeps are "
-                    "not counted as executed FP64)")
+            f64u, f32u = regauge_edge_flops(chi, mixed)
+            f64, f32 = f64u * units, f32u * units
+            exe64 = regauge_flops_executed(chi, units, int(dlt["regauge_svd_sweeps"]), mixed)
+            unit_count = "edges per launch x the Vidal-gauge step's algorithmic flops, split by pipe"
             tr = kernel_traffic(kname, mixed, chi) if traffic else None
-        ach = alg / sec / 1e12
-        ex = exe / sec / 1e12
-        o = {"kernel": kname, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-             "traffic": tr, "peak_source": peaks.note(fp64), "algorithmic_flops_per_launch": alg / nl,
-             "avg_launch_us": ms / nl * 1e3, "launches": nl, "unit_count": unit_count,
-             "executed_flops_per_launch": exe / nl, "executed_tflops": ex, "executed_frac": ex / peak, "note": note}
+        t64, t32 = f64 / (peaks.fp64 * 1e12), f32 / (peaks.fp32 * 1e12)
+        pipe64 = t64 >= t32
+        fpipe, peak = (f64, peaks.fp64) if pipe64 else (f32, peaks.fp32)
+        ach = fpipe / sec / 1e12
+        o = {"kernel": kname, "bound": "alu", "pipe": "fp64" if pipe64 else "fp32", "achieved": ach, "peak": peak,
+             "unit": "TFLOP/s", "frac": ach / peak, "traffic": tr, "peak_source": peaks.note(pipe64),
+             "algorithmic_fp64_flops_per_launch": f64 / nl, "algorithmic_fp32_flops_per_launch": f32 / nl,
+             "roofline_us_per_launch": max(t64, t32) / nl * 1e6, "avg_launch_us": ms / nl * 1e3, "launches": nl,
+             "unit_count": unit_count, "executed_fp64_flops_per_launch": exe64 / nl,
+             "executed_fp64_frac": exe64 / sec / 1e12 / peaks.fp64}
         if kname == "bp_kernel":
             o["sweeps_per_launch"] = int(dlt["bp_sweeps"]) / nl
             o["us_per_sweep"] = ms * 1e3 / max(int(dlt["bp_sweeps"]), 1)
+            o["note"] = ("the working set is L2-resident; each sweep waits for the neighbouring blocks' previous "
+                         "sweep (or a grid barrier), so the sweep's latency, not a pipe, bounds it")
         out[kname] = o
     return out
+
+
+def layer_roofline(roofs: dict) -> dict:
+    """The layer's roofline time as the sum of its kernels' roofline times (they run one after
+    another), over the measured time of the same launches."""
+    t_roof = sum(r["roofline_us_per_launch"] * r["launches"] for r in roofs.values())
+    t_meas = sum(r["avg_launch_us"] * r["launches"] for r in roofs.values())
+    return {"frac": t_roof / t_meas if t_meas else None, "roofline_us": t_roof, "measured_us": t_meas,
+            "note": "sum over the gates, BP and regauge launches of max(F64/P64, F32/P32) per launch"}
 
 
 # ---------------------------------------------------------------------------
@@ -623,7 +650,7 @@ def run_gtqa(a):
                     "bp_sweeps_per_layer": run64["stats"]["bp_sweeps"] / S,
                     "bp_layers_at_max_iter": run64["stats"]["bp_not_converged_calls"] / S,
                     "speedup_mixed_over_fp64": run64["t_ms"] / main["t_ms"],
-                    "marginal_error_per_layer": per, "roofline": r64,
+                    "marginal_error_per_layer": per, "roofline": r64, "layer_roofline": layer_roofline(r64),
                     "note": "the same timed layers on the FP64 path"}
             if not a.no_whole:
                 whole = whole_anneal(G, make, inst, main, run64, stream, flush, props.multi_processor_count)
@@ -672,7 +699,7 @@ def run_gtqa(a):
         "bp_exact_passes": main["stats"]["bp_exact_passes"],
         "fp64_path": fp64, "whole_anneal": whole,
         "roofline": roofs[dom], "roofline_other_kernels": {k: v for k, v in roofs.items() if k != dom},
-        "kernel_share": kernel_share,
+        "layer_roofline": layer_roofline(roofs), "kernel_share": kernel_share,
         "alu_peaks_tflops": {"fp32": peaks.fp32, "fp64": peaks.fp64, "fp32_measured": peaks.fp32_meas,
                              "fp64_measured": peaks.fp64_meas},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(main["stats"]["launches"]), "clocks": ck,
@@ -786,7 +813,8 @@ def batched_legs(G, stream, flush, peaks: Peaks, W: int, S: int, fp64) -> dict:
                      "batch_layers_per_s": L / (r["t_ms"] / 1e3), "ms_per_layer": r["t_ms"] / L,
                      "bp_sweeps_per_layer": r["stats"]["bp_sweeps"] / L,
                      "fp64_single_instance_layers_per_s": (fp64 or {}).get("value"),
-                     "roofline": roofs[dom], "roofline_other_kernels": {k: v for k, v in roofs.items() if k != dom}}
+                     "roofline": roofs[dom], "roofline_other_kernels": {k: v for k, v in roofs.items() if k != dom},
+                     "layer_roofline": layer_roofline(roofs)}
     return out
 
 
@@ -809,7 +837,8 @@ def scale_leg(G, stream, flush, peaks: Peaks, fp64) -> dict:
             "layers_timed": {"count": L, "first": timed[0], "last": timed[-1]},
             "layers_per_s": L / (r["t_ms"] / 1e3), "ms_per_layer": r["t_ms"] / L,
             "bp_sweeps_per_layer": r["stats"]["bp_sweeps"] / L,
-            "roofline": roofs[dom], "roofline_other_kernels": {k: v for k, v in roofs.items() if k != dom}}
+            "roofline": roofs[dom], "roofline_other_kernels": {k: v for k, v in roofs.items() if k != dom},
+            "layer_roofline": layer_roofline(roofs)}
 
 
 def walk_range(G, s, w, timed, stream, flush) -> dict:
@@ -893,8 +922,74 @@ def ncu_scale(a):
     print(json.dumps({"ncu_scale": a.ncu_scale, "chi": 8, "precision": "mixed"}))
 
 
+def bp_study(a):
+    """How flooding BP behaves over the single-instance anneal (no timing): per layer the sweeps
+    of the FP64 path and whether they reached max_iter; at three late layers the distance of
+    every sweep of a 160-sweep run from the warm start, with the change of each message between
+    consecutive sweeps (d1) and two sweeps apart (d2): a period-2 oscillation gives d2 << d1, a
+    steady drift d2 ~ 2 d1.  The same anneal with the fields of the paper's QUBO runs,
+    h ~ N(0, 1), is run beside it in FP64 and mixed, with the objective of each read-out."""
+    from instances import make_instance
+    from paper_2409_12240_gb300 import gtqa as G
+    G.load(build_if_missing=True)
+    K, dt, tol, mi, chi = WL["K"], WL["dt"], WL["tol"], WL["max_iter"], WL["chi"]
+    out = {}
+    for hname, hs in (("h_std_0.1", 0.1), ("h_std_1", 1.0)):
+        inst = make_instance(WL["n"], WL["seed"], h_std=hs)
+        res = {}
+        for pname, prec in (("fp64", G.GTQA_FP64), ("mixed", G.GTQA_MIXED)):
+            s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour, G.gtqa_options_init(precision=prec))
+            sweeps, maxit, states = [], [], {}
+            prev = G.gtqa_stats(s)
+            for k in range(1, K + 1):
+                if hs == 0.1 and prec == G.GTQA_FP64 and k in (1501, 2001, 2801):
+                    states[k] = G.gtqa_get_state(s)
+                G.gtqa_anneal_graph(s, k, k, K, dt, tol, mi)
+                st = G.gtqa_stats(s)
+                sweeps.append(st["bp_sweeps"] - prev["bp_sweeps"])
+                maxit.append(st["bp_not_converged_calls"] - prev["bp_not_converged_calls"])
+                prev = st
+            rho, sign = G.gtqa_marginals(s)
+            G.gtqa_destroy(s)
+            sw = np.array(sweeps)
+            first = int(np.argmax(np.array(maxit) > 0)) + 1 if any(maxit) else None
+            res[pname] = {"mean_sweeps": float(sw.mean()), "layers_at_max_iter": float(np.mean(maxit)),
+                          "first_max_iter_layer": first,
+                          "sweeps_per_100_layers": [float(x) for x in sw.reshape(-1, 100).mean(axis=1)],
+                          "histogram": {"bins": [1, 2, 3, 5, 10, 20, 50, 100, 101],
+                                        "counts": np.histogram(sw, bins=[1, 2, 3, 5, 10, 20, 50, 100, 101])[0].tolist()},
+                          "E": energy(inst, sign), "sign": sign}
+            if states:
+                traces = {}
+                for k, (Gm, L, Mg) in states.items():
+                    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour)
+                    G.gtqa_set_state(s, Gm, L, Mg)
+                    G.gtqa_trotter_layer(s, k / K, dt)
+                    dists, ms = [], []
+                    for t in range(160):
+                        _, d, _ = G.gtqa_bp_sweep(s, 0.0, 1, G.GTQA_BP_WARM_START if t == 0 else 0)
+                        dists.append(d)
+                        ms.append(G.gtqa_get_state(s)[2])
+                    G.gtqa_destroy(s)
+                    ms = np.array(ms)
+                    d1 = np.linalg.norm(ms[1:] - ms[:-1], axis=(2, 3)).sum(axis=1)
+                    d2 = np.linalg.norm(ms[2:] - ms[:-2], axis=(2, 3)).sum(axis=1)
+                    moving = (np.linalg.norm(ms[-1] - ms[-2], axis=(1, 2)) > 1e-6).mean()
+                    traces[str(k)] = {"dist_per_sweep": [float(dists[i]) for i in (0, 1, 2, 5, 10, 20, 50, 100, 159)],
+                                      "dist_min_max_last_100": [float(min(dists[60:])), float(max(dists[60:]))],
+                                      "d2_over_d1_last_50": float(np.mean(d2[-50:] / d1[-50:])),
+                                      "messages_moving_last_sweep": float(moving)}
+                res["fp64_traces"] = traces
+        res["sign_agreement_mixed_fp64"] = float(np.mean(res["mixed"].pop("sign") == res["fp64"].pop("sign")))
+        out[hname] = res
+    print(json.dumps({"bp_study": out, "workload": WORKLOAD_NAME}))
+
+
 def main():
     a = parse()
+    if a.bp_study:
+        bp_study(a)
+        return
     if a.ncu_case is not None:
         ncu_case(a)
         return

@@ -100,6 +100,11 @@ typedef struct gtqa_stats_t {
                                 (persistent path: when a sweep's lower bound falls under tol) */
     int64_t regauge_svd_sweeps; /* Jacobi sweeps of the regauge's eigen-decompositions and SVDs
                                    (persistent path; work counter) */
+    int32_t gate_svd_sweeps_max;      /* most FP64 Jacobi sweeps of one gate-core SVD since creation
+                                         (the FP64 polish sweeps in GTQA_MIXED; persistent path) */
+    int32_t gate_svd_sweeps32_max;    /* GTQA_MIXED: most FP32 preconditioning sweeps of one gate-core SVD */
+    int32_t regauge_svd_sweeps_max;   /* the same two maxima for the regauge's decompositions */
+    int32_t regauge_svd_sweeps32_max;
 } gtqa_stats_t;
 
 /* kernels timed by the optional profiler (gtqa_profile) */

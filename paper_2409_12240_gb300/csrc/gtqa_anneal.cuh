@@ -66,6 +66,10 @@ struct Control {
     long long regauged;      // regauge-policy layers: regauged (BP and gauge finding ran)
     long long reg_skipped;   // and skipped (R at or below the threshold)
     long long exact_passes;  // separate exact-distance passes (bp_exact_pass) run by BP
+    int gate_sw_max;         // most FP64 Jacobi sweeps of one gate-core SVD (polish sweeps in the mixed mode)
+    int gate_sw32_max;       // mixed mode: most FP32 preconditioning sweeps of one gate-core SVD
+    int reg_sw_max;          // the same for the regauge's eigen-decompositions and SVD
+    int reg_sw32_max;
 };
 
 struct Ctx {
@@ -266,6 +270,9 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
     }
     if (tid == 0) sm.nrot = 0;
     team_bar<TEAM>(team);
+    // rounding-level entries of the core (graded spectra of the early anneal) are zeroed first
+    if constexpr (TEAM <= 32) prune_noise<NM>(sm.M, tid, WarpGroup{group_mask<TEAM>()});
+    else prune_noise<NM>(sm.M, tid, TeamGroup<TEAM>{team, &sm.flag});
 
     // ---- SVD of M ----
     // FP64 mode: one-sided Jacobi in FP64 from V = I.
@@ -292,13 +299,15 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
     } else {
         for (int t = tid; t < NM * NM; t += TEAM) sm.M32[t] = ccast<float>(sm.M[t]);
         team_bar<TEAM>(team);
+        int sw32;
         if constexpr (TEAM <= 32) {
             WarpGroup grp{group_mask<TEAM>()};
-            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true, nullptr, 1e-3f);
+            sw32 = jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true, nullptr, 1e-3f);
         } else {
             TeamGroup<TEAM> grp{team, &sm.flag};
-            jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true, nullptr, 1e-3f);
+            sw32 = jacobi_svd<NM, float>(sm.M32, sm.V32, tid, grp, group_mask<NM>(), 1e-6f, 40, true, nullptr, 1e-3f);
         }
+        if (tid == 0) atomicMax(&c.ctl->gate_sw32_max, sw32);
         team_bar<TEAM>(team);
         for (int t = tid; t < NM * NM; t += TEAM) sm.V[t] = ccast<double>(sm.V32[t]);
         team_bar<TEAM>(team);
@@ -371,6 +380,7 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
             atomicAdd(&c.stats[1], Mode::mixed ? 2.0 * (double)log1pf(-(float)disc) : 2.0 * log1p(-disc));
             atomicAdd(&c.stats[2], (double)sweeps * (NM - 1) * (NM / 2));
             atomicAdd(&c.stats[3], (double)sm.nrot);
+            atomicMax(&c.ctl->gate_sw_max, sweeps);
             sm.keep = keep;
         }
     }
@@ -995,14 +1005,19 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
         // FP32-preconditioned path, whose result is FP64-accurate as well
         const int x = tid / GJ, g = tid % GJ;
         WarpGroup grp{group_mask<GJ>()};
-        int sw;
+        prune_noise<CHI>(sm.Am[x], g, grp);
+        int sw, sw32 = 0;
         if constexpr (Mode::mixed)
             sw = mixed_svd<CHI>(sm.Am[x], sm.Vm[x], sm.A32[x], sm.V32[x], sm.T1[x], sm.T2[x], sm.nrm[x], g, grp,
-                                group_mask<CHI>(), 1e-13, 3e-7, nullptr);
+                                group_mask<CHI>(), 1e-13, 3e-7, nullptr, &sw32);
         else
             sw = jacobi_svd<CHI, double, WarpGroup, true, true>(sm.Am[x], sm.Vm[x], g, grp, group_mask<CHI>(), 1e-15, 60,
                                                                 true, nullptr, 3e-8);
-        if (g == 0) atomicAdd(&c.stats[4], (double)sw);
+        if (g == 0) {
+            atomicAdd(&c.stats[4], (double)sw);
+            atomicMax(&c.ctl->reg_sw_max, sw);
+            atomicMax(&c.ctl->reg_sw32_max, sw32);
+        }
     }
     team_bar<TEAM>(team);
     for (int t = tid; t < 2 * CHI; t += TEAM) {
@@ -1045,14 +1060,19 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
     team_bar<TEAM>(team);
     if (tid < GJ) {
         WarpGroup grp{group_mask<GJ>()};
-        int sw;
+        prune_noise<CHI>(sm.M, tid, grp);
+        int sw, sw32 = 0;
         if constexpr (Mode::mixed)
             sw = mixed_svd<CHI>(sm.M, sm.VM, sm.A32[0], sm.V32[0], sm.T1[0], sm.T2[0], sm.nrm[0], tid, grp,
-                                group_mask<CHI>(), 1e-13, 3e-7, nullptr);
+                                group_mask<CHI>(), 1e-13, 3e-7, nullptr, &sw32);
         else
             sw = jacobi_svd<CHI, double, WarpGroup, true, true>(sm.M, sm.VM, tid, grp, group_mask<CHI>(), 1e-15, 60, true,
                                                                 nullptr, 3e-8);
-        if (tid == 0) atomicAdd(&c.stats[4], (double)sw);
+        if (tid == 0) {
+            atomicAdd(&c.stats[4], (double)sw);
+            atomicMax(&c.ctl->reg_sw_max, sw);
+            atomicMax(&c.ctl->reg_sw32_max, sw32);
+        }
     }
     team_bar<TEAM>(team);
     for (int cc = tid; cc < CHI; cc += TEAM) {

@@ -13,6 +13,43 @@
 
 using namespace gtqa;
 
+// Dispatch on precision mode and phase kernel to the launcher units (compiled in gtqa_units.cu).
+// Kept out of gtqa_launch.h: in a unit that sees the launchers' definitions these calls would
+// instantiate every kernel set there.
+namespace gtqa {
+inline bool phase_shape(bool mixed, int pk, int CHI, size_t* sb, int* tpb) {
+    switch (pk) {
+        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::shape(CHI, sb, tpb)
+                                    : PhaseUnit<ModeFP64, PK_GATES>::shape(CHI, sb, tpb);
+        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::shape(CHI, sb, tpb)
+                                 : PhaseUnit<ModeFP64, PK_BP>::shape(CHI, sb, tpb);
+        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::shape(CHI, sb, tpb)
+                              : PhaseUnit<ModeFP64, PK_REGAUGE>::shape(CHI, sb, tpb);
+    }
+}
+inline cudaError_t phase_prepare(bool mixed, int pk, int CHI, size_t smem, int* bps) {
+    switch (pk) {
+        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::prepare(CHI, smem, bps)
+                                    : PhaseUnit<ModeFP64, PK_GATES>::prepare(CHI, smem, bps);
+        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::prepare(CHI, smem, bps)
+                                 : PhaseUnit<ModeFP64, PK_BP>::prepare(CHI, smem, bps);
+        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::prepare(CHI, smem, bps)
+                              : PhaseUnit<ModeFP64, PK_REGAUGE>::prepare(CHI, smem, bps);
+    }
+}
+inline cudaError_t phase_launch(bool mixed, int pk, int CHI, const Ctx& c, size_t smem, cudaStream_t st) {
+    switch (pk) {
+        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::launch(CHI, c, smem, st)
+                                    : PhaseUnit<ModeFP64, PK_GATES>::launch(CHI, c, smem, st);
+        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::launch(CHI, c, smem, st)
+                                 : PhaseUnit<ModeFP64, PK_BP>::launch(CHI, c, smem, st);
+        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::launch(CHI, c, smem, st)
+                              : PhaseUnit<ModeFP64, PK_REGAUGE>::launch(CHI, c, smem, st);
+    }
+}
+
+}  // namespace gtqa
+
 struct gtqa_state {
     int B = 0, n = 0, m = 0;
     int chi = 0, CHI = 0;
@@ -1954,6 +1991,10 @@ int gtqa_stats(gtqa_state* s, gtqa_stats_t* out) {
     out->bp_not_converged_calls = ctl.nc_calls;
     out->bp_exact_passes = ctl.exact_passes;
     out->regauge_svd_sweeps = (int64_t)st[4];
+    out->gate_svd_sweeps_max = ctl.gate_sw_max;
+    out->gate_svd_sweeps32_max = ctl.gate_sw32_max;
+    out->regauge_svd_sweeps_max = ctl.reg_sw_max;
+    out->regauge_svd_sweeps32_max = ctl.reg_sw32_max;
     return ctl.err ? ctl.err : GTQA_OK;
 }
 

@@ -3,6 +3,7 @@
 // Jacobi SVD used for every small matrix decomposition of the method.
 #pragma once
 
+#include <climits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -70,6 +71,7 @@ struct WarpGroup {
     unsigned mask;
     __device__ __forceinline__ void sync() const { __syncwarp(mask); }
     __device__ __forceinline__ bool any(int p) const { return __any_sync(mask, p) != 0; }
+    __device__ __forceinline__ int max_int(int v) const { return __reduce_max_sync(mask, v); }
 };
 
 // Synchronisation policy for a group that is the whole thread block.
@@ -83,6 +85,14 @@ struct BlockGroup {
         if (p) atomicOr(flag, 1);
         __syncthreads();
         return *flag != 0;
+    }
+    __device__ __forceinline__ int max_int(int v) const {
+        __syncthreads();
+        if (threadIdx.x == 0) *flag = INT_MIN;
+        __syncthreads();
+        atomicMax(flag, v);
+        __syncthreads();
+        return *flag;
     }
 };
 
@@ -141,6 +151,31 @@ __device__ __forceinline__ float nr_sqrt(float x) { return x > 0.f ? sqrtf(x) : 
 // |gamma| > tol * sqrt(alpha beta).  On exit A holds U*S (columns unsorted) and
 // V the accumulated right rotations: A_in = (A_out) V^H.
 // ---------------------------------------------------------------------------
+// Zeroes the entries of an N x N complex matrix (column-major, shared) that lie more than 2^100
+// (about 1e30) below its largest entry.  Every value kept by the method's cut-offs (singular
+// values above 1e-14 s_0, message eigenvalues above 1e-13 w_max) is far above that, while such
+// rounding-level columns would keep one-sided Jacobi rotating pairs whose angle underflows
+// (a column of norm ~1e-44 next to one of norm ~1 in the early anneal).  The test compares the
+// exponent bits of the entries, on the integer pipe.  The group has N^2/2 lanes.
+__device__ __forceinline__ int exp_bits(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff); }
+template <int N, typename Group>
+__device__ void prune_noise(C<double>* A, int g, const Group& grp) {
+    constexpr int NN = N * N, L = NN / 2;
+    int e = 0;
+#pragma unroll
+    for (int j = 0; j < NN / L; ++j) {
+        const C<double> a = A[g + j * L];
+        e = max(e, max(exp_bits(a.x), exp_bits(a.y)));
+    }
+    const int emax = grp.max_int(e);
+#pragma unroll
+    for (int j = 0; j < NN / L; ++j) {
+        const C<double> a = A[g + j * L];
+        if (max(exp_bits(a.x), exp_bits(a.y)) < emax - 100) A[g + j * L] = C<double>{0.0, 0.0};
+    }
+    grp.sync();
+}
+
 __device__ __forceinline__ void round_robin_pair(int N, int step, int k, int& p, int& q) {
     if (k == 0) {
         p = step;
@@ -171,6 +206,10 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
     }
     grp.sync();
     const R tol2 = tol * tol, quad2 = quad_tol * quad_tol;
+    // a pair whose |gamma|^2 lies near the bottom of the range is orthogonal in absolute terms
+    // (the matrices here are normalised); taking it as converged also keeps the reciprocal
+    // square root away from subnormal inputs
+    const R gmin = sizeof(R) == 8 ? (R)1e-290 : (R)1e-36;
     const bool quad = quad_tol > (R)0;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
@@ -187,16 +226,22 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
             gam.y = group_sum<N>(gam.y, pair_mask);
             const R g2 = gam.x * gam.x + gam.y * gam.y;
             const R ab = alpha * beta;
-            if (g2 > (R)0 && g2 > tol2 * ab) {
+            if (g2 > gmin && g2 > tol2 * ab) {
                 if (g2 > quad2 * ab) big = 1;
                 const R rg = nr_rsqrt(g2);                      // 1 / |gamma|
                 const R zeta = (beta - alpha) * ((R)0.5 * rg);
                 R t;
                 if constexpr (F32ANGLE) {
-                    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) in FP32; 1/(2 zeta) for huge zeta
-                    const float zf = (float)zeta, azf = fabsf(zf);
-                    const float tf = azf < 1e18f ? __frcp_rn(azf + sqrtf(fmaf(azf, azf, 1.f))) : 0.5f * __frcp_rn(azf);
-                    t = (R)(zf >= 0.f ? tf : -tf);
+                    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) in FP32; for huge zeta (beyond the FP32
+                    // range when a column is tiny) t = 1/(2 zeta) in FP64, so the rotation does not vanish
+                    const R az = fabs(zeta);
+                    if (az < (R)1e18) {
+                        const float azf = (float)az;
+                        const float tf = __frcp_rn(azf + sqrtf(fmaf(azf, azf, 1.f)));
+                        t = (R)(zeta >= (R)0 ? tf : -tf);
+                    } else {
+                        t = (zeta >= (R)0 ? (R)0.5 : (R)-0.5) * nr_rcp(az);
+                    }
                 } else {
                     const R az = fabs(zeta);
                     // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), the smaller root; 1/(2 zeta) for huge zeta
@@ -228,13 +273,21 @@ __device__ int jacobi_svd(C<R>* A, C<R>* V, int g, const Group& grp, unsigned pa
     return sweep;   // sweeps run, including the final one (without rotations unless quad_tol stopped it)
 }
 
+// True if x (an updated squared norm) is negative, zero or below about half of ref, from the
+// raw bits only.
+__device__ __forceinline__ bool norm_collapsed(double x, double ref) {
+    const long long b = __double_as_longlong(x);
+    return b <= 0 || (int)((b >> 52) & 0x7ff) + 1 < exp_bits(ref);
+}
+
 // FP64 polish of a one-sided Jacobi SVD (same layout, pairing and rotations as
 // jacobi_svd<N, double>) for columns that are already nearly orthogonal, as after an
 // FP32 solve and an FP64 Newton-Schulz step.  Fewer FP64 instructions per step:
 //  * the squared column norms are kept in nrm[N] (shared) and, in steps whose rotations are all
 //    small, updated as alpha' = alpha - tau |gamma|^2 and beta' = beta + tau |gamma|^2 (the two
 //    eigenvalues of the pair's 2x2 Gram matrix) instead of two reductions per step; after a
-//    large rotation, where that update can cancel, they are recomputed;
+//    large rotation, or where the update would remove more than half of a norm (it then
+//    cancels), they are recomputed;
 //  * the rotation is parametrised by tau = t / |gamma| = 2 sign(D) / (|D| + sqrt(D^2 + 4|gamma|^2)),
 //    D = beta - alpha, solved in FP32 on values scaled by an approximate 1/(alpha + beta);
 //    then t^2 = tau^2 |gamma|^2, c = 1/sqrt(1 + t^2) and s e = c tau gamma are formed in FP64,
@@ -300,7 +353,7 @@ __device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, con
             gam.y = group_sum<N>(gam.y, pair_mask);
             const double g2 = gam.x * gam.x + gam.y * gam.y;
             const double ab = alpha * beta;
-            const bool rot = g2 > 0.0 && g2 > tol2 * ab;
+            const bool rot = g2 > 1e-290 && g2 > tol2 * ab;   // as in jacobi_svd
             double tau = 0.0, t2 = 0.0;
             if (rot) {
                 const bool rp = (rel >> p) & 1u, rq = (rel >> q) & 1u;
@@ -331,11 +384,17 @@ __device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, con
                 V[q * N + r] = se * vp + c * vq;
                 if (r == 0 && nrot) ++*nrot;
             }
-            if (series) {
+            // the updated norms; the smaller one loses |m|, and where that cancels (a column nearly
+            // parallel to a larger one) the update loses its precision and can turn negative, so
+            // both are then recomputed from the columns, as after a large rotation.  The test
+            // reads the sign and exponent bits (integer pipe): a drop below half or a sign change
+            const double m = tau * g2;   // 0 without a rotation
+            const double np_ = alpha - m, nq_ = beta + m;
+            const bool exact = !series || (rot && (norm_collapsed(np_, alpha) || norm_collapsed(nq_, beta)));
+            if (!exact) {
                 if (rot && r == 0) {
-                    const double m = tau * g2;
-                    nrm[p] = alpha - m;
-                    nrm[q] = beta + m;
+                    nrm[p] = np_;
+                    nrm[q] = nq_;
                 }
             } else {
                 // a large rotation: the update alpha - tau |gamma|^2 can cancel, so the two
@@ -366,12 +425,13 @@ __device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, con
 template <int N, typename Group>
 __device__ int mixed_svd(C<double>* A, C<double>* V, C<float>* A32, C<float>* V32, C<double>* T1, C<double>* T2,
                          double* nrm, int g, const Group& grp, unsigned pair_mask, double tol, double quad_tol,
-                         int* nrot) {
+                         int* nrot, int* sweeps32 = nullptr) {
     using CD = C<double>;
     constexpr int NN = N * N, L = NN / 2;
     for (int t = g; t < NN; t += L) A32[t] = ccast<float>(A[t]);
     grp.sync();
-    jacobi_svd<N, float>(A32, V32, g, grp, pair_mask, 1e-6f, 40, true, nullptr, 1e-3f);
+    const int sw32 = jacobi_svd<N, float>(A32, V32, g, grp, pair_mask, 1e-6f, 40, true, nullptr, 1e-3f);
+    if (sweeps32) *sweeps32 = sw32;
     for (int t = g; t < NN; t += L) V[t] = ccast<double>(V32[t]);
     grp.sync();
     for (int t = g; t < NN; t += L) {   // T1 = V^H V
@@ -450,6 +510,14 @@ struct TeamGroup {
         if (p) atomicOr(flag, 1);
         team_bar<TEAM>(team);
         return *(volatile int*)flag != 0;
+    }
+    __device__ __forceinline__ int max_int(int v) const {
+        team_bar<TEAM>(team);
+        if ((threadIdx.x % TEAM) == 0) *flag = INT_MIN;
+        team_bar<TEAM>(team);
+        atomicMax(flag, v);
+        team_bar<TEAM>(team);
+        return *(volatile int*)flag;
     }
 };
 

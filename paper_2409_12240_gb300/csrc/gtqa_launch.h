@@ -68,35 +68,4 @@ cudaError_t plain_single_gates_launch(int CHI, int D, int pm, void* Gamma, const
                                       cudaStream_t st);
 cudaError_t ising16_gates_launch(const Gate16Args& a, int pm, cudaStream_t st);
 
-inline bool phase_shape(bool mixed, int pk, int CHI, size_t* sb, int* tpb) {
-    switch (pk) {
-        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::shape(CHI, sb, tpb)
-                                    : PhaseUnit<ModeFP64, PK_GATES>::shape(CHI, sb, tpb);
-        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::shape(CHI, sb, tpb)
-                                 : PhaseUnit<ModeFP64, PK_BP>::shape(CHI, sb, tpb);
-        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::shape(CHI, sb, tpb)
-                              : PhaseUnit<ModeFP64, PK_REGAUGE>::shape(CHI, sb, tpb);
-    }
-}
-inline cudaError_t phase_prepare(bool mixed, int pk, int CHI, size_t smem, int* bps) {
-    switch (pk) {
-        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::prepare(CHI, smem, bps)
-                                    : PhaseUnit<ModeFP64, PK_GATES>::prepare(CHI, smem, bps);
-        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::prepare(CHI, smem, bps)
-                                 : PhaseUnit<ModeFP64, PK_BP>::prepare(CHI, smem, bps);
-        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::prepare(CHI, smem, bps)
-                              : PhaseUnit<ModeFP64, PK_REGAUGE>::prepare(CHI, smem, bps);
-    }
-}
-inline cudaError_t phase_launch(bool mixed, int pk, int CHI, const Ctx& c, size_t smem, cudaStream_t st) {
-    switch (pk) {
-        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::launch(CHI, c, smem, st)
-                                    : PhaseUnit<ModeFP64, PK_GATES>::launch(CHI, c, smem, st);
-        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::launch(CHI, c, smem, st)
-                                 : PhaseUnit<ModeFP64, PK_BP>::launch(CHI, c, smem, st);
-        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::launch(CHI, c, smem, st)
-                              : PhaseUnit<ModeFP64, PK_REGAUGE>::launch(CHI, c, smem, st);
-    }
-}
-
 }  // namespace gtqa

@@ -60,7 +60,9 @@ class gtqa_stats_t(ctypes.Structure):
                 ("discarded_weight", ctypes.c_double), ("log_fidelity", ctypes.c_double),
                 ("svd_pairs", ctypes.c_int64), ("svd_rotations", ctypes.c_int64), ("bp_sweeps", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("bp_calls", ctypes.c_int64), ("bp_not_converged_calls", ctypes.c_int64),
-                ("bp_exact_passes", ctypes.c_int64), ("regauge_svd_sweeps", ctypes.c_int64)]
+                ("bp_exact_passes", ctypes.c_int64), ("regauge_svd_sweeps", ctypes.c_int64),
+                ("gate_svd_sweeps_max", ctypes.c_int32), ("gate_svd_sweeps32_max", ctypes.c_int32),
+                ("regauge_svd_sweeps_max", ctypes.c_int32), ("regauge_svd_sweeps32_max", ctypes.c_int32)]
 
 
 class GTQAError(RuntimeError):
