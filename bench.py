@@ -586,6 +586,32 @@ def walk(G, s, K: int, dt: float, tol: float, mi: int, timed: Sequence[int], str
             "snaps": snap_out, "rho": rho, "sign": sign, "clocks": ck}
 
 
+KERNELS = ("gates_kernel", "bp_kernel", "regauge_kernel")
+
+
+def tune_launch(G, make_state, K: int, dt: float, tol: float, mi: int, k_tune: int) -> dict:
+    """gtqa_autotune on a separate state annealed (untimed) through layers 1..k_tune-1 of the
+    workload, timing layer k_tune; returns the launch table it picks (per kernel: grid,
+    shape variant, threads per block, team) and the time the search took."""
+    s = make_state()
+    try:
+        if k_tune > 1:
+            G.gtqa_anneal_graph(s, 1, k_tune - 1, K, dt, tol, mi)
+        t0 = time.perf_counter()
+        G.gtqa_autotune(s, k_tune / K, dt, tol, mi)
+        t_s = time.perf_counter() - t0
+        table = G.gtqa_launch_shape(s)
+    finally:
+        G.gtqa_destroy(s)
+    return {"table": table, "tuned_at_layer": k_tune, "search_s": round(t_s, 3)}
+
+
+def apply_launch(G, s, tuned: dict) -> None:
+    t = tuned["table"]
+    G.gtqa_set_shape(s, [t[k]["variant"] for k in KERNELS])
+    G.gtqa_set_grid(s, [t[k]["grid"] for k in KERNELS])
+
+
 def run_gtqa(a):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -614,9 +640,13 @@ def run_gtqa(a):
         return G.gtqa_create(x.n, x.edges, x.J if J is None else J, x.h, chi, x.colour,
                              G.gtqa_options_init(precision=p, cuda_stream=stream.cuda_stream))
 
+    # ---- launch shapes: gtqa_autotune from the state before the middle layer of the anneal ----
+    tuned = tune_launch(G, lambda: make(prec), Ks, dt, tol, mi, Ks // 2)
+
     # ---- the timed run of the chosen precision ----
     clocks = Clocks(local)
     s = make(prec)
+    apply_launch(G, s, tuned)
     main = walk(G, s, Ks, dt, tol, mi, timed, stream, flush, snaps=SNAPSHOTS, profile=True, clocks=clocks, dist=dist)
     G.gtqa_destroy(s)
     t_ms, value = replica_throughput(main["t_ms"], S, world, dist, "cuda")
@@ -640,7 +670,9 @@ def run_gtqa(a):
     try:
         run64 = None
         if mixed and not a.no_fp64:
+            tuned64 = tune_launch(G, lambda: make(G.GTQA_FP64), Ks, dt, tol, mi, Ks // 2)
             s = make(G.GTQA_FP64)
+            apply_launch(G, s, tuned64)
             run64 = walk(G, s, Ks, dt, tol, mi, timed, stream, flush, snaps=SNAPSHOTS,
                          save_before=sorted(set(err_layers) | set(cpu_layers)), profile=True, state_dir=state_dir)
             G.gtqa_destroy(s)
@@ -651,9 +683,9 @@ def run_gtqa(a):
                     "bp_layers_at_max_iter": run64["stats"]["bp_not_converged_calls"] / S,
                     "speedup_mixed_over_fp64": run64["t_ms"] / main["t_ms"],
                     "marginal_error_per_layer": per, "roofline": r64, "layer_roofline": layer_roofline(r64),
-                    "note": "the same timed layers on the FP64 path"}
+                    "launch": tuned64, "note": "the same timed layers on the FP64 path"}
             if not a.no_whole:
-                whole = whole_anneal(G, make, inst, main, run64, stream, flush, props.multi_processor_count)
+                whole = whole_anneal(G, make, inst, main, run64, stream, flush, props.multi_processor_count, tuned64)
         if rank == 0 and world == 1 and not a.no_cpu and run64 is not None:
             with open(os.path.join(state_dir, "layers.json"), "w") as f:
                 json.dump({"layers": cpu_layers, "sweeps": [int(run64["per_layer"][k]["sweeps"]) for k in cpu_layers]}, f)
@@ -670,6 +702,7 @@ def run_gtqa(a):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s3 = make(prec)
+        apply_launch(G, s3, tuned)
         for k in range(1, Ks + 1):
             G.gtqa_anneal_graph(s3, k, k, Ks, dt, tol, mi)
             G.gtqa_marginals(s3, rho_h, sign_h)
@@ -697,7 +730,7 @@ def run_gtqa(a):
         "bp_sweeps_per_layer": main["stats"]["bp_sweeps"] / nl,
         "bp_layers_at_max_iter": main["stats"]["bp_not_converged_calls"] / nl,
         "bp_exact_passes": main["stats"]["bp_exact_passes"],
-        "fp64_path": fp64, "whole_anneal": whole,
+        "launch": tuned, "fp64_path": fp64, "whole_anneal": whole,
         "roofline": roofs[dom], "roofline_other_kernels": {k: v for k, v in roofs.items() if k != dom},
         "layer_roofline": layer_roofline(roofs), "kernel_share": kernel_share,
         "alu_peaks_tflops": {"fp32": peaks.fp32, "fp64": peaks.fp64, "fp32_measured": peaks.fp32_meas,
@@ -745,7 +778,7 @@ def per_layer_error(G, make, layers: Sequence[int], state_dir: str) -> dict:
             "note": "one layer in each mode from the same FP64 state at layer k-1"}
 
 
-def whole_anneal(G, make, inst, main, run64, stream, flush, sms: int) -> dict:
+def whole_anneal(G, make, inst, main, run64, stream, flush, sms: int, tuned64: dict) -> dict:
     """The read-out over the whole anneal: the mixed run and FP64 runs whose inputs differ at
     rounding level (every J_ab moved by one ulp; every J_ab scaled by 1 + 2^-24 xi with seeded
     signs xi, the size of complex64 rounding; another grid size of the persistent kernels,
@@ -760,6 +793,7 @@ def whole_anneal(G, make, inst, main, run64, stream, flush, sms: int) -> dict:
     finals = {"mixed": main["sign"], "fp64": run64["sign"]}
     for name, kw in runs.items():
         s = make(G.GTQA_FP64, J=kw.get("J"))
+        apply_launch(G, s, tuned64)   # the FP64 run's launch shapes
         if "grid" in kw:
             G.gtqa_set_grid(s, [kw["grid"]] * 3)
         r = walk(G, s, Ks, dt, tol, mi, [], stream, flush, snaps=SNAPSHOTS)
@@ -796,10 +830,15 @@ def batched_legs(G, stream, flush, peaks: Peaks, W: int, S: int, fp64) -> dict:
             "256_uneven": (make_batch(BATCH_WL["B"], seed=BATCH_WL["seed"]), BATCH_WL["K"], BATCH_WL["dt"],
                            BATCH_WL["tol"], BATCH_WL["max_iter"])}
     for name, (insts, K, dt, tol, mi) in legs.items():
-        s = G.gtqa_create_batch([x.n for x in insts], [x.edges for x in insts], [x.J for x in insts],
-                                [x.h for x in insts], 4, [x.colour for x in insts],
-                                G.gtqa_options_init(precision=G.GTQA_MIXED, cuda_stream=stream.cuda_stream))
-        timed = sample_layers(min(W, K - 1), min(S, K - min(W, K - 1)), K)
+        def mk():
+            return G.gtqa_create_batch([x.n for x in insts], [x.edges for x in insts], [x.J for x in insts],
+                                       [x.h for x in insts], 4, [x.colour for x in insts],
+                                       G.gtqa_options_init(precision=G.GTQA_MIXED, cuda_stream=stream.cuda_stream))
+        w0 = min(W, K - 1)
+        tuned = tune_launch(G, mk, K, dt, tol, mi, w0 + 1)
+        s = mk()
+        apply_launch(G, s, tuned)
+        timed = sample_layers(w0, min(S, K - w0), K)
         r = walk(G, s, K, dt, tol, mi, timed, stream, flush, profile=True)
         G.gtqa_destroy(s)
         N = sum(x.n for x in insts)
@@ -812,7 +851,7 @@ def batched_legs(G, stream, flush, peaks: Peaks, W: int, S: int, fp64) -> dict:
                      "instance_layers_per_s": len(insts) * L / (r["t_ms"] / 1e3),
                      "batch_layers_per_s": L / (r["t_ms"] / 1e3), "ms_per_layer": r["t_ms"] / L,
                      "bp_sweeps_per_layer": r["stats"]["bp_sweeps"] / L,
-                     "fp64_single_instance_layers_per_s": (fp64 or {}).get("value"),
+                     "fp64_single_instance_layers_per_s": (fp64 or {}).get("value"), "launch": tuned,
                      "roofline": roofs[dom], "roofline_other_kernels": {k: v for k, v in roofs.items() if k != dom},
                      "layer_roofline": layer_roofline(roofs)}
     return out
@@ -824,16 +863,24 @@ def scale_leg(G, stream, flush, peaks: Peaks, fp64) -> dict:
     from instances import make_instance
     w = SCALE_WL
     inst = make_instance(w["n"], w["seed"])
-    s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, w["chi"], inst.colour,
-                      G.gtqa_options_init(precision=G.GTQA_MIXED, cuda_stream=stream.cuda_stream))
+
+    def mk():
+        return G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, w["chi"], inst.colour,
+                             G.gtqa_options_init(precision=G.GTQA_MIXED, cuda_stream=stream.cuda_stream))
+    s = mk()
     timed = list(range(w["warm"] + 1, w["warm"] + w["steps"] + 1))
     G.gtqa_anneal_graph(s, 1, w["warm"], w["K"], w["dt"], w["tol"], w["max_iter"])
+    # gtqa_autotune on this state, timing the first timed layer (it restores the state)
+    t0 = time.perf_counter()
+    G.gtqa_autotune(s, timed[0] / w["K"], w["dt"], w["tol"], w["max_iter"])
+    tuned = {"table": G.gtqa_launch_shape(s), "tuned_at_layer": timed[0],
+             "search_s": round(time.perf_counter() - t0, 3)}
     r = walk_range(G, s, w, timed, stream, flush)
     G.gtqa_destroy(s)
     roofs = rooflines(r["prof"], r["stats"], w["chi"], inst.n, inst.m, True, peaks, traffic=False)
     dom = max(roofs, key=lambda kn: r["prof"][kn][1])
     L = len(timed)
-    return {"n": inst.n, "m": inst.m, "chi": w["chi"], "K": w["K"], "dt": w["dt"],
+    return {"n": inst.n, "m": inst.m, "chi": w["chi"], "K": w["K"], "dt": w["dt"], "launch": tuned,
             "layers_timed": {"count": L, "first": timed[0], "last": timed[-1]},
             "layers_per_s": L / (r["t_ms"] / 1e3), "ms_per_layer": r["t_ms"] / L,
             "bp_sweeps_per_layer": r["stats"]["bp_sweeps"] / L,

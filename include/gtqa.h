@@ -190,21 +190,44 @@ int gtqa_anneal(gtqa_state* s, int32_t k_begin, int32_t k_end, int32_t K, double
 
 /*
  * Autotuner of the launch shapes.  Each of the three phase kernels (gates, BP, regauge) is a
- * persistent cooperative launch of `grid` blocks, one per SM at most.  For each kernel in turn,
- * gtqa_autotune times one launch of the layer (tau, dt) with BP to (tol, max_iter) from the
- * state's current contents.  It tries each candidate grid: all SMs, 7/8 ... 1/2 of them, and
- * the fewest blocks that cover the kernel's work in one round of teams.  The earlier phases of
- * the layer run untimed first, so that each kernel sees its real inputs.  The median of three
- * runs decides, and the fastest grid is kept for the state.  The state's contents and
- * statistics are restored afterwards.  grid_out (nullable, 3 ints) receives the chosen grid
- * sizes.  Results do not depend on the grid, except for the rounding order of the BP distance
- * sum.  Synchronises.  Returns GTQA_ERR_UNSUPPORTED for a plain-path state (gtqa_create).
+ * persistent cooperative launch of `grid` blocks, one per SM at most, in one of a few compiled
+ * launch-shape variants (threads per block and team sizes; see gtqa_launch_shape).  For each
+ * kernel in turn, gtqa_autotune times one launch of the layer (tau, dt) with BP to
+ * (tol, max_iter) from the state's current contents, for every variant whose shared memory fits
+ * on an SM and, per variant, each candidate grid: all SMs and, when the kernel's work fits in one
+ * round of that variant's teams, 7/8 ... 1/2 of them and the fewest blocks that cover it.  The
+ * earlier phases of the layer run untimed first, so that each kernel sees its real inputs.  The
+ * median of three runs decides, and the fastest (variant, grid) pair is kept for the state.  The
+ * state is snapshotted once (into device memory when a copy fits in free memory, else into host
+ * memory), its contents and statistics are restored afterwards, and a layer graph captured by
+ * gtqa_anneal_graph is dropped (the next call captures the new shapes).  grid_out (nullable,
+ * 3 ints) receives the chosen grid sizes.  Results do not depend on the grid; across variants
+ * they differ only in the rounding order of BP's contraction and distance sums.  Synchronises.
+ * Returns GTQA_ERR_UNSUPPORTED for a plain-path state (gtqa_create).
  */
 int gtqa_autotune(gtqa_state* s, double tau, double dt, double tol, int32_t max_iter, int32_t* grid_out);
 
 /* Set the grid sizes (blocks of the gates, BP and regauge kernels, each 1..number of SMs), for
- * example to apply gtqa_autotune's choice from another state of the same shape. */
+ * example to apply gtqa_autotune's choice from another state of the same shape.  Drops a
+ * captured layer graph. */
 int gtqa_set_grid(gtqa_state* s, const int32_t* grid);
+
+/*
+ * Launch-shape variants (3 ints: gates, BP, regauge).  The gates kernel has variants 0 and 1,
+ * BP and regauge 0, 1 and 2; variant 0 is the default of gtqa_create_batch.  For CHI <= 4
+ * (threads per block, BP vertex team, regauge-vertex team) are (512, 64, 32), (256, 64, 32) and
+ * (512, 128, 64); for CHI = 8 they are (256, 256, 128), (512, 256, 128) and (512, 512, 256).
+ * The gate-edge team (2 CHI^2 threads) and the regauge-edge team (CHI^2) are fixed.
+ * GTQA_ERR_INVALID_ARG for an index out of range, GTQA_ERR_UNSUPPORTED when a variant's
+ * shared memory does not fit on an SM (the state keeps its shapes) or for a plain-path state.
+ * Drops a captured layer graph.
+ */
+int gtqa_set_shape(gtqa_state* s, const int32_t* variant);
+
+/* The current launch table: out[4 k .. 4 k + 3] = grid blocks, shape variant, threads per
+ * block and team size (gate edge, BP vertex, regauge vertex) of kernel k = gates, BP, regauge
+ * (12 ints).  GTQA_ERR_UNSUPPORTED for a plain-path state. */
+int gtqa_launch_shape(gtqa_state* s, int32_t* out);
 
 /*
  * gtqa_anneal with the paper's occasional regauging (Sec. II C: the Vidal gauge is restored

@@ -133,13 +133,25 @@ __device__ __forceinline__ double lam_get(const double* lam, int CHI, int e, int
     return e < 0 ? (j == 0 ? 1.0 : 0.0) : __ldcg(lam + (size_t)e * CHI + j);
 }
 
-template <int CHI> struct Shape {
-    static constexpr int TPB = CHI >= 8 ? 256 : 512;
-    static constexpr int TG = 2 * CHI * CHI;                    // gate team
-    static constexpr int TB = CHI >= 8 ? 256 : 64;               // BP team (one vertex)
-    static constexpr int TR = CHI * CHI;                        // regauge-edge team
-    static constexpr int TV = 32;                               // BP-init team (one warp)
-    static constexpr int TRV = CHI >= 8 ? 128 : 32;             // regauge-vertex team
+// Launch shapes of the persistent phase kernels: threads per block and team sizes.  The gate
+// team TG (one lane per element pair of the Jacobi SVD of the 2CHI x 2CHI core), the
+// regauge-edge team TR and the BP-init team TV are fixed by their algorithms; the block size
+// TPB, the BP vertex team TB and the regauge-vertex team TRV come in NSHAPE variants, which
+// gtqa_autotune times kernel by kernel.  Variant 0 is the default:
+//   CHI <= 4: (TPB, TB, TRV) = (512, 64, 32), (256, 64, 32), (512, 128, 64)
+//   CHI  = 8:                  (256, 256, 128), (512, 256, 128), (512, 512, 256)
+constexpr int NSHAPE = 3;
+template <int CHI, int V = 0> struct Shape {
+    static_assert(V >= 0 && V < NSHAPE, "launch-shape variant");
+    static constexpr bool BIG = CHI >= 8;
+    static constexpr int TPB = V == 0 ? (BIG ? 256 : 512) : (V == 1 ? (BIG ? 512 : 256) : 512);
+    static constexpr int TG = 2 * CHI * CHI;                                           // gate team
+    static constexpr int TB = V == 2 ? (BIG ? 512 : 128) : (BIG ? 256 : 64);            // BP team (one vertex)
+    static constexpr int TR = CHI * CHI;                                               // regauge-edge team
+    static constexpr int TV = 32;                                                      // BP-init team (one warp)
+    // warps of a block that run the BP init (its per-warp scratch grows as CHI^3)
+    static constexpr int NIT = BIG && TPB / 32 > 8 ? 8 : TPB / 32;
+    static constexpr int TRV = V == 2 ? (BIG ? 256 : 64) : (BIG ? 128 : 32);           // regauge-vertex team
 };
 
 // ===========================================================================
@@ -562,14 +574,14 @@ __device__ void bp_init_vertex(const Ctx& c, int a, int tid, int cur, bool warm,
 // diagonals, D0, t0, this vertex's previous outgoing messages) are cached in the
 // team's shared memory across sweeps.
 // ===========================================================================
-template <int CHI, class Mode>
+template <int CHI, class Mode, int TB>
 struct BPSm {
     using TS = typename Mode::TS;
     static constexpr int H2 = 2 * CHI * CHI * CHI, CC = CHI * CHI, NP = Mode::mixed ? 3 : 2;
     // F in two halves over the physical index (summed at use) unless the team is NPART lanes
     // per (j, j') that split the (i, u) sum and meet by shuffles
-    static constexpr int NPART = Shape<CHI>::TB / CC;
-    static constexpr bool FSPLIT = !(Shape<CHI>::TB % CC == 0 && NPART <= 32 && (2 * CHI) % NPART == 0);
+    static constexpr int NPART = TB / CC;
+    static constexpr bool FSPLIT = !(TB % CC == 0 && NPART <= 32 && (2 * CHI) % NPART == 0);
     // T, P and Q in the natural index order [i][j0][j1][j2] with one padding element after
     // every (i, j0) plane, so that a stride along slot 0 does not map to one bank
     static constexpr int PS = CC + 1, H2P = 2 * CHI * PS;
@@ -591,11 +603,11 @@ struct BPSm {
     int cached;          // vertex held in the cache, -1 if none
 };
 
-template <int CHI, class Mode>
-__device__ void bp_prepare(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode>& sm) {
+template <int CHI, class Mode, int TB>
+__device__ void bp_prepare(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode, TB>& sm) {
     using TS = typename Mode::TS;
     using CT = C<TS>;
-    constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H2 = 2 * CHI * CHI * CHI;
+    constexpr int TEAM = TB, CC = CHI * CHI, H2 = 2 * CHI * CHI * CHI;
     team_bar<TEAM>(team);   // the team may still be reading the previous vertex's cache
     if (tid < 3) {
         const int4 ve = c.vert_edges[a];
@@ -637,17 +649,17 @@ __device__ void bp_prepare(const Ctx& c, int a, int tid, int team, int cur, BPSm
 
 // First part of the sweep for vertex a: incoming messages, the contractions, and the
 // traces of the three outgoing messages (left in sm.trs).
-template <int CHI, class Mode>
-__device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode>& sm, bool have_pre,
+template <int CHI, class Mode, int TB>
+__device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<CHI, Mode, TB>& sm, bool have_pre,
                          C<typename Mode::TS> pre) {
     using TS = typename Mode::TS;
     using CT = C<TS>;
-    constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI, H = CHI * CHI * CHI, H2 = 2 * H;
+    using SM = BPSm<CHI, Mode, TB>;
+    constexpr int TEAM = TB, CC = CHI * CHI, H = CHI * CHI * CHI, H2 = 2 * H;
     // strides in the padded shared-memory layout: slot 0, slot 1 (slot 2 has stride 1), i
-    constexpr int S0 = BPSm<CHI, Mode>::PS, S1 = CHI, HP = CHI * BPSm<CHI, Mode>::PS;
-    if (sm.cached != a) bp_prepare<CHI, Mode>(c, a, tid, team, cur, sm);
+    constexpr int S0 = SM::PS, S1 = CHI, HP = CHI * SM::PS;
+    if (sm.cached != a) bp_prepare<CHI, Mode, TB>(c, a, tid, team, cur, sm);
     const CT* src = (const CT*)c.msg[cur];
-    CT* dst = (CT*)c.msg[cur ^ 1];
     const CT z = CT{(TS)0, (TS)0};
     // incoming messages (prefetched into `pre` by the caller when have_pre)
     for (int t = tid; t < 3 * CC; t += TEAM) {
@@ -666,7 +678,7 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
     team_bar<TEAM>(team);
     // first contractions along one slot: P_k[.., x@k, ..] = sum_q T[.., q@k, ..] y_k[q][x]
     //   FP64: y = m (k = 0, 1); mixed: y = delta (k = 0, 1, 2)
-    constexpr int NP = BPSm<CHI, Mode>::NP;
+    constexpr int NP = SM::NP;
     constexpr bool EVEN = H2 % TEAM == 0;   // whole tensors per team pass: slots fixed at compile time
     auto slot_stride = [](int k) { return k == 0 ? S0 : (k == 1 ? S1 : 1); };
     // e: natural index of an element, pe: its padded position
@@ -728,7 +740,7 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
     }
     team_bar<TEAM>(team);
     // overlaps with conj(T): F_s[j][j'] = sum over (i, u@o0, v@o1) of Q_s[.., j@s] conj(T[.., j'@s])
-    if constexpr (BPSm<CHI, Mode>::FSPLIT) {
+    if constexpr (SM::FSPLIT) {
         // one half of the sum per physical index i, added at use
         for (int t = tid; t < 2 * 3 * CC; t += TEAM) {
             const int i = t / (3 * CC), rem = t % (3 * CC);
@@ -750,7 +762,7 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
     } else {
         // lane = (j, j') * NPART + part; each part sums 2 CHI / NPART of the (i, u) pairs,
         // then a shuffle sum over the NPART adjacent lanes
-        constexpr int NPART = BPSm<CHI, Mode>::NPART, PER = 2 * CHI / NPART;
+        constexpr int NPART = SM::NPART, PER = 2 * CHI / NPART;
         const int r = tid / NPART, part = tid % NPART;
         const int j = r / CHI, jp = r % CHI;
 #pragma unroll
@@ -780,7 +792,7 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
         CT trs = z;
 #pragma unroll
         for (int j = 0; j < CHI; ++j)
-            trs = trs + (BPSm<CHI, Mode>::FSPLIT ? sm.Fh[0][k][j * CHI + j] + sm.Fh[1][k][j * CHI + j]
+            trs = trs + (SM::FSPLIT ? sm.Fh[0][k][j * CHI + j] + sm.Fh[1][k][j * CHI + j]
                                                   : sm.Fh[0][k][j * CHI + j]);
         sm.trs[k] = trs;
     }
@@ -790,28 +802,29 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
 // R10: messages are divided by their complex trace), one lane per message, by the first
 // warp of the block: FP64 instructions cost the same for 1 or 32 active lanes, so one
 // warp does this for all teams.  Mixed: the trace is t0 + tr Fd.
-template <int CHI, class Mode>
-__device__ void bp_trace_rcp(BPSm<CHI, Mode>* all, int nteams) {
+template <int CHI, class Mode, int TB>
+__device__ void bp_trace_rcp(BPSm<CHI, Mode, TB>* all, int nteams) {
     using TS = typename Mode::TS;
-    const int l = threadIdx.x;
-    if (l >= 3 * nteams) return;
-    BPSm<CHI, Mode>& sm = all[l / 3];
-    const int k = l % 3;
-    cd tr = ccast<double>(sm.trs[k]);
-    if constexpr (Mode::mixed) tr = tr + sm.t0[k];
-    const double n2 = norm2(tr);
-    // the mixed mode rounds the result to FP32, so one Newton step (relative error ~2^-44) suffices
-    const double in2 = n2 > 0.0 ? (Mode::mixed ? nr_rcp1(n2) : nr_rcp(n2)) : 0.0;
-    sm.itr[k] = ccast<TS>(cd{tr.x * in2, -tr.y * in2});
+    for (int l = threadIdx.x; l < 3 * nteams; l += 32) {
+        BPSm<CHI, Mode, TB>& sm = all[l / 3];
+        const int k = l % 3;
+        cd tr = ccast<double>(sm.trs[k]);
+        if constexpr (Mode::mixed) tr = tr + sm.t0[k];
+        const double n2 = norm2(tr);
+        // the mixed mode rounds the result to FP32, so one Newton step (relative error ~2^-44) suffices
+        const double in2 = n2 > 0.0 ? (Mode::mixed ? nr_rcp1(n2) : nr_rcp(n2)) : 0.0;
+        sm.itr[k] = ccast<TS>(cd{tr.x * in2, -tr.y * in2});
+    }
 }
 
 // Second part: new messages m' = F / tr F (mixed: delta' = (D0 + Fd - m0 tr Fd) / (t0 + tr Fd))
 // and the distance of App. B, added to *dacc.
-template <int CHI, class Mode>
-__device__ void bp_back(const Ctx& c, int tid, int team, int cur, bool exact, BPSm<CHI, Mode>& sm, double* gacc) {
+template <int CHI, class Mode, int TB>
+__device__ void bp_back(const Ctx& c, int tid, int team, int cur, bool exact, BPSm<CHI, Mode, TB>& sm,
+                        double* gacc) {
     using TS = typename Mode::TS;
     using CT = C<TS>;
-    constexpr int TEAM = Shape<CHI>::TB, CC = CHI * CHI;
+    constexpr int TEAM = TB, CC = CHI * CHI;
     CT* dst = (CT*)c.msg[cur ^ 1];
     const CT z = CT{(TS)0, (TS)0};
     constexpr int GJ = CC / 2;
@@ -824,7 +837,7 @@ __device__ void bp_back(const Ctx& c, int tid, int team, int cur, bool exact, BP
         CT d = z;
         if (out >= 0) {
             const CT itr = sm.itr[k];
-            const CT f = BPSm<CHI, Mode>::FSPLIT ? sm.Fh[0][k][r] + sm.Fh[1][k][r] : sm.Fh[0][k][r];
+            const CT f = BPSm<CHI, Mode, TB>::FSPLIT ? sm.Fh[0][k][r] + sm.Fh[1][k][r] : sm.Fh[0][k][r];
             CT num = f;
             if constexpr (Mode::mixed) {
                 const int j = r / CHI, jp = r % CHI;
@@ -907,12 +920,12 @@ __device__ void bp_copy_vertex(const Ctx& c, int a, int tid, int TEAM, int cur) 
 // Exact distance of the sweep that wrote msg[cur_new] for the instances with need[b]
 // set: trace norms of new - old for every directed message, one group of CHI^2/2
 // threads per message (whole block, after a grid barrier).  Accumulates into ex[b].
-template <int CHI, class Mode>
+template <int CHI, class Mode, int TPB>
 __device__ void bp_exact_pass(const Ctx& c, int cur_new, const int* need, C<typename Mode::TS>* scratch,
                               double* bacc, double* ex) {
     using TS = typename Mode::TS;
     using CT = C<TS>;
-    constexpr int CC = CHI * CHI, GJ = CC / 2, TPB = Shape<CHI>::TPB, NG = TPB / GJ;
+    constexpr int CC = CHI * CHI, GJ = CC / 2, NG = TPB / GJ;
     const int gi = threadIdx.x / GJ, g = threadIdx.x % GJ;
     CT* Dm = scratch + gi * CC;
     const CT* nw = (const CT*)c.msg[cur_new];
@@ -1116,11 +1129,11 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
 }
 
 // regauge, vertex part: Gamma_a = T_a x_slot X (team TV, buffers in shared memory)
-template <int CHI, class Mode>
+template <int CHI, class Mode, int TEAM>
 __device__ void regauge_vertex(const Ctx& c, int a, int tid, int team, C<typename Mode::TS>* buf) {
     using TS = typename Mode::TS;
     using CT = C<TS>;
-    constexpr int H = CHI * CHI * CHI, CC = CHI * CHI, TEAM = Shape<CHI>::TRV;
+    constexpr int H = CHI * CHI * CHI, CC = CHI * CHI;
     const int4 ve = c.vert_edges[a];
     const int es[3] = {ve.x, ve.y, ve.z};
     CT* b0 = buf;
@@ -1162,28 +1175,28 @@ __device__ void regauge_vertex(const Ctx& c, int a, int tid, int team, C<typenam
 // ===========================================================================
 // the persistent kernel
 // ===========================================================================
-template <int CHI, class Mode, unsigned PH>
+template <int CHI, class Mode, unsigned PH, int V = 0>
 struct SmemSize {
-    static constexpr int TPB = Shape<CHI>::TPB;
-    static constexpr size_t gate = sizeof(GateSm<CHI>) * (TPB / Shape<CHI>::TG);
+    using S = Shape<CHI, V>;
+    static constexpr int TPB = S::TPB;
+    static constexpr size_t gate = sizeof(GateSm<CHI>) * (TPB / S::TG);
     // per-team caches, block sums (64 doubles), scratch of the exact-distance pass
-    static constexpr size_t bp = sizeof(BPSm<CHI, Mode>) * (TPB / Shape<CHI>::TB) + 64 * sizeof(double) +
+    static constexpr size_t bp = sizeof(BPSm<CHI, Mode, S::TB>) * (TPB / S::TB) + 64 * sizeof(double) +
                                  sizeof(C<typename Mode::TS>) * 2 * TPB;
-    static constexpr size_t rg = sizeof(RGSm<CHI>) * (TPB / Shape<CHI>::TR);
+    static constexpr size_t rg = sizeof(RGSm<CHI>) * (TPB / S::TR);
     static constexpr size_t rv =
-        sizeof(C<typename Mode::TS>) * (4 * CHI * CHI * CHI + 3 * CHI * CHI) * (TPB / Shape<CHI>::TRV);
+        sizeof(C<typename Mode::TS>) * (4 * CHI * CHI * CHI + 3 * CHI * CHI) * (TPB / S::TRV);
     static constexpr size_t init =
-        (sizeof(double) * 6 * CHI + (Mode::mixed ? sizeof(cd) * (2 * CHI * CHI * CHI + 3 * CHI * CHI) : 0)) *
-        (TPB / 32);
+        (sizeof(double) * 6 * CHI + (Mode::mixed ? sizeof(cd) * (2 * CHI * CHI * CHI + 3 * CHI * CHI) : 0)) * S::NIT;
     static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
     // bytes before the per-instance flags (which follow at this offset in the BP kernel)
     static constexpr size_t value = mx(mx((PH & PH_GATES) ? gate : 0, (PH & PH_BP) ? mx(bp, init) : 0),
                                        (PH & PH_REGAUGE) ? mx(rg, rv) : 0) + 16;
 };
 
-template <int CHI, class Mode, unsigned PH>
+template <int CHI, class Mode, unsigned PH, int V>
 __device__ __forceinline__ void anneal_body(const Ctx& c) {
-    using S = Shape<CHI>;
+    using S = Shape<CHI, V>;
     extern __shared__ __align__(16) unsigned char smem[];
     GridBarrier gb = grid_barrier_init(c.bar ? c.bar : &c.ctl->bar_count, &c.ctl->err, (unsigned)c.bar_expect);
     const int nteams_total_g = c.nblocks * (S::TPB / S::TG);
@@ -1233,13 +1246,15 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
         if constexpr ((PH & PH_BP) != 0u) {
             if (skip_regauge) continue;
             {
+                static_assert(S::TV == 32, "one warp per BP-init team");
                 const int team = threadIdx.x / S::TV, tid = threadIdx.x % S::TV;
-                const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * (S::TPB / S::TV);
+                const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * S::NIT;
                 double* wsm = reinterpret_cast<double*>(smem) + team * 6 * CHI;
-                cd* tsm = reinterpret_cast<cd*>(reinterpret_cast<double*>(smem) + (S::TPB / 32) * 6 * CHI) +
+                cd* tsm = reinterpret_cast<cd*>(reinterpret_cast<double*>(smem) + S::NIT * 6 * CHI) +
                           team * (2 * CHI * CHI * CHI + 3 * CHI * CHI);
-                for (int a = gteam; a < c.n; a += nt)
-                    bp_init_vertex<CHI, Mode>(c, a, tid, cur, (c.phases & PH_WARM) != 0, wsm, tsm);
+                if (team < S::NIT)
+                    for (int a = gteam; a < c.n; a += nt)
+                        bp_init_vertex<CHI, Mode>(c, a, tid, cur, (c.phases & PH_WARM) != 0, wsm, tsm);
                 const int g = blockIdx.x * S::TPB + threadIdx.x;
                 for (int b = g; b < c.B; b += c.nblocks * S::TPB) {
                     c.inst_done[b] = 0;   // host-visible copy
@@ -1252,16 +1267,17 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
             const int team = threadIdx.x / S::TB, tid = threadIdx.x % S::TB;
             const int tpb_teams = S::TPB / S::TB;
             using CT_ = C<typename Mode::TS>;
-            BPSm<CHI, Mode>& sm = reinterpret_cast<BPSm<CHI, Mode>*>(smem)[team];
-            double* bsum = reinterpret_cast<double*>(smem + sizeof(BPSm<CHI, Mode>) * tpb_teams);
+            using SMB = BPSm<CHI, Mode, S::TB>;
+            SMB& sm = reinterpret_cast<SMB*>(smem)[team];
+            double* bsum = reinterpret_cast<double*>(smem + sizeof(SMB) * tpb_teams);
             // every block keeps its own copy of the per-instance state; all blocks take
             // identical decisions from the same accumulators, so one barrier per sweep suffices
             // (two when a sweep's lower bound falls under the threshold and the exact
             // distance is computed afterwards)
-            int* done = reinterpret_cast<int*>(smem + SmemSize<CHI, Mode, PH>::value);
+            int* done = reinterpret_cast<int*>(smem + SmemSize<CHI, Mode, PH, V>::value);
             int* exnow = done + c.B;   // this sweep computes the exact distance inline
             int* need = exnow + c.B;   // exact distance needed after the sweep
-            double* thr = reinterpret_cast<double*>(smem + SmemSize<CHI, Mode, PH>::value +
+            double* thr = reinterpret_cast<double*>(smem + SmemSize<CHI, Mode, PH, V>::value +
                                                     (3 * sizeof(int) * (size_t)c.B + 7) / 8 * 8);
             double* thr_hi = thr + c.B;                               // bound that lets a sweep continue
             float* thr3 = reinterpret_cast<float*>(thr_hi + c.B);     // inline-exact trigger
@@ -1280,7 +1296,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
             __syncthreads();
             const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * tpb_teams;
             const int inst0 = gteam < c.n ? c.vert_inst[gteam] : 0;   // the first round's vertex
-            BPSm<CHI, Mode>* all = reinterpret_cast<BPSm<CHI, Mode>*>(smem);
+            SMB* all = reinterpret_cast<SMB*>(smem);
             bool have_pre = false;
             CT_ pre = CT_{0, 0};
             int* sflag = reinterpret_cast<int*>(bsum + 48);   // [2]: need | open << 1, per sweep parity
@@ -1307,11 +1323,11 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                         if (done[inst]) bp_copy_vertex<CHI, Mode>(c, a, tid, S::TB, cur);
                         else act = true;
                     }
-                    if (act) bp_front<CHI, Mode>(c, a, tid, team, cur, sm, base == 0 && have_pre, pre);
+                    if (act) bp_front<CHI, Mode, S::TB>(c, a, tid, team, cur, sm, base == 0 && have_pre, pre);
                     __syncthreads();
-                    if (threadIdx.x < 32) bp_trace_rcp<CHI, Mode>(all, tpb_teams);
+                    if (threadIdx.x < 32) bp_trace_rcp<CHI, Mode, S::TB>(all, tpb_teams);
                     __syncthreads();
-                    if (act) bp_back<CHI, Mode>(c, tid, team, cur, exnow[inst] != 0, sm, c.B == 1 ? nullptr : acc + inst);
+                    if (act) bp_back<CHI, Mode, S::TB>(c, tid, team, cur, exnow[inst] != 0, sm, c.B == 1 ? nullptr : acc + inst);
                     else if (tid < 3) sm.dl[tid] = 0;
                     if (c.B == 1) {
                         __syncthreads();
@@ -1372,7 +1388,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 if (threadIdx.x == 0) sflag[(it + 1) & 1] = 0;
                 if (fl & 1) {
                     if (blockIdx.x == 0 && threadIdx.x == 0) ++c.ctl->exact_passes;
-                    bp_exact_pass<CHI, Mode>(c, cur, need, scratch, bsum + 32, ex);
+                    bp_exact_pass<CHI, Mode, S::TPB>(c, cur, need, scratch, bsum + 32, ex);
                     if (!grid_sync(gb, c.spin_limit)) return;
                     for (int b = threadIdx.x; b < c.B; b += S::TPB) {
                         if (!need[b]) continue;
@@ -1436,7 +1452,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 CT* buf = reinterpret_cast<CT*>(smem) + (size_t)team * (4 * CHI * CHI * CHI + 3 * CHI * CHI);
                 const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * (S::TPB / S::TRV);
                 for (int a = gteam; a < c.n; a += nt) {
-                    regauge_vertex<CHI, Mode>(c, a, tid, team, buf);
+                    regauge_vertex<CHI, Mode, S::TRV>(c, a, tid, team, buf);
                     team_bar<S::TRV>(team);
                 }
                 if (!grid_sync(gb, c.spin_limit)) return;
@@ -1449,12 +1465,14 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
 }
 
 // The three phase kernels (one cooperative launch each).
-template <int CHI, class Mode>
-__global__ void __launch_bounds__(Shape<CHI>::TPB, 1) gates_kernel(Ctx c) { anneal_body<CHI, Mode, PH_GATES>(c); }
-template <int CHI, class Mode>
-__global__ void __launch_bounds__(Shape<CHI>::TPB, 1) bp_kernel(Ctx c) { anneal_body<CHI, Mode, PH_BP>(c); }
-template <int CHI, class Mode>
-__global__ void __launch_bounds__(Shape<CHI>::TPB, 1) regauge_kernel(Ctx c) { anneal_body<CHI, Mode, PH_REGAUGE>(c); }
+template <int CHI, class Mode, int V>
+__global__ void __launch_bounds__(Shape<CHI, V>::TPB, 1) gates_kernel(Ctx c) { anneal_body<CHI, Mode, PH_GATES, V>(c); }
+template <int CHI, class Mode, int V>
+__global__ void __launch_bounds__(Shape<CHI, V>::TPB, 1) bp_kernel(Ctx c) { anneal_body<CHI, Mode, PH_BP, V>(c); }
+template <int CHI, class Mode, int V>
+__global__ void __launch_bounds__(Shape<CHI, V>::TPB, 1) regauge_kernel(Ctx c) {
+    anneal_body<CHI, Mode, PH_REGAUGE, V>(c);
+}
 
 // marginals rho_a = sum Gamma Gamma^* prod lambda^2 / tr and the read-out (one warp per vertex)
 template <int CHI, class Mode>

@@ -17,34 +17,34 @@ using namespace gtqa;
 // Kept out of gtqa_launch.h: in a unit that sees the launchers' definitions these calls would
 // instantiate every kernel set there.
 namespace gtqa {
-inline bool phase_shape(bool mixed, int pk, int CHI, size_t* sb, int* tpb) {
+inline bool phase_shape(bool mixed, int pk, int CHI, int v, size_t* sb, int* tpb, int* team) {
     switch (pk) {
-        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::shape(CHI, sb, tpb)
-                                    : PhaseUnit<ModeFP64, PK_GATES>::shape(CHI, sb, tpb);
-        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::shape(CHI, sb, tpb)
-                                 : PhaseUnit<ModeFP64, PK_BP>::shape(CHI, sb, tpb);
-        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::shape(CHI, sb, tpb)
-                              : PhaseUnit<ModeFP64, PK_REGAUGE>::shape(CHI, sb, tpb);
+        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::shape(CHI, v, sb, tpb, team)
+                                    : PhaseUnit<ModeFP64, PK_GATES>::shape(CHI, v, sb, tpb, team);
+        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::shape(CHI, v, sb, tpb, team)
+                                 : PhaseUnit<ModeFP64, PK_BP>::shape(CHI, v, sb, tpb, team);
+        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::shape(CHI, v, sb, tpb, team)
+                              : PhaseUnit<ModeFP64, PK_REGAUGE>::shape(CHI, v, sb, tpb, team);
     }
 }
-inline cudaError_t phase_prepare(bool mixed, int pk, int CHI, size_t smem, int* bps) {
+inline cudaError_t phase_prepare(bool mixed, int pk, int CHI, int v, size_t smem, int* bps) {
     switch (pk) {
-        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::prepare(CHI, smem, bps)
-                                    : PhaseUnit<ModeFP64, PK_GATES>::prepare(CHI, smem, bps);
-        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::prepare(CHI, smem, bps)
-                                 : PhaseUnit<ModeFP64, PK_BP>::prepare(CHI, smem, bps);
-        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::prepare(CHI, smem, bps)
-                              : PhaseUnit<ModeFP64, PK_REGAUGE>::prepare(CHI, smem, bps);
+        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::prepare(CHI, v, smem, bps)
+                                    : PhaseUnit<ModeFP64, PK_GATES>::prepare(CHI, v, smem, bps);
+        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::prepare(CHI, v, smem, bps)
+                                 : PhaseUnit<ModeFP64, PK_BP>::prepare(CHI, v, smem, bps);
+        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::prepare(CHI, v, smem, bps)
+                              : PhaseUnit<ModeFP64, PK_REGAUGE>::prepare(CHI, v, smem, bps);
     }
 }
-inline cudaError_t phase_launch(bool mixed, int pk, int CHI, const Ctx& c, size_t smem, cudaStream_t st) {
+inline cudaError_t phase_launch(bool mixed, int pk, int CHI, int v, const Ctx& c, size_t smem, cudaStream_t st) {
     switch (pk) {
-        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::launch(CHI, c, smem, st)
-                                    : PhaseUnit<ModeFP64, PK_GATES>::launch(CHI, c, smem, st);
-        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::launch(CHI, c, smem, st)
-                                 : PhaseUnit<ModeFP64, PK_BP>::launch(CHI, c, smem, st);
-        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::launch(CHI, c, smem, st)
-                              : PhaseUnit<ModeFP64, PK_REGAUGE>::launch(CHI, c, smem, st);
+        case PK_GATES: return mixed ? PhaseUnit<ModeMixed, PK_GATES>::launch(CHI, v, c, smem, st)
+                                    : PhaseUnit<ModeFP64, PK_GATES>::launch(CHI, v, c, smem, st);
+        case PK_BP: return mixed ? PhaseUnit<ModeMixed, PK_BP>::launch(CHI, v, c, smem, st)
+                                 : PhaseUnit<ModeFP64, PK_BP>::launch(CHI, v, c, smem, st);
+        default: return mixed ? PhaseUnit<ModeMixed, PK_REGAUGE>::launch(CHI, v, c, smem, st)
+                              : PhaseUnit<ModeFP64, PK_REGAUGE>::launch(CHI, v, c, smem, st);
     }
 }
 
@@ -59,6 +59,9 @@ struct gtqa_state {
     int ncol = 0;
     int nblocks = 0;
     size_t smem[PK_COUNT] = {0, 0, 0};   // dynamic shared memory of the three phase kernels
+    int shape[PK_COUNT] = {0, 0, 0};     // their launch-shape variants (gtqa_autotune, gtqa_set_shape)
+    int tpb[PK_COUNT] = {0, 0, 0};       // threads per block and team size of each kernel's variant
+    int team[PK_COUNT] = {0, 0, 0};
     std::vector<int> h_inst_m;
     // device buffers
     void* Gamma = nullptr;
@@ -250,6 +253,16 @@ bool graph_collect(gtqa_state* s) {
         s->prof_units[kinds[q]] += units[q];
     }
     return true;
+}
+
+// Drop the captured layer graph: its launches carry the grid sizes and shapes of the capture.
+bool drop_graph(gtqa_state* s) {
+    const bool ok = graph_collect(s);
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    s->gexec = nullptr;
+    s->graph = nullptr;
+    return ok;
 }
 
 void prof_collect(gtqa_state* s) {
@@ -559,6 +572,28 @@ Ctx make_ctx(const gtqa_state* s) {
     return c;
 }
 
+// Select launch-shape variant v of phase kernel pk: its dynamic shared memory (with the BP
+// kernel's per-instance part), the kernel's opt-in shared-memory limit, and a check that a
+// block fits on an SM.  GTQA_ERR_UNSUPPORTED for a variant that does not exist or does not
+// fit; the state keeps its previous shape then.
+int apply_shape(gtqa_state* s, int pk, int v) {
+    if (v < 0 || v >= shape_count(pk)) return GTQA_ERR_UNSUPPORTED;
+    size_t base = 0;
+    int tpb = 0, team = 0, bps = 0;
+    if (!phase_shape(mixed(s), pk, s->CHI, v, &base, &tpb, &team)) return GTQA_ERR_UNSUPPORTED;
+    const size_t smem = (base + (pk == PK_BP ? bp_instance_smem(s->B) : 0) + 15) / 16 * 16;
+    const cudaError_t pe = phase_prepare(mixed(s), pk, s->CHI, v, smem, &bps);
+    if (pe != cudaSuccess || bps < 1) {
+        cudaGetLastError();
+        return (pe == cudaSuccess || pe == cudaErrorInvalidValue) ? GTQA_ERR_UNSUPPORTED : GTQA_ERR_CUDA;
+    }
+    s->shape[pk] = v;
+    s->smem[pk] = smem;
+    s->tpb[pk] = tpb;
+    s->team[pk] = team;
+    return GTQA_OK;
+}
+
 // One cooperative launch of a phase kernel.
 int run(gtqa_state* s, const Ctx& c0, int pk, int kind, long long units) {
     cudaError_t e;
@@ -571,7 +606,7 @@ int run(gtqa_state* s, const Ctx& c0, int pk, int kind, long long units) {
     c.bar = &s->ctl->bar_pk[pk];
     {
         ProfScope ps(s, kind, units);
-        e = phase_launch(mixed(s), pk, s->CHI, c, s->smem[pk], s->stream);
+        e = phase_launch(mixed(s), pk, s->CHI, s->shape[pk], c, s->smem[pk], s->stream);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -710,18 +745,10 @@ int create_impl(int B, const int* n, const int* m, const int* edges, const int* 
         return GTQA_ERR_CUDA;
     }
     for (int pk = 0; pk < PK_COUNT && !s->plain; ++pk) {
-        size_t base = 0;
-        int tpb = 0, bps = 0;
-        if (!phase_shape(mixed(s), pk, s->CHI, &base, &tpb)) {
+        const int src = apply_shape(s, pk, 0);
+        if (src != GTQA_OK) {
             delete s;
-            return GTQA_ERR_UNSUPPORTED;
-        }
-        s->smem[pk] = (base + (pk == PK_BP ? bp_instance_smem(B) : 0) + 15) / 16 * 16;
-        const cudaError_t pe = phase_prepare(mixed(s), pk, s->CHI, s->smem[pk], &bps);
-        if (pe != cudaSuccess || bps < 1) {
-            cudaGetLastError();
-            delete s;
-            return pe != cudaSuccess ? GTQA_ERR_CUDA : GTQA_ERR_UNSUPPORTED;
+            return src;
         }
     }
     s->nblocks = sms;
@@ -1197,14 +1224,10 @@ int anneal_launches(gtqa_state* s, int k_begin, int k_end, int K, double dt, dou
     return GTQA_OK;
 }
 
-// Work teams per block of each phase kernel (the regauge counts its edge teams).
-template <int CHI>
-int teams_per_block_t(int pk) {
-    using S = Shape<CHI>;
-    return pk == PK_GATES ? S::TPB / S::TG : (pk == PK_BP ? S::TPB / S::TB : S::TPB / S::TR);
-}
-int teams_per_block(int pk, int CHI) {
-    return CHI == 2 ? teams_per_block_t<2>(pk) : (CHI == 4 ? teams_per_block_t<4>(pk) : teams_per_block_t<8>(pk));
+// Work teams per block of a phase kernel in its current shape (the regauge counts its edge
+// teams of CHI^2 threads).
+int teams_per_block(const gtqa_state* s, int pk) {
+    return s->tpb[pk] / std::max(1, pk == PK_REGAUGE ? s->CHI * s->CHI : s->team[pk]);
 }
 
 // Zero the per-kernel barrier counters (stream-ordered, between launches).
@@ -1275,8 +1298,42 @@ int gtqa_set_grid(gtqa_state* s, const int32_t* grid) {
     if (!grid) return GTQA_ERR_INVALID_ARG;
     for (int pk = 0; pk < PK_COUNT; ++pk)
         if (grid[pk] < 1 || grid[pk] > s->nblocks) return GTQA_ERR_INVALID_ARG;
+    if (!drop_graph(s)) return GTQA_ERR_CUDA;
     for (int pk = 0; pk < PK_COUNT; ++pk) s->grid[pk] = grid[pk];
     return zero_barriers(s);
+}
+
+int gtqa_set_shape(gtqa_state* s, const int32_t* variant) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (!variant) return GTQA_ERR_INVALID_ARG;
+    if (s->plain) return GTQA_ERR_UNSUPPORTED;
+    for (int pk = 0; pk < PK_COUNT; ++pk)
+        if (variant[pk] < 0 || variant[pk] >= shape_count(pk)) return GTQA_ERR_INVALID_ARG;
+    if (!drop_graph(s)) return GTQA_ERR_CUDA;
+    int old[PK_COUNT];
+    for (int pk = 0; pk < PK_COUNT; ++pk) old[pk] = s->shape[pk];
+    for (int pk = 0; pk < PK_COUNT; ++pk) {
+        if ((rc = apply_shape(s, pk, variant[pk])) != GTQA_OK) {
+            for (int q = 0; q < pk; ++q) apply_shape(s, q, old[q]);
+            return rc;
+        }
+    }
+    return zero_barriers(s);
+}
+
+int gtqa_launch_shape(gtqa_state* s, int32_t* out) {
+    int rc = check_state(s);
+    if (rc) return rc;
+    if (!out) return GTQA_ERR_INVALID_ARG;
+    if (s->plain) return GTQA_ERR_UNSUPPORTED;
+    for (int pk = 0; pk < PK_COUNT; ++pk) {
+        out[4 * pk + 0] = s->grid[pk];
+        out[4 * pk + 1] = s->shape[pk];
+        out[4 * pk + 2] = s->tpb[pk];
+        out[4 * pk + 3] = s->team[pk];
+    }
+    return GTQA_OK;
 }
 
 int gtqa_autotune(gtqa_state* s, double tau, double dt, double tol, int32_t max_iter, int32_t* grid_out) {
@@ -1284,8 +1341,9 @@ int gtqa_autotune(gtqa_state* s, double tau, double dt, double tol, int32_t max_
     if (rc) return rc;
     if (!std::isfinite(tau) || !std::isfinite(dt) || !(tol >= 0.0) || max_iter < 1) return GTQA_ERR_INVALID_ARG;
     if (s->plain) return GTQA_ERR_UNSUPPORTED;
-    // snapshot of everything a layer writes, restored before every timed launch and at the end
-    struct Buf { void* p; size_t bytes; std::vector<unsigned char> h; };
+    // snapshot of everything a layer writes, restored before every timed launch and at the end:
+    // in one device buffer when it fits in free device memory, else in host memory
+    struct Buf { void* p; size_t bytes; std::vector<unsigned char> h; size_t off; };
     const size_t gel = gamma_elems(s), mel = msg_elems(s), eb = elem_bytes(s);
     std::vector<Buf> bufs = {{s->Gamma, gel * eb, {}}, {s->T, gel * eb, {}}, {s->lam, sizeof(double) * s->m * s->CHI, {}},
                              {s->msg[0], mel * eb, {}}, {s->msg[1], mel * eb, {}},
@@ -1294,17 +1352,41 @@ int gtqa_autotune(gtqa_state* s, double tau, double dt, double tol, int32_t max_
                              {s->stats, sizeof(double) * kStats, {}}, {s->ctl, sizeof(Control), {}},
                              {s->acc, sizeof(double) * 6 * s->B, {}}, {s->inst_done, sizeof(int) * s->B, {}},
                              {s->inst_iters, sizeof(int) * s->B, {}}, {s->inst_dist, sizeof(double) * s->B, {}}};
+    size_t total = 0;
     for (auto& b : bufs) {
-        b.h.resize(b.bytes);
-        if (b.bytes && !cuda_ok(s, cudaMemcpyAsync(b.h.data(), b.p, b.bytes, cudaMemcpyDeviceToHost, s->stream)))
-            return GTQA_ERR_CUDA;
+        b.off = total;
+        total += (b.bytes + 255) / 256 * 256;
+    }
+    struct DevSnap {
+        unsigned char* p = nullptr;
+        ~DevSnap() { if (p) cudaFree(p); }
+    } dev;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && total + (256u << 20) < free_b &&
+        cudaMalloc((void**)&dev.p, total) != cudaSuccess) {
+        dev.p = nullptr;
+    }
+    cudaGetLastError();
+    for (auto& b : bufs) {
+        if (!b.bytes) continue;
+        cudaError_t e;
+        if (dev.p) {
+            e = cudaMemcpyAsync(dev.p + b.off, b.p, b.bytes, cudaMemcpyDeviceToDevice, s->stream);
+        } else {
+            b.h.resize(b.bytes);
+            e = cudaMemcpyAsync(b.h.data(), b.p, b.bytes, cudaMemcpyDeviceToHost, s->stream);
+        }
+        if (!cuda_ok(s, e)) return GTQA_ERR_CUDA;
     }
     if (!cuda_ok(s, cudaStreamSynchronize(s->stream))) return GTQA_ERR_CUDA;
     // the restored control block holds barrier counts of the snapshot's grid sizes: zero them
     auto restore = [&]() {
-        for (auto& b : bufs)
-            if (b.bytes && !cuda_ok(s, cudaMemcpyAsync(b.p, b.h.data(), b.bytes, cudaMemcpyHostToDevice, s->stream)))
-                return false;
+        for (auto& b : bufs) {
+            if (!b.bytes) continue;
+            const cudaError_t e = dev.p ? cudaMemcpyAsync(b.p, dev.p + b.off, b.bytes, cudaMemcpyDeviceToDevice, s->stream)
+                                        : cudaMemcpyAsync(b.p, b.h.data(), b.bytes, cudaMemcpyHostToDevice, s->stream);
+            if (!cuda_ok(s, e)) return false;
+        }
         return zero_barriers(s) == GTQA_OK;
     };
     const long long layers = s->layers, gates = s->gates, launches = s->launches;
@@ -1317,56 +1399,72 @@ int gtqa_autotune(gtqa_state* s, double tau, double dt, double tol, int32_t max_
     c.tX1 = dt * (1.0 - tau);
     c.tol = tol;
     c.max_iter = max_iter;
-    // work units per phase kernel and teams per block: candidates are all SMs, fewer blocks in
-    // steps of 1/8, and the fewest blocks that still cover the work in one round
+    // per phase kernel, every launch-shape variant that fits; per variant, the grid candidates
+    // are all SMs and, when the work fits in one round of that variant's teams, fewer blocks in
+    // steps of 1/8 and the fewest blocks that still cover the work in one round
+    if (!drop_graph(s)) return GTQA_ERR_CUDA;
     const int full = s->nblocks;
     const long long units[PK_COUNT] = {s->m, s->n, s->m};
-    const int tpb_teams[PK_COUNT] = {teams_per_block(PK_GATES, s->CHI), teams_per_block(PK_BP, s->CHI),
-                                     teams_per_block(PK_REGAUGE, s->CHI)};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!cuda_ok(s, cudaEventCreate(&e0)) || !cuda_ok(s, cudaEventCreate(&e1))) return GTQA_ERR_CUDA;
-    int best[PK_COUNT];
+    // median of three timed launches of kernel pk with the state's current grid and shape
+    auto time_kernel = [&](int pk, float* med) {
+        std::vector<float> ts;
+        for (int rep = 0; rep < 3; ++rep) {
+            if (!restore()) return GTQA_ERR_CUDA;
+            // the phases before the timed one, untimed, so that it sees its real inputs
+            Ctx ci = c;
+            int r;
+            ci.phases = PH_GATES;
+            if (pk >= PK_BP && (r = run(s, ci, PK_GATES, GTQA_K_TROTTER, s->m))) return r;
+            ci.phases = PH_BP | PH_WARM;
+            if (pk >= PK_REGAUGE && (r = run(s, ci, PK_BP, GTQA_K_BP, s->n))) return r;
+            ci.phases = pk == PK_GATES ? PH_GATES : (pk == PK_BP ? (PH_BP | PH_WARM) : PH_REGAUGE);
+            cudaEventRecord(e0, s->stream);
+            if ((r = run(s, ci, pk, pk, units[pk]))) return r;
+            cudaEventRecord(e1, s->stream);
+            float ms = 0.f;
+            if (!cuda_ok(s, cudaEventSynchronize(e1)) || !cuda_ok(s, cudaEventElapsedTime(&ms, e0, e1)))
+                return GTQA_ERR_CUDA;
+            ts.push_back(ms);
+        }
+        std::sort(ts.begin(), ts.end());
+        *med = ts[1];
+        return GTQA_OK;
+    };
     rc = GTQA_OK;
     for (int pk = 0; pk < PK_COUNT && rc == GTQA_OK; ++pk) {
-        std::vector<int> cand;
-        for (int q = 8; q >= 4; --q) cand.push_back(std::max(1, full * q / 8));
-        const long long one_round = (units[pk] + tpb_teams[pk] - 1) / std::max(1, tpb_teams[pk]);
-        if (one_round >= 1 && one_round < full) cand.push_back((int)one_round);
-        std::sort(cand.begin(), cand.end());
-        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-        double tbest = 1e300;
-        best[pk] = s->grid[pk];
-        const int keep = s->grid[pk];
-        for (int g : cand) {
-            s->grid[pk] = g;
-            std::vector<float> ts;
-            for (int rep = 0; rep < 3 && rc == GTQA_OK; ++rep) {
-                if (!restore()) { rc = GTQA_ERR_CUDA; break; }
-                // the phases before the timed one, untimed, so that it sees its real inputs
-                Ctx ci = c;
-                ci.phases = PH_GATES;
-                if (pk >= PK_BP && (rc = run(s, ci, PK_GATES, GTQA_K_TROTTER, s->m))) break;
-                ci.phases = PH_BP | PH_WARM;
-                if (pk >= PK_REGAUGE && (rc = run(s, ci, PK_BP, GTQA_K_BP, s->n))) break;
-                ci.phases = pk == PK_GATES ? PH_GATES : (pk == PK_BP ? (PH_BP | PH_WARM) : PH_REGAUGE);
-                cudaEventRecord(e0, s->stream);
-                if ((rc = run(s, ci, pk, pk, units[pk]))) break;
-                cudaEventRecord(e1, s->stream);
-                float ms = 0.f;
-                if (!cuda_ok(s, cudaEventSynchronize(e1)) || !cuda_ok(s, cudaEventElapsedTime(&ms, e0, e1))) {
-                    rc = GTQA_ERR_CUDA;
-                    break;
-                }
-                ts.push_back(ms);
+        float tbest = 3.0e38f;
+        int best_g = s->grid[pk], best_v = s->shape[pk];
+        const int keep_g = s->grid[pk], keep_v = s->shape[pk];
+        for (int v = 0; v < shape_count(pk) && rc == GTQA_OK; ++v) {
+            const int arc = apply_shape(s, pk, v);
+            if (arc == GTQA_ERR_UNSUPPORTED) continue;   // does not fit on an SM
+            if ((rc = arc) != GTQA_OK) break;
+            const int tpb_teams = teams_per_block(s, pk);
+            // fewer blocks than SMs only pay when the work fits in one round of teams
+            std::vector<int> cand = {full};
+            const long long one_round = (units[pk] + tpb_teams - 1) / std::max(1, tpb_teams);
+            if (one_round < full) {
+                for (int q = 7; q >= 4; --q) cand.push_back(std::max(1, full * q / 8));
+                if (one_round >= 1) cand.push_back((int)one_round);
             }
-            if (rc != GTQA_OK) break;
-            std::sort(ts.begin(), ts.end());
-            if (ts[ts.size() / 2] < tbest) {
-                tbest = ts[ts.size() / 2];
-                best[pk] = g;
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            for (int g : cand) {
+                s->grid[pk] = g;
+                float med = 0.f;
+                if ((rc = time_kernel(pk, &med)) != GTQA_OK) break;
+                if (med < tbest) {
+                    tbest = med;
+                    best_g = g;
+                    best_v = v;
+                }
             }
         }
-        s->grid[pk] = rc == GTQA_OK ? best[pk] : keep;
+        const int arc = apply_shape(s, pk, rc == GTQA_OK ? best_v : keep_v);
+        if (rc == GTQA_OK) rc = arc;
+        s->grid[pk] = rc == GTQA_OK ? best_g : keep_g;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -14,6 +14,10 @@ namespace gtqa {
 
 enum PhaseKernel { PK_GATES = 0, PK_BP = 1, PK_REGAUGE = 2, PK_COUNT = 3 };
 
+// Launch-shape variants that differ for a phase kernel: the gates kernel depends on the block
+// size only, which its third variant would repeat.
+constexpr int shape_count(int pk) { return pk == PK_GATES ? 2 : NSHAPE; }
+
 // Shared memory the BP kernel keeps per instance after its fixed part: three int flags
 // (padded to 8 bytes), two FP64 thresholds and one float threshold.
 inline size_t bp_instance_smem(long long B) { return (12 * (size_t)B + 7) / 8 * 8 + 20 * (size_t)B; }
@@ -22,11 +26,13 @@ inline size_t bp_instance_smem(long long B) { return (12 * (size_t)B + 7) / 8 * 
 // (gtqa_units.cuh) are compiled only in gtqa_units.cu, which the build compiles once per
 // (mode, phase) with an explicit instantiation, so the instantiation sets build in
 // parallel; every other unit links against them.
+// Every call takes the launch-shape variant v (0 .. shape_count(PK) - 1) besides CHI; shape
+// also returns the kernel's team size (gate edge, BP vertex or regauge vertex team).
 template <class Mode, int PK>
 struct PhaseUnit {
-    static bool shape(int CHI, size_t* smem_base, int* tpb);
-    static cudaError_t prepare(int CHI, size_t smem, int* blocks_per_sm);
-    static cudaError_t launch(int CHI, const Ctx& c, size_t smem, cudaStream_t st);
+    static bool shape(int CHI, int v, size_t* smem_base, int* tpb, int* team);
+    static cudaError_t prepare(int CHI, int v, size_t smem, int* blocks_per_sm);
+    static cudaError_t launch(int CHI, int v, const Ctx& c, size_t smem, cudaStream_t st);
 };
 
 // Marginals, residual and measurement-sampling kernels of one mode (instantiated in the

@@ -45,9 +45,9 @@ int setup(void** addr, size_t* smem) {
     }
     size_t base = 0;
     int tpb = 0, bps = 0;
-    if (!PhaseUnit<ModeFP64, PK_BP>::shape(kChi, &base, &tpb)) return GTQA_ERR_UNSUPPORTED;
+    if (!PhaseUnit<ModeFP64, PK_BP>::shape(kChi, 0, &base, &tpb, nullptr)) return GTQA_ERR_UNSUPPORTED;
     const size_t sm = (base + bp_instance_smem(1) + 15) / 16 * 16;
-    if (PhaseUnit<ModeFP64, PK_BP>::prepare(kChi, sm, &bps) != cudaSuccess || bps < 1) {
+    if (PhaseUnit<ModeFP64, PK_BP>::prepare(kChi, 0, sm, &bps) != cudaSuccess || bps < 1) {
         cudaGetLastError();
         return GTQA_ERR_CUDA;
     }
@@ -170,7 +170,7 @@ extern "C" int gtqa_bp_static(int32_t n, int32_t m, const int32_t* vert_edges, c
     c.nblocks = sms;
     c.bar_expect = sms;
     c.spin_limit = 1LL << 22;
-    if (PhaseUnit<ModeFP64, PK_BP>::launch(kChi, c, smem, st) != cudaSuccess) {
+    if (PhaseUnit<ModeFP64, PK_BP>::launch(kChi, 0, c, smem, st) != cudaSuccess) {
         cudaGetLastError();
         return GTQA_ERR_CUDA;
     }

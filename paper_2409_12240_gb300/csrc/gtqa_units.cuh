@@ -21,43 +21,68 @@ R by_chi(int CHI, R bad, F&& f) {
     }
 }
 
+// Calls f with the launch-shape variant of phase kernel PK as a compile-time constant.
+template <int PK, class R, class F>
+R by_shape(int v, R bad, F&& f) {
+    switch (v) {
+        case 0: return f(std::integral_constant<int, 0>{});
+        case 1: return f(std::integral_constant<int, 1>{});
+        case 2:
+            if constexpr (shape_count(PK) > 2) return f(std::integral_constant<int, 2>{});
+            else return bad;
+        default: return bad;
+    }
+}
+
 constexpr unsigned phase_bits(int PK) { return PK == PK_GATES ? PH_GATES : (PK == PK_BP ? PH_BP : PH_REGAUGE); }
 
-template <int CHI, class Mode, int PK>
+template <int CHI, class Mode, int PK, int V>
 constexpr auto phase_kernel() {
-    if constexpr (PK == PK_GATES) return gates_kernel<CHI, Mode>;
-    else if constexpr (PK == PK_BP) return bp_kernel<CHI, Mode>;
-    else return regauge_kernel<CHI, Mode>;
+    if constexpr (PK == PK_GATES) return gates_kernel<CHI, Mode, V>;
+    else if constexpr (PK == PK_BP) return bp_kernel<CHI, Mode, V>;
+    else return regauge_kernel<CHI, Mode, V>;
 }
 
 template <class Mode, int PK>
-bool PhaseUnit<Mode, PK>::shape(int CHI, size_t* smem_base, int* tpb) {
+bool PhaseUnit<Mode, PK>::shape(int CHI, int v, size_t* smem_base, int* tpb, int* team) {
     return by_chi(CHI, false, [&](auto k) {
         constexpr int X = decltype(k)::value;
-        *smem_base = SmemSize<X, Mode, phase_bits(PK)>::value;
-        *tpb = Shape<X>::TPB;
-        return true;
+        return by_shape<PK>(v, false, [&](auto w) {
+            constexpr int V = decltype(w)::value;
+            using S = Shape<X, V>;
+            *smem_base = SmemSize<X, Mode, phase_bits(PK), V>::value;
+            *tpb = S::TPB;
+            if (team) *team = PK == PK_GATES ? S::TG : (PK == PK_BP ? S::TB : S::TRV);
+            return true;
+        });
     });
 }
 
 template <class Mode, int PK>
-cudaError_t PhaseUnit<Mode, PK>::prepare(int CHI, size_t smem, int* bps) {
+cudaError_t PhaseUnit<Mode, PK>::prepare(int CHI, int v, size_t smem, int* bps) {
     return by_chi(CHI, cudaErrorInvalidValue, [&](auto k) {
         constexpr int X = decltype(k)::value;
-        const cudaError_t e = raise_smem_limit(phase_kernel<X, Mode, PK>(), smem);
-        if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, phase_kernel<X, Mode, PK>(), Shape<X>::TPB, smem);
+        return by_shape<PK>(v, cudaErrorInvalidValue, [&](auto w) {
+            constexpr int V = decltype(w)::value;
+            const cudaError_t e = raise_smem_limit(phase_kernel<X, Mode, PK, V>(), smem);
+            if (e != cudaSuccess) return e;
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, phase_kernel<X, Mode, PK, V>(),
+                                                                 Shape<X, V>::TPB, smem);
+        });
     });
 }
 
 template <class Mode, int PK>
-cudaError_t PhaseUnit<Mode, PK>::launch(int CHI, const Ctx& c, size_t smem, cudaStream_t st) {
+cudaError_t PhaseUnit<Mode, PK>::launch(int CHI, int v, const Ctx& c, size_t smem, cudaStream_t st) {
     return by_chi(CHI, cudaErrorInvalidValue, [&](auto k) {
         constexpr int X = decltype(k)::value;
-        Ctx copy = c;
-        void* args[] = {&copy};
-        return cudaLaunchCooperativeKernel((const void*)phase_kernel<X, Mode, PK>(), dim3(c.nblocks),
-                                           dim3(Shape<X>::TPB), args, smem, st);
+        return by_shape<PK>(v, cudaErrorInvalidValue, [&](auto w) {
+            constexpr int V = decltype(w)::value;
+            Ctx copy = c;
+            void* args[] = {&copy};
+            return cudaLaunchCooperativeKernel((const void*)phase_kernel<X, Mode, PK, V>(), dim3(c.nblocks),
+                                               dim3(Shape<X, V>::TPB), args, smem, st);
+        });
     });
 }
 

@@ -43,7 +43,7 @@ EXPORTED = [
     "gtqa_barrier_bench", "gtqa_residual", "gtqa_entropy", "gtqa_spectral_bipartition", "gtqa_sample",
     "gtqa_trotter_split", "gtqa_anneal_ex", "gtqa_apply_gates", "gtqa_apply_single_qubit_gates",
     "gtqa_max_degree", "gtqa_anneal_graph", "gtqa_autotune", "gtqa_set_grid", "gtqa_gate_layers",
-    "gtqa_anneal_policy", "gtqa_regauge_counts",
+    "gtqa_anneal_policy", "gtqa_regauge_counts", "gtqa_set_shape", "gtqa_launch_shape",
 ]
 KERNEL_KINDS = ["gates_kernel", "bp_kernel", "regauge_kernel", "marginals_kernel"]
 
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         "gtqa_regauge_counts": (I32, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "gtqa_autotune": (I32, [P, D, D, D, I32, P]),
         "gtqa_set_grid": (I32, [P, P]),
+        "gtqa_set_shape": (I32, [P, P]),
+        "gtqa_launch_shape": (I32, [P, P]),
         "gtqa_gate_layers": (I32, [I32, I32, P, I32, P, P, ctypes.POINTER(I32)]),
         "gtqa_trotter_split": (I32, [P, D, D, D]),
         "gtqa_anneal_ex": (I32, [P, I32, I32, I32, D, D, I32, I32, P]),
@@ -276,8 +278,8 @@ def gtqa_anneal_graph(s: int, k_begin: int, k_end: int, K: int, dt: float, tol: 
 
 
 def gtqa_autotune(s: int, tau: float, dt: float, tol: float, max_iter: int) -> Tuple[int, int, int]:
-    """Time each phase kernel's candidate grid sizes on the current state; keep and return the
-    fastest (gates, BP, regauge)."""
+    """Time each phase kernel's launch-shape variants and candidate grid sizes on the current
+    state; keep the fastest and return the grid sizes (gates, BP, regauge)."""
     g = np.zeros(3, dtype=np.int32)
     _check(load().gtqa_autotune(s, float(tau), float(dt), float(tol), int(max_iter), g.ctypes.data), "gtqa_autotune")
     return int(g[0]), int(g[1]), int(g[2])
@@ -286,6 +288,22 @@ def gtqa_autotune(s: int, tau: float, dt: float, tol: float, max_iter: int) -> T
 def gtqa_set_grid(s: int, grid) -> None:
     g = np.ascontiguousarray(np.asarray(grid, dtype=np.int32))
     _check(load().gtqa_set_grid(s, g.ctypes.data), "gtqa_set_grid")
+
+
+def gtqa_set_shape(s: int, variant) -> None:
+    """Launch-shape variant per phase kernel (gates 0-1, BP 0-2, regauge 0-2)."""
+    v = np.ascontiguousarray(np.asarray(variant, dtype=np.int32))
+    if v.shape != (3,):
+        raise ValueError("gtqa_set_shape: three variants (gates, BP, regauge)")
+    _check(load().gtqa_set_shape(s, v.ctypes.data), "gtqa_set_shape")
+
+
+def gtqa_launch_shape(s: int) -> dict:
+    """The launch table: per kernel its grid, variant, threads per block and team size."""
+    out = np.zeros(12, dtype=np.int32)
+    _check(load().gtqa_launch_shape(s, out.ctypes.data), "gtqa_launch_shape")
+    return {k: {"grid": int(out[4 * q]), "variant": int(out[4 * q + 1]), "threads_per_block": int(out[4 * q + 2]),
+                "team": int(out[4 * q + 3])} for q, k in enumerate(KERNEL_KINDS[:3])}
 
 
 def gtqa_gate_layers(n: int, edges, edge) -> Tuple[np.ndarray, int]:

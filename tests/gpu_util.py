@@ -36,13 +36,17 @@ def message_spectra(M):
     return np.linalg.eigvalsh(Mh)
 
 
-def run_pair(inst, chi, K, dt, tol, max_iter, layers, precision=0, check_every=1):
-    """Run `layers` annealing layers on both sides; returns per-layer diffs."""
+def run_pair(inst, chi, K, dt, tol, max_iter, layers, precision=0, check_every=1, shape=None):
+    """Run `layers` annealing layers on both sides; returns per-layer diffs.  `shape` (three
+    variant indices) selects the launch shapes of the GPU side's phase kernels."""
     G = lib()
     opt = G.gtqa_options_init(precision=precision)
     s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour, opt)
     out = {"rho": [], "lam": [], "msg_abs": [], "msg_spec": [], "iters": [], "gamma": []}
     try:
+        if shape is not None:
+            G.gtqa_set_shape(s, shape)
+            out["launch"] = G.gtqa_launch_shape(s)
         n, m, C, _ = G.gtqa_sizes(s)
         st = O.plus_state(inst.n, inst.edges)
         for k in range(1, layers + 1):

@@ -163,8 +163,8 @@ def test_profiled_graph_replays_time_each_phase_and_keep_results():
 
 def test_autotune_restores_the_state_and_keeps_results():
     """gtqa_autotune leaves the state and statistics as they were, keeps grid sizes within the SM
-    count, and the layers it then runs give the results of the default grid (FP64, bitwise on
-    lambda and marginals)."""
+    count, and the layers it then runs give the results of the default launch shapes (FP64; a
+    different BP vertex team changes only the rounding order of its sums)."""
     import numpy as np
     from instances import make_instance
     G = U.lib()
@@ -190,4 +190,4 @@ def test_autotune_restores_the_state_and_keeps_results():
             res.append((G.gtqa_get_state(s)[1], G.gtqa_marginals(s)[0]))
         finally:
             G.gtqa_destroy(s)
-    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert np.abs(res[0][0] - res[1][0]).max() < 1e-12 and np.abs(res[0][1] - res[1][1]).max() < 1e-12
