@@ -786,7 +786,9 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
         }
     }
     team_bar<TEAM>(team);
-    // traces of the outgoing messages
+    // traces of the outgoing messages; in the mixed mode also their reciprocals, in FP32 by
+    // the same lane (the message correction is rounded to FP32, so a reciprocal with FP32
+    // relative error adds noise of the size of that rounding)
     if (tid < 3 * CC && tid % CC == 0) {
         const int k = tid / CC;
         CT trs = z;
@@ -795,24 +797,29 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
             trs = trs + (SM::FSPLIT ? sm.Fh[0][k][j * CHI + j] + sm.Fh[1][k][j * CHI + j]
                                                   : sm.Fh[0][k][j * CHI + j]);
         sm.trs[k] = trs;
+        if constexpr (Mode::mixed) {
+            const float tx = (float)sm.t0[k].x + trs.x, ty = (float)sm.t0[k].y + trs.y;
+            const float n2 = fmaf(tx, tx, ty * ty);
+            const float in2 = n2 > 0.f ? __frcp_rn(n2) : 0.f;
+            sm.itr[k] = CT{tx * in2, -ty * in2};
+        }
     }
 }
 
 // Reciprocals of the complex traces of every team's outgoing messages in FP64 (reading
 // R10: messages are divided by their complex trace), one lane per message, by the first
 // warp of the block: FP64 instructions cost the same for 1 or 32 active lanes, so one
-// warp does this for all teams.  Mixed: the trace is t0 + tr Fd.
+// warp does this for all teams.  FP64 mode only (the mixed mode forms them in bp_front).
 template <int CHI, class Mode, int TB>
 __device__ void bp_trace_rcp(BPSm<CHI, Mode, TB>* all, int nteams) {
     using TS = typename Mode::TS;
     for (int l = threadIdx.x; l < 3 * nteams; l += 32) {
         BPSm<CHI, Mode, TB>& sm = all[l / 3];
         const int k = l % 3;
-        cd tr = ccast<double>(sm.trs[k]);
-        if constexpr (Mode::mixed) tr = tr + sm.t0[k];
+        static_assert(!Mode::mixed, "FP64 trace reciprocals");
+        const cd tr = ccast<double>(sm.trs[k]);
         const double n2 = norm2(tr);
-        // the mixed mode rounds the result to FP32, so one Newton step (relative error ~2^-44) suffices
-        const double in2 = n2 > 0.0 ? (Mode::mixed ? nr_rcp1(n2) : nr_rcp(n2)) : 0.0;
+        const double in2 = n2 > 0.0 ? nr_rcp(n2) : 0.0;
         sm.itr[k] = ccast<TS>(cd{tr.x * in2, -tr.y * in2});
     }
 }
@@ -1324,9 +1331,13 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                         else act = true;
                     }
                     if (act) bp_front<CHI, Mode, S::TB>(c, a, tid, team, cur, sm, base == 0 && have_pre, pre);
-                    __syncthreads();
-                    if (threadIdx.x < 32) bp_trace_rcp<CHI, Mode, S::TB>(all, tpb_teams);
-                    __syncthreads();
+                    if constexpr (Mode::mixed) {
+                        team_bar<S::TB>(team);   // the team's own trace reciprocals (bp_front)
+                    } else {
+                        __syncthreads();
+                        if (threadIdx.x < 32) bp_trace_rcp<CHI, Mode, S::TB>(all, tpb_teams);
+                        __syncthreads();
+                    }
                     if (act) bp_back<CHI, Mode, S::TB>(c, tid, team, cur, exnow[inst] != 0, sm, c.B == 1 ? nullptr : acc + inst);
                     else if (tid < 3) sm.dl[tid] = 0;
                     if (c.B == 1) {
