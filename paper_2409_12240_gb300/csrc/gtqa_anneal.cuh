@@ -578,10 +578,16 @@ template <int CHI, class Mode, int TB>
 struct BPSm {
     using TS = typename Mode::TS;
     static constexpr int H2 = 2 * CHI * CHI * CHI, CC = CHI * CHI, NP = Mode::mixed ? 3 : 2;
-    // F in two halves over the physical index (summed at use) unless the team is NPART lanes
-    // per (j, j') that split the (i, u) sum and meet by shuffles
-    static constexpr int NPART = TB / CC;
-    static constexpr bool FSPLIT = !(TB % CC == 0 && NPART <= 32 && (2 * CHI) % NPART == 0);
+    // lanes that share one 2 x 2 block of an outgoing message, each summing a slice of the
+    // 2 CHI^2 columns: the largest power of two (at most 32 and 2 CHI^2) that keeps all
+    // 3 (CHI/2)^2 blocks of the three slots within the team
+    static constexpr int fslices() {
+        int ns = 1;
+        while (2 * ns <= 32 && 2 * ns <= 2 * CC && 3 * (CHI / 2) * (CHI / 2) * 2 * ns <= TB) ns *= 2;
+        return ns;
+    }
+    static constexpr int NS = fslices();
+    static_assert(CHI % 2 == 0 && 3 * (CHI / 2) * (CHI / 2) * NS <= TB, "BP team too small for the overlap stage");
     // T, P and Q in the natural index order [i][j0][j1][j2] with one padding element after
     // every (i, j0) plane, so that a stride along slot 0 does not map to one bank
     static constexpr int PS = CC + 1, H2P = 2 * CHI * PS;
@@ -590,7 +596,7 @@ struct BPSm {
     C<TS> Q[3][H2P];     // per outgoing slot
     C<TS> min[3][CC];    // incoming messages (mixed: m0 + delta)
     C<TS> din[3][CC];    // mixed: incoming delta
-    C<TS> Fh[2][3][CC];  // the two physical-index halves of the outgoing messages
+    C<TS> F[3][CC];      // the outgoing messages before normalisation
     C<TS> prev[3][CC];   // outgoing messages of the previous sweep
     C<TS> D[3][CC];      // new - old, for the trace norm
     cf D0f[3][CC];       // mixed: warm-start defect
@@ -739,50 +745,48 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
         }
     }
     team_bar<TEAM>(team);
-    // overlaps with conj(T): F_s[j][j'] = sum over (i, u@o0, v@o1) of Q_s[.., j@s] conj(T[.., j'@s])
-    if constexpr (SM::FSPLIT) {
-        // one half of the sum per physical index i, added at use
-        for (int t = tid; t < 2 * 3 * CC; t += TEAM) {
-            const int i = t / (3 * CC), rem = t % (3 * CC);
-            const int s = rem / CC, r = rem % CC;
-            if (sm.es[s] < 0) continue;
-            const int j = r / CHI, jp = r % CHI;
-            const int ss = slot_stride(s);
-            const int so = s == 0 ? S1 : S0, st2 = s == 2 ? S1 : 1;   // strides of the two other slots
-            CT acc = z;
+    // overlaps with conj(T): F_s[j][j'] = sum over the 2 CHI^2 columns (i, u@o0, v@o1) of
+    // Q_s[.., j@s, ..] conj(T[.., j'@s, ..]).  A lane holds a 2 x 2 block of (j, j') over a
+    // slice of the columns, so that every element it loads feeds two products; the NS lanes
+    // of a block then sum by shuffles.
+    {
+        constexpr int NBJ = CHI / 2, NB = NBJ * NBJ, K = 2 * CC, NS = SM::NS, CPL = K / NS;
+        if (tid < 3 * NB * NS) {
+            const int s = tid / (NB * NS), rem = tid % (NB * NS);
+            const int b = rem / NS, slice = rem % NS;
+            const int j0 = 2 * (b / NBJ), jp0 = 2 * (b % NBJ);
+            if (sm.es[s] >= 0) {   // the same for the NS lanes of a block
+                const int ss = slot_stride(s);
+                const int so = s == 0 ? S1 : S0, st2 = s == 2 ? S1 : 1;   // strides of the two other slots
+                const CT* Qs = sm.Q[s];
+                CT a00 = z, a01 = z, a10 = z, a11 = z;
 #pragma unroll
-            for (int u = 0; u < CHI; ++u)
-#pragma unroll
-                for (int v = 0; v < CHI; ++v) {
-                    const int off = i * HP + u * so + v * st2;
-                    acc = cfmac(sm.T[off + jp * ss], sm.Q[s][off + j * ss], acc);
+                for (int w = 0; w < CPL; ++w) {
+                    const int cl = slice * CPL + w;
+                    const int off = (cl / CC) * HP + ((cl / CHI) % CHI) * so + (cl % CHI) * st2;
+                    const CT q0 = Qs[off + j0 * ss], q1 = Qs[off + (j0 + 1) * ss];
+                    const CT t0 = sm.T[off + jp0 * ss], t1 = sm.T[off + (jp0 + 1) * ss];
+                    a00 = cfmac(t0, q0, a00);
+                    a01 = cfmac(t1, q0, a01);
+                    a10 = cfmac(t0, q1, a10);
+                    a11 = cfmac(t1, q1, a11);
                 }
-            sm.Fh[i][s][r] = acc;
-        }
-    } else {
-        // lane = (j, j') * NPART + part; each part sums 2 CHI / NPART of the (i, u) pairs,
-        // then a shuffle sum over the NPART adjacent lanes
-        constexpr int NPART = SM::NPART, PER = 2 * CHI / NPART;
-        const int r = tid / NPART, part = tid % NPART;
-        const int j = r / CHI, jp = r % CHI;
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            if (sm.es[s] < 0) continue;
-            const int ss = slot_stride(s);
-            const int so = s == 0 ? S1 : S0, st2 = s == 2 ? S1 : 1;
-            CT acc = z;
-#pragma unroll
-            for (int h = 0; h < PER; ++h) {
-                const int cmb = part * PER + h, i = cmb / CHI, u = cmb % CHI;
-#pragma unroll
-                for (int v = 0; v < CHI; ++v) {
-                    const int off = i * HP + u * so + v * st2;
-                    acc = cfmac(sm.T[off + jp * ss], sm.Q[s][off + j * ss], acc);
+                const unsigned gm = group_mask<NS>();
+                a00.x = group_sum<NS>(a00.x, gm);
+                a00.y = group_sum<NS>(a00.y, gm);
+                a01.x = group_sum<NS>(a01.x, gm);
+                a01.y = group_sum<NS>(a01.y, gm);
+                a10.x = group_sum<NS>(a10.x, gm);
+                a10.y = group_sum<NS>(a10.y, gm);
+                a11.x = group_sum<NS>(a11.x, gm);
+                a11.y = group_sum<NS>(a11.y, gm);
+                if (slice == 0) {
+                    sm.F[s][j0 * CHI + jp0] = a00;
+                    sm.F[s][j0 * CHI + jp0 + 1] = a01;
+                    sm.F[s][(j0 + 1) * CHI + jp0] = a10;
+                    sm.F[s][(j0 + 1) * CHI + jp0 + 1] = a11;
                 }
             }
-            acc.x = group_sum<NPART>(acc.x, group_mask<NPART>());
-            acc.y = group_sum<NPART>(acc.y, group_mask<NPART>());
-            if (part == 0) sm.Fh[0][s][r] = acc;
         }
     }
     team_bar<TEAM>(team);
@@ -793,9 +797,7 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
         const int k = tid / CC;
         CT trs = z;
 #pragma unroll
-        for (int j = 0; j < CHI; ++j)
-            trs = trs + (SM::FSPLIT ? sm.Fh[0][k][j * CHI + j] + sm.Fh[1][k][j * CHI + j]
-                                                  : sm.Fh[0][k][j * CHI + j]);
+        for (int j = 0; j < CHI; ++j) trs = trs + sm.F[k][j * CHI + j];
         sm.trs[k] = trs;
         if constexpr (Mode::mixed) {
             const float tx = (float)sm.t0[k].x + trs.x, ty = (float)sm.t0[k].y + trs.y;
@@ -844,7 +846,7 @@ __device__ void bp_back(const Ctx& c, int tid, int team, int cur, bool exact, BP
         CT d = z;
         if (out >= 0) {
             const CT itr = sm.itr[k];
-            const CT f = BPSm<CHI, Mode, TB>::FSPLIT ? sm.Fh[0][k][r] + sm.Fh[1][k][r] : sm.Fh[0][k][r];
+            const CT f = sm.F[k][r];
             CT num = f;
             if constexpr (Mode::mixed) {
                 const int j = r / CHI, jp = r % CHI;
