@@ -486,7 +486,8 @@ __device__ void bp_init_vertex(const Ctx& c, int a, int tid, int cur, bool warm,
     constexpr int H = CHI * CHI * CHI, CC = CHI * CHI, TEAM = Shape<CHI>::TV;
     const int4 ve = c.vert_edges[a];
     const int es[3] = {ve.x, ve.y, ve.z};
-    // wsm[0 .. 3CHI): lambda^{1/2} per slot; wsm[3CHI .. 6CHI): m0 diagonal per slot
+    // wsm[0 .. 3CHI): lambda^{1/2} per slot; wsm[3CHI .. 6CHI): m0 diagonal per slot;
+    // wsm[6CHI .. 6CHI + 3): (sum lambda)^{-1/2} per slot
     if (tid < 3 * CHI) {
         const int k = tid / CHI, j = tid % CHI;
         const double lj = lam_get(c.lam, CHI, es[k], j);
@@ -494,17 +495,21 @@ __device__ void bp_init_vertex(const Ctx& c, int a, int tid, int cur, bool warm,
         double s = 0.0;
         for (int q = 0; q < CHI; ++q) s += lam_get(c.lam, CHI, es[k], q);
         wsm[3 * CHI + tid] = s > 0.0 ? lj * nr_rcp(s) : 0.0;
+        if (j == 0) wsm[6 * CHI + k] = s > 0.0 ? nr_rsqrt(s) : 0.0;
     }
     __syncwarp();
     const C<TS>* g = (const C<TS>*)c.Gamma + (size_t)a * 2 * H;
     C<TS>* T = (C<TS>*)c.T + (size_t)a * 2 * H;
+    // mixed: tsm holds T~ = T prod_k m0_k[j_k]^{1/2} (T as stored, in FP64), so that the warm
+    // start's contraction below needs no weights in its inner loop
+    const double iso = Mode::mixed ? wsm[6 * CHI] * wsm[6 * CHI + 1] * wsm[6 * CHI + 2] : 0.0;
     for (int t = tid; t < 2 * H; t += TEAM) {
         const int r = t % H;
         const int j0 = r / CC, j1 = (r / CHI) % CHI, j2 = r % CHI;
         const double f = wsm[j0] * wsm[CHI + j1] * wsm[2 * CHI + j2];
         const C<TS> tv = ccast<TS>(f * ccast<double>(ldcg(g + t)));
         T[t] = tv;
-        if constexpr (Mode::mixed) tsm[t] = ccast<double>(tv);
+        if constexpr (Mode::mixed) tsm[t] = (f * iso) * ccast<double>(tv);
     }
     int out[3];
     for (int s = 0; s < 3; ++s) out[s] = es[s] >= 0 ? 2 * es[s] + (a == c.edge_info[es[s]].x ? 0 : 1) : -1;
@@ -519,7 +524,10 @@ __device__ void bp_init_vertex(const Ctx& c, int a, int tid, int cur, bool warm,
     }
     if constexpr (Mode::mixed) {
         __syncwarp();
-        // upper triangle (j <= j') of F0 for the 3 outgoing slots, items spread over the warp
+        // upper triangle (j <= j') of F0 for the 3 outgoing slots, items spread over the warp:
+        //   F0_s[j][j'] = sum_{i,p,q} m0_o0[p] m0_o1[q] T[.., j@s, ..] conj(T[.., j'@s, ..])
+        //              = (sum T~[.., j@s, ..] conj(T~[.., j'@s, ..])) / (m0_s[j] m0_s[j'])^{1/2},
+        // and 0 where m0_s[j] or m0_s[j'] vanishes (T vanishes there too)
         constexpr int NU = CHI * (CHI + 1) / 2;
         cd* F = tsm + 2 * H;   // [3][CC]
         for (int item = tid; item < 3 * NU; item += TEAM) {
@@ -533,17 +541,17 @@ __device__ void bp_init_vertex(const Ctx& c, int a, int tid, int cur, bool warm,
             const int ss = sstride<CHI>(s), s0 = sstride<CHI>(o0), s1 = sstride<CHI>(o1);
             cd f = cd{0.0, 0.0};
             for (int p = 0; p < CHI; ++p) {
-                const double wp = wsm[3 * CHI + o0 * CHI + p];
-                if (wp == 0.0) continue;
+                if (wsm[o0 * CHI + p] == 0.0) continue;
                 for (int q = 0; q < CHI; ++q) {
-                    const double w = wp * wsm[3 * CHI + o1 * CHI + q];
-                    if (w == 0.0) continue;
+                    if (wsm[o1 * CHI + q] == 0.0) continue;
                     for (int ii = 0; ii < 2; ++ii) {
                         const int base = ii * H + p * s0 + q * s1;
-                        f = cfmac(tsm[base + jp * ss], w * tsm[base + j * ss], f);
+                        f = cfmac(tsm[base + jp * ss], tsm[base + j * ss], f);
                     }
                 }
             }
+            const double d = wsm[3 * CHI + s * CHI + j] * wsm[3 * CHI + s * CHI + jp];
+            f = d > 0.0 ? nr_rsqrt(d) * f : cd{0.0, 0.0};
             F[s * CC + j * CHI + jp] = f;
             if (jp != j) F[s * CC + jp * CHI + j] = conj(f);
         }
@@ -605,6 +613,7 @@ struct BPSm {
     C<TS> trs[3];        // traces of the outgoing messages (mixed: of the correction terms)
     C<TS> itr[3];        // 1 / trace, formed in FP64
     TS dl[3];
+    TS dsum[3];          // one instance: the team's distance summed over the rounds of a sweep
     int es[3], out_idx[3], in_idx[3];
     int cached;          // vertex held in the cache, -1 if none
 };
@@ -790,38 +799,31 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
         }
     }
     team_bar<TEAM>(team);
-    // traces of the outgoing messages; in the mixed mode also their reciprocals, in FP32 by
-    // the same lane (the message correction is rounded to FP32, so a reciprocal with FP32
-    // relative error adds noise of the size of that rounding)
+    // traces of the outgoing messages (their reciprocals follow in FP64, bp_trace_rcp)
     if (tid < 3 * CC && tid % CC == 0) {
         const int k = tid / CC;
         CT trs = z;
 #pragma unroll
         for (int j = 0; j < CHI; ++j) trs = trs + sm.F[k][j * CHI + j];
         sm.trs[k] = trs;
-        if constexpr (Mode::mixed) {
-            const float tx = (float)sm.t0[k].x + trs.x, ty = (float)sm.t0[k].y + trs.y;
-            const float n2 = fmaf(tx, tx, ty * ty);
-            const float in2 = n2 > 0.f ? __frcp_rn(n2) : 0.f;
-            sm.itr[k] = CT{tx * in2, -ty * in2};
-        }
     }
 }
 
 // Reciprocals of the complex traces of every team's outgoing messages in FP64 (reading
 // R10: messages are divided by their complex trace), one lane per message, by the first
 // warp of the block: FP64 instructions cost the same for 1 or 32 active lanes, so one
-// warp does this for all teams.  FP64 mode only (the mixed mode forms them in bp_front).
+// warp does this for all teams.  Mixed: the trace is t0 + tr Fd.
 template <int CHI, class Mode, int TB>
 __device__ void bp_trace_rcp(BPSm<CHI, Mode, TB>* all, int nteams) {
     using TS = typename Mode::TS;
     for (int l = threadIdx.x; l < 3 * nteams; l += 32) {
         BPSm<CHI, Mode, TB>& sm = all[l / 3];
         const int k = l % 3;
-        static_assert(!Mode::mixed, "FP64 trace reciprocals");
-        const cd tr = ccast<double>(sm.trs[k]);
+        cd tr = ccast<double>(sm.trs[k]);
+        if constexpr (Mode::mixed) tr = tr + sm.t0[k];
         const double n2 = norm2(tr);
-        const double in2 = n2 > 0.0 ? nr_rcp(n2) : 0.0;
+        // the mixed mode rounds the result to FP32, so one Newton step (relative error ~2^-44) suffices
+        const double in2 = n2 > 0.0 ? (Mode::mixed ? nr_rcp1(n2) : nr_rcp(n2)) : 0.0;
         sm.itr[k] = ccast<TS>(cd{tr.x * in2, -tr.y * in2});
     }
 }
@@ -870,7 +872,7 @@ __device__ void bp_back(const Ctx& c, int tid, int team, int cur, bool exact, BP
                 if (tid % CC == 0) {
                     const TS f = sm.out_idx[tid / CC] >= 0 ? nr_sqrt(f2) : (TS)0;
                     if (gacc) atomicAdd(gacc, (double)f);
-                    else sm.dl[tid / CC] = f;
+                    else sm.dsum[tid / CC] += f;
                 }
             }
             return;
@@ -906,7 +908,11 @@ __device__ void bp_back(const Ctx& c, int tid, int team, int cur, bool exact, BP
         }
     }
     team_bar<TEAM>(team);
-    if (gacc && tid == 0) atomicAdd(gacc, (double)sm.dl[0] + (double)sm.dl[1] + (double)sm.dl[2]);
+    if (gacc) {
+        if (tid == 0) atomicAdd(gacc, (double)sm.dl[0] + (double)sm.dl[1] + (double)sm.dl[2]);
+    } else if (tid < 3) {
+        sm.dsum[tid] += sm.dl[tid];
+    }
 }
 
 // copy a frozen instance's outgoing messages to the other buffer
@@ -1196,7 +1202,7 @@ struct SmemSize {
     static constexpr size_t rv =
         sizeof(C<typename Mode::TS>) * (4 * CHI * CHI * CHI + 3 * CHI * CHI) * (TPB / S::TRV);
     static constexpr size_t init =
-        (sizeof(double) * 6 * CHI + (Mode::mixed ? sizeof(cd) * (2 * CHI * CHI * CHI + 3 * CHI * CHI) : 0)) * S::NIT;
+        (sizeof(double) * (6 * CHI + 4) + (Mode::mixed ? sizeof(cd) * (2 * CHI * CHI * CHI + 3 * CHI * CHI) : 0)) * S::NIT;
     static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
     // bytes before the per-instance flags (which follow at this offset in the BP kernel)
     static constexpr size_t value = mx(mx((PH & PH_GATES) ? gate : 0, (PH & PH_BP) ? mx(bp, init) : 0),
@@ -1258,8 +1264,8 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 static_assert(S::TV == 32, "one warp per BP-init team");
                 const int team = threadIdx.x / S::TV, tid = threadIdx.x % S::TV;
                 const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * S::NIT;
-                double* wsm = reinterpret_cast<double*>(smem) + team * 6 * CHI;
-                cd* tsm = reinterpret_cast<cd*>(reinterpret_cast<double*>(smem) + S::NIT * 6 * CHI) +
+                double* wsm = reinterpret_cast<double*>(smem) + team * (6 * CHI + 4);
+                cd* tsm = reinterpret_cast<cd*>(reinterpret_cast<double*>(smem) + S::NIT * (6 * CHI + 4)) +
                           team * (2 * CHI * CHI * CHI + 3 * CHI * CHI);
                 if (team < S::NIT)
                     for (int a = gteam; a < c.n; a += nt)
@@ -1302,6 +1308,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                 thr3[b] = (float)(3.0 * t);
             }
             if (tid == 0) sm.cached = -1;   // T and D0 changed in the init phase
+            if (tid < 3) sm.dsum[tid] = 0;
             __syncthreads();
             const int gteam = team * c.nblocks + blockIdx.x, nt = c.nblocks * tpb_teams;
             const int inst0 = gteam < c.n ? c.vert_inst[gteam] : 0;   // the first round's vertex
@@ -1321,8 +1328,7 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                     acc_next[b] = 0.0;
                     ex_next[b] = 0.0;
                 }
-                // rounds of one vertex per team; the block synchronises three times per round
-                typename Mode::TS bl = 0;   // thread 0: this block's distance (one instance)
+                // rounds of one vertex per team; the block synchronises twice per round
                 for (int base = 0; base < c.n; base += nt) {
                     const int a = base + gteam;
                     int inst = 0;
@@ -1333,29 +1339,24 @@ __device__ __forceinline__ void anneal_body(const Ctx& c) {
                         else act = true;
                     }
                     if (act) bp_front<CHI, Mode, S::TB>(c, a, tid, team, cur, sm, base == 0 && have_pre, pre);
-                    if constexpr (Mode::mixed) {
-                        team_bar<S::TB>(team);   // the team's own trace reciprocals (bp_front)
-                    } else {
-                        __syncthreads();
-                        if (threadIdx.x < 32) bp_trace_rcp<CHI, Mode, S::TB>(all, tpb_teams);
-                        __syncthreads();
-                    }
+                    __syncthreads();
+                    if (threadIdx.x < 32) bp_trace_rcp<CHI, Mode, S::TB>(all, tpb_teams);
+                    __syncthreads();
                     if (act) bp_back<CHI, Mode, S::TB>(c, tid, team, cur, exnow[inst] != 0, sm, c.B == 1 ? nullptr : acc + inst);
-                    else if (tid < 3) sm.dl[tid] = 0;
-                    if (c.B == 1) {
-                        __syncthreads();
-                        if (threadIdx.x < 32) {
-                            typename Mode::TS v = 0;
-                            for (int q = threadIdx.x; q < 3 * tpb_teams; q += 32) v += all[q / 3].dl[q % 3];
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                            bl += v;
-                        }
-                    }
                 }
-                if (c.B == 1 && threadIdx.x == 0) atomicAdd(acc, (double)bl);
                 cur ^= 1;
-                if (!grid_sync(gb, c.spin_limit)) return;
+                // one instance: the first warp sums the teams' distances between the block's
+                // barrier and its arrival at the grid barrier
+                if (!grid_sync_pre(gb, c.spin_limit, [&]() {
+                        if (c.B != 1) return;
+                        typename Mode::TS v = 0;
+                        for (int q = threadIdx.x; q < 3 * tpb_teams; q += 32) v += all[q / 3].dsum[q % 3];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (threadIdx.x == 0) atomicAdd(acc, (double)v);
+                    }))
+                    return;
+                if (tid < 3) sm.dsum[tid] = 0;   // read by the first warp before the barrier
                 // the next sweep's incoming messages of this team's first vertex are loaded
                 // now, so that their latency overlaps the decision below
                 have_pre = false;

@@ -601,6 +601,39 @@ __device__ __forceinline__ bool grid_sync(GridBarrier& gb, long long limit) {
     return ok_shared != 0;   // one value per block, so the whole block leaves together
 }
 
+// grid_sync with a step of the first warp between the block's barrier and its arrival: pre()
+// runs on warp 0 once the block's shared-memory writes are visible to it, and thread 0's
+// release arrival follows in program order, so what pre() writes to global memory is visible
+// to every block that passes this barrier.
+template <class Pre>
+__device__ __forceinline__ bool grid_sync_pre(GridBarrier& gb, long long limit, Pre&& pre) {
+    __shared__ int ok_pre;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        pre();
+        __syncwarp();
+    }
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long old = atom_add_release_u64(gb.count, 1ull);
+        if (old + 1ull < gb.next) {
+            long long polls = 0;
+            while (ld_acquire_u64(gb.count) < gb.next) {
+                if (++polls > limit) {
+                    atomicExch(gb.err, 6);   // GTQA_ERR_TIMEOUT
+                    ok = 0;
+                    break;
+                }
+                if (polls > 2048) __nanosleep(32);
+            }
+        }
+        gb.next += gb.nblocks;
+        ok_pre = ok;
+    }
+    __syncthreads();
+    return ok_pre != 0;
+}
+
 // The dynamic shared-memory limit is an attribute of the kernel function, shared by
 // every state in the process, while the BP kernel's need grows with the number of
 // instances.  The limit is therefore raised to the device maximum (not to one state's
