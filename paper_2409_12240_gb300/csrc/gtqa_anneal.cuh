@@ -354,11 +354,11 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
         team_bar<TEAM>(team);
         if constexpr (TEAM <= 32) {
             WarpGroup grp{group_mask<TEAM>()};
-            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-12, 1e-6, 60, &nrot,
+            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-12, 1e-5, 60, &nrot,
                                        c.chi, &sm.relmask);
         } else {
             TeamGroup<TEAM> grp{team, &sm.flag};
-            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-12, 1e-6, 60, &nrot,
+            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-12, 1e-5, 60, &nrot,
                                        c.chi, &sm.relmask);
         }
     }
