@@ -595,6 +595,12 @@ struct BPSm {
         return ns;
     }
     static constexpr int NS = fslices();
+    // FP64 mode: the overlap stage keeps every lane busy instead (FP64 instructions cost per
+    // warp, so the fewer per lane the better): NPART lanes per (j, j') split the (i, u) sum
+    // and meet by shuffles, or, where that does not divide, the sum in two halves over the
+    // physical index i, added at use
+    static constexpr int NPART = TB / CC;
+    static constexpr bool HALVES = !(TB % CC == 0 && NPART <= 32 && (2 * CHI) % NPART == 0);
     static_assert(CHI % 2 == 0 && 3 * (CHI / 2) * (CHI / 2) * NS <= TB, "BP team too small for the overlap stage");
     // T, P and Q in the natural index order [i][j0][j1][j2] with one padding element after
     // every (i, j0) plane, so that a stride along slot 0 does not map to one bank
@@ -605,6 +611,7 @@ struct BPSm {
     C<TS> min[3][CC];    // incoming messages (mixed: m0 + delta)
     C<TS> din[3][CC];    // mixed: incoming delta
     C<TS> F[3][CC];      // the outgoing messages before normalisation
+    C<TS> F1[Mode::mixed ? 1 : 3][CC];   // FP64 mode with HALVES: the i = 1 half
     C<TS> prev[3][CC];   // outgoing messages of the previous sweep
     C<TS> D[3][CC];      // new - old, for the trace norm
     cf D0f[3][CC];       // mixed: warm-start defect
@@ -755,10 +762,10 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
     }
     team_bar<TEAM>(team);
     // overlaps with conj(T): F_s[j][j'] = sum over the 2 CHI^2 columns (i, u@o0, v@o1) of
-    // Q_s[.., j@s, ..] conj(T[.., j'@s, ..]).  A lane holds a 2 x 2 block of (j, j') over a
-    // slice of the columns, so that every element it loads feeds two products; the NS lanes
-    // of a block then sum by shuffles.
-    {
+    // Q_s[.., j@s, ..] conj(T[.., j'@s, ..]).  Mixed mode: a lane holds a 2 x 2 block of
+    // (j, j') over a slice of the columns, so that every element it loads feeds two products;
+    // the NS lanes of a block then sum by shuffles.
+    if constexpr (Mode::mixed) {
         constexpr int NBJ = CHI / 2, NB = NBJ * NBJ, K = 2 * CC, NS = SM::NS, CPL = K / NS;
         if (tid < 3 * NB * NS) {
             const int s = tid / (NB * NS), rem = tid % (NB * NS);
@@ -797,6 +804,48 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
                 }
             }
         }
+    } else if constexpr (SM::HALVES) {
+        for (int t = tid; t < 2 * 3 * CC; t += TEAM) {
+            const int i = t / (3 * CC), rem = t % (3 * CC);
+            const int s = rem / CC, r = rem % CC;
+            if (sm.es[s] < 0) continue;
+            const int j = r / CHI, jp = r % CHI;
+            const int ss = slot_stride(s);
+            const int so = s == 0 ? S1 : S0, st2 = s == 2 ? S1 : 1;   // strides of the two other slots
+            CT acc = z;
+#pragma unroll
+            for (int u = 0; u < CHI; ++u)
+#pragma unroll
+                for (int v = 0; v < CHI; ++v) {
+                    const int off = i * HP + u * so + v * st2;
+                    acc = cfmac(sm.T[off + jp * ss], sm.Q[s][off + j * ss], acc);
+                }
+            if (i == 0) sm.F[s][r] = acc;
+            else sm.F1[s][r] = acc;
+        }
+    } else {
+        constexpr int NPART = SM::NPART, PER = 2 * CHI / NPART;
+        const int r = tid / NPART, part = tid % NPART;
+        const int j = r / CHI, jp = r % CHI;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            if (sm.es[s] < 0) continue;
+            const int ss = slot_stride(s);
+            const int so = s == 0 ? S1 : S0, st2 = s == 2 ? S1 : 1;
+            CT acc = z;
+#pragma unroll
+            for (int h = 0; h < PER; ++h) {
+                const int cmb = part * PER + h, i = cmb / CHI, u = cmb % CHI;
+#pragma unroll
+                for (int v = 0; v < CHI; ++v) {
+                    const int off = i * HP + u * so + v * st2;
+                    acc = cfmac(sm.T[off + jp * ss], sm.Q[s][off + j * ss], acc);
+                }
+            }
+            acc.x = group_sum<NPART>(acc.x, group_mask<NPART>());
+            acc.y = group_sum<NPART>(acc.y, group_mask<NPART>());
+            if (part == 0) sm.F[s][r] = acc;
+        }
     }
     team_bar<TEAM>(team);
     // traces of the outgoing messages (their reciprocals follow in FP64, bp_trace_rcp)
@@ -804,7 +853,10 @@ __device__ void bp_front(const Ctx& c, int a, int tid, int team, int cur, BPSm<C
         const int k = tid / CC;
         CT trs = z;
 #pragma unroll
-        for (int j = 0; j < CHI; ++j) trs = trs + sm.F[k][j * CHI + j];
+        for (int j = 0; j < CHI; ++j) {
+            trs = trs + sm.F[k][j * CHI + j];
+            if constexpr (!Mode::mixed && SM::HALVES) trs = trs + sm.F1[k][j * CHI + j];
+        }
         sm.trs[k] = trs;
     }
 }
@@ -848,7 +900,8 @@ __device__ void bp_back(const Ctx& c, int tid, int team, int cur, bool exact, BP
         CT d = z;
         if (out >= 0) {
             const CT itr = sm.itr[k];
-            const CT f = sm.F[k][r];
+            CT f = sm.F[k][r];
+            if constexpr (!Mode::mixed && BPSm<CHI, Mode, TB>::HALVES) f = f + sm.F1[k][r];
             CT num = f;
             if constexpr (Mode::mixed) {
                 const int j = r / CHI, jp = r % CHI;
