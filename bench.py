@@ -480,8 +480,13 @@ def rooflines(prof: dict, dlt: dict, chi: int, n: int, m: int, mixed: bool, peak
         if kname == "bp_kernel":
             o["sweeps_per_launch"] = int(dlt["bp_sweeps"]) / nl
             o["us_per_sweep"] = ms * 1e3 / max(int(dlt["bp_sweeps"]), 1)
-            o["note"] = ("the working set is L2-resident; each sweep waits for the neighbouring blocks' previous "
-                         "sweep (or a grid barrier), so the sweep's latency, not a pipe, bounds it")
+            o["note"] = ("the working set is L2-resident; each sweep ends in a grid barrier after which the "
+                         "neighbours' messages come from L2, so the sweep's latency, not a pipe, bounds it")
+        elif kname == "gates_kernel":
+            o["note"] = ("algorithmic count: two Householder QRs of the (2 chi^2) x (2 chi) side matrices per edge; "
+                         "the kernel factors the four chi^2 x chi blocks of one physical index each (a quarter of "
+                         "that QR work), so frac can exceed 1 where the QR dominates (chi = 8); "
+                         "executed_fp64_frac is the FP64 work the kernel issues")
         out[kname] = o
     return out
 
