@@ -292,7 +292,7 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
     // step V <- V (3I - V^H V)/2 makes it unitary to ~1e-14; the FP64 Jacobi then polishes
     // W = M V (typically two sweeps; the confirming sweep is skipped by the quadratic
     // stop).  The result is an FP64 SVD of M with a fraction of the FP64 instructions.
-    int nrot = 0, sweeps;
+    int nrot = 0, sweeps, nsteps = 0;
     // FP32 rotation angles with FP64-exact rotations; the confirming sweep is skipped
     // once a sweep's rotations are all below sqrt(tol) (quadratic convergence)
     auto svd64 = [&](bool init_v, double tol, double quad) {
@@ -354,12 +354,12 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
         team_bar<TEAM>(team);
         if constexpr (TEAM <= 32) {
             WarpGroup grp{group_mask<TEAM>()};
-            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-12, 1e-5, 60, &nrot,
-                                       c.chi, &sm.relmask);
+            sweeps = jacobi_polish<NM, decltype(grp), true>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-12,
+                                                            1e-5, 60, &nrot, c.chi, &sm.relmask, &nsteps);
         } else {
             TeamGroup<TEAM> grp{team, &sm.flag};
-            sweeps = jacobi_polish<NM>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-12, 1e-5, 60, &nrot,
-                                       c.chi, &sm.relmask);
+            sweeps = jacobi_polish<NM, decltype(grp), true>(sm.M, sm.V, sm.sig, tid, grp, group_mask<NM>(), 1e-12,
+                                                            1e-5, 60, &nrot, c.chi, &sm.relmask, &nsteps);
         }
     }
     if (nrot) atomicAdd(&sm.nrot, nrot);
@@ -390,7 +390,8 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
             atomicAdd(&c.stats[0], disc);
             // log of the gate fidelity (1 - disc)^2, Eq. (gate_fidelity); a float log in the mixed mode
             atomicAdd(&c.stats[1], Mode::mixed ? 2.0 * (double)log1pf(-(float)disc) : 2.0 * log1p(-disc));
-            atomicAdd(&c.stats[2], (double)sweeps * (NM - 1) * (NM / 2));
+            // Jacobi pairs examined (the mixed polish runs partial sweeps)
+            atomicAdd(&c.stats[2], (double)(Mode::mixed ? nsteps : sweeps * (NM - 1)) * (NM / 2));
             atomicAdd(&c.stats[3], (double)sm.nrot);
             atomicMax(&c.ctl->gate_sw_max, sweeps);
             sm.keep = keep;

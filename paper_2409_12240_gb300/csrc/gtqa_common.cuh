@@ -72,6 +72,7 @@ struct WarpGroup {
     __device__ __forceinline__ void sync() const { __syncwarp(mask); }
     __device__ __forceinline__ bool any(int p) const { return __any_sync(mask, p) != 0; }
     __device__ __forceinline__ int max_int(int v) const { return __reduce_max_sync(mask, v); }
+    __device__ __forceinline__ unsigned or_bits(unsigned v) const { return __reduce_or_sync(mask, v); }
 };
 
 // Synchronisation policy for a group that is the whole thread block.
@@ -93,6 +94,14 @@ struct BlockGroup {
         atomicMax(flag, v);
         __syncthreads();
         return *flag;
+    }
+    __device__ __forceinline__ unsigned or_bits(unsigned v) const {
+        __syncthreads();
+        if (threadIdx.x == 0) *flag = 0;
+        __syncthreads();
+        if (v) atomicOr(reinterpret_cast<unsigned*>(flag), v);
+        __syncthreads();
+        return *reinterpret_cast<volatile unsigned*>(flag);
     }
 };
 
@@ -302,12 +311,19 @@ __device__ __forceinline__ bool norm_collapsed(double x, double ref) {
 // a pair of such a column p with a smaller one q is judged by |gamma| against alpha_p (the
 // size of the rotation of the kept column) rather than sqrt(alpha_p beta_q).  The kept
 // columns then converge as with keep_rank = N, while rotations among discarded columns, which
-// leave the kept subspace unchanged, no longer force a confirming sweep.  Every pair is still
-// rotated in each sweep that runs.  Returns the sweeps run.
-template <int N, typename Group>
+// leave the kept subspace unchanged, no longer force a confirming sweep.
+// PARTIAL: every pair is rotated in the first sweep; a later sweep runs only the steps of the
+// round-robin schedule in which the previous sweep made a rotation above quad_tol.  A pair
+// whose rotation in a sweep stayed below quad_tol is orthogonal after it to about quad_tol
+// times the largest rotation of that sweep (the rotations of its columns with the others
+// reintroduce only products of their sizes), which is the accuracy of the quadratic stop, so
+// those steps need no second pass.  Otherwise every pair is rotated in each sweep that runs.
+// Returns the sweeps run (partial ones included); *nsteps (if given, group lane 0) counts the
+// steps run, of N / 2 pairs each.
+template <int N, typename Group, bool PARTIAL = false>
 __device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, const Group& grp, unsigned pair_mask,
                              double tol, double quad_tol, int max_sweeps, int* nrot, int keep_rank = N,
-                             unsigned* relmask = nullptr) {
+                             unsigned* relmask = nullptr, int* nsteps = nullptr) {
     using CD = C<double>;
     const int k = g / N;
     const int r = g % N;
@@ -340,10 +356,16 @@ __device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, con
     }
     const unsigned rel = partial ? *relmask : 0xffffffffu;
     const double tol2 = tol * tol, quad2 = quad_tol * quad_tol;
+    static_assert(N - 1 <= 32, "one bit per step");
+    unsigned steps = N - 1 == 32 ? 0xffffffffu : (1u << (N - 1)) - 1u;   // steps this sweep runs
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         int big = 0;
+        unsigned bigsteps = 0u;   // this lane's steps with a rotation above quad_tol
         for (int step = 0; step < N - 1; ++step) {
+            if (PARTIAL && !((steps >> step) & 1u)) continue;   // the same for the whole group
+            int bstep = 0;   // this lane's pair rotated by more than quad_tol
+            if (nsteps && g == 0) ++*nsteps;
             int p, q;
             round_robin_pair(N, step, k, p, q);
             const CD ap = A[p * N + r], aq = A[q * N + r];
@@ -358,10 +380,10 @@ __device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, con
             if (rot) {
                 const bool rp = (rel >> p) & 1u, rq = (rel >> q) & 1u;
                 if (rp && rq) {
-                    if (g2 > quad2 * ab) big = 1;
+                    if (g2 > quad2 * ab) bstep = 1;
                 } else if (rp || rq) {
                     const double mx = alpha > beta ? alpha : beta;
-                    if (g2 > quad2 * mx * mx) big = 1;
+                    if (g2 > quad2 * mx * mx) bstep = 1;
                 }
                 const double d = beta - alpha;
                 double rsc;
@@ -406,9 +428,17 @@ __device__ int jacobi_polish(C<double>* A, C<double>* V, double* nrm, int g, con
                     nrm[q] = nq;
                 }
             }
+            big |= bstep;
+            if (bstep) bigsteps |= 1u << step;
             grp.sync();
         }
-        if (!grp.any(big)) {
+        if constexpr (PARTIAL) {
+            steps = grp.or_bits(bigsteps);
+            if (!steps) {
+                ++sweep;
+                break;
+            }
+        } else if (!grp.any(big)) {
             ++sweep;
             break;
         }
@@ -518,6 +548,14 @@ struct TeamGroup {
         atomicMax(flag, v);
         team_bar<TEAM>(team);
         return *(volatile int*)flag;
+    }
+    __device__ __forceinline__ unsigned or_bits(unsigned v) const {
+        team_bar<TEAM>(team);
+        if ((threadIdx.x % TEAM) == 0) *flag = 0;
+        team_bar<TEAM>(team);
+        if (v) atomicOr(reinterpret_cast<unsigned*>(flag), v);
+        team_bar<TEAM>(team);
+        return *reinterpret_cast<volatile unsigned*>(flag);
     }
 };
 
