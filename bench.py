@@ -970,6 +970,8 @@ def ncu_scale(a):
     K, dt, tol, mi = 500, 0.05, 1e-8, 100
     s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, 8, inst.colour, G.gtqa_options_init(precision=G.GTQA_MIXED))
     try:
+        # the launch shapes gtqa_autotune picks at this shape (512-thread blocks for all three kernels)
+        G.gtqa_set_shape(s, (1, 1, 1))
         G.gtqa_anneal(s, 1, 5, K, dt, tol, mi)
         G.gtqa_trotter_layer(s, 6 / K, dt)
         G.gtqa_bp_sweep(s, 0.0, 10, G.GTQA_BP_WARM_START)
