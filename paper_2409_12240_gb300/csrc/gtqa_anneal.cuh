@@ -171,6 +171,7 @@ struct GateSm {
     double w[2][CHI * CHI];
     double lab[CHI];
     double sig[2 * CHI];
+    double isig[2 * CHI];      // 1 / sig
     cd ph[4];
     int perm[2 * CHI];
     int keep;
@@ -367,7 +368,9 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
     for (int cc = tid; cc < NM; cc += TEAM) {
         double s2 = 0.0;
         for (int r = 0; r < NM; ++r) s2 += norm2(sm.M[cc * NM + r]);
-        sm.sig[cc] = nr_sqrt(s2);
+        const double sv = nr_sqrt(s2);
+        sm.sig[cc] = sv;
+        sm.isig[cc] = sv > 0.0 ? nr_rcp(sv) : 0.0;
     }
     team_bar<TEAM>(team);
     for (int cc = tid; cc < NM; cc += TEAM) sm.perm[desc_rank(sm.sig, NM, cc)] = cc;
@@ -412,7 +415,7 @@ __device__ void gate_edge(const Ctx& c, int e, int tid, int team, GateSm<CHI>& s
         if (r0 < CHI && cc < keep) {
             const int pc = sm.perm[cc];
             const int row = i * CHI + r0;
-            const cd u = (x == 0) ? nr_rcp(sm.sig[pc]) * sm.M[pc * NM + row] : conj(sm.V[pc * NM + row]);
+            const cd u = (x == 0) ? sm.isig[pc] * sm.M[pc * NM + row] : conj(sm.V[pc * NM + row]);
             E0[cc] = ccast<RB>(u);
         }
     }
@@ -1039,11 +1042,13 @@ struct RGSm {
     cd Am[2][CHI * CHI];
     cd Vm[2][CHI * CHI];
     double w[2][CHI];
+    double wq[2][CHI], wiq[2][CHI];   // w^{1/2} and w^{-1/2} of the kept eigenvalues, else 0
     cd sq[2][CHI * CHI];
     cd isq[2][CHI * CHI];
     cd M[CHI * CHI];
     cd VM[CHI * CHI];
     double sig[CHI];
+    double isig[CHI];   // 1 / sig (0 for a zero singular value)
     int perm[CHI];
     double scal[2];
     // mixed mode: scratch of the FP32-preconditioned SVDs
@@ -1114,17 +1119,26 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
         sm.w[x][k] = sg >= 0.0 ? wv : -wv;
     }
     team_bar<TEAM>(team);
+    // the roots of each eigenvalue once (eigenvalues at or below the cut-off count as zero)
+    for (int t = tid; t < 2 * CHI; t += TEAM) {
+        const int x = t / CHI, k = t % CHI;
+        double wmax = 0.0;
+        for (int q = 0; q < CHI; ++q) wmax = fmax(wmax, sm.w[x][q]);
+        const double wk = sm.w[x][k];
+        const bool kept = wk > c.eig_cut * wmax;
+        const double isq = kept ? nr_rsqrt(wk) : 0.0;
+        sm.wiq[x][k] = isq;
+        sm.wq[x][k] = kept ? wk * isq : 0.0;
+    }
+    team_bar<TEAM>(team);
     for (int t = tid; t < 2 * CC; t += TEAM) {
         const int x = t / CC, r = t % CC;
         const int j = r / CHI, jp = r % CHI;
-        double wmax = 0.0;
-        for (int k = 0; k < CHI; ++k) wmax = fmax(wmax, sm.w[x][k]);
         cd s1 = cd{0.0, 0.0}, s2 = cd{0.0, 0.0};
         for (int k = 0; k < CHI; ++k) {
-            const double wk = sm.w[x][k];
-            if (!(wk > c.eig_cut * wmax)) continue;
-            const double isq = nr_rsqrt(wk);
-            const double sq = wk * isq;
+            const double isq = sm.wiq[x][k];
+            if (!(isq > 0.0)) continue;
+            const double sq = sm.wq[x][k];
             const cd vv = sm.Vm[x][k * CHI + j] * conj(sm.Vm[x][k * CHI + jp]);
             s1 = cfma(cd{sq, 0.0}, vv, s1);
             s2 = cfma(cd{isq, 0.0}, vv, s2);
@@ -1160,7 +1174,9 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
     for (int cc = tid; cc < CHI; cc += TEAM) {
         double n2 = 0.0;
         for (int r = 0; r < CHI; ++r) n2 += norm2(sm.M[cc * CHI + r]);
-        sm.sig[cc] = nr_sqrt(n2);
+        const double sv = nr_sqrt(n2);
+        sm.sig[cc] = sv;
+        sm.isig[cc] = sv > 0.0 ? nr_rcp(sv) : 0.0;
     }
     team_bar<TEAM>(team);
     for (int cc = tid; cc < CHI; cc += TEAM) sm.perm[desc_rank(sm.sig, CHI, cc)] = cc;
@@ -1188,7 +1204,7 @@ __device__ void regauge_edge(const Ctx& c, int e, int tid, int team, int cur, RG
         const bool kept = sm.scal[0] > 0.0 && s > c.svd_cut * sm.sig[sm.perm[0]];
         if (kept) {
             for (int jp = 0; jp < CHI; ++jp) {
-                const cd u = (x == 0) ? nr_rcp(s) * sm.M[pc * CHI + jp] : conj(sm.VM[pc * CHI + jp]);
+                const cd u = (x == 0) ? sm.isig[pc] * sm.M[pc * CHI + jp] : conj(sm.VM[pc * CHI + jp]);
                 acc = cfma(sm.isq[x][jp * CHI + jpp], u, acc);
             }
             acc = sm.scal[1] * acc;
