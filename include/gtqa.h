@@ -90,7 +90,8 @@ typedef struct gtqa_stats_t {
     double last_bp_dist;     /* dist/|E| after the last sweep (max over instances), App. B */
     double discarded_weight; /* sum over gates of sum_{dropped} s^2 / sum s^2 */
     double log_fidelity;     /* sum over gates of log f, f = (1 - discarded)^2, Eq. (gate_fidelity) */
-    int64_t svd_pairs;       /* column pairs examined by the gate-core Jacobi SVDs (work counter) */
+    int64_t svd_pairs;       /* column pairs examined by the gate-core FP64 Jacobi sweeps (the polish
+                                in GTQA_MIXED; work counter) */
     int64_t svd_rotations;   /* rotations applied by the gate-core Jacobi SVDs (work counter) */
     int64_t bp_sweeps;       /* BP sweeps run since creation (sum over calls, max over instances) */
     int64_t launches;        /* kernels launched by the library since creation */
@@ -101,7 +102,9 @@ typedef struct gtqa_stats_t {
     int64_t regauge_svd_sweeps; /* Jacobi sweeps of the regauge's eigen-decompositions and SVDs
                                    (persistent path; work counter) */
     int32_t gate_svd_sweeps_max;      /* most FP64 Jacobi sweeps of one gate-core SVD since creation
-                                         (the FP64 polish sweeps in GTQA_MIXED; persistent path) */
+                                         (the FP64 polish sweeps in GTQA_MIXED, whose sweeps after
+                                         the first run only the schedule steps that still rotate
+                                         by more than the stop threshold; persistent path) */
     int32_t gate_svd_sweeps32_max;    /* GTQA_MIXED: most FP32 preconditioning sweeps of one gate-core SVD */
     int32_t regauge_svd_sweeps_max;   /* the same two maxima for the regauge's decompositions */
     int32_t regauge_svd_sweeps32_max;
