@@ -101,7 +101,18 @@ def test_null_handles_are_rejected(G):
     lib = G.load()
     assert lib.gtqa_trotter_layer(None, 0.5, 0.1) == G.GTQA_ERR_INVALID_ARG
     assert lib.gtqa_regauge(None) == G.GTQA_ERR_INVALID_ARG
+    three = (ctypes.c_int32 * 3)(0, 0, 0)
+    table = (ctypes.c_int32 * 12)()
+    assert lib.gtqa_set_shape(None, three) == G.GTQA_ERR_INVALID_ARG
+    assert lib.gtqa_launch_shape(None, table) == G.GTQA_ERR_INVALID_ARG
     lib.gtqa_destroy(None)
+
+
+def test_set_shape_wants_one_variant_per_phase_kernel(G):
+    """The binding checks the shape of the variant list before it reaches the library."""
+    for bad in ((0, 0), (0, 0, 0, 0), ((0, 0, 0),)):
+        with pytest.raises(ValueError):
+            G.gtqa_set_shape(0, bad)
 
 
 def test_library_colouring_uses_delta_colours_when_it_can(G):
