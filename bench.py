@@ -45,6 +45,9 @@ WORKLOAD_NAME = ("random 3-regular n=1000 (m=1500, 3-colour schedule), J~N(0,1),
                  "chi=4, K=3200 layers, dt=0.2, BP tol 1e-8, max 100 sweeps")
 # the batched configuration: 256 instances with n uniform over even values in [50, 1000]
 BATCH_WL = dict(B=256, seed=0, chi=4, K=400, dt=0.05, tol=1e-8, max_iter=100)
+# the precision and bond-dimension sweep: n = 1000 (seed 1), K = 1000, dt = 0.2; layers 1..3
+# untimed, layers 4..43 timed
+SWEEP_WL = dict(n=1000, seed=1, K=1000, dt=0.2, tol=1e-8, max_iter=100, warm=3, steps=40, chis=(2, 4, 8, 16))
 # the scale configuration: n = 100000, chi = 8
 SCALE_WL = dict(n=100000, seed=2, chi=8, K=500, dt=0.05, tol=1e-8, max_iter=100, warm=5, steps=10)
 SNAPSHOTS = (800, 1600, 2400, 3200)
@@ -72,6 +75,15 @@ def parse(argv=None):
                    help="profiling case: anneal layers 1..K0, then one gates launch, one BP launch of 1 sweep "
                         "and, from the same state, one of 21 sweeps (warm start, no regauge); no timing")
     p.add_argument("--budget", type=float, default=20.0, help=argparse.SUPPRESS)
+    p.add_argument("--chi-sweep", action="store_true",
+                   help="the precision and bond-dimension sweep (n = 1000, chi in {2, 4, 8, 16}, FP64, mixed "
+                        "and complex64, three coupling types): layers/s, BP sweeps and the error against FP64 per cell")
+    p.add_argument("--policy-study", action="store_true",
+                   help="the regauge policy on the single-instance workload (mixed): R after the gates and "
+                        "100 layers with and without a threshold from three points of the anneal")
+    p.add_argument("--deg4-study", action="store_true",
+                   help="a random 4-regular graph (plain kernels): layers/s, BP sweeps and the mixed and "
+                        "complex64 errors against FP64")
     p.add_argument("--bp-study", action="store_true",
                    help="no timing: BP sweeps per layer over the anneal, sweep-by-sweep traces at three late "
                         "layers, and the same anneal with h ~ N(0, 1)")
@@ -1045,8 +1057,190 @@ def bp_study(a):
     print(json.dumps({"bp_study": out, "workload": WORKLOAD_NAME}))
 
 
+def chi_sweep(a):
+    """The precision and bond-dimension sweep.  Three coupling types on the same seeded graph
+    (J = +1 with h = 0, J = -1 with h = 0 (the MaxCut couplings of Sec. IV A), and J ~ N(0, 1)
+    with h ~ N(0, 0.1)), chi in {2, 4, 8, 16}, each in the FP64, mixed and complex64 modes, with
+    the default launch shapes.  Layers 1..3 run untimed.  Layers 4..43 are then timed one by one
+    with CUDA events on the library's stream (gtqa_anneal, one layer per call), each after an
+    L2 flush outside the events.  Each cell reports layers/s and BP sweeps per layer over the
+    timed layers.  It also reports max / mean |rho - rho_FP64| per vertex after layer 43, against
+    the FP64 cell of the same couplings and chi (the FP64 path agrees with the oracle to 1e-10),
+    and the sign agreement over the clear vertices (none for the Z2-symmetric h = 0 couplings)."""
+    import torch
+    from instances import make_instance
+    from paper_2409_12240_gb300 import gtqa as G
+    G.load(build_if_missing=True)
+    w = SWEEP_WL
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    timed = list(range(w["warm"] + 1, w["warm"] + w["steps"] + 1))
+    modes = (("fp64", G.GTQA_FP64), ("mixed", G.GTQA_MIXED), ("complex64", G.GTQA_C64))
+    out = {}
+    for cname, J, hs in (("J=+1,h=0", "ferro", 0.0), ("J=-1,h=0 (MaxCut)", "maxcut", 0.0),
+                         ("J~N(0,1),h~N(0,0.1)", "gauss", 0.1)):
+        inst = make_instance(w["n"], w["seed"], J=J, h_std=hs)
+        cells = {}
+        for chi in w["chis"]:
+            row, ref = {}, None
+            for mname, prec in modes:
+                s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour,
+                                  G.gtqa_options_init(precision=prec, cuda_stream=stream.cuda_stream))
+                try:
+                    G.gtqa_anneal(s, 1, w["warm"], w["K"], w["dt"], w["tol"], w["max_iter"])
+                    t_ms, st0, st1 = timed_layers(
+                        G, s, timed, lambda s_, k: G.gtqa_anneal(s_, k, k, w["K"], w["dt"], w["tol"], w["max_iter"]),
+                        stream, flush)
+                    rho, sign = G.gtqa_marginals(s)
+                finally:
+                    G.gtqa_destroy(s)
+                cell = {"layers_per_s": len(timed) / (t_ms / 1e3),
+                        "bp_sweeps_per_layer": (st1["bp_sweeps"] - st0["bp_sweeps"]) / len(timed)}
+                if ref is None:
+                    ref = (rho, sign)
+                else:
+                    cell.update(compare_marginals(rho, sign, *ref))
+                row[mname] = cell
+            cells[str(chi)] = row
+        out[cname] = cells
+    print(json.dumps({"chi_sweep": out, "n": w["n"], "seed": w["seed"], "K": w["K"], "dt": w["dt"], "tol": w["tol"],
+                      "max_iter": w["max_iter"], "layers_timed": {"first": timed[0], "last": timed[-1]},
+                      "error_reference": "the FP64 cell of the same couplings and chi, after the last timed layer"}))
+
+
+def timed_layers(G, s, layers: Sequence[int], run, stream, flush) -> Tuple[float, dict, dict]:
+    """Runs run(s, k) for each layer k, each bracketed by CUDA events on the library's stream
+    after an L2 flush outside the events; returns the summed time (ms) and the statistics
+    before and after."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in layers]
+    torch.cuda.synchronize()
+    st0 = G.gtqa_stats(s)
+    with torch.cuda.stream(stream):
+        for j, k in enumerate(layers):
+            flush.fill_(k & 0xFF)
+            ev[j][0].record(stream)
+            run(s, k)
+            ev[j][1].record(stream)
+    torch.cuda.synchronize()
+    st1 = G.gtqa_stats(s)
+    return float(sum(e0.elapsed_time(e1) for e0, e1 in ev)), st0, st1
+
+
+POLICY_WL = dict(starts=(300, 1500, 2800), layers=100, threshold=1e-2)
+
+
+def policy_study(a):
+    """The regauge policy (Sec. II C: regauge only when the residual R of App. C is large) on the
+    single-instance workload in the mixed mode.  The mixed path anneals layers 1..k0-1 for
+    k0 in {300, 1500, 2800}.  From each of these states: R after the gates of layer k0; layers
+    k0..k0+99 with the regauge in every layer; the same layers through gtqa_anneal_policy with
+    R threshold 1e-2.  Each run reports layers/s (per-layer CUDA events after an L2 flush) and
+    the regauged and skipped counts.  The policy run also reports its marginals against the
+    every-layer run after the last layer."""
+    import torch
+    from paper_2409_12240_gb300 import gtqa as G
+    G.load(build_if_missing=True)
+    K, dt, tol, mi, chi = WL["K"], WL["dt"], WL["tol"], WL["max_iter"], WL["chi"]
+    inst = instance()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def make():
+        return G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, chi, inst.colour,
+                             G.gtqa_options_init(precision=G.GTQA_MIXED, cuda_stream=stream.cuda_stream))
+    s = make()
+    states, k_done = {}, 0
+    for k0 in POLICY_WL["starts"]:
+        G.gtqa_anneal_graph(s, k_done + 1, k0 - 1, K, dt, tol, mi)
+        k_done = k0 - 1
+        states[k0] = G.gtqa_get_state(s)
+    G.gtqa_destroy(s)
+    thr = POLICY_WL["threshold"]
+    out = {}
+    for k0, st in states.items():
+        layers = list(range(k0, k0 + POLICY_WL["layers"]))
+        res = {}
+        s = make()
+        G.gtqa_set_state(s, *st)
+        G.gtqa_trotter_layer(s, k0 / K, dt)
+        res["R_after_gates"] = G.gtqa_residual(s)
+        G.gtqa_destroy(s)
+        rho = {}
+        for name, run in (("every_layer", lambda s_, k: G.gtqa_anneal(s_, k, k, K, dt, tol, mi)),
+                          (f"threshold_{thr:g}", lambda s_, k: G.gtqa_anneal_policy(s_, k, k, K, dt, tol, mi, thr))):
+            s = make()
+            try:
+                G.gtqa_set_state(s, *st)
+                r0 = G.gtqa_regauge_counts(s)
+                t_ms, st0, st1 = timed_layers(G, s, layers, run, stream, flush)
+                r1 = G.gtqa_regauge_counts(s)
+                rho[name] = G.gtqa_marginals(s)
+            finally:
+                G.gtqa_destroy(s)
+            cell = {"layers_per_s": len(layers) / (t_ms / 1e3),
+                    "bp_sweeps_per_layer": (st1["bp_sweeps"] - st0["bp_sweeps"]) / len(layers)}
+            if name != "every_layer":
+                cell.update({"regauged": r1[0] - r0[0], "skipped": r1[1] - r0[1]})
+                cell["against_every_layer"] = compare_marginals(*rho[name], *rho["every_layer"])
+            res[name] = cell
+        out[str(k0)] = res
+    print(json.dumps({"policy_study": out, "workload": WORKLOAD_NAME, "precision": "mixed",
+                      "layers_per_start": POLICY_WL["layers"], "threshold": thr}))
+
+
+DEG4_WL = dict(n=200, seed=0, chi=4, K=20, dt=0.3, tol=1e-10, max_iter=100, warm=1, steps=11)
+
+
+def deg4_study(a):
+    """A seeded random 4-regular graph (Sec. V), n = 200, J ~ N(0, 1), h ~ N(0, 0.1), chi = 4,
+    K = 20, dt = 0.3, BP tol 1e-10, on the plain kernels.  Layer 1 runs untimed; layers 2..12
+    are timed one by one (CUDA events after an L2 flush).  Per precision mode: layers/s, BP
+    sweeps per layer, and for the mixed and complex64 modes max / mean |rho - rho_FP64| after
+    layer 12 with the sign agreement over clear vertices."""
+    import torch
+    from instances import make_instance
+    from paper_2409_12240_gb300 import gtqa as G
+    G.load(build_if_missing=True)
+    w = DEG4_WL
+    inst = make_instance(w["n"], w["seed"], d=4)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    layers = list(range(w["warm"] + 1, w["warm"] + w["steps"] + 1))
+    out, ref = {}, None
+    for mname, prec in (("fp64", G.GTQA_FP64), ("mixed", G.GTQA_MIXED), ("complex64", G.GTQA_C64)):
+        s = G.gtqa_create(inst.n, inst.edges, inst.J, inst.h, w["chi"], inst.colour,
+                          G.gtqa_options_init(precision=prec, cuda_stream=stream.cuda_stream))
+        try:
+            G.gtqa_anneal(s, 1, w["warm"], w["K"], w["dt"], w["tol"], w["max_iter"])
+            t_ms, st0, st1 = timed_layers(
+                G, s, layers, lambda s_, k: G.gtqa_anneal(s_, k, k, w["K"], w["dt"], w["tol"], w["max_iter"]),
+                stream, flush)
+            rho, sign = G.gtqa_marginals(s)
+        finally:
+            G.gtqa_destroy(s)
+        cell = {"layers_per_s": len(layers) / (t_ms / 1e3),
+                "bp_sweeps_per_layer": (st1["bp_sweeps"] - st0["bp_sweeps"]) / len(layers)}
+        if ref is None:
+            ref = (rho, sign)
+        else:
+            cell.update(compare_marginals(rho, sign, *ref))
+        out[mname] = cell
+    print(json.dumps({"deg4_study": out, **{k: w[k] for k in ("n", "seed", "chi", "K", "dt", "tol", "max_iter")},
+                      "layers_timed": {"first": layers[0], "last": layers[-1]}}))
+
+
 def main():
     a = parse()
+    if a.policy_study:
+        policy_study(a)
+        return
+    if a.deg4_study:
+        deg4_study(a)
+        return
+    if a.chi_sweep:
+        chi_sweep(a)
+        return
     if a.bp_study:
         bp_study(a)
         return
