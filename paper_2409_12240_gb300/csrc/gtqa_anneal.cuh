@@ -1598,23 +1598,33 @@ __global__ void marginals_kernel2(const C<typename Mode::TS>* Gamma, const doubl
 // one warp per (vertex, incident edge); delta is the identity on the bond indices with
 // lambda > 0 (the padded indices do not exist in the state).  The trace norm is the sum of
 // singular values of the C x C difference (FP64 Jacobi).  Adds the unnormalised sum to *out.
+// R of App. C, unnormalised: the sum over the 2m directed bonds (a, s) of the trace norm of
+// delta - sum Gamma_a Gamma_a^* lambda^2 lambda^2 (the weights of the two other slots).  One
+// warp handles IPW consecutive (vertex, slot) items: first the CHI^2 elements of every item's
+// matrix, spread over the lanes, then one Jacobi SVD per item on its own group of GJ lanes,
+// so that up to 32 lanes share each FP64 instruction of the trace norms.
 template <int CHI, class Mode>
 __global__ void residual_kernel(const C<typename Mode::TS>* Gamma, const double* lam, const int4* vert_edges, int n,
                                 double* out) {
     constexpr int H = CHI * CHI * CHI, CC = CHI * CHI, GJ = CC / 2 > 0 ? CC / 2 : 1, WPB = 8;
-    __shared__ cd Dsm[WPB][CC];
+    constexpr int IPW = 32 / GJ > 0 ? 32 / GJ : 1;
+    static_assert(GJ * IPW <= 32 || IPW == 1, "items of one warp");
+    __shared__ cd Dsm[WPB][IPW][CC];
     const int wib = threadIdx.x / 32, lane = threadIdx.x & 31;
-    const int item = blockIdx.x * WPB + wib;
-    if (item >= 3 * n) return;
-    const int a = item / 3, s = item % 3;
-    const int4 ve = vert_edges[a];
-    const int es[3] = {ve.x, ve.y, ve.z};
-    if (es[s] < 0) return;
-    int o0, o1;
-    others_of(s, o0, o1);
-    const int ss = sstride<CHI>(s), s0 = sstride<CHI>(o0), s1 = sstride<CHI>(o1);
-    const C<typename Mode::TS>* g = Gamma + (size_t)a * 2 * H;
-    for (int r = lane; r < CC; r += 32) {
+    const int item0 = (blockIdx.x * WPB + wib) * IPW;
+    if (item0 >= 3 * n) return;   // the whole warp
+    for (int t = lane; t < IPW * CC; t += 32) {
+        const int q = t / CC, r = t % CC;
+        const int item = item0 + q;
+        if (item >= 3 * n) continue;
+        const int a = item / 3, s = item % 3;
+        const int4 ve = vert_edges[a];
+        const int es[3] = {ve.x, ve.y, ve.z};
+        if (es[s] < 0) continue;
+        int o0, o1;
+        others_of(s, o0, o1);
+        const int ss = sstride<CHI>(s), s0 = sstride<CHI>(o0), s1 = sstride<CHI>(o1);
+        const C<typename Mode::TS>* g = Gamma + (size_t)a * 2 * H;
         const int j = r / CHI, jp = r % CHI;
         cd acc = cd{0.0, 0.0};
         for (int i = 0; i < 2; ++i)
@@ -1628,22 +1638,32 @@ __global__ void residual_kernel(const C<typename Mode::TS>* Gamma, const double*
                 }
             }
         const double act = (j == jp && lam_get(lam, CHI, es[s], j) > 0.0) ? 1.0 : 0.0;
-        Dsm[wib][r] = cd{act - acc.x, -acc.y};
+        Dsm[wib][q][r] = cd{act - acc.x, -acc.y};
     }
     __syncwarp();
-    if (lane < GJ) {
+    const int q = lane / GJ, g = lane % GJ, item = item0 + q;
+    bool valid = q < IPW && item < 3 * n;
+    if (valid) {
+        const int4 ve = vert_edges[item / 3];
+        const int s = item % 3;
+        valid = (s == 0 ? ve.x : (s == 1 ? ve.y : ve.z)) >= 0;
+    }
+    if (valid) {   // the same for the GJ lanes of an item
         WarpGroup grp{group_mask<GJ>()};
-        jacobi_svd<CHI, double, WarpGroup, false>(Dsm[wib], nullptr, lane, grp, group_mask<CHI>(), 1e-15, 60, false);
-    }
-    __syncwarp();
-    if (lane == 0) {
-        double sacc = 0.0;
-        for (int cc = 0; cc < CHI; ++cc) {
-            double n2 = 0.0;
-            for (int r = 0; r < CHI; ++r) n2 += norm2(Dsm[wib][cc * CHI + r]);
-            sacc += nr_sqrt(n2);
+        // FP32 rotation angles with FP64-exact rotations and the quadratic stop, as in the
+        // exact trace norms of the BP distance (the singular values stay FP64-accurate)
+        jacobi_svd<CHI, double, WarpGroup, false, true>(Dsm[wib][q], nullptr, g, grp, group_mask<CHI>(), 1e-15, 60,
+                                                        false, nullptr, 3e-8);
+        grp.sync();
+        if (g == 0) {
+            double sacc = 0.0;
+            for (int cc = 0; cc < CHI; ++cc) {
+                double n2 = 0.0;
+                for (int r = 0; r < CHI; ++r) n2 += norm2(Dsm[wib][q][cc * CHI + r]);
+                sacc += nr_sqrt(n2);
+            }
+            atomicAdd(out, sacc);
         }
-        atomicAdd(out, sacc);
     }
 }
 

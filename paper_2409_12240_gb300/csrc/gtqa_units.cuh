@@ -101,9 +101,11 @@ template <class Mode>
 cudaError_t AuxUnit<Mode>::residual(int CHI, const void* G, const double* lam, const int4* ve, int n, double* out,
                                     cudaStream_t st) {
     return by_chi(CHI, cudaErrorInvalidValue, [&](auto k) {
-        constexpr int X = decltype(k)::value, WPB = 8;
-        residual_kernel<X, Mode><<<(3 * n + WPB - 1) / WPB, 32 * WPB, 0, st>>>((const C<typename Mode::TS>*)G, lam,
-                                                                             ve, n, out);
+        // WPB warps per block, each taking IPW (vertex, slot) items (as in residual_kernel)
+        constexpr int X = decltype(k)::value, WPB = 8, GJ = X * X / 2, IPW = 32 / GJ > 0 ? 32 / GJ : 1;
+        const int warps = (3 * n + IPW - 1) / IPW;
+        residual_kernel<X, Mode><<<(warps + WPB - 1) / WPB, 32 * WPB, 0, st>>>((const C<typename Mode::TS>*)G, lam,
+                                                                              ve, n, out);
         return cudaGetLastError();
     });
 }
