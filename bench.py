@@ -75,6 +75,10 @@ def parse(argv=None):
                    help="profiling case: anneal layers 1..K0, then one gates launch, one BP launch of 1 sweep "
                         "and, from the same state, one of 21 sweeps (warm start, no regauge); no timing")
     p.add_argument("--budget", type=float, default=20.0, help=argparse.SUPPRESS)
+    p.add_argument("--traffic-record", default=None, metavar="CSV",
+                   help="no GPU: write the traffic record of the phase kernels from an ncu CSV of "
+                        "'--ncu-case 1500' (dram__bytes_read.sum and dram__bytes_write.sum of its gates, two BP and "
+                        "regauge launches), tagged with the hash of the current kernel sources")
     p.add_argument("--chi-sweep", action="store_true",
                    help="the precision and bond-dimension sweep (n = 1000, chi in {2, 4, 8, 16}, FP64, mixed "
                         "and complex64, three coupling types): layers/s, BP sweeps and the error against FP64 per cell")
@@ -416,12 +420,8 @@ def kernel_traffic(kernel: str, mixed: bool, chi: int, sweeps_per_launch: float 
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    h = hashlib.sha256()
-    for p in TRAFFIC_SOURCES:
-        with open(p, "rb") as f:
-            h.update(f.read())
     r = rec.get("mixed" if mixed else "fp64")
-    if not r or r.get("sources_sha256") != h.hexdigest() or r.get("chi") != chi or kernel not in r:
+    if not r or r.get("sources_sha256") != sources_sha256() or r.get("chi") != chi or kernel not in r:
         return None
     k = r[kernel]
     if kernel == "bp_kernel":
@@ -1230,8 +1230,68 @@ def deg4_study(a):
                       "layers_timed": {"first": layers[0], "last": layers[-1]}}))
 
 
+TRAFFIC_CASE = 1500
+TRAFFIC_NCU = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
+               "-k regex:\"gates_kernel|bp_kernel|regauge_kernel\" -s 4500 -c 4 --csv --log-file traffic.csv "
+               f"python bench.py --ncu-case {TRAFFIC_CASE}")
+
+
+def sources_sha256() -> str:
+    h = hashlib.sha256()
+    for p in TRAFFIC_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_record(path: str) -> dict:
+    """Reads the ncu CSV of the four captured launches of `--ncu-case 1500` (mixed: the gates
+    launch of layer 1501, BP launches of 1 and 21 sweeps from the same state, the regauge) and
+    writes the per-launch DRAM bytes to the traffic record with the hash of the kernel sources.
+    The BP launch's bytes are split into a fixed part and a part per sweep."""
+    import csv
+    with open(path, newline="") as f:
+        rows = list(csv.reader(f))
+    head = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
+    cols = {name: j for j, name in enumerate(rows[head])}
+    launches: Dict[int, dict] = {}
+    for r in rows[head + 1:]:
+        if len(r) < len(cols) or r[cols["Metric Name"]] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        if r[cols["Metric Unit"]] not in ("byte", "bytes"):
+            raise ValueError(f"unexpected unit {r[cols['Metric Unit']]!r}: capture with --csv (base units)")
+        L = launches.setdefault(int(r[cols["ID"]]), {"kernel": r[cols["Kernel Name"]]})
+        L[r[cols["Metric Name"]]] = float(r[cols["Metric Value"]].replace(",", ""))
+    seq = [launches[i] for i in sorted(launches)]
+    names = [next(k for k in ("gates_kernel", "bp_kernel", "regauge_kernel") if k in L["kernel"]) for L in seq]
+    if names != ["gates_kernel", "bp_kernel", "bp_kernel", "regauge_kernel"]:
+        raise ValueError(f"expected the gates, two BP and the regauge launches, got {names}")
+    tot = [L["dram__bytes_read.sum"] + L["dram__bytes_write.sum"] for L in seq]
+    per_sweep = (tot[2] - tot[1]) / 20.0
+    rec = {"mixed": {
+        "chi": WL["chi"], "sources_sha256": sources_sha256(),
+        "case": f"python bench.py --ncu-case {TRAFFIC_CASE} (n=1000, chi=4, mixed, 3-colour schedule, gates in "
+                f"256-thread blocks; launches after layer {TRAFFIC_CASE})",
+        "command": TRAFFIC_NCU,
+        "gates_kernel": {"bytes_per_launch": tot[0]},
+        "bp_kernel": {"fixed_bytes": tot[1] - per_sweep, "bytes_per_sweep": per_sweep,
+                      "note": (f"1-sweep launch {seq[1]['dram__bytes_read.sum']:.0f} B read, "
+                               f"{seq[1]['dram__bytes_write.sum']:.0f} B write; 21-sweep launch "
+                               f"{seq[2]['dram__bytes_read.sum']:.0f} B read, {seq[2]['dram__bytes_write.sum']:.0f} B "
+                               "write; per sweep = the difference / 20, fixed = the 1-sweep launch minus one sweep: "
+                               "the sweeps run from L2")},
+        "regauge_kernel": {"bytes_per_launch": tot[3]}}}
+    with open(TRAFFIC_FILE, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    return rec
+
+
 def main():
     a = parse()
+    if a.traffic_record:
+        print(json.dumps(traffic_record(a.traffic_record)))
+        return
     if a.policy_study:
         policy_study(a)
         return

@@ -34,7 +34,7 @@ def _nvcc() -> str:
 
 
 def _deps() -> List[str]:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))]
     files.append(os.path.join(INCLUDE, "gtqa.h"))
     return files
 

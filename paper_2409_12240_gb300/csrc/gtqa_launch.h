@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "gtqa_anneal.cuh"
+#include "gtqa_aux.cuh"
 #include "gtqa_general.cuh"
 #include "gtqa_plain.cuh"
 #include <algorithm>
