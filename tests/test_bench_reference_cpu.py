@@ -79,3 +79,78 @@ def test_traffic_record_from_an_ncu_csv(tmp_path, monkeypatch):
         pass
     else:
         raise AssertionError("a capture of three launches was accepted")
+
+
+def test_study_modes_print_their_tables(monkeypatch, capsys):
+    """The bond-dimension sweep, regauge-policy and degree-4 study modes, run against a stand-in
+    of the library and of torch's CUDA events (no GPU): every cell of each table is present,
+    with rates from the events, sweeps from the statistics, and errors against the FP64 cell."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+    import bench
+    from paper_2409_12240_gb300 import gtqa as G
+
+    class Ev:
+        def __init__(self, **kw):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return 2.0   # ms per timed layer
+
+    class Ctx:
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *a):
+            return False
+
+    monkeypatch.setattr(torch.cuda, "Event", Ev)
+    monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: type("S", (), {"cuda_stream": 0})())
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: Ctx())
+    real_empty = torch.empty
+    monkeypatch.setattr(torch, "empty", lambda *a, **k: real_empty(16, dtype=torch.uint8))
+    sizes, sweeps, prec_of = {}, {"n": 0}, {}
+
+    def create(n, edges, J, h, chi, colour, opt=None):
+        sizes["n"] = n
+        prec_of["p"] = opt
+        return 1
+
+    def stats(s):
+        sweeps["n"] += 5
+        return {"bp_sweeps": sweeps["n"]}
+
+    def marginals(s):
+        n = sizes["n"]
+        rho = np.zeros((n, 2, 2), complex)
+        rho[:, 0, 0] = 0.7 + 1e-6 * (prec_of["p"] or 0)
+        rho[:, 1, 1] = 1 - rho[:, 0, 0]
+        return rho, np.ones(n, np.int8)
+
+    fakes = dict(load=lambda **k: None, gtqa_create=create, gtqa_options_init=lambda precision=0, **k: precision,
+                 gtqa_anneal=lambda *a: None, gtqa_anneal_graph=lambda *a: None, gtqa_anneal_policy=lambda *a: None,
+                 gtqa_trotter_layer=lambda *a: None, gtqa_residual=lambda s: 1e-3,
+                 gtqa_regauge_counts=lambda s: (0, 0), gtqa_stats=stats,
+                 gtqa_get_state=lambda s: (np.zeros(1), np.zeros(1), np.zeros(1)),
+                 gtqa_set_state=lambda s, a, b, c: None, gtqa_destroy=lambda s: None, gtqa_marginals=marginals)
+    for k, v in fakes.items():
+        monkeypatch.setattr(G, k, v)
+    bench.chi_sweep(None)
+    t = json.loads(capsys.readouterr().out)["chi_sweep"]
+    assert len(t) == 3 and all(list(c) == ["2", "4", "8", "16"] for c in t.values())
+    cell = t["J~N(0,1),h~N(0,0.1)"]["4"]
+    assert list(cell) == ["fp64", "mixed", "complex64"] and abs(cell["fp64"]["layers_per_s"] - 500.0) < 1e-9
+    assert "max_abs" not in cell["fp64"] and abs(cell["mixed"]["max_abs"] - 1e-6) < 1e-12
+    assert cell["mixed"]["bp_sweeps_per_layer"] == 5 / 40 and cell["mixed"]["sign_agreement"] == 1.0
+    bench.policy_study(None)
+    p = json.loads(capsys.readouterr().out)["policy_study"]
+    assert list(p) == ["300", "1500", "2800"] and p["300"]["R_after_gates"] == 1e-3
+    assert p["1500"]["threshold_0.01"]["against_every_layer"]["max_abs"] == 0.0
+    bench.deg4_study(None)
+    d = json.loads(capsys.readouterr().out)["deg4_study"]
+    assert list(d) == ["fp64", "mixed", "complex64"] and abs(d["complex64"]["layers_per_s"] - 500.0) < 1e-9
