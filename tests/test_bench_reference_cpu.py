@@ -154,3 +154,35 @@ def test_study_modes_print_their_tables(monkeypatch, capsys):
     bench.deg4_study(None)
     d = json.loads(capsys.readouterr().out)["deg4_study"]
     assert list(d) == ["fp64", "mixed", "complex64"] and abs(d["complex64"]["layers_per_s"] - 500.0) < 1e-9
+
+
+def test_roofline_arithmetic():
+    """The per-unit algorithmic counts of the bench against the method's cost table (edge gate
+    with truncation about 2.4e5 flops, Vidal-gauge step about 5.5e4, a directed BP message
+    48 chi^4 at chi = 4), and the roofline objects built from them: achieved work over the
+    measured time, frac against the binding pipe's peak, and the layer's sum."""
+    sys.path.insert(0, ROOT)
+    import bench
+    g64, g32 = bench.edge_gate_flops(4, False)
+    assert g32 == 0 and abs(g64 / 2.4e5 - 1) < 0.1
+    r64, r32 = bench.regauge_edge_flops(4, False)
+    assert r32 == 0 and abs(r64 / 5.5e4 - 1) < 0.15
+    assert bench.bp_sweep_flops(4, 1000, True) == 1000 * 3 * 48 * 4 ** 4
+    m64, m32 = bench.edge_gate_flops(4, True)
+    assert m64 < g64 and m32 > 0     # the mixed gate moves the SVD sweeps and Q applications to FP32
+    peaks = object.__new__(bench.Peaks)
+    peaks.sms, peaks.mhz, peaks.fp32_meas, peaks.fp64_meas = 152, 2070.0, 78.0, 1.25
+    peaks.fp32 = 152 * 128 * 2 * 2070e6 / 1e12
+    peaks.fp64 = 152 * 2 * 2 * 2070e6 / 1e12
+    # (launches, total ms, units processed over those launches)
+    prof = {"gates_kernel": (10, 3.0, 15000), "bp_kernel": (10, 4.0, 10000), "regauge_kernel": (10, 0.8, 15000)}
+    dlt = {"svd_pairs": 0, "svd_rotations": 0, "bp_sweeps": 650, "regauge_svd_sweeps": 0}
+    roofs = bench.rooflines(prof, dlt, 4, 1000, 1500, True, peaks, traffic=False)
+    bp = roofs["bp_kernel"]
+    assert bp["pipe"] == "fp32" and abs(bp["achieved"] - 650 * 3.6864e7 / 4e-3 / 1e12) < 1e-9
+    assert abs(bp["frac"] - bp["achieved"] / peaks.fp32) < 1e-12 and bp["us_per_sweep"] == 4000 / 650
+    ga = roofs["gates_kernel"]
+    assert ga["pipe"] == "fp64" and abs(ga["achieved"] - 15000 * m64 / 3e-3 / 1e12) < 1e-9
+    lay = bench.layer_roofline(roofs)
+    t_roof = sum(r["roofline_us_per_launch"] * 10 for r in roofs.values())
+    assert abs(lay["frac"] - t_roof / 7800.0) < 1e-12 and abs(lay["measured_us"] - 7800.0) < 1e-9
